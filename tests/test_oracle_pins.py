@@ -1,0 +1,248 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these re-types the oracle's formulas: each compares the oracle with a
+closed form, an invariant, a brute-force evaluation of Eq. 7, a round trip
+through Eq. 6, or a value printed in the paper.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_10295_gb300 import synth
+from tests import gauge
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ---------------------------------------------------------------- constants
+def test_omega_unit_matches_textbook_thz():
+    # sqrt(eV/(A^2 amu)) / (2 pi) = 15.633302 THz (standard conversion factor);
+    # h = 4.135667696e-15 eV s.
+    f_thz = 15.633302
+    h_ev_s = 4.135667696e-15
+    assert abs(oracle.OMEGA_UNIT_EV - f_thz * 1e12 * h_ev_s) < 1e-8
+
+
+# ---------------------------------------------------------------- phases
+def test_phase_properties():
+    rng = np.random.default_rng(1)
+    k = rng.random((50, 3))
+    R = rng.integers(-9, 10, size=(40, 3)).astype(np.int32)
+    P = oracle.phases(k, R)
+    assert np.allclose(np.abs(P), 1.0, atol=1e-15)
+    # R = 0 column is exactly 1
+    P0 = oracle.phases(k, np.zeros((1, 3), np.int32))
+    assert np.all(P0 == 1.0)
+    # periodic in k with period 1 (integer shift), product rule e^{ik.R}e^{ik'.R} = e^{i(k+k').R}
+    G = rng.integers(-3, 4, size=(50, 3))
+    assert np.abs(oracle.phases(k + G, R) - P).max() < 1e-12
+    k2 = rng.random((50, 3))
+    assert np.abs(oracle.phases(k, R) * oracle.phases(k2, R) - oracle.phases(k + k2, R)).max() < 1e-12
+    # explicit value: k=(1/4,0,0), R=(1,0,0) -> i
+    assert abs(oracle.phases(np.array([[0.25, 0, 0]]), np.array([[1, 0, 0]]))[0, 0] - 1j) < 1e-15
+
+
+# ---------------------------------------------------------------- hermiticity / ASR
+@pytest.mark.parametrize("box", [None, (synth.centred_range(4), synth.centred_range(4), synth.centred_range(4))])
+def test_hermiticity_and_asr(box):
+    wl = synth.make_workload("si_tiny", nq=8, nk=8, box=box, with_coupling=False)
+    # H(-R) = H(R)^dagger and Phi(-R) = Phi(R)^T imply Hermitian H(k), D(q)
+    Hk = oracle.hamiltonian_k(wl.kpts, wl.Re, wl.we, wl.H_Re)
+    assert np.abs(Hk - Hk.conj().transpose(0, 2, 1)).max() < 1e-14 * np.abs(Hk).max()
+    Dq = oracle.dynamical_matrix(wl.qpts, wl.Rp, wl.wp, wl.Phi_Rp, wl.masses)
+    assert np.abs(Dq - Dq.conj().transpose(0, 2, 1)).max() < 1e-14 * np.abs(Dq).max()
+    # ASR: three zero modes at Gamma, eigenvectors along sqrt(M) translations
+    D0 = oracle.dynamical_matrix(np.zeros((1, 3)), wl.Rp, wl.wp, wl.Phi_Rp, wl.masses)[0]
+    lam, e = np.linalg.eigh(D0)
+    assert np.all(np.abs(lam[:3]) <= 1e-12 * lam[-1])
+    assert lam[3] > 1e-6 * lam[-1]
+    m = np.repeat(wl.masses, 3)
+    for a in range(3):
+        t = np.zeros(3 * wl.na)
+        t[a::3] = np.sqrt(m[a::3])
+        t /= np.linalg.norm(t)
+        # translation lies in the zero-mode subspace
+        assert np.linalg.norm(e[:, :3].conj().T @ t) > 1 - 1e-10
+    # spring model is positive semidefinite at every q
+    om, _, _ = oracle.phonon_eigen(Dq, wl.masses)
+    assert np.all(om >= -1e-6 * om.max())
+
+
+# ---------------------------------------------------------------- closed forms
+def test_one_band_chain_closed_form():
+    eps0, t = 0.37, -1.25
+    R = np.array([[-1, 0, 0], [0, 0, 0], [1, 0, 0]], np.int32)
+    H = np.array([t, eps0, t], dtype=np.complex128).reshape(3, 1, 1)
+    k = np.stack([np.linspace(0, 1, 41), np.zeros(41), np.zeros(41)], -1)
+    eps, _ = oracle.electron_eigen(oracle.hamiltonian_k(k, R, np.ones(3), H))
+    assert np.abs(eps[:, 0] - (eps0 + 2 * t * np.cos(2 * np.pi * k[:, 0]))).max() < 1e-14
+
+
+def test_spring_chain_closed_form():
+    K, M = 3.7, 28.0855
+    R = np.array([[-1, 0, 0], [0, 0, 0], [1, 0, 0]], np.int32)
+    Phi = np.zeros((3, 3, 3))
+    Phi[1, 0, 0] = 2 * K
+    Phi[0, 0, 0] = Phi[2, 0, 0] = -K
+    q = np.stack([np.linspace(0, 1, 37), np.zeros(37), np.zeros(37)], -1)
+    om, _, _ = oracle.phonon_eigen(oracle.dynamical_matrix(q, R, np.ones(3), Phi, [M]), [M])
+    # y, z modes carry no springs: zero; the x mode is the textbook chain
+    expect = 2 * np.sqrt(K / M) * np.abs(np.sin(np.pi * q[:, 0])) * 0.0646541513
+    assert np.abs(om[:, 2] - expect).max() < 1e-9 * expect.max()
+    assert np.abs(om[:, :2]).max() < 1e-12
+
+
+def _plane_wave_inputs(nb=4, na=2, seed=3):
+    rng = np.random.default_rng(seed)
+    R = synth.box_vectors(range(-1, 2), range(-1, 2), range(0, 1))
+    ne = len(R)
+    nm = 3 * na
+    masses = np.array([12.0, 31.0][:na])
+    # H nonzero only at R=0: H0 = Q diag(1..nb) Q^H with Q the unitary DFT matrix
+    Q = np.exp(2j * np.pi * np.outer(np.arange(nb), np.arange(nb)) / nb) / np.sqrt(nb)
+    H = np.zeros((ne, nb, nb), np.complex128)
+    i0 = int(np.where((R == 0).all(1))[0][0])
+    H[i0] = Q @ np.diag(np.arange(1.0, nb + 1)) @ Q.conj().T
+    # Phi nonzero only at R=0, diagonal with D = Phi/M ascending and distinct
+    dvals = np.arange(1.0, nm + 1) * 0.7
+    Phi = np.zeros((ne, nm, nm))
+    Phi[i0] = np.diag(dvals * np.repeat(masses, 3))
+    e0, p0 = 5, 2          # Re0 index, Rp0 index
+    Gt = rng.standard_normal((nm, nb, nb)) + 1j * rng.standard_normal((nm, nb, nb))
+    gW = np.zeros((ne, nm, ne, nb, nb), np.complex128)
+    gW[p0, :, e0] = Gt
+    we = rng.uniform(0.5, 1.5, ne)
+    wp = rng.uniform(0.5, 1.5, ne)
+
+    class A:
+        pass
+    a = A()
+    a.H_Re, a.Phi_Rp, a.g_ReRp, a.Re, a.Rp, a.we, a.wp, a.masses = H, Phi, gW, R, R, we, wp, masses
+    return a, Q, Gt, e0, p0, dvals, i0
+
+
+def test_single_R_plane_wave_closed_form():
+    a, Q, Gt, e0, p0, dvals, i0 = _plane_wave_inputs()
+    rng = np.random.default_rng(4)
+    k = rng.random((7, 3))
+    q = rng.random((5, 3))
+    eps_k, eps_kq, omega, g = oracle.interpolate(a, k, q)
+    nb = Q.shape[0]
+    # H(k) = we(0) H0 and D(q) = wp(0) Phi0/M at every point
+    assert np.abs(eps_k - a.we[i0] * np.arange(1.0, nb + 1)).max() < 1e-13
+    assert np.abs(omega - np.sqrt(a.wp[i0] * dvals) * 0.0646541513).max() < 1e-9
+    m = np.repeat(a.masses, 3)
+    # |g_mn nu| = we0 wp0 |(Q^H Gt_nu Q)_mn| / sqrt(M_nu); the phase of g(k,q)/g(0,0)
+    # is exactly e^{2 pi i (k.Re0 + q.Rp0)} (same gauge at every point).
+    QGQ = np.einsum("am,vab,bn->vmn", Q.conj(), Gt, Q)
+    expect_abs = a.we[e0] * a.wp[p0] * np.abs(QGQ) / np.sqrt(m)[:, None, None]
+    assert np.abs(np.abs(g) - expect_abs[None, None]).max() < 1e-12
+    _, _, _, g00 = oracle.interpolate(a, np.zeros((1, 3)), np.zeros((1, 3)))
+    ph = np.exp(2j * np.pi * (k @ a.Re[e0])[None, :] + 2j * np.pi * (q @ a.Rp[p0])[:, None])
+    assert np.abs(g - ph[:, :, None, None, None] * g00[0, 0][None, None]).max() < 1e-12
+
+
+# ---------------------------------------------------------------- factorisation vs Eq. 7
+def test_nested_equals_single_loop():
+    wl = synth.make_workload("si_tiny", nb=3, nk=6, nq=5)
+    eps_k, eps_kq, omega, g, ev = oracle.interpolate(wl, return_eigvecs=True)
+    for iq in range(len(wl.qpts)):
+        for ik in range(len(wl.kpts)):
+            ref = oracle.g_single_loop(wl.kpts[ik], wl.qpts[iq], wl.Re, wl.we, wl.Rp, wl.wp, wl.g_ReRp,
+                                       ev["V_k"][ik], ev["V_kq"][iq, ik], ev["u"][iq])
+            assert np.abs(g[iq, ik] - ref).max() < 1e-13 * max(1.0, np.abs(ref).max())
+
+
+# ---------------------------------------------------------------- Wannier round trip (Eq. 7 then Eq. 6)
+def test_wannier_round_trip():
+    wl = synth.make_workload("si_tiny")
+    coarse = synth.uniform_grid(3, 3, 3)          # the 3x3x3 BvK grid of the [-1,1]^3 box
+    eps_k, eps_kq, omega, g, ev = oracle.interpolate(wl, coarse, coarse, return_eigvecs=True)
+    rec = oracle.g_bloch_to_wannier(coarse, coarse, wl.Re, wl.Rp, g, ev["V_k"], ev["V_kq"], ev["u"])
+    assert np.abs(rec - wl.g_ReRp).max() < 1e-12 * np.abs(wl.g_ReRp).max()
+
+
+# ---------------------------------------------------------------- gauge-free invariants
+def test_unitarity_invariant_and_periodicity():
+    wl = synth.make_workload("si_tiny", nk=9, nq=4)
+    eps_k, eps_kq, omega, g, ev = oracle.interpolate(wl, return_eigvecs=True)
+    G1 = oracle.g_rp_to_q(wl.qpts, wl.Rp, wl.wp, wl.g_ReRp)
+    P = oracle.phases(wl.kpts, wl.Re, wl.we)
+    for iq in range(4):
+        Gk = np.einsum("ke,cemn->kcmn", P, G1[iq])
+        Gv = np.einsum("cv,kcmn->kvmn", ev["u"][iq], Gk)
+        lhs = (np.abs(g[iq]) ** 2).sum((-1, -2))
+        rhs = (np.abs(Gv) ** 2).sum((-1, -2))
+        assert np.abs(lhs - rhs).max() < 1e-12 * rhs.max()
+    # periodicity g(k+G, q+G') equals g(k,q) on gauge-invariant subspace sums
+    rng = np.random.default_rng(5)
+    Gk_shift = rng.integers(-2, 3, size=wl.kpts.shape)
+    Gq_shift = rng.integers(-2, 3, size=wl.qpts.shape)
+    e2k, e2kq, om2, g2 = oracle.interpolate(wl, wl.kpts + Gk_shift, wl.qpts + Gq_shift)
+    assert gauge.max_rel_S(g2, g, eps_k, eps_kq, omega) < 1e-11
+    assert gauge.max_rel_eps(e2k, eps_k) < 1e-13
+
+
+def test_linearity_in_coupling():
+    wl = synth.make_workload("si_tiny", nk=5, nq=3)
+    rng = np.random.default_rng(6)
+    _, _, _, g1, ev = oracle.interpolate(wl, return_eigvecs=True)
+    import copy
+    wl2 = copy.copy(wl)
+    extra = rng.standard_normal(wl.g_ReRp.shape) + 1j * rng.standard_normal(wl.g_ReRp.shape)
+    wl2.g_ReRp = extra
+    _, _, _, g2 = oracle.interpolate(wl2)
+    wl3 = copy.copy(wl)
+    alpha = 0.3 - 1.7j
+    wl3.g_ReRp = wl.g_ReRp + alpha * extra
+    _, _, _, g3 = oracle.interpolate(wl3)
+    # same H, Phi -> same eigenvectors (deterministic), so g is linear elementwise
+    assert np.abs(g3 - (g1 + alpha * g2)).max() < 1e-12 * np.abs(g3).max()
+
+
+# ---------------------------------------------------------------- adjoint
+def test_adjoint_central_differences_and_euler():
+    wl = synth.make_workload("si_tiny", nb=4, nk=6, nq=3)
+    eps_k, _, _, _ = oracle.interpolate(wl)
+    w_nk, _ = oracle.fermi_weights(eps_k, 2)
+    L, grad = oracle.loss_and_grad(wl, wl.kpts, wl.qpts, w_nk, 1e-6)
+    # Euler: L is homogeneous of degree 2 in gW -> Re<grad, gW> = 2L
+    assert abs(np.real(np.vdot(grad, wl.g_ReRp)) - 2 * L) < 1e-12 * abs(L)
+    import copy
+    rng = np.random.default_rng(7)
+    flat = wl.g_ReRp.reshape(-1)
+    idx = rng.choice(flat.size, size=25, replace=False)
+    h = 1e-6
+    for i in idx:
+        for part, unit in (("re", 1.0), ("im", 1j)):
+            plus = copy.copy(wl)
+            minus = copy.copy(wl)
+            gp = flat.copy()
+            gm = flat.copy()
+            gp[i] += unit * h
+            gm[i] -= unit * h
+            plus.g_ReRp = gp.reshape(wl.g_ReRp.shape)
+            minus.g_ReRp = gm.reshape(wl.g_ReRp.shape)
+            _, _, om, gpl = oracle.interpolate(plus)
+            _, _, _, gmi = oracle.interpolate(minus)
+            d = (oracle.loss(gpl, om, w_nk, 1e-6) - oracle.loss(gmi, om, w_nk, 1e-6)) / (2 * h)
+            ref = grad.reshape(-1)[i].real if part == "re" else grad.reshape(-1)[i].imag
+            assert abs(d - ref) <= 1e-6 * max(1.0, np.abs(grad).max())
+
+
+# ---------------------------------------------------------------- paper-printed values
+def test_table3_sizes_and_cost_ratio():
+    rows = [list(map(float, l.split())) for l in open(os.path.join(HERE, "golden", "zsnr_gw_sizes.txt"))
+            if l.strip() and not l.startswith("#")]
+    for w, nb, nm, ne, np_, size in rows:
+        gib = 16 * nb * nb * nm * ne * np_ / 2 ** 30
+        # printed with 2 significant digits (1 decimal below 10)
+        assert abs(gib - size) <= max(0.05, 0.005 * size) + 0.5 * (size >= 10), (w, gib, size)
+    # Eq. 12: NL/SL ratio for silicon is about 1/93 when Nk >> Np
+    nb, nm, ne, np_, nk = 8, 6, 617, 93, 10 ** 6
+    sl = (nb * nb * nm * ne * np_ + nb * nb * nm * ne + 2 * nb * nb * nm + nb * nb * nm * nm) * nk
+    nl = nb * nb * nm * ne * np_ + (nb * nb * nm * ne + 2 * nb * nb * nm + nb * nb * nm * nm) * nk
+    assert abs(sl / nl - 93) < 1.0
