@@ -1,0 +1,170 @@
+/*
+ * libeph: Wannier interpolation of electron-phonon matrix elements on one GB300.
+ *
+ * The library computes, for fine k and q points, the quantities of the paper's
+ * nested-loop algorithm (arxiv 2603.10295, section "Analysis of computational
+ * complexity", Eqs. 9-10, which refactor the interpolation formula Eq. 7):
+ *
+ *   eps_nk, U_k       eigenpairs of H(k)   = sum_Re w_e e^{i k.Re} H(Re)
+ *   omega_qnu, e_qnu  eigenpairs of D(q)   = sum_Rp w_p e^{i q.Rp} Phi(Rp)/sqrt(M M')
+ *   g(Re,q)           = sum_Rp e^{i q.Rp} g(Re,Rp)                          (Eq. 9)
+ *   g_mnnu(k,q)       = sum U_{mm',k+q} U*_{nn',k} u_{ka,nu}(q) e^{i k.Re} g(Re,q)   (Eq. 10)
+ *
+ * Conventions:
+ *   - e^{i k.R} = exp(2 pi i sum_j k_j n_j), k in crystal (reciprocal-basis)
+ *     coordinates, R = (n1,n2,n3) integer lattice coordinates; the argument is
+ *     formed in FP64 and reduced exactly (t - rint(t)) before sincospi.
+ *   - U_{nn'k} = conj(V_k[n'][n]) where V_k holds the eigenvectors of H(k) as
+ *     columns in ascending eigenvalue order, so g_nu(k,q) = V_{k+q}^H G V_k.
+ *   - u_{ka,nu}(q) = e_{ka,nu}(q)/sqrt(M_kappa) (M in amu), index ka = 3*kappa+alpha.
+ *   - omega = sign(lambda) sqrt(|lambda|) * hbar sqrt(eV/(A^2 amu)) in eV.
+ *   - complex numbers are (re, im) pairs of doubles (complex128) or floats (complex64).
+ *
+ * Errors: every entry point returns EPH_OK (0) or a negative code; a per-context
+ * message is available from eph_last_error.  Nothing exits or throws across
+ * the ABI.  A context is not thread-safe: calls on one context must not run
+ * concurrently; they are ordered on the context's CUDA stream.
+ */
+#ifndef EPH_H
+#define EPH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eph_ctx eph_ctx;
+
+enum eph_status {
+  EPH_OK = 0,
+  EPH_EINVAL = -1,    /* bad argument: NULL pointer, non-positive or unsupported size */
+  EPH_ENOMEM = -2,    /* device allocation failed */
+  EPH_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+  EPH_ENOTCONV = -4,  /* a batched Jacobi eigensolve hit its sweep cap */
+  EPH_ESTATE = -5,    /* call out of order (e.g. eph_interp_q before eph_set_k) */
+  EPH_ENOTSUP = -6    /* size or form not supported by this build */
+};
+
+enum eph_form {
+  EPH_FORM_FP64 = 0,  /* every contraction in FP64 (DFMA) */
+  EPH_FORM_MIXED = 1  /* Re->k contraction as split-precision tensor-core products, FP32 accumulation;
+                         phases, H(k)/H(k+q)/D(q) and their eigensolves stay FP64 */
+};
+
+typedef struct eph_options {
+  int form;          /* enum eph_form */
+  int device_ptrs;   /* 0: k/q lists and outputs are host pointers (the call copies and
+                        synchronises); 1: they are device pointers (CUDA-visible memory) */
+  int q_batch;       /* q points per internal batch, 0 = automatic */
+  int k_tile;        /* k points per internal tile, 0 = automatic (bounded by workspace_mb) */
+  int max_sweeps;    /* Jacobi sweep cap, 0 = default (20) */
+  int workspace_mb;  /* soft cap on the per-call workspace in MiB, 0 = default (4096) */
+} eph_options;
+
+/* Fills *opt with the defaults (FP64 form, host pointers, automatic batching). */
+void eph_default_options(eph_options* opt);
+
+/*
+ * Creates a context on the current CUDA device and uploads the Wannier-space
+ * data (paper Eq. 3 and the electron/phonon Wannier Hamiltonians).
+ *
+ *   nb, na           Wannier functions and atoms per cell; nm = 3*na modes.
+ *   ne, np           number of electron (Re) and phonon (Rp) lattice vectors.
+ *   H_Re    [ne][nb][nb] complex128, eV      H(Re) = <w_m0|H|w_nRe>
+ *   Phi_Rp  [np][nm][nm] double, eV/A^2     force constants Phi_{ka,k'b}(Rp)
+ *   g_ReRp  [np][nm][ne][nb][nb] complex128, eV   g_{m'n'ka}(Re,Rp) (Eq. 3),
+ *                                           16*nb*nb*nm*ne*np bytes (Table 3 caption)
+ *   Re [ne][3], Rp [np][3]  integer lattice coordinates
+ *   we [ne], wp [np]        per-vector weights (Wigner-Seitz degeneracies); NULL = all 1
+ *   masses [na]             amu
+ *   opt                     NULL = defaults
+ *   cuda_stream             cudaStream_t to order all work on; NULL = a stream the
+ *                           context creates and owns
+ * All inputs are HOST pointers; they are copied and may be freed on return.
+ * Supported sizes: 1 <= nb <= 16 and 1 <= nm <= 16 (batched warp Jacobi);
+ * larger sizes return EPH_ENOTSUP.  On success *out owns device memory until
+ * eph_destroy.
+ */
+int eph_create(eph_ctx** out, int nb, int na, int ne, int np,
+               const double* H_Re, const double* Phi_Rp, const double* g_ReRp,
+               const int* Re, const double* we, const int* Rp, const double* wp,
+               const double* masses, const eph_options* opt, void* cuda_stream);
+
+/*
+ * Sets the fine k list: phases e^{i k.Re}, H(k) and its batched FP64
+ * eigensolve stay resident on the device for later eph_interp_q calls.
+ *   kpts  [nk][3] crystal coordinates        (host or device, see device_ptrs)
+ *   eps_k [nk][nb] eV ascending, may be NULL (host or device)
+ */
+int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k);
+
+/*
+ * Interpolates for nq q points against the resident k list (paper Eqs. 9-10
+ * with the D(q) and H(k+q) eigensolves).
+ *   qpts   [nq][3] crystal coordinates
+ *   eps_kq [nq][nk][nb] eV (eigenvalues of H(k+q)), may be NULL
+ *   omega  [nq][nm] eV, may be NULL
+ *   g      [nq][nk][nm][nb][nb]: complex128 in the FP64 form, complex64 in the
+ *          mixed form; may be NULL (then only eps_kq/omega are produced)
+ * Returns EPH_ESTATE if eph_set_k has not been called.
+ */
+int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g);
+
+/* eph_set_k followed by eph_interp_q. */
+int eph_interp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
+               double* eps_k, double* eps_kq, double* omega, void* g);
+
+/*
+ * Scalar L = sum_{q,k,nu,m,n} w_nk |g_mnnu(k,q)|^2 / omega_qnu over modes with
+ * omega_qnu > omega_min, and its gradient with respect to g(Re,Rp) with the
+ * eigenvectors U and e held fixed (hand-written adjoint of Eqs. 9-10; the
+ * Re->k stage is recomputed, never stored).
+ *   w_nk         [nk][nb] weights (host or device per device_ptrs)
+ *   L_out        one double (host or device)
+ *   grad_g_ReRp  [np][nm][ne][nb][nb] complex128, dL/dRe(g) + i dL/dIm(g)
+ *                (the PyTorch convention for a real scalar of complex inputs)
+ * Uses the k list given here (it replaces the resident one).
+ */
+int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
+                        const double* w_nk, double omega_min, double* L_out, double* grad_g_ReRp);
+
+/* Releases every device resource of the context (NULL is a no-op). */
+void eph_destroy(eph_ctx* ctx);
+
+/* Static description of a status code. */
+const char* eph_strerror(int code);
+
+/* Message of the last failing call on this context ("" if none). */
+const char* eph_last_error(const eph_ctx* ctx);
+
+/* Number of kernels this context has launched since creation (instrumentation). */
+long long eph_kernel_launches(const eph_ctx* ctx);
+
+/* Stages of the pipeline, for per-stage kernel timing. */
+enum eph_stage {
+  EPH_STAGE_PHASE = 0, /* phase factors e^{i k.R} (exact FP64 reduction + sincospi)             */
+  EPH_STAGE_FT_Q = 1,  /* Rp->q contraction of g (Eq. 9) and D(q)                              */
+  EPH_STAGE_EIG = 2,   /* batched Hermitian Jacobi eigensolves of H(k), H(k+q), D(q)            */
+  EPH_STAGE_MODE = 3,  /* mode rotation by u(q), phonon post-processing, per-q operand assembly */
+  EPH_STAGE_FT_K = 4,  /* Re->k contraction (Eq. 10 Fourier sum) fused with H(k+q)              */
+  EPH_STAGE_BAND = 5,  /* band rotation V_{k+q}^H G V_k                                         */
+  EPH_STAGE_ADJ = 6,   /* adjoint (backward) kernels                                            */
+  EPH_NSTAGES = 8
+};
+
+/*
+ * enable != 0: every kernel the context launches is bracketed by CUDA events
+ * on the context's stream and its duration is added to its stage when the
+ * call completes.  eph_profile_read returns the accumulated milliseconds and
+ * launch count of one stage; eph_profile_reset clears them.
+ */
+int eph_profile(eph_ctx* ctx, int enable);
+int eph_profile_read(const eph_ctx* ctx, int stage, double* ms, long long* launches);
+int eph_profile_reset(eph_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPH_H */

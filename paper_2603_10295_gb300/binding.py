@@ -1,0 +1,222 @@
+"""ctypes binding of libeph (argument marshalling only).
+
+The names follow the C-ABI in include/eph.h: eph_create, eph_set_k,
+eph_interp_q, eph_interp, eph_interp_backward, eph_destroy.  Every step of the
+computation runs in the library's CUDA kernels; this module only converts
+numpy arrays / torch tensors to pointers.  If the shared library is missing,
+loading fails loudly: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libeph.so")
+
+EPH_OK, EPH_EINVAL, EPH_ENOMEM, EPH_ECUDA, EPH_ENOTCONV, EPH_ESTATE, EPH_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+FORMS = {"fp64": 0, "mixed": 1}
+
+#: every symbol declared in include/eph.h
+EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "eph_interp",
+           "eph_interp_backward", "eph_destroy", "eph_strerror", "eph_last_error", "eph_kernel_launches",
+           "eph_profile", "eph_profile_read", "eph_profile_reset")
+STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj")
+
+
+class EphOptions(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int), ("device_ptrs", ctypes.c_int), ("q_batch", ctypes.c_int),
+                ("k_tile", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("workspace_mb", ctypes.c_int)]
+
+
+class EphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libeph error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Loads libeph.so (raises if it has not been built: no fallback exists)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libeph is not built ({p} missing); run `python -m paper_2603_10295_gb300.build_lib`")
+    lib = ctypes.CDLL(p)
+    vp, ip, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.eph_default_options.argtypes = [ctypes.POINTER(EphOptions)]
+    lib.eph_default_options.restype = None
+    lib.eph_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, dp, dp, dp, vp, dp, vp, dp, dp,
+                               ctypes.POINTER(EphOptions), vp]
+    lib.eph_create.restype = i
+    lib.eph_set_k.argtypes = [vp, i, dp, dp]
+    lib.eph_set_k.restype = i
+    lib.eph_interp_q.argtypes = [vp, i, dp, dp, dp, vp]
+    lib.eph_interp_q.restype = i
+    lib.eph_interp.argtypes = [vp, i, dp, i, dp, dp, dp, dp, vp]
+    lib.eph_interp.restype = i
+    lib.eph_interp_backward.argtypes = [vp, i, dp, i, dp, dp, d, dp, dp]
+    lib.eph_interp_backward.restype = i
+    lib.eph_destroy.argtypes = [vp]
+    lib.eph_destroy.restype = None
+    lib.eph_strerror.argtypes = [i]
+    lib.eph_strerror.restype = ctypes.c_char_p
+    lib.eph_last_error.argtypes = [vp]
+    lib.eph_last_error.restype = ctypes.c_char_p
+    lib.eph_kernel_launches.argtypes = [vp]
+    lib.eph_kernel_launches.restype = ctypes.c_longlong
+    lib.eph_profile.argtypes = [vp, i]
+    lib.eph_profile.restype = i
+    lib.eph_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    lib.eph_profile_read.restype = i
+    lib.eph_profile_reset.argtypes = [vp]
+    lib.eph_profile_reset.restype = i
+    del ip
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Pointer of a contiguous numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to libeph must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to libeph must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+class Context:
+    """One eph_ctx: Wannier data resident on the current CUDA device.
+
+    host mode (device_ptrs=False): k/q lists and outputs are numpy arrays;
+    device mode (device_ptrs=True): they are CUDA torch tensors (or raw device
+    pointers as ints) and calls are ordered on `stream`.
+    """
+
+    def __init__(self, nb, na, H_Re, Phi_Rp, g_ReRp, Re, Rp, masses, we=None, wp=None, form="fp64",
+                 device_ptrs=False, q_batch=0, k_tile=0, max_sweeps=0, workspace_mb=0, stream=None):
+        self.lib = load_library()
+        self.nb, self.na, self.nm = int(nb), int(na), 3 * int(na)
+        H_Re = np.ascontiguousarray(H_Re, dtype=np.complex128)
+        Phi_Rp = np.ascontiguousarray(Phi_Rp, dtype=np.float64)
+        g_ReRp = np.ascontiguousarray(g_ReRp, dtype=np.complex128)
+        Re = np.ascontiguousarray(Re, dtype=np.int32)
+        Rp = np.ascontiguousarray(Rp, dtype=np.int32)
+        masses = np.ascontiguousarray(masses, dtype=np.float64)
+        we = None if we is None else np.ascontiguousarray(we, dtype=np.float64)
+        wp = None if wp is None else np.ascontiguousarray(wp, dtype=np.float64)
+        self.ne, self.np_ = len(Re), len(Rp)
+        self.form = form
+        self.device_ptrs = bool(device_ptrs)
+        opt = EphOptions()
+        self.lib.eph_default_options(ctypes.byref(opt))
+        opt.form = FORMS[form]
+        opt.device_ptrs = int(device_ptrs)
+        opt.q_batch, opt.k_tile, opt.max_sweeps, opt.workspace_mb = q_batch, k_tile, max_sweeps, workspace_mb
+        handle = ctypes.c_void_p()
+        st = None
+        if stream is not None:
+            st = stream if isinstance(stream, int) else int(stream.cuda_stream)
+        rc = self.lib.eph_create(ctypes.byref(handle), self.nb, self.na, self.ne, self.np_, _ptr(H_Re),
+                                 _ptr(Phi_Rp), _ptr(g_ReRp), _ptr(Re), _ptr(we), _ptr(Rp), _ptr(wp), _ptr(masses),
+                                 ctypes.byref(opt), st)
+        if rc != EPH_OK:
+            raise EphError(rc, self.lib.eph_strerror(rc).decode())
+        self.handle = handle
+        self.nk = 0
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        return cls(wl.nb, wl.na, wl.H_Re, wl.Phi_Rp, wl.g_ReRp, wl.Re, wl.Rp, wl.masses, wl.we, wl.wp, **kw)
+
+    def _check(self, rc):
+        if rc != EPH_OK:
+            raise EphError(rc, self.lib.eph_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.eph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launches(self) -> int:
+        return int(self.lib.eph_kernel_launches(self.handle))
+
+    def profile(self, enable=True):
+        self._check(self.lib.eph_profile(self.handle, int(bool(enable))))
+
+    def profile_reset(self):
+        self._check(self.lib.eph_profile_reset(self.handle))
+
+    def profile_read(self):
+        """{stage: (milliseconds, launches)} accumulated since the last reset."""
+        out = {}
+        for i, name in enumerate(STAGES):
+            ms = ctypes.c_double()
+            n = ctypes.c_longlong()
+            self._check(self.lib.eph_profile_read(self.handle, i, ctypes.byref(ms), ctypes.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
+    # -- raw calls (buffers already allocated by the caller) -----------------
+    def eph_set_k(self, nk, kpts, eps_k=None):
+        self._check(self.lib.eph_set_k(self.handle, int(nk), _ptr(kpts), _ptr(eps_k)))
+        self.nk = int(nk)
+
+    def eph_interp_q(self, nq, qpts, eps_kq=None, omega=None, g=None):
+        self._check(self.lib.eph_interp_q(self.handle, int(nq), _ptr(qpts), _ptr(eps_kq), _ptr(omega), _ptr(g)))
+
+    def eph_interp_backward(self, nk, kpts, nq, qpts, w_nk, omega_min, L_out, grad):
+        self._check(self.lib.eph_interp_backward(self.handle, int(nk), _ptr(kpts), int(nq), _ptr(qpts), _ptr(w_nk),
+                                                 float(omega_min), _ptr(L_out), _ptr(grad)))
+
+    # -- host-mode conveniences (numpy in, numpy out) ----------------------
+    def set_k(self, kpts):
+        kpts = np.ascontiguousarray(kpts, dtype=np.float64)
+        eps_k = np.empty((len(kpts), self.nb))
+        self.eph_set_k(len(kpts), kpts, eps_k)
+        return eps_k
+
+    def interp_q(self, qpts, want_g=True):
+        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
+        nq = len(qpts)
+        eps_kq = np.empty((nq, self.nk, self.nb))
+        omega = np.empty((nq, self.nm))
+        g = None
+        if want_g:
+            dt = np.complex128 if self.form == "fp64" else np.complex64
+            g = np.empty((nq, self.nk, self.nm, self.nb, self.nb), dtype=dt)
+        self.eph_interp_q(nq, qpts, eps_kq, omega, g)
+        return eps_kq, omega, g
+
+    def interp(self, kpts, qpts, want_g=True):
+        eps_k = self.set_k(kpts)
+        eps_kq, omega, g = self.interp_q(qpts, want_g)
+        return eps_k, eps_kq, omega, g
+
+    def loss_and_grad(self, kpts, qpts, w_nk, omega_min):
+        kpts = np.ascontiguousarray(kpts, dtype=np.float64)
+        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
+        w_nk = np.ascontiguousarray(w_nk, dtype=np.float64)
+        L = np.zeros(1)
+        grad = np.empty((self.np_, self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
+        self.eph_interp_backward(len(kpts), kpts, len(qpts), qpts, w_nk, omega_min, L, grad)
+        return float(L[0]), grad

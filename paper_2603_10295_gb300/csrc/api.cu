@@ -1,0 +1,510 @@
+// C-ABI of libeph: context, resident Wannier data and the per-call pipeline of
+// the nested-loop interpolation (paper Eqs. 9-10, Fig. 1b):
+//
+//   eph_set_k     P_k = e^{i k.Re} w_e;  H(k) = P_k H(Re);  Jacobi -> eps_k, V_k
+//   eph_interp_q  per q batch:  P_q(Rp), e^{i q.Re};  D(q) -> Jacobi -> omega, u
+//                 G1 = P_q(Rp) g(Re,Rp)                        (Eq. 9, Rp -> q)
+//                 W_q = [ e^{i q.Re} H(Re) | u^T G1 ]          (mode rotation)
+//                 per k tile:  Y = P_k W_q  gives H(k+q) and G3 in one FP64 GEMM
+//                              Jacobi(H(k+q)) -> eps_kq, V_{k+q}
+//                              g = V_{k+q}^H G3_nu V_k          (band rotation)
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "eph.h"
+#include "eph_kernels.cuh"
+
+using eph::launch_band_rotate;
+using eph::launch_jacobi;
+using eph::launch_mode_rotate;
+using eph::launch_phase;
+using eph::launch_phonon_post;
+using eph::launch_scale_rows;
+using eph::launch_skinny;
+using eph::launch_skinny_real;
+using eph::launch_zgemm;
+
+namespace {
+
+struct DBuf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace
+
+struct eph_ctx {
+  int nb = 0, na = 0, nm = 0, ne = 0, np = 0;
+  eph_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  double omega_unit = 0.0;
+  // resident Wannier-space data
+  double2* H = nullptr;        // [ne][nb*nb]
+  double* Phi = nullptr;       // [np][nm*nm]
+  double* dscale = nullptr;    // [nm*nm]  1/sqrt(M_k M_k')
+  double* invsqrtm = nullptr;  // [nm]
+  double2* gW = nullptr;       // [np][nm*ne*nb*nb]
+  int* Re = nullptr;
+  int* Rp = nullptr;
+  double* we = nullptr;
+  double* wp = nullptr;
+  int* status = nullptr;
+  // resident k list
+  int nk = 0;
+  bool k_ready = false;
+  DBuf kpts, Pk, eps_k, Uk, Hk_tmp;
+  // per-call workspace
+  DBuf qpts, Qe, Pp, D, lamq, evq, omq, uq, G1, W, Y, eps_tile, Ukq, g_stage;
+  long long launches = 0;
+  std::string err;
+  // per-stage event timing
+  bool prof = false;
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  double stage_ms[EPH_NSTAGES] = {};
+  long long stage_n[EPH_NSTAGES] = {};
+};
+
+namespace {
+
+int fail(eph_ctx* c, int code, const char* what, cudaError_t e = cudaSuccess) {
+  if (c) {
+    char buf[512];
+    if (e != cudaSuccess)
+      snprintf(buf, sizeof buf, "%s: %s (%s)", eph_strerror(code), what, cudaGetErrorString(e));
+    else
+      snprintf(buf, sizeof buf, "%s: %s", eph_strerror(code), what);
+    c->err = buf;
+  }
+  return code;
+}
+
+int ensure(eph_ctx* c, DBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.n >= bytes) return EPH_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.n = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, EPH_ENOMEM, "workspace allocation", e);
+  }
+  b.n = bytes;
+  return EPH_OK;
+}
+
+void release(DBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.n = 0;
+}
+
+template <class T>
+T* as(DBuf& b) {
+  return static_cast<T*>(b.p);
+}
+
+cudaEvent_t take_event(eph_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// After the stream has drained: fold pending event pairs into the stage totals.
+void collect_profile(eph_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->stage_ms[p.stage] += ms;
+      c->stage_n[p.stage] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->pool.push_back(p.a);
+    c->pool.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+double omega_unit_ev() {
+  // hbar sqrt(eV / (A^2 amu)) in eV, CODATA 2018 values
+  const double hbar = 1.054571817e-34, ev = 1.602176634e-19, amu = 1.66053906660e-27, ang = 1e-10;
+  return hbar * std::sqrt(ev / (ang * ang * amu)) / ev;
+}
+
+}  // namespace
+
+#define EPH_CK(call)                                              \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return fail(ctx, EPH_ECUDA, #call, e_); \
+  } while (0)
+#define EPH_LAUNCH_S(stage, call)                                 \
+  do {                                                            \
+    cudaEvent_t ea_ = nullptr, eb_ = nullptr;                     \
+    if (ctx->prof) {                                              \
+      ea_ = take_event(ctx);                                      \
+      eb_ = take_event(ctx);                                      \
+      if (ea_) cudaEventRecord(ea_, ctx->stream);                 \
+    }                                                             \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return fail(ctx, EPH_ECUDA, #call, e_); \
+    ++ctx->launches;                                              \
+    if (ea_ && eb_) {                                             \
+      cudaEventRecord(eb_, ctx->stream);                          \
+      ctx->pending.push_back({(stage), ea_, eb_});                \
+    }                                                             \
+  } while (0)
+#define EPH_TRY(call)           \
+  do {                          \
+    int r_ = (call);            \
+    if (r_ != EPH_OK) return r_; \
+  } while (0)
+
+extern "C" {
+
+void eph_default_options(eph_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof *opt);
+  opt->form = EPH_FORM_FP64;
+}
+
+const char* eph_strerror(int code) {
+  switch (code) {
+    case EPH_OK: return "ok";
+    case EPH_EINVAL: return "invalid argument";
+    case EPH_ENOMEM: return "out of device memory";
+    case EPH_ECUDA: return "CUDA error";
+    case EPH_ENOTCONV: return "eigensolver did not converge";
+    case EPH_ESTATE: return "call out of order";
+    case EPH_ENOTSUP: return "not supported";
+    default: return "unknown status";
+  }
+}
+
+const char* eph_last_error(const eph_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+long long eph_kernel_launches(const eph_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int eph_profile(eph_ctx* ctx, int enable) {
+  if (!ctx) return EPH_EINVAL;
+  ctx->prof = enable != 0;
+  return EPH_OK;
+}
+
+int eph_profile_read(const eph_ctx* ctx, int stage, double* ms, long long* launches) {
+  if (!ctx || stage < 0 || stage >= EPH_NSTAGES) return EPH_EINVAL;
+  if (ms) *ms = ctx->stage_ms[stage];
+  if (launches) *launches = ctx->stage_n[stage];
+  return EPH_OK;
+}
+
+int eph_profile_reset(eph_ctx* ctx) {
+  if (!ctx) return EPH_EINVAL;
+  for (int i = 0; i < EPH_NSTAGES; ++i) {
+    ctx->stage_ms[i] = 0.0;
+    ctx->stage_n[i] = 0;
+  }
+  return EPH_OK;
+}
+
+void eph_destroy(eph_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  void* ptrs[] = {ctx->H, ctx->Phi, ctx->dscale, ctx->invsqrtm, ctx->gW, ctx->Re, ctx->Rp, ctx->we, ctx->wp, ctx->status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  DBuf* bufs[] = {&ctx->kpts, &ctx->Pk, &ctx->eps_k, &ctx->Uk, &ctx->Hk_tmp, &ctx->qpts, &ctx->Qe, &ctx->Pp,
+                  &ctx->D, &ctx->lamq, &ctx->evq, &ctx->omq, &ctx->uq, &ctx->G1, &ctx->W, &ctx->Y,
+                  &ctx->eps_tile, &ctx->Ukq, &ctx->g_stage};
+  for (DBuf* b : bufs) release(*b);
+  for (auto& p : ctx->pending) {
+    ctx->pool.push_back(p.a);
+    ctx->pool.push_back(p.b);
+  }
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re, const double* Phi_Rp,
+               const double* g_ReRp, const int* Re, const double* we, const int* Rp, const double* wp,
+               const double* masses, const eph_options* opt, void* cuda_stream) {
+  if (!out) return EPH_EINVAL;
+  *out = nullptr;
+  if (nb < 1 || na < 1 || ne < 1 || np < 1 || !H_Re || !Phi_Rp || !g_ReRp || !Re || !Rp || !masses)
+    return EPH_EINVAL;
+  eph_ctx* ctx = new eph_ctx();
+  ctx->nb = nb;
+  ctx->na = na;
+  ctx->nm = 3 * na;
+  ctx->ne = ne;
+  ctx->np = np;
+  if (opt)
+    ctx->opt = *opt;
+  else
+    eph_default_options(&ctx->opt);
+  if (ctx->opt.max_sweeps <= 0) ctx->opt.max_sweeps = 20;
+  if (ctx->opt.workspace_mb <= 0) ctx->opt.workspace_mb = 4096;
+  int rc = EPH_OK;
+  const int nm = ctx->nm, nb2 = nb * nb;
+  auto bail = [&](int code) {
+    eph_destroy(ctx);
+    return code;
+  };
+  if (ctx->opt.form != EPH_FORM_FP64) {
+    fail(ctx, EPH_ENOTSUP, "only the FP64 form is available in this build");
+    return bail(EPH_ENOTSUP);
+  }
+  if (nb > 16 || nm > 16) return bail(EPH_ENOTSUP);
+  for (int i = 0; i < na; ++i)
+    if (!(masses[i] > 0.0)) return bail(EPH_EINVAL);
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(EPH_ECUDA);
+    ctx->own_stream = true;
+  }
+  ctx->omega_unit = omega_unit_ev();
+  const size_t szH = (size_t)ne * nb2 * sizeof(double2);
+  const size_t szPhi = (size_t)np * nm * nm * sizeof(double);
+  const size_t szG = (size_t)np * nm * ne * nb2 * sizeof(double2);
+  struct Up {
+    void** dst;
+    const void* src;
+    size_t n;
+  };
+  double* dsc = new double[(size_t)nm * nm];
+  double* ism = new double[nm];
+  double* wones_e = new double[ne];
+  double* wones_p = new double[np];
+  for (int a = 0; a < nm; ++a) {
+    ism[a] = 1.0 / std::sqrt(masses[a / 3]);
+    for (int b = 0; b < nm; ++b) dsc[a * nm + b] = 1.0 / std::sqrt(masses[a / 3] * masses[b / 3]);
+  }
+  for (int i = 0; i < ne; ++i) wones_e[i] = we ? we[i] : 1.0;
+  for (int i = 0; i < np; ++i) wones_p[i] = wp ? wp[i] : 1.0;
+  Up ups[] = {{(void**)&ctx->H, H_Re, szH},
+              {(void**)&ctx->Phi, Phi_Rp, szPhi},
+              {(void**)&ctx->gW, g_ReRp, szG},
+              {(void**)&ctx->Re, Re, (size_t)ne * 3 * sizeof(int)},
+              {(void**)&ctx->Rp, Rp, (size_t)np * 3 * sizeof(int)},
+              {(void**)&ctx->we, wones_e, (size_t)ne * sizeof(double)},
+              {(void**)&ctx->wp, wones_p, (size_t)np * sizeof(double)},
+              {(void**)&ctx->dscale, dsc, (size_t)nm * nm * sizeof(double)},
+              {(void**)&ctx->invsqrtm, ism, (size_t)nm * sizeof(double)}};
+  for (Up& u : ups) {
+    cudaError_t e = cudaMalloc(u.dst, u.n);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rc = EPH_ENOMEM;
+      break;
+    }
+    e = cudaMemcpy(*u.dst, u.src, u.n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      rc = EPH_ECUDA;
+      break;
+    }
+  }
+  delete[] dsc;
+  delete[] ism;
+  delete[] wones_e;
+  delete[] wones_p;
+  if (rc != EPH_OK) return bail(rc);
+  if (cudaMalloc(&ctx->status, sizeof(int)) != cudaSuccess || cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess)
+    return bail(EPH_ENOMEM);
+  *out = ctx;
+  return EPH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Copies n bytes from a caller pointer (host or device per opt) into a device buffer.
+int stage_in(eph_ctx* ctx, DBuf& b, const void* src, size_t n, const void** dev) {
+  if (ctx->opt.device_ptrs) {
+    *dev = src;
+    return EPH_OK;
+  }
+  EPH_TRY(ensure(ctx, b, n));
+  EPH_CK(cudaMemcpyAsync(b.p, src, n, cudaMemcpyHostToDevice, ctx->stream));
+  *dev = b.p;
+  return EPH_OK;
+}
+
+cudaMemcpyKind out_kind(const eph_ctx* ctx) {
+  return ctx->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+int finish(eph_ctx* ctx) {
+  int h = 0;
+  EPH_CK(cudaMemcpyAsync(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  EPH_CK(cudaStreamSynchronize(ctx->stream));
+  collect_profile(ctx);
+  if (h) {
+    cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return fail(ctx, EPH_ENOTCONV, "a batched Jacobi eigensolve reached the sweep cap");
+  }
+  return EPH_OK;
+}
+
+}  // namespace
+
+extern "C" int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k) {
+  if (!ctx) return EPH_EINVAL;
+  if (nk < 1 || !kpts) return fail(ctx, EPH_EINVAL, "eph_set_k: nk < 1 or kpts NULL");
+  ctx->k_ready = false;
+  const int nb = ctx->nb, ne = ctx->ne, nb2 = nb * nb;
+  const void* dk = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->kpts, kpts, (size_t)nk * 3 * sizeof(double), &dk));
+  if (ctx->opt.device_ptrs) {  // keep a private copy: the k list must outlive the caller's buffer
+    EPH_TRY(ensure(ctx, ctx->kpts, (size_t)nk * 3 * sizeof(double)));
+    EPH_CK(cudaMemcpyAsync(ctx->kpts.p, dk, (size_t)nk * 3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  EPH_TRY(ensure(ctx, ctx->Pk, (size_t)nk * ne * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->eps_k, (size_t)nk * nb * sizeof(double)));
+  EPH_TRY(ensure(ctx, ctx->Uk, (size_t)nk * nb2 * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->Hk_tmp, (size_t)nk * nb2 * sizeof(double2)));
+  EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(as<double>(ctx->kpts), nk, ctx->Re, ctx->we, ne, as<double2>(ctx->Pk), ne, ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nk, nb2, ne, as<double2>(ctx->Pk), ne, 0, ctx->H, nb2, 0, as<double2>(ctx->Hk_tmp), nb2, 0,
+                          1, ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(as<double2>(ctx->Hk_tmp), nb2, nb, nb, nk, as<double>(ctx->eps_k), nb,
+                           as<double2>(ctx->Uk), nb2, ctx->opt.max_sweeps, ctx->status, ctx->stream));
+  if (eps_k)
+    EPH_CK(cudaMemcpyAsync(eps_k, ctx->eps_k.p, (size_t)nk * nb * sizeof(double), out_kind(ctx), ctx->stream));
+  int rc = finish(ctx);
+  if (rc != EPH_OK) return rc;
+  ctx->nk = nk;
+  ctx->k_ready = true;
+  return EPH_OK;
+}
+
+extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
+  if (!ctx) return EPH_EINVAL;
+  if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
+  if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
+  const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, np = ctx->np, nk = ctx->nk;
+  const int nb2 = nb * nb;
+  const long NW = (long)nb2 * (1 + nm);  // columns of W_q: H part | G2 part
+  const long gcols = (long)nm * nb2;      // g elements per (q,k)
+  int QB = ctx->opt.q_batch > 0 ? ctx->opt.q_batch : 4;
+  if (QB > 16) QB = 16;
+  if (QB > nq) QB = nq;
+  const bool host = !ctx->opt.device_ptrs;
+  // bytes per (q,k) pair in the k stage
+  const size_t per_pair = (size_t)NW * 16 + (size_t)nb2 * 16 + (size_t)nb * 8 + (host && g ? (size_t)gcols * 16 : 0);
+  const size_t budget = (size_t)ctx->opt.workspace_mb << 20;
+  long KT = ctx->opt.k_tile > 0 ? ctx->opt.k_tile : (long)(budget / (per_pair * QB));
+  if (KT > nk) KT = nk;
+  if (KT > 64) KT -= KT % 64;
+  if (KT < 1) KT = 1;
+
+  const void* dq = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
+  EPH_TRY(ensure(ctx, ctx->Qe, (size_t)QB * ne * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->Pp, (size_t)QB * np * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->D, (size_t)QB * nm * nm * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->lamq, (size_t)QB * nm * sizeof(double)));
+  EPH_TRY(ensure(ctx, ctx->evq, (size_t)QB * nm * nm * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->omq, (size_t)QB * nm * sizeof(double)));
+  EPH_TRY(ensure(ctx, ctx->uq, (size_t)QB * nm * nm * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->G1, (size_t)QB * nm * ne * nb2 * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->W, (size_t)QB * ne * NW * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->Y, (size_t)QB * KT * NW * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->eps_tile, (size_t)QB * KT * nb * sizeof(double)));
+  EPH_TRY(ensure(ctx, ctx->Ukq, (size_t)QB * KT * nb2 * sizeof(double2)));
+  if (host && g) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)QB * KT * gcols * sizeof(double2)));
+
+  const double* qdev = static_cast<const double*>(dq);
+  double2* Qe = as<double2>(ctx->Qe);
+  double2* Pp = as<double2>(ctx->Pp);
+  double2* W = as<double2>(ctx->W);
+  double2* Y = as<double2>(ctx->Y);
+  for (int q0 = 0; q0 < nq; q0 += QB) {
+    const int nqb = (nq - q0 < QB) ? nq - q0 : QB;
+    const double* qb = qdev + 3L * q0;
+    // phases for the batch: e^{i q.Re} (unweighted: P_k carries w_e) and w_p e^{i q.Rp}
+    EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(qb, nqb, ctx->Re, nullptr, ne, Qe, ne, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(qb, nqb, ctx->Rp, ctx->wp, np, Pp, np, ctx->stream));
+    // D(q), eigenpairs, omega and u = e / sqrt(M)
+    EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny_real(nqb, (long)nm * nm, np, Pp, np, ctx->Phi, (long)nm * nm, ctx->dscale,
+                                  as<double2>(ctx->D), (long)nm * nm, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(as<double2>(ctx->D), (long)nm * nm, nm, nm, nqb, as<double>(ctx->lamq), nm,
+                             as<double2>(ctx->evq), (long)nm * nm, ctx->opt.max_sweeps, ctx->status, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_MODE, launch_phonon_post(as<double>(ctx->lamq), as<double2>(ctx->evq), nqb, nm, ctx->invsqrtm,
+                                  ctx->omega_unit, as<double>(ctx->omq), as<double2>(ctx->uq), ctx->stream));
+    if (omega)
+      EPH_CK(cudaMemcpyAsync(omega + (long)q0 * nm, ctx->omq.p, (size_t)nqb * nm * sizeof(double), out_kind(ctx),
+                             ctx->stream));
+    // Eq. 9: G1 = sum_Rp w_p e^{i q.Rp} g(Re,Rp)
+    const long X = (long)nm * ne * nb2;
+    EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, X, np, Pp, np, ctx->gW, X, as<double2>(ctx->G1), X, ctx->stream));
+    // W_q = [ e^{i q.Re} H(Re) | mode-rotated G1 ], row e of length NW
+    EPH_LAUNCH_S(EPH_STAGE_MODE, launch_scale_rows(Qe, nqb, ctx->H, ne, nb2, W, NW, (long)ne * NW, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_MODE, launch_mode_rotate(as<double2>(ctx->G1), as<double2>(ctx->uq), nqb, nm, ne, nb2, W + nb2, NW,
+                                  (long)ne * NW, ctx->stream));
+    for (long k0 = 0; k0 < nk; k0 += KT) {
+      const int nkt = (int)((nk - k0 < KT) ? nk - k0 : KT);
+      // Y[q][k] = sum_Re w_e e^{i k.Re} W_q[Re]: H(k+q) (first nb^2 columns) and G3 (rest)
+      EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nkt, (int)NW, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0, W, NW, (long)ne * NW, Y, NW,
+                              (long)nkt * NW, nqb, ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(Y, NW, nb, nb, (long)nqb * nkt, as<double>(ctx->eps_tile), nb, as<double2>(ctx->Ukq),
+                               nb2, ctx->opt.max_sweeps, ctx->status, ctx->stream));
+      if (eps_kq)
+        for (int iq = 0; iq < nqb; ++iq)  // one contiguous copy per q (rows of the tile)
+          EPH_CK(cudaMemcpyAsync(eps_kq + ((long)(q0 + iq) * nk + k0) * nb,
+                                 as<double>(ctx->eps_tile) + (long)iq * nkt * nb, (size_t)nkt * nb * sizeof(double),
+                                 out_kind(ctx), ctx->stream));
+      if (g) {
+        double2* gout = static_cast<double2*>(g);
+        if (host) {
+          EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, NW, as<double2>(ctx->Ukq), as<double2>(ctx->Uk) + k0 * nb2, nqb,
+                                        nkt, nm, nb, as<double2>(ctx->g_stage), (long)nkt * gcols, ctx->stream));
+          for (int iq = 0; iq < nqb; ++iq)
+            EPH_CK(cudaMemcpyAsync(gout + ((long)(q0 + iq) * nk + k0) * gcols,
+                                   as<double2>(ctx->g_stage) + (long)iq * nkt * gcols,
+                                   (size_t)nkt * gcols * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+        } else {
+          EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, NW, as<double2>(ctx->Ukq), as<double2>(ctx->Uk) + k0 * nb2, nqb,
+                                        nkt, nm, nb, gout + ((long)q0 * nk + k0) * gcols, (long)nk * gcols,
+                                        ctx->stream));
+        }
+      }
+    }
+  }
+  return finish(ctx);
+}
+
+extern "C" int eph_interp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts, double* eps_k,
+                          double* eps_kq, double* omega, void* g) {
+  int rc = eph_set_k(ctx, nk, kpts, eps_k);
+  if (rc != EPH_OK) return rc;
+  return eph_interp_q(ctx, nq, qpts, eps_kq, omega, g);
+}
+
+extern "C" int eph_interp_backward(eph_ctx* ctx, int, const double*, int, const double*, const double*, double, double*,
+                                   double*) {
+  if (!ctx) return EPH_EINVAL;
+  return fail(ctx, EPH_ENOTSUP, "eph_interp_backward is not available in this build");
+}

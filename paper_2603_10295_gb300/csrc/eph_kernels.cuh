@@ -1,0 +1,61 @@
+// Internal launch interface of the libeph CUDA kernels (sm_103a).
+// Every launcher enqueues on `st` and returns cudaGetLastError() of the launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eph {
+
+// ---- complex helpers (double2 / float2 = re, im) ---------------------------
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// ---- phases (paper Eq. 7 factors e^{i k.Re}, e^{i q.Rp}) --------------------
+// P[i*ldp + r] = w[r] * exp(2 pi i pts_i . R_r); w may be null (weight 1).
+cudaError_t launch_phase(const double* pts, int n, const int* R, const double* w, int nR,
+                         double2* P, long ldp, cudaStream_t st);
+// B[q][e][j] = Q[q][e] * H[e][j] for j < cols; output row stride ldb, batch stride sB.
+cudaError_t launch_scale_rows(const double2* Q, int nq, const double2* H, int ne, int cols,
+                              double2* B, long ldb, long sB, cudaStream_t st);
+
+// ---- FP64 complex GEMM: C[b] = A[b] * B[b], row-major -----------------------
+// A: M x K (lda, batch stride sA, may be 0), B: K x N (ldb, sB), C: M x N (ldc, sC).
+cudaError_t launch_zgemm(int M, int N, int K, const double2* A, long lda, long sA,
+                         const double2* B, long ldb, long sB, double2* C, long ldc, long sC,
+                         int batch, cudaStream_t st);
+// Adjoint form C[b] = A[b]^H * B[b] (A stored M_A x K_A = K x M), accumulate if acc.
+cudaError_t launch_zgemm_ah(int M, int N, int K, const double2* A, long lda, long sA,
+                            const double2* B, long ldb, long sB, double2* C, long ldc, long sC,
+                            int batch, int acc, cudaStream_t st);
+// Skinny rows: C[m][x] = sum_r P[m][r] * B[r][x], m < M <= 16 (P row stride ldp).
+cudaError_t launch_skinny(int M, long N, int K, const double2* P, long ldp, const double2* B, long ldb,
+                          double2* C, long ldc, cudaStream_t st);
+// Skinny with real right operand (force constants): C[m][x] = sum_r P[m][r] * Breal[r][x] * s[x]
+cudaError_t launch_skinny_real(int M, long N, int K, const double2* P, long ldp, const double* B,
+                               long ldb, const double* colscale, double2* C, long ldc, cudaStream_t st);
+
+// ---- batched Hermitian eigensolver (cyclic parallel Jacobi, FP64) -----------
+// A[b] at A + b*sA (n x n, row stride lda); eigenvalues ascending to w + b*sw,
+// eigenvectors as columns to V + b*sV (n x n, row stride n). n <= 16.
+// status: device int, OR-ed with 1 if a matrix hit max_sweeps.
+cudaError_t launch_jacobi(const double2* A, long sA, long lda, int n, long batch, double* w, long sw,
+                          double2* V, long sV, int max_sweeps, int* status, cudaStream_t st);
+
+// ---- phonon post-processing: omega = sign(l) sqrt|l| * unit; u = e / sqrt(M)
+cudaError_t launch_phonon_post(const double* lam, const double2* e, int nq, int nm, const double* invsqrtm,
+                               double unit, double* omega, double2* u, cudaStream_t st);
+
+// ---- mode rotation: G2[q][e][nu][b] = sum_c u[q][c][nu] G1[q][c][e][b] -----------
+// G2 written with row stride ldw (per e) and batch stride sW, starting at column 0.
+cudaError_t launch_mode_rotate(const double2* G1, const double2* u, int nq, int nm, int ne, int nb2,
+                               double2* W, long ldw, long sW, cudaStream_t st);
+
+// ---- band rotation: g[q][k][nu] = Ukq[q][k]^H G3[q][k][nu] Uk[k] ---------------
+// G3 rows: Y + (q*nk + k)*ldy (nm*nb*nb complex per row); Ukq [q][k][nb][nb];
+// Uk [k][nb][nb]; output g + q*sgq + k*nm*nb*nb.
+cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq,
+                               int nk, int nm, int nb, double2* g, long sgq, cudaStream_t st);
+
+}  // namespace eph

@@ -1,0 +1,149 @@
+// Rotations of Eq. 10 and phonon post-processing (FP64).
+//   mode rotation  G2[q][Re][nu][b] = sum_{ka} u_{ka,nu}(q) G1[q][ka][Re][b]
+//                  (applied once per q, before the Re sum, with which it commutes)
+//   band rotation  g[q][k][nu] = V_{k+q}^H G3[q][k][nu] V_k   (U_{mm',k+q} U*_{nn',k})
+//   phonons        omega = sign(l) sqrt|l| * hbar sqrt(eV/(A^2 amu)), u = e / sqrt(M)
+#include "eph_kernels.cuh"
+
+namespace eph {
+
+__global__ void k_phonon_post(const double* __restrict__ lam, const double2* __restrict__ e, int nq, int nm,
+                              const double* __restrict__ invsqrtm, double unit, double* __restrict__ omega,
+                              double2* __restrict__ u) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long tot = (long)nq * nm * nm;
+  if (idx >= tot) return;
+  int q = (int)(idx / ((long)nm * nm));
+  int rem = (int)(idx - (long)q * nm * nm);
+  int r = rem / nm, nu = rem - r * nm;
+  double2 ev = e[idx];
+  double s = invsqrtm[r];
+  u[idx] = make_double2(ev.x * s, ev.y * s);
+  if (r == 0) {
+    double l = lam[(long)q * nm + nu];
+    omega[(long)q * nm + nu] = copysign(sqrt(fabs(l)), l) * unit;
+  }
+}
+
+cudaError_t launch_phonon_post(const double* lam, const double2* e, int nq, int nm, const double* invsqrtm,
+                               double unit, double* omega, double2* u, cudaStream_t st) {
+  long tot = (long)nq * nm * nm;
+  if (tot <= 0) return cudaSuccess;
+  k_phonon_post<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(lam, e, nq, nm, invsqrtm, unit, omega, u);
+  return cudaGetLastError();
+}
+
+// One thread per (q, e, b): reads the nm values G1[q][:][e][b] (coalesced over b),
+// writes the nm rotated values.  u[q] is staged in shared memory.
+template <int NMX>
+__global__ void __launch_bounds__(256) k_mode_rotate(const double2* __restrict__ G1, const double2* __restrict__ u,
+                                                     int nm, int ne, int nb2, double2* __restrict__ W, long ldw,
+                                                     long sW) {
+  __shared__ double2 us[NMX * NMX];
+  const int q = blockIdx.y;
+  for (int t = threadIdx.x; t < nm * nm; t += blockDim.x) us[t] = u[(long)q * nm * nm + t];
+  __syncthreads();
+  const long per_q = (long)ne * nb2;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= per_q) return;
+  const int e = (int)(idx / nb2);
+  const int b = (int)(idx - (long)e * nb2);
+  double2 acc[NMX];
+#pragma unroll
+  for (int v = 0; v < NMX; ++v) acc[v] = make_double2(0.0, 0.0);
+  const double2* src = G1 + (long)q * nm * per_q + (long)e * nb2 + b;
+  for (int c = 0; c < nm; ++c) {
+    const double2 gv = src[(long)c * per_q];
+#pragma unroll
+    for (int v = 0; v < NMX; ++v) {
+      if (v < nm) {
+        const double2 uv = us[c * nm + v];
+        acc[v].x = fma(uv.x, gv.x, fma(-uv.y, gv.y, acc[v].x));
+        acc[v].y = fma(uv.x, gv.y, fma(uv.y, gv.x, acc[v].y));
+      }
+    }
+  }
+  double2* dst = W + (long)q * sW + (long)e * ldw + b;
+#pragma unroll
+  for (int v = 0; v < NMX; ++v)
+    if (v < nm) dst[(long)v * nb2] = acc[v];
+}
+
+cudaError_t launch_mode_rotate(const double2* G1, const double2* u, int nq, int nm, int ne, int nb2, double2* W,
+                               long ldw, long sW, cudaStream_t st) {
+  if (nq <= 0) return cudaSuccess;
+  if (nm > 16 || nq > 65535) return cudaErrorInvalidValue;
+  long per_q = (long)ne * nb2;
+  dim3 grid((unsigned)((per_q + 255) / 256), nq);
+  k_mode_rotate<16><<<grid, 256, 0, st>>>(G1, u, nm, ne, nb2, W, ldw, sW);
+  return cudaGetLastError();
+}
+
+// One CTA per (q,k) pair: stage V_k, V_{k+q} and the nm nb x nb blocks of G3 in
+// shared memory, T = G3_nu V_k, then g_nu = V_{k+q}^H T (2 nb^3 nm CMAC per pair).
+__global__ void __launch_bounds__(128) k_band_rotate(const double2* __restrict__ Y, long ldy,
+                                                     const double2* __restrict__ Ukq,
+                                                     const double2* __restrict__ Uk, int nk, int nm, int nb,
+                                                     double2* __restrict__ g, long sgq) {
+  extern __shared__ double2 sm[];
+  const int nb2 = nb * nb;
+  double2* uk = sm;
+  double2* ukq = uk + nb2;
+  double2* G = ukq + nb2;
+  double2* T = G + nm * nb2;
+  const long pair = blockIdx.x;  // q*nk + k
+  const int k = (int)(pair % nk);
+  const long q = pair / nk;
+  const double2* grow = Y + pair * ldy;
+  for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
+    uk[t] = Uk[(long)k * nb2 + t];
+    ukq[t] = Ukq[pair * nb2 + t];
+  }
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) G[t] = grow[t];
+  __syncthreads();
+  // T[nu][a][n] = sum_b G[nu][a][b] uk[b][n]
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2;
+    const int a = rem / nb, n = rem - a * nb;
+    const double2* gr = G + nu * nb2 + a * nb;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b = 0; b < nb; ++b) {
+      const double2 x = gr[b], y = uk[b * nb + n];
+      acc.x = fma(x.x, y.x, fma(-x.y, y.y, acc.x));
+      acc.y = fma(x.x, y.y, fma(x.y, y.x, acc.y));
+    }
+    T[t] = acc;
+  }
+  __syncthreads();
+  // g[nu][m][n] = sum_a conj(ukq[a][m]) T[nu][a][n]
+  double2* out = g + q * sgq + (long)k * nm * nb2;
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2;
+    const int m = rem / nb, n = rem - m * nb;
+    const double2* tc = T + nu * nb2 + n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int a = 0; a < nb; ++a) {
+      const double2 x = ukq[a * nb + m], y = tc[a * nb];
+      acc.x = fma(x.x, y.x, fma(x.y, y.y, acc.x));
+      acc.y = fma(x.x, y.y, fma(-x.y, y.x, acc.y));
+    }
+    out[t] = acc;
+  }
+}
+
+cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
+                               int nm, int nb, double2* g, long sgq, cudaStream_t st) {
+  long pairs = (long)nq * nk;
+  if (pairs <= 0) return cudaSuccess;
+  size_t smem = (size_t)(2 * nb * nb + 2 * nm * nb * nb) * sizeof(double2);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_band_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
+  k_band_rotate<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq);
+  return cudaGetLastError();
+}
+
+}  // namespace eph

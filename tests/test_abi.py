@@ -1,0 +1,67 @@
+"""Host-side checks of the C-ABI library: it builds, loads, exports every
+symbol that include/eph.h declares, and rejects bad arguments before touching
+the GPU.  No compute call is made here (no GPU on this host)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2603_10295_gb300 import binding, build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(binding.LIB_PATH):
+        build_lib.build()
+    return binding.load_library()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "eph.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(eph_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_binding_exports():
+    assert header_functions() == sorted(binding.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True).stdout
+    syms = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    for name in header_functions():
+        assert name in syms, name
+        assert hasattr(lib, name)
+
+
+def test_status_strings(lib):
+    for code in range(0, -7, -1):
+        s = lib.eph_strerror(code)
+        assert s and s != b"unknown status"
+    assert lib.eph_strerror(-99) == b"unknown status"
+
+
+def test_create_rejects_bad_arguments_without_gpu(lib):
+    h = ctypes.c_void_p()
+    opt = binding.EphOptions()
+    lib.eph_default_options(ctypes.byref(opt))
+    assert opt.form == 0 and opt.device_ptrs == 0
+    # NULL inputs and non-positive sizes are rejected before any CUDA call
+    assert lib.eph_create(ctypes.byref(h), 0, 1, 1, 1, None, None, None, None, None, None, None, None,
+                          ctypes.byref(opt), None) == binding.EPH_EINVAL
+    assert lib.eph_create(ctypes.byref(h), 4, 1, 1, 1, None, None, None, None, None, None, None, None,
+                          ctypes.byref(opt), None) == binding.EPH_EINVAL
+    assert not h.value
+    assert lib.eph_set_k(None, 1, None, None) == binding.EPH_EINVAL
+    assert lib.eph_interp_q(None, 1, None, None, None, None) == binding.EPH_EINVAL
+    lib.eph_destroy(None)
+    assert lib.eph_last_error(None) == b""
+
+
+def test_product_path_has_no_fallback(tmp_path):
+    with pytest.raises(RuntimeError):
+        binding.load_library(str(tmp_path / "missing.so"))
