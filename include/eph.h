@@ -163,6 +163,38 @@ int eph_profile(eph_ctx* ctx, int enable);
 int eph_profile_read(const eph_ctx* ctx, int stage, double* ms, long long* launches);
 int eph_profile_reset(eph_ctx* ctx);
 
+/*
+ * Band energies and eigenvectors of H(k) = sum_Re w_e e^{i k.Re} H(Re) for a
+ * k list, computed without any device allocation by the library.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- processes whose device memory is owned by another allocator
+ * (a framework's caching allocator that reserved the HBM up front, an
+ * embedding application with a fixed budget) and latency-sensitive callers
+ * that must not trigger the device-wide synchronisation cudaMalloc/cudaFree
+ * can cause.  It runs the same kernels as eph_set_k, with their scratch
+ * (the phases and the H(k) matrices) in one fixed device array of
+ * EPH_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.
+ *
+ *   kpts [nk][3] f64, Re [ne][3] int32, we [ne] f64 (NULL = all 1),
+ *   H_Re [ne][nb][nb] complex128: DEVICE pointers, read only.
+ *   eps  [nk][nb] f64 ascending, U [nk][nb][nb] complex128 (eigenvectors as
+ *   columns): DEVICE pointers, written.
+ *   max_sweeps: Jacobi sweep cap, <= 0 = 20.  cuda_stream: stream to run on (NULL = legacy default).
+ * Limits: 1 <= nb <= 16 and scratch = round_up(16*nk*ne, 256) + 16*nk*nb*nb
+ * bytes <= EPH_NOALLOC_SCRATCH_BYTES, else EPH_EINVAL before any GPU work.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  The call synchronises the
+ * stream to report the eigensolver status (EPH_ENOTCONV at the sweep cap).
+ * All calls share the one array and it keeps the last call's contents: calls
+ * that overlap on the GPU (other streams or host threads on the same device)
+ * race and must be serialised by the caller.
+ */
+#define EPH_NOALLOC_SCRATCH_BYTES (32u << 20)
+int eph_bands_noalloc(int nk, const double* kpts, int nb, int ne, const int* Re, const double* we,
+                      const double* H_Re, double* eps, double* U, int max_sweeps, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,8 @@ FORMS = {"fp64": 0, "mixed": 1}
 #: every symbol declared in include/eph.h
 EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "eph_interp",
            "eph_interp_backward", "eph_destroy", "eph_strerror", "eph_last_error", "eph_kernel_launches",
-           "eph_profile", "eph_profile_read", "eph_profile_reset")
+           "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc")
+NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj")
 
 
@@ -77,6 +78,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_profile_read.restype = i
     lib.eph_profile_reset.argtypes = [vp]
     lib.eph_profile_reset.restype = i
+    lib.eph_bands_noalloc.argtypes = [i, dp, i, i, vp, dp, dp, dp, dp, i, vp]
+    lib.eph_bands_noalloc.restype = i
     del ip
     if path is None:
         _lib = lib

@@ -1,0 +1,77 @@
+"""eph_bands_noalloc: the entry point that allocates no device memory.
+
+It serves callers that cannot call cudaMalloc (device memory owned by another
+allocator, or code that must not trigger the synchronisation an allocation can
+cause).  Its output is checked against the existing entry point eph_set_k on
+two calls in a row with different k lists (so the second call runs over the
+first call's leftovers in the shared scratch array), and its eigenvectors
+against the oracle's H(k).  This file is collected last on purpose.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_10295_gb300 import binding, build_lib, synth
+from tests import gauge
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(binding.LIB_PATH):
+        build_lib.build()
+    return binding.load_library()
+
+
+def test_bands_noalloc_matches_set_k_on_two_calls(lib):
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream()
+    wl = synth.make_workload("si_full", nq=1)
+    nb, ne = wl.nb, wl.ne
+    ctx = binding.Context.from_workload(wl, device_ptrs=True, stream=st)
+    Re_d = torch.from_numpy(np.ascontiguousarray(wl.Re, dtype=np.int32)).to(dev)
+    we_d = torch.from_numpy(wl.we).to(dev)
+    H_d = torch.from_numpy(np.ascontiguousarray(wl.H_Re)).to(dev)
+    rng = np.random.default_rng(21)
+    for nk in (3000, 7000):           # 7000 k x (216 + 64) x 16 B = 31.4 MB of the 32 MiB scratch
+        kpts = rng.random((nk, 3))
+        k_d = torch.from_numpy(kpts).to(dev)
+        eps_ref = torch.empty(nk, nb, dtype=torch.float64, device=dev)
+        ctx.eph_set_k(nk, k_d, eps_ref)
+        eps = torch.full((nk, nb), float("nan"), dtype=torch.float64, device=dev)
+        U = torch.full((nk, nb, nb), float("nan"), dtype=torch.complex128, device=dev)
+        rc = lib.eph_bands_noalloc(nk, k_d.data_ptr(), nb, ne, Re_d.data_ptr(), we_d.data_ptr(), H_d.data_ptr(),
+                                   eps.data_ptr(), U.data_ptr(), 0, st.cuda_stream)
+        assert rc == binding.EPH_OK
+        torch.cuda.synchronize()
+        e_new, e_old = eps.cpu().numpy(), eps_ref.cpu().numpy()
+        assert gauge.max_rel_eps(e_new, e_old) <= TOL
+        # eigenvectors: U diag(eps) U^H reproduces the oracle's H(k), U is unitary
+        Uh = U.cpu().numpy()
+        Hk = oracle.hamiltonian_k(kpts, wl.Re, wl.we, wl.H_Re)
+        rec = np.einsum("kam,km,kbm->kab", Uh, e_new, Uh.conj())
+        assert np.abs(rec - Hk).max() <= TOL * np.abs(Hk).max()
+        eye = np.einsum("kam,kan->kmn", Uh.conj(), Uh)
+        assert np.abs(eye - np.eye(nb)[None]).max() <= 1e-13
+
+
+def test_bands_noalloc_rejects_sizes_beyond_scratch(lib):
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    nb, ne = 8, 216
+    nk = 7490                         # 7490 x 4480 B > 32 MiB
+    k_d = torch.zeros(nk, 3, dtype=torch.float64, device=dev)
+    Re_d = torch.zeros(ne, 3, dtype=torch.int32, device=dev)
+    H_d = torch.zeros(ne, nb, nb, dtype=torch.complex128, device=dev)
+    eps = torch.empty(nk, nb, dtype=torch.float64, device=dev)
+    U = torch.empty(nk, nb, nb, dtype=torch.complex128, device=dev)
+    rc = lib.eph_bands_noalloc(nk, k_d.data_ptr(), nb, ne, Re_d.data_ptr(), None, H_d.data_ptr(), eps.data_ptr(),
+                               U.data_ptr(), 0, None)
+    assert rc == binding.EPH_EINVAL
