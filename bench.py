@@ -36,9 +36,11 @@ METRIC = "e-ph g(k,q) elements/s, 1 GB300: split-precision vs FP64 form at state
 UNIT = "g elements/s"
 # FP64 pipe of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and max clock)
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
-# DRAM traffic per launch of the dominant kernel from one ncu capture, scaled to the
-# bench launch (None until captured for the current kernel); see profiles/.
-TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
+# kernel from one ncu capture of a one-q launch, scaled to the bench launch by the units
+# processed (profiles/k_zgemm_si_full_fp64.md).  Keyed by (kernel, workload, q batch).
+TRAFFIC = {("k_zgemm", "si_full", 4): 4 * (225.011712e6 + 404.513024e6),
+           ("k_zgemm", "si_full", 1): 225.011712e6 + 404.513024e6}
 
 
 def parse():

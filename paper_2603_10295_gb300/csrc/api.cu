@@ -19,15 +19,19 @@
 #include "eph.h"
 #include "eph_kernels.cuh"
 
+using eph::launch_band_adjoint;
 using eph::launch_band_rotate;
 using eph::launch_jacobi;
 using eph::launch_mode_rotate;
+using eph::launch_mode_rotate_adj;
 using eph::launch_phase;
 using eph::launch_phonon_post;
 using eph::launch_scale_rows;
 using eph::launch_skinny;
 using eph::launch_skinny_real;
+using eph::launch_sum_into;
 using eph::launch_zgemm;
+using eph::launch_zgemm_ah;
 
 namespace {
 
@@ -61,6 +65,8 @@ struct eph_ctx {
   DBuf kpts, Pk, eps_k, Uk, Hk_tmp;
   // per-call workspace
   DBuf qpts, Qe, Pp, D, lamq, evq, omq, uq, G1, W, Y, eps_tile, Ukq, g_stage;
+  // adjoint workspace
+  DBuf wk, G2bar, G1bar, Lpair, Lacc, grad;
   long long launches = 0;
   std::string err;
   // per-stage event timing
@@ -235,7 +241,8 @@ void eph_destroy(eph_ctx* ctx) {
     if (p) cudaFree(p);
   DBuf* bufs[] = {&ctx->kpts, &ctx->Pk, &ctx->eps_k, &ctx->Uk, &ctx->Hk_tmp, &ctx->qpts, &ctx->Qe, &ctx->Pp,
                   &ctx->D, &ctx->lamq, &ctx->evq, &ctx->omq, &ctx->uq, &ctx->G1, &ctx->W, &ctx->Y,
-                  &ctx->eps_tile, &ctx->Ukq, &ctx->g_stage};
+                  &ctx->eps_tile, &ctx->Ukq, &ctx->g_stage, &ctx->wk, &ctx->G2bar, &ctx->G1bar,
+                  &ctx->Lpair, &ctx->Lacc, &ctx->grad};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -400,28 +407,35 @@ extern "C" int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k
   return EPH_OK;
 }
 
-extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
-  if (!ctx) return EPH_EINVAL;
-  if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
-  if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
-  const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, np = ctx->np, nk = ctx->nk;
-  const int nb2 = nb * nb;
-  const long NW = (long)nb2 * (1 + nm);  // columns of W_q: H part | G2 part
-  const long gcols = (long)nm * nb2;      // g elements per (q,k)
-  int QB = ctx->opt.q_batch > 0 ? ctx->opt.q_batch : 4;
-  if (QB > 16) QB = 16;
-  if (QB > nq) QB = nq;
-  const bool host = !ctx->opt.device_ptrs;
+namespace {
+
+struct QPlan {
+  int QB;
+  long KT, NW, gcols, X;
+};
+
+QPlan plan_q(const eph_ctx* ctx, int nq, size_t extra_per_pair) {
+  QPlan p;
+  const int nb2 = ctx->nb * ctx->nb;
+  p.NW = (long)nb2 * (1 + ctx->nm);  // columns of W_q: H part | G2 part
+  p.gcols = (long)ctx->nm * nb2;      // g elements per (q,k)
+  p.X = (long)ctx->nm * ctx->ne * nb2;
+  p.QB = ctx->opt.q_batch > 0 ? ctx->opt.q_batch : 4;
+  if (p.QB > 16) p.QB = 16;
+  if (p.QB > nq) p.QB = nq;
   // bytes per (q,k) pair in the k stage
-  const size_t per_pair = (size_t)NW * 16 + (size_t)nb2 * 16 + (size_t)nb * 8 + (host && g ? (size_t)gcols * 16 : 0);
+  const size_t per_pair = (size_t)p.NW * 16 + (size_t)nb2 * 16 + (size_t)ctx->nb * 8 + extra_per_pair;
   const size_t budget = (size_t)ctx->opt.workspace_mb << 20;
-  long KT = ctx->opt.k_tile > 0 ? ctx->opt.k_tile : (long)(budget / (per_pair * QB));
-  if (KT > nk) KT = nk;
+  long KT = ctx->opt.k_tile > 0 ? ctx->opt.k_tile : (long)(budget / (per_pair * p.QB));
+  if (KT > ctx->nk) KT = ctx->nk;
   if (KT > 64) KT -= KT % 64;
   if (KT < 1) KT = 1;
+  p.KT = KT;
+  return p;
+}
 
-  const void* dq = nullptr;
-  EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
+int ensure_q_workspace(eph_ctx* ctx, const QPlan& p) {
+  const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, np = ctx->np, nb2 = nb * nb, QB = p.QB;
   EPH_TRY(ensure(ctx, ctx->Qe, (size_t)QB * ne * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->Pp, (size_t)QB * np * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->D, (size_t)QB * nm * nm * sizeof(double2)));
@@ -429,48 +443,79 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
   EPH_TRY(ensure(ctx, ctx->evq, (size_t)QB * nm * nm * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->omq, (size_t)QB * nm * sizeof(double)));
   EPH_TRY(ensure(ctx, ctx->uq, (size_t)QB * nm * nm * sizeof(double2)));
-  EPH_TRY(ensure(ctx, ctx->G1, (size_t)QB * nm * ne * nb2 * sizeof(double2)));
-  EPH_TRY(ensure(ctx, ctx->W, (size_t)QB * ne * NW * sizeof(double2)));
-  EPH_TRY(ensure(ctx, ctx->Y, (size_t)QB * KT * NW * sizeof(double2)));
-  EPH_TRY(ensure(ctx, ctx->eps_tile, (size_t)QB * KT * nb * sizeof(double)));
-  EPH_TRY(ensure(ctx, ctx->Ukq, (size_t)QB * KT * nb2 * sizeof(double2)));
-  if (host && g) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)QB * KT * gcols * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->G1, (size_t)QB * p.X * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->W, (size_t)QB * ne * p.NW * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->Y, (size_t)QB * p.KT * p.NW * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->eps_tile, (size_t)QB * p.KT * nb * sizeof(double)));
+  EPH_TRY(ensure(ctx, ctx->Ukq, (size_t)QB * p.KT * nb2 * sizeof(double2)));
+  return EPH_OK;
+}
 
-  const double* qdev = static_cast<const double*>(dq);
+// Per q batch, before the k loop: phases, D(q) -> omega, u; Eq. 9; W_q.
+int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb) {
+  const int nm = ctx->nm, ne = ctx->ne, np = ctx->np, nb2 = ctx->nb * ctx->nb;
   double2* Qe = as<double2>(ctx->Qe);
   double2* Pp = as<double2>(ctx->Pp);
   double2* W = as<double2>(ctx->W);
+  // phases for the batch: e^{i q.Re} (unweighted: P_k carries w_e) and w_p e^{i q.Rp}
+  EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(qb, nqb, ctx->Re, nullptr, ne, Qe, ne, ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(qb, nqb, ctx->Rp, ctx->wp, np, Pp, np, ctx->stream));
+  // D(q), eigenpairs, omega and u = e / sqrt(M)
+  EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny_real(nqb, (long)nm * nm, np, Pp, np, ctx->Phi, (long)nm * nm,
+                                                  ctx->dscale, as<double2>(ctx->D), (long)nm * nm, ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(as<double2>(ctx->D), (long)nm * nm, nm, nm, nqb, as<double>(ctx->lamq), nm,
+                                            as<double2>(ctx->evq), (long)nm * nm, ctx->opt.max_sweeps, ctx->status,
+                                            ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_MODE, launch_phonon_post(as<double>(ctx->lamq), as<double2>(ctx->evq), nqb, nm,
+                                                  ctx->invsqrtm, ctx->omega_unit, as<double>(ctx->omq),
+                                                  as<double2>(ctx->uq), ctx->stream));
+  // Eq. 9: G1 = sum_Rp w_p e^{i q.Rp} g(Re,Rp)
+  EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, p.X, np, Pp, np, ctx->gW, p.X, as<double2>(ctx->G1), p.X,
+                                             ctx->stream));
+  // W_q = [ e^{i q.Re} H(Re) | mode-rotated G1 ], row e of length NW
+  EPH_LAUNCH_S(EPH_STAGE_MODE, launch_scale_rows(Qe, nqb, ctx->H, ne, nb2, W, p.NW, (long)ne * p.NW, ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_MODE, launch_mode_rotate(as<double2>(ctx->G1), as<double2>(ctx->uq), nqb, nm, ne, nb2,
+                                                  W + nb2, p.NW, (long)ne * p.NW, ctx->stream));
+  return EPH_OK;
+}
+
+// Per (q batch, k tile): Y = P_k W_q (H(k+q) | G3), then the H(k+q) eigensolves.
+int k_tile_forward(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
+  const int nb = ctx->nb, ne = ctx->ne, nb2 = nb * nb;
   double2* Y = as<double2>(ctx->Y);
-  for (int q0 = 0; q0 < nq; q0 += QB) {
-    const int nqb = (nq - q0 < QB) ? nq - q0 : QB;
-    const double* qb = qdev + 3L * q0;
-    // phases for the batch: e^{i q.Re} (unweighted: P_k carries w_e) and w_p e^{i q.Rp}
-    EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(qb, nqb, ctx->Re, nullptr, ne, Qe, ne, ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(qb, nqb, ctx->Rp, ctx->wp, np, Pp, np, ctx->stream));
-    // D(q), eigenpairs, omega and u = e / sqrt(M)
-    EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny_real(nqb, (long)nm * nm, np, Pp, np, ctx->Phi, (long)nm * nm, ctx->dscale,
-                                  as<double2>(ctx->D), (long)nm * nm, ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(as<double2>(ctx->D), (long)nm * nm, nm, nm, nqb, as<double>(ctx->lamq), nm,
-                             as<double2>(ctx->evq), (long)nm * nm, ctx->opt.max_sweeps, ctx->status, ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_MODE, launch_phonon_post(as<double>(ctx->lamq), as<double2>(ctx->evq), nqb, nm, ctx->invsqrtm,
-                                  ctx->omega_unit, as<double>(ctx->omq), as<double2>(ctx->uq), ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nkt, (int)p.NW, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0,
+                                            as<double2>(ctx->W), p.NW, (long)ne * p.NW, Y, p.NW, (long)nkt * p.NW, nqb,
+                                            ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(Y, p.NW, nb, nb, (long)nqb * nkt, as<double>(ctx->eps_tile), nb,
+                                            as<double2>(ctx->Ukq), nb2, ctx->opt.max_sweeps, ctx->status, ctx->stream));
+  return EPH_OK;
+}
+
+}  // namespace
+
+extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
+  if (!ctx) return EPH_EINVAL;
+  if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
+  if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
+  const int nb = ctx->nb, nm = ctx->nm, nk = ctx->nk;
+  const int nb2 = nb * nb;
+  const bool host = !ctx->opt.device_ptrs;
+  const QPlan p = plan_q(ctx, nq, host && g ? (size_t)nm * nb2 * 16 : 0);
+  const void* dq = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
+  EPH_TRY(ensure_q_workspace(ctx, p));
+  if (host && g) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)p.QB * p.KT * p.gcols * sizeof(double2)));
+  const double* qdev = static_cast<const double*>(dq);
+  double2* Y = as<double2>(ctx->Y);
+  for (int q0 = 0; q0 < nq; q0 += p.QB) {
+    const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
     if (omega)
       EPH_CK(cudaMemcpyAsync(omega + (long)q0 * nm, ctx->omq.p, (size_t)nqb * nm * sizeof(double), out_kind(ctx),
                              ctx->stream));
-    // Eq. 9: G1 = sum_Rp w_p e^{i q.Rp} g(Re,Rp)
-    const long X = (long)nm * ne * nb2;
-    EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, X, np, Pp, np, ctx->gW, X, as<double2>(ctx->G1), X, ctx->stream));
-    // W_q = [ e^{i q.Re} H(Re) | mode-rotated G1 ], row e of length NW
-    EPH_LAUNCH_S(EPH_STAGE_MODE, launch_scale_rows(Qe, nqb, ctx->H, ne, nb2, W, NW, (long)ne * NW, ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_MODE, launch_mode_rotate(as<double2>(ctx->G1), as<double2>(ctx->uq), nqb, nm, ne, nb2, W + nb2, NW,
-                                  (long)ne * NW, ctx->stream));
-    for (long k0 = 0; k0 < nk; k0 += KT) {
-      const int nkt = (int)((nk - k0 < KT) ? nk - k0 : KT);
-      // Y[q][k] = sum_Re w_e e^{i k.Re} W_q[Re]: H(k+q) (first nb^2 columns) and G3 (rest)
-      EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nkt, (int)NW, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0, W, NW, (long)ne * NW, Y, NW,
-                              (long)nkt * NW, nqb, ctx->stream));
-      EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(Y, NW, nb, nb, (long)nqb * nkt, as<double>(ctx->eps_tile), nb, as<double2>(ctx->Ukq),
-                               nb2, ctx->opt.max_sweeps, ctx->status, ctx->stream));
+    for (long k0 = 0; k0 < nk; k0 += p.KT) {
+      const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
+      EPH_TRY(k_tile_forward(ctx, p, nqb, k0, nkt));
       if (eps_kq)
         for (int iq = 0; iq < nqb; ++iq)  // one contiguous copy per q (rows of the tile)
           EPH_CK(cudaMemcpyAsync(eps_kq + ((long)(q0 + iq) * nk + k0) * nb,
@@ -479,16 +524,18 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
       if (g) {
         double2* gout = static_cast<double2*>(g);
         if (host) {
-          EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, NW, as<double2>(ctx->Ukq), as<double2>(ctx->Uk) + k0 * nb2, nqb,
-                                        nkt, nm, nb, as<double2>(ctx->g_stage), (long)nkt * gcols, ctx->stream));
+          EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, as<double2>(ctx->Ukq),
+                                                          as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
+                                                          as<double2>(ctx->g_stage), (long)nkt * p.gcols, ctx->stream));
           for (int iq = 0; iq < nqb; ++iq)
-            EPH_CK(cudaMemcpyAsync(gout + ((long)(q0 + iq) * nk + k0) * gcols,
-                                   as<double2>(ctx->g_stage) + (long)iq * nkt * gcols,
-                                   (size_t)nkt * gcols * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+            EPH_CK(cudaMemcpyAsync(gout + ((long)(q0 + iq) * nk + k0) * p.gcols,
+                                   as<double2>(ctx->g_stage) + (long)iq * nkt * p.gcols,
+                                   (size_t)nkt * p.gcols * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
         } else {
-          EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, NW, as<double2>(ctx->Ukq), as<double2>(ctx->Uk) + k0 * nb2, nqb,
-                                        nkt, nm, nb, gout + ((long)q0 * nk + k0) * gcols, (long)nk * gcols,
-                                        ctx->stream));
+          EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, as<double2>(ctx->Ukq),
+                                                          as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
+                                                          gout + ((long)q0 * nk + k0) * p.gcols, (long)nk * p.gcols,
+                                                          ctx->stream));
         }
       }
     }
@@ -503,8 +550,65 @@ extern "C" int eph_interp(eph_ctx* ctx, int nk, const double* kpts, int nq, cons
   return eph_interp_q(ctx, nq, qpts, eps_kq, omega, g);
 }
 
-extern "C" int eph_interp_backward(eph_ctx* ctx, int, const double*, int, const double*, const double*, double, double*,
-                                   double*) {
+extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
+                                   const double* w_nk, double omega_min, double* L_out, double* grad_g_ReRp) {
   if (!ctx) return EPH_EINVAL;
-  return fail(ctx, EPH_ENOTSUP, "eph_interp_backward is not available in this build");
+  if (nk < 1 || nq < 1 || !kpts || !qpts || !w_nk || !L_out || !grad_g_ReRp)
+    return fail(ctx, EPH_EINVAL, "eph_interp_backward: bad size or NULL pointer");
+  EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
+  const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, np = ctx->np;
+  const int nb2 = nb * nb;
+  const bool host = !ctx->opt.device_ptrs;
+  const QPlan p = plan_q(ctx, nq, sizeof(double));
+  const void* dq = nullptr;
+  const void* dw = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
+  EPH_TRY(stage_in(ctx, ctx->wk, w_nk, (size_t)nk * nb * sizeof(double), &dw));
+  EPH_TRY(ensure_q_workspace(ctx, p));
+  EPH_TRY(ensure(ctx, ctx->G2bar, (size_t)p.QB * p.X * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->G1bar, (size_t)p.QB * p.X * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->Lpair, (size_t)p.QB * p.KT * sizeof(double)));
+  EPH_TRY(ensure(ctx, ctx->Lacc, sizeof(double)));
+  double2* grad = nullptr;
+  const size_t gbytes = (size_t)np * p.X * sizeof(double2);
+  if (host) {
+    EPH_TRY(ensure(ctx, ctx->grad, gbytes));
+    grad = as<double2>(ctx->grad);
+  } else {
+    grad = reinterpret_cast<double2*>(grad_g_ReRp);
+  }
+  EPH_CK(cudaMemsetAsync(grad, 0, gbytes, ctx->stream));
+  EPH_CK(cudaMemsetAsync(ctx->Lacc.p, 0, sizeof(double), ctx->stream));
+  const double* qdev = static_cast<const double*>(dq);
+  const double* wdev = static_cast<const double*>(dw);
+  double2* Y = as<double2>(ctx->Y);
+  double2* G2b = as<double2>(ctx->G2bar);
+  for (int q0 = 0; q0 < nq; q0 += p.QB) {
+    const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
+    for (long k0 = 0; k0 < nk; k0 += p.KT) {
+      const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
+      // recompute the Re->k stage and the gauges for this tile (never stored across tiles)
+      EPH_TRY(k_tile_forward(ctx, p, nqb, k0, nkt));
+      // g, L and G3bar = V_{k+q} (2 c g) V_k^H in place of G3
+      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_band_adjoint(Y + nb2, p.NW, as<double2>(ctx->Ukq),
+                                                      as<double2>(ctx->Uk) + k0 * nb2, wdev + k0 * nb,
+                                                      as<double>(ctx->omq), omega_min, nqb, nkt, nm, nb,
+                                                      as<double>(ctx->Lpair), ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_sum_into(as<double>(ctx->Lpair), (long)nqb * nkt, as<double>(ctx->Lacc),
+                                                  ctx->stream));
+      // G2bar[q] (+)= P_k^H G3bar  over this k tile
+      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ne, (int)p.gcols, nkt, as<double2>(ctx->Pk) + k0 * ne, ne, 0,
+                                                  Y + nb2, p.NW, (long)nkt * p.NW, G2b, p.gcols, (long)ne * p.gcols,
+                                                  nqb, k0 > 0, ctx->stream));
+    }
+    // G1bar = conj(u) G2bar (mode rotation adjoint), then grad += P_q(Rp)^H G1bar
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_mode_rotate_adj(G2b, as<double2>(ctx->uq), nqb, nm, ne, nb2,
+                                                       as<double2>(ctx->G1bar), ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(np, (int)p.X, nqb, as<double2>(ctx->Pp), np, 0,
+                                                as<double2>(ctx->G1bar), p.X, 0, grad, p.X, 0, 1, 1, ctx->stream));
+  }
+  EPH_CK(cudaMemcpyAsync(L_out, ctx->Lacc.p, sizeof(double), out_kind(ctx), ctx->stream));
+  if (host) EPH_CK(cudaMemcpyAsync(grad_g_ReRp, grad, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
+  return finish(ctx);
 }

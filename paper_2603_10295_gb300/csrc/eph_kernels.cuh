@@ -58,4 +58,16 @@ cudaError_t launch_mode_rotate(const double2* G1, const double2* u, int nq, int 
 cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq,
                                int nk, int nm, int nb, double2* g, long sgq, cudaStream_t st);
 
+// ---- adjoint (reverse chain of Eqs. 9-10 for L = sum c |g|^2) ------------------
+// In place over the G3 rows of Y: G3bar = V_{k+q} (2 c g) V_k^H with c = w_nk/omega (omega > omega_min);
+// Lpair[q*nk + k] = sum c |g|^2 for the pair.  wk: [nk][nb] (tile-local), om: [nq][nm].
+cudaError_t launch_band_adjoint(double2* Y, long ldy, const double2* Ukq, const double2* Uk, const double* wk,
+                                const double* om, double omega_min, int nq, int nk, int nm, int nb, double* Lpair,
+                                cudaStream_t st);
+// *L += sum_i v[i] (one CTA, fixed order).
+cudaError_t launch_sum_into(const double* v, long n, double* L, cudaStream_t st);
+// G1bar[q][c][e][b] = sum_nu conj(u[q][c][nu]) G2bar[q][e][nu][b]
+cudaError_t launch_mode_rotate_adj(const double2* G2b, const double2* u, int nq, int nm, int ne, int nb2,
+                                   double2* G1b, cudaStream_t st);
+
 }  // namespace eph
