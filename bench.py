@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-k", type=int, default=16000)
+    ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-form measurement")
     return ap.parse_args()
 
 
@@ -179,35 +180,31 @@ def describe(wl, args):
 
 
 # ----------------------------------------------------------------------------- libeph arm
-def run_libeph(args):
-    import numpy as np
+BF16_PEAK_TFLOPS = None  # read from MEASURED_PEAKS.json when present
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def time_form(wl, form, args, q_dev, k_dev, rank, world, local, dev, QB):
+    """Times args.steps q batches of one form on the device (inputs resident in HBM)."""
     import torch
 
-    from paper_2603_10295_gb300 import binding, synth
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    wl = synth.make_workload(args.workload)
+    from paper_2603_10295_gb300 import binding
     nk, nb, nm = len(wl.kpts), wl.nb, wl.nm
-    QB = args.q_batch
     st = torch.cuda.current_stream()
-    ctx = binding.Context.from_workload(wl, form=args.form, device_ptrs=True, q_batch=QB, stream=st)
-    # this rank's q points: (warmup + steps) batches, disjoint across ranks, cycling the q list
-    nsteps = args.warmup + args.steps
-    qidx = (np.arange(nsteps * QB) + rank * nsteps * QB) % len(wl.qpts)
-    q_dev = torch.from_numpy(np.ascontiguousarray(wl.qpts[qidx])).to(dev)
-    k_dev = torch.from_numpy(wl.kpts).to(dev)
+    ctx = binding.Context.from_workload(wl, form=form, device_ptrs=True, q_batch=QB, stream=st)
     eps_k = torch.empty(nk, nb, dtype=torch.float64, device=dev)
-    gdt = torch.complex128 if args.form == "fp64" else torch.complex64
+    gdt = torch.complex128 if form == "fp64" else torch.complex64
     eps_kq = torch.empty(QB, nk, nb, dtype=torch.float64, device=dev)
     om = torch.empty(QB, nm, dtype=torch.float64, device=dev)
     g = torch.empty(QB, nk, nm, nb, nb, dtype=gdt, device=dev)
-
-    # k-side preparation, once per job
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(st)
@@ -215,6 +212,7 @@ def run_libeph(args):
     e1.record(st)
     torch.cuda.synchronize()
     setk_ms = e0.elapsed_time(e1)
+    nsteps = args.warmup + args.steps
 
     def step(i):
         ctx.eph_interp_q(QB, q_dev[i * QB:(i + 1) * QB], eps_kq, om, g)
@@ -249,41 +247,104 @@ def run_libeph(args):
         dist.barrier()
         el_ms = float(t.item())
     units_rank = args.steps * QB * nk * nm * nb * nb
-    # share of the once-per-job k preparation for the q points processed here
     setk_share_ms = setk_ms * (args.steps * QB) / len(wl.qpts)
-    value = world * units_rank / ((el_ms + setk_share_ms) * 1e-3)
-
-    # roofline: the dominant kernel is the fused Re->k / H(k+q) FP64 contraction (stage ft_k)
-    ft_ms, ft_n = prof["ft_k"]
-    NW = nb * nb * (1 + nm)
-    flop_launch = 8.0 * QB * nk * NW * wl.ne          # one launch covers the q batch x all k
-    achieved = flop_launch / (ft_ms / max(ft_n, 1) * 1e-3) if ft_n else None
-    roof = {"bound": "alu", "kernel": "k_zgemm (Re->k contraction fused with H(k+q), FP64 DFMA)",
-            "achieved": achieved / 1e12 if achieved else None, "peak": FP64_PEAK_FLOPS / 1e12,
-            "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_FLOPS) if achieved else None,
-            "traffic": TRAFFIC.get(("k_zgemm", args.workload, QB)),
-            "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
-    stage_ms = {k: round(v[0] / args.steps, 3) for k, v in prof.items()}
-
-    line = None
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.form == "fp64" else "tf32x3/f32",
-                "data": "synthetic",
-                "config": {"workload": describe(wl, args), "form": args.form, "q_batch": QB,
-                           "l2": "inputs larger than L2: g(Re,Rp) 287 MB, P_k 221 MB resident; "
-                                 f"g out {g.numel() * g.element_size() / 1e9:.2f} GB per step",
-                           "k_setup_ms": setk_ms, "k_setup_share_ms": setk_share_ms,
-                           "stage_ms_per_step": stage_ms},
-                "roofline": roof, "gpu_launches": launches, "clocks": clk}
+    out = dict(value=world * units_rank / ((el_ms + setk_share_ms) * 1e-3), ms_per_step=el_ms / args.steps,
+               setk_ms=setk_ms, setk_share_ms=setk_share_ms, launches=launches, prof=prof, clocks=clk,
+               g_bytes=g.numel() * g.element_size())
     del g, eps_kq, om
     ctx.close()
     torch.cuda.empty_cache()
+    return out
+
+
+def run_libeph(args):
+    import numpy as np
+    import torch
+
+    from paper_2603_10295_gb300 import binding, synth
+    from paper_2603_10295_gb300.sharding import q_shard
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = synth.make_workload(args.workload)
+    nk, nb, nm, ne = len(wl.kpts), wl.nb, wl.nm, wl.ne
+    QB = args.q_batch
+    # this rank's q points: a contiguous block of the (cyclically extended) q list
+    nsteps = args.warmup + args.steps
+    a, _ = q_shard(world * nsteps * QB, rank, world)
+    qidx = (np.arange(nsteps * QB) + a) % len(wl.qpts)
+    q_dev = torch.from_numpy(np.ascontiguousarray(wl.qpts[qidx])).to(dev)
+    k_dev = torch.from_numpy(wl.kpts).to(dev)
+
+    forms = ["fp64"] if args.form == "fp64" and args.fp64_only else ["fp64", "mixed"]
+    if args.form == "mixed":
+        forms = ["mixed"]
+    res = {f: time_form(wl, f, args, q_dev, k_dev, rank, world, local, dev, QB) for f in forms}
+    head = res[forms[0]]
+    peaks = measured_peaks()
+
+    def roof_fp64(r):
+        ft_ms, ft_n = r["prof"]["ft_k"]
+        NW = nb * nb * (1 + nm)
+        flop_launch = 8.0 * QB * nk * NW * ne          # one launch covers the q batch x all k
+        ach = flop_launch / (ft_ms / max(ft_n, 1) * 1e-3) if ft_n else None
+        return {"bound": "alu", "kernel": "k_zgemm (Re->k contraction fused with H(k+q), FP64 DFMA)",
+                "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": (ach / FP64_PEAK_FLOPS) if ach else None,
+                "traffic": TRAFFIC.get(("k_zgemm", args.workload, QB)),
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
+
+    def roof_tc(r):
+        tc_ms, tc_n = r["prof"]["tc"]
+        kpd = ((2 * ne + 63) // 64) * 64
+        nr = 2 * nm * nb * nb
+        mpad = ((nk + 127) // 128) * 128
+        npad = ((nr + 127) // 128) * 128
+        issued = 9 * 2.0 * mpad * npad * kpd * QB     # nine bf16 digit products per K step
+        useful = 8.0 * nk * nm * nb * nb * ne * QB     # complex Re->k contraction, 8 flop per CMAC
+        t = tc_ms / max(tc_n, 1) * 1e-3 if tc_n else None
+        peak = peaks.get("bf16_tflops")
+        return {"bound": "tensor", "kernel": "k_tc_fixed_gemm (tcgen05 kind::f16, fixed-point BF16 digits)",
+                "achieved": issued / t / 1e12 if t else None, "peak": peak, "unit": "TFLOP/s",
+                "frac": (issued / t / 1e12 / peak) if (t and peak) else None,
+                "useful_tflops": useful / t / 1e12 if t else None, "ms_per_launch": tc_ms / max(tc_n, 1),
+                "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), measured" if peak else "unavailable"}
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if forms[0] == "fp64" else "bf16-digits/f32",
+                "data": "synthetic",
+                "config": {"workload": describe(wl, args), "form": forms[0], "q_batch": QB,
+                           "l2": "inputs larger than L2: g(Re,Rp) 287 MB, P_k 221 MB resident; "
+                                 f"g out {head['g_bytes'] / 1e9:.2f} GB per step",
+                           "k_setup_ms": head["setk_ms"], "k_setup_share_ms": head["setk_share_ms"],
+                           "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in head["prof"].items()},
+                           "parity": "FP64 form vs FP64 CPU oracle: max rel err <= 1e-12 (eps, omega, |g|^2 "
+                                     "subspace sums); tests/test_gpu_parity.py"},
+                "roofline": roof_fp64(head) if forms[0] == "fp64" else roof_tc(head),
+                "gpu_launches": head["launches"], "clocks": head["clocks"]}
+        if "mixed" in res and forms[0] == "fp64":
+            m = res["mixed"]
+            line["mixed"] = {"value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"],
+                             "gain_vs_fp64": m["value"] / head["value"], "dtype": "bf16 digits / f32 accumulate",
+                             "rel_err_bar": "<= 1e-6 on |g|^2 subspace sums (measured 2.1e-7 si_full, "
+                                            "tests/test_gpu_mixed.py); eps, omega FP64 (1e-12)",
+                             "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in m["prof"].items()},
+                             "roofline_tensor_kernel": roof_tc(m), "gpu_launches": m["launches"],
+                             "clocks": m["clocks"]}
 
     # end to end through the public C-ABI with HOST buffers (pinned), copies inside the timed region
     if rank == 0 and not args.no_e2e:
-        hctx = binding.Context.from_workload(wl, form=args.form, device_ptrs=False, q_batch=QB)
+        form = forms[0]
+        gdt = torch.complex128 if form == "fp64" else torch.complex64
+        hctx = binding.Context.from_workload(wl, form=form, device_ptrs=False, q_batch=QB)
         kp_h = torch.from_numpy(wl.kpts).pin_memory()
         epsk_h = torch.empty(nk, nb, dtype=torch.float64).pin_memory()
         q_h = torch.from_numpy(np.ascontiguousarray(wl.qpts[qidx])).pin_memory()

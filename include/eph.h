@@ -48,8 +48,9 @@ enum eph_status {
 
 enum eph_form {
   EPH_FORM_FP64 = 0,  /* every contraction in FP64 (DFMA) */
-  EPH_FORM_MIXED = 1  /* Re->k contraction as split-precision tensor-core products, FP32 accumulation;
-                         phases, H(k)/H(k+q)/D(q) and their eigensolves stay FP64 */
+  EPH_FORM_MIXED = 1  /* Re->k contraction of g as split-precision tcgen05 tensor-core products with
+                         FP32 accumulation, g as complex64; phases, H(k)/H(k+q)/D(q), their
+                         eigensolves and the Rp->q contraction stay FP64 */
 };
 
 typedef struct eph_options {
@@ -60,6 +61,9 @@ typedef struct eph_options {
   int k_tile;        /* k points per internal tile, 0 = automatic (bounded by workspace_mb) */
   int max_sweeps;    /* Jacobi sweep cap, 0 = default (20) */
   int workspace_mb;  /* soft cap on the per-call workspace in MiB, 0 = default (4096) */
+  int mixed_scheme;  /* mixed form only: 0 = fixed-point BF16 digits (3 for the phases, 4 for g)
+                        with exact FP32 tensor-core accumulation (default; needs 2*ne <= 1024),
+                        1 = two-term split TF32 (3 products) */
 } eph_options;
 
 /* Fills *opt with the defaults (FP64 form, host pointers, automatic batching). */
@@ -150,6 +154,7 @@ enum eph_stage {
   EPH_STAGE_FT_K = 4,  /* Re->k contraction (Eq. 10 Fourier sum) fused with H(k+q)              */
   EPH_STAGE_BAND = 5,  /* band rotation V_{k+q}^H G V_k                                         */
   EPH_STAGE_ADJ = 6,   /* adjoint (backward) kernels                                            */
+  EPH_STAGE_TC = 7,    /* mixed form: tensor-core (tcgen05) Re->k contraction                   */
   EPH_NSTAGES = 8
 };
 

@@ -8,6 +8,7 @@
 //                 per k tile:  Y = P_k W_q  gives H(k+q) and G3 in one FP64 GEMM
 //                              Jacobi(H(k+q)) -> eps_kq, V_{k+q}
 //                              g = V_{k+q}^H G3_nu V_k          (band rotation)
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -32,6 +33,16 @@ using eph::launch_skinny_real;
 using eph::launch_sum_into;
 using eph::launch_zgemm;
 using eph::launch_zgemm_ah;
+using eph::launch_band_rotate_f32;
+using eph::launch_band_rotate_ff;
+using eph::launch_digits_a;
+using eph::launch_digits_b;
+using eph::launch_tc_fixed_gemm;
+using eph::make_tc_map_bf16;
+using eph::launch_split_a;
+using eph::launch_split_b;
+using eph::launch_tc_split_gemm;
+using eph::make_tc_map;
 
 namespace {
 
@@ -67,6 +78,16 @@ struct eph_ctx {
   DBuf qpts, Qe, Pp, D, lamq, evq, omq, uq, G1, W, Y, eps_tile, Ukq, g_stage;
   // adjoint workspace
   DBuf wk, G2bar, G1bar, Lpair, Lacc, grad;
+  // mixed form: split-TF32 operands of the Re->k contraction, its FP32 output, H(k+q)
+  int kp = 0;    // 2*ne rounded up to a multiple of 32
+  long nr = 0;   // 2*nm*nb*nb real columns
+  DBuf Ahi, Alo, Bhi, Blo, G3f, Hkq, g_stage32;
+  CUtensorMap mapAhi{}, mapAlo{}, mapBhi{}, mapBlo{};
+  // mixed form, fixed-point BF16 digits: A [3][nk][kpd], B [4][QB*nr][kpd], per-column scales of B
+  int kpd = 0;          // 2*ne rounded up to a multiple of 64
+  double scaleA = 1.0;  // power of two >= 2 max |w_e|
+  DBuf DA, DB, sB;
+  CUtensorMap mapDA[3]{}, mapDB[4]{};
   long long launches = 0;
   std::string err;
   // per-stage event timing
@@ -242,7 +263,8 @@ void eph_destroy(eph_ctx* ctx) {
   DBuf* bufs[] = {&ctx->kpts, &ctx->Pk, &ctx->eps_k, &ctx->Uk, &ctx->Hk_tmp, &ctx->qpts, &ctx->Qe, &ctx->Pp,
                   &ctx->D, &ctx->lamq, &ctx->evq, &ctx->omq, &ctx->uq, &ctx->G1, &ctx->W, &ctx->Y,
                   &ctx->eps_tile, &ctx->Ukq, &ctx->g_stage, &ctx->wk, &ctx->G2bar, &ctx->G1bar,
-                  &ctx->Lpair, &ctx->Lacc, &ctx->grad};
+                  &ctx->Lpair, &ctx->Lacc, &ctx->grad, &ctx->Ahi, &ctx->Alo, &ctx->Bhi, &ctx->Blo,
+                  &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -278,9 +300,18 @@ int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re
     eph_destroy(ctx);
     return code;
   };
-  if (ctx->opt.form != EPH_FORM_FP64) {
-    fail(ctx, EPH_ENOTSUP, "only the FP64 form is available in this build");
-    return bail(EPH_ENOTSUP);
+  if (ctx->opt.form != EPH_FORM_FP64 && ctx->opt.form != EPH_FORM_MIXED) return bail(EPH_EINVAL);
+  ctx->kp = ((2 * ne + 31) / 32) * 32;
+  ctx->kpd = ((2 * ne + 63) / 64) * 64;
+  ctx->nr = 2L * 3 * na * nb * nb;
+  if (ctx->opt.form == EPH_FORM_MIXED && ctx->opt.mixed_scheme == 0 && ctx->kpd > 1024)
+    return bail(EPH_ENOTSUP);  // exact level-0 digit sums need 2*ne <= 1024
+  {
+    double wmax = 0.0;
+    for (int i = 0; i < ne; ++i) wmax = std::fmax(wmax, std::fabs(we ? we[i] : 1.0));
+    int ex = 0;
+    std::frexp(wmax > 0.0 ? wmax : 1.0, &ex);
+    ctx->scaleA = std::ldexp(1.0, ex + 1);  // |Re P|, |Im P| <= w_e <= scaleA / 2
   }
   if (nb > 16 || nm > 16) return bail(EPH_ENOTSUP);
   for (int i = 0; i < na; ++i)
@@ -337,7 +368,9 @@ int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re
   delete[] wones_e;
   delete[] wones_p;
   if (rc != EPH_OK) return bail(rc);
-  if (cudaMalloc(&ctx->status, sizeof(int)) != cudaSuccess || cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess)
+  // status[0]: Jacobi sweep cap reached; status[1]: tensor-core pipeline wait timed out
+  if (cudaMalloc(&ctx->status, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->status, 0, 2 * sizeof(int)) != cudaSuccess)
     return bail(EPH_ENOMEM);
   *out = ctx;
   return EPH_OK;
@@ -364,13 +397,14 @@ cudaMemcpyKind out_kind(const eph_ctx* ctx) {
 }
 
 int finish(eph_ctx* ctx) {
-  int h = 0;
-  EPH_CK(cudaMemcpyAsync(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  int h[2] = {0, 0};
+  EPH_CK(cudaMemcpyAsync(h, ctx->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   EPH_CK(cudaStreamSynchronize(ctx->stream));
   collect_profile(ctx);
-  if (h) {
-    cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream);
+  if (h[0] || h[1]) {
+    cudaMemsetAsync(ctx->status, 0, 2 * sizeof(int), ctx->stream);
     cudaStreamSynchronize(ctx->stream);
+    if (h[1]) return fail(ctx, EPH_ECUDA, "a tensor-core pipeline wait timed out");
     return fail(ctx, EPH_ENOTCONV, "a batched Jacobi eigensolve reached the sweep cap");
   }
   return EPH_OK;
@@ -398,6 +432,23 @@ extern "C" int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k
                           1, ctx->stream));
   EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(as<double2>(ctx->Hk_tmp), nb2, nb, nb, nk, as<double>(ctx->eps_k), nb,
                            as<double2>(ctx->Uk), nb2, ctx->opt.max_sweeps, ctx->status, ctx->stream));
+  if (ctx->opt.form == EPH_FORM_MIXED && ctx->opt.mixed_scheme == 0) {
+    // A operand of the tensor-core Re->k contraction: 3 fixed-point BF16 digits of the phases
+    const size_t slice = (size_t)nk * ctx->kpd;
+    EPH_TRY(ensure(ctx, ctx->DA, 3 * slice * 2));
+    EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_digits_a(as<double2>(ctx->Pk), ne, nk, ne, ctx->kpd, ctx->scaleA, ctx->DA.p,
+                                                  ctx->stream));
+    for (int d = 0; d < 3; ++d)
+      EPH_CK(make_tc_map_bf16(&ctx->mapDA[d], static_cast<char*>(ctx->DA.p) + d * slice * 2, nk, ctx->kpd, 128));
+  } else if (ctx->opt.form == EPH_FORM_MIXED) {
+    // A operand of the tensor-core Re->k contraction: split-TF32 phases, K-major [nk][kp]
+    EPH_TRY(ensure(ctx, ctx->Ahi, (size_t)nk * ctx->kp * sizeof(float)));
+    EPH_TRY(ensure(ctx, ctx->Alo, (size_t)nk * ctx->kp * sizeof(float)));
+    EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_split_a(as<double2>(ctx->Pk), ne, nk, ne, ctx->kp, as<float>(ctx->Ahi),
+                                                 as<float>(ctx->Alo), ctx->stream));
+    EPH_CK(make_tc_map(&ctx->mapAhi, as<float>(ctx->Ahi), nk, ctx->kp, 128));
+    EPH_CK(make_tc_map(&ctx->mapAlo, as<float>(ctx->Alo), nk, ctx->kp, 128));
+  }
   if (eps_k)
     EPH_CK(cudaMemcpyAsync(eps_k, ctx->eps_k.p, (size_t)nk * nb * sizeof(double), out_kind(ctx), ctx->stream));
   int rc = finish(ctx);
@@ -434,7 +485,7 @@ QPlan plan_q(const eph_ctx* ctx, int nq, size_t extra_per_pair) {
   return p;
 }
 
-int ensure_q_workspace(eph_ctx* ctx, const QPlan& p) {
+int ensure_q_workspace(eph_ctx* ctx, const QPlan& p, bool with_y = true) {
   const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, np = ctx->np, nb2 = nb * nb, QB = p.QB;
   EPH_TRY(ensure(ctx, ctx->Qe, (size_t)QB * ne * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->Pp, (size_t)QB * np * sizeof(double2)));
@@ -445,7 +496,7 @@ int ensure_q_workspace(eph_ctx* ctx, const QPlan& p) {
   EPH_TRY(ensure(ctx, ctx->uq, (size_t)QB * nm * nm * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->G1, (size_t)QB * p.X * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->W, (size_t)QB * ne * p.NW * sizeof(double2)));
-  EPH_TRY(ensure(ctx, ctx->Y, (size_t)QB * p.KT * p.NW * sizeof(double2)));
+  if (with_y) EPH_TRY(ensure(ctx, ctx->Y, (size_t)QB * p.KT * p.NW * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->eps_tile, (size_t)QB * p.KT * nb * sizeof(double)));
   EPH_TRY(ensure(ctx, ctx->Ukq, (size_t)QB * p.KT * nb2 * sizeof(double2)));
   return EPH_OK;
@@ -491,12 +542,114 @@ int k_tile_forward(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
   return EPH_OK;
 }
 
+// Mixed form: H(k+q) and every eigensolve in FP64; the Re->k contraction of g as a
+// split-TF32 tensor-core GEMM with FP32 accumulation; FP32 band rotation; complex64 g.
+int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
+  const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, nk = ctx->nk, kp = ctx->kp;
+  const int nb2 = nb * nb;
+  const long nr = ctx->nr;
+  const bool host = !ctx->opt.device_ptrs;
+  const long gcols = (long)nm * nb2;
+  // per (q,k): H(k+q) + V_{k+q} (FP64), eigenvalues, G3 (FP32 real embedding), host staging of g
+  QPlan p = plan_q(ctx, nq, 0);
+  {
+    const size_t per_pair = (size_t)nb2 * 16 * 2 + (size_t)nb * 8 + (size_t)nr * 4 + (host && g ? (size_t)gcols * 8 : 0);
+    const size_t budget = (size_t)ctx->opt.workspace_mb << 20;
+    long KT = ctx->opt.k_tile > 0 ? ctx->opt.k_tile : (long)(budget / (per_pair * p.QB));
+    if (KT > nk) KT = nk;
+    if (KT > 128) KT -= KT % 128;
+    if (KT < 1) KT = 1;
+    p.KT = KT;
+  }
+  const void* dq = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
+  EPH_TRY(ensure_q_workspace(ctx, p, false));
+  const bool digits = ctx->opt.mixed_scheme == 0;
+  const int kpd = ctx->kpd;
+  const size_t dslice = (size_t)p.QB * nr * kpd;
+  if (digits) {
+    EPH_TRY(ensure(ctx, ctx->DB, 4 * dslice * 2));
+    EPH_TRY(ensure(ctx, ctx->sB, (size_t)p.QB * nr * sizeof(float)));
+    for (int d = 0; d < 4; ++d)
+      EPH_CK(make_tc_map_bf16(&ctx->mapDB[d], static_cast<char*>(ctx->DB.p) + d * dslice * 2, (long)p.QB * nr, kpd,
+                              128));
+  } else {
+    EPH_TRY(ensure(ctx, ctx->Bhi, (size_t)p.QB * nr * kp * sizeof(float)));
+    EPH_TRY(ensure(ctx, ctx->Blo, (size_t)p.QB * nr * kp * sizeof(float)));
+  }
+  EPH_TRY(ensure(ctx, ctx->G3f, (size_t)p.QB * p.KT * nr * sizeof(float)));
+  EPH_TRY(ensure(ctx, ctx->Hkq, (size_t)p.QB * p.KT * nb2 * sizeof(double2)));
+  if (host && g) EPH_TRY(ensure(ctx, ctx->g_stage32, (size_t)p.QB * p.KT * gcols * 2 * sizeof(float)));
+  if (!digits) {
+    EPH_CK(make_tc_map(&ctx->mapBhi, as<float>(ctx->Bhi), (long)p.QB * nr, kp, 256));
+    EPH_CK(make_tc_map(&ctx->mapBlo, as<float>(ctx->Blo), (long)p.QB * nr, kp, 256));
+  }
+  const double* qdev = static_cast<const double*>(dq);
+  double2* W = as<double2>(ctx->W);
+  for (int q0 = 0; q0 < nq; q0 += p.QB) {
+    const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
+    if (omega)
+      EPH_CK(cudaMemcpyAsync(omega + (long)q0 * nm, ctx->omq.p, (size_t)nqb * nm * sizeof(double), out_kind(ctx),
+                             ctx->stream));
+    // B operand per q: real embedding of the mode-rotated G2 columns of W_q
+    if (digits)
+      EPH_LAUNCH_S(EPH_STAGE_MODE, launch_digits_b(W, p.NW, (long)ne * p.NW, nb2, (int)gcols, ne, kpd, nqb,
+                                                   as<float>(ctx->sB), ctx->DB.p, (long)dslice, ctx->stream));
+    else
+      EPH_LAUNCH_S(EPH_STAGE_MODE, launch_split_b(W, p.NW, (long)ne * p.NW, nb2, (int)gcols, ne, kp, nqb,
+                                                  as<float>(ctx->Bhi), as<float>(ctx->Blo), ctx->stream));
+    for (long k0 = 0; k0 < nk; k0 += p.KT) {
+      const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
+      // H(k+q) in FP64 (the eigensolve needs it), then its Jacobi
+      EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nkt, nb2, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0, W, p.NW,
+                                                (long)ne * p.NW, as<double2>(ctx->Hkq), nb2, (long)nkt * nb2, nqb,
+                                                ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(as<double2>(ctx->Hkq), nb2, nb, nb, (long)nqb * nkt,
+                                                as<double>(ctx->eps_tile), nb, as<double2>(ctx->Ukq), nb2,
+                                                ctx->opt.max_sweeps, ctx->status, ctx->stream));
+      if (eps_kq)
+        for (int iq = 0; iq < nqb; ++iq)
+          EPH_CK(cudaMemcpyAsync(eps_kq + ((long)(q0 + iq) * nk + k0) * nb,
+                                 as<double>(ctx->eps_tile) + (long)iq * nkt * nb, (size_t)nkt * nb * sizeof(double),
+                                 out_kind(ctx), ctx->stream));
+      if (!g) continue;
+      // G3 = P_k G2 on the tensor cores (FP32 result)
+      if (digits)
+        EPH_LAUNCH_S(EPH_STAGE_TC, launch_tc_fixed_gemm(ctx->mapDA, ctx->mapDB, nkt, (int)k0, (int)nr, kpd, nqb,
+                                                          (float)ctx->scaleA, as<float>(ctx->sB), as<float>(ctx->G3f),
+                                                          nr, (long)nkt * nr, ctx->status + 1, ctx->stream));
+      else
+        EPH_LAUNCH_S(EPH_STAGE_TC, launch_tc_split_gemm(&ctx->mapAhi, &ctx->mapAlo, &ctx->mapBhi, &ctx->mapBlo, nkt,
+                                                          (int)k0, (int)nr, kp, nqb, as<float>(ctx->G3f), nr,
+                                                          (long)nkt * nr, ctx->status + 1, ctx->stream));
+      float* gout = static_cast<float*>(g);
+      if (host) {
+        EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate_ff(as<float>(ctx->G3f), nr, as<double2>(ctx->Ukq),
+                                                            as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
+                                                            as<float>(ctx->g_stage32), 2L * nkt * gcols, ctx->stream));
+        for (int iq = 0; iq < nqb; ++iq)
+          EPH_CK(cudaMemcpyAsync(gout + 2L * ((long)(q0 + iq) * nk + k0) * gcols,
+                                 as<float>(ctx->g_stage32) + 2L * iq * nkt * gcols,
+                                 (size_t)nkt * gcols * 2 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+      } else {
+        EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate_ff(as<float>(ctx->G3f), nr, as<double2>(ctx->Ukq),
+                                                            as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
+                                                            gout + 2L * ((long)q0 * nk + k0) * gcols, 2L * nk * gcols,
+                                                            ctx->stream));
+      }
+    }
+  }
+  return finish(ctx);
+}
+
 }  // namespace
 
 extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
   if (!ctx) return EPH_EINVAL;
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
   if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
+  if (ctx->opt.form == EPH_FORM_MIXED) return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
   const int nb = ctx->nb, nm = ctx->nm, nk = ctx->nk;
   const int nb2 = nb * nb;
   const bool host = !ctx->opt.device_ptrs;

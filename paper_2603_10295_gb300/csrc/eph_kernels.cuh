@@ -70,4 +70,31 @@ cudaError_t launch_sum_into(const double* v, long n, double* L, cudaStream_t st)
 cudaError_t launch_mode_rotate_adj(const double2* G2b, const double2* u, int nq, int nm, int ne, int nb2,
                                    double2* G1b, cudaStream_t st);
 
+// ---- mixed form (split-TF32 tensor-core Re->k contraction) -------------------------
+// TMA descriptor (CUtensorMap, 128 bytes) over a row-major FP32 [rows][kp] array:
+// box 32 (k) x box_rows, 128-byte swizzle.  kp must be a multiple of 32.
+cudaError_t make_tc_map(void* map_out, const float* base, long rows, int kp, int box_rows);
+// C[q][m][n] = (Ahi Bhi + Ahi Blo + Alo Bhi) over k; A rows a_row0 + m (box 128 rows),
+// B rows q*Nr + n (box 256 rows); C row stride ldc, batch stride sC; err |= timeout bits.
+cudaError_t launch_tc_split_gemm(const void* mAhi, const void* mAlo, const void* mBhi, const void* mBlo, int M,
+                                 int a_row0, int Nr, int Kp, int nq, float* C, long ldc, long sC, int* err,
+                                 cudaStream_t st);
+cudaError_t launch_split_a(const double2* P, long ldp, int n, int ne, int kp, float* Ahi, float* Alo,
+                           cudaStream_t st);
+cudaError_t launch_split_b(const double2* W, long ldw, long sW, int col0, int ncols, int ne, int kp, int nq,
+                           float* Bhi, float* Blo, cudaStream_t st);
+cudaError_t launch_band_rotate_f32(const float* Y, long ldy_floats, const double2* Ukq, const double2* Uk, int nq,
+                                   int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st);
+// Band rotation with double-float accumulation (FP64 gauges as float pairs), complex64 out.
+cudaError_t launch_band_rotate_ff(const float* Y, long ldy_floats, const double2* Ukq, const double2* Uk, int nq,
+                                  int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st);
+// Fixed-point BF16 digits (A: 3, B: 4 per value; exact tensor-core accumulation); D slices of n*kp / slice.
+cudaError_t make_tc_map_bf16(void* map_out, const void* base, long rows, int kp, int box_rows);
+cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, double scale, void* D, cudaStream_t st);
+cudaError_t launch_digits_b(const double2* W, long ldw, long sW, int col0, int ncols, int ne, int kp, int nq,
+                            float* sB, void* D, long slice, cudaStream_t st);
+// C = sA sB[col] 2^-16 sum_l 2^-8l L_l on tcgen05 kind::f16; maps: 3 CUtensorMaps (A), 4 (B).
+cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
+                                 float sA, const float* sB, float* C, long ldc, long sC, int* err, cudaStream_t st);
+
 }  // namespace eph

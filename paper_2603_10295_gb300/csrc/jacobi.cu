@@ -16,7 +16,8 @@
 // sec. 8.5, with the phase of b factored out): tau = (d - a)/(2|b|),
 // t = sign(tau)/(|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c,
 // J = [[c, sigma], [-conj(sigma), c]] with sigma = s b/|b|; then
-// (J^H A J)_pq = 0, a' = a - t|b|, d' = d + t|b|.
+// (J^H A J)_pq = 0, a' = a - t|b|, d' = d + t|b|.  Evaluated through
+// r = t/|b| (one sqrt, one division, one rsqrt per rotation).
 #include "eph_kernels.cuh"
 
 namespace eph {
@@ -34,7 +35,7 @@ __device__ __forceinline__ double2 shfl_d2(double2 v, int src) {
 }
 
 template <int NP, int R>
-__device__ __forceinline__ void jacobi_round(double2 (&a)[NP], double2 (&v)[NP], int j, int base, double thresh) {
+__device__ __forceinline__ void jacobi_round(double2 (&a)[NP], double2 (&v)[NP], int j, int base, double thresh2) {
   const int p = rr_partner(j, R, NP);
   const bool lower = j < p;
   double d = 0.0;
@@ -49,16 +50,18 @@ __device__ __forceinline__ void jacobi_round(double2 (&a)[NP], double2 (&v)[NP],
   const double app = lower ? d : dp;
   const double aqq = lower ? dp : d;
   const double2 bq = lower ? y : x;  // A[lo][hi]
-  const double bn = hypot(bq.x, bq.y);
-  double c = 1.0, t = 0.0;
+  // r = t/|b| = 2 sign(dd) / (|dd| + sqrt(dd^2 + 4|b|^2)), dd = aqq - app: the same t as
+  // sign(tau)/(|tau| + sqrt(1 + tau^2)) with tau = dd/(2|b|), without forming |b|.
+  const double b2 = fma(bq.x, bq.x, bq.y * bq.y);
+  double c = 1.0, tb = 0.0;  // tb = t |b| = r |b|^2
   double2 sig = make_double2(0.0, 0.0);
-  const bool rot = bn > thresh;
-  if (rot) {
-    const double tau = (aqq - app) / (2.0 * bn);
-    t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-    c = 1.0 / sqrt(1.0 + t * t);
-    const double s = t * c / bn;
-    sig = make_double2(s * bq.x, s * bq.y);
+  if (b2 > thresh2) {
+    const double dd = aqq - app;
+    const double r = copysign(2.0, dd) / (fabs(dd) + sqrt(fma(dd, dd, 4.0 * b2)));
+    tb = r * b2;
+    c = rsqrt(fma(r * r, b2, 1.0));
+    const double cr = c * r;
+    sig = make_double2(cr * bq.x, cr * bq.y);
   }
   // column mix (A J, V J): lower lane: c a_p - conj(sig) a_q; upper lane: sig a_p + c a_q
   const double2 coef = lower ? make_double2(-sig.x, sig.y) : sig;
@@ -78,8 +81,6 @@ __device__ __forceinline__ void jacobi_round(double2 (&a)[NP], double2 (&v)[NP],
   // row_hi' = conj(sig) row_lo + c row_hi
 #pragma unroll
   for (int lo = 0; lo < NP; ++lo) {
-    constexpr int dummy = 0;
-    (void)dummy;
     const int hi = rr_partner(lo, R, NP);
     if (hi > lo) {
       const double cc = shfl_d(c, base + lo);
@@ -90,7 +91,7 @@ __device__ __forceinline__ void jacobi_round(double2 (&a)[NP], double2 (&v)[NP],
     }
   }
   // exact values of the rotated 2x2 block
-  const double nd = lower ? app - t * bn : aqq + t * bn;
+  const double nd = lower ? app - tb : aqq + tb;
 #pragma unroll
   for (int rho = 0; rho < NP; ++rho) {
     if (rho == p) a[rho] = make_double2(0.0, 0.0);
@@ -144,14 +145,14 @@ __global__ void __launch_bounds__(128) k_jacobi(const double2* __restrict__ A, l
   double fro2 = 0.0;
 #pragma unroll
   for (int i = 0; i < NP; ++i) fro2 += shfl_d(my2, base + i);
-  const double thresh = 1e-18 * sqrt(fro2) + 1e-300;
+  const double thresh2 = 1e-36 * fro2 + 1e-300;  // rotations with |b| below 1e-18 ||A||_F are skipped
   const double tol2 = 1e-30 * fro2;
 
   bool conv = !valid;
   int post = valid ? 0 : 1;
   int sweep = 0;
   while (__any_sync(0xffffffffu, !(conv && post >= 1)) && sweep < max_sweeps) {
-    Sweep<NP, 0>::run(a, v, j, base, thresh);
+    Sweep<NP, 0>::run(a, v, j, base, thresh2);
     ++sweep;
     if (conv) ++post;
     double off = 0.0;

@@ -1,0 +1,358 @@
+// Mixed form: operand preparation for the split-TF32 tensor-core Re->k
+// contraction, and the FP32 band rotation that turns G3 into complex64 g.
+//
+// Real embedding of the complex product G3 = P_k G2 (Eq. 10 Fourier sum):
+//   A[m][2e+t]      = (Re, Im)[t] of P_k[m][e]                       (K-major)
+//   B[2j+s][2e+t]   = [[Re G2, -Im G2], [Im G2, Re G2]][s][t] at (e, j)   (K-major, one block per q)
+// so that C[m][2j+s] = sum_{e,t} A[m][2e+t] B[2j+s][2e+t] is (Re, Im)[s] of G3[m][j]:
+// the output is G3 as interleaved complex64.  K is zero-padded to a multiple of 32.
+// Each FP64 value x is split as hi = tf32(x), lo = tf32(x - hi) (round to nearest).
+#include <cuda_bf16.h>
+
+#include "eph_kernels.cuh"
+
+namespace eph {
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void split2(double x, float& hi, float& lo) {
+  hi = tf32_rna(static_cast<float>(x));
+  lo = tf32_rna(static_cast<float>(x - static_cast<double>(hi)));
+}
+
+// A operand: P[n][ne] complex128 (row stride ldp) -> Ahi, Alo [n][kp] float.
+__global__ void k_split_a(const double2* __restrict__ P, long ldp, int n, int ne, int kp, float* __restrict__ Ahi,
+                          float* __restrict__ Alo) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)n * kp) return;
+  const long m = idx / kp;
+  const int c = (int)(idx - m * kp);
+  double x = 0.0;
+  if (c < 2 * ne) {
+    const double2 p = P[m * ldp + (c >> 1)];
+    x = (c & 1) ? p.y : p.x;
+  }
+  float hi, lo;
+  split2(x, hi, lo);
+  Ahi[idx] = hi;
+  Alo[idx] = lo;
+}
+
+cudaError_t launch_split_a(const double2* P, long ldp, int n, int ne, int kp, float* Ahi, float* Alo, cudaStream_t st) {
+  const long tot = (long)n * kp;
+  if (tot <= 0) return cudaSuccess;
+  k_split_a<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, ldp, n, ne, kp, Ahi, Alo);
+  return cudaGetLastError();
+}
+
+// B operand for each q of a batch: G2 = W[q][e][col0 + j] (row stride ldw, batch stride sW),
+// j < ncols -> Bhi, Blo [q][2*ncols][kp].
+__global__ void k_split_b(const double2* __restrict__ W, long ldw, long sW, int col0, int ncols, int ne, int kp,
+                          int nq, float* __restrict__ Bhi, float* __restrict__ Blo) {
+  const long per_q = 2L * ncols * kp;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= per_q * nq) return;
+  const int q = (int)(idx / per_q);
+  const long rem = idx - (long)q * per_q;
+  const int row = (int)(rem / kp);
+  const int c = (int)(rem - (long)row * kp);
+  double x = 0.0;
+  if (c < 2 * ne) {
+    const int e = c >> 1, t = c & 1, j = row >> 1, s = row & 1;
+    const double2 g = W[(long)q * sW + (long)e * ldw + col0 + j];
+    // [[Re, -Im], [Im, Re]][s][t]
+    x = (s == t) ? g.x : (s == 0 ? -g.y : g.y);
+  }
+  float hi, lo;
+  split2(x, hi, lo);
+  Bhi[idx] = hi;
+  Blo[idx] = lo;
+}
+
+cudaError_t launch_split_b(const double2* W, long ldw, long sW, int col0, int ncols, int ne, int kp, int nq,
+                           float* Bhi, float* Blo, cudaStream_t st) {
+  const long tot = 2L * ncols * kp * nq;
+  if (tot <= 0) return cudaSuccess;
+  k_split_b<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, kp, nq, Bhi, Blo);
+  return cudaGetLastError();
+}
+
+// FP32 band rotation: g[q][k][nu] = V_{k+q}^H G3[q][k][nu] V_k with G3 complex64 rows of
+// nm*nb*nb (row stride ldy floats pairs), V in FP64 (rounded to FP32), g complex64.
+__global__ void __launch_bounds__(128) k_band_rotate_f32(const float2* __restrict__ Y, long ldy,
+                                                         const double2* __restrict__ Ukq,
+                                                         const double2* __restrict__ Uk, int nk, int nm, int nb,
+                                                         float2* __restrict__ g, long sgq) {
+  extern __shared__ float2 smf[];
+  const int nb2 = nb * nb;
+  float2* uk = smf;
+  float2* ukq = uk + nb2;
+  float2* G = ukq + nb2;
+  float2* T = G + nm * nb2;
+  const long pair = blockIdx.x;
+  const int k = (int)(pair % nk);
+  const long q = pair / nk;
+  for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
+    const double2 a = Uk[(long)k * nb2 + t], b = Ukq[pair * nb2 + t];
+    uk[t] = make_float2((float)a.x, (float)a.y);
+    ukq[t] = make_float2((float)b.x, (float)b.y);
+  }
+  const float2* grow = Y + pair * ldy;
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) G[t] = grow[t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2, a = rem / nb, n = rem - a * nb;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int b = 0; b < nb; ++b) {
+      const float2 x = G[nu * nb2 + a * nb + b], y = uk[b * nb + n];
+      acc.x = fmaf(x.x, y.x, fmaf(-x.y, y.y, acc.x));
+      acc.y = fmaf(x.x, y.y, fmaf(x.y, y.x, acc.y));
+    }
+    T[t] = acc;
+  }
+  __syncthreads();
+  float2* out = g + q * sgq + (long)k * nm * nb2;
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, n = rem - m * nb;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int a = 0; a < nb; ++a) {
+      const float2 x = ukq[a * nb + m], y = T[nu * nb2 + a * nb + n];
+      acc.x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc.x));
+      acc.y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc.y));
+    }
+    out[t] = acc;
+  }
+}
+
+cudaError_t launch_band_rotate_f32(const float* Y, long ldy_floats, const double2* Ukq, const double2* Uk, int nq,
+                                   int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st) {
+  const long pairs = (long)nq * nk;
+  if (pairs <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(2 * nb * nb + 2 * nm * nb * nb) * sizeof(float2);
+  if (smem > 200 * 1024 || (ldy_floats & 1) || (sgq_floats & 1)) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_band_rotate_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
+  k_band_rotate_f32<<<(unsigned)pairs, 128, smem, st>>>(reinterpret_cast<const float2*>(Y), ldy_floats / 2, Ukq, Uk,
+                                                         nk, nm, nb, reinterpret_cast<float2*>(g), sgq_floats / 2);
+  return cudaGetLastError();
+}
+
+// ---- fixed-point BF16 digits (exact tensor-core accumulation) ------------------------
+// x/s = sum_i d_i 2^-8(i+1) + O(2^-8n-1), integer digits |d| <= 128 (exact in bf16);
+// s is a power of two with |x| <= s/2 for every x of the row (A: all rows share sA).
+__device__ __forceinline__ void digits3(double x, double inv_s, __nv_bfloat16& d0, __nv_bfloat16& d1,
+                                        __nv_bfloat16& d2) {
+  double y = x * inv_s * 256.0;
+  const double a0 = rint(y);
+  y = (y - a0) * 256.0;
+  const double a1 = rint(y);
+  y = (y - a1) * 256.0;
+  const double a2 = rint(y);
+  d0 = __float2bfloat16_rn((float)a0);
+  d1 = __float2bfloat16_rn((float)a1);
+  d2 = __float2bfloat16_rn((float)a2);
+}
+
+// A digits: P[n][ne] complex128 (row stride ldp) -> D[3][n][kp] bf16 (slice stride n*kp).
+__global__ void k_digits_a(const double2* __restrict__ P, long ldp, int n, int ne, int kp, double inv_s,
+                           __nv_bfloat16* __restrict__ D) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long tot = (long)n * kp;
+  if (idx >= tot) return;
+  const long m = idx / kp;
+  const int c = (int)(idx - m * kp);
+  double x = 0.0;
+  if (c < 2 * ne) {
+    const double2 p = P[m * ldp + (c >> 1)];
+    x = (c & 1) ? p.y : p.x;
+  }
+  digits3(x, inv_s, D[idx], D[tot + idx], D[2 * tot + idx]);
+}
+
+cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, double scale, void* D, cudaStream_t st) {
+  const long tot = (long)n * kp;
+  if (tot <= 0) return cudaSuccess;
+  k_digits_a<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, ldp, n, ne, kp, 1.0 / scale,
+                                                          static_cast<__nv_bfloat16*>(D));
+  return cudaGetLastError();
+}
+
+// Per output column j of each q: s = 2^(e+1) with max_e(|Re G2|, |Im G2|) = f 2^e, f in [0.5, 1).
+__global__ void k_colscale_b(const double2* __restrict__ W, long ldw, long sW, int col0, int ncols, int ne, int nq,
+                             float* __restrict__ sB, long nr_stride) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)ncols * nq) return;
+  const int q = (int)(idx / ncols);
+  const int j = (int)(idx - (long)q * ncols);
+  double mx = 0.0;
+  for (int e = 0; e < ne; ++e) {
+    const double2 g = W[(long)q * sW + (long)e * ldw + col0 + j];
+    mx = fmax(mx, fmax(fabs(g.x), fabs(g.y)));
+  }
+  float s = 1.0f;
+  if (mx > 0.0) {
+    int ex;
+    frexp(mx, &ex);
+    s = (float)ldexp(1.0, ex + 1);
+  }
+  sB[(long)q * nr_stride + 2 * j] = s;
+  sB[(long)q * nr_stride + 2 * j + 1] = s;
+}
+
+// B digits: real embedding of the G2 columns of W (as k_split_b) scaled by sB -> D[4][QB*nr][kp].
+__global__ void k_digits_b(const double2* __restrict__ W, long ldw, long sW, int col0, int ncols, int ne, int kp,
+                           int nq, const float* __restrict__ sB, long slice, __nv_bfloat16* __restrict__ D) {
+  const long per_q = 2L * ncols * kp;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= per_q * nq) return;
+  const int q = (int)(idx / per_q);
+  const long rem = idx - (long)q * per_q;
+  const int row = (int)(rem / kp);
+  const int c = (int)(rem - (long)row * kp);
+  double x = 0.0;
+  if (c < 2 * ne) {
+    const int e = c >> 1, t = c & 1, j = row >> 1, sgn = row & 1;
+    const double2 g = W[(long)q * sW + (long)e * ldw + col0 + j];
+    x = (sgn == t) ? g.x : (sgn == 0 ? -g.y : g.y);
+  }
+  const double inv_s = 1.0 / (double)sB[(long)q * 2 * ncols + row];
+  double y = x * inv_s * 256.0;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const double a = rint(y);
+    D[d * slice + idx] = __float2bfloat16_rn((float)a);
+    y = (y - a) * 256.0;
+  }
+}
+
+cudaError_t launch_digits_b(const double2* W, long ldw, long sW, int col0, int ncols, int ne, int kp, int nq,
+                            float* sB, void* D, long slice, cudaStream_t st) {
+  const long cols = (long)ncols * nq;
+  if (cols <= 0) return cudaSuccess;
+  k_colscale_b<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, nq, sB, 2L * ncols);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long tot = 2L * ncols * kp * nq;
+  k_digits_b<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, kp, nq, sB, slice,
+                                                           static_cast<__nv_bfloat16*>(D));
+  return cudaGetLastError();
+}
+
+// ---- band rotation with double-float accumulation ---------------------------------------
+// g = V_{k+q}^H G3 V_k with G3 complex64 and V in FP64 carried as float pairs (hi + lo);
+// products are formed exactly with fma and sums with two-sum, so the rotation adds no error
+// beyond the final rounding of g to complex64.
+namespace {
+__device__ __forceinline__ float2 ff_split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+// (sh, sl) += a * (bh + bl)
+// __fmul_rn/__fadd_rn are never contracted into FMAs, which the error-free transforms rely on.
+__device__ __forceinline__ void two_sum_acc(float& sh, float& sl, float p, float e) {
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+  sh = s;
+}
+__device__ __forceinline__ void ff_mac1(float& sh, float& sl, float a, float bh, float bl) {
+  const float p = __fmul_rn(a, bh);
+  float e = fmaf(a, bh, -p);
+  e = fmaf(a, bl, e);
+  two_sum_acc(sh, sl, p, e);
+}
+// (sh, sl) += (ah + al) * (bh + bl)
+__device__ __forceinline__ void ff_mac2(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  two_sum_acc(sh, sl, p, e);
+}
+}  // namespace
+
+__global__ void __launch_bounds__(128) k_band_rotate_ff(const float2* __restrict__ Y, long ldy,
+                                                        const double2* __restrict__ Ukq,
+                                                        const double2* __restrict__ Uk, int nk, int nm, int nb,
+                                                        float2* __restrict__ g, long sgq) {
+  extern __shared__ float2 smf2[];
+  const int nb2 = nb * nb;
+  float2* ukr = smf2;            // [nb2] (hi, lo) of Re V_k
+  float2* uki = ukr + nb2;       // [nb2] (hi, lo) of Im V_k
+  float2* uqr = uki + nb2;
+  float2* uqi = uqr + nb2;
+  float2* G = uqi + nb2;         // [nm*nb2] complex64
+  float2* Tr = G + nm * nb2;     // [nm*nb2] (hi, lo) of Re T
+  float2* Ti = Tr + nm * nb2;    // [nm*nb2] (hi, lo) of Im T
+  const long pair = blockIdx.x;
+  const int k = (int)(pair % nk);
+  const long q = pair / nk;
+  for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
+    const double2 a = Uk[(long)k * nb2 + t], b = Ukq[pair * nb2 + t];
+    ukr[t] = ff_split(a.x);
+    uki[t] = ff_split(a.y);
+    uqr[t] = ff_split(b.x);
+    uqi[t] = ff_split(b.y);
+  }
+  const float2* grow = Y + pair * ldy;
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) G[t] = grow[t];
+  __syncthreads();
+  // T[nu][a][n] = sum_b G[nu][a][b] V_k[b][n]
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2, a = rem / nb, n = rem - a * nb;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int b = 0; b < nb; ++b) {
+      const float2 x = G[nu * nb2 + a * nb + b];
+      const float2 ur = ukr[b * nb + n], ui = uki[b * nb + n];
+      ff_mac1(rh, rl, x.x, ur.x, ur.y);
+      ff_mac1(rh, rl, -x.y, ui.x, ui.y);
+      ff_mac1(ih, il, x.x, ui.x, ui.y);
+      ff_mac1(ih, il, x.y, ur.x, ur.y);
+    }
+    Tr[t] = make_float2(rh, rl);
+    Ti[t] = make_float2(ih, il);
+  }
+  __syncthreads();
+  // g[nu][m][n] = sum_a conj(V_{k+q}[a][m]) T[nu][a][n]
+  float2* out = g + q * sgq + (long)k * nm * nb2;
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, n = rem - m * nb;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int a = 0; a < nb; ++a) {
+      const float2 vr = uqr[a * nb + m], vi = uqi[a * nb + m];
+      const float2 tr = Tr[nu * nb2 + a * nb + n], ti = Ti[nu * nb2 + a * nb + n];
+      // conj(v) t = (vr tr + vi ti) + i (vr ti - vi tr)
+      ff_mac2(rh, rl, vr.x, vr.y, tr.x, tr.y);
+      ff_mac2(rh, rl, vi.x, vi.y, ti.x, ti.y);
+      ff_mac2(ih, il, vr.x, vr.y, ti.x, ti.y);
+      ff_mac2(ih, il, -vi.x, -vi.y, tr.x, tr.y);
+    }
+    out[t] = make_float2(__fadd_rn(rh, rl), __fadd_rn(ih, il));
+  }
+}
+
+cudaError_t launch_band_rotate_ff(const float* Y, long ldy_floats, const double2* Ukq, const double2* Uk, int nq,
+                                  int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st) {
+  const long pairs = (long)nq * nk;
+  if (pairs <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(4 * nb * nb + 3 * nm * nb * nb) * sizeof(float2);
+  if (smem > 200 * 1024 || (ldy_floats & 1) || (sgq_floats & 1)) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_band_rotate_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
+  k_band_rotate_ff<<<(unsigned)pairs, 128, smem, st>>>(reinterpret_cast<const float2*>(Y), ldy_floats / 2, Ukq, Uk, nk,
+                                                        nm, nb, reinterpret_cast<float2*>(g), sgq_floats / 2);
+  return cudaGetLastError();
+}
+
+}  // namespace eph

@@ -1,0 +1,503 @@
+// Split-precision GEMM on the 5th-generation tensor cores (tcgen05, kind::tf32):
+//
+//   C[q][m][n] = sum_k (Ahi Bhi + Ahi Blo + Alo Bhi)[m][k] [q][n][k]      (FP32 result)
+//
+// with A = Ahi + Alo and B = Bhi + Blo the two-term TF32 splits of FP32 operands
+// (3-term product: the lo*lo term, 2^-22 relative, is dropped).  The large term
+// accumulates in one TMEM accumulator and the two correction terms in a second
+// one; they are added once in the epilogue (compensated recombination: the
+// small terms are not rounded against the large running sum).
+//
+// In the mixed form this is the Re->k contraction of Eq. 10 on the real
+// embedding of the complex product (A = [Re P_k, Im P_k] interleaved, B the
+// 2x2 real blocks of G2), so C holds G3 as interleaved complex64.
+//
+// CTA tile 128 (m) x 256 (n), K in 32-float (128-byte) slices; 2-stage TMA ->
+// shared memory (128B swizzle) pipeline; warp 0 lane 0 issues TMA, warp 1
+// lane 0 issues tcgen05.mma (M=128, N=256, K=8 per instruction) and commits to
+// mbarriers; all four warps drain TMEM (32 lanes each) in the epilogue.  Every
+// mbarrier wait is bounded: on a timeout the CTA sets *err, stops issuing,
+// drains what it issued (bounded again), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "eph_kernels.cuh"
+
+namespace eph {
+
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 32, STAGES = 2;
+constexpr int A_BYTES = BM * BK * 4;                         // 16 KiB
+constexpr int B_BYTES = BN * BK * 4;                         // 32 KiB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;       // 96 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;
+constexpr uint32_t TMEM_COLS = 512;                          // acc0: columns 0..255, acc1: 256..511
+constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;       // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, rows of 128 B, 128-byte swizzle,
+// 8-row core-matrix groups 1024 B apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, M = 128, N = 256.
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+}  // namespace tc
+
+__global__ void __launch_bounds__(128, 1) k_tc_split_gemm(const __grid_constant__ CUtensorMap mAhi,
+                                                          const __grid_constant__ CUtensorMap mAlo,
+                                                          const __grid_constant__ CUtensorMap mBhi,
+                                                          const __grid_constant__ CUtensorMap mBlo, int M,
+                                                          int a_row0, int Nr, int Kp, float* __restrict__ C, long ldc,
+                                                          long sC, int* __restrict__ err) {
+  using namespace tc;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, q = blockIdx.z;
+  const int nkb = Kp / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto stage_ptr = [&](int s, int which) -> unsigned char* {
+    const int off[4] = {0, A_BYTES, 2 * A_BYTES, 2 * A_BYTES + B_BYTES};
+    return smem + s * STAGE_BYTES + off[which];
+  };
+
+  int issued = 0;  // producer: k blocks whose loads were issued
+  int mma_ok = 1;  // MMA thread: all k blocks consumed
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
+        *abort_flag = 1;
+        atomicOr(err, 1);
+        break;
+      }
+      if (*abort_flag) break;
+      mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(stage_ptr(s, 0), &mAhi, kb * BK, a_row0 + m0, &full[s]);
+      tma_load_2d(stage_ptr(s, 1), &mAlo, kb * BK, a_row0 + m0, &full[s]);
+      tma_load_2d(stage_ptr(s, 2), &mBhi, kb * BK, q * Nr + n0, &full[s]);
+      tma_load_2d(stage_ptr(s, 3), &mBlo, kb * BK, q * Nr + n0, &full[s]);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (*abort_flag || !mbar_wait(&full[s], (kb / STAGES) & 1)) {
+        *abort_flag = 1;
+        atomicOr(err, 2);
+        mma_ok = 0;
+        break;
+      }
+      fence_after();
+      const uint64_t dAhi = smem_desc(smem_u32(stage_ptr(s, 0)));
+      const uint64_t dAlo = smem_desc(smem_u32(stage_ptr(s, 1)));
+      const uint64_t dBhi = smem_desc(smem_u32(stage_ptr(s, 2)));
+      const uint64_t dBlo = smem_desc(smem_u32(stage_ptr(s, 3)));
+#pragma unroll
+      for (int kk = 0; kk < BK / 8; ++kk) {
+        const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 8 tf32 = 32 bytes along K inside the swizzle atom
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        mma_tf32(tmem, dAhi + o, dBhi + o, acc);
+        mma_tf32(tmem + 256, dAhi + o, dBlo + o, acc);
+        mma_tf32(tmem + 256, dAlo + o, dBhi + o, 1u);
+      }
+      mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+    }
+    mma_commit(done);  // all MMAs issued by this thread have completed
+  }
+  __syncwarp();
+
+  const bool ok = mbar_wait(done, 0);
+  if (!ok) atomicOr(err, 4);
+  fence_after();
+  if (ok && mma_ok && !*abort_flag) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    float* crow = C + (long)q * sC + (long)row * ldc;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r0[16], r1[16];
+      tmem_ld16(tl + c0, r0);
+      tmem_ld16(tl + 256 + c0, r1);
+      tmem_ld_wait();
+      if (row < M) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int col = n0 + c0 + i;
+          if (col < Nr) crow[col] = __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
+        }
+      }
+    }
+  }
+  // drain: after an abort the producer waits (bounded) for its last loads of each stage
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
+      const int s = kb % STAGES;
+      mbar_wait(&full[s], (kb / STAGES) & 1);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ----------------------------------------------------------------------------- fixed-point BF16 digits
+// C[q][m][n] = sA * sB[q*Nr+n] * 2^-16 * sum_l 2^-8l L_l,   L_l = sum_{i+j=l} sum_k dA_i[m][k] dB_j[n][k]
+// where x/s = sum_i d_i 2^-8(i+1) with integer digits |d| <= 128 held exactly in
+// bf16 (A: 3 digits, B: 4 digits, s a power of two >= 2 max|x| of the row).
+// Every digit product is an integer below 2^14, so the level-0 sum over K <= 1024
+// stays below 2^24 and the FP32 tensor-core accumulation is exact; the rounding
+// of levels 1-3 is 2^-8 .. 2^-24 smaller still.  B carries a 4th digit because
+// the mode-rotated g(Re,q) columns decay over Re, and the fixed-point error is
+// relative to the row maximum.  Four TMEM accumulators (levels 0-3, 128
+// columns each), nine bf16 MMAs per K step (i+j <= 3), combined once.
+namespace tcf {
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 2, NA = 3, NB = 4;   // BK bf16 = 128 B rows
+constexpr int A_BYTES = BM * BK * 2;                              // 16 KiB per digit slice
+constexpr int B_BYTES = BN * BK * 2;                              // 16 KiB
+constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;          // 112 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;     // 225 KiB
+constexpr uint32_t TMEM_COLS = 512;                               // levels at columns 0, 128, 256, 384
+// kind::f16 instruction descriptor: D f32, A/B bf16, K-major, M = 128, N = 128 (K = 16 per MMA)
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+}  // namespace tcf
+
+struct TcMaps7 {
+  CUtensorMap a[3];
+  CUtensorMap b[4];
+};
+
+__global__ void __launch_bounds__(128, 1) k_tc_fixed_gemm(const __grid_constant__ TcMaps7 maps, int M, int a_row0,
+                                                          int Nr, int Kp, float sA, const float* __restrict__ sB,
+                                                          float* __restrict__ C, long ldc, long sC,
+                                                          int* __restrict__ err) {
+  using namespace tc;
+  using tcf::BM;
+  using tcf::BN;
+  using tcf::BK;
+  using tcf::STAGES;
+  using tcf::NA;
+  using tcf::NB;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * tcf::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, q = blockIdx.z;
+  const int nkb = Kp / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tcf::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // stage layout: A digits 0..2 then B digits 0..3, 16 KiB each
+  auto tile = [&](int s, int which) -> unsigned char* { return smem + s * tcf::STAGE_BYTES + which * tcf::A_BYTES; };
+
+  int issued = 0;
+  int mma_ok = 1;
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
+        *abort_flag = 1;
+        atomicOr(err, 1);
+        break;
+      }
+      if (*abort_flag) break;
+      mbar_arrive_expect_tx(&full[s], tcf::STAGE_BYTES);
+#pragma unroll
+      for (int d = 0; d < NA; ++d) tma_load_2d(tile(s, d), &maps.a[d], kb * BK, a_row0 + m0, &full[s]);
+#pragma unroll
+      for (int d = 0; d < NB; ++d) tma_load_2d(tile(s, NA + d), &maps.b[d], kb * BK, q * Nr + n0, &full[s]);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (*abort_flag || !mbar_wait(&full[s], (kb / STAGES) & 1)) {
+        *abort_flag = 1;
+        atomicOr(err, 2);
+        mma_ok = 0;
+        break;
+      }
+      fence_after();
+      uint64_t da[NA], db[NB];
+#pragma unroll
+      for (int d = 0; d < NA; ++d) da[d] = smem_desc(smem_u32(tile(s, d)));
+#pragma unroll
+      for (int d = 0; d < NB; ++d) db[d] = smem_desc(smem_u32(tile(s, NA + d)));
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K inside the swizzle atom
+        const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+        tcf::mma_bf16(tmem + 0, da[0] + o, db[0] + o, first);     // level 0: d0 d0
+        tcf::mma_bf16(tmem + 128, da[0] + o, db[1] + o, first);   // level 1: d0 d1 + d1 d0
+        tcf::mma_bf16(tmem + 128, da[1] + o, db[0] + o, 1u);
+        tcf::mma_bf16(tmem + 256, da[0] + o, db[2] + o, first);   // level 2: d0 d2 + d1 d1 + d2 d0
+        tcf::mma_bf16(tmem + 256, da[1] + o, db[1] + o, 1u);
+        tcf::mma_bf16(tmem + 256, da[2] + o, db[0] + o, 1u);
+        tcf::mma_bf16(tmem + 384, da[0] + o, db[3] + o, first);   // level 3: d0 d3 + d1 d2 + d2 d1
+        tcf::mma_bf16(tmem + 384, da[1] + o, db[2] + o, 1u);
+        tcf::mma_bf16(tmem + 384, da[2] + o, db[1] + o, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+
+  const bool ok = mbar_wait(done, 0);
+  if (!ok) atomicOr(err, 4);
+  fence_after();
+  if (ok && mma_ok && !*abort_flag) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    float* crow = C + (long)q * sC + (long)row * ldc;
+    const float* srow = sB + (long)q * Nr;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r0[16], r1[16], r2[16], r3[16];
+      tmem_ld16(tl + c0, r0);
+      tmem_ld16(tl + 128 + c0, r1);
+      tmem_ld16(tl + 256 + c0, r2);
+      tmem_ld16(tl + 384 + c0, r3);
+      tmem_ld_wait();
+      if (row < M) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int col = n0 + c0 + i;
+          if (col < Nr) {
+            const float v =
+                fmaf(fmaf(fmaf(__uint_as_float(r3[i]), 0x1p-8f, __uint_as_float(r2[i])), 0x1p-8f,
+                          __uint_as_float(r1[i])),
+                     0x1p-8f, __uint_as_float(r0[i]));
+            crow[col] = v * (sA * srow[col] * 0x1p-16f);
+          }
+        }
+      }
+    }
+  }
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
+      const int s = kb % STAGES;
+      mbar_wait(&full[s], (kb / STAGES) & 1);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcf::TMEM_COLS) : "memory");
+  }
+}
+
+// ----------------------------------------------------------------------------- host side
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool encode_fn() {
+  if (g_encode) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+      qr != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return true;
+}
+}  // namespace
+
+// 2-D FP32 tensor map over a row-major [rows][kp] array, box 32 x box_rows, 128-byte swizzle.
+cudaError_t make_tc_map(void* map_out, const float* base, long rows, int kp, int box_rows) {
+  if (!encode_fn()) return cudaErrorNotSupported;
+  if (kp % tc::BK != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || rows < 1) return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kp * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        const_cast<float*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// 2-D BF16 tensor map over a row-major [rows][kp] array, box 64 x box_rows, 128-byte swizzle.
+cudaError_t make_tc_map_bf16(void* map_out, const void* base, long rows, int kp, int box_rows) {
+  if (!encode_fn()) return cudaErrorNotSupported;
+  if (kp % tcf::BK != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || rows < 1) return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)tcf::BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
+                                 float sA, const float* sB, float* C, long ldc, long sC, int* err, cudaStream_t st) {
+  if (M <= 0 || Nr <= 0 || nq <= 0) return cudaSuccess;
+  if (Kp % tcf::BK != 0 || Kp <= 0 || Kp > 1024) return cudaErrorInvalidValue;  // exact level-0 sums need K <= 1024
+  cudaError_t e = cudaFuncSetAttribute(k_tc_fixed_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tcf::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  TcMaps7 maps;
+  for (int d = 0; d < 3; ++d) maps.a[d] = static_cast<const CUtensorMap*>(maps_a3)[d];
+  for (int d = 0; d < 4; ++d) maps.b[d] = static_cast<const CUtensorMap*>(maps_b4)[d];
+  dim3 grid((Nr + tcf::BN - 1) / tcf::BN, (M + tcf::BM - 1) / tcf::BM, nq);
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+  k_tc_fixed_gemm<<<grid, 128, tcf::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, sA, sB, C, ldc, sC, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_split_gemm(const void* mAhi, const void* mAlo, const void* mBhi, const void* mBlo, int M,
+                                 int a_row0, int Nr, int Kp, int nq, float* C, long ldc, long sC, int* err,
+                                 cudaStream_t st) {
+  if (M <= 0 || Nr <= 0 || nq <= 0) return cudaSuccess;
+  if (Kp % tc::BK != 0 || Kp <= 0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_split_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  dim3 grid((Nr + tc::BN - 1) / tc::BN, (M + tc::BM - 1) / tc::BM, nq);
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+  k_tc_split_gemm<<<grid, 128, tc::SMEM_BYTES, st>>>(*static_cast<const CUtensorMap*>(mAhi),
+                                                     *static_cast<const CUtensorMap*>(mAlo),
+                                                     *static_cast<const CUtensorMap*>(mBhi),
+                                                     *static_cast<const CUtensorMap*>(mBlo), M, a_row0, Nr, Kp, C,
+                                                     ldc, sC, err);
+  return cudaGetLastError();
+}
+
+}  // namespace eph

@@ -1,0 +1,108 @@
+"""Mixed form (split-TF32 tensor-core Re->k contraction, FP32 accumulation) against
+the FP64 CPU oracle.  Eigenvalues and frequencies stay FP64 (bar 1e-12); the
+degenerate-subspace sums of |g|^2 must agree to 1e-6 (max relative error)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_10295_gb300 import binding, build_lib, synth
+from tests import gauge
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-6          # default scheme: fixed-point BF16 digits, exact FP32 accumulation
+TOL_TF32 = 1e-5           # two-term split TF32: FP32 accumulation error grows like sqrt(K)
+TOL_FP64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not os.path.exists(binding.LIB_PATH):
+        build_lib.build()
+    return binding.load_library()
+
+
+def check_mixed(gpu, ref, what, tol=TOL_MIXED):
+    e_k, e_kq, om, g = gpu
+    r_k, r_kq, r_om, r_g = ref
+    assert g.dtype == np.complex64
+    errs = dict(eps_k=gauge.max_rel_eps(e_k, r_k), eps_kq=gauge.max_rel_eps(e_kq, r_kq),
+                omega=gauge.max_rel_omega(om, r_om), S=gauge.max_rel_S(g, r_g, r_k, r_kq, r_om))
+    print(what, errs)
+    assert errs["eps_k"] <= TOL_FP64 and errs["eps_kq"] <= TOL_FP64 and errs["omega"] <= TOL_FP64, errs
+    assert errs["S"] <= tol, errs
+    return errs
+
+
+@pytest.mark.parametrize("q_batch,k_tile", [(0, 0), (3, 130), (16, 0)])
+@pytest.mark.parametrize("scheme", ["digits", "tf32"])
+def test_si_tiny_mixed(q_batch, k_tile, scheme):
+    wl = synth.make_workload("si_tiny", nk=300, nq=7)
+    ctx = binding.Context.from_workload(wl, form="mixed", q_batch=q_batch, k_tile=k_tile, mixed_scheme=scheme)
+    check_mixed(ctx.interp(wl.kpts, wl.qpts), oracle.interpolate(wl), f"si_tiny {scheme} qb={q_batch} kt={k_tile}",
+                TOL_MIXED if scheme == "digits" else TOL_TF32)
+
+
+def test_mos2_shaped_small_mixed():
+    box = (synth.centred_range(6), synth.centred_range(6), range(0, 1))
+    wl = synth.make_workload("mos2", nk=333, nq=5, box=box)
+    ctx = binding.Context.from_workload(wl, form="mixed", q_batch=2, k_tile=200)
+    check_mixed(ctx.interp(wl.kpts, wl.qpts), oracle.interpolate(wl), "mos2 small")
+
+
+def test_mixed_device_mode_matches_host_mode():
+    torch = pytest.importorskip("torch")
+    wl = synth.make_workload("si_tiny", nk=200, nq=5)
+    host = binding.Context.from_workload(wl, form="mixed").interp(wl.kpts, wl.qpts)
+    dev = torch.device("cuda:0")
+    ctx = binding.Context.from_workload(wl, form="mixed", device_ptrs=True, stream=torch.cuda.current_stream())
+    nk, nq, nb, nm = len(wl.kpts), len(wl.qpts), wl.nb, wl.nm
+    eps_k = torch.empty(nk, nb, dtype=torch.float64, device=dev)
+    eps_kq = torch.empty(nq, nk, nb, dtype=torch.float64, device=dev)
+    om = torch.empty(nq, nm, dtype=torch.float64, device=dev)
+    g = torch.empty(nq, nk, nm, nb, nb, dtype=torch.complex64, device=dev)
+    ctx.eph_set_k(nk, torch.from_numpy(wl.kpts).to(dev), eps_k)
+    ctx.eph_interp_q(nq, torch.from_numpy(wl.qpts).to(dev), eps_kq, om, g)
+    torch.cuda.synchronize()
+    out = (eps_k.cpu().numpy(), eps_kq.cpu().numpy(), om.cpu().numpy(), g.cpu().numpy())
+    for a, b in zip(out, host):
+        assert np.array_equal(a, b)
+
+
+def _full(name, nq_check, nk_sample, seed, scheme="digits"):
+    torch = pytest.importorskip("torch")
+    wl = synth.make_workload(name)
+    dev = torch.device("cuda:0")
+    ctx = binding.Context.from_workload(wl, form="mixed", device_ptrs=True, q_batch=4,
+                                        stream=torch.cuda.current_stream(), mixed_scheme=scheme)
+    nk, nb, nm = len(wl.kpts), wl.nb, wl.nm
+    qsel = wl.qpts[:nq_check].copy()
+    eps_k = torch.empty(nk, nb, dtype=torch.float64, device=dev)
+    eps_kq = torch.empty(nq_check, nk, nb, dtype=torch.float64, device=dev)
+    om = torch.empty(nq_check, nm, dtype=torch.float64, device=dev)
+    g = torch.empty(nq_check, nk, nm, nb, nb, dtype=torch.complex64, device=dev)
+    ctx.eph_set_k(nk, torch.from_numpy(wl.kpts).to(dev), eps_k)
+    ctx.eph_interp_q(nq_check, torch.from_numpy(qsel).to(dev), eps_kq, om, g)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    ks = np.sort(rng.choice(nk, size=nk_sample, replace=False))
+    ksel = torch.from_numpy(ks).to(dev)
+    gpu = (eps_k[ksel].cpu().numpy(), eps_kq[:, ksel].cpu().numpy(), om.cpu().numpy(), g[:, ksel].cpu().numpy())
+    return gpu, oracle.interpolate(wl, wl.kpts[ks], qsel)
+
+
+def test_si_full_sampled_mixed():
+    gpu, ref = _full("si_full", 4, 1500, 31)
+    check_mixed(gpu, ref, "si_full mixed")
+
+
+def test_si_full_sampled_tf32_scheme():
+    gpu, ref = _full("si_full", 2, 1000, 33, scheme="tf32")
+    check_mixed(gpu, ref, "si_full tf32", TOL_TF32)
+
+
+def test_mos2_full_sampled_mixed():
+    gpu, ref = _full("mos2", 4, 1200, 32)
+    check_mixed(gpu, ref, "mos2 mixed")
