@@ -39,8 +39,7 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
 # kernel from one ncu capture of a one-q launch, scaled to the bench launch by the units
 # processed (profiles/k_zgemm_si_full_fp64.md).  Keyed by (kernel, workload, q batch).
-TRAFFIC = {("k_zgemm", "si_full", 4): 4 * (225.011712e6 + 404.513024e6),
-           ("k_zgemm", "si_full", 1): 225.011712e6 + 404.513024e6}
+TRAFFIC = {}
 
 
 def parse():
@@ -290,11 +289,14 @@ def run_libeph(args):
     def roof_fp64(r):
         ft_ms, ft_n = r["prof"]["ft_k"]
         NW = nb * nb * (1 + nm)
-        flop_launch = 8.0 * QB * nk * NW * ne          # one launch covers the q batch x all k
-        ach = flop_launch / (ft_ms / max(ft_n, 1) * 1e-3) if ft_n else None
-        return {"bound": "alu", "kernel": "k_zgemm (Re->k contraction fused with H(k+q), FP64 DFMA)",
+        cmac_launch = float(QB) * nk * NW * ne         # one launch covers the q batch x all k
+        t = ft_ms / max(ft_n, 1) * 1e-3 if ft_n else None
+        # the kernel's algorithm (3M complex product) spends 3 DFMA = 6 flop per complex multiply-add
+        ach = 6.0 * cmac_launch / t if t else None
+        return {"bound": "alu", "kernel": "k_zgemm (Re->k contraction fused with H(k+q), FP64 DFMA, 3M)",
                 "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": (ach / FP64_PEAK_FLOPS) if ach else None,
+                "flop_per_cmac": 6, "complex_equiv_tflops": 8.0 * cmac_launch / t / 1e12 if t else None,
                 "traffic": TRAFFIC.get(("k_zgemm", args.workload, QB)),
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
 

@@ -33,6 +33,7 @@ using eph::launch_skinny_real;
 using eph::launch_sum_into;
 using eph::launch_zgemm;
 using eph::launch_zgemm_ah;
+using eph::launch_zgemm_df;
 using eph::launch_band_rotate_f32;
 using eph::launch_band_rotate_ff;
 using eph::launch_digits_a;
@@ -601,8 +602,9 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
                                                   as<float>(ctx->Bhi), as<float>(ctx->Blo), ctx->stream));
     for (long k0 = 0; k0 < nk; k0 += p.KT) {
       const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
-      // H(k+q) in FP64 (the eigensolve needs it), then its Jacobi
-      EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nkt, nb2, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0, W, p.NW,
+      // H(k+q) to ~1e-13 (double-float on the FP32 pipe; the eigensolve needs FP64-class input),
+      // then its FP64 Jacobi
+      EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm_df(nkt, nb2, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0, W, p.NW,
                                                 (long)ne * p.NW, as<double2>(ctx->Hkq), nb2, (long)nkt * nb2, nqb,
                                                 ctx->stream));
       EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(as<double2>(ctx->Hkq), nb2, nb, nb, (long)nqb * nkt,

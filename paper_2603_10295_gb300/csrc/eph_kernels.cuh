@@ -25,6 +25,9 @@ cudaError_t launch_scale_rows(const double2* Q, int nq, const double2* H, int ne
 cudaError_t launch_zgemm(int M, int N, int K, const double2* A, long lda, long sA,
                          const double2* B, long ldb, long sB, double2* C, long ldc, long sC,
                          int batch, cudaStream_t st);
+// Same product on the FP32 pipe in double-float arithmetic (~1e-13 relative), FP64 in/out.
+cudaError_t launch_zgemm_df(int M, int N, int K, const double2* A, long lda, long sA, const double2* B, long ldb,
+                            long sB, double2* C, long ldc, long sC, int batch, cudaStream_t st);
 // Adjoint form C[b] = A[b]^H * B[b] (A stored M_A x K_A = K x M), accumulate if acc.
 cudaError_t launch_zgemm_ah(int M, int N, int K, const double2* A, long lda, long sA,
                             const double2* B, long ldb, long sB, double2* C, long ldc, long sC,

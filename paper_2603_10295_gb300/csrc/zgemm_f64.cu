@@ -2,7 +2,8 @@
 //
 // On GB300 the FP64 pipe issues about two DFMA per clock per SM, so these
 // kernels are bound by FP64 arithmetic, not by memory: a 64x64 register tile
-// per 256-thread CTA with 8-deep shared-memory staging keeps the pipe fed.
+// per 256-thread CTA with 8-deep shared-memory staging keeps the pipe fed, and
+// the tiled GEMM spends three DFMA per complex multiply-add (3M form).
 //   - k_zgemm:   C = A B or C (+)= A^H B   (Fourier sums over Re: H(k), H(k+q),
 //                Re->k of g (Eq. 10); adjoint sums over k and q)
 //   - k_skinny:  few rows times a wide operand (Rp->q of g, Eq. 9; D(q))
@@ -22,12 +23,16 @@ __device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
 }  // namespace
 
 // ADJ: op(A) = A^H with A stored K x M (row stride lda).  ACC: C += result.
+// Complex products use the 3-multiplication form (Gauss / "3M"): with the pre-added
+// sums s_a = a_r + a_i and s_b = b_r + b_i staged once per shared-memory tile,
+//   t1 += a_r b_r,  t2 += a_i b_i,  t3 += s_a s_b,   C = (t1 - t2) + i (t3 - t1 - t2),
+// i.e. three DFMA per complex multiply-add instead of four.
 template <bool ADJ, bool ACC>
 __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, const double2* __restrict__ A, long lda,
                                                long sA, const double2* __restrict__ B, long ldb, long sB,
                                                double2* __restrict__ C, long ldc, long sC) {
-  __shared__ double2 As[BK][BM];
-  __shared__ double2 Bs[BK][BN];
+  __shared__ double3 As[BK][BM];  // (re, im, re + im)
+  __shared__ double3 Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -35,36 +40,42 @@ __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, const double
   A += b * sA;
   B += b * sB;
   C += b * sC;
-  double2 acc[4][4];
+  double t1[4][4], t2[4][4], t3[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < 4; ++j) t1[i][j] = t2[i][j] = t3[i][j] = 0.0;
 
   for (int k0 = 0; k0 < K; k0 += BK) {
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
       int idx = tid + 256 * l;
+      double2 v;
+      int am, ak;
       if (!ADJ) {
-        int m = idx >> 3, kk = idx & 7;
-        int gm = m0 + m, gk = k0 + kk;
-        As[kk][m] = (gm < M && gk < K) ? A[(long)gm * lda + gk] : make_double2(0.0, 0.0);
+        am = idx >> 3;
+        ak = idx & 7;
+        const int gm = m0 + am, gk = k0 + ak;
+        v = (gm < M && gk < K) ? A[(long)gm * lda + gk] : make_double2(0.0, 0.0);
       } else {
-        int kk = idx >> 6, m = idx & 63;
-        int gm = m0 + m, gk = k0 + kk;
-        double2 v = (gm < M && gk < K) ? A[(long)gk * lda + gm] : make_double2(0.0, 0.0);
-        As[kk][m] = make_double2(v.x, -v.y);
+        ak = idx >> 6;
+        am = idx & 63;
+        const int gm = m0 + am, gk = k0 + ak;
+        v = (gm < M && gk < K) ? A[(long)gk * lda + gm] : make_double2(0.0, 0.0);
+        v.y = -v.y;
       }
+      As[ak][am] = make_double3(v.x, v.y, v.x + v.y);
       {
         int kk = idx >> 6, n = idx & 63;
         int gn = n0 + n, gk = k0 + kk;
-        Bs[kk][n] = (gn < N && gk < K) ? B[(long)gk * ldb + gn] : make_double2(0.0, 0.0);
+        const double2 w = (gn < N && gk < K) ? B[(long)gk * ldb + gn] : make_double2(0.0, 0.0);
+        Bs[kk][n] = make_double3(w.x, w.y, w.x + w.y);
       }
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double2 a[4], bb[4];
+      double3 a[4], bb[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -72,7 +83,11 @@ __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, const double
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cmac(acc[i][j], a[i], bb[j]);
+        for (int j = 0; j < 4; ++j) {
+          t1[i][j] = fma(a[i].x, bb[j].x, t1[i][j]);
+          t2[i][j] = fma(a[i].y, bb[j].y, t2[i][j]);
+          t3[i][j] = fma(a[i].z, bb[j].z, t3[i][j]);
+        }
     }
     __syncthreads();
   }
@@ -84,12 +99,13 @@ __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, const double
     for (int j = 0; j < 4; ++j) {
       int gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
+      const double2 r = make_double2(t1[i][j] - t2[i][j], t3[i][j] - t1[i][j] - t2[i][j]);
       double2* p = C + (long)gm * ldc + gn;
       if (ACC) {
         double2 o = *p;
-        *p = make_double2(o.x + acc[i][j].x, o.y + acc[i][j].y);
+        *p = make_double2(o.x + r.x, o.y + r.y);
       } else {
-        *p = acc[i][j];
+        *p = r;
       }
     }
   }
@@ -197,6 +213,111 @@ cudaError_t launch_skinny(int M, long N, int K, const double2* P, long ldp, cons
 cudaError_t launch_skinny_real(int M, long N, int K, const double2* P, long ldp, const double* B, long ldb,
                                const double* colscale, double2* C, long ldc, cudaStream_t st) {
   return skinny_dispatch<true>(M, N, K, P, ldp, B, ldb, colscale, C, ldc, st);
+}
+
+// ----------------------------------------------------------------------------
+// Double-float complex GEMM on the FP32 pipe: C = A B with FP64 inputs and output,
+// every operand carried as a pair of floats (hi + lo, ~48 bits) and every product
+// formed exactly with an FMA and accumulated with a two-sum.  Relative error
+// ~1e-13 of the sum of |terms|, at about one fifth of the DFMA time on GB300
+// (12 FP32 operations per real multiply-add at 64x the FP64 rate).  Used where
+// FP64-class accuracy is needed but not FP64 itself (H(k+q) for the mixed form).
+// ----------------------------------------------------------------------------
+namespace {
+struct ff2 {  // complex double-float: (re_hi, re_lo, im_hi, im_lo)
+  float rh, rl, ih, il;
+};
+__device__ __forceinline__ float4 to_ff(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+// (sh, sl) += (ah + al)(bh + bl); products error-free via FMA, sum via two-sum.
+// __fmul_rn/__fadd_rn are never contracted into FMAs, which the transforms rely on.
+__device__ __forceinline__ void dfmac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb)), e));
+  sh = s;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_zgemm_df(int M, int N, int K, const double2* __restrict__ A, long lda,
+                                                  long sA, const double2* __restrict__ B, long ldb, long sB,
+                                                  double2* __restrict__ C, long ldc, long sC) {
+  __shared__ float4 As[BK][BM];
+  __shared__ float4 Bs[BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const long b = blockIdx.z;
+  A += b * sA;
+  B += b * sB;
+  C += b * sC;
+  ff2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = ff2{0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const int idx = tid + 256 * l;
+      {
+        const int m = idx >> 3, kk = idx & 7, gm = m0 + m, gk = k0 + kk;
+        As[kk][m] = to_ff((gm < M && gk < K) ? A[(long)gm * lda + gk] : make_double2(0.0, 0.0));
+      }
+      {
+        const int kk = idx >> 6, n = idx & 63, gn = n0 + n, gk = k0 + kk;
+        Bs[kk][n] = to_ff((gn < N && gk < K) ? B[(long)gk * ldb + gn] : make_double2(0.0, 0.0));
+      }
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < BK; ++kk) {
+      float4 a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          ff2& c = acc[i][j];
+          // (ar + i ai)(br + i bi): re += ar br - ai bi, im += ar bi + ai br
+          dfmac(c.rh, c.rl, a[i].x, a[i].y, bb[j].x, bb[j].y);
+          dfmac(c.rh, c.rl, -a[i].z, -a[i].w, bb[j].z, bb[j].w);
+          dfmac(c.ih, c.il, a[i].x, a[i].y, bb[j].z, bb[j].w);
+          dfmac(c.ih, c.il, a[i].z, a[i].w, bb[j].x, bb[j].y);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      const ff2& c = acc[i][j];
+      C[(long)gm * ldc + gn] = make_double2((double)c.rh + (double)c.rl, (double)c.ih + (double)c.il);
+    }
+  }
+}
+
+cudaError_t launch_zgemm_df(int M, int N, int K, const double2* A, long lda, long sA, const double2* B, long ldb,
+                            long sB, double2* C, long ldc, long sC, int batch, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  if (!grid_ok(M, N, batch)) return cudaErrorInvalidConfiguration;
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+  k_zgemm_df<<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+  return cudaGetLastError();
 }
 
 }  // namespace eph
