@@ -64,6 +64,8 @@ typedef struct eph_options {
   int mixed_scheme;  /* mixed form only: 0 = fixed-point BF16 digits (3 for the phases, 4 for g)
                         with exact FP32 tensor-core accumulation (default; needs 2*ne <= 1024),
                         1 = two-term split TF32 (3 products) */
+  int eig_plain_fp64; /* 0 (default): Jacobi sweeps preconditioned in FP32, then FP64 sweeps to
+                         full FP64 accuracy; 1: FP64 sweeps only */
 } eph_options;
 
 /* Fills *opt with the defaults (FP64 form, host pointers, automatic batching). */

@@ -30,7 +30,7 @@ STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 class EphOptions(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("device_ptrs", ctypes.c_int), ("q_batch", ctypes.c_int),
                 ("k_tile", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("workspace_mb", ctypes.c_int),
-                ("mixed_scheme", ctypes.c_int)]
+                ("mixed_scheme", ctypes.c_int), ("eig_plain_fp64", ctypes.c_int)]
 
 
 class EphError(RuntimeError):
@@ -112,7 +112,7 @@ class Context:
 
     def __init__(self, nb, na, H_Re, Phi_Rp, g_ReRp, Re, Rp, masses, we=None, wp=None, form="fp64",
                  device_ptrs=False, q_batch=0, k_tile=0, max_sweeps=0, workspace_mb=0, stream=None,
-                 mixed_scheme="digits"):
+                 mixed_scheme="digits", eig_plain_fp64=False):
         self.lib = load_library()
         self.nb, self.na, self.nm = int(nb), int(na), 3 * int(na)
         H_Re = np.ascontiguousarray(H_Re, dtype=np.complex128)
@@ -132,6 +132,7 @@ class Context:
         opt.device_ptrs = int(device_ptrs)
         opt.q_batch, opt.k_tile, opt.max_sweeps, opt.workspace_mb = q_batch, k_tile, max_sweeps, workspace_mb
         opt.mixed_scheme = {"digits": 0, "tf32": 1}[mixed_scheme]
+        opt.eig_plain_fp64 = int(bool(eig_plain_fp64))
         handle = ctypes.c_void_p()
         st = None
         if stream is not None:

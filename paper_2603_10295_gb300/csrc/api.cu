@@ -22,7 +22,6 @@
 
 using eph::launch_band_adjoint;
 using eph::launch_band_rotate;
-using eph::launch_jacobi;
 using eph::launch_mode_rotate;
 using eph::launch_mode_rotate_adj;
 using eph::launch_phase;
@@ -141,6 +140,14 @@ void release(DBuf& b) {
 template <class T>
 T* as(DBuf& b) {
   return static_cast<T*>(b.p);
+}
+
+// Batched eigensolve: FP32-preconditioned FP64 Jacobi unless the plain FP64 sweeps are requested.
+cudaError_t eig(const eph_ctx* c, const double2* A, long sA, long lda, int n, long batch, double* w, long sw,
+                double2* V, long sV) {
+  if (c->opt.eig_plain_fp64)
+    return eph::launch_jacobi(A, sA, lda, n, batch, w, sw, V, sV, c->opt.max_sweeps, c->status, c->stream);
+  return eph::launch_jacobi_mixed(A, sA, lda, n, batch, w, sw, V, sV, c->opt.max_sweeps, c->status, c->stream);
 }
 
 cudaEvent_t take_event(eph_ctx* c) {
@@ -431,8 +438,8 @@ extern "C" int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k
   EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(as<double>(ctx->kpts), nk, ctx->Re, ctx->we, ne, as<double2>(ctx->Pk), ne, ctx->stream));
   EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nk, nb2, ne, as<double2>(ctx->Pk), ne, 0, ctx->H, nb2, 0, as<double2>(ctx->Hk_tmp), nb2, 0,
                           1, ctx->stream));
-  EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(as<double2>(ctx->Hk_tmp), nb2, nb, nb, nk, as<double>(ctx->eps_k), nb,
-                           as<double2>(ctx->Uk), nb2, ctx->opt.max_sweeps, ctx->status, ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, as<double2>(ctx->Hk_tmp), nb2, nb, nb, nk, as<double>(ctx->eps_k), nb,
+                           as<double2>(ctx->Uk), nb2));
   if (ctx->opt.form == EPH_FORM_MIXED && ctx->opt.mixed_scheme == 0) {
     // A operand of the tensor-core Re->k contraction: 3 fixed-point BF16 digits of the phases
     const size_t slice = (size_t)nk * ctx->kpd;
@@ -515,9 +522,8 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb) {
   // D(q), eigenpairs, omega and u = e / sqrt(M)
   EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny_real(nqb, (long)nm * nm, np, Pp, np, ctx->Phi, (long)nm * nm,
                                                   ctx->dscale, as<double2>(ctx->D), (long)nm * nm, ctx->stream));
-  EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(as<double2>(ctx->D), (long)nm * nm, nm, nm, nqb, as<double>(ctx->lamq), nm,
-                                            as<double2>(ctx->evq), (long)nm * nm, ctx->opt.max_sweeps, ctx->status,
-                                            ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, as<double2>(ctx->D), (long)nm * nm, nm, nm, nqb, as<double>(ctx->lamq), nm,
+                                  as<double2>(ctx->evq), (long)nm * nm));
   EPH_LAUNCH_S(EPH_STAGE_MODE, launch_phonon_post(as<double>(ctx->lamq), as<double2>(ctx->evq), nqb, nm,
                                                   ctx->invsqrtm, ctx->omega_unit, as<double>(ctx->omq),
                                                   as<double2>(ctx->uq), ctx->stream));
@@ -538,8 +544,8 @@ int k_tile_forward(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
   EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nkt, (int)p.NW, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0,
                                             as<double2>(ctx->W), p.NW, (long)ne * p.NW, Y, p.NW, (long)nkt * p.NW, nqb,
                                             ctx->stream));
-  EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(Y, p.NW, nb, nb, (long)nqb * nkt, as<double>(ctx->eps_tile), nb,
-                                            as<double2>(ctx->Ukq), nb2, ctx->opt.max_sweeps, ctx->status, ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, Y, p.NW, nb, nb, (long)nqb * nkt, as<double>(ctx->eps_tile), nb,
+                                            as<double2>(ctx->Ukq), nb2));
   return EPH_OK;
 }
 
@@ -607,9 +613,8 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
       EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm_df(nkt, nb2, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0, W, p.NW,
                                                 (long)ne * p.NW, as<double2>(ctx->Hkq), nb2, (long)nkt * nb2, nqb,
                                                 ctx->stream));
-      EPH_LAUNCH_S(EPH_STAGE_EIG, launch_jacobi(as<double2>(ctx->Hkq), nb2, nb, nb, (long)nqb * nkt,
-                                                as<double>(ctx->eps_tile), nb, as<double2>(ctx->Ukq), nb2,
-                                                ctx->opt.max_sweeps, ctx->status, ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, as<double2>(ctx->Hkq), nb2, nb, nb, (long)nqb * nkt,
+                                      as<double>(ctx->eps_tile), nb, as<double2>(ctx->Ukq), nb2));
       if (eps_kq)
         for (int iq = 0; iq < nqb; ++iq)
           EPH_CK(cudaMemcpyAsync(eps_kq + ((long)(q0 + iq) * nk + k0) * nb,

@@ -33,49 +33,72 @@ __device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync
 __device__ __forceinline__ double2 shfl_d2(double2 v, int src) {
   return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
+__device__ __forceinline__ float shfl_d(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float2 shfl_d2(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
 
-template <int NP, int R>
-__device__ __forceinline__ void jacobi_round(double2 (&a)[NP], double2 (&v)[NP], int j, int base, double thresh2) {
+template <typename T>
+struct Cx;
+template <>
+struct Cx<double> {
+  using T2 = double2;
+  __device__ static T2 make(double x, double y) { return make_double2(x, y); }
+  __device__ static double rsq(double x) { return rsqrt(x); }
+};
+template <>
+struct Cx<float> {
+  using T2 = float2;
+  __device__ static T2 make(float x, float y) { return make_float2(x, y); }
+  __device__ static float rsq(float x) { return rsqrtf(x); }
+};
+
+// One round of the circle schedule in precision T (double for the eigensolve proper,
+// float for the preconditioning sweeps of k_jacobi_mixed).
+template <int NP, int R, typename T>
+__device__ __forceinline__ void jacobi_round(typename Cx<T>::T2 (&a)[NP], typename Cx<T>::T2 (&v)[NP], int j, int base,
+                                             T thresh2) {
+  using T2 = typename Cx<T>::T2;
   const int p = rr_partner(j, R, NP);
   const bool lower = j < p;
-  double d = 0.0;
-  double2 x = make_double2(0.0, 0.0);
+  T d = 0;
+  T2 x = Cx<T>::make(0, 0);
 #pragma unroll
   for (int rho = 0; rho < NP; ++rho) {
     if (rho == j) d = a[rho].x;
     if (rho == p) x = a[rho];
   }
-  const double dp = shfl_d(d, base + p);
-  const double2 y = shfl_d2(x, base + p);
-  const double app = lower ? d : dp;
-  const double aqq = lower ? dp : d;
-  const double2 bq = lower ? y : x;  // A[lo][hi]
+  const T dp = shfl_d(d, base + p);
+  const T2 y = shfl_d2(x, base + p);
+  const T app = lower ? d : dp;
+  const T aqq = lower ? dp : d;
+  const T2 bq = lower ? y : x;  // A[lo][hi]
   // r = t/|b| = 2 sign(dd) / (|dd| + sqrt(dd^2 + 4|b|^2)), dd = aqq - app: the same t as
   // sign(tau)/(|tau| + sqrt(1 + tau^2)) with tau = dd/(2|b|), without forming |b|.
-  const double b2 = fma(bq.x, bq.x, bq.y * bq.y);
-  double c = 1.0, tb = 0.0;  // tb = t |b| = r |b|^2
-  double2 sig = make_double2(0.0, 0.0);
+  const T b2 = fma(bq.x, bq.x, bq.y * bq.y);
+  T c = 1, tb = 0;  // tb = t |b| = r |b|^2
+  T2 sig = Cx<T>::make(0, 0);
   if (b2 > thresh2) {
-    const double dd = aqq - app;
-    const double r = copysign(2.0, dd) / (fabs(dd) + sqrt(fma(dd, dd, 4.0 * b2)));
+    const T dd = aqq - app;
+    const T r = copysign(T(2), dd) / (fabs(dd) + sqrt(fma(dd, dd, T(4) * b2)));
     tb = r * b2;
-    c = rsqrt(fma(r * r, b2, 1.0));
-    const double cr = c * r;
-    sig = make_double2(cr * bq.x, cr * bq.y);
+    c = Cx<T>::rsq(fma(r * r, b2, T(1)));
+    const T cr = c * r;
+    sig = Cx<T>::make(cr * bq.x, cr * bq.y);
   }
   // column mix (A J, V J): lower lane: c a_p - conj(sig) a_q; upper lane: sig a_p + c a_q
-  const double2 coef = lower ? make_double2(-sig.x, sig.y) : sig;
+  const T2 coef = lower ? Cx<T>::make(-sig.x, sig.y) : sig;
 #pragma unroll
   for (int rho = 0; rho < NP; ++rho) {
-    const double2 o = shfl_d2(a[rho], base + p);
-    const double2 m = a[rho];
-    a[rho] = make_double2(fma(c, m.x, fma(coef.x, o.x, -coef.y * o.y)), fma(c, m.y, fma(coef.x, o.y, coef.y * o.x)));
+    const T2 o = shfl_d2(a[rho], base + p);
+    const T2 m = a[rho];
+    a[rho] = Cx<T>::make(fma(c, m.x, fma(coef.x, o.x, -coef.y * o.y)), fma(c, m.y, fma(coef.x, o.y, coef.y * o.x)));
   }
 #pragma unroll
   for (int rho = 0; rho < NP; ++rho) {
-    const double2 o = shfl_d2(v[rho], base + p);
-    const double2 m = v[rho];
-    v[rho] = make_double2(fma(c, m.x, fma(coef.x, o.x, -coef.y * o.y)), fma(c, m.y, fma(coef.x, o.y, coef.y * o.x)));
+    const T2 o = shfl_d2(v[rho], base + p);
+    const T2 m = v[rho];
+    v[rho] = Cx<T>::make(fma(c, m.x, fma(coef.x, o.x, -coef.y * o.y)), fma(c, m.y, fma(coef.x, o.y, coef.y * o.x)));
   }
   // row mix (J^H A) for every pair of this round: row_lo' = c row_lo - sig row_hi,
   // row_hi' = conj(sig) row_lo + c row_hi
@@ -83,33 +106,48 @@ __device__ __forceinline__ void jacobi_round(double2 (&a)[NP], double2 (&v)[NP],
   for (int lo = 0; lo < NP; ++lo) {
     const int hi = rr_partner(lo, R, NP);
     if (hi > lo) {
-      const double cc = shfl_d(c, base + lo);
-      const double2 ss = shfl_d2(sig, base + lo);
-      const double2 xl = a[lo], xh = a[hi];
-      a[lo] = make_double2(fma(cc, xl.x, -fma(ss.x, xh.x, -ss.y * xh.y)), fma(cc, xl.y, -fma(ss.x, xh.y, ss.y * xh.x)));
-      a[hi] = make_double2(fma(cc, xh.x, fma(ss.x, xl.x, ss.y * xl.y)), fma(cc, xh.y, fma(ss.x, xl.y, -ss.y * xl.x)));
+      const T cc = shfl_d(c, base + lo);
+      const T2 ss = shfl_d2(sig, base + lo);
+      const T2 xl = a[lo], xh = a[hi];
+      a[lo] = Cx<T>::make(fma(cc, xl.x, -fma(ss.x, xh.x, -ss.y * xh.y)), fma(cc, xl.y, -fma(ss.x, xh.y, ss.y * xh.x)));
+      a[hi] = Cx<T>::make(fma(cc, xh.x, fma(ss.x, xl.x, ss.y * xl.y)), fma(cc, xh.y, fma(ss.x, xl.y, -ss.y * xl.x)));
     }
   }
   // exact values of the rotated 2x2 block
-  const double nd = lower ? app - tb : aqq + tb;
+  const T nd = lower ? app - tb : aqq + tb;
 #pragma unroll
   for (int rho = 0; rho < NP; ++rho) {
-    if (rho == p) a[rho] = make_double2(0.0, 0.0);
-    if (rho == j) a[rho] = make_double2(nd, 0.0);
+    if (rho == p) a[rho] = Cx<T>::make(0, 0);
+    if (rho == j) a[rho] = Cx<T>::make(nd, 0);
   }
 }
 
-template <int NP, int R>
+template <int NP, int R, typename T>
 struct Sweep {
-  __device__ __forceinline__ static void run(double2 (&a)[NP], double2 (&v)[NP], int j, int base, double thr) {
-    jacobi_round<NP, R>(a, v, j, base, thr);
-    Sweep<NP, R + 1>::run(a, v, j, base, thr);
+  using T2 = typename Cx<T>::T2;
+  __device__ __forceinline__ static void run(T2 (&a)[NP], T2 (&v)[NP], int j, int base, T thr) {
+    jacobi_round<NP, R, T>(a, v, j, base, thr);
+    Sweep<NP, R + 1, T>::run(a, v, j, base, thr);
   }
 };
-template <int NP>
-struct Sweep<NP, NP - 1> {
-  __device__ __forceinline__ static void run(double2 (&)[NP], double2 (&)[NP], int, int, double) {}
+template <int NP, typename T>
+struct Sweep<NP, NP - 1, T> {
+  using T2 = typename Cx<T>::T2;
+  __device__ __forceinline__ static void run(T2 (&)[NP], T2 (&)[NP], int, int, T) {}
 };
+
+// Off-diagonal squared Frobenius norm of the group's matrix (all lanes get it).
+template <int NP, typename T2>
+__device__ __forceinline__ auto group_off2(const T2 (&a)[NP], int j, int base) {
+  decltype(a[0].x) off = 0;
+#pragma unroll
+  for (int r = 0; r < NP; ++r)
+    if (r != j) off = fma(a[r].x, a[r].x, fma(a[r].y, a[r].y, off));
+  decltype(a[0].x) tot = 0;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) tot += shfl_d(off, base + i);
+  return tot;
+}
 
 }  // namespace
 
@@ -152,7 +190,7 @@ __global__ void __launch_bounds__(128) k_jacobi(const double2* __restrict__ A, l
   int post = valid ? 0 : 1;
   int sweep = 0;
   while (__any_sync(0xffffffffu, !(conv && post >= 1)) && sweep < max_sweeps) {
-    Sweep<NP, 0>::run(a, v, j, base, thresh2);
+    Sweep<NP, 0, double>::run(a, v, j, base, thresh2);
     ++sweep;
     if (conv) ++post;
     double off = 0.0;
@@ -184,6 +222,189 @@ __global__ void __launch_bounds__(128) k_jacobi(const double2* __restrict__ A, l
     for (int r = 0; r < NP; ++r)
       if (r < n) out[(long)r * n + rank] = v[r];
   }
+}
+
+// FP32-preconditioned variant: the same sweeps first run in FP32 (64x the FP64
+// rate on GB300) to an off-diagonal norm of ~1e-6 ||A||; V is then made unitary
+// to rounding level with two FP64 Newton-Schulz steps V <- V (3I - V^H V)/2, the FP64
+// matrix is rotated, A' = V^H A V (off-diagonal ~1e-7 ||A||), and FP64 sweeps
+// finish it (quadratic convergence: about two sweeps) to an off-diagonal norm
+// below 1e-17 ||A||_F.  The result is the eigendecomposition of the FP64 A.
+template <int NP>
+__global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict__ A, long sA, long lda, int n,
+                                                      long batch, double* __restrict__ w, long sw,
+                                                      double2* __restrict__ V, long sV, int max_sweeps,
+                                                      int* __restrict__ status) {
+  constexpr int G = 32 / NP;
+  const int lane = threadIdx.x & 31;
+  const int grp0 = lane / NP;
+  const bool in_group = grp0 < G;
+  const int grp = in_group ? grp0 : 0;
+  const int j = in_group ? lane - grp * NP : 0;
+  const int base = grp * NP;
+  const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long mat = warp * G + grp;
+  const bool valid = in_group && mat < batch;
+
+  double2 a[NP];
+#pragma unroll
+  for (int r = 0; r < NP; ++r) a[r] = (valid && r < n && j < n) ? A[mat * sA + (long)r * lda + j] : make_double2(0.0, 0.0);
+#pragma unroll
+  for (int r = 0; r < NP; ++r)
+    if (r == j) a[r].y = 0.0;
+  double my2 = 0.0;
+#pragma unroll
+  for (int r = 0; r < NP; ++r) my2 = fma(a[r].x, a[r].x, fma(a[r].y, a[r].y, my2));
+  double fro2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) fro2 += shfl_d(my2, base + i);
+
+  // ---- FP32 preconditioning sweeps
+  double2 v[NP];
+  {
+    float2 af[NP], vf[NP];
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      af[r] = make_float2((float)a[r].x, (float)a[r].y);
+      vf[r] = make_float2(r == j ? 1.f : 0.f, 0.f);
+    }
+    const float fro2f = (float)fro2;
+    const float thr32 = 1e-30f * fro2f + 1e-37f;
+    const float tol32 = 1e-12f * fro2f;
+    bool c32 = !valid;
+    int s32 = 0;
+    while (__any_sync(0xffffffffu, !c32) && s32 < 12) {
+      Sweep<NP, 0, float>::run(af, vf, j, base, thr32);
+      ++s32;
+      const float off = group_off2<NP>(af, j, base);  // shuffles: every lane takes part
+      if (valid && off <= tol32) c32 = true;
+    }
+#pragma unroll
+    for (int r = 0; r < NP; ++r) v[r] = make_double2((double)vf[r].x, (double)vf[r].y);
+  }
+  // ---- FP64: two Newton-Schulz steps, v_j' = 1.5 v_j - 0.5 sum_i v_i (v_i^H v_j)
+  // (non-unitarity 5e-7 -> 4e-13 -> rounding level)
+  double2 vn[NP];
+#pragma unroll 1
+  for (int it = 0; it < 2; ++it) {
+#pragma unroll
+    for (int r = 0; r < NP; ++r) vn[r] = make_double2(1.5 * v[r].x, 1.5 * v[r].y);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      double2 vi[NP];
+      double gx = 0.0, gy = 0.0;
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        vi[r] = shfl_d2(v[r], base + i);
+        gx = fma(vi[r].x, v[r].x, fma(vi[r].y, v[r].y, gx));
+        gy = fma(vi[r].x, v[r].y, fma(-vi[r].y, v[r].x, gy));
+      }
+      gx *= 0.5;
+      gy *= 0.5;
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        vn[r].x = fma(-vi[r].x, gx, fma(vi[r].y, gy, vn[r].x));
+        vn[r].y = fma(-vi[r].x, gy, fma(-vi[r].y, gx, vn[r].y));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NP; ++r) v[r] = vn[r];
+  }
+  // ---- A' = V^H A V:  w = A v_j (columns of A from all lanes), then A'[i][j] = v_i^H w
+  {
+    double2 wv[NP];
+#pragma unroll
+    for (int r = 0; r < NP; ++r) wv[r] = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int s2 = 0; s2 < NP; ++s2) {
+      const double2 vs = vn[s2];
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        const double2 cs = shfl_d2(a[r], base + s2);  // A[r][s2]
+        wv[r].x = fma(cs.x, vs.x, fma(-cs.y, vs.y, wv[r].x));
+        wv[r].y = fma(cs.x, vs.y, fma(cs.y, vs.x, wv[r].y));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      double ax = 0.0, ay = 0.0;
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        const double2 vi = shfl_d2(vn[r], base + i);
+        ax = fma(vi.x, wv[r].x, fma(vi.y, wv[r].y, ax));
+        ay = fma(vi.x, wv[r].y, fma(-vi.y, wv[r].x, ay));
+      }
+      a[i] = make_double2(ax, (i == j) ? 0.0 : ay);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NP; ++r) v[r] = vn[r];
+  // padded columns stay exact unit vectors with zero coupling
+  if (j >= n) {
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      a[r] = make_double2(0.0, 0.0);
+      v[r] = make_double2(r == j ? 1.0 : 0.0, 0.0);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NP; ++r)
+    if (r >= n && j < n) a[r] = make_double2(0.0, 0.0);
+
+  // ---- FP64 sweeps to full accuracy
+  const double thresh2 = 1e-36 * fro2 + 1e-300;
+  const double tol2 = 1e-34 * fro2;
+  bool conv = !valid;
+  int sweep = 0;
+  while (__any_sync(0xffffffffu, !conv) && sweep < max_sweeps) {
+    Sweep<NP, 0, double>::run(a, v, j, base, thresh2);
+    ++sweep;
+    const double off = group_off2<NP>(a, j, base);  // shuffles: every lane takes part
+    if (valid && off <= tol2) conv = true;
+  }
+  if (valid && j == 0 && !conv) atomicOr(status, 1);
+
+  double lam = 0.0;
+#pragma unroll
+  for (int r = 0; r < NP; ++r)
+    if (r == j) lam = a[r].x;
+  int rank = 0;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const double li = shfl_d(lam, base + i);
+    if (i < n && (li < lam || (li == lam && i < j))) ++rank;
+  }
+  if (valid && j < n) {
+    w[mat * sw + rank] = lam;
+    double2* out = V + mat * sV;
+#pragma unroll
+    for (int r = 0; r < NP; ++r)
+      if (r < n) out[(long)r * n + rank] = v[r];
+  }
+}
+
+cudaError_t launch_jacobi_mixed(const double2* A, long sA, long lda, int n, long batch, double* w, long sw, double2* V,
+                                long sV, int max_sweeps, int* status, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  if (n < 1 || n > 16) return cudaErrorInvalidValue;
+  int np = (n + 1) & ~1;
+  if (np < 2) np = 2;
+  const int G = 32 / np;
+  const long warps = (batch + G - 1) / G;
+  const int threads = 128;
+  const long blocks = (warps * 32 + threads - 1) / threads;
+  if (blocks > 2147483647L) return cudaErrorInvalidConfiguration;
+#define EPH_JM(NPV)                                                                                              \
+  case NPV:                                                                                                      \
+    k_jacobi_mixed<NPV><<<(unsigned)blocks, threads, 0, st>>>(A, sA, lda, n, batch, w, sw, V, sV, max_sweeps, status); \
+    break;
+  switch (np) {
+    EPH_JM(2) EPH_JM(4) EPH_JM(6) EPH_JM(8) EPH_JM(10) EPH_JM(12)
+    default:  // 14, 16: the register-resident preconditioning would spill; plain FP64 sweeps
+      return launch_jacobi(A, sA, lda, n, batch, w, sw, V, sV, max_sweeps, status, st);
+  }
+#undef EPH_JM
+  return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi(const double2* A, long sA, long lda, int n, long batch, double* w, long sw, double2* V,

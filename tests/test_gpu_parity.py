@@ -35,11 +35,13 @@ def check(gpu, ref, tol, what=""):
 
 
 @pytest.mark.parametrize("q_batch,k_tile", [(0, 0), (3, 20), (16, 64), (1, 1)])
-def test_si_tiny_fp64(q_batch, k_tile):
+@pytest.mark.parametrize("plain", [False, True])
+def test_si_tiny_fp64(q_batch, k_tile, plain):
+    # plain: FP64 Jacobi sweeps only; else FP32-preconditioned sweeps finished in FP64
     wl = synth.make_workload("si_tiny")
-    ctx = binding.Context.from_workload(wl, q_batch=q_batch, k_tile=k_tile)
+    ctx = binding.Context.from_workload(wl, q_batch=q_batch, k_tile=k_tile, eig_plain_fp64=plain)
     gpu = ctx.interp(wl.kpts, wl.qpts)
-    check(gpu, oracle.interpolate(wl), TOL_FP64, f"si_tiny qb={q_batch} kt={k_tile}")
+    check(gpu, oracle.interpolate(wl), TOL_FP64, f"si_tiny qb={q_batch} kt={k_tile} plain={plain}")
 
 
 def test_mos2_shaped_small_fp64():
@@ -49,7 +51,7 @@ def test_mos2_shaped_small_fp64():
     check(ctx.interp(wl.kpts, wl.qpts), oracle.interpolate(wl), TOL_FP64, "mos2 small")
 
 
-@pytest.mark.parametrize("nb,nk,nq", [(1, 5, 3), (2, 1, 1), (3, 7, 2), (16, 9, 2)])
+@pytest.mark.parametrize("nb,nk,nq", [(1, 5, 3), (2, 1, 1), (3, 7, 2), (11, 6, 2), (12, 5, 2), (16, 9, 2)])
 def test_edge_sizes(nb, nk, nq):
     wl = synth.make_workload("si_tiny", nb=nb, nk=nk, nq=nq)
     ctx = binding.Context.from_workload(wl)
@@ -110,7 +112,7 @@ def test_error_paths():
         ctx.interp_q(wl.qpts)
     assert ei.value.code == binding.EPH_ESTATE
     # a sweep cap of 1 cannot converge an 8x8 Jacobi: reported, not hung
-    ctx1 = binding.Context.from_workload(wl, max_sweeps=1)
+    ctx1 = binding.Context.from_workload(wl, max_sweeps=1, eig_plain_fp64=True)
     with pytest.raises(binding.EphError) as ei:
         ctx1.set_k(wl.kpts)
     assert ei.value.code == binding.EPH_ENOTCONV
