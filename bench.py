@@ -36,10 +36,14 @@ METRIC = "e-ph g(k,q) elements/s, 1 GB300: split-precision vs FP64 form at state
 UNIT = "g elements/s"
 # FP64 pipe of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and max clock)
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
-# kernel from one ncu capture of a one-q launch, scaled to the bench launch by the units
-# processed (profiles/k_zgemm_si_full_fp64.md).  Keyed by (kernel, workload, q batch).
-TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one ncu
+# capture of a one-q launch, scaled to the bench launch by the units processed
+# (profiles/k_zgemm_si_full_fp64.md, profiles/k_tc_fixed_gemm_si_full.md).
+# Keyed by (kernel, workload, q batch).
+TRAFFIC = {("k_zgemm", "si_full", 4): 4 * (224.901120e6 + 405.762048e6),
+           ("k_zgemm", "si_full", 1): 224.901120e6 + 405.762048e6,
+           ("k_tc_fixed_gemm", "si_full", 4): 4 * (175.208704e6 + 152.453888e6),
+           ("k_tc_fixed_gemm", "si_full", 1): 175.208704e6 + 152.453888e6}
 
 
 def parse():
@@ -314,7 +318,7 @@ def run_libeph(args):
                 "achieved": issued / t / 1e12 if t else None, "peak": peak, "unit": "TFLOP/s",
                 "frac": (issued / t / 1e12 / peak) if (t and peak) else None,
                 "useful_tflops": useful / t / 1e12 if t else None, "ms_per_launch": tc_ms / max(tc_n, 1),
-                "traffic": None,
+                "traffic": TRAFFIC.get(("k_tc_fixed_gemm", args.workload, QB)),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), measured" if peak else "unavailable"}
 
     line = None

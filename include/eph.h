@@ -66,6 +66,9 @@ typedef struct eph_options {
                         1 = two-term split TF32 (3 products) */
   int eig_plain_fp64; /* 0 (default): Jacobi sweeps preconditioned in FP32, then FP64 sweeps to
                          full FP64 accuracy; 1: FP64 sweeps only */
+  int async;          /* 1: eph_interp_q only enqueues work on the context's stream (device pointers
+                         required, no host synchronisation, no event timing) so that a sequence of
+                         calls can be captured into one CUDA graph; its status is read by eph_sync */
 } eph_options;
 
 /* Fills *opt with the defaults (FP64 form, host pointers, automatic batching). */
@@ -169,6 +172,23 @@ enum eph_stage {
 int eph_profile(eph_ctx* ctx, int enable);
 int eph_profile_read(const eph_ctx* ctx, int stage, double* ms, long long* launches);
 int eph_profile_reset(eph_ctx* ctx);
+
+/*
+ * Batching support (several materials / uneven q batches in one captured CUDA graph):
+ *   eph_reserve   sizes every workspace buffer for calls of up to nq q points with the
+ *                 resident k list, so that later eph_interp_q calls allocate nothing
+ *                 (a requirement for stream capture).
+ *   eph_sync      synchronises the context's stream, reads and clears the device status
+ *                 flags of the work enqueued since the last check (async mode).
+ *   eph_autotune  picks q_batch and k_tile for nq q points by timing candidate
+ *                 decompositions (q_batch 1..16, k tiles of nk, nk/2, nk/4) with CUDA
+ *                 events on the context's stream; the choice is stored in the context
+ *                 and cached per problem shape for the process.  Needs device pointers
+ *                 and synchronous mode; allocates its probe outputs.
+ */
+int eph_reserve(eph_ctx* ctx, int nq);
+int eph_sync(eph_ctx* ctx);
+int eph_autotune(eph_ctx* ctx, int nq, const double* qpts, int* q_batch_out, int* k_tile_out);
 
 /*
  * Band energies and eigenvectors of H(k) = sum_Re w_e e^{i k.Re} H(Re) for a

@@ -22,7 +22,8 @@ FORMS = {"fp64": 0, "mixed": 1}
 #: every symbol declared in include/eph.h
 EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "eph_interp",
            "eph_interp_backward", "eph_destroy", "eph_strerror", "eph_last_error", "eph_kernel_launches",
-           "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc")
+           "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc",
+           "eph_reserve", "eph_sync", "eph_autotune")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -30,7 +31,7 @@ STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 class EphOptions(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("device_ptrs", ctypes.c_int), ("q_batch", ctypes.c_int),
                 ("k_tile", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("workspace_mb", ctypes.c_int),
-                ("mixed_scheme", ctypes.c_int), ("eig_plain_fp64", ctypes.c_int)]
+                ("mixed_scheme", ctypes.c_int), ("eig_plain_fp64", ctypes.c_int), ("async_", ctypes.c_int)]
 
 
 class EphError(RuntimeError):
@@ -81,6 +82,12 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_profile_reset.restype = i
     lib.eph_bands_noalloc.argtypes = [i, dp, i, i, vp, dp, dp, dp, dp, i, vp]
     lib.eph_bands_noalloc.restype = i
+    lib.eph_reserve.argtypes = [vp, i]
+    lib.eph_reserve.restype = i
+    lib.eph_sync.argtypes = [vp]
+    lib.eph_sync.restype = i
+    lib.eph_autotune.argtypes = [vp, i, dp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.eph_autotune.restype = i
     del ip
     if path is None:
         _lib = lib
@@ -112,7 +119,7 @@ class Context:
 
     def __init__(self, nb, na, H_Re, Phi_Rp, g_ReRp, Re, Rp, masses, we=None, wp=None, form="fp64",
                  device_ptrs=False, q_batch=0, k_tile=0, max_sweeps=0, workspace_mb=0, stream=None,
-                 mixed_scheme="digits", eig_plain_fp64=False):
+                 mixed_scheme="digits", eig_plain_fp64=False, async_mode=False):
         self.lib = load_library()
         self.nb, self.na, self.nm = int(nb), int(na), 3 * int(na)
         H_Re = np.ascontiguousarray(H_Re, dtype=np.complex128)
@@ -126,6 +133,7 @@ class Context:
         self.ne, self.np_ = len(Re), len(Rp)
         self.form = form
         self.device_ptrs = bool(device_ptrs)
+        self.async_mode = bool(async_mode)
         opt = EphOptions()
         self.lib.eph_default_options(ctypes.byref(opt))
         opt.form = FORMS[form]
@@ -133,6 +141,7 @@ class Context:
         opt.q_batch, opt.k_tile, opt.max_sweeps, opt.workspace_mb = q_batch, k_tile, max_sweeps, workspace_mb
         opt.mixed_scheme = {"digits": 0, "tf32": 1}[mixed_scheme]
         opt.eig_plain_fp64 = int(bool(eig_plain_fp64))
+        opt.async_ = int(bool(async_mode))
         handle = ctypes.c_void_p()
         st = None
         if stream is not None:
@@ -190,6 +199,17 @@ class Context:
 
     def eph_interp_q(self, nq, qpts, eps_kq=None, omega=None, g=None):
         self._check(self.lib.eph_interp_q(self.handle, int(nq), _ptr(qpts), _ptr(eps_kq), _ptr(omega), _ptr(g)))
+
+    def eph_reserve(self, nq):
+        self._check(self.lib.eph_reserve(self.handle, int(nq)))
+
+    def eph_sync(self):
+        self._check(self.lib.eph_sync(self.handle))
+
+    def eph_autotune(self, nq, qpts):
+        qb, kt = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.eph_autotune(self.handle, int(nq), _ptr(qpts), ctypes.byref(qb), ctypes.byref(kt)))
+        return qb.value, kt.value
 
     def eph_interp_backward(self, nk, kpts, nq, qpts, w_nk, omega_min, L_out, grad):
         self._check(self.lib.eph_interp_backward(self.handle, int(nk), _ptr(kpts), int(nq), _ptr(qpts), _ptr(w_nk),

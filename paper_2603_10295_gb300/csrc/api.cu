@@ -15,6 +15,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "eph.h"
@@ -196,7 +198,7 @@ double omega_unit_ev() {
 #define EPH_LAUNCH_S(stage, call)                                 \
   do {                                                            \
     cudaEvent_t ea_ = nullptr, eb_ = nullptr;                     \
-    if (ctx->prof) {                                              \
+    if (ctx->prof && !ctx->opt.async) {                           \
       ea_ = take_event(ctx);                                      \
       eb_ = take_event(ctx);                                      \
       if (ea_) cudaEventRecord(ea_, ctx->stream);                 \
@@ -405,6 +407,7 @@ cudaMemcpyKind out_kind(const eph_ctx* ctx) {
 }
 
 int finish(eph_ctx* ctx) {
+  if (ctx->opt.async) return EPH_OK;  // status is read by eph_sync
   int h[2] = {0, 0};
   EPH_CK(cudaMemcpyAsync(h, ctx->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   EPH_CK(cudaStreamSynchronize(ctx->stream));
@@ -551,8 +554,9 @@ int k_tile_forward(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
 
 // Mixed form: H(k+q) and every eigensolve in FP64; the Re->k contraction of g as a
 // split-TF32 tensor-core GEMM with FP32 accumulation; FP32 band rotation; complex64 g.
-int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
-  const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, nk = ctx->nk, kp = ctx->kp;
+// Workspace plan of the mixed form for nq q points (allocates; nothing is launched).
+int prepare_mixed(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
+  const int nb = ctx->nb, nm = ctx->nm, nk = ctx->nk, kp = ctx->kp;
   const int nb2 = nb * nb;
   const long nr = ctx->nr;
   const bool host = !ctx->opt.device_ptrs;
@@ -560,7 +564,7 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
   // per (q,k): H(k+q) + V_{k+q} (FP64), eigenvalues, G3 (FP32 real embedding), host staging of g
   QPlan p = plan_q(ctx, nq, 0);
   {
-    const size_t per_pair = (size_t)nb2 * 16 * 2 + (size_t)nb * 8 + (size_t)nr * 4 + (host && g ? (size_t)gcols * 8 : 0);
+    const size_t per_pair = (size_t)nb2 * 16 * 2 + (size_t)nb * 8 + (size_t)nr * 4 + (host && want_g ? (size_t)gcols * 8 : 0);
     const size_t budget = (size_t)ctx->opt.workspace_mb << 20;
     long KT = ctx->opt.k_tile > 0 ? ctx->opt.k_tile : (long)(budget / (per_pair * p.QB));
     if (KT > nk) KT = nk;
@@ -568,8 +572,6 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
     if (KT < 1) KT = 1;
     p.KT = KT;
   }
-  const void* dq = nullptr;
-  EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
   EPH_TRY(ensure_q_workspace(ctx, p, false));
   const bool digits = ctx->opt.mixed_scheme == 0;
   const int kpd = ctx->kpd;
@@ -577,16 +579,36 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
   if (digits) {
     EPH_TRY(ensure(ctx, ctx->DB, 4 * dslice * 2));
     EPH_TRY(ensure(ctx, ctx->sB, (size_t)p.QB * nr * sizeof(float)));
-    for (int d = 0; d < 4; ++d)
-      EPH_CK(make_tc_map_bf16(&ctx->mapDB[d], static_cast<char*>(ctx->DB.p) + d * dslice * 2, (long)p.QB * nr, kpd,
-                              128));
   } else {
     EPH_TRY(ensure(ctx, ctx->Bhi, (size_t)p.QB * nr * kp * sizeof(float)));
     EPH_TRY(ensure(ctx, ctx->Blo, (size_t)p.QB * nr * kp * sizeof(float)));
   }
   EPH_TRY(ensure(ctx, ctx->G3f, (size_t)p.QB * p.KT * nr * sizeof(float)));
   EPH_TRY(ensure(ctx, ctx->Hkq, (size_t)p.QB * p.KT * nb2 * sizeof(double2)));
-  if (host && g) EPH_TRY(ensure(ctx, ctx->g_stage32, (size_t)p.QB * p.KT * gcols * 2 * sizeof(float)));
+  if (host && want_g) EPH_TRY(ensure(ctx, ctx->g_stage32, (size_t)p.QB * p.KT * gcols * 2 * sizeof(float)));
+  *out = p;
+  return EPH_OK;
+}
+
+// Mixed form: H(k+q) and every eigensolve in FP64; the Re->k contraction of g as a
+// split-TF32 tensor-core GEMM with FP32 accumulation; FP32 band rotation; complex64 g.
+int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
+  const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, nk = ctx->nk, kp = ctx->kp;
+  const int nb2 = nb * nb;
+  const long nr = ctx->nr;
+  const bool host = !ctx->opt.device_ptrs;
+  const long gcols = (long)nm * nb2;
+  QPlan p;
+  EPH_TRY(prepare_mixed(ctx, nq, g != nullptr, &p));
+  const void* dq = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
+  const bool digits = ctx->opt.mixed_scheme == 0;
+  const int kpd = ctx->kpd;
+  const size_t dslice = (size_t)p.QB * nr * kpd;
+  if (digits)
+    for (int d = 0; d < 4; ++d)
+      EPH_CK(make_tc_map_bf16(&ctx->mapDB[d], static_cast<char*>(ctx->DB.p) + d * dslice * 2, (long)p.QB * nr, kpd,
+                              128));
   if (!digits) {
     EPH_CK(make_tc_map(&ctx->mapBhi, as<float>(ctx->Bhi), (long)p.QB * nr, kp, 256));
     EPH_CK(make_tc_map(&ctx->mapBlo, as<float>(ctx->Blo), (long)p.QB * nr, kp, 256));
@@ -650,21 +672,31 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
   return finish(ctx);
 }
 
+// Workspace plan of the FP64 form for nq q points (allocates; nothing is launched).
+int prepare_fp64(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
+  const bool host = !ctx->opt.device_ptrs;
+  const QPlan p = plan_q(ctx, nq, host && want_g ? (size_t)ctx->nm * ctx->nb * ctx->nb * 16 : 0);
+  EPH_TRY(ensure_q_workspace(ctx, p));
+  if (host && want_g) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)p.QB * p.KT * p.gcols * sizeof(double2)));
+  *out = p;
+  return EPH_OK;
+}
+
 }  // namespace
 
 extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
   if (!ctx) return EPH_EINVAL;
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
   if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
+  if (ctx->opt.async && !ctx->opt.device_ptrs) return fail(ctx, EPH_EINVAL, "async mode needs device pointers");
   if (ctx->opt.form == EPH_FORM_MIXED) return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
   const int nb = ctx->nb, nm = ctx->nm, nk = ctx->nk;
   const int nb2 = nb * nb;
   const bool host = !ctx->opt.device_ptrs;
-  const QPlan p = plan_q(ctx, nq, host && g ? (size_t)nm * nb2 * 16 : 0);
+  QPlan p;
+  EPH_TRY(prepare_fp64(ctx, nq, g != nullptr, &p));
   const void* dq = nullptr;
   EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
-  EPH_TRY(ensure_q_workspace(ctx, p));
-  if (host && g) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)p.QB * p.KT * p.gcols * sizeof(double2)));
   const double* qdev = static_cast<const double*>(dq);
   double2* Y = as<double2>(ctx->Y);
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
@@ -771,4 +803,120 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
   EPH_CK(cudaMemcpyAsync(L_out, ctx->Lacc.p, sizeof(double), out_kind(ctx), ctx->stream));
   if (host) EPH_CK(cudaMemcpyAsync(grad_g_ReRp, grad, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
   return finish(ctx);
+}
+
+extern "C" int eph_sync(eph_ctx* ctx) {
+  if (!ctx) return EPH_EINVAL;
+  int h[2] = {0, 0};
+  EPH_CK(cudaMemcpyAsync(h, ctx->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  EPH_CK(cudaStreamSynchronize(ctx->stream));
+  collect_profile(ctx);
+  if (h[0] || h[1]) {
+    EPH_CK(cudaMemsetAsync(ctx->status, 0, 2 * sizeof(int), ctx->stream));
+    EPH_CK(cudaStreamSynchronize(ctx->stream));
+    if (h[1]) return fail(ctx, EPH_ECUDA, "a tensor-core pipeline wait timed out");
+    return fail(ctx, EPH_ENOTCONV, "a batched Jacobi eigensolve reached the sweep cap");
+  }
+  return EPH_OK;
+}
+
+extern "C" int eph_reserve(eph_ctx* ctx, int nq) {
+  if (!ctx) return EPH_EINVAL;
+  if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_reserve before eph_set_k");
+  if (nq < 1) return fail(ctx, EPH_EINVAL, "eph_reserve: nq < 1");
+  QPlan p;
+  EPH_TRY(ensure(ctx, ctx->qpts, (size_t)nq * 3 * sizeof(double)));
+  if (ctx->opt.form == EPH_FORM_MIXED) return prepare_mixed(ctx, nq, true, &p);
+  return prepare_fp64(ctx, nq, true, &p);
+}
+
+namespace {
+struct TuneKey {
+  int form, scheme, nb, nm, ne, np, nk, nq;
+  bool operator<(const TuneKey& o) const {
+    const int a[8] = {form, scheme, nb, nm, ne, np, nk, nq}, b[8] = {o.form, o.scheme, o.nb, o.nm, o.ne, o.np, o.nk, o.nq};
+    for (int i = 0; i < 8; ++i)
+      if (a[i] != b[i]) return a[i] < b[i];
+    return false;
+  }
+};
+std::map<TuneKey, std::pair<int, int>> g_tuned;
+std::mutex g_tune_mutex;
+}  // namespace
+
+extern "C" int eph_autotune(eph_ctx* ctx, int nq, const double* qpts, int* q_batch_out, int* k_tile_out) {
+  if (!ctx) return EPH_EINVAL;
+  if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_autotune before eph_set_k");
+  if (nq < 1 || !qpts || !ctx->opt.device_ptrs || ctx->opt.async)
+    return fail(ctx, EPH_EINVAL, "eph_autotune needs nq >= 1, device pointers and synchronous mode");
+  const TuneKey key{ctx->opt.form, ctx->opt.mixed_scheme, ctx->nb, ctx->nm, ctx->ne, ctx->np, ctx->nk, nq};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      ctx->opt.q_batch = it->second.first;
+      ctx->opt.k_tile = it->second.second;
+      if (q_batch_out) *q_batch_out = ctx->opt.q_batch;
+      if (k_tile_out) *k_tile_out = ctx->opt.k_tile;
+      return EPH_OK;
+    }
+  }
+  const int nk = ctx->nk, nb = ctx->nb, nm = ctx->nm;
+  const size_t gbytes = (size_t)nq * nk * nm * nb * nb * (ctx->opt.form == EPH_FORM_MIXED ? 8 : 16);
+  double *eps = nullptr, *om = nullptr;
+  void* g = nullptr;
+  if (cudaMalloc(&eps, (size_t)nq * nk * nb * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&om, (size_t)nq * nm * sizeof(double)) != cudaSuccess || cudaMalloc(&g, gbytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(eps);
+    cudaFree(om);
+    cudaFree(g);
+    return fail(ctx, EPH_ENOMEM, "eph_autotune probe buffers");
+  }
+  const int q0 = ctx->opt.q_batch, k0 = ctx->opt.k_tile;
+  const int qbs[] = {1, 2, 4, 8, 16};
+  const long kts[] = {0, (long)((nk + 1) / 2), (long)((nk + 3) / 4)};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bq = q0, bk = k0, rc = EPH_OK;
+  for (int qb : qbs) {
+    if (qb > nq) break;
+    for (long kt : kts) {
+      if (kt != 0 && kt >= nk) continue;
+      ctx->opt.q_batch = qb;
+      ctx->opt.k_tile = (int)kt;
+      rc = eph_interp_q(ctx, nq, qpts, eps, om, g);  // warm-up: sizes the workspace
+      if (rc != EPH_OK) break;
+      cudaEventRecord(e0, ctx->stream);
+      rc = eph_interp_q(ctx, nq, qpts, eps, om, g);
+      cudaEventRecord(e1, ctx->stream);
+      if (rc != EPH_OK) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bq = qb;
+        bk = (int)kt;
+      }
+    }
+    if (rc != EPH_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(eps);
+  cudaFree(om);
+  cudaFree(g);
+  ctx->opt.q_batch = (rc == EPH_OK) ? bq : q0;
+  ctx->opt.k_tile = (rc == EPH_OK) ? bk : k0;
+  if (rc != EPH_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[key] = {bq, bk};
+  }
+  if (q_batch_out) *q_batch_out = bq;
+  if (k_tile_out) *k_tile_out = bk;
+  return EPH_OK;
 }

@@ -1,0 +1,96 @@
+"""Batching: two materials of different shape (silicon-like Nb=8/Nm=6 and
+MoS2-like Nb=11/Nm=9) with uneven q batches, in both forms, captured into one
+CUDA graph; replays must reproduce the eager results exactly, also after new q
+points are copied into the captured inputs.  The autotuner must pick a valid
+decomposition that leaves the results unchanged."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_10295_gb300 import binding, build_lib, synth
+from tests import gauge
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not os.path.exists(binding.LIB_PATH):
+        build_lib.build()
+    return binding.load_library()
+
+
+def _materials():
+    si = synth.make_workload("si_tiny", nk=150, nq=40)
+    box = (synth.centred_range(6), synth.centred_range(6), range(0, 1))
+    mo = synth.make_workload("mos2", nk=120, nq=40, box=box)
+    return [(si, [3, 5, 1]), (mo, [2, 7])]
+
+
+def _buffers(torch, wl, nq, form, dev):
+    nk, nb, nm = len(wl.kpts), wl.nb, wl.nm
+    gdt = torch.complex128 if form == "fp64" else torch.complex64
+    return (torch.empty(nq, nk, nb, dtype=torch.float64, device=dev), torch.empty(nq, nm, dtype=torch.float64, device=dev),
+            torch.empty(nq, nk, nm, nb, nb, dtype=gdt, device=dev))
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_graph_replay_matches_eager(form):
+    torch = pytest.importorskip("torch")
+    from paper_2603_10295_gb300.batching import GraphBatcher
+    dev = torch.device("cuda:0")
+    gb = GraphBatcher(dev)
+    eager, keep = [], []
+    for wl, batches in _materials():
+        ctx = binding.Context.from_workload(wl, form=form, device_ptrs=True, async_mode=True, stream=gb.stream)
+        ctx.eph_set_k(len(wl.kpts), torch.from_numpy(wl.kpts).to(dev))
+        ref_ctx = binding.Context.from_workload(wl, form=form)
+        ref_ctx.set_k(wl.kpts)
+        q0 = 0
+        for nq in batches:
+            q = torch.from_numpy(wl.qpts[q0:q0 + nq].copy()).to(dev)
+            bufs = _buffers(torch, wl, nq, form, dev)
+            gb.add(ctx, q, *bufs)
+            eager.append((ref_ctx, wl, q0, nq, bufs))
+            q0 += nq
+        keep.append(ctx)
+    gb.capture()
+    for shift in (0, 20):                        # second round: new q points copied into the captured inputs
+        if shift:
+            for (ref_ctx, wl, q0, nq, _), item in zip(eager, gb.items):
+                item[1].copy_(torch.from_numpy(wl.qpts[q0 + shift:q0 + shift + nq].copy()).to(dev))
+        gb.replay()
+        gb.check()
+        for (ref_ctx, wl, q0, nq, bufs) in eager:
+            e_kq, om, g = ref_ctx.interp_q(wl.qpts[q0 + shift:q0 + shift + nq])
+            assert np.array_equal(bufs[0].cpu().numpy(), e_kq)
+            assert np.array_equal(bufs[1].cpu().numpy(), om)
+            assert np.array_equal(bufs[2].cpu().numpy(), g)
+
+
+def test_autotune_picks_valid_tiles_and_keeps_results():
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    wl = synth.make_workload("si_tiny", nk=500, nq=6)
+    ctx = binding.Context.from_workload(wl, device_ptrs=True, stream=torch.cuda.current_stream())
+    nk = len(wl.kpts)
+    ctx.eph_set_k(nk, torch.from_numpy(wl.kpts).to(dev))
+    q = torch.from_numpy(wl.qpts).to(dev)
+    bufs0 = _buffers(torch, wl, 6, "fp64", dev)
+    ctx.eph_interp_q(6, q, *bufs0)
+    qb, kt = ctx.eph_autotune(6, q)
+    assert 1 <= qb <= 6 and 0 <= kt < nk
+    bufs1 = _buffers(torch, wl, 6, "fp64", dev)
+    ctx.eph_interp_q(6, q, *bufs1)
+    torch.cuda.synchronize()
+    for a, b in zip(bufs0, bufs1):
+        assert np.allclose(a.cpu().numpy(), b.cpu().numpy(), rtol=0, atol=1e-13)
+    # second context of the same shape reuses the cached choice
+    ctx2 = binding.Context.from_workload(wl, device_ptrs=True, stream=torch.cuda.current_stream())
+    ctx2.eph_set_k(nk, torch.from_numpy(wl.kpts).to(dev))
+    assert ctx2.eph_autotune(6, q) == (qb, kt)
+    # and the results still match the oracle
+    ref = oracle.interpolate(wl)
+    assert gauge.max_rel_S(bufs1[2].cpu().numpy(), ref[3], ref[0], ref[1], ref[2]) <= 1e-12
