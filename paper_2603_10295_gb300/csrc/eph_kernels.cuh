@@ -46,10 +46,12 @@ cudaError_t launch_skinny_real(int M, long N, int K, const double2* P, long ldp,
 cudaError_t launch_jacobi(const double2* A, long sA, long lda, int n, long batch, double* w, long sw,
                           double2* V, long sV, int max_sweeps, int* status, cudaStream_t st);
 
-// Same contract; FP32 preconditioning sweeps, one FP64 Newton-Schulz re-orthonormalisation,
-// then FP64 sweeps (n <= 12; larger n run the plain FP64 kernel).
+// Same contract; FP32 preconditioning sweeps, two FP64 Newton-Schulz re-orthonormalisations,
+// then FP64 sweeps to an off-diagonal norm <= polish_tol ||A||_F (n <= 12; larger n run the
+// plain FP64 kernel).
 cudaError_t launch_jacobi_mixed(const double2* A, long sA, long lda, int n, long batch, double* w, long sw,
-                                double2* V, long sV, int max_sweeps, int* status, cudaStream_t st);
+                                double2* V, long sV, int max_sweeps, double polish_tol, int* status,
+                                cudaStream_t st);
 
 // ---- phonon post-processing: omega = sign(l) sqrt|l| * unit; u = e / sqrt(M)
 cudaError_t launch_phonon_post(const double* lam, const double2* e, int nq, int nm, const double* invsqrtm,
