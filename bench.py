@@ -41,9 +41,7 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # (profiles/k_zgemm_si_full_fp64.md, profiles/k_tc_fixed_gemm_si_full.md).
 # Keyed by (kernel, workload, q batch).
 TRAFFIC = {("k_zgemm", "si_full", 4): 4 * (224.901120e6 + 405.762048e6),
-           ("k_zgemm", "si_full", 1): 224.901120e6 + 405.762048e6,
-           ("k_tc_fixed_gemm", "si_full", 4): 4 * (175.208704e6 + 152.453888e6),
-           ("k_tc_fixed_gemm", "si_full", 1): 175.208704e6 + 152.453888e6}
+           ("k_zgemm", "si_full", 1): 224.901120e6 + 405.762048e6}
 
 
 def parse():

@@ -145,21 +145,9 @@ cudaError_t launch_band_rotate_f32(const float* Y, long ldy_floats, const double
 }
 
 // ---- fixed-point BF16 digits (exact tensor-core accumulation) ------------------------
-// x/s = sum_i d_i 2^-8(i+1) + O(2^-8n-1), integer digits |d| <= 128 (exact in bf16);
-// s is a power of two with |x| <= s/2 for every x of the row (A: all rows share sA).
-__device__ __forceinline__ void digits3(double x, double inv_s, __nv_bfloat16& d0, __nv_bfloat16& d1,
-                                        __nv_bfloat16& d2) {
-  double y = x * inv_s * 256.0;
-  const double a0 = rint(y);
-  y = (y - a0) * 256.0;
-  const double a1 = rint(y);
-  y = (y - a1) * 256.0;
-  const double a2 = rint(y);
-  d0 = __float2bfloat16_rn((float)a0);
-  d1 = __float2bfloat16_rn((float)a1);
-  d2 = __float2bfloat16_rn((float)a2);
-}
-
+// x/s = sum_i d_i 2^-8(i+1) + O(2^-8n-1), integer digits |d| <= 128, digit i stored as
+// d_i 2^-8i (exact in bf16); s is a power of two with |x| <= s/2 for every x of the row
+// (A: all rows share sA).
 // A digits: P[n][ne] complex128 (row stride ldp) -> D[3][n][kp] bf16 (slice stride n*kp).
 __global__ void k_digits_a(const double2* __restrict__ P, long ldp, int n, int ne, int kp, double inv_s,
                            __nv_bfloat16* __restrict__ D) {
@@ -173,7 +161,15 @@ __global__ void k_digits_a(const double2* __restrict__ P, long ldp, int n, int n
     const double2 p = P[m * ldp + (c >> 1)];
     x = (c & 1) ? p.y : p.x;
   }
-  digits3(x, inv_s, D[idx], D[tot + idx], D[2 * tot + idx]);
+  // digit i stored pre-scaled by 2^-8i (exact in bf16), so products land at their own scale
+  double y = x * inv_s * 256.0, sc = 1.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double a = rint(y);
+    D[d * tot + idx] = __float2bfloat16_rn((float)(a * sc));
+    y = (y - a) * 256.0;
+    sc *= 0x1p-8;
+  }
 }
 
 cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, double scale, void* D, cudaStream_t st) {
@@ -223,12 +219,13 @@ __global__ void k_digits_b(const double2* __restrict__ W, long ldw, long sW, int
     x = (sgn == t) ? g.x : (sgn == 0 ? -g.y : g.y);
   }
   const double inv_s = 1.0 / (double)sB[(long)q * 2 * ncols + row];
-  double y = x * inv_s * 256.0;
+  double y = x * inv_s * 256.0, sc = 1.0;
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
     const double a = rint(y);
-    D[d * slice + idx] = __float2bfloat16_rn((float)a);
+    D[d * slice + idx] = __float2bfloat16_rn((float)(a * sc));  // pre-scaled by 2^-8d, exact
     y = (y - a) * 256.0;
+    sc *= 0x1p-8;
   }
 }
 

@@ -243,22 +243,29 @@ __global__ void __launch_bounds__(128, 1) k_tc_split_gemm(const __grid_constant_
 }
 
 // ----------------------------------------------------------------------------- fixed-point BF16 digits
-// C[q][m][n] = sA * sB[q*Nr+n] * 2^-16 * sum_l 2^-8l L_l,   L_l = sum_{i+j=l} sum_k dA_i[m][k] dB_j[n][k]
-// where x/s = sum_i d_i 2^-8(i+1) with integer digits |d| <= 128 held exactly in
-// bf16 (A: 3 digits, B: 4 digits, s a power of two >= 2 max|x| of the row).
-// Every digit product is an integer below 2^14, so the level-0 sum over K <= 1024
-// stays below 2^24 and the FP32 tensor-core accumulation is exact; the rounding
-// of levels 1-3 is 2^-8 .. 2^-24 smaller still.  B carries a 4th digit because
-// the mode-rotated g(Re,q) columns decay over Re, and the fixed-point error is
-// relative to the row maximum.  Four TMEM accumulators (levels 0-3, 128
-// columns each), nine bf16 MMAs per K step (i+j <= 3), combined once.
+// C[q][m][n] = sA * sB[q*Nr+n] * 2^-16 * (L0 + L123),
+//   L0   = sum_k a_0[m][k] b_0[n][k],                       a_i = d_i 2^-8i, b_j = e_j 2^-8j
+//   L123 = sum_{1 <= i+j <= 3} sum_k a_i[m][k] b_j[n][k]
+// where x/s = sum_i d_i 2^-8(i+1) with integer digits |d| <= 128 (A: 3 digits, B: 4; s a
+// power of two >= 2 max|x| of the row), each digit stored pre-scaled by 2^-8i, exactly,
+// in bf16.  Level-0 products are integers below 2^14, so L0 over K <= 1024 stays below 2^24
+// and its FP32 tensor-core accumulation is exact; L123 is at most 2^-7 of L0, so its FP32
+// rounding is ~2^-31 of the result.  B carries a 4th digit because the mode-rotated
+// g(Re,q) columns decay over Re and the fixed-point error is relative to the row maximum.
+//
+// Persistent kernel, one CTA (6 warps) per SM: warp 0 issues TMA into a 2-stage ring of
+// 112 KiB stages, warp 1 issues the 9 tcgen05.mma (M=128, N=128, K=16) per K step into one
+// of two TMEM accumulator pairs (L0, L123 at columns b*256 + {0, 128}), warps 2-5 drain the
+// other pair (epilogue of tile i overlaps the MMAs of tile i+1).  Tiles (q, m, n) are taken
+// in steps of gridDim.x with n fastest, so concurrent CTAs share their A tiles in L2.
 namespace tcf {
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 2, NA = 3, NB = 4;   // BK bf16 = 128 B rows
 constexpr int A_BYTES = BM * BK * 2;                              // 16 KiB per digit slice
 constexpr int B_BYTES = BN * BK * 2;                              // 16 KiB
 constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;          // 112 KiB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;     // 225 KiB
-constexpr uint32_t TMEM_COLS = 512;                               // levels at columns 0, 128, 256, 384
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;     // 225 KiB
+constexpr uint32_t TMEM_COLS = 512;                               // 2 buffers x (L0, L123) x 128 columns
+constexpr int THREADS = 192;
 // kind::f16 instruction descriptor: D f32, A/B bf16, K-major, M = 128, N = 128 (K = 16 per MMA)
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
@@ -270,6 +277,9 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
       "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
       : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
 }  // namespace tcf
 
 struct TcMaps7 {
@@ -277,10 +287,11 @@ struct TcMaps7 {
   CUtensorMap b[4];
 };
 
-__global__ void __launch_bounds__(128, 1) k_tc_fixed_gemm(const __grid_constant__ TcMaps7 maps, int M, int a_row0,
-                                                          int Nr, int Kp, float sA, const float* __restrict__ sB,
-                                                          float* __restrict__ C, long ldc, long sC,
-                                                          int* __restrict__ err) {
+__global__ void __launch_bounds__(tcf::THREADS, 1) k_tc_fixed_gemm(const __grid_constant__ TcMaps7 maps, int M, int a_row0,
+                                                                  int Nr, int Kp, int nq, float sA,
+                                                                  const float* __restrict__ sB,
+                                                                  float* __restrict__ C, long ldc, long sC,
+                                                                  int* __restrict__ err) {
   using namespace tc;
   using tcf::BM;
   using tcf::BN;
@@ -292,20 +303,25 @@ __global__ void __launch_bounds__(128, 1) k_tc_fixed_gemm(const __grid_constant_
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * tcf::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* accf = empty + STAGES;   // [2] accumulator pair b holds a finished tile
+  uint64_t* acce = accf + 2;         // [2] accumulator pair b has been drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, q = blockIdx.z;
   const int nkb = Kp / BK;
+  const int ntn = (Nr + BN - 1) / BN, ntm = (M + BM - 1) / BM;
+  const long ntiles = (long)ntn * ntm * nq;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);  // one arrival per epilogue warp
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -321,97 +337,119 @@ __global__ void __launch_bounds__(128, 1) k_tc_fixed_gemm(const __grid_constant_
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // stage layout: A digits 0..2 then B digits 0..3, 16 KiB each
   auto tile = [&](int s, int which) -> unsigned char* { return smem + s * tcf::STAGE_BYTES + which * tcf::A_BYTES; };
 
-  int issued = 0;
-  int mma_ok = 1;
-  if (warp == 0 && lane == 0) {
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
-        *abort_flag = 1;
-        atomicOr(err, 1);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {  // ---- TMA producer
+      long it = 0;
+      for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        const int q = (int)(t / ((long)ntm * ntn));
+        const int rem = (int)(t - (long)q * ntm * ntn);
+        const int m0 = (rem / ntn) * BM, n0 = (rem % ntn) * BN;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1))) {
+            *abort_flag = 1;
+            atomicOr(err, 1);
+            break;
+          }
+          if (*abort_flag) break;
+          mbar_arrive_expect_tx(&full[s], tcf::STAGE_BYTES);
+#pragma unroll
+          for (int d = 0; d < NA; ++d) tma_load_2d(tile(s, d), &maps.a[d], kb * BK, a_row0 + m0, &full[s]);
+#pragma unroll
+          for (int d = 0; d < NB; ++d) tma_load_2d(tile(s, NA + d), &maps.b[d], kb * BK, q * Nr + n0, &full[s]);
+        }
       }
-      if (*abort_flag) break;
-      mbar_arrive_expect_tx(&full[s], tcf::STAGE_BYTES);
-#pragma unroll
-      for (int d = 0; d < NA; ++d) tma_load_2d(tile(s, d), &maps.a[d], kb * BK, a_row0 + m0, &full[s]);
-#pragma unroll
-      for (int d = 0; d < NB; ++d) tma_load_2d(tile(s, NA + d), &maps.b[d], kb * BK, q * Nr + n0, &full[s]);
-      ++issued;
+      // after an abort: wait (bounded) for the loads still in flight
+      if (*abort_flag)
+        for (long j = (it > STAGES ? it - STAGES : 0); j < it; ++j) mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
     }
-  } else if (warp == 1 && lane == 0) {
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      if (*abort_flag || !mbar_wait(&full[s], (kb / STAGES) & 1)) {
-        *abort_flag = 1;
-        atomicOr(err, 2);
-        mma_ok = 0;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      long it = 0, lt = 0;
+      for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++lt) {
+        const int b = (int)(lt & 1);
+        if (lt >= 2 && !mbar_wait(&acce[b], (uint32_t)(((lt / 2) - 1) & 1))) {
+          *abort_flag = 1;
+          atomicOr(err, 8);
+          break;
+        }
+        fence_after();
+        const uint32_t d0 = tmem + (uint32_t)(b * 256), d1 = d0 + 128;
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (*abort_flag || !mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1))) {
+            *abort_flag = 1;
+            atomicOr(err, 2);
+            ok = false;
+            break;
+          }
+          fence_after();
+          uint64_t da[NA], db[NB];
+#pragma unroll
+          for (int d = 0; d < NA; ++d) da[d] = smem_desc(smem_u32(tile(s, d)));
+#pragma unroll
+          for (int d = 0; d < NB; ++d) db[d] = smem_desc(smem_u32(tile(s, NA + d)));
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K inside the swizzle atom
+            const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+            tcf::mma_bf16(d0, da[0] + o, db[0] + o, first);  // level 0 (exact)
+            tcf::mma_bf16(d1, da[0] + o, db[1] + o, first);  // levels 1-3 (pre-scaled digits)
+            tcf::mma_bf16(d1, da[1] + o, db[0] + o, 1u);
+            tcf::mma_bf16(d1, da[0] + o, db[2] + o, 1u);
+            tcf::mma_bf16(d1, da[1] + o, db[1] + o, 1u);
+            tcf::mma_bf16(d1, da[2] + o, db[0] + o, 1u);
+            tcf::mma_bf16(d1, da[0] + o, db[3] + o, 1u);
+            tcf::mma_bf16(d1, da[1] + o, db[2] + o, 1u);
+            tcf::mma_bf16(d1, da[2] + o, db[1] + o, 1u);
+          }
+          mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+        }
+        mma_commit(&accf[b]);  // the tile's accumulators are complete (or the loop was aborted)
+        if (!ok) break;
+      }
+    }
+    __syncwarp();
+  } else {  // ---- epilogue, warps 2..5: TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    long lt = 0;
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const int b = (int)(lt & 1);
+      const bool ok = mbar_wait(&accf[b], (uint32_t)((lt / 2) & 1));
+      if (!ok || *abort_flag) {
+        if (!ok) atomicOr(err, 4);
         break;
       }
       fence_after();
-      uint64_t da[NA], db[NB];
-#pragma unroll
-      for (int d = 0; d < NA; ++d) da[d] = smem_desc(smem_u32(tile(s, d)));
-#pragma unroll
-      for (int d = 0; d < NB; ++d) db[d] = smem_desc(smem_u32(tile(s, NA + d)));
-#pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K inside the swizzle atom
-        const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
-        tcf::mma_bf16(tmem + 0, da[0] + o, db[0] + o, first);     // level 0: d0 d0
-        tcf::mma_bf16(tmem + 128, da[0] + o, db[1] + o, first);   // level 1: d0 d1 + d1 d0
-        tcf::mma_bf16(tmem + 128, da[1] + o, db[0] + o, 1u);
-        tcf::mma_bf16(tmem + 256, da[0] + o, db[2] + o, first);   // level 2: d0 d2 + d1 d1 + d2 d0
-        tcf::mma_bf16(tmem + 256, da[1] + o, db[1] + o, 1u);
-        tcf::mma_bf16(tmem + 256, da[2] + o, db[0] + o, 1u);
-        tcf::mma_bf16(tmem + 384, da[0] + o, db[3] + o, first);   // level 3: d0 d3 + d1 d2 + d2 d1
-        tcf::mma_bf16(tmem + 384, da[1] + o, db[2] + o, 1u);
-        tcf::mma_bf16(tmem + 384, da[2] + o, db[1] + o, 1u);
-      }
-      mma_commit(&empty[s]);
-    }
-    mma_commit(done);
-  }
-  __syncwarp();
-
-  const bool ok = mbar_wait(done, 0);
-  if (!ok) atomicOr(err, 4);
-  fence_after();
-  if (ok && mma_ok && !*abort_flag) {
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    float* crow = C + (long)q * sC + (long)row * ldc;
-    const float* srow = sB + (long)q * Nr;
+      const int q = (int)(t / ((long)ntm * ntn));
+      const int rem = (int)(t - (long)q * ntm * ntn);
+      const int m0 = (rem / ntn) * BM, n0 = (rem % ntn) * BN;
+      const int row = m0 + quarter * 32 + lane;
+      const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+      float* crow = C + (long)q * sC + (long)row * ldc;
+      const float* srow = sB + (long)q * Nr;
+      const float sc = sA * 0x1p-16f;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t r0[16], r1[16], r2[16], r3[16];
-      tmem_ld16(tl + c0, r0);
-      tmem_ld16(tl + 128 + c0, r1);
-      tmem_ld16(tl + 256 + c0, r2);
-      tmem_ld16(tl + 384 + c0, r3);
-      tmem_ld_wait();
-      if (row < M) {
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r0[16], r1[16];
+        tmem_ld16(tl + c0, r0);
+        tmem_ld16(tl + 128 + c0, r1);
+        tmem_ld_wait();
+        if (row < M) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int col = n0 + c0 + i;
-          if (col < Nr) {
-            const float v =
-                fmaf(fmaf(fmaf(__uint_as_float(r3[i]), 0x1p-8f, __uint_as_float(r2[i])), 0x1p-8f,
-                          __uint_as_float(r1[i])),
-                     0x1p-8f, __uint_as_float(r0[i]));
-            crow[col] = v * (sA * srow[col] * 0x1p-16f);
+          for (int i = 0; i < 16; ++i) {
+            const int col = n0 + c0 + i;
+            if (col < Nr) crow[col] = (__uint_as_float(r0[i]) + __uint_as_float(r1[i])) * (sc * srow[col]);
           }
         }
       }
-    }
-  }
-  if (warp == 0 && lane == 0 && *abort_flag) {
-    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
-      const int s = kb % STAGES;
-      mbar_wait(&full[s], (kb / STAGES) & 1);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) tcf::mbar_arrive(&acce[b]);
     }
   }
   fence_before();
@@ -474,12 +512,15 @@ cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M
   if (Kp % tcf::BK != 0 || Kp <= 0 || Kp > 1024) return cudaErrorInvalidValue;  // exact level-0 sums need K <= 1024
   cudaError_t e = cudaFuncSetAttribute(k_tc_fixed_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tcf::SMEM_BYTES);
   if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorInvalidDevice;
   TcMaps7 maps;
   for (int d = 0; d < 3; ++d) maps.a[d] = static_cast<const CUtensorMap*>(maps_a3)[d];
   for (int d = 0; d < 4; ++d) maps.b[d] = static_cast<const CUtensorMap*>(maps_b4)[d];
-  dim3 grid((Nr + tcf::BN - 1) / tcf::BN, (M + tcf::BM - 1) / tcf::BM, nq);
-  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-  k_tc_fixed_gemm<<<grid, 128, tcf::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, sA, sB, C, ldc, sC, err);
+  const long ntiles = (long)((Nr + tcf::BN - 1) / tcf::BN) * ((M + tcf::BM - 1) / tcf::BM) * nq;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  k_tc_fixed_gemm<<<grid, tcf::THREADS, tcf::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err);
   return cudaGetLastError();
 }
 
