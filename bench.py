@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-k", type=int, default=16000)
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-form measurement")
+    ap.add_argument("--no-backward", action="store_true", help="skip the adjoint measurement")
     return ap.parse_args()
 
 
@@ -258,6 +259,43 @@ def time_form(wl, form, args, q_dev, k_dev, rank, world, local, dev, QB):
     return out
 
 
+def time_backward(args):
+    """eph_interp_backward on the differentiation workload (mos2_diff: 48x48 k x 256 q, FP64)."""
+    import numpy as np
+    import torch
+
+    from paper_2603_10295_gb300 import binding, synth
+    wl = synth.make_workload("mos2_diff")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.cuda.current_stream()
+    ctx = binding.Context.from_workload(wl, device_ptrs=True, stream=st)
+    nk, nq, nb = len(wl.kpts), len(wl.qpts), wl.nb
+    k_d = torch.from_numpy(wl.kpts).to(dev)
+    q_d = torch.from_numpy(wl.qpts).to(dev)
+    e_d = torch.empty(nk, nb, dtype=torch.float64, device=dev)
+    ctx.eph_set_k(nk, k_d, e_d)
+    # Fermi weights at 300 K around the median of band 3 (1-based) over the k grid
+    e = e_d.cpu().numpy()
+    mu = float(np.median(e[:, 2]))
+    w_d = torch.from_numpy(1.0 / (np.exp((e - mu) / 0.025852) + 1.0)).to(dev)
+    L = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.empty(wl.g_ReRp.shape, dtype=torch.complex128, device=dev)
+    ctx.eph_interp_backward(nk, k_d, nq, q_d, w_d, 1e-6, L, grad)      # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        ctx.eph_interp_backward(nk, k_d, nq, q_d, w_d, 1e-6, L, grad)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx.close()
+    return {"workload": "mos2_diff: Nb=11 Nm=9 Ne=Np=144, 48x48 k x 256 q, FP64 adjoint (forward recomputed)",
+            "ms_per_call": ms, "g_elements_per_s": nk * nq * wl.nm * nb * nb / (ms * 1e-3),
+            "parity": "vs FP64 CPU adjoint <= 1e-12, central differences <= 1e-6 (tests/test_gpu_adjoint.py)"}
+
+
 def run_libeph(args):
     import numpy as np
     import torch
@@ -370,6 +408,8 @@ def run_libeph(args):
                        "h2d_bytes_per_step": QB * 3 * 8,
                        "d2h_bytes_per_step": g_h.numel() * g_h.element_size() + ekq_h.numel() * 8 + om_h.numel() * 8}
         del g_h
+    if rank == 0 and not args.no_backward:
+        line["backward"] = time_backward(args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_k)
     if rank == 0:

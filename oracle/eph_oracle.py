@@ -118,8 +118,8 @@ def g_req_to_bloch(kpts, Re, we, G1q, V_k, V_kq, u_q) -> np.ndarray:
     nm, ne, nb, _ = G1q.shape
     # sum over Re: Gk[k][ka][m'][n']
     Gk = np.einsum("ke,cemn->kcmn", P, G1q)
-    # band rotation U_{mm',k+q} U*_{nn',k}: V_{k+q}^H Gk V_k
-    Gb = np.einsum("kam,kcab,kbn->kcmn", V_kq.conj(), Gk, V_k)
+    # band rotation U_{mm',k+q} U*_{nn',k}: V_{k+q}^H Gk V_k (two matrix products per (k, ka))
+    Gb = np.matmul(np.matmul(V_kq.conj().transpose(0, 2, 1)[:, None], Gk), V_k[:, None])
     # mode rotation by u_{kappa alpha, nu}(q)
     return np.einsum("cv,kcmn->kvmn", u_q, Gb)
 

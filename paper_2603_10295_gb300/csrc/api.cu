@@ -90,6 +90,9 @@ struct eph_ctx {
   double scaleA = 1.0;  // power of two >= 2 max |w_e|
   DBuf DA, DB, sB;
   CUtensorMap mapDA[3]{}, mapDB[4]{};
+  // shapes beyond the warp kernels (nb or nm > 16): CTA Jacobi work, transposed u, band-rotation temp
+  bool big = false;
+  DBuf jwork, ut, Tbuf;
   long long launches = 0;
   std::string err;
   // per-stage event timing
@@ -148,8 +151,20 @@ T* as(DBuf& b) {
 // The FP64 form polishes to an off-diagonal norm of 1e-17 ||A|| (full FP64 eigenvectors);
 // the mixed form, whose g is bound at 1e-6, to 1e-12 ||A|| (eigenvalues still within
 // 1e-12 ||A|| by Weyl's bound), about one FP64 sweep fewer.
-cudaError_t eig(const eph_ctx* c, const double2* A, long sA, long lda, int n, long batch, double* w, long sw,
+cudaError_t eig(eph_ctx* c, const double2* A, long sA, long lda, int n, long batch, double* w, long sw,
                 double2* V, long sV) {
+  if (n > 16) {  // CTA-per-matrix FP64 Jacobi on a global working copy
+    const size_t need = (size_t)batch * n * n * sizeof(double2);
+    if (c->jwork.n < need) {
+      if (c->jwork.p) cudaFree(c->jwork.p);
+      c->jwork.p = nullptr;
+      c->jwork.n = 0;
+      if (cudaMalloc(&c->jwork.p, need) != cudaSuccess) return cudaErrorMemoryAllocation;
+      c->jwork.n = need;
+    }
+    return eph::launch_jacobi_big(A, sA, lda, n, batch, w, sw, V, sV, static_cast<double2*>(c->jwork.p),
+                                  c->opt.max_sweeps, c->status, c->stream);
+  }
   if (c->opt.eig_plain_fp64)
     return eph::launch_jacobi(A, sA, lda, n, batch, w, sw, V, sV, c->opt.max_sweeps, c->status, c->stream);
   const double tol = c->opt.form == EPH_FORM_MIXED ? 1e-12 : 1e-17;
@@ -278,7 +293,8 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->D, &ctx->lamq, &ctx->evq, &ctx->omq, &ctx->uq, &ctx->G1, &ctx->W, &ctx->Y,
                   &ctx->eps_tile, &ctx->Ukq, &ctx->g_stage, &ctx->wk, &ctx->G2bar, &ctx->G1bar,
                   &ctx->Lpair, &ctx->Lacc, &ctx->grad, &ctx->Ahi, &ctx->Alo, &ctx->Bhi, &ctx->Blo,
-                  &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB};
+                  &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut,
+                  &ctx->Tbuf};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -327,7 +343,14 @@ int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re
     std::frexp(wmax > 0.0 ? wmax : 1.0, &ex);
     ctx->scaleA = std::ldexp(1.0, ex + 1);  // |Re P|, |Im P| <= w_e <= scaleA / 2
   }
-  if (nb > 16 || nm > 16) return bail(EPH_ENOTSUP);
+  // nb, nm <= 16: warp-resident Jacobi and rotations; up to 256: CTA Jacobi and GEMM rotations
+  // (FP64 form, forward only)
+  if (nb > 256 || nm > 256) return bail(EPH_ENOTSUP);
+  ctx->big = nb > 16 || nm > 16 || (size_t)(2 * nb * nb + 2 * nm * nb * nb) * 16 > 200 * 1024;
+  if (ctx->big && ctx->opt.form != EPH_FORM_FP64) {
+    fail(ctx, EPH_ENOTSUP, "nb or nm > 16 is supported by the FP64 form only");
+    return bail(EPH_ENOTSUP);
+  }
   for (int i = 0; i < na; ++i)
     if (!(masses[i] > 0.0)) return bail(EPH_EINVAL);
   if (cuda_stream) {
@@ -490,10 +513,12 @@ QPlan plan_q(const eph_ctx* ctx, int nq, size_t extra_per_pair) {
   if (p.QB > 16) p.QB = 16;
   if (p.QB > nq) p.QB = nq;
   // bytes per (q,k) pair in the k stage
-  const size_t per_pair = (size_t)p.NW * 16 + (size_t)nb2 * 16 + (size_t)ctx->nb * 8 + extra_per_pair;
+  size_t per_pair = (size_t)p.NW * 16 + (size_t)nb2 * 16 + (size_t)ctx->nb * 8 + extra_per_pair;
+  if (ctx->big) per_pair += (size_t)ctx->nm * nb2 * 16 / p.QB + (size_t)nb2 * 16;  // band temp, Jacobi copy
   const size_t budget = (size_t)ctx->opt.workspace_mb << 20;
   long KT = ctx->opt.k_tile > 0 ? ctx->opt.k_tile : (long)(budget / (per_pair * p.QB));
   if (KT > ctx->nk) KT = ctx->nk;
+  if (p.QB * KT > 65535) KT = 65535 / p.QB;  // CTA-per-matrix eigensolve grid
   if (KT > 64) KT -= KT % 64;
   if (KT < 1) KT = 1;
   p.KT = KT;
@@ -539,8 +564,48 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb) {
                                              ctx->stream));
   // W_q = [ e^{i q.Re} H(Re) | mode-rotated G1 ], row e of length NW
   EPH_LAUNCH_S(EPH_STAGE_MODE, launch_scale_rows(Qe, nqb, ctx->H, ne, nb2, W, p.NW, (long)ne * p.NW, ctx->stream));
-  EPH_LAUNCH_S(EPH_STAGE_MODE, launch_mode_rotate(as<double2>(ctx->G1), as<double2>(ctx->uq), nqb, nm, ne, nb2,
-                                                  W + nb2, p.NW, (long)ne * p.NW, ctx->stream));
+  if (nm <= 16) {
+    EPH_LAUNCH_S(EPH_STAGE_MODE, launch_mode_rotate(as<double2>(ctx->G1), as<double2>(ctx->uq), nqb, nm, ne, nb2,
+                                                    W + nb2, p.NW, (long)ne * p.NW, ctx->stream));
+  } else {
+    // G2[e][nu][b] = sum_c u[c][nu] G1[c][e][b]: one GEMM per q, batched over Re (u^T from a transpose)
+    EPH_TRY(ensure(ctx, ctx->ut, (size_t)nqb * nm * nm * sizeof(double2)));
+    EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_transpose(as<double2>(ctx->uq), nm, nqb, as<double2>(ctx->ut), ctx->stream));
+    for (int iq = 0; iq < nqb; ++iq)
+      EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_zgemm_b2(nm, nb2, nm, as<double2>(ctx->ut) + (long)iq * nm * nm, nm, 0, 0,
+                                                        as<double2>(ctx->G1) + (long)iq * p.X, (long)ne * nb2, nb2, 0,
+                                                        W + (long)iq * ne * p.NW + nb2, nb2, p.NW, 0, ne, 1, 0,
+                                                        ctx->stream));
+  }
+  return EPH_OK;
+}
+
+// Band rotation g_nu = V_{k+q}^H G3_nu V_k for one (q batch, k tile): the shared-memory kernel
+// for small shapes, two GEMMs batched over (k, nu) otherwise.
+int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2* out, long sgq) {
+  const int nb = ctx->nb, nm = ctx->nm, nb2 = nb * nb;
+  double2* Y = as<double2>(ctx->Y);
+  const double2* Uk = as<double2>(ctx->Uk) + k0 * nb2;
+  if (!ctx->big) {
+    EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, as<double2>(ctx->Ukq), Uk, nqb, nkt, nm, nb, out,
+                                                    sgq, ctx->stream));
+    return EPH_OK;
+  }
+  double2* T = as<double2>(ctx->Tbuf);
+  const int kc = 65535 / nm;  // batch-size limit of one launch
+  for (int iq = 0; iq < nqb; ++iq)
+    for (int kb = 0; kb < nkt; kb += kc) {
+      const int nkc = nkt - kb < kc ? nkt - kb : kc;
+      // T[k][nu] = G3[q][k][nu] V_k
+      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zgemm_b2(nb, nb, nb, Y + ((long)iq * nkt + kb) * p.NW + nb2, nb, p.NW,
+                                                        nb2, Uk + (long)kb * nb2, nb, nb2, 0, T, nb, (long)nm * nb2,
+                                                        nb2, nkc, nm, 0, ctx->stream));
+      // g[q][k][nu] = V_{k+q}^H T[k][nu]
+      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zgemm_b2(nb, nb, nb, as<double2>(ctx->Ukq) + ((long)iq * nkt + kb) * nb2,
+                                                        nb, nb2, 0, T, nb, (long)nm * nb2, nb2,
+                                                        out + (long)iq * sgq + (long)kb * nm * nb2, nb,
+                                                        (long)nm * nb2, nb2, nkc, nm, 1, ctx->stream));
+    }
   return EPH_OK;
 }
 
@@ -681,6 +746,13 @@ int prepare_fp64(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
   const bool host = !ctx->opt.device_ptrs;
   const QPlan p = plan_q(ctx, nq, host && want_g ? (size_t)ctx->nm * ctx->nb * ctx->nb * 16 : 0);
   EPH_TRY(ensure_q_workspace(ctx, p));
+  if (ctx->big) {
+    const int nb2 = ctx->nb * ctx->nb, nmax = ctx->nb > ctx->nm ? ctx->nb : ctx->nm;
+    EPH_TRY(ensure(ctx, ctx->Tbuf, (size_t)p.KT * ctx->nm * nb2 * sizeof(double2)));
+    EPH_TRY(ensure(ctx, ctx->ut, (size_t)p.QB * ctx->nm * ctx->nm * sizeof(double2)));
+    const size_t jw = (size_t)(p.QB * p.KT > ctx->nk ? p.QB * p.KT : ctx->nk) * nmax * nmax * sizeof(double2);
+    EPH_TRY(ensure(ctx, ctx->jwork, jw));
+  }
   if (host && want_g) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)p.QB * p.KT * p.gcols * sizeof(double2)));
   *out = p;
   return EPH_OK;
@@ -720,18 +792,13 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
       if (g) {
         double2* gout = static_cast<double2*>(g);
         if (host) {
-          EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, as<double2>(ctx->Ukq),
-                                                          as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
-                                                          as<double2>(ctx->g_stage), (long)nkt * p.gcols, ctx->stream));
+          EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0, as<double2>(ctx->g_stage), (long)nkt * p.gcols));
           for (int iq = 0; iq < nqb; ++iq)
             EPH_CK(cudaMemcpyAsync(gout + ((long)(q0 + iq) * nk + k0) * p.gcols,
                                    as<double2>(ctx->g_stage) + (long)iq * nkt * p.gcols,
                                    (size_t)nkt * p.gcols * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
         } else {
-          EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, as<double2>(ctx->Ukq),
-                                                          as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
-                                                          gout + ((long)q0 * nk + k0) * p.gcols, (long)nk * p.gcols,
-                                                          ctx->stream));
+          EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0, gout + ((long)q0 * nk + k0) * p.gcols, (long)nk * p.gcols));
         }
       }
     }
@@ -751,6 +818,7 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
   if (!ctx) return EPH_EINVAL;
   if (nk < 1 || nq < 1 || !kpts || !qpts || !w_nk || !L_out || !grad_g_ReRp)
     return fail(ctx, EPH_EINVAL, "eph_interp_backward: bad size or NULL pointer");
+  if (ctx->big) return fail(ctx, EPH_ENOTSUP, "eph_interp_backward supports nb, nm <= 16");
   EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
   const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, np = ctx->np;
   const int nb2 = nb * nb;

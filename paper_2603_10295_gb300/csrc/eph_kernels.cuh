@@ -25,6 +25,12 @@ cudaError_t launch_scale_rows(const double2* Q, int nq, const double2* H, int ne
 cudaError_t launch_zgemm(int M, int N, int K, const double2* A, long lda, long sA,
                          const double2* B, long ldb, long sB, double2* C, long ldc, long sC,
                          int batch, cudaStream_t st);
+// Two-level batch: z = b1 * nbat2 + b2, operand offsets b1*s + b2*s2; adj: op(A) = A^H (A stored K x M).
+cudaError_t launch_zgemm_b2(int M, int N, int K, const double2* A, long lda, long sA, long sA2, const double2* B,
+                            long ldb, long sB, long sB2, double2* C, long ldc, long sC, long sC2, int nbat1,
+                            int nbat2, int adj, cudaStream_t st);
+// out[b][j][i] = in[b][i][j] for a batch of n x n complex matrices.
+cudaError_t launch_transpose(const double2* in, int n, long batch, double2* out, cudaStream_t st);
 // Same product on the FP32 pipe in double-float arithmetic (~1e-13 relative), FP64 in/out.
 cudaError_t launch_zgemm_df(int M, int N, int K, const double2* A, long lda, long sA, const double2* B, long ldb,
                             long sB, double2* C, long ldc, long sC, int batch, cudaStream_t st);
@@ -52,6 +58,11 @@ cudaError_t launch_jacobi(const double2* A, long sA, long lda, int n, long batch
 cudaError_t launch_jacobi_mixed(const double2* A, long sA, long lda, int n, long batch, double* w, long sw,
                                 double2* V, long sV, int max_sweeps, double polish_tol, int* status,
                                 cudaStream_t st);
+
+// 16 < n <= 256: one CTA per matrix, FP64 parallel Jacobi on a global working copy
+// work [batch][n][n]; V must be packed (sV = n*n).
+cudaError_t launch_jacobi_big(const double2* A, long sA, long lda, int n, long batch, double* w, long sw, double2* V,
+                              long sV, double2* work, int max_sweeps, int* status, cudaStream_t st);
 
 // ---- phonon post-processing: omega = sign(l) sqrt|l| * unit; u = e / sqrt(M)
 cudaError_t launch_phonon_post(const double* lam, const double2* e, int nq, int nm, const double* invsqrtm,

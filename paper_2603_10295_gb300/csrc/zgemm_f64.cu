@@ -27,19 +27,21 @@ __device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
 // sums s_a = a_r + a_i and s_b = b_r + b_i staged once per shared-memory tile,
 //   t1 += a_r b_r,  t2 += a_i b_i,  t3 += s_a s_b,   C = (t1 - t2) + i (t3 - t1 - t2),
 // i.e. three DFMA per complex multiply-add instead of four.
+// Batch index z = b1 * nbat2 + b2 with operand offsets b1 s*1 + b2 s*2 (nbat2 = 1: plain batch).
 template <bool ADJ, bool ACC>
 __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, const double2* __restrict__ A, long lda,
                                                long sA, const double2* __restrict__ B, long ldb, long sB,
-                                               double2* __restrict__ C, long ldc, long sC) {
+                                               double2* __restrict__ C, long ldc, long sC, int nbat2, long sA2,
+                                               long sB2, long sC2) {
   __shared__ double3 As[BK][BM];  // (re, im, re + im)
   __shared__ double3 Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const long b = blockIdx.z;
-  A += b * sA;
-  B += b * sB;
-  C += b * sC;
+  const long b1 = blockIdx.z / nbat2, b2 = blockIdx.z - b1 * nbat2;
+  A += b1 * sA + b2 * sA2;
+  B += b1 * sB + b2 * sB2;
+  C += b1 * sC + b2 * sC2;
   double t1[4][4], t2[4][4], t3[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -120,7 +122,21 @@ cudaError_t launch_zgemm(int M, int N, int K, const double2* A, long lda, long s
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   if (!grid_ok(M, N, batch)) return cudaErrorInvalidConfiguration;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
-  k_zgemm<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+  k_zgemm<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zgemm_b2(int M, int N, int K, const double2* A, long lda, long sA, long sA2, const double2* B,
+                            long ldb, long sB, long sB2, double2* C, long ldc, long sC, long sC2, int nbat1,
+                            int nbat2, int adj, cudaStream_t st) {
+  const long batch = (long)nbat1 * nbat2;
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535 || !grid_ok(M, N, 1)) return cudaErrorInvalidConfiguration;
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, (unsigned)batch);
+  if (adj)
+    k_zgemm<true, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nbat2, sA2, sB2, sC2);
+  else
+    k_zgemm<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nbat2, sA2, sB2, sC2);
   return cudaGetLastError();
 }
 
@@ -130,9 +146,9 @@ cudaError_t launch_zgemm_ah(int M, int N, int K, const double2* A, long lda, lon
   if (!grid_ok(M, N, batch)) return cudaErrorInvalidConfiguration;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
   if (acc)
-    k_zgemm<true, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+    k_zgemm<true, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0);
   else
-    k_zgemm<true, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+    k_zgemm<true, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0);
   return cudaGetLastError();
 }
 
@@ -213,6 +229,23 @@ cudaError_t launch_skinny(int M, long N, int K, const double2* P, long ldp, cons
 cudaError_t launch_skinny_real(int M, long N, int K, const double2* P, long ldp, const double* B, long ldb,
                                const double* colscale, double2* C, long ldc, cudaStream_t st) {
   return skinny_dispatch<true>(M, N, K, P, ldp, B, ldb, colscale, C, ldc, st);
+}
+
+// Plain transpose of a batch of square matrices: out[b][j][i] = in[b][i][j].
+__global__ void k_transpose(const double2* __restrict__ in, int n, long batch, double2* __restrict__ out) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long nn = (long)n * n;
+  if (idx >= nn * batch) return;
+  const long b = idx / nn;
+  const int r = (int)((idx - b * nn) / n), c = (int)(idx - b * nn - (long)r * n);
+  out[b * nn + (long)c * n + r] = in[idx];
+}
+
+cudaError_t launch_transpose(const double2* in, int n, long batch, double2* out, cudaStream_t st) {
+  const long tot = (long)n * n * batch;
+  if (tot <= 0) return cudaSuccess;
+  k_transpose<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, n, batch, out);
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------

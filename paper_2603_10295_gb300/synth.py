@@ -215,13 +215,15 @@ def _lattice(spec):
 
 
 def make_workload(name: str, seed: int = 0, nq: int | None = None, nk: int | None = None,
-                  nb: int | None = None, box=None, with_coupling: bool = True) -> Workload:
-    """Build a named workload.  nq/nk/nb/box override the config (smaller cases for tests)."""
+                  nb: int | None = None, box=None, with_coupling: bool = True, na: int | None = None) -> Workload:
+    """Build a named workload.  nq/nk/nb/na/box override the config (smaller cases for tests)."""
     cfg = dict(CONFIGS[name])
     rng = np.random.default_rng(seed)
     lat = _lattice(cfg["lattice"])
     nb = cfg["nb"] if nb is None else nb
     masses = np.asarray(cfg["masses"], dtype=np.float64)
+    if na is not None:
+        masses = np.resize(masses, na)
     na = len(masses)
     R = box_vectors(*(box if box is not None else cfg["box"]))
     lamH, lamP, lamG = cfg["lam"]

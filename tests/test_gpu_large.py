@@ -1,0 +1,69 @@
+"""Shapes beyond the warp-resident kernels (nb or nm > 16): CTA-per-matrix
+Jacobi, GEMM-based mode and band rotations (FP64 form).  The main case is the
+narrowest zigzag-stanene ribbon of the paper's Table 3 (Nb=32, Nm=54) on the
+15-vector 1-D box of the stanene workload."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_10295_gb300 import binding, build_lib, synth
+from tests import gauge
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not os.path.exists(binding.LIB_PATH):
+        build_lib.build()
+    return binding.load_library()
+
+
+def check(gpu, ref, what):
+    e_k, e_kq, om, g = gpu
+    r_k, r_kq, r_om, r_g = ref
+    errs = dict(eps_k=gauge.max_rel_eps(e_k, r_k), eps_kq=gauge.max_rel_eps(e_kq, r_kq),
+                omega=gauge.max_rel_omega(om, r_om), S=gauge.max_rel_S(g, r_g, r_k, r_kq, r_om))
+    print(what, errs)
+    for k, v in errs.items():
+        assert v <= TOL_FP64, (what, errs)
+
+
+def test_zsnr_narrowest_ribbon_shape():
+    wl = synth.make_workload("stanene", nb=32, na=18, nk=6, nq=3)
+    assert (wl.nb, wl.nm, wl.ne) == (32, 54, 15)
+    ctx = binding.Context.from_workload(wl, q_batch=2, k_tile=4)
+    check(ctx.interp(wl.kpts, wl.qpts), oracle.interpolate(wl), "zsnr 32/54")
+
+
+@pytest.mark.parametrize("nb,na", [(20, 2), (8, 7)])
+def test_mixed_small_and_large(nb, na):
+    # large bands with small modes, and small bands with large modes
+    wl = synth.make_workload("si_tiny", nb=nb, na=na, nk=9, nq=4)
+    ctx = binding.Context.from_workload(wl, q_batch=3)
+    check(ctx.interp(wl.kpts, wl.qpts), oracle.interpolate(wl), f"nb={nb} nm={3 * na}")
+
+
+def test_large_shapes_rejected_where_not_supported():
+    wl = synth.make_workload("si_tiny", nb=20, nk=4, nq=2)
+    with pytest.raises(binding.EphError) as ei:
+        binding.Context.from_workload(wl, form="mixed")
+    assert ei.value.code == binding.EPH_ENOTSUP
+    ctx = binding.Context.from_workload(wl)
+    with pytest.raises(binding.EphError) as ei:
+        ctx.loss_and_grad(wl.kpts, wl.qpts, np.ones((len(wl.kpts), wl.nb)), 1e-6)
+    assert ei.value.code == binding.EPH_ENOTSUP
+
+
+def test_stanene_full_shape_few_points():
+    # the stanene-nanoribbon workload's full shapes: Nb=120, Na=60 (Nm=180), Ne=Np=15,
+    # g(Re,Rp) 9.33 GB; two k and one q point keep the FP64 oracle affordable
+    wl = synth.make_workload("stanene", nk=2, nq=1)
+    assert (wl.nb, wl.nm, wl.ne) == (120, 180, 15)
+    ctx = binding.Context.from_workload(wl)
+    gpu = ctx.interp(wl.kpts, wl.qpts)
+    check(gpu, oracle.interpolate(wl), "stanene 120/180")
