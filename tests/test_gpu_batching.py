@@ -1,6 +1,6 @@
-"""Batching: two materials of different shape (silicon-like Nb=8/Nm=6 and
-MoS2-like Nb=11/Nm=9) with uneven q batches, in both forms, captured into one
-CUDA graph; replays must reproduce the eager results exactly, also after new q
+"""Batching: materials of different shape (silicon-like Nb=8/Nm=6, MoS2-like
+Nb=11/Nm=9 and, in the FP64 form, a stanene-family ribbon Nb=32/Nm=54) with
+uneven q batches, in both forms, captured into one CUDA graph; replays must reproduce the eager results exactly, also after new q
 points are copied into the captured inputs.  The autotuner must pick a valid
 decomposition that leaves the results unchanged."""
 import os
@@ -22,11 +22,15 @@ def lib():
     return binding.load_library()
 
 
-def _materials():
+def _materials(form):
     si = synth.make_workload("si_tiny", nk=150, nq=40)
     box = (synth.centred_range(6), synth.centred_range(6), range(0, 1))
     mo = synth.make_workload("mos2", nk=120, nq=40, box=box)
-    return [(si, [3, 5, 1]), (mo, [2, 7])]
+    mats = [(si, [3, 5, 1]), (mo, [2, 7])]
+    if form == "fp64":
+        # a stanene-family ribbon (Table 3's narrowest: Nb=32, Nm=54) on the 15-vector 1-D box
+        mats.append((synth.make_workload("stanene", nb=32, na=18, nk=10, nq=40), [1, 2]))
+    return mats
 
 
 def _buffers(torch, wl, nq, form, dev):
@@ -43,7 +47,7 @@ def test_graph_replay_matches_eager(form):
     dev = torch.device("cuda:0")
     gb = GraphBatcher(dev)
     eager, keep = [], []
-    for wl, batches in _materials():
+    for wl, batches in _materials(form):
         ctx = binding.Context.from_workload(wl, form=form, device_ptrs=True, async_mode=True, stream=gb.stream)
         ctx.eph_set_k(len(wl.kpts), torch.from_numpy(wl.kpts).to(dev))
         ref_ctx = binding.Context.from_workload(wl, form=form)
