@@ -383,8 +383,7 @@ def run_libeph(args):
                              "clocks": m["clocks"]}
 
     # end to end through the public C-ABI with HOST buffers (pinned), copies inside the timed region
-    if rank == 0 and not args.no_e2e:
-        form = forms[0]
+    def e2e(form):
         gdt = torch.complex128 if form == "fp64" else torch.complex64
         hctx = binding.Context.from_workload(wl, form=form, device_ptrs=False, q_batch=QB)
         kp_h = torch.from_numpy(wl.kpts).pin_memory()
@@ -404,10 +403,16 @@ def run_libeph(args):
         t_e2e = time.perf_counter() - t0
         hctx.close()
         e2e_units = args.steps * QB * nk * nm * nb * nb
-        line["e2e"] = {"value": e2e_units / (t_e2e + t_setk * (args.steps * QB) / len(wl.qpts)), "unit": UNIT,
-                       "h2d_bytes_per_step": QB * 3 * 8,
-                       "d2h_bytes_per_step": g_h.numel() * g_h.element_size() + ekq_h.numel() * 8 + om_h.numel() * 8}
+        out = {"value": e2e_units / (t_e2e + t_setk * (args.steps * QB) / len(wl.qpts)), "unit": UNIT,
+               "h2d_bytes_per_step": QB * 3 * 8,
+               "d2h_bytes_per_step": g_h.numel() * g_h.element_size() + ekq_h.numel() * 8 + om_h.numel() * 8}
         del g_h
+        return out
+
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e(forms[0])
+        if "mixed" in line:
+            line["mixed"]["e2e"] = e2e("mixed")
     if rank == 0 and not args.no_backward:
         line["backward"] = time_backward(args)
     if rank == 0 and not args.no_cpu_baseline:

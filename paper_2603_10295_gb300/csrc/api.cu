@@ -35,7 +35,6 @@ using eph::launch_sum_into;
 using eph::launch_zgemm;
 using eph::launch_zgemm_ah;
 using eph::launch_zgemm_df;
-using eph::launch_band_rotate_f32;
 using eph::launch_band_rotate_ff;
 using eph::launch_digits_a;
 using eph::launch_digits_b;

@@ -104,8 +104,6 @@ cudaError_t launch_split_a(const double2* P, long ldp, int n, int ne, int kp, fl
                            cudaStream_t st);
 cudaError_t launch_split_b(const double2* W, long ldw, long sW, int col0, int ncols, int ne, int kp, int nq,
                            float* Bhi, float* Blo, cudaStream_t st);
-cudaError_t launch_band_rotate_f32(const float* Y, long ldy_floats, const double2* Ukq, const double2* Uk, int nq,
-                                   int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st);
 // Band rotation with double-float accumulation (FP64 gauges as float pairs), complex64 out.
 cudaError_t launch_band_rotate_ff(const float* Y, long ldy_floats, const double2* Ukq, const double2* Uk, int nq,
                                   int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st);

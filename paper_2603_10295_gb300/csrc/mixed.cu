@@ -81,69 +81,6 @@ cudaError_t launch_split_b(const double2* W, long ldw, long sW, int col0, int nc
   return cudaGetLastError();
 }
 
-// FP32 band rotation: g[q][k][nu] = V_{k+q}^H G3[q][k][nu] V_k with G3 complex64 rows of
-// nm*nb*nb (row stride ldy floats pairs), V in FP64 (rounded to FP32), g complex64.
-__global__ void __launch_bounds__(128) k_band_rotate_f32(const float2* __restrict__ Y, long ldy,
-                                                         const double2* __restrict__ Ukq,
-                                                         const double2* __restrict__ Uk, int nk, int nm, int nb,
-                                                         float2* __restrict__ g, long sgq) {
-  extern __shared__ float2 smf[];
-  const int nb2 = nb * nb;
-  float2* uk = smf;
-  float2* ukq = uk + nb2;
-  float2* G = ukq + nb2;
-  float2* T = G + nm * nb2;
-  const long pair = blockIdx.x;
-  const int k = (int)(pair % nk);
-  const long q = pair / nk;
-  for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
-    const double2 a = Uk[(long)k * nb2 + t], b = Ukq[pair * nb2 + t];
-    uk[t] = make_float2((float)a.x, (float)a.y);
-    ukq[t] = make_float2((float)b.x, (float)b.y);
-  }
-  const float2* grow = Y + pair * ldy;
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) G[t] = grow[t];
-  __syncthreads();
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
-    const int nu = t / nb2, rem = t - nu * nb2, a = rem / nb, n = rem - a * nb;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int b = 0; b < nb; ++b) {
-      const float2 x = G[nu * nb2 + a * nb + b], y = uk[b * nb + n];
-      acc.x = fmaf(x.x, y.x, fmaf(-x.y, y.y, acc.x));
-      acc.y = fmaf(x.x, y.y, fmaf(x.y, y.x, acc.y));
-    }
-    T[t] = acc;
-  }
-  __syncthreads();
-  float2* out = g + q * sgq + (long)k * nm * nb2;
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
-    const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, n = rem - m * nb;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int a = 0; a < nb; ++a) {
-      const float2 x = ukq[a * nb + m], y = T[nu * nb2 + a * nb + n];
-      acc.x = fmaf(x.x, y.x, fmaf(x.y, y.y, acc.x));
-      acc.y = fmaf(x.x, y.y, fmaf(-x.y, y.x, acc.y));
-    }
-    out[t] = acc;
-  }
-}
-
-cudaError_t launch_band_rotate_f32(const float* Y, long ldy_floats, const double2* Ukq, const double2* Uk, int nq,
-                                   int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st) {
-  const long pairs = (long)nq * nk;
-  if (pairs <= 0) return cudaSuccess;
-  const size_t smem = (size_t)(2 * nb * nb + 2 * nm * nb * nb) * sizeof(float2);
-  if (smem > 200 * 1024 || (ldy_floats & 1) || (sgq_floats & 1)) return cudaErrorInvalidValue;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_band_rotate_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
-  k_band_rotate_f32<<<(unsigned)pairs, 128, smem, st>>>(reinterpret_cast<const float2*>(Y), ldy_floats / 2, Ukq, Uk,
-                                                         nk, nm, nb, reinterpret_cast<float2*>(g), sgq_floats / 2);
-  return cudaGetLastError();
-}
-
 // ---- fixed-point BF16 digits (exact tensor-core accumulation) ------------------------
 // x/s = sum_i d_i 2^-8(i+1) + O(2^-8n-1), integer digits |d| <= 128, digit i stored as
 // d_i 2^-8i (exact in bf16); s is a power of two with |x| <= s/2 for every x of the row
