@@ -226,7 +226,8 @@ __global__ void __launch_bounds__(128) k_jacobi(const double2* __restrict__ A, l
 
 // FP32-preconditioned variant: the same sweeps first run in FP32 (64x the FP64
 // rate on GB300) to an off-diagonal norm of ~1e-6 ||A||; V is then made unitary
-// to rounding level with two FP64 Newton-Schulz steps V <- V (3I - V^H V)/2, the FP64
+// to rounding level with two FP64 Newton-Schulz steps V <- V (3I - V^H V)/2 (one step,
+// non-unitarity ~4e-13, when polishing to 1e-12), the FP64
 // matrix is rotated, A' = V^H A V (off-diagonal ~1e-7 ||A||), and FP64 sweeps
 // finish it (quadratic convergence) to an off-diagonal norm below
 // polish_tol ||A||_F: 1e-17 (about two sweeps) gives the FP64 eigendecomposition;
@@ -284,11 +285,12 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
 #pragma unroll
     for (int r = 0; r < NP; ++r) v[r] = make_double2((double)vf[r].x, (double)vf[r].y);
   }
-  // ---- FP64: two Newton-Schulz steps, v_j' = 1.5 v_j - 0.5 sum_i v_i (v_i^H v_j)
-  // (non-unitarity 5e-7 -> 4e-13 -> rounding level)
+  // ---- FP64 Newton-Schulz steps, v_j' = 1.5 v_j - 0.5 sum_i v_i (v_i^H v_j)
+  // (non-unitarity 5e-7 -> 4e-13 -> rounding level); one step when polishing to 1e-12
   double2 vn[NP];
+  const int ns_steps = polish_tol >= 1e-13 ? 1 : 2;
 #pragma unroll 1
-  for (int it = 0; it < 2; ++it) {
+  for (int it = 0; it < ns_steps; ++it) {
 #pragma unroll
     for (int r = 0; r < NP; ++r) vn[r] = make_double2(1.5 * v[r].x, 1.5 * v[r].y);
 #pragma unroll

@@ -278,7 +278,7 @@ __device__ __forceinline__ void dfmac(float& sh, float& sl, float ah, float al, 
 }
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_zgemm_df(int M, int N, int K, const double2* __restrict__ A, long lda,
+__global__ void __launch_bounds__(256, 2) k_zgemm_df(int M, int N, int K, const double2* __restrict__ A, long lda,
                                                   long sA, const double2* __restrict__ B, long ldb, long sB,
                                                   double2* __restrict__ C, long ldc, long sC) {
   __shared__ float4 As[BK][BM];

