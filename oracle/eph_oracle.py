@@ -241,3 +241,39 @@ def fermi_weights(eps_k, band_index, kT=0.025852):
     """w_nk = 1/(exp((eps-mu)/kT)+1) with mu the median of band `band_index` over the k grid."""
     mu = float(np.median(eps_k[:, band_index]))
     return 1.0 / (np.exp((eps_k - mu) / kT) + 1.0), mu
+
+
+# ----------------------------------------------------------------------------
+# Downstream consumer: electron linewidths (imaginary part of the Fan-Migdal self-energy).
+# ----------------------------------------------------------------------------
+def bose(omega, kT):
+    """n_B(omega) = 1 / (exp(omega/kT) - 1)."""
+    return 1.0 / np.expm1(omega / kT)
+
+
+def fermi(eps, mu, kT):
+    """f(eps) = 1 / (exp((eps - mu)/kT) + 1)."""
+    return 1.0 / (np.exp((eps - mu) / kT) + 1.0)
+
+
+def gaussian(x, sigma):
+    return np.exp(-0.5 * (x / sigma) ** 2) / (sigma * np.sqrt(2.0 * np.pi))
+
+
+def linewidths(eps_k, eps_kq, omega, g, wq, kT, mu, sigma, omega_min):
+    """Gamma_nk = pi sum_q w_q sum_{m, nu: omega > omega_min} |g_mnnu(k,q)|^2 / (2 omega_qnu)
+         x [ (n_qnu + f_{m,k+q}) delta(eps_nk - eps_{m,k+q} + omega_qnu)
+           + (n_qnu + 1 - f_{m,k+q}) delta(eps_nk - eps_{m,k+q} - omega_qnu) ]
+    with Gaussian delta of width sigma (phonon absorption and emission terms of the
+    imaginary part of the Fan-Migdal self-energy).  Returns [nk][nb] in units of |g|^2/eV^2.
+    eps_k [nk][nb], eps_kq [nq][nk][nb], omega [nq][nm], g [nq][nk][nm][nb][nb], wq [nq].
+    """
+    om = np.asarray(omega)[:, None, :, None, None]                 # q, -, nu, -, -
+    ok = om > omega_min
+    oms = np.where(ok, om, 1.0)
+    nB = np.where(ok, bose(oms, kT), 0.0)
+    fm = fermi(np.asarray(eps_kq), mu, kT)[:, :, None, :, None]      # q, k, -, m, -
+    de = np.asarray(eps_k)[None, :, None, None, :] - np.asarray(eps_kq)[:, :, None, :, None]   # eps_nk - eps_mk+q
+    term = (nB + fm) * gaussian(de + oms, sigma) + (nB + 1.0 - fm) * gaussian(de - oms, sigma)
+    contrib = np.where(ok, np.abs(g) ** 2 / (2.0 * oms) * term, 0.0)  # [q][k][nu][m][n]
+    return np.pi * np.einsum("q,qkvmn->kn", np.asarray(wq, dtype=np.float64), contrib)

@@ -246,3 +246,27 @@ def test_table3_sizes_and_cost_ratio():
     sl = (nb * nb * nm * ne * np_ + nb * nb * nm * ne + 2 * nb * nb * nm + nb * nb * nm * nm) * nk
     nl = nb * nb * nm * ne * np_ + (nb * nb * nm * ne + 2 * nb * nb * nm + nb * nb * nm * nm) * nk
     assert abs(sl / nl - 93) < 1.0
+
+
+# ---------------------------------------------------------------- linewidth consumer
+def test_linewidths_closed_form_and_properties():
+    # one band, one mode, constant coupling: Gamma is pi |g|^2/(2w) times the two
+    # Gaussian-weighted occupation terms, written out by hand here
+    kT, mu, sig, w, g0 = 0.025852, 0.1, 0.02, 0.05, 0.3 + 0.4j
+    eps_k = np.array([[0.17]])
+    eps_kq = np.array([[[0.13]]])
+    omega = np.array([[w]])
+    g = np.full((1, 1, 1, 1, 1), g0)
+    nB = 1.0 / (np.exp(w / kT) - 1.0)
+    f = 1.0 / (np.exp((0.13 - mu) / kT) + 1.0)
+    gau = lambda x: np.exp(-x * x / (2 * sig * sig)) / (sig * np.sqrt(2 * np.pi))
+    expect = np.pi * abs(g0) ** 2 / (2 * w) * ((nB + f) * gau(0.04 + w) + (nB + 1 - f) * gau(0.04 - w))
+    got = oracle.linewidths(eps_k, eps_kq, omega, g, [1.0], kT, mu, sig, 1e-6)
+    assert abs(got[0, 0] - expect) < 1e-14 * expect
+    # modes below omega_min contribute nothing; Gamma >= 0 and linear in the q weights
+    assert oracle.linewidths(eps_k, eps_kq, omega, g, [1.0], kT, mu, sig, 0.06)[0, 0] == 0.0
+    wl = synth.make_workload("si_tiny", nk=5, nq=3)
+    ek, ekq, om, gg = oracle.interpolate(wl)
+    G1 = oracle.linewidths(ek, ekq, om, gg, [1.0, 2.0, 0.5], kT, 0.0, 0.1, 1e-6)
+    G2 = oracle.linewidths(ek, ekq, om, gg, [2.0, 4.0, 1.0], kT, 0.0, 0.1, 1e-6)
+    assert np.all(G1 >= 0) and np.abs(G2 - 2 * G1).max() < 1e-13 * np.abs(G1).max()
