@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--cpu-sample-k", type=int, default=16000)
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-form measurement")
     ap.add_argument("--no-backward", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--no-linewidths", action="store_true", help="skip the fused linewidth measurement")
     return ap.parse_args()
 
 
@@ -296,6 +297,34 @@ def time_backward(args):
             "parity": "vs FP64 CPU adjoint <= 1e-12, central differences <= 1e-6 (tests/test_gpu_adjoint.py)"}
 
 
+def time_linewidths(wl, args, q_dev, k_dev, dev, QB):
+    """eph_linewidths (fused consumer, FP64) over the same q points the timed steps cover."""
+    import torch
+
+    from paper_2603_10295_gb300 import binding
+    nk, nb, nm = len(wl.kpts), wl.nb, wl.nm
+    st = torch.cuda.current_stream()
+    ctx = binding.Context.from_workload(wl, device_ptrs=True, q_batch=QB, stream=st)
+    eps_k = torch.empty(nk, nb, dtype=torch.float64, device=dev)
+    ctx.eph_set_k(nk, k_dev, eps_k)
+    gamma = torch.empty(nk, nb, dtype=torch.float64, device=dev)
+    nq = args.steps * QB
+    qs = q_dev[args.warmup * QB:args.warmup * QB + nq]
+    ctx.eph_linewidths(QB, q_dev[:QB], None, 0.025852, 0.0, 0.05, 1e-6, gamma)   # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    ctx.eph_linewidths(nq, qs, None, 0.025852, 0.0, 0.05, 1e-6, gamma)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    return {"what": f"electron linewidths (imaginary Fan-Migdal self-energy, 300 K, Gaussian 0.05 eV) over "
+                    f"{nq} q x {nk} k, g never written to HBM",
+            "ms_per_step": ms / args.steps, "g_elements_per_s": nq * nk * nm * nb * nb / (ms * 1e-3),
+            "parity": "vs oracle.linewidths <= 1e-10 per k (tests/test_gpu_linewidths.py)"}
+
+
 def run_libeph(args):
     import numpy as np
     import torch
@@ -413,6 +442,8 @@ def run_libeph(args):
         line["e2e"] = e2e(forms[0])
         if "mixed" in line:
             line["mixed"]["e2e"] = e2e("mixed")
+    if rank == 0 and not args.no_linewidths:
+        line["linewidths"] = time_linewidths(wl, args, q_dev, k_dev, dev, QB)
     if rank == 0 and not args.no_backward:
         line["backward"] = time_backward(args)
     if rank == 0 and not args.no_cpu_baseline:

@@ -138,6 +138,22 @@ int eph_interp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* q
 int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
                         const double* w_nk, double omega_min, double* L_out, double* grad_g_ReRp);
 
+/*
+ * Electron linewidths from the interpolated couplings without writing g (a fused
+ * downstream consumer; the paper's mobility and self-energy workloads consume g this
+ * way): for the resident k list and nq q points,
+ *   gamma[k][n] = pi sum_q w_q sum_{m, nu: omega_qnu > omega_min} |g_mnnu(k,q)|^2 / (2 omega_qnu)
+ *     x [ (n_B(omega) + f(e_{m,k+q})) delta(e_nk - e_{m,k+q} + omega)
+ *       + (n_B(omega) + 1 - f(e_{m,k+q})) delta(e_nk - e_{m,k+q} - omega) ]
+ * with n_B = 1/(exp(omega/kT) - 1), f = 1/(exp((e - mu)/kT) + 1) and a Gaussian delta of
+ * width sigma (all in eV); g as eph_interp_q defines it.  Units: |g|^2 / eV^2.
+ *   qpts [nq][3], wq [nq] q weights (NULL = all 1), gamma [nk][nb] (overwritten with the
+ *   sum over these q points); host or device pointers per device_ptrs.
+ * FP64 form with nb, nm <= 16; EPH_ENOTSUP otherwise.
+ */
+int eph_linewidths(eph_ctx* ctx, int nq, const double* qpts, const double* wq, double kT, double mu,
+                   double sigma, double omega_min, double* gamma);
+
 /* Releases every device resource of the context (NULL is a no-op). */
 void eph_destroy(eph_ctx* ctx);
 

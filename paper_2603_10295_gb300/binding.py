@@ -23,7 +23,7 @@ FORMS = {"fp64": 0, "mixed": 1}
 EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "eph_interp",
            "eph_interp_backward", "eph_destroy", "eph_strerror", "eph_last_error", "eph_kernel_launches",
            "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc",
-           "eph_reserve", "eph_sync", "eph_autotune")
+           "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -88,6 +88,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_sync.restype = i
     lib.eph_autotune.argtypes = [vp, i, dp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.eph_autotune.restype = i
+    lib.eph_linewidths.argtypes = [vp, i, dp, dp, d, d, d, d, dp]
+    lib.eph_linewidths.restype = i
     del ip
     if path is None:
         _lib = lib
@@ -210,6 +212,17 @@ class Context:
         qb, kt = ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.eph_autotune(self.handle, int(nq), _ptr(qpts), ctypes.byref(qb), ctypes.byref(kt)))
         return qb.value, kt.value
+
+    def eph_linewidths(self, nq, qpts, wq, kT, mu, sigma, omega_min, gamma):
+        self._check(self.lib.eph_linewidths(self.handle, int(nq), _ptr(qpts), _ptr(wq), float(kT), float(mu),
+                                            float(sigma), float(omega_min), _ptr(gamma)))
+
+    def linewidths(self, qpts, wq=None, kT=0.025852, mu=0.0, sigma=0.05, omega_min=1e-6):
+        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
+        wq = None if wq is None else np.ascontiguousarray(wq, dtype=np.float64)
+        gamma = np.empty((self.nk, self.nb))
+        self.eph_linewidths(len(qpts), qpts, wq, kT, mu, sigma, omega_min, gamma)
+        return gamma
 
     def eph_interp_backward(self, nk, kpts, nq, qpts, w_nk, omega_min, L_out, grad):
         self._check(self.lib.eph_interp_backward(self.handle, int(nk), _ptr(kpts), int(nq), _ptr(qpts), _ptr(w_nk),

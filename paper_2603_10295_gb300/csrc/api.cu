@@ -92,6 +92,8 @@ struct eph_ctx {
   // shapes beyond the warp kernels (nb or nm > 16): CTA Jacobi work, transposed u, band-rotation temp
   bool big = false;
   DBuf jwork, ut, Tbuf;
+  // linewidth consumer: q weights, per-(q,k) partials, accumulator
+  DBuf wqb, lwpart, lwacc;
   long long launches = 0;
   std::string err;
   // per-stage event timing
@@ -293,7 +295,7 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->eps_tile, &ctx->Ukq, &ctx->g_stage, &ctx->wk, &ctx->G2bar, &ctx->G1bar,
                   &ctx->Lpair, &ctx->Lacc, &ctx->grad, &ctx->Ahi, &ctx->Alo, &ctx->Bhi, &ctx->Blo,
                   &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut,
-                  &ctx->Tbuf};
+                  &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -990,4 +992,50 @@ extern "C" int eph_autotune(eph_ctx* ctx, int nq, const double* qpts, int* q_bat
   if (q_batch_out) *q_batch_out = bq;
   if (k_tile_out) *k_tile_out = bk;
   return EPH_OK;
+}
+
+extern "C" int eph_linewidths(eph_ctx* ctx, int nq, const double* qpts, const double* wq, double kT, double mu,
+                              double sigma, double omega_min, double* gamma) {
+  if (!ctx) return EPH_EINVAL;
+  if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_linewidths before eph_set_k");
+  if (nq < 1 || !qpts || !gamma || !(kT > 0.0) || !(sigma > 0.0))
+    return fail(ctx, EPH_EINVAL, "eph_linewidths: nq < 1, NULL pointer, or kT/sigma not positive");
+  if (ctx->opt.form != EPH_FORM_FP64 || ctx->big)
+    return fail(ctx, EPH_ENOTSUP, "eph_linewidths: FP64 form with nb, nm <= 16");
+  const int nb = ctx->nb, nm = ctx->nm, nk = ctx->nk, nb2 = nb * nb;
+  QPlan p;
+  EPH_TRY(prepare_fp64(ctx, nq, false, &p));
+  const void* dq = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
+  EPH_TRY(ensure(ctx, ctx->wqb, (size_t)nq * sizeof(double)));
+  if (wq) {
+    EPH_CK(cudaMemcpyAsync(ctx->wqb.p, wq, (size_t)nq * sizeof(double),
+                           ctx->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    std::vector<double> ones((size_t)nq, 1.0);
+    EPH_CK(cudaMemcpyAsync(ctx->wqb.p, ones.data(), (size_t)nq * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    EPH_CK(cudaStreamSynchronize(ctx->stream));  // the host vector dies at scope exit
+  }
+  EPH_TRY(ensure(ctx, ctx->lwpart, (size_t)p.QB * p.KT * nb * sizeof(double)));
+  EPH_TRY(ensure(ctx, ctx->lwacc, (size_t)nk * nb * sizeof(double)));
+  EPH_CK(cudaMemsetAsync(ctx->lwacc.p, 0, (size_t)nk * nb * sizeof(double), ctx->stream));
+  const double* qdev = static_cast<const double*>(dq);
+  double2* Y = as<double2>(ctx->Y);
+  for (int q0 = 0; q0 < nq; q0 += p.QB) {
+    const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
+    for (long k0 = 0; k0 < nk; k0 += p.KT) {
+      const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
+      EPH_TRY(k_tile_forward(ctx, p, nqb, k0, nkt));
+      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_linewidth(
+                                       Y + nb2, p.NW, as<double2>(ctx->Ukq), as<double2>(ctx->Uk) + k0 * nb2,
+                                       as<double>(ctx->eps_k) + k0 * nb, as<double>(ctx->eps_tile),
+                                       as<double>(ctx->omq), as<double>(ctx->wqb) + q0, nqb, nkt, nm, nb, kT, mu, sigma,
+                                       omega_min, as<double>(ctx->lwpart), ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_sum_over_q(as<double>(ctx->lwpart), nqb, (long)nkt * nb,
+                                                          as<double>(ctx->lwacc) + k0 * nb, ctx->stream));
+    }
+  }
+  EPH_CK(cudaMemcpyAsync(gamma, ctx->lwacc.p, (size_t)nk * nb * sizeof(double), out_kind(ctx), ctx->stream));
+  return finish(ctx);
 }

@@ -79,6 +79,15 @@ cudaError_t launch_mode_rotate(const double2* G1, const double2* u, int nq, int 
 cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq,
                                int nk, int nm, int nb, double2* g, long sgq, cudaStream_t st);
 
+// ---- fused consumer: electron linewidths from each (q,k) tile without writing g -----------
+// part[q][k][n] = pi w_q sum_{m,nu} |g|^2/(2 omega) [(n_B + f) delta(e - e' + omega) + (n_B + 1 - f) delta(e - e' - omega)]
+cudaError_t launch_band_linewidth(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, const double* epsk,
+                                  const double* epskq, const double* om, const double* wq, int nq, int nk, int nm,
+                                  int nb, double kT, double mu, double sigma, double omega_min, double* part,
+                                  cudaStream_t st);
+// acc[k][n] += sum_q part[q][k][n]
+cudaError_t launch_sum_over_q(const double* part, int nq, long per_q, double* acc, cudaStream_t st);
+
 // ---- adjoint (reverse chain of Eqs. 9-10 for L = sum c |g|^2) ------------------
 // In place over the G3 rows of Y: G3bar = V_{k+q} (2 c g) V_k^H with c = w_nk/omega (omega > omega_min);
 // Lpair[q*nk + k] = sum c |g|^2 for the pair.  wk: [nk][nb] (tile-local), om: [nq][nm].

@@ -147,3 +147,122 @@ cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, c
 }
 
 }  // namespace eph
+
+namespace eph {
+
+// Fused consumer: the band rotation of one (q,k) pair into shared memory, then the
+// pair's contribution to the electron linewidth of each band n,
+//   part[n] = pi w_q sum_{m, nu: omega > omega_min} |g_mn nu|^2 / (2 omega_nu)
+//             x [ (n_B + f_m) delta(e_n - e'_m + omega_nu) + (n_B + 1 - f_m) delta(e_n - e'_m - omega_nu) ],
+// Gaussian delta of width sigma, n_B = 1/(exp(omega/kT) - 1), f_m = 1/(exp((e'_m - mu)/kT) + 1)
+// (e_n = eps_k, e'_m = eps_{k+q}).  g itself is never written to global memory.
+__global__ void __launch_bounds__(128) k_band_linewidth(const double2* __restrict__ Y, long ldy,
+                                                        const double2* __restrict__ Ukq,
+                                                        const double2* __restrict__ Uk,
+                                                        const double* __restrict__ epsk,
+                                                        const double* __restrict__ epskq,
+                                                        const double* __restrict__ om, const double* __restrict__ wq,
+                                                        int nk, int nm, int nb, double kT, double mu, double sigma,
+                                                        double omega_min, double* __restrict__ part) {
+  extern __shared__ double2 sm[];
+  const int nb2 = nb * nb;
+  double2* uk = sm;
+  double2* ukq = uk + nb2;
+  double2* G = ukq + nb2;
+  double2* T = G + nm * nb2;
+  double* fm = reinterpret_cast<double*>(T + nm * nb2);  // [nb] occupations at k+q
+  double* nbose = fm + nb;                                // [nm] Bose factors (0 for excluded modes)
+  const long pair = blockIdx.x;
+  const int k = (int)(pair % nk);
+  const long q = pair / nk;
+  const double2* grow = Y + pair * ldy;
+  for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
+    uk[t] = Uk[(long)k * nb2 + t];
+    ukq[t] = Ukq[pair * nb2 + t];
+  }
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) G[t] = grow[t];
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) fm[t] = 1.0 / (exp((epskq[pair * nb + t] - mu) / kT) + 1.0);
+  for (int t = threadIdx.x; t < nm; t += blockDim.x) {
+    const double w = om[q * nm + t];
+    nbose[t] = (w > omega_min) ? 1.0 / expm1(w / kT) : 0.0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2, a = rem / nb, n = rem - a * nb;
+    const double2* gr = G + nu * nb2 + a * nb;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b = 0; b < nb; ++b) {
+      const double2 x = gr[b], y = uk[b * nb + n];
+      acc.x = fma(x.x, y.x, fma(-x.y, y.y, acc.x));
+      acc.y = fma(x.x, y.y, fma(x.y, y.x, acc.y));
+    }
+    T[t] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {  // g overwrites G
+    const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, n = rem - m * nb;
+    const double2* tc = T + nu * nb2 + n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int a = 0; a < nb; ++a) {
+      const double2 x = ukq[a * nb + m], y = tc[a * nb];
+      acc.x = fma(x.x, y.x, fma(x.y, y.y, acc.x));
+      acc.y = fma(x.x, y.y, fma(-x.y, y.x, acc.y));
+    }
+    G[t] = acc;
+  }
+  __syncthreads();
+  const double inv = 1.0 / (sigma * sqrt(2.0 * 3.141592653589793238));
+  const double c = -0.5 / (sigma * sigma);
+  for (int n = threadIdx.x; n < nb; n += blockDim.x) {
+    const double en = epsk[(long)k * nb + n];
+    double s = 0.0;
+    for (int nu = 0; nu < nm; ++nu) {
+      const double w = om[q * nm + nu];
+      if (!(w > omega_min)) continue;
+      const double nB = nbose[nu];
+      for (int m = 0; m < nb; ++m) {
+        const double2 gv = G[nu * nb2 + m * nb + n];
+        const double de = en - epskq[pair * nb + m];
+        const double xa = de + w, xe = de - w;
+        const double term = (nB + fm[m]) * exp(c * xa * xa) + (nB + 1.0 - fm[m]) * exp(c * xe * xe);
+        s = fma(fma(gv.x, gv.x, gv.y * gv.y) / (2.0 * w), term, s);
+      }
+    }
+    part[pair * nb + n] = 3.141592653589793238 * wq[q] * inv * s;
+  }
+}
+
+cudaError_t launch_band_linewidth(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, const double* epsk,
+                                  const double* epskq, const double* om, const double* wq, int nq, int nk, int nm,
+                                  int nb, double kT, double mu, double sigma, double omega_min, double* part,
+                                  cudaStream_t st) {
+  const long pairs = (long)nq * nk;
+  if (pairs <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(2 * nb * nb + 2 * nm * nb * nb) * sizeof(double2) + (size_t)(nb + nm) * sizeof(double);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_band_linewidth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
+  k_band_linewidth<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, epsk, epskq, om, wq, nk, nm, nb, kT, mu, sigma,
+                                                       omega_min, part);
+  return cudaGetLastError();
+}
+
+// acc[k][n] += sum_{q < nq} part[q][k][n] (fixed order over q).
+__global__ void k_sum_over_q(const double* __restrict__ part, int nq, long per_q, double* __restrict__ acc) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= per_q) return;
+  double s = acc[idx];
+  for (int q = 0; q < nq; ++q) s += part[(long)q * per_q + idx];
+  acc[idx] = s;
+}
+
+cudaError_t launch_sum_over_q(const double* part, int nq, long per_q, double* acc, cudaStream_t st) {
+  if (per_q <= 0 || nq <= 0) return cudaSuccess;
+  k_sum_over_q<<<(unsigned)((per_q + 255) / 256), 256, 0, st>>>(part, nq, per_q, acc);
+  return cudaGetLastError();
+}
+
+}  // namespace eph
