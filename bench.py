@@ -36,12 +36,12 @@ METRIC = "e-ph g(k,q) elements/s, 1 GB300: split-precision vs FP64 form at state
 UNIT = "g elements/s"
 # FP64 pipe of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and max clock)
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one ncu
-# capture of a one-q launch, scaled to the bench launch by the units processed
-# (profiles/k_zgemm_si_full_fp64.md, profiles/k_tc_fixed_gemm_si_full.md).
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one bench launch, from a
+# one-pass ncu capture of that launch (q batch 4: 4 q x 16320 k for k_zgemm, 4 q x 64000 k
+# for k_tc_fixed_gemm); profiles/k_zgemm_si_full_fp64.md, profiles/k_tc_fixed_gemm_si_full.md.
 # Keyed by (kernel, workload, q batch).
-TRAFFIC = {("k_zgemm", "si_full", 4): 4 * (224.901120e6 + 405.762048e6),
-           ("k_zgemm", "si_full", 1): 224.901120e6 + 405.762048e6}
+TRAFFIC = {("k_zgemm", "si_full", 4): 65482240.0 + 409080320.0,
+           ("k_tc_fixed_gemm", "si_full", 4): 194695936.0 + 740889600.0}
 
 
 def parse():
@@ -358,32 +358,39 @@ def run_libeph(args):
     def roof_fp64(r):
         ft_ms, ft_n = r["prof"]["ft_k"]
         NW = nb * nb * (1 + nm)
-        cmac_launch = float(QB) * nk * NW * ne         # one launch covers the q batch x all k
+        # the timed steps cover steps x QB q points x all k; each launch one (q batch, k tile)
+        cmac_launch = float(args.steps) * QB * nk * NW * ne / max(ft_n, 1)
         t = ft_ms / max(ft_n, 1) * 1e-3 if ft_n else None
+        nkt = -(-nk // max(ft_n // max(args.steps, 1), 1))
+        # P_k tile read, W_q read, Y = [H(k+q) | G3] written once (complex128)
+        algo_bytes = 16.0 * (nkt * ne + QB * ne * NW + QB * nkt * NW)
         # the kernel's algorithm (3M complex product) spends 3 DFMA = 6 flop per complex multiply-add
         ach = 6.0 * cmac_launch / t if t else None
         return {"bound": "alu", "kernel": "k_zgemm (Re->k contraction fused with H(k+q), FP64 DFMA, 3M)",
                 "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": (ach / FP64_PEAK_FLOPS) if ach else None,
                 "flop_per_cmac": 6, "complex_equiv_tflops": 8.0 * cmac_launch / t / 1e12 if t else None,
-                "traffic": TRAFFIC.get(("k_zgemm", args.workload, QB)),
+                "traffic": TRAFFIC.get(("k_zgemm", args.workload, QB)), "algorithmic_bytes": algo_bytes,
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
 
     def roof_tc(r):
         tc_ms, tc_n = r["prof"]["tc"]
         kpd = ((2 * ne + 63) // 64) * 64
         nr = 2 * nm * nb * nb
-        mpad = ((nk + 127) // 128) * 128
+        tiles = max(tc_n // max(args.steps, 1), 1)      # k tiles per q batch
+        mpad = ((-(-nk // tiles) + 127) // 128) * 128
         npad = ((nr + 127) // 128) * 128
         issued = 9 * 2.0 * mpad * npad * kpd * QB     # nine bf16 digit products per K step
-        useful = 8.0 * nk * nm * nb * nb * ne * QB     # complex Re->k contraction, 8 flop per CMAC
+        useful = 8.0 * nk * nm * nb * nb * ne * QB / tiles     # complex Re->k contraction, 8 flop per CMAC
         t = tc_ms / max(tc_n, 1) * 1e-3 if tc_n else None
+        # A digits (3) and B digits (4) in bf16 read once, the FP32 product written once
+        algo_bytes = 2.0 * (3 * mpad * kpd + 4 * QB * npad * kpd) + 4.0 * QB * min(mpad, nk) * nr
         peak = peaks.get("bf16_tflops")
         return {"bound": "tensor", "kernel": "k_tc_fixed_gemm (tcgen05 kind::f16, fixed-point BF16 digits)",
                 "achieved": issued / t / 1e12 if t else None, "peak": peak, "unit": "TFLOP/s",
                 "frac": (issued / t / 1e12 / peak) if (t and peak) else None,
                 "useful_tflops": useful / t / 1e12 if t else None, "ms_per_launch": tc_ms / max(tc_n, 1),
-                "traffic": TRAFFIC.get(("k_tc_fixed_gemm", args.workload, QB)),
+                "traffic": TRAFFIC.get(("k_tc_fixed_gemm", args.workload, QB)), "algorithmic_bytes": algo_bytes,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), measured" if peak else "unavailable"}
 
     line = None

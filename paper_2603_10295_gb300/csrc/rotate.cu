@@ -199,35 +199,34 @@ __global__ void __launch_bounds__(128) k_band_linewidth(const double2* __restric
     T[t] = acc;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {  // g overwrites G
-    const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, n = rem - m * nb;
-    const double2* tc = T + nu * nb2 + n;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int a = 0; a < nb; ++a) {
-      const double2 x = ukq[a * nb + m], y = tc[a * nb];
-      acc.x = fma(x.x, y.x, fma(x.y, y.y, acc.x));
-      acc.y = fma(x.x, y.y, fma(-x.y, y.x, acc.y));
-    }
-    G[t] = acc;
-  }
-  __syncthreads();
+  // each thread forms one g_{m n nu} and its term; the terms overwrite G (free after T)
   const double inv = 1.0 / (sigma * sqrt(2.0 * 3.141592653589793238));
   const double c = -0.5 / (sigma * sigma);
-  for (int n = threadIdx.x; n < nb; n += blockDim.x) {
-    const double en = epsk[(long)k * nb + n];
-    double s = 0.0;
-    for (int nu = 0; nu < nm; ++nu) {
-      const double w = om[q * nm + nu];
-      if (!(w > omega_min)) continue;
-      const double nB = nbose[nu];
-      for (int m = 0; m < nb; ++m) {
-        const double2 gv = G[nu * nb2 + m * nb + n];
-        const double de = en - epskq[pair * nb + m];
-        const double xa = de + w, xe = de - w;
-        const double term = (nB + fm[m]) * exp(c * xa * xa) + (nB + 1.0 - fm[m]) * exp(c * xe * xe);
-        s = fma(fma(gv.x, gv.x, gv.y * gv.y) / (2.0 * w), term, s);
+  double* term = reinterpret_cast<double*>(G);  // [nu][m][n]
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, n = rem - m * nb;
+    const double w = om[q * nm + nu];
+    double v = 0.0;
+    if (w > omega_min) {
+      const double2* tc = T + nu * nb2 + n;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int a = 0; a < nb; ++a) {
+        const double2 x = ukq[a * nb + m], y = tc[a * nb];
+        acc.x = fma(x.x, y.x, fma(x.y, y.y, acc.x));
+        acc.y = fma(x.x, y.y, fma(-x.y, y.x, acc.y));
       }
+      const double nB = nbose[nu], f = fm[m];
+      const double de = epsk[(long)k * nb + n] - epskq[pair * nb + m];
+      const double xa = de + w, xe = de - w;
+      const double d = (nB + f) * exp(c * xa * xa) + (nB + 1.0 - f) * exp(c * xe * xe);
+      v = fma(acc.x, acc.x, acc.y * acc.y) / (2.0 * w) * d;
     }
+    term[t] = v;
+  }
+  __syncthreads();
+  for (int n = threadIdx.x; n < nb; n += blockDim.x) {  // fixed-order sum over (nu, m)
+    double s = 0.0;
+    for (int j = 0; j < nm * nb; ++j) s += term[j * nb + n];
     part[pair * nb + n] = 3.141592653589793238 * wq[q] * inv * s;
   }
 }

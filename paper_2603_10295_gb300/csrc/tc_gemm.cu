@@ -256,10 +256,20 @@ __global__ void __launch_bounds__(128, 1) k_tc_split_gemm(const __grid_constant_
 // Persistent kernel, one CTA (6 warps) per SM: warp 0 issues TMA into a 2-stage ring of
 // 112 KiB stages, warp 1 issues the 9 tcgen05.mma (M=128, N=128, K=16) per K step into one
 // of two TMEM accumulator pairs (L0, L123 at columns b*256 + {0, 128}), warps 2-5 drain the
-// other pair (epilogue of tile i overlaps the MMAs of tile i+1).  Tiles (q, m, n) are taken
-// in steps of gridDim.x with n fastest, so concurrent CTAs share their A tiles in L2.
+// other pair (epilogue of tile i overlaps the MMAs of tile i+1).  Tiles (m, q, n) are taken
+// in steps of gridDim.x with n fastest, then q: the CTAs that need one A row tile (every
+// q and n) run at the same time and read it from DRAM once.
 namespace tcf {
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 2, NA = 3, NB = 4;   // BK bf16 = 128 B rows
+
+__device__ __forceinline__ void tile_coords(long t, int ntn, int nq, int* q, int* m0, int* n0) {
+  const long per_m = (long)ntn * nq;
+  const long mt = t / per_m;
+  const int rem = (int)(t - mt * per_m);
+  *q = rem / ntn;
+  *m0 = (int)mt * BM;
+  *n0 = (rem - *q * ntn) * BN;
+}
 constexpr int A_BYTES = BM * BK * 2;                              // 16 KiB per digit slice
 constexpr int B_BYTES = BN * BK * 2;                              // 16 KiB
 constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;          // 112 KiB
@@ -343,9 +353,8 @@ __global__ void __launch_bounds__(tcf::THREADS, 1) k_tc_fixed_gemm(const __grid_
     if (lane == 0) {  // ---- TMA producer
       long it = 0;
       for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-        const int q = (int)(t / ((long)ntm * ntn));
-        const int rem = (int)(t - (long)q * ntm * ntn);
-        const int m0 = (rem / ntn) * BM, n0 = (rem % ntn) * BN;
+        int q, m0, n0;
+        tcf::tile_coords(t, ntn, nq, &q, &m0, &n0);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = (int)(it % STAGES);
           if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1))) {
@@ -425,9 +434,8 @@ __global__ void __launch_bounds__(tcf::THREADS, 1) k_tc_fixed_gemm(const __grid_
         break;
       }
       fence_after();
-      const int q = (int)(t / ((long)ntm * ntn));
-      const int rem = (int)(t - (long)q * ntm * ntn);
-      const int m0 = (rem / ntn) * BM, n0 = (rem % ntn) * BN;
+      int q, m0, n0;
+      tcf::tile_coords(t, ntn, nq, &q, &m0, &n0);
       const int row = m0 + quarter * 32 + lane;
       const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
       float* crow = C + (long)q * sC + (long)row * ldc;

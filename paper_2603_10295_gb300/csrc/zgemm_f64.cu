@@ -37,8 +37,12 @@ __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, const double
   __shared__ double3 Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const long b1 = blockIdx.z / nbat2, b2 = blockIdx.z - b1 * nbat2;
+  // grid.x runs over (column block, batch) with the column block fastest, so the CTAs
+  // that share one row block of A (all batches) run back to back and reuse it from L2
+  const int nN = (N + BN - 1) / BN;
+  const long z = blockIdx.x / nN;
+  const int m0 = blockIdx.y * BM, n0 = (int)(blockIdx.x - z * nN) * BN;
+  const long b1 = z / nbat2, b2 = z - b1 * nbat2;
   A += b1 * sA + b2 * sA2;
   B += b1 * sB + b2 * sB2;
   C += b1 * sC + b2 * sC2;
@@ -121,7 +125,7 @@ cudaError_t launch_zgemm(int M, int N, int K, const double2* A, long lda, long s
                          long sB, double2* C, long ldc, long sC, int batch, cudaStream_t st) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   if (!grid_ok(M, N, batch)) return cudaErrorInvalidConfiguration;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+  dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
   k_zgemm<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0);
   return cudaGetLastError();
 }
@@ -132,7 +136,7 @@ cudaError_t launch_zgemm_b2(int M, int N, int K, const double2* A, long lda, lon
   const long batch = (long)nbat1 * nbat2;
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   if (batch > 65535 || !grid_ok(M, N, 1)) return cudaErrorInvalidConfiguration;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, (unsigned)batch);
+  dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
   if (adj)
     k_zgemm<true, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nbat2, sA2, sB2, sC2);
   else
@@ -144,7 +148,7 @@ cudaError_t launch_zgemm_ah(int M, int N, int K, const double2* A, long lda, lon
                             long sB, double2* C, long ldc, long sC, int batch, int acc, cudaStream_t st) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   if (!grid_ok(M, N, batch)) return cudaErrorInvalidConfiguration;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+  dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
   if (acc)
     k_zgemm<true, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0);
   else
@@ -285,8 +289,9 @@ __global__ void __launch_bounds__(256, 2) k_zgemm_df(int M, int N, int K, const 
   __shared__ float4 Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const long b = blockIdx.z;
+  const int nN = (N + BN - 1) / BN;  // grid.x = (column block, batch), column block fastest
+  const long b = blockIdx.x / nN;
+  const int m0 = blockIdx.y * BM, n0 = (int)(blockIdx.x - b * nN) * BN;
   A += b * sA;
   B += b * sB;
   C += b * sC;
@@ -348,7 +353,7 @@ cudaError_t launch_zgemm_df(int M, int N, int K, const double2* A, long lda, lon
                             long sB, double2* C, long ldc, long sC, int batch, cudaStream_t st) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   if (!grid_ok(M, N, batch)) return cudaErrorInvalidConfiguration;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+  dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
   k_zgemm_df<<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
   return cudaGetLastError();
 }
