@@ -223,6 +223,17 @@ def loss_and_grad(a, kpts, qpts, w_nk, omega_min):
     L = loss(g, omega, w_nk, omega_min)
     c = loss_weights(omega, w_nk, omega_min)
     gbar = 2.0 * c[:, :, :, None, :] * g                           # [nq][nk][nu][m][n]
+    return L, vjp(a, kpts, qpts, gbar, ev)
+
+
+def vjp(a, kpts, qpts, gbar, ev):
+    """A^H gbar for the linear map A: g(Re,Rp) -> g(k,q) (Eqs. 9-10 and the band rotation of
+    Eq. 7) at fixed gauges ev = interpolate(..., return_eigvecs=True)[4]; gbar [nq][nk][nm][nb][nb]
+    in the dL/dRe + i dL/dIm convention.  Reverse chain: Gk_bar = sum_nu conj(u) V_kq gbar V_k^H;
+    G1_bar = sum_k conj(P_k) Gk_bar; grad = sum_q conj(P_q) G1_bar.
+    """
+    kpts = np.asarray(kpts, dtype=np.float64)
+    qpts = np.asarray(qpts, dtype=np.float64)
     Pk = phases(kpts, a.Re, a.we)                                  # [nk][ne]
     Pq = phases(qpts, a.Rp, a.wp)                                  # [nq][np]
     V_k, V_kq, u = ev["V_k"], ev["V_kq"], ev["u"]
@@ -233,8 +244,7 @@ def loss_and_grad(a, kpts, qpts, w_nk, omega_min):
         Gb_bar = np.einsum("kam,kvmn,kbn->kvab", V_kq[iq], gbar[iq], V_k.conj())   # V_kq gbar V_k^H
         Gk_bar = np.einsum("cv,kvab->kcab", u[iq].conj(), Gb_bar)
         G1bar[iq] = np.einsum("ke,kcab->ceab", Pk.conj(), Gk_bar)
-    grad = (Pq.conj().T @ G1bar.reshape(nq, -1)).reshape(a.g_ReRp.shape)
-    return L, grad
+    return (Pq.conj().T @ G1bar.reshape(nq, -1)).reshape(a.g_ReRp.shape)
 
 
 def fermi_weights(eps_k, band_index, kT=0.025852):

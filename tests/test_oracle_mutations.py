@@ -20,11 +20,13 @@ PIN_FUNCS = [
     pins.test_nested_equals_single_loop,
     pins.test_wannier_round_trip,
     pins.test_unitarity_invariant_and_periodicity,
+    pins.test_vjp_is_the_adjoint_of_the_interpolation,
 ]
 
 _orig_phases = eo.phases
 _orig_g_req = eo.g_req_to_bloch
 _orig_phonon = eo.phonon_eigen
+_orig_vjp = eo.vjp
 
 
 def _phase_sign(pts, R, w=None):
@@ -56,6 +58,14 @@ def _phonon_no_mass(Dq, masses):
     return om, e, e
 
 
+def _vjp_u_unconjugated(a, kpts, qpts, gbar, ev):
+    return _orig_vjp(a, kpts, qpts, gbar, dict(ev, u=ev["u"].conj()))
+
+
+def _vjp_kq_gauge_conjugated(a, kpts, qpts, gbar, ev):
+    return _orig_vjp(a, kpts, qpts, gbar, dict(ev, V_kq=ev["V_kq"].conj()))
+
+
 MUTATIONS = {
     "phase_sign": ("phases", _phase_sign),
     "phase_missing_2pi": ("phases", _phase_unreduced_wrong_scale),
@@ -63,6 +73,8 @@ MUTATIONS = {
     "band_rotation_swapped_gauges": ("g_req_to_bloch", _g_req_swap_gauges),
     "mode_rotation_transposed": ("g_req_to_bloch", _g_req_u_transposed),
     "mode_vector_without_mass": ("phonon_eigen", _phonon_no_mass),
+    "vjp_mode_rotation_unconjugated": ("vjp", _vjp_u_unconjugated),
+    "vjp_band_gauge_conjugated": ("vjp", _vjp_kq_gauge_conjugated),
 }
 
 

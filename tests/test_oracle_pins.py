@@ -233,6 +233,30 @@ def test_adjoint_central_differences_and_euler():
             assert abs(d - ref) <= 1e-6 * max(1.0, np.abs(grad).max())
 
 
+def test_vjp_is_the_adjoint_of_the_interpolation():
+    # g(k,q) is linear in g(Re,Rp) at fixed H, Phi (fixed gauges), so for any upstream gbar
+    # and direction d: Re<vjp(gbar), d> = Re<gbar, A(d)>, A(d) = interpolation of d.
+    import copy
+    wl = synth.make_workload("si_tiny", nb=3, nk=5, nq=3)
+    rng = np.random.default_rng(31)
+    _, _, _, g, ev = oracle.interpolate(wl, return_eigvecs=True)
+    gbar = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+    d = rng.standard_normal(wl.g_ReRp.shape) + 1j * rng.standard_normal(wl.g_ReRp.shape)
+    wd = copy.copy(wl)
+    wd.g_ReRp = d
+    _, _, _, Ad = oracle.interpolate(wd)
+    lhs = np.real(np.vdot(oracle.vjp(wl, wl.kpts, wl.qpts, gbar, ev), d))
+    rhs = np.real(np.vdot(gbar, Ad))
+    assert abs(lhs - rhs) <= 1e-12 * np.sum(np.abs(gbar) * np.abs(Ad))
+    # and the loss gradient is the vjp of 2 c g
+    w_nk = rng.uniform(0.0, 1.0, (len(wl.kpts), wl.nb))
+    _, grad = oracle.loss_and_grad(wl, wl.kpts, wl.qpts, w_nk, 1e-6)
+    _, _, om, _ = oracle.interpolate(wl)
+    c = oracle.loss_weights(om, w_nk, 1e-6)
+    assert np.abs(oracle.vjp(wl, wl.kpts, wl.qpts, 2 * c[:, :, :, None, :] * g, ev) - grad).max() \
+        <= 1e-14 * np.abs(grad).max()
+
+
 # ---------------------------------------------------------------- paper-printed values
 def test_table3_sizes_and_cost_ratio():
     rows = [list(map(float, l.split())) for l in open(os.path.join(HERE, "golden", "zsnr_gw_sizes.txt"))
