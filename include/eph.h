@@ -139,6 +139,23 @@ int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int nq, const 
                         const double* w_nk, double omega_min, double* L_out, double* grad_g_ReRp);
 
 /*
+ * Vector-Jacobian product of the interpolation (the adjoint chain of Eqs. 9-10 and the
+ * band rotation of Eq. 7, applied to an arbitrary upstream gradient): with U_k, U_{k+q}
+ * and e_q held fixed, g(k,q) is linear in g(Re,Rp), and
+ *   grad_g_ReRp = A^H grad_g,   A: g(Re,Rp) -> g(k,q) of eph_interp_q,
+ * i.e. for a real scalar L(g) and grad_g = dL/dRe(g) + i dL/dIm(g) (PyTorch convention)
+ * it returns dL/dRe(gW) + i dL/dIm(gW).  The gauges are recomputed bit for bit as
+ * eph_set_k / eph_interp_q produce them for the same context, so grad_g must refer to g
+ * as this context returned it.
+ *   kpts [nk][3], qpts [nq][3]; grad_g [nq][nk][nm][nb][nb] complex128; grad_g_ReRp
+ *   [np][nm][ne][nb][nb] complex128 (overwritten).  Host or device pointers per
+ *   device_ptrs.  Replaces the context's k list (as eph_set_k).
+ * FP64 form with nb, nm <= 16; EPH_ENOTSUP otherwise.
+ */
+int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts, const void* grad_g,
+                   double* grad_g_ReRp);
+
+/*
  * Electron linewidths from the interpolated couplings without writing g (a fused
  * downstream consumer; the paper's mobility and self-energy workloads consume g this
  * way): for the resident k list and nq q points,

@@ -23,7 +23,7 @@ FORMS = {"fp64": 0, "mixed": 1}
 EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "eph_interp",
            "eph_interp_backward", "eph_destroy", "eph_strerror", "eph_last_error", "eph_kernel_launches",
            "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc",
-           "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths")
+           "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths", "eph_interp_vjp")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -90,6 +90,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_autotune.restype = i
     lib.eph_linewidths.argtypes = [vp, i, dp, dp, d, d, d, d, dp]
     lib.eph_linewidths.restype = i
+    lib.eph_interp_vjp.argtypes = [vp, i, dp, i, dp, vp, dp]
+    lib.eph_interp_vjp.restype = i
     del ip
     if path is None:
         _lib = lib
@@ -212,6 +214,20 @@ class Context:
         qb, kt = ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.eph_autotune(self.handle, int(nq), _ptr(qpts), ctypes.byref(qb), ctypes.byref(kt)))
         return qb.value, kt.value
+
+    def eph_interp_vjp(self, nk, kpts, nq, qpts, grad_g, grad_g_ReRp):
+        self._check(self.lib.eph_interp_vjp(self.handle, int(nk), _ptr(kpts), int(nq), _ptr(qpts), _ptr(grad_g),
+                                            _ptr(grad_g_ReRp)))
+
+    def vjp(self, kpts, qpts, grad_g):
+        """dL/dg(Re,Rp) for an upstream gradient grad_g [nq][nk][nm][nb][nb] (complex128)."""
+        kpts = np.ascontiguousarray(kpts, dtype=np.float64)
+        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
+        grad_g = np.ascontiguousarray(grad_g, dtype=np.complex128)
+        out = np.empty((self.np_, self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
+        self.eph_interp_vjp(len(kpts), kpts, len(qpts), qpts, grad_g, out)
+        self.nk = len(kpts)   # the call replaces the context's k list
+        return out
 
     def eph_linewidths(self, nq, qpts, wq, kT, mu, sigma, omega_min, gamma):
         self._check(self.lib.eph_linewidths(self.handle, int(nq), _ptr(qpts), _ptr(wq), float(kT), float(mu),

@@ -9,6 +9,36 @@
 
 namespace eph {
 
+// G3bar[nu] = V_{k+q} gbar[nu] V_k^H for one pair, all threads of the CTA:
+// gbar in G (shared), T shared scratch of nm nb^2, result to the row (global).
+__device__ __forceinline__ void back_rotate(const double2* G, double2* T, const double2* uk, const double2* ukq,
+                                            int nm, int nb, double2* row) {
+  const int nb2 = nb * nb;
+  // S[nu][m][b] = sum_n gbar[nu][m][n] conj(uk[b][n])   (in T)
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, b = rem - m * nb;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int n = 0; n < nb; ++n) {
+      const double2 x = G[nu * nb2 + m * nb + n], y = uk[b * nb + n];
+      acc.x = fma(x.x, y.x, fma(x.y, y.y, acc.x));
+      acc.y = fma(x.y, y.x, fma(-x.x, y.y, acc.y));
+    }
+    T[t] = acc;
+  }
+  __syncthreads();
+  // G3bar[nu][a][b] = sum_m ukq[a][m] S[nu][m][b]  -> back into the row
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2, a = rem / nb, b = rem - a * nb;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int m = 0; m < nb; ++m) {
+      const double2 x = ukq[a * nb + m], y = T[nu * nb2 + m * nb + b];
+      acc.x = fma(x.x, y.x, fma(-x.y, y.y, acc.x));
+      acc.y = fma(x.x, y.y, fma(x.y, y.x, acc.y));
+    }
+    row[t] = acc;
+  }
+}
+
 // Per (q,k) pair: g from G3 (band rotation), L_pair = sum c |g|^2, then
 // G3bar = V_{k+q} (2 c g) V_k^H written over the pair's G3 row in place.
 __global__ void __launch_bounds__(128) k_band_adjoint(double2* __restrict__ Y, long ldy,
@@ -61,29 +91,7 @@ __global__ void __launch_bounds__(128) k_band_adjoint(double2* __restrict__ Y, l
     G[t] = make_double2(2.0 * c * acc.x, 2.0 * c * acc.y);
   }
   __syncthreads();
-  // S[nu][m][b] = sum_n gbar[nu][m][n] conj(uk[b][n])   (in T)
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
-    const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, b = rem - m * nb;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int n = 0; n < nb; ++n) {
-      const double2 x = G[nu * nb2 + m * nb + n], y = uk[b * nb + n];
-      acc.x = fma(x.x, y.x, fma(x.y, y.y, acc.x));
-      acc.y = fma(x.y, y.x, fma(-x.x, y.y, acc.y));
-    }
-    T[t] = acc;
-  }
-  __syncthreads();
-  // G3bar[nu][a][b] = sum_m ukq[a][m] S[nu][m][b]  -> back into the row
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
-    const int nu = t / nb2, rem = t - nu * nb2, a = rem / nb, b = rem - a * nb;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int m = 0; m < nb; ++m) {
-      const double2 x = ukq[a * nb + m], y = T[nu * nb2 + m * nb + b];
-      acc.x = fma(x.x, y.x, fma(-x.y, y.y, acc.x));
-      acc.y = fma(x.x, y.y, fma(x.y, y.x, acc.y));
-    }
-    row[t] = acc;
-  }
+  back_rotate(G, T, uk, ukq, nm, nb, row);
   // deterministic block reduction of the pair's L
   for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
@@ -104,6 +112,46 @@ cudaError_t launch_band_adjoint(double2* Y, long ldy, const double2* Ukq, const 
   }
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
   k_band_adjoint<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, wk, om, omega_min, nk, nm, nb, Lpair);
+  return cudaGetLastError();
+}
+
+// Vector-Jacobian product of the band rotation for an arbitrary upstream gradient:
+// G3bar = V_{k+q} gbar V_k^H written over the pair's G3 row (gbar[q][k][nu][m][n] with
+// q stride sgq).
+__global__ void __launch_bounds__(128) k_band_vjp(double2* __restrict__ Y, long ldy, const double2* __restrict__ gbar,
+                                                  long sgq, const double2* __restrict__ Ukq,
+                                                  const double2* __restrict__ Uk, int nk, int nm, int nb) {
+  extern __shared__ double2 sm[];
+  const int nb2 = nb * nb;
+  double2* uk = sm;
+  double2* ukq = uk + nb2;
+  double2* G = ukq + nb2;
+  double2* T = G + nm * nb2;
+  const long pair = blockIdx.x;
+  const int k = (int)(pair % nk);
+  const long q = pair / nk;
+  const double2* gb = gbar + q * sgq + (long)k * nm * nb2;
+  for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
+    uk[t] = Uk[(long)k * nb2 + t];
+    ukq[t] = Ukq[pair * nb2 + t];
+  }
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) G[t] = gb[t];
+  __syncthreads();
+  back_rotate(G, T, uk, ukq, nm, nb, Y + pair * ldy);
+}
+
+cudaError_t launch_band_vjp(double2* Y, long ldy, const double2* gbar, long sgq, const double2* Ukq,
+                            const double2* Uk, int nq, int nk, int nm, int nb, cudaStream_t st) {
+  const long pairs = (long)nq * nk;
+  if (pairs <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(2 * nb * nb + 2 * nm * nb * nb) * sizeof(double2);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_band_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
+  k_band_vjp<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, gbar, sgq, Ukq, Uk, nk, nm, nb);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@
 #include "eph_kernels.cuh"
 
 using eph::launch_band_adjoint;
+using eph::launch_band_vjp;
 using eph::launch_band_rotate;
 using eph::launch_mode_rotate;
 using eph::launch_mode_rotate_adj;
@@ -874,6 +875,73 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
                                                 as<double2>(ctx->G1bar), p.X, 0, grad, p.X, 0, 1, 1, ctx->stream));
   }
   EPH_CK(cudaMemcpyAsync(L_out, ctx->Lacc.p, sizeof(double), out_kind(ctx), ctx->stream));
+  if (host) EPH_CK(cudaMemcpyAsync(grad_g_ReRp, grad, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
+  return finish(ctx);
+}
+
+extern "C" int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
+                              const void* grad_g, double* grad_g_ReRp) {
+  if (!ctx) return EPH_EINVAL;
+  if (nk < 1 || nq < 1 || !kpts || !qpts || !grad_g || !grad_g_ReRp)
+    return fail(ctx, EPH_EINVAL, "eph_interp_vjp: bad size or NULL pointer");
+  if (ctx->big || ctx->opt.form != EPH_FORM_FP64)
+    return fail(ctx, EPH_ENOTSUP, "eph_interp_vjp: FP64 form with nb, nm <= 16");
+  EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
+  const int nb = ctx->nb, ne = ctx->ne, np = ctx->np;
+  const int nb2 = nb * nb;
+  const bool host = !ctx->opt.device_ptrs;
+  const long gcols = (long)ctx->nm * nb2;
+  const QPlan p = plan_q(ctx, nq, host ? (size_t)gcols * sizeof(double2) : 0);
+  const void* dq = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
+  EPH_TRY(ensure_q_workspace(ctx, p));
+  EPH_TRY(ensure(ctx, ctx->G2bar, (size_t)p.QB * p.X * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->G1bar, (size_t)p.QB * p.X * sizeof(double2)));
+  if (host) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)p.QB * p.KT * gcols * sizeof(double2)));
+  double2* grad = nullptr;
+  const size_t gbytes = (size_t)np * p.X * sizeof(double2);
+  if (host) {
+    EPH_TRY(ensure(ctx, ctx->grad, gbytes));
+    grad = as<double2>(ctx->grad);
+  } else {
+    grad = reinterpret_cast<double2*>(grad_g_ReRp);
+  }
+  EPH_CK(cudaMemsetAsync(grad, 0, gbytes, ctx->stream));
+  const double* qdev = static_cast<const double*>(dq);
+  const double2* gin = static_cast<const double2*>(grad_g);
+  double2* Y = as<double2>(ctx->Y);
+  double2* G2b = as<double2>(ctx->G2bar);
+  for (int q0 = 0; q0 < nq; q0 += p.QB) {
+    const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
+    for (long k0 = 0; k0 < nk; k0 += p.KT) {
+      const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
+      // only H(k+q) and its eigenvectors: g is linear in g(Re,Rp), so G3 itself is not needed
+      EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nkt, nb2, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0,
+                                                as<double2>(ctx->W), p.NW, (long)ne * p.NW, Y, p.NW,
+                                                (long)nkt * p.NW, nqb, ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, Y, p.NW, nb, nb, (long)nqb * nkt, as<double>(ctx->eps_tile), nb,
+                                      as<double2>(ctx->Ukq), nb2));
+      const double2* gb = gin + ((long)q0 * nk + k0) * gcols;
+      long sgq = (long)nk * gcols;
+      if (host) {
+        for (int iq = 0; iq < nqb; ++iq)
+          EPH_CK(cudaMemcpyAsync(as<double2>(ctx->g_stage) + (long)iq * nkt * gcols, gb + (long)iq * nk * gcols,
+                                 (size_t)nkt * gcols * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+        gb = as<double2>(ctx->g_stage);
+        sgq = (long)nkt * gcols;
+      }
+      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_band_vjp(Y + nb2, p.NW, gb, sgq, as<double2>(ctx->Ukq),
+                                                  as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, ctx->nm, nb, ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ne, (int)p.gcols, nkt, as<double2>(ctx->Pk) + k0 * ne, ne, 0,
+                                                  Y + nb2, p.NW, (long)nkt * p.NW, G2b, p.gcols, (long)ne * p.gcols,
+                                                  nqb, k0 > 0, ctx->stream));
+    }
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_mode_rotate_adj(G2b, as<double2>(ctx->uq), nqb, ctx->nm, ne, nb2,
+                                                       as<double2>(ctx->G1bar), ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(np, (int)p.X, nqb, as<double2>(ctx->Pp), np, 0,
+                                                as<double2>(ctx->G1bar), p.X, 0, grad, p.X, 0, 1, 1, ctx->stream));
+  }
   if (host) EPH_CK(cudaMemcpyAsync(grad_g_ReRp, grad, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
   return finish(ctx);
 }

@@ -94,6 +94,9 @@ cudaError_t launch_sum_over_q(const double* part, int nq, long per_q, double* ac
 cudaError_t launch_band_adjoint(double2* Y, long ldy, const double2* Ukq, const double2* Uk, const double* wk,
                                 const double* om, double omega_min, int nq, int nk, int nm, int nb, double* Lpair,
                                 cudaStream_t st);
+// G3bar = V_{k+q} gbar V_k^H over the pair's G3 row, gbar given ([q][k][nu][m][n], q stride sgq)
+cudaError_t launch_band_vjp(double2* Y, long ldy, const double2* gbar, long sgq, const double2* Ukq,
+                            const double2* Uk, int nq, int nk, int nm, int nb, cudaStream_t st);
 // *L += sum_i v[i] (one CTA, fixed order).
 cudaError_t launch_sum_into(const double* v, long n, double* L, cudaStream_t st);
 // G1bar[q][c][e][b] = sum_nu conj(u[q][c][nu]) G2bar[q][e][nu][b]
