@@ -36,12 +36,16 @@ METRIC = "e-ph g(k,q) elements/s, 1 GB300: split-precision vs FP64 form at state
 UNIT = "g elements/s"
 # FP64 pipe of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and max clock)
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one bench launch, from a
-# one-pass ncu capture of that launch (q batch 4: 4 q x 16320 k for k_zgemm, 4 q x 64000 k
-# for k_tc_fixed_gemm); profiles/k_zgemm_si_full_fp64.md, profiles/k_tc_fixed_gemm_si_full.md.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one bench launch (q batch 4
+# x 64000 k), from an ncu capture of that launch; profiles/k_zgemm_si_full_fp64.md,
+# profiles/k_tc_fixed_gemm_si_full.md, profiles/k_jacobi_mixed_si_full.md.
 # Keyed by (kernel, workload, q batch).
-TRAFFIC = {("k_zgemm", "si_full", 4): 65482240.0 + 409080320.0,
-           ("k_tc_fixed_gemm", "si_full", 4): 194695936.0 + 740889600.0}
+# FP64 flops per matrix of the batched H(k+q) eigensolve (2 x DFMA + DADD + DMUL thread
+# instructions executed, from one ncu capture; profiles/k_jacobi_mixed_si_full.md), keyed by (nb, form)
+EIG_FP64_FLOPS = {(8, "fp64"): (2 * 6418943830 + 1816575880 + 181247980) / 256000}
+TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 194695936.0 + 740889600.0,
+           ("k_zgemm", "si_full", 4): 242432512.0 + 1777470464.0,
+           ("k_jacobi_mixed", "si_full", 4): 263648512.0 + 231078400.0}
 
 
 def parse():
@@ -59,6 +63,9 @@ def parse():
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-form measurement")
     ap.add_argument("--no-backward", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-linewidths", action="store_true", help="skip the fused linewidth measurement")
+    ap.add_argument("--k-path", default="grid", choices=["grid", "list"],
+                    help="FP64 form: sum-factorised Re->k on the workload's uniform k grid, or the dense "
+                         "Re->k GEMM on the k list")
     return ap.parse_args()
 
 
@@ -195,7 +202,7 @@ def measured_peaks():
         return {}
 
 
-def time_form(wl, form, args, q_dev, k_dev, rank, world, local, dev, QB):
+def time_form(wl, form, args, q_dev, k_dev, rank, world, local, dev, QB, use_grid=False):
     """Times args.steps q batches of one form on the device (inputs resident in HBM)."""
     import torch
 
@@ -211,7 +218,10 @@ def time_form(wl, form, args, q_dev, k_dev, rank, world, local, dev, QB):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(st)
-    ctx.eph_set_k(nk, k_dev, eps_k)
+    if use_grid:
+        ctx.eph_set_k_grid(*wl.kgrid, None, eps_k)
+    else:
+        ctx.eph_set_k(nk, k_dev, eps_k)
     e1.record(st)
     torch.cuda.synchronize()
     setk_ms = e0.elapsed_time(e1)
@@ -297,7 +307,7 @@ def time_backward(args):
             "parity": "vs FP64 CPU adjoint <= 1e-12, central differences <= 1e-6 (tests/test_gpu_adjoint.py)"}
 
 
-def time_linewidths(wl, args, q_dev, k_dev, dev, QB):
+def time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=False):
     """eph_linewidths (fused consumer, FP64) over the same q points the timed steps cover."""
     import torch
 
@@ -306,7 +316,10 @@ def time_linewidths(wl, args, q_dev, k_dev, dev, QB):
     st = torch.cuda.current_stream()
     ctx = binding.Context.from_workload(wl, device_ptrs=True, q_batch=QB, stream=st)
     eps_k = torch.empty(nk, nb, dtype=torch.float64, device=dev)
-    ctx.eph_set_k(nk, k_dev, eps_k)
+    if use_grid:
+        ctx.eph_set_k_grid(*wl.kgrid, None, eps_k)
+    else:
+        ctx.eph_set_k(nk, k_dev, eps_k)
     gamma = torch.empty(nk, nb, dtype=torch.float64, device=dev)
     nq = args.steps * QB
     qs = q_dev[args.warmup * QB:args.warmup * QB + nq]
@@ -348,12 +361,64 @@ def run_libeph(args):
     q_dev = torch.from_numpy(np.ascontiguousarray(wl.qpts[qidx])).to(dev)
     k_dev = torch.from_numpy(wl.kpts).to(dev)
 
-    forms = ["fp64"] if args.form == "fp64" and args.fp64_only else ["fp64", "mixed"]
+    use_grid = args.k_path == "grid" and wl.kgrid is not None
+    # (form, grid) legs: the headline first, then the dense-GEMM k-list path of both forms
+    legs = [("fp64", use_grid)]
     if args.form == "mixed":
-        forms = ["mixed"]
-    res = {f: time_form(wl, f, args, q_dev, k_dev, rank, world, local, dev, QB) for f in forms}
-    head = res[forms[0]]
+        legs = [("mixed", False)]
+    elif not args.fp64_only:
+        if use_grid:
+            legs.append(("fp64", False))
+        legs.append(("mixed", False))
+    res = {(f, gr): time_form(wl, f, args, q_dev, k_dev, rank, world, local, dev, QB, use_grid=gr) for f, gr in legs}
+    head = res[legs[0]]
+    forms = [legs[0][0]]
     peaks = measured_peaks()
+
+    def roof_axis(r):
+        # axis-1 transform of the product-grid path (k_axis_dft, the last and largest of three):
+        # per output element B1 complex terms; paired form 2 FP64 FMA + 1 add per term and output
+        ft_ms, ft_n = r["prof"]["ft_k"]
+        B1 = int(wl.Re[:, 0].max() - wl.Re[:, 0].min() + 1)
+        NW = nb * nb * (1 + nm)
+        outs = float(QB) * nk * NW
+        return {"kernel": "k_axis_dft (axis 1 of the sum-factorised Re->k contraction)",
+                "complex_terms_per_output": B1, "outputs_per_step": outs,
+                "stage_ms_per_step": ft_ms / args.steps,
+                "note": "stage ft_k also holds the scatter and the axis-3, axis-2 transforms"}
+
+    def roof_band(r):
+        bd_ms, bd_n = r["prof"]["band"]
+        cmac = 2.0 * nb ** 3 * nm * QB * nk          # V_kq^H G3 V_k per (q,k) pair
+        t = bd_ms / max(args.steps, 1) * 1e-3
+        ach = 8.0 * cmac / t
+        return {"bound": "alu", "kernel": "k_band_rotate (FP64)", "achieved": ach / 1e12,
+                "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_FLOPS,
+                "flop_per_cmac": 8}
+
+    def roof_eig(r):
+        eg_ms, eg_n = r["prof"]["eig"]
+        per = EIG_FP64_FLOPS.get((nb, "fp64"))
+        t = eg_ms / max(eg_n, 1) * 1e-3
+        mats = float(args.steps) * QB * nk / max(eg_n, 1)
+        ach = per * mats / t if per else None
+        return {"bound": "alu", "kernel": "k_jacobi_mixed<%d> (FP32 sweeps, FP64 Newton-Schulz, V^H A V, FP64 "
+                                          "sweeps)" % (nb + (nb & 1)),
+                "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_FLOPS if ach else None,
+                "fp64_flop_per_matrix": per, "matrices_per_launch": mats,
+                "traffic": TRAFFIC.get(("k_jacobi_mixed", args.workload, QB)),
+                "algorithmic_bytes": mats * (nb * nb * 16 + nb * nb * 16 + nb * 8),
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
+
+    def dominant_roofline(r):
+        st = {k: v[0] for k, v in r["prof"].items()}
+        top = max(("ft_k", "eig", "band"), key=lambda s: st.get(s, 0.0))
+        if top == "eig":
+            return roof_eig(r)
+        if top == "band":
+            return roof_band(r)
+        return roof_fp64(r)
 
     def roof_fp64(r):
         ft_ms, ft_n = r["prof"]["ft_k"]
@@ -400,18 +465,36 @@ def run_libeph(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if forms[0] == "fp64" else "bf16-digits/f32",
                 "data": "synthetic",
                 "config": {"workload": describe(wl, args), "form": forms[0], "q_batch": QB,
+                           "k_path": ("uniform grid %dx%dx%d, sum-factorised Re->k (eph_set_k_grid)" % wl.kgrid)
+                           if legs[0][1] else "k list, dense Re->k GEMM (eph_set_k)",
                            "l2": "inputs larger than L2: g(Re,Rp) 287 MB, P_k 221 MB resident; "
                                  f"g out {head['g_bytes'] / 1e9:.2f} GB per step",
                            "k_setup_ms": head["setk_ms"], "k_setup_share_ms": head["setk_share_ms"],
                            "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in head["prof"].items()},
                            "parity": "FP64 form vs FP64 CPU oracle: max rel err <= 1e-12 (eps, omega, |g|^2 "
                                      "subspace sums); tests/test_gpu_parity.py"},
-                "roofline": roof_fp64(head) if forms[0] == "fp64" else roof_tc(head),
+                "roofline": dominant_roofline(head) if forms[0] == "fp64" else roof_tc(head),
                 "gpu_launches": head["launches"], "clocks": head["clocks"]}
-        if "mixed" in res and forms[0] == "fp64":
-            m = res["mixed"]
+        if forms[0] == "fp64":
+            line["stage_rooflines"] = {"band": roof_band(head)}
+            if legs[0][1]:
+                line["stage_rooflines"]["ft_k"] = roof_axis(head)
+        if ("fp64", False) in res and legs[0] != ("fp64", False):
+            fl = res[("fp64", False)]
+            line["fp64_k_list"] = {"value": fl["value"], "unit": UNIT, "ms_per_step": fl["ms_per_step"],
+                                   "what": "FP64 form on the same k points as a plain k list (dense Re->k GEMM)",
+                                   "stage_ms_per_step": {k: round(v[0] / args.steps, 3)
+                                                         for k, v in fl["prof"].items()},
+                                   "roofline": roof_fp64(fl), "gpu_launches": fl["launches"],
+                                   "clocks": fl["clocks"]}
+        if ("mixed", False) in res and forms[0] == "fp64":
+            m = res[("mixed", False)]
+            base = res[("fp64", False)]
             line["mixed"] = {"value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"],
-                             "gain_vs_fp64": m["value"] / head["value"], "dtype": "bf16 digits / f32 accumulate",
+                             "k_path": "k list, Re->k on tcgen05",
+                             "gain_vs_fp64": m["value"] / base["value"],
+                             "gain_vs": "FP64 form on the same k list (dense GEMM)",
+                             "dtype": "bf16 digits / f32 accumulate",
                              "rel_err_bar": "<= 1e-6 on |g|^2 subspace sums (measured 2.1e-7 si_full, "
                                             "tests/test_gpu_mixed.py); eps, omega FP64 (1e-12)",
                              "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in m["prof"].items()},
@@ -419,7 +502,7 @@ def run_libeph(args):
                              "clocks": m["clocks"]}
 
     # end to end through the public C-ABI with HOST buffers (pinned), copies inside the timed region
-    def e2e(form):
+    def e2e(form, grid=False):
         gdt = torch.complex128 if form == "fp64" else torch.complex64
         hctx = binding.Context.from_workload(wl, form=form, device_ptrs=False, q_batch=QB)
         kp_h = torch.from_numpy(wl.kpts).pin_memory()
@@ -429,7 +512,10 @@ def run_libeph(args):
         ekq_h = torch.empty(QB, nk, nb, dtype=torch.float64).pin_memory()
         om_h = torch.empty(QB, nm, dtype=torch.float64).pin_memory()
         t0 = time.perf_counter()
-        hctx.eph_set_k(nk, kp_h, epsk_h)
+        if grid:
+            hctx.eph_set_k_grid(*wl.kgrid, None, epsk_h)
+        else:
+            hctx.eph_set_k(nk, kp_h, epsk_h)
         t_setk = time.perf_counter() - t0
         for i in range(args.warmup):
             hctx.eph_interp_q(QB, q_h[i * QB:(i + 1) * QB], ekq_h, om_h, g_h)
@@ -446,11 +532,11 @@ def run_libeph(args):
         return out
 
     if rank == 0 and not args.no_e2e:
-        line["e2e"] = e2e(forms[0])
+        line["e2e"] = e2e(forms[0], grid=legs[0][1])
         if "mixed" in line:
             line["mixed"]["e2e"] = e2e("mixed")
     if rank == 0 and not args.no_linewidths:
-        line["linewidths"] = time_linewidths(wl, args, q_dev, k_dev, dev, QB)
+        line["linewidths"] = time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=legs[0][1])
     if rank == 0 and not args.no_backward:
         line["backward"] = time_backward(args)
     if rank == 0 and not args.no_cpu_baseline:

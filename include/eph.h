@@ -91,9 +91,10 @@ void eph_default_options(eph_options* opt);
  *   cuda_stream             cudaStream_t to order all work on; NULL = a stream the
  *                           context creates and owns
  * All inputs are HOST pointers; they are copied and may be freed on return.
- * Supported sizes: 1 <= nb <= 16 and 1 <= nm <= 16 (batched warp Jacobi);
- * larger sizes return EPH_ENOTSUP.  On success *out owns device memory until
- * eph_destroy.
+ * Supported sizes: 1 <= nb, nm <= 16 in both forms (warp-resident Jacobi and
+ * rotations); up to 256 in the FP64 form (one CTA per eigensolve, GEMM rotations;
+ * forward only); larger sizes, and the mixed form beyond 16, return EPH_ENOTSUP.
+ * On success *out owns device memory until eph_destroy.
  */
 int eph_create(eph_ctx** out, int nb, int na, int ne, int np,
                const double* H_Re, const double* Phi_Rp, const double* g_ReRp,
@@ -107,6 +108,21 @@ int eph_create(eph_ctx** out, int nb, int na, int ne, int np,
  *   eps_k [nk][nb] eV ascending, may be NULL (host or device)
  */
 int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k);
+
+/*
+ * Sets the fine k list to the uniform grid k = (j1/n1, j2/n2, j3/n3) + shift, k index
+ * (j1 n2 + j2) n3 + j3 (j3 fastest), and computes what eph_set_k computes for it.
+ * On such a grid the phase of Eq. 10 (and of the H(k+q) sum of Eq. 4) factorises per
+ * axis, e^{2 pi i k.Re} = prod_a e^{2 pi i k_a n_a}, so later eph_interp_q,
+ * eph_linewidths calls evaluate the Re->k contraction as three one-axis transforms over
+ * the bounding box of the Re list (B_a terms per output instead of ne): the same sum,
+ * term for term, to rounding.  Used in the FP64 form when the Re vectors are distinct
+ * and their box has extents <= 32 and volume <= 8 ne; otherwise the general path runs
+ * on the generated k list.
+ *   shift [3] HOST pointer (NULL = 0); eps_k [nk][nb] as in eph_set_k (may be NULL).
+ * EPH_EINVAL for n_a < 1 or nk > 2^31 - 1.
+ */
+int eph_set_k_grid(eph_ctx* ctx, int n1, int n2, int n3, const double* shift, double* eps_k);
 
 /*
  * Interpolates for nq q points against the resident k list (paper Eqs. 9-10
@@ -187,8 +203,8 @@ long long eph_kernel_launches(const eph_ctx* ctx);
 enum eph_stage {
   EPH_STAGE_PHASE = 0, /* phase factors e^{i k.R} (exact FP64 reduction + sincospi)             */
   EPH_STAGE_FT_Q = 1,  /* Rp->q contraction of g (Eq. 9) and D(q)                              */
-  EPH_STAGE_EIG = 2,   /* batched Hermitian Jacobi eigensolves of H(k), H(k+q), D(q)            */
-  EPH_STAGE_MODE = 3,  /* mode rotation by u(q), phonon post-processing, per-q operand assembly */
+  EPH_STAGE_EIG = 2,   /* batched Hermitian Jacobi eigensolves of H(k), H(k+q)                   */
+  EPH_STAGE_MODE = 3,  /* D(q) eigensolve, mode rotation by u(q), per-q operand assembly         */
   EPH_STAGE_FT_K = 4,  /* Re->k contraction (Eq. 10 Fourier sum) fused with H(k+q)              */
   EPH_STAGE_BAND = 5,  /* band rotation V_{k+q}^H G V_k                                         */
   EPH_STAGE_ADJ = 6,   /* adjoint (backward) kernels                                            */

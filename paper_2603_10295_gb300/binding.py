@@ -23,7 +23,8 @@ FORMS = {"fp64": 0, "mixed": 1}
 EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "eph_interp",
            "eph_interp_backward", "eph_destroy", "eph_strerror", "eph_last_error", "eph_kernel_launches",
            "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc",
-           "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths", "eph_interp_vjp")
+           "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths", "eph_interp_vjp",
+           "eph_set_k_grid")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -92,6 +93,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_linewidths.restype = i
     lib.eph_interp_vjp.argtypes = [vp, i, dp, i, dp, vp, dp]
     lib.eph_interp_vjp.restype = i
+    lib.eph_set_k_grid.argtypes = [vp, i, i, i, dp, dp]
+    lib.eph_set_k_grid.restype = i
     del ip
     if path is None:
         _lib = lib
@@ -201,6 +204,11 @@ class Context:
         self._check(self.lib.eph_set_k(self.handle, int(nk), _ptr(kpts), _ptr(eps_k)))
         self.nk = int(nk)
 
+    def eph_set_k_grid(self, n1, n2, n3, shift=None, eps_k=None):
+        sh = None if shift is None else np.ascontiguousarray(shift, dtype=np.float64)
+        self._check(self.lib.eph_set_k_grid(self.handle, int(n1), int(n2), int(n3), _ptr(sh), _ptr(eps_k)))
+        self.nk = int(n1) * int(n2) * int(n3)
+
     def eph_interp_q(self, nq, qpts, eps_kq=None, omega=None, g=None):
         self._check(self.lib.eph_interp_q(self.handle, int(nq), _ptr(qpts), _ptr(eps_kq), _ptr(omega), _ptr(g)))
 
@@ -249,6 +257,11 @@ class Context:
         kpts = np.ascontiguousarray(kpts, dtype=np.float64)
         eps_k = np.empty((len(kpts), self.nb))
         self.eph_set_k(len(kpts), kpts, eps_k)
+        return eps_k
+
+    def set_k_grid(self, n1, n2, n3, shift=None):
+        eps_k = np.empty((int(n1) * int(n2) * int(n3), self.nb))
+        self.eph_set_k_grid(n1, n2, n3, shift, eps_k)
         return eps_k
 
     def interp_q(self, qpts, want_g=True):

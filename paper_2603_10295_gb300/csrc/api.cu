@@ -11,6 +11,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -95,6 +96,14 @@ struct eph_ctx {
   DBuf jwork, ut, Tbuf;
   // linewidth consumer: q weights, per-(q,k) partials, accumulator
   DBuf wqb, lwpart, lwacc;
+  // product k grid (sum-factorised Re->k): bounding box of the Re list, axis phase tables,
+  // the scattered W_q box and the two partial transforms of a q batch
+  bool boxable = false;  // Re vectors distinct, box extents <= 32, box volume <= 8 ne
+  int bmin[3] = {0, 0, 0}, bext[3] = {1, 1, 1};
+  bool has_grid = false;
+  int gn[3] = {0, 0, 0};
+  double gshift[3] = {0.0, 0.0, 0.0};
+  DBuf rebox, E1, E2, E3, Wbox, S1, S2;
   long long launches = 0;
   std::string err;
   // per-stage event timing
@@ -296,7 +305,8 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->eps_tile, &ctx->Ukq, &ctx->g_stage, &ctx->wk, &ctx->G2bar, &ctx->G1bar,
                   &ctx->Lpair, &ctx->Lacc, &ctx->grad, &ctx->Ahi, &ctx->Alo, &ctx->Bhi, &ctx->Blo,
                   &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut,
-                  &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc};
+                  &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc, &ctx->rebox, &ctx->E1,
+                  &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -407,6 +417,40 @@ int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re
   delete[] wones_e;
   delete[] wones_p;
   if (rc != EPH_OK) return bail(rc);
+  {  // bounding box of the Re list for the product-grid path
+    int lo[3] = {Re[0], Re[1], Re[2]}, hi[3] = {Re[0], Re[1], Re[2]};
+    for (int e = 0; e < ne; ++e)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], Re[3 * e + d]);
+        hi[d] = std::max(hi[d], Re[3 * e + d]);
+      }
+    long vol = 1;
+    bool ok = true;
+    for (int d = 0; d < 3; ++d) {
+      ctx->bmin[d] = lo[d];
+      ctx->bext[d] = hi[d] - lo[d] + 1;
+      ok = ok && ctx->bext[d] <= 32;
+      vol *= ctx->bext[d];
+    }
+    ok = ok && vol <= 8L * ne;
+    if (ok) {
+      std::vector<int> box((size_t)ne);
+      std::vector<char> seen((size_t)vol, 0);
+      for (int e = 0; e < ne && ok; ++e) {
+        const int b = ((Re[3 * e] - lo[0]) * ctx->bext[1] + (Re[3 * e + 1] - lo[1])) * ctx->bext[2] +
+                      (Re[3 * e + 2] - lo[2]);
+        ok = !seen[(size_t)b];
+        seen[(size_t)b] = 1;
+        box[(size_t)e] = b;
+      }
+      if (ok) {
+        if (ensure(ctx, ctx->rebox, (size_t)ne * sizeof(int)) != EPH_OK) return bail(EPH_ENOMEM);
+        if (cudaMemcpy(ctx->rebox.p, box.data(), (size_t)ne * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+          return bail(EPH_ECUDA);
+      }
+    }
+    ctx->boxable = ok;
+  }
   // status[0]: Jacobi sweep cap reached; status[1]: tensor-core pipeline wait timed out
   if (cudaMalloc(&ctx->status, 2 * sizeof(int)) != cudaSuccess ||
       cudaMemset(ctx->status, 0, 2 * sizeof(int)) != cudaSuccess)
@@ -452,17 +496,59 @@ int finish(eph_ctx* ctx) {
 
 }  // namespace
 
+namespace {
+int set_k_resident(eph_ctx* ctx, int nk, double* eps_k);
+}
+
 extern "C" int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k) {
   if (!ctx) return EPH_EINVAL;
   if (nk < 1 || !kpts) return fail(ctx, EPH_EINVAL, "eph_set_k: nk < 1 or kpts NULL");
   ctx->k_ready = false;
-  const int nb = ctx->nb, ne = ctx->ne, nb2 = nb * nb;
+  ctx->has_grid = false;
   const void* dk = nullptr;
   EPH_TRY(stage_in(ctx, ctx->kpts, kpts, (size_t)nk * 3 * sizeof(double), &dk));
   if (ctx->opt.device_ptrs) {  // keep a private copy: the k list must outlive the caller's buffer
     EPH_TRY(ensure(ctx, ctx->kpts, (size_t)nk * 3 * sizeof(double)));
     EPH_CK(cudaMemcpyAsync(ctx->kpts.p, dk, (size_t)nk * 3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   }
+  return set_k_resident(ctx, nk, eps_k);
+}
+
+extern "C" int eph_set_k_grid(eph_ctx* ctx, int n1, int n2, int n3, const double* shift, double* eps_k) {
+  if (!ctx) return EPH_EINVAL;
+  if (n1 < 1 || n2 < 1 || n3 < 1 || (long)n1 * n2 * n3 > 2147483647L)
+    return fail(ctx, EPH_EINVAL, "eph_set_k_grid: bad grid size");
+  ctx->k_ready = false;
+  ctx->has_grid = false;
+  const double s[3] = {shift ? shift[0] : 0.0, shift ? shift[1] : 0.0, shift ? shift[2] : 0.0};
+  const int nk = n1 * n2 * n3;
+  EPH_TRY(ensure(ctx, ctx->kpts, (size_t)nk * 3 * sizeof(double)));
+  EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_grid_points(n1, n2, n3, s, as<double>(ctx->kpts), ctx->stream));
+  EPH_TRY(set_k_resident(ctx, nk, eps_k));
+  // the sum-factorised Re->k path: FP64 form, warp-sized shapes, Re inside a small box
+  const int gn[3] = {n1, n2, n3};
+  if (ctx->boxable && ctx->opt.form == EPH_FORM_FP64 && !ctx->big) {
+    DBuf* E[3] = {&ctx->E1, &ctx->E2, &ctx->E3};
+    for (int d = 0; d < 3; ++d) {
+      if ((size_t)gn[d] * ctx->bext[d] * sizeof(double2) > 160 * 1024) return EPH_OK;  // GEMM path
+    }
+    for (int d = 0; d < 3; ++d) {
+      EPH_TRY(ensure(ctx, *E[d], (size_t)gn[d] * ctx->bext[d] * sizeof(double2)));
+      EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_axis_phase(gn[d], ctx->bext[d], ctx->bmin[d], s[d],
+                                                           as<double2>(*E[d]), ctx->stream));
+      ctx->gn[d] = gn[d];
+      ctx->gshift[d] = s[d];
+    }
+    EPH_TRY(finish(ctx));
+    ctx->has_grid = true;
+  }
+  return EPH_OK;
+}
+
+namespace {
+// H(k), its eigenpairs and the k-side operands for the k list already in ctx->kpts.
+int set_k_resident(eph_ctx* ctx, int nk, double* eps_k) {
+  const int nb = ctx->nb, ne = ctx->ne, nb2 = nb * nb;
   EPH_TRY(ensure(ctx, ctx->Pk, (size_t)nk * ne * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->eps_k, (size_t)nk * nb * sizeof(double)));
   EPH_TRY(ensure(ctx, ctx->Uk, (size_t)nk * nb2 * sizeof(double2)));
@@ -497,6 +583,7 @@ extern "C" int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k
   ctx->k_ready = true;
   return EPH_OK;
 }
+}  // namespace
 
 namespace {
 
@@ -520,8 +607,13 @@ QPlan plan_q(const eph_ctx* ctx, int nq, size_t extra_per_pair) {
   const size_t budget = (size_t)ctx->opt.workspace_mb << 20;
   long KT = ctx->opt.k_tile > 0 ? ctx->opt.k_tile : (long)(budget / (per_pair * p.QB));
   if (KT > ctx->nk) KT = ctx->nk;
-  if (p.QB * KT > 65535) KT = 65535 / p.QB;  // CTA-per-matrix eigensolve grid
-  if (KT > 64) KT -= KT % 64;
+  if (ctx->big && p.QB * KT > 65535) KT = 65535 / p.QB;  // CTA-per-matrix eigensolve grid
+  if (ctx->has_grid) {  // whole j1 slabs of the grid
+    const long slab = (long)ctx->gn[1] * ctx->gn[2];
+    KT = KT < slab ? slab : KT - KT % slab;
+  } else if (KT > 64 && KT < ctx->nk) {
+    KT -= KT % 64;
+  }
   if (KT < 1) KT = 1;
   p.KT = KT;
   return p;
@@ -541,11 +633,19 @@ int ensure_q_workspace(eph_ctx* ctx, const QPlan& p, bool with_y = true) {
   if (with_y) EPH_TRY(ensure(ctx, ctx->Y, (size_t)QB * p.KT * p.NW * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->eps_tile, (size_t)QB * p.KT * nb * sizeof(double)));
   EPH_TRY(ensure(ctx, ctx->Ukq, (size_t)QB * p.KT * nb2 * sizeof(double2)));
+  if (ctx->has_grid) {
+    const long B1 = ctx->bext[0], B2 = ctx->bext[1], B3 = ctx->bext[2];
+    const long N2 = ctx->gn[1], N3 = ctx->gn[2];
+    EPH_TRY(ensure(ctx, ctx->Wbox, (size_t)QB * B1 * B2 * B3 * p.NW * sizeof(double2)));
+    EPH_TRY(ensure(ctx, ctx->S1, (size_t)QB * B1 * B2 * N3 * p.NW * sizeof(double2)));
+    EPH_TRY(ensure(ctx, ctx->S2, (size_t)QB * B1 * N2 * N3 * p.NW * sizeof(double2)));
+  }
   return EPH_OK;
 }
 
-// Per q batch, before the k loop: phases, D(q) -> omega, u; Eq. 9; W_q.
-int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb) {
+// Per q batch, before the k loop: phases, D(q) -> omega, u; Eq. 9; W_q; on a product k grid
+// (grid_stages) also the first two axis transforms of W_q.
+int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid_stages = true) {
   const int nm = ctx->nm, ne = ctx->ne, np = ctx->np, nb2 = ctx->nb * ctx->nb;
   double2* Qe = as<double2>(ctx->Qe);
   double2* Pp = as<double2>(ctx->Pp);
@@ -556,8 +656,8 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb) {
   // D(q), eigenpairs, omega and u = e / sqrt(M)
   EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny_real(nqb, (long)nm * nm, np, Pp, np, ctx->Phi, (long)nm * nm,
                                                   ctx->dscale, as<double2>(ctx->D), (long)nm * nm, ctx->stream));
-  EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, as<double2>(ctx->D), (long)nm * nm, nm, nm, nqb, as<double>(ctx->lamq), nm,
-                                  as<double2>(ctx->evq), (long)nm * nm));
+  EPH_LAUNCH_S(EPH_STAGE_MODE, eig(ctx, as<double2>(ctx->D), (long)nm * nm, nm, nm, nqb, as<double>(ctx->lamq), nm,
+                                   as<double2>(ctx->evq), (long)nm * nm));
   EPH_LAUNCH_S(EPH_STAGE_MODE, launch_phonon_post(as<double>(ctx->lamq), as<double2>(ctx->evq), nqb, nm,
                                                   ctx->invsqrtm, ctx->omega_unit, as<double>(ctx->omq),
                                                   as<double2>(ctx->uq), ctx->stream));
@@ -578,6 +678,23 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb) {
                                                         as<double2>(ctx->G1) + (long)iq * p.X, (long)ne * nb2, nb2, 0,
                                                         W + (long)iq * ne * p.NW + nb2, nb2, p.NW, 0, ne, 1, 0,
                                                         ctx->stream));
+  }
+  if (ctx->has_grid && grid_stages) {
+    // sum factorisation of Eq. 10 (and H(k+q)): W_q scattered into the Re box (with w_e),
+    // then the transforms along axes 3 and 2; axis 1 runs per k slab in k_tile_forward
+    const int B1 = ctx->bext[0], B2 = ctx->bext[1], B3 = ctx->bext[2];
+    const int N2 = ctx->gn[1], N3 = ctx->gn[2];
+    const long NW = p.NW, vol = (long)B1 * B2 * B3;
+    EPH_CK(cudaMemsetAsync(ctx->Wbox.p, 0, (size_t)nqb * vol * NW * sizeof(double2), ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_box_scatter(W, (long)ne * NW, NW, ne, (int)NW, as<int>(ctx->rebox),
+                                                         ctx->we, as<double2>(ctx->Wbox), vol * NW, nqb, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_axis_dft(as<double2>(ctx->Wbox), (long)B3 * NW, nqb * B1 * B2, NW, B3,
+                                                      as<double2>(ctx->E3), N3, 0, N3, ctx->gshift[2] == 0.0,
+                                                      as<double2>(ctx->S1), (long)N3 * NW, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_axis_dft(as<double2>(ctx->S1), (long)B2 * N3 * NW, nqb * B1,
+                                                      (long)N3 * NW, B2, as<double2>(ctx->E2), N2, 0, N2,
+                                                      ctx->gshift[1] == 0.0, as<double2>(ctx->S2),
+                                                      (long)N2 * N3 * NW, ctx->stream));
   }
   return EPH_OK;
 }
@@ -615,9 +732,19 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
 int k_tile_forward(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
   const int nb = ctx->nb, ne = ctx->ne, nb2 = nb * nb;
   double2* Y = as<double2>(ctx->Y);
-  EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nkt, (int)p.NW, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0,
-                                            as<double2>(ctx->W), p.NW, (long)ne * p.NW, Y, p.NW, (long)nkt * p.NW, nqb,
-                                            ctx->stream));
+  if (ctx->has_grid) {  // axis-1 transform of the slabs j1 in [j0, j0 + nj) (tiles are whole slabs)
+    const long slab = (long)ctx->gn[1] * ctx->gn[2];
+    const int j0 = (int)(k0 / slab), nj = (int)(nkt / slab), B1 = ctx->bext[0], N1 = ctx->gn[0];
+    const long C = slab * p.NW;
+    const int paired = ctx->gshift[0] == 0.0 && j0 == 0 && nj == N1;
+    EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_axis_dft(as<double2>(ctx->S2), (long)B1 * C, nqb, C, B1,
+                                                      as<double2>(ctx->E1), N1, j0, nj, paired, Y,
+                                                      (long)nkt * p.NW, ctx->stream));
+  } else {
+    EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nkt, (int)p.NW, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0,
+                                              as<double2>(ctx->W), p.NW, (long)ne * p.NW, Y, p.NW, (long)nkt * p.NW,
+                                              nqb, ctx->stream));
+  }
   EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, Y, p.NW, nb, nb, (long)nqb * nkt, as<double>(ctx->eps_tile), nb,
                                             as<double2>(ctx->Ukq), nb2));
   return EPH_OK;
@@ -913,7 +1040,7 @@ extern "C" int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, 
   double2* G2b = as<double2>(ctx->G2bar);
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
     const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
-    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb, false));
     for (long k0 = 0; k0 < nk; k0 += p.KT) {
       const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
       // only H(k+q) and its eigenvectors: g is linear in g(Re,Rp), so G3 itself is not needed

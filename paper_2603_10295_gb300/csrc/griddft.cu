@@ -1,0 +1,173 @@
+// Re->k contraction on a product k grid (Eq. 10, and the H(k+q) sum of Eq. 4), by sum
+// factorisation.  On k = (j1/N1 + s1, j2/N2 + s2, j3/N3 + s3) the phase of a lattice vector
+// n = (n1, n2, n3) factorises, e^{2 pi i k.n} = prod_a e^{2 pi i (j_a/N_a + s_a) n_a}, so with
+// the Re list scattered into its bounding box b = (b1, b2, b3), n_a = nmin_a + b_a,
+//   Y[j1 j2 j3][c] = sum_b1 E1[j1][b1] sum_b2 E2[j2][b2] sum_b3 E3[j3][b3] Wbox[b1 b2 b3][c]
+// is three small DFTs along one axis each (B_a terms per output instead of |Re|).  Every
+// product of the definition appears once: the result equals the direct sum up to rounding.
+#include "eph_kernels.cuh"
+
+namespace eph {
+
+// E[j][b] = exp(2 pi i (j/N + s) (nmin + b)).  The argument is reduced exactly: j n mod N in
+// integers, then frac(s n) (s n exact for the dyadic shifts used on grids is not assumed:
+// it is formed in FP64 and reduced like the k.R argument of k_phase).
+__global__ void k_axis_phase(int N, int B, int nmin, double shift, double2* __restrict__ E) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * B) return;
+  const int j = idx / B, b = idx - j * B;
+  const long n = (long)nmin + b;
+  long m = ((long)j * n) % N;
+  if (m < 0) m += N;
+  double t = (double)m / (double)N;
+  const double sn = shift * (double)n;
+  t += sn - rint(sn);
+  const double r = t - rint(t);
+  double s, c;
+  sincospi(2.0 * r, &s, &c);
+  E[idx] = make_double2(c, s);
+}
+
+cudaError_t launch_axis_phase(int N, int B, int nmin, double shift, double2* E, cudaStream_t st) {
+  const int total = N * B;
+  if (total <= 0) return cudaSuccess;
+  k_axis_phase<<<(total + 255) / 256, 256, 0, st>>>(N, B, nmin, shift, E);
+  return cudaGetLastError();
+}
+
+// Wbox[q][box[e]][c] = w_e W[q][e][c] (Wbox zeroed beforehand; box[] is injective).
+__global__ void k_box_scatter(const double2* __restrict__ W, long sWq, long ldw, int ne, int ncols,
+                              const int* __restrict__ box, const double* __restrict__ we, double2* __restrict__ Wbox,
+                              long sBq, int nq) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long per_q = (long)ne * ncols;
+  if (idx >= per_q * nq) return;
+  const int q = (int)(idx / per_q);
+  const long rem = idx - (long)q * per_q;
+  const int e = (int)(rem / ncols);
+  const int c = (int)(rem - (long)e * ncols);
+  const double2 v = W[q * sWq + (long)e * ldw + c];
+  const double w = we[e];
+  Wbox[q * sBq + (long)box[e] * ncols + c] = make_double2(w * v.x, w * v.y);
+}
+
+cudaError_t launch_box_scatter(const double2* W, long sWq, long ldw, int ne, int ncols, const int* box,
+                               const double* we, double2* Wbox, long sBq, int nq, cudaStream_t st) {
+  const long total = (long)nq * ne * ncols;
+  if (total <= 0) return cudaSuccess;
+  k_box_scatter<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(W, sWq, ldw, ne, ncols, box, we, Wbox, sBq, nq);
+  return cudaGetLastError();
+}
+
+// One axis: out[a][j - j0][c] = sum_{b < B} E[j][b] in[a][b][c] for j0 <= j < j0 + nj.
+// One thread per (a, c): the B inputs stay in registers, E (nj x B) is broadcast from shared
+// memory.  paired: the range is the whole axis with no shift, so E[N - j] = conj(E[j]) and one
+// pass over b gives both outputs j and N - j from four real sums (2 FP64 FMA per complex term
+// and output); otherwise the three-multiplication form (3 FMA per complex term).
+template <int BMAX>
+__global__ void __launch_bounds__(256) k_axis_dft(const double2* __restrict__ in, long sa_in, long C, int B,
+                                                  const double2* __restrict__ E, int N, int j0, int nj, int paired,
+                                                  double2* __restrict__ out, long sa_out) {
+  extern __shared__ double2 es[];  // [nj][B]
+  const int a = blockIdx.y;
+  for (int t = threadIdx.x; t < nj * B; t += blockDim.x) es[t] = E[(long)j0 * B + t];
+  __syncthreads();
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double xr[BMAX], xi[BMAX];
+  const double2* src = in + (long)a * sa_in + c;
+#pragma unroll
+  for (int b = 0; b < BMAX; ++b) {
+    if (b < B) {
+      const double2 v = src[(long)b * C];
+      xr[b] = v.x;
+      xi[b] = v.y;
+    } else {
+      xr[b] = 0.0;
+      xi[b] = 0.0;
+    }
+  }
+  double2* dst = out + (long)a * sa_out + c;
+  if (paired) {
+    // j = 0 .. N/2; j and N - j share the four sums
+    for (int j = 0; 2 * j <= N; ++j) {
+      const double2* e = es + j * B;
+      double p1 = 0.0, p2 = 0.0, p3 = 0.0, p4 = 0.0;  // sum c xr, s xi, c xi, s xr
+#pragma unroll
+      for (int b = 0; b < BMAX; ++b) {
+        if (b < B) {
+          const double2 w = e[b];
+          p1 = fma(w.x, xr[b], p1);
+          p2 = fma(w.y, xi[b], p2);
+          p3 = fma(w.x, xi[b], p3);
+          p4 = fma(w.y, xr[b], p4);
+        }
+      }
+      dst[(long)j * C] = make_double2(p1 - p2, p3 + p4);
+      const int jm = N - j;
+      if (j != 0 && jm != j) dst[(long)jm * C] = make_double2(p1 + p2, p3 - p4);
+    }
+  } else {
+    double xs[BMAX];
+#pragma unroll
+    for (int b = 0; b < BMAX; ++b) xs[b] = xr[b] + xi[b];
+    for (int j = 0; j < nj; ++j) {
+      const double2* e = es + j * B;
+      double t1 = 0.0, t2 = 0.0, t3 = 0.0;  // sum er xr, ei xi, (er + ei)(xr + xi)
+#pragma unroll
+      for (int b = 0; b < BMAX; ++b) {
+        if (b < B) {
+          const double2 w = e[b];
+          t1 = fma(w.x, xr[b], t1);
+          t2 = fma(w.y, xi[b], t2);
+          t3 = fma(w.x + w.y, xs[b], t3);
+        }
+      }
+      dst[(long)j * C] = make_double2(t1 - t2, t3 - t1 - t2);
+    }
+  }
+}
+
+cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
+                            int nj, int paired, double2* out, long sa_out, cudaStream_t st) {
+  if (A <= 0 || C <= 0 || nj <= 0) return cudaSuccess;
+  if (B < 1 || B > 32 || A > 65535 || j0 < 0 || j0 + nj > N) return cudaErrorInvalidValue;
+  if (paired && (j0 != 0 || nj != N)) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)nj * B * sizeof(double2);
+  if (smem > 160 * 1024) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((C + 255) / 256), (unsigned)A, 1);
+  auto go = [&](auto kern) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, 256, smem, st>>>(in, sa_in, C, B, E, N, j0, nj, paired, out, sa_out);
+    return cudaGetLastError();
+  };
+  if (B <= 8) return go(k_axis_dft<8>);
+  if (B <= 16) return go(k_axis_dft<16>);
+  return go(k_axis_dft<32>);
+}
+
+// kpts[(j1 n2 + j2) n3 + j3] = (j1/n1 + s1, j2/n2 + s2, j3/n3 + s3)
+__global__ void k_grid_points(int n1, int n2, int n3, double s1, double s2, double s3, double* __restrict__ k) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long nk = (long)n1 * n2 * n3;
+  if (idx >= nk) return;
+  const int j3 = (int)(idx % n3);
+  const long r = idx / n3;
+  const int j2 = (int)(r % n2);
+  const int j1 = (int)(r / n2);
+  k[3 * idx] = (double)j1 / (double)n1 + s1;
+  k[3 * idx + 1] = (double)j2 / (double)n2 + s2;
+  k[3 * idx + 2] = (double)j3 / (double)n3 + s3;
+}
+
+cudaError_t launch_grid_points(int n1, int n2, int n3, const double* shift, double* k, cudaStream_t st) {
+  const long nk = (long)n1 * n2 * n3;
+  if (nk <= 0) return cudaSuccess;
+  k_grid_points<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(n1, n2, n3, shift[0], shift[1], shift[2], k);
+  return cudaGetLastError();
+}
+
+}  // namespace eph
