@@ -136,6 +136,102 @@ struct Sweep<NP, NP - 1, T> {
   __device__ __forceinline__ static void run(T2 (&)[NP], T2 (&)[NP], int, int, T) {}
 };
 
+// FP64 polish round (after preconditioning every rotation is tiny): where every pair of the
+// warp has r^2 |b|^2 < 1e-12, the rotations are applied unnormalised, J/c with c^2 =
+// 1/(1 + r^2 |b|^2): the updates lose the multiplication by c (4 instead of 6 FP64 operations
+// per complex element) and no rsqrt is needed.  J/c is a scalar multiple of the unitary J on
+// its 2x2 block, so A stays Hermitian and V's columns stay orthogonal to within the product
+// of the scale deviation (< 1e-12) and later angles (< 1e-6); every lane accumulates its
+// column's scale 1 + delta (delta += eps + delta eps, eps = r^2 |b|^2) and the caller divides
+// it out at the end.  Otherwise the columns are brought back to unit scale and the round is
+// the normalised one.
+template <int NP, int R>
+__device__ __forceinline__ void polish_round(double2 (&a)[NP], double2 (&v)[NP], int j, int base, double thresh2,
+                                             double& delta) {
+  const int p = rr_partner(j, R, NP);
+  const bool lower = j < p;
+  double d = 0;
+  double2 x = make_double2(0, 0);
+#pragma unroll
+  for (int rho = 0; rho < NP; ++rho) {
+    if (rho == j) d = a[rho].x;
+    if (rho == p) x = a[rho];
+  }
+  const double dp = shfl_d(d, base + p);
+  const double2 y = shfl_d2(x, base + p);
+  const double app = lower ? d : dp;
+  const double aqq = lower ? dp : d;
+  const double2 bq = lower ? y : x;
+  const double b2 = fma(bq.x, bq.x, bq.y * bq.y);
+  double r = 0, tb = 0, eps = 0;
+  if (b2 > thresh2) {
+    const double dd = aqq - app;
+    r = copysign(2.0, dd) / (fabs(dd) + sqrt(fma(dd, dd, 4.0 * b2)));
+    tb = r * b2;
+    eps = r * r * b2;
+  }
+  if (__all_sync(0xffffffffu, eps < 1e-12)) {
+    const double2 sg = make_double2(r * bq.x, r * bq.y);  // sigma / c
+    const double2 coef = lower ? make_double2(-sg.x, sg.y) : sg;
+#pragma unroll
+    for (int rho = 0; rho < NP; ++rho) {
+      const double2 o = shfl_d2(a[rho], base + p);
+      const double2 m = a[rho];
+      a[rho] = make_double2(fma(coef.x, o.x, fma(-coef.y, o.y, m.x)), fma(coef.x, o.y, fma(coef.y, o.x, m.y)));
+    }
+#pragma unroll
+    for (int rho = 0; rho < NP; ++rho) {
+      const double2 o = shfl_d2(v[rho], base + p);
+      const double2 m = v[rho];
+      v[rho] = make_double2(fma(coef.x, o.x, fma(-coef.y, o.y, m.x)), fma(coef.x, o.y, fma(coef.y, o.x, m.y)));
+    }
+#pragma unroll
+    for (int lo = 0; lo < NP; ++lo) {
+      const int hi = rr_partner(lo, R, NP);
+      if (hi > lo) {
+        const double2 ss = shfl_d2(sg, base + lo);
+        const double2 xl = a[lo], xh = a[hi];
+        a[lo] = make_double2(fma(-ss.x, xh.x, fma(ss.y, xh.y, xl.x)), fma(-ss.x, xh.y, fma(-ss.y, xh.x, xl.y)));
+        a[hi] = make_double2(fma(ss.x, xl.x, fma(ss.y, xl.y, xh.x)), fma(ss.x, xl.y, fma(-ss.y, xl.x, xh.y)));
+      }
+    }
+    const double nd = (lower ? app - tb : aqq + tb) * (1.0 + eps);
+#pragma unroll
+    for (int rho = 0; rho < NP; ++rho) {
+      if (rho == p) a[rho] = make_double2(0, 0);
+      if (rho == j) a[rho] = make_double2(nd, 0);
+    }
+    delta = fma(delta, eps, delta + eps);
+  } else {
+    // a normalised rotation may mix two columns of different scale: first bring every column
+    // back to unit scale, A_ij /= sqrt((1 + delta_i)(1 + delta_j)), v_j /= sqrt(1 + delta_j)
+    if (__any_sync(0xffffffffu, delta != 0.0)) {
+      const double sc = fma(delta, fma(0.375, delta, -0.5), 1.0);
+#pragma unroll
+      for (int rho = 0; rho < NP; ++rho) {
+        const double f = sc * shfl_d(sc, base + rho);
+        a[rho] = make_double2(a[rho].x * f, a[rho].y * f);
+        v[rho] = make_double2(v[rho].x * sc, v[rho].y * sc);
+      }
+      delta = 0.0;
+    }
+    jacobi_round<NP, R, double>(a, v, j, base, thresh2);
+  }
+}
+
+template <int NP, int R>
+struct PolishSweep {
+  __device__ __forceinline__ static void run(double2 (&a)[NP], double2 (&v)[NP], int j, int base, double thr,
+                                             double& delta) {
+    polish_round<NP, R>(a, v, j, base, thr, delta);
+    PolishSweep<NP, R + 1>::run(a, v, j, base, thr, delta);
+  }
+};
+template <int NP>
+struct PolishSweep<NP, NP - 1> {
+  __device__ __forceinline__ static void run(double2 (&)[NP], double2 (&)[NP], int, int, double, double&) {}
+};
+
 // Off-diagonal squared Frobenius norm of the group's matrix (all lanes get it).
 template <int NP, typename T2>
 __device__ __forceinline__ auto group_off2(const T2 (&a)[NP], int j, int base) {
@@ -285,14 +381,15 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
 #pragma unroll
     for (int r = 0; r < NP; ++r) v[r] = make_double2((double)vf[r].x, (double)vf[r].y);
   }
-  // ---- FP64 Newton-Schulz steps, v_j' = 1.5 v_j - 0.5 sum_i v_i (v_i^H v_j)
-  // (non-unitarity 5e-7 -> 4e-13 -> rounding level); one step when polishing to 1e-12
-  double2 vn[NP];
+  // ---- Newton-Schulz steps V <- V (3I - V^H V)/2 = V - V E/2, E = V^H V - I: the Gram matrix in
+  // FP64; the correction V E/2 (|E| ~ 1e-7, then ~1e-14) needs only FP32's relative precision
+  // (non-unitarity after the steps: ~1e-14, then rounding level); one step when polishing to 1e-12
   const int ns_steps = polish_tol >= 1e-13 ? 1 : 2;
 #pragma unroll 1
   for (int it = 0; it < ns_steps; ++it) {
+    float2 corr[NP];
 #pragma unroll
-    for (int r = 0; r < NP; ++r) vn[r] = make_double2(1.5 * v[r].x, 1.5 * v[r].y);
+    for (int r = 0; r < NP; ++r) corr[r] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       double2 vi[NP];
@@ -303,17 +400,22 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
         gx = fma(vi[r].x, v[r].x, fma(vi[r].y, v[r].y, gx));
         gy = fma(vi[r].x, v[r].y, fma(-vi[r].y, v[r].x, gy));
       }
-      gx *= 0.5;
-      gy *= 0.5;
+      if (i == j) gx -= 1.0;
+      const float ex = (float)gx, ey = (float)gy;
 #pragma unroll
       for (int r = 0; r < NP; ++r) {
-        vn[r].x = fma(-vi[r].x, gx, fma(vi[r].y, gy, vn[r].x));
-        vn[r].y = fma(-vi[r].x, gy, fma(-vi[r].y, gx, vn[r].y));
+        const float vx = (float)vi[r].x, vy = (float)vi[r].y;
+        corr[r].x = fmaf(vx, ex, fmaf(-vy, ey, corr[r].x));
+        corr[r].y = fmaf(vx, ey, fmaf(vy, ex, corr[r].y));
       }
     }
 #pragma unroll
-    for (int r = 0; r < NP; ++r) v[r] = vn[r];
+    for (int r = 0; r < NP; ++r) {
+      v[r].x -= (double)(0.5f * corr[r].x);
+      v[r].y -= (double)(0.5f * corr[r].y);
+    }
   }
+  double2 (&vn)[NP] = v;
   // ---- A' = V^H A V:  w = A v_j (columns of A from all lanes), then A'[i][j] = v_i^H w
   {
     double2 wv[NP];
@@ -341,8 +443,6 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       a[i] = make_double2(ax, (i == j) ? 0.0 : ay);
     }
   }
-#pragma unroll
-  for (int r = 0; r < NP; ++r) v[r] = vn[r];
   // padded columns stay exact unit vectors with zero coupling
   if (j >= n) {
 #pragma unroll
@@ -360,18 +460,25 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
   const double tol2 = polish_tol * polish_tol * fro2;
   bool conv = !valid;
   int sweep = 0;
+  double delta = 0.0;  // this column's accumulated scale 1 + delta from unnormalised rotations
   while (__any_sync(0xffffffffu, !conv) && sweep < max_sweeps) {
-    Sweep<NP, 0, double>::run(a, v, j, base, thresh2);
+    PolishSweep<NP, 0>::run(a, v, j, base, thresh2, delta);
     ++sweep;
     const double off = group_off2<NP>(a, j, base);  // shuffles: every lane takes part
     if (valid && off <= tol2) conv = true;
   }
   if (valid && j == 0 && !conv) atomicOr(status, 1);
 
+  // undo the scales: column j of V carries sqrt(1 + delta), diagonal entry j carries 1 + delta
+  // (delta < 1e-10: the second-order series are exact to rounding)
   double lam = 0.0;
 #pragma unroll
   for (int r = 0; r < NP; ++r)
     if (r == j) lam = a[r].x;
+  lam = fma(-lam, delta * (1.0 - delta), lam);
+  const double vs = fma(delta, fma(0.375, delta, -0.5), 1.0);
+#pragma unroll
+  for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x * vs, v[r].y * vs);
   int rank = 0;
 #pragma unroll
   for (int i = 0; i < NP; ++i) {

@@ -79,64 +79,107 @@ cudaError_t launch_mode_rotate(const double2* G1, const double2* u, int nq, int 
   return cudaGetLastError();
 }
 
-// One CTA per (q,k) pair: stage V_k, V_{k+q} and the nm nb x nb blocks of G3 in
-// shared memory, T = G3_nu V_k, then g_nu = V_{k+q}^H T (2 nb^3 nm CMAC per pair).
+// One (q,k) pair of the band rotation in shared memory, three-multiplication complex
+// products (3 FMA per complex multiply-add instead of 4): V_k and G3 are staged with the
+// sums re + im, V_{k+q} with re - im, so that
+//   T = G3_nu V_k:          t1 = sum x.re y.re, t2 = sum x.im y.im, t3 = sum (x.re + x.im)(y.re + y.im),
+//                           T = (t1 - t2, t3 - t1 - t2);
+//   g = V_{k+q}^H T (conj): t3 = sum (x.re - x.im)(y.re + y.im), g = (t1 + t2, t3 - t1 + t2).
+struct PairSmem {
+  double2 *uk, *ukq, *G, *T;
+  double *uks, *ukqd, *Gs, *Ts;
+};
+
+__device__ __forceinline__ PairSmem pair_smem(void* base, int nb, int nm) {
+  const int nb2 = nb * nb, x = nm * nb2;
+  PairSmem p;
+  p.uk = static_cast<double2*>(base);
+  p.ukq = p.uk + nb2;
+  p.G = p.ukq + nb2;
+  p.T = p.G + x;
+  p.uks = reinterpret_cast<double*>(p.T + x);
+  p.ukqd = p.uks + nb2;
+  p.Gs = p.ukqd + nb2;
+  p.Ts = p.Gs + x;
+  return p;
+}
+
+__host__ __device__ constexpr size_t pair_smem_bytes(int nb, int nm) {
+  return (size_t)(2 * nb * nb + 2 * nm * nb * nb) * (sizeof(double2) + sizeof(double));
+}
+
+// Stages the pair and forms T = G3 V_k (all threads of the CTA; ends with a barrier).
+__device__ __forceinline__ void pair_stage1(const PairSmem& s, const double2* __restrict__ grow,
+                                            const double2* __restrict__ ukg, const double2* __restrict__ ukqg,
+                                            int nm, int nb) {
+  const int nb2 = nb * nb;
+  for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
+    const double2 a = ukg[t], b = ukqg[t];
+    s.uk[t] = a;
+    s.uks[t] = a.x + a.y;
+    s.ukq[t] = b;
+    s.ukqd[t] = b.x - b.y;
+  }
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const double2 a = grow[t];
+    s.G[t] = a;
+    s.Gs[t] = a.x + a.y;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
+    const int nu = t / nb2, rem = t - nu * nb2, a = rem / nb, n = rem - a * nb;
+    const int g0 = nu * nb2 + a * nb;
+    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      const double2 x = s.G[g0 + b], y = s.uk[b * nb + n];
+      t1 = fma(x.x, y.x, t1);
+      t2 = fma(x.y, y.y, t2);
+      t3 = fma(s.Gs[g0 + b], s.uks[b * nb + n], t3);
+    }
+    const double2 v = make_double2(t1 - t2, t3 - t1 - t2);
+    s.T[t] = v;
+    s.Ts[t] = v.x + v.y;
+  }
+  __syncthreads();
+}
+
+// g[nu][m][n] = sum_a conj(V_{k+q}[a][m]) T[nu][a][n] for element t = (nu, m, n).
+__device__ __forceinline__ double2 pair_g(const PairSmem& s, int t, int nb) {
+  const int nb2 = nb * nb;
+  const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, n = rem - m * nb;
+  const int t0 = nu * nb2 + n;
+  double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+  for (int a = 0; a < nb; ++a) {
+    const double2 x = s.ukq[a * nb + m], y = s.T[t0 + a * nb];
+    t1 = fma(x.x, y.x, t1);
+    t2 = fma(x.y, y.y, t2);
+    t3 = fma(s.ukqd[a * nb + m], s.Ts[t0 + a * nb], t3);
+  }
+  return make_double2(t1 + t2, t3 - t1 + t2);
+}
+
+// One CTA per (q,k) pair: g_nu = V_{k+q}^H G3_nu V_k (2 nb^3 nm CMAC per pair).
 __global__ void __launch_bounds__(128) k_band_rotate(const double2* __restrict__ Y, long ldy,
                                                      const double2* __restrict__ Ukq,
                                                      const double2* __restrict__ Uk, int nk, int nm, int nb,
                                                      double2* __restrict__ g, long sgq) {
   extern __shared__ double2 sm[];
+  const PairSmem s = pair_smem(sm, nb, nm);
   const int nb2 = nb * nb;
-  double2* uk = sm;
-  double2* ukq = uk + nb2;
-  double2* G = ukq + nb2;
-  double2* T = G + nm * nb2;
   const long pair = blockIdx.x;  // q*nk + k
   const int k = (int)(pair % nk);
   const long q = pair / nk;
-  const double2* grow = Y + pair * ldy;
-  for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
-    uk[t] = Uk[(long)k * nb2 + t];
-    ukq[t] = Ukq[pair * nb2 + t];
-  }
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) G[t] = grow[t];
-  __syncthreads();
-  // T[nu][a][n] = sum_b G[nu][a][b] uk[b][n]
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
-    const int nu = t / nb2, rem = t - nu * nb2;
-    const int a = rem / nb, n = rem - a * nb;
-    const double2* gr = G + nu * nb2 + a * nb;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int b = 0; b < nb; ++b) {
-      const double2 x = gr[b], y = uk[b * nb + n];
-      acc.x = fma(x.x, y.x, fma(-x.y, y.y, acc.x));
-      acc.y = fma(x.x, y.y, fma(x.y, y.x, acc.y));
-    }
-    T[t] = acc;
-  }
-  __syncthreads();
-  // g[nu][m][n] = sum_a conj(ukq[a][m]) T[nu][a][n]
+  pair_stage1(s, Y + pair * ldy, Uk + (long)k * nb2, Ukq + pair * nb2, nm, nb);
   double2* out = g + q * sgq + (long)k * nm * nb2;
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
-    const int nu = t / nb2, rem = t - nu * nb2;
-    const int m = rem / nb, n = rem - m * nb;
-    const double2* tc = T + nu * nb2 + n;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int a = 0; a < nb; ++a) {
-      const double2 x = ukq[a * nb + m], y = tc[a * nb];
-      acc.x = fma(x.x, y.x, fma(x.y, y.y, acc.x));
-      acc.y = fma(x.x, y.y, fma(-x.y, y.x, acc.y));
-    }
-    out[t] = acc;
-  }
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) out[t] = pair_g(s, t, nb);
 }
 
 cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
                                int nm, int nb, double2* g, long sgq, cudaStream_t st) {
   long pairs = (long)nq * nk;
   if (pairs <= 0) return cudaSuccess;
-  size_t smem = (size_t)(2 * nb * nb + 2 * nm * nb * nb) * sizeof(double2);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const size_t smem = pair_smem_bytes(nb, nm);
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_band_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -145,10 +188,6 @@ cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, c
   k_band_rotate<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq);
   return cudaGetLastError();
 }
-
-}  // namespace eph
-
-namespace eph {
 
 // Fused consumer: the band rotation of one (q,k) pair into shared memory, then the
 // pair's contribution to the electron linewidth of each band n,
@@ -165,61 +204,34 @@ __global__ void __launch_bounds__(128) k_band_linewidth(const double2* __restric
                                                         int nk, int nm, int nb, double kT, double mu, double sigma,
                                                         double omega_min, double* __restrict__ part) {
   extern __shared__ double2 sm[];
+  const PairSmem s = pair_smem(sm, nb, nm);
   const int nb2 = nb * nb;
-  double2* uk = sm;
-  double2* ukq = uk + nb2;
-  double2* G = ukq + nb2;
-  double2* T = G + nm * nb2;
-  double* fm = reinterpret_cast<double*>(T + nm * nb2);  // [nb] occupations at k+q
-  double* nbose = fm + nb;                                // [nm] Bose factors (0 for excluded modes)
+  double* fm = reinterpret_cast<double*>(reinterpret_cast<char*>(sm) + pair_smem_bytes(nb, nm));  // [nb] at k+q
+  double* nbose = fm + nb;  // [nm] Bose factors (0 for excluded modes)
   const long pair = blockIdx.x;
   const int k = (int)(pair % nk);
   const long q = pair / nk;
-  const double2* grow = Y + pair * ldy;
-  for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
-    uk[t] = Uk[(long)k * nb2 + t];
-    ukq[t] = Ukq[pair * nb2 + t];
-  }
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) G[t] = grow[t];
   for (int t = threadIdx.x; t < nb; t += blockDim.x) fm[t] = 1.0 / (exp((epskq[pair * nb + t] - mu) / kT) + 1.0);
   for (int t = threadIdx.x; t < nm; t += blockDim.x) {
     const double w = om[q * nm + t];
     nbose[t] = (w > omega_min) ? 1.0 / expm1(w / kT) : 0.0;
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
-    const int nu = t / nb2, rem = t - nu * nb2, a = rem / nb, n = rem - a * nb;
-    const double2* gr = G + nu * nb2 + a * nb;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int b = 0; b < nb; ++b) {
-      const double2 x = gr[b], y = uk[b * nb + n];
-      acc.x = fma(x.x, y.x, fma(-x.y, y.y, acc.x));
-      acc.y = fma(x.x, y.y, fma(x.y, y.x, acc.y));
-    }
-    T[t] = acc;
-  }
-  __syncthreads();
+  pair_stage1(s, Y + pair * ldy, Uk + (long)k * nb2, Ukq + pair * nb2, nm, nb);
   // each thread forms one g_{m n nu} and its term; the terms overwrite G (free after T)
   const double inv = 1.0 / (sigma * sqrt(2.0 * 3.141592653589793238));
   const double c = -0.5 / (sigma * sigma);
-  double* term = reinterpret_cast<double*>(G);  // [nu][m][n]
+  double* term = reinterpret_cast<double*>(s.G);  // [nu][m][n]
   for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
     const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, n = rem - m * nb;
     const double w = om[q * nm + nu];
     double v = 0.0;
     if (w > omega_min) {
-      const double2* tc = T + nu * nb2 + n;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int a = 0; a < nb; ++a) {
-        const double2 x = ukq[a * nb + m], y = tc[a * nb];
-        acc.x = fma(x.x, y.x, fma(x.y, y.y, acc.x));
-        acc.y = fma(x.x, y.y, fma(-x.y, y.x, acc.y));
-      }
+      const double2 gv = pair_g(s, t, nb);
       const double nB = nbose[nu], f = fm[m];
       const double de = epsk[(long)k * nb + n] - epskq[pair * nb + m];
       const double xa = de + w, xe = de - w;
       const double d = (nB + f) * exp(c * xa * xa) + (nB + 1.0 - f) * exp(c * xe * xe);
-      v = fma(acc.x, acc.x, acc.y * acc.y) / (2.0 * w) * d;
+      v = fma(gv.x, gv.x, gv.y * gv.y) / (2.0 * w) * d;
     }
     term[t] = v;
   }
@@ -237,8 +249,8 @@ cudaError_t launch_band_linewidth(const double2* Y, long ldy, const double2* Ukq
                                   cudaStream_t st) {
   const long pairs = (long)nq * nk;
   if (pairs <= 0) return cudaSuccess;
-  const size_t smem = (size_t)(2 * nb * nb + 2 * nm * nb * nb) * sizeof(double2) + (size_t)(nb + nm) * sizeof(double);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const size_t smem = pair_smem_bytes(nb, nm) + (size_t)(nb + nm) * sizeof(double);
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_band_linewidth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
