@@ -362,14 +362,15 @@ def run_libeph(args):
     k_dev = torch.from_numpy(wl.kpts).to(dev)
 
     use_grid = args.k_path == "grid" and wl.kgrid is not None
-    # (form, grid) legs: the headline first, then the dense-GEMM k-list path of both forms
+    # (form, grid) legs: the headline first, the mixed form on the same path, then the
+    # dense-GEMM k-list path of both forms
     legs = [("fp64", use_grid)]
     if args.form == "mixed":
-        legs = [("mixed", False)]
+        legs = [("mixed", use_grid)]
     elif not args.fp64_only:
+        legs.append(("mixed", use_grid))
         if use_grid:
-            legs.append(("fp64", False))
-        legs.append(("mixed", False))
+            legs += [("fp64", False), ("mixed", False)]
     res = {(f, gr): time_form(wl, f, args, q_dev, k_dev, rank, world, local, dev, QB, use_grid=gr) for f, gr in legs}
     head = res[legs[0]]
     forms = [legs[0][0]]
@@ -479,27 +480,32 @@ def run_libeph(args):
             line["stage_rooflines"] = {"band": roof_band(head)}
             if legs[0][1]:
                 line["stage_rooflines"]["ft_k"] = roof_axis(head)
-        if ("fp64", False) in res and legs[0] != ("fp64", False):
-            fl = res[("fp64", False)]
-            line["fp64_k_list"] = {"value": fl["value"], "unit": UNIT, "ms_per_step": fl["ms_per_step"],
-                                   "what": "FP64 form on the same k points as a plain k list (dense Re->k GEMM)",
-                                   "stage_ms_per_step": {k: round(v[0] / args.steps, 3)
-                                                         for k, v in fl["prof"].items()},
-                                   "roofline": roof_fp64(fl), "gpu_launches": fl["launches"],
-                                   "clocks": fl["clocks"]}
-        if ("mixed", False) in res and forms[0] == "fp64":
-            m = res[("mixed", False)]
-            base = res[("fp64", False)]
+        if ("mixed", use_grid) in res and forms[0] == "fp64":
+            m = res[("mixed", use_grid)]
             line["mixed"] = {"value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"],
-                             "k_path": "k list, Re->k on tcgen05",
-                             "gain_vs_fp64": m["value"] / base["value"],
-                             "gain_vs": "FP64 form on the same k list (dense GEMM)",
-                             "dtype": "bf16 digits / f32 accumulate",
-                             "rel_err_bar": "<= 1e-6 on |g|^2 subspace sums (measured 2.1e-7 si_full, "
-                                            "tests/test_gpu_mixed.py); eps, omega FP64 (1e-12)",
+                             "k_path": line["config"]["k_path"],
+                             "gain_vs_fp64": m["value"] / head["value"],
+                             "dtype": "f64 Re->k and eigensolve polish, double-float band rotation, c64 g"
+                                      if use_grid else "bf16 digits / f32 accumulate",
+                             "rel_err_bar": "<= 1e-6 on |g|^2 subspace sums (tests/test_gpu_mixed.py, "
+                                            "tests/test_gpu_grid.py); eps, omega <= 1e-10",
                              "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in m["prof"].items()},
-                             "roofline_tensor_kernel": roof_tc(m), "gpu_launches": m["launches"],
-                             "clocks": m["clocks"]}
+                             "gpu_launches": m["launches"], "clocks": m["clocks"]}
+            if not use_grid:
+                line["mixed"]["roofline_tensor_kernel"] = roof_tc(m)
+        if use_grid and ("fp64", False) in res:
+            fl, ml = res[("fp64", False)], res[("mixed", False)]
+            line["k_list"] = {
+                "what": "the same k points as a plain k list: dense Re->k GEMM (FP64) or tcgen05 (mixed)",
+                "fp64": {"value": fl["value"], "unit": UNIT, "ms_per_step": fl["ms_per_step"],
+                         "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in fl["prof"].items()},
+                         "roofline": roof_fp64(fl), "gpu_launches": fl["launches"], "clocks": fl["clocks"]},
+                "mixed": {"value": ml["value"], "unit": UNIT, "ms_per_step": ml["ms_per_step"],
+                          "gain_vs_fp64": ml["value"] / fl["value"], "dtype": "bf16 digits / f32 accumulate",
+                          "rel_err_bar": "<= 1e-6 on |g|^2 subspace sums (measured 2.1e-7 si_full)",
+                          "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in ml["prof"].items()},
+                          "roofline_tensor_kernel": roof_tc(ml), "gpu_launches": ml["launches"],
+                          "clocks": ml["clocks"]}}
 
     # end to end through the public C-ABI with HOST buffers (pinned), copies inside the timed region
     def e2e(form, grid=False):
@@ -534,7 +540,7 @@ def run_libeph(args):
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(forms[0], grid=legs[0][1])
         if "mixed" in line:
-            line["mixed"]["e2e"] = e2e("mixed")
+            line["mixed"]["e2e"] = e2e("mixed", grid=use_grid)
     if rank == 0 and not args.no_linewidths:
         line["linewidths"] = time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=legs[0][1])
     if rank == 0 and not args.no_backward:

@@ -116,9 +116,10 @@ int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k);
  * axis, e^{2 pi i k.Re} = prod_a e^{2 pi i k_a n_a}, so later eph_interp_q,
  * eph_linewidths calls evaluate the Re->k contraction as three one-axis transforms over
  * the bounding box of the Re list (B_a terms per output instead of ne): the same sum,
- * term for term, to rounding.  Used in the FP64 form when the Re vectors are distinct
- * and their box has extents <= 32 and volume <= 8 ne; otherwise the general path runs
- * on the generated k list.
+ * term for term, to rounding.  Used when nb, nm <= 16, the Re vectors are distinct and
+ * their box has extents <= 32 and volume <= 8 ne; otherwise the general path runs on the
+ * generated k list.  In the mixed form the contraction is then FP64 as well and only the
+ * band rotation runs in double-float arithmetic on the FP32 pipe (g complex64).
  *   shift [3] HOST pointer (NULL = 0); eps_k [nk][nb] as in eph_set_k (may be NULL).
  * EPH_EINVAL for n_a < 1 or nk > 2^31 - 1.
  */

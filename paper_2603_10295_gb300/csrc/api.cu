@@ -525,9 +525,9 @@ extern "C" int eph_set_k_grid(eph_ctx* ctx, int n1, int n2, int n3, const double
   EPH_TRY(ensure(ctx, ctx->kpts, (size_t)nk * 3 * sizeof(double)));
   EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_grid_points(n1, n2, n3, s, as<double>(ctx->kpts), ctx->stream));
   EPH_TRY(set_k_resident(ctx, nk, eps_k));
-  // the sum-factorised Re->k path: FP64 form, warp-sized shapes, Re inside a small box
+  // the sum-factorised Re->k path: warp-sized shapes, Re inside a small box
   const int gn[3] = {n1, n2, n3};
-  if (ctx->boxable && ctx->opt.form == EPH_FORM_FP64 && !ctx->big) {
+  if (ctx->boxable && !ctx->big) {
     DBuf* E[3] = {&ctx->E1, &ctx->E2, &ctx->E3};
     for (int d = 0; d < 3; ++d) {
       if ((size_t)gn[d] * ctx->bext[d] * sizeof(double2) > 160 * 1024) return EPH_OK;  // GEMM path
@@ -705,6 +705,11 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
   const int nb = ctx->nb, nm = ctx->nm, nb2 = nb * nb;
   double2* Y = as<double2>(ctx->Y);
   const double2* Uk = as<double2>(ctx->Uk) + k0 * nb2;
+  if (ctx->opt.form == EPH_FORM_MIXED) {  // product-grid path of the mixed form: complex64 g, sgq in elements
+    EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_rotate_ff_f64(Y + nb2, p.NW, as<double2>(ctx->Ukq), Uk, nqb, nkt, nm,
+                                                               nb, reinterpret_cast<float2*>(out), sgq, ctx->stream));
+    return EPH_OK;
+  }
   if (!ctx->big) {
     EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, as<double2>(ctx->Ukq), Uk, nqb, nkt, nm, nb, out,
                                                     sgq, ctx->stream));
@@ -894,10 +899,12 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
   if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
   if (ctx->opt.async && !ctx->opt.device_ptrs) return fail(ctx, EPH_EINVAL, "async mode needs device pointers");
-  if (ctx->opt.form == EPH_FORM_MIXED) return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
+  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid) return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
+  // FP64 form, and the mixed form on a product k grid (FP64 Re->k, complex64 band rotation)
   const int nb = ctx->nb, nm = ctx->nm, nk = ctx->nk;
   const int nb2 = nb * nb;
   const bool host = !ctx->opt.device_ptrs;
+  const size_t esz = ctx->opt.form == EPH_FORM_MIXED ? sizeof(float2) : sizeof(double2);
   QPlan p;
   EPH_TRY(prepare_fp64(ctx, nq, g != nullptr, &p));
   const void* dq = nullptr;
@@ -919,15 +926,18 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
                                  as<double>(ctx->eps_tile) + (long)iq * nkt * nb, (size_t)nkt * nb * sizeof(double),
                                  out_kind(ctx), ctx->stream));
       if (g) {
-        double2* gout = static_cast<double2*>(g);
+        char* gout = static_cast<char*>(g);
+        char* stage = static_cast<char*>(ctx->g_stage.p);
         if (host) {
-          EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0, as<double2>(ctx->g_stage), (long)nkt * p.gcols));
+          EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0, reinterpret_cast<double2*>(stage), (long)nkt * p.gcols));
           for (int iq = 0; iq < nqb; ++iq)
-            EPH_CK(cudaMemcpyAsync(gout + ((long)(q0 + iq) * nk + k0) * p.gcols,
-                                   as<double2>(ctx->g_stage) + (long)iq * nkt * p.gcols,
-                                   (size_t)nkt * p.gcols * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+            EPH_CK(cudaMemcpyAsync(gout + ((long)(q0 + iq) * nk + k0) * p.gcols * esz,
+                                   stage + (long)iq * nkt * p.gcols * esz, (size_t)nkt * p.gcols * esz,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
         } else {
-          EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0, gout + ((long)q0 * nk + k0) * p.gcols, (long)nk * p.gcols));
+          EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0,
+                              reinterpret_cast<double2*>(gout + ((long)q0 * nk + k0) * p.gcols * esz),
+                              (long)nk * p.gcols));
         }
       }
     }
@@ -1094,16 +1104,17 @@ extern "C" int eph_reserve(eph_ctx* ctx, int nq) {
   if (nq < 1) return fail(ctx, EPH_EINVAL, "eph_reserve: nq < 1");
   QPlan p;
   EPH_TRY(ensure(ctx, ctx->qpts, (size_t)nq * 3 * sizeof(double)));
-  if (ctx->opt.form == EPH_FORM_MIXED) return prepare_mixed(ctx, nq, true, &p);
+  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid) return prepare_mixed(ctx, nq, true, &p);
   return prepare_fp64(ctx, nq, true, &p);
 }
 
 namespace {
 struct TuneKey {
-  int form, scheme, nb, nm, ne, np, nk, nq;
+  int form, scheme, grid, nb, nm, ne, np, nk, nq;
   bool operator<(const TuneKey& o) const {
-    const int a[8] = {form, scheme, nb, nm, ne, np, nk, nq}, b[8] = {o.form, o.scheme, o.nb, o.nm, o.ne, o.np, o.nk, o.nq};
-    for (int i = 0; i < 8; ++i)
+    const int a[9] = {form, scheme, grid, nb, nm, ne, np, nk, nq};
+    const int b[9] = {o.form, o.scheme, o.grid, o.nb, o.nm, o.ne, o.np, o.nk, o.nq};
+    for (int i = 0; i < 9; ++i)
       if (a[i] != b[i]) return a[i] < b[i];
     return false;
   }
@@ -1117,7 +1128,8 @@ extern "C" int eph_autotune(eph_ctx* ctx, int nq, const double* qpts, int* q_bat
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_autotune before eph_set_k");
   if (nq < 1 || !qpts || !ctx->opt.device_ptrs || ctx->opt.async)
     return fail(ctx, EPH_EINVAL, "eph_autotune needs nq >= 1, device pointers and synchronous mode");
-  const TuneKey key{ctx->opt.form, ctx->opt.mixed_scheme, ctx->nb, ctx->nm, ctx->ne, ctx->np, ctx->nk, nq};
+  const TuneKey key{ctx->opt.form, ctx->opt.mixed_scheme, ctx->has_grid ? 1 : 0, ctx->nb, ctx->nm, ctx->ne, ctx->np,
+                    ctx->nk, nq};
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find(key);

@@ -131,6 +131,9 @@ cudaError_t launch_split_b(const double2* W, long ldw, long sW, int col0, int nc
 // Band rotation with double-float accumulation (FP64 gauges as float pairs), complex64 out.
 cudaError_t launch_band_rotate_ff(const float* Y, long ldy_floats, const double2* Ukq, const double2* Uk, int nq,
                                   int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st);
+// the same from complex128 G3 rows (product-grid path of the mixed form); g complex64, sgq in elements
+cudaError_t launch_band_rotate_ff_f64(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
+                                      int nm, int nb, float2* g, long sgq, cudaStream_t st);
 // Fixed-point BF16 digits (A: 3, B: 4 per value; exact tensor-core accumulation); D slices of n*kp / slice.
 cudaError_t make_tc_map_bf16(void* map_out, const void* base, long rows, int kp, int box_rows);
 cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, double scale, void* D, cudaStream_t st);

@@ -213,7 +213,13 @@ __device__ __forceinline__ void ff_mac2(float& sh, float& sl, float ah, float al
 }
 }  // namespace
 
-__global__ void __launch_bounds__(128) k_band_rotate_ff(const float2* __restrict__ Y, long ldy,
+__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+// G3 in complex64 (from the tensor-core contraction) or complex128 (from the FP64 grid path,
+// rounded to complex64 on load: 6e-8 relative, as the FP32 accumulation of the former).
+template <typename TIn>
+__global__ void __launch_bounds__(128) k_band_rotate_ff(const TIn* __restrict__ Y, long ldy,
                                                         const double2* __restrict__ Ukq,
                                                         const double2* __restrict__ Uk, int nk, int nm, int nb,
                                                         float2* __restrict__ g, long sgq) {
@@ -236,8 +242,8 @@ __global__ void __launch_bounds__(128) k_band_rotate_ff(const float2* __restrict
     uqr[t] = ff_split(b.x);
     uqi[t] = ff_split(b.y);
   }
-  const float2* grow = Y + pair * ldy;
-  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) G[t] = grow[t];
+  const TIn* grow = Y + pair * ldy;
+  for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) G[t] = to_f2(grow[t]);
   __syncthreads();
   // T[nu][a][n] = sum_b G[nu][a][b] V_k[b][n]
   for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
@@ -280,12 +286,30 @@ cudaError_t launch_band_rotate_ff(const float* Y, long ldy_floats, const double2
   const size_t smem = (size_t)(4 * nb * nb + 3 * nm * nb * nb) * sizeof(float2);
   if (smem > 200 * 1024 || (ldy_floats & 1) || (sgq_floats & 1)) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_band_rotate_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_band_rotate_ff<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
-  k_band_rotate_ff<<<(unsigned)pairs, 128, smem, st>>>(reinterpret_cast<const float2*>(Y), ldy_floats / 2, Ukq, Uk, nk,
-                                                        nm, nb, reinterpret_cast<float2*>(g), sgq_floats / 2);
+  k_band_rotate_ff<float2><<<(unsigned)pairs, 128, smem, st>>>(reinterpret_cast<const float2*>(Y), ldy_floats / 2, Ukq,
+                                                                Uk, nk, nm, nb, reinterpret_cast<float2*>(g),
+                                                                sgq_floats / 2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_rotate_ff_f64(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
+                                      int nm, int nb, float2* g, long sgq, cudaStream_t st) {
+  const long pairs = (long)nq * nk;
+  if (pairs <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(4 * nb * nb + 3 * nm * nb * nb) * sizeof(float2);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_band_rotate_ff<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
+  k_band_rotate_ff<double2><<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq);
   return cudaGetLastError();
 }
 

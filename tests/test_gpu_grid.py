@@ -85,7 +85,7 @@ def test_grid_linewidths_equal_list_path():
 
 
 def test_mixed_form_accepts_grid():
-    # the mixed form keeps its tensor-core path on the generated k list
+    # the mixed form on a grid: FP64 sum-factorised Re->k, double-float band rotation, complex64 g
     wl = synth.make_workload("si_tiny", nq=3)
     ctx = binding.Context.from_workload(wl, form="mixed")
     eps_k = ctx.set_k_grid(4, 3, 5)
@@ -126,3 +126,18 @@ def test_si_full_grid_sampled():
     gpu = (eps_k[ksel].cpu().numpy(), eps_kq[:, ksel].cpu().numpy(), om.cpu().numpy(), g[:, ksel].cpu().numpy())
     assert np.array_equal(wl.kpts, synth.uniform_grid(*wl.kgrid))
     check(gpu, oracle.interpolate(wl, wl.kpts[ks], qsel), TOL_FP64, "si_full grid")
+
+
+@pytest.mark.parametrize("k_tile", [0, 24])
+def test_mixed_grid_mos2_shaped(k_tile):
+    box = (synth.centred_range(6), synth.centred_range(6), range(0, 1))
+    wl = synth.make_workload("mos2", nq=4, box=box)
+    ctx = binding.Context.from_workload(wl, form="mixed", k_tile=k_tile)
+    eps_k = ctx.set_k_grid(8, 6, 1)
+    e_kq, om, g = ctx.interp_q(wl.qpts)
+    assert g.dtype == np.complex64
+    ref = oracle.interpolate(wl, grid_points(8, 6, 1), wl.qpts)
+    assert gauge.max_rel_eps(eps_k, ref[0]) <= 1e-10
+    assert gauge.max_rel_eps(e_kq, ref[1]) <= 1e-10
+    assert gauge.max_rel_omega(om, ref[2]) <= 1e-10
+    assert gauge.max_rel_S(g, ref[3], ref[0], ref[1], ref[2]) <= 1e-6
