@@ -137,11 +137,12 @@ struct Sweep<NP, NP - 1, T> {
 };
 
 // FP64 polish round (after preconditioning every rotation is tiny): where every pair of the
-// warp has r^2 |b|^2 < 1e-12, the rotations are applied unnormalised, J/c with c^2 =
+// warp has |b|^2 < 1e-11 (a_qq - a_pp)^2, the rotations are applied unnormalised, J/c with c^2 =
 // 1/(1 + r^2 |b|^2): the updates lose the multiplication by c (4 instead of 6 FP64 operations
-// per complex element) and no rsqrt is needed.  J/c is a scalar multiple of the unitary J on
-// its 2x2 block, so A stays Hermitian and V's columns stay orthogonal to within the product
-// of the scale deviation (< 1e-12) and later angles (< 1e-6); every lane accumulates its
+// per complex element), and r needs one reciprocal instead of a square root and a division.
+// J/c is a scalar multiple of the unitary J on its 2x2 block, so A stays Hermitian and V's
+// columns stay orthogonal to within the product of the scale deviations (a few 1e-11 at most)
+// and later angles (< 3e-6); every lane accumulates its
 // column's scale 1 + delta (delta += eps + delta eps, eps = r^2 |b|^2) and the caller divides
 // it out at the end.  Otherwise the columns are brought back to unit scale and the round is
 // the normalised one.
@@ -163,14 +164,17 @@ __device__ __forceinline__ void polish_round(double2 (&a)[NP], double2 (&v)[NP],
   const double aqq = lower ? dp : d;
   const double2 bq = lower ? y : x;
   const double b2 = fma(bq.x, bq.x, bq.y * bq.y);
-  double r = 0, tb = 0, eps = 0;
-  if (b2 > thresh2) {
-    const double dd = aqq - app;
-    r = copysign(2.0, dd) / (fabs(dd) + sqrt(fma(dd, dd, 4.0 * b2)));
-    tb = r * b2;
-    eps = r * r * b2;
-  }
-  if (__all_sync(0xffffffffu, eps < 1e-12)) {
+  const double dd = aqq - app;
+  // tiny rotation: |b|^2 < 1e-11 dd^2, where r = 2 sign(dd) / (|dd| + sqrt(dd^2 + 4|b|^2))
+  // = (1/dd)(1 - |b|^2/dd^2 + 2|b|^4/dd^4 - ...) to within 1e-21 relative from its first two terms
+  const bool tiny = b2 <= thresh2 || b2 < 1e-11 * (dd * dd);
+  if (__all_sync(0xffffffffu, tiny)) {
+    double r = 0.0;
+    if (b2 > thresh2) {
+      const double rd = 1.0 / dd;
+      r = rd * fma(-b2 * rd, rd, 1.0);
+    }
+    const double tb = r * b2, eps = r * r * b2;
     const double2 sg = make_double2(r * bq.x, r * bq.y);  // sigma / c
     const double2 coef = lower ? make_double2(-sg.x, sg.y) : sg;
 #pragma unroll
@@ -360,8 +364,9 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
 
   // ---- FP32 preconditioning sweeps
   double2 v[NP];
+  float2 vf[NP];  // the FP32 eigenvectors, kept for the FP32 part of the Newton-Schulz corrections
   {
-    float2 af[NP], vf[NP];
+    float2 af[NP];
 #pragma unroll
     for (int r = 0; r < NP; ++r) {
       af[r] = make_float2((float)a[r].x, (float)a[r].y);
@@ -402,11 +407,13 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       }
       if (i == j) gx -= 1.0;
       const float ex = (float)gx, ey = (float)gy;
+      // V E with V at FP32 precision: the FP32 eigenvectors (within 1e-7 of V) by shuffle,
+      // no FP64 -> FP32 conversions
 #pragma unroll
       for (int r = 0; r < NP; ++r) {
-        const float vx = (float)vi[r].x, vy = (float)vi[r].y;
-        corr[r].x = fmaf(vx, ex, fmaf(-vy, ey, corr[r].x));
-        corr[r].y = fmaf(vx, ey, fmaf(vy, ex, corr[r].y));
+        const float2 w = shfl_d2(vf[r], base + i);
+        corr[r].x = fmaf(w.x, ex, fmaf(-w.y, ey, corr[r].x));
+        corr[r].y = fmaf(w.x, ey, fmaf(w.y, ex, corr[r].y));
       }
     }
 #pragma unroll
