@@ -136,6 +136,22 @@ struct Sweep<NP, NP - 1, T> {
   __device__ __forceinline__ static void run(T2 (&)[NP], T2 (&)[NP], int, int, T) {}
 };
 
+// Undoes the column scales of unnormalised rotations (all lanes of the warp):
+// A_ij /= sqrt((1 + delta_i)(1 + delta_j)), v_j /= sqrt(1 + delta_j); delta < 1e-9, so
+// 1/sqrt(1 + delta) = 1 - delta/2 + 3 delta^2/8 to rounding.
+template <int NP>
+__device__ __forceinline__ void unit_scale(double2 (&a)[NP], double2 (&v)[NP], int base, double& delta) {
+  if (!__any_sync(0xffffffffu, delta != 0.0)) return;
+  const double sc = fma(delta, fma(0.375, delta, -0.5), 1.0);
+#pragma unroll
+  for (int rho = 0; rho < NP; ++rho) {
+    const double f = sc * shfl_d(sc, base + rho);
+    a[rho] = make_double2(a[rho].x * f, a[rho].y * f);
+    v[rho] = make_double2(v[rho].x * sc, v[rho].y * sc);
+  }
+  delta = 0.0;
+}
+
 // FP64 polish round (after preconditioning every rotation is tiny): where every pair of the
 // warp has |b|^2 < 1e-11 (a_qq - a_pp)^2, the rotations are applied unnormalised, J/c with c^2 =
 // 1/(1 + r^2 |b|^2): the updates lose the multiplication by c (4 instead of 6 FP64 operations
@@ -208,17 +224,8 @@ __device__ __forceinline__ void polish_round(double2 (&a)[NP], double2 (&v)[NP],
     delta = fma(delta, eps, delta + eps);
   } else {
     // a normalised rotation may mix two columns of different scale: first bring every column
-    // back to unit scale, A_ij /= sqrt((1 + delta_i)(1 + delta_j)), v_j /= sqrt(1 + delta_j)
-    if (__any_sync(0xffffffffu, delta != 0.0)) {
-      const double sc = fma(delta, fma(0.375, delta, -0.5), 1.0);
-#pragma unroll
-      for (int rho = 0; rho < NP; ++rho) {
-        const double f = sc * shfl_d(sc, base + rho);
-        a[rho] = make_double2(a[rho].x * f, a[rho].y * f);
-        v[rho] = make_double2(v[rho].x * sc, v[rho].y * sc);
-      }
-      delta = 0.0;
-    }
+    // back to unit scale
+    unit_scale<NP>(a, v, base, delta);
     jacobi_round<NP, R, double>(a, v, j, base, thresh2);
   }
 }
@@ -473,11 +480,52 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     ++sweep;
     const double off = group_off2<NP>(a, j, base);  // shuffles: every lane takes part
     if (valid && off <= tol2) conv = true;
+    if (__all_sync(0xffffffffu, conv)) break;
+    // first-order finish: once every remaining angle |A_ij / (A_jj - A_ii)| is below 1e-8, the
+    // eigenvalues have converged (their error is second order, below 1e-16 ||A||) and
+    // v_j += sum_i v_i A_ij / (A_jj - A_ii) completes the eigenvectors to 1e-16 (the update is
+    // anti-Hermitian to first order, so V stays unitary to the same order): one pass of
+    // NP-1 column updates instead of a sweep
+    unit_scale<NP>(a, v, base, delta);
+    double lj = 0.0;
+#pragma unroll
+    for (int r = 0; r < NP; ++r)
+      if (r == j) lj = a[r].x;
+    bool small = true;
+    double li[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      li[i] = shfl_d(lj, base + i);
+      const double gap = lj - li[i];
+      const double m2 = fma(a[i].x, a[i].x, a[i].y * a[i].y);
+      if (i != j && !(m2 <= 1e-16 * (gap * gap))) small = false;
+    }
+    if (__all_sync(0xffffffffu, small)) {
+      double2 dv[NP];
+#pragma unroll
+      for (int r = 0; r < NP; ++r) dv[r] = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        const bool use = i != j && (a[i].x != 0.0 || a[i].y != 0.0);
+        const double inv = use ? 1.0 / (lj - li[i]) : 0.0;
+        const double2 x = make_double2(a[i].x * inv, a[i].y * inv);
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+          const double2 w = shfl_d2(v[r], base + i);
+          dv[r].x = fma(w.x, x.x, fma(-w.y, x.y, dv[r].x));
+          dv[r].y = fma(w.x, x.y, fma(w.y, x.x, dv[r].y));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x + dv[r].x, v[r].y + dv[r].y);
+      conv = true;
+      break;
+    }
   }
   if (valid && j == 0 && !conv) atomicOr(status, 1);
 
   // undo the scales: column j of V carries sqrt(1 + delta), diagonal entry j carries 1 + delta
-  // (delta < 1e-10: the second-order series are exact to rounding)
+  // (delta < 1e-9: the second-order series are exact to rounding)
   double lam = 0.0;
 #pragma unroll
   for (int r = 0; r < NP; ++r)
