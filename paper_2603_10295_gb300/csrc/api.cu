@@ -98,8 +98,8 @@ struct eph_ctx {
   DBuf wqb, lwpart, lwacc;
   // product k grid (sum-factorised Re->k): bounding box of the Re list, axis phase tables,
   // the scattered W_q box and the two partial transforms of a q batch
-  bool boxable = false;  // Re vectors distinct, box extents <= 32, box volume <= 8 ne
-  int bmin[3] = {0, 0, 0}, bext[3] = {1, 1, 1};
+  bool boxable = false;  // Re vectors distinct, box extents <= 33, box volume <= 8 ne
+  int bext[3] = {1, 1, 1};  // 2 M + 1 symmetric slots per axis (M = max |n| along it)
   bool has_grid = false;
   int gn[3] = {0, 0, 0};
   double gshift[3] = {0.0, 0.0, 0.0};
@@ -417,28 +417,25 @@ int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re
   delete[] wones_e;
   delete[] wones_p;
   if (rc != EPH_OK) return bail(rc);
-  {  // bounding box of the Re list for the product-grid path
-    int lo[3] = {Re[0], Re[1], Re[2]}, hi[3] = {Re[0], Re[1], Re[2]};
+  {  // symmetric slot box of the Re list for the product-grid path: along each axis slot 0 holds
+     // n = 0 and slots 2m - 1, 2m hold n = +m, -m
+    int M[3] = {0, 0, 0};
     for (int e = 0; e < ne; ++e)
-      for (int d = 0; d < 3; ++d) {
-        lo[d] = std::min(lo[d], Re[3 * e + d]);
-        hi[d] = std::max(hi[d], Re[3 * e + d]);
-      }
+      for (int d = 0; d < 3; ++d) M[d] = std::max(M[d], std::abs(Re[3 * e + d]));
     long vol = 1;
     bool ok = true;
     for (int d = 0; d < 3; ++d) {
-      ctx->bmin[d] = lo[d];
-      ctx->bext[d] = hi[d] - lo[d] + 1;
-      ok = ok && ctx->bext[d] <= 32;
+      ctx->bext[d] = 2 * M[d] + 1;
+      ok = ok && ctx->bext[d] <= 33;
       vol *= ctx->bext[d];
     }
     ok = ok && vol <= 8L * ne;
     if (ok) {
+      auto slot = [](int n) { return n == 0 ? 0 : (n > 0 ? 2 * n - 1 : -2 * n); };
       std::vector<int> box((size_t)ne);
       std::vector<char> seen((size_t)vol, 0);
       for (int e = 0; e < ne && ok; ++e) {
-        const int b = ((Re[3 * e] - lo[0]) * ctx->bext[1] + (Re[3 * e + 1] - lo[1])) * ctx->bext[2] +
-                      (Re[3 * e + 2] - lo[2]);
+        const int b = (slot(Re[3 * e]) * ctx->bext[1] + slot(Re[3 * e + 1])) * ctx->bext[2] + slot(Re[3 * e + 2]);
         ok = !seen[(size_t)b];
         seen[(size_t)b] = 1;
         box[(size_t)e] = b;
@@ -534,8 +531,8 @@ extern "C" int eph_set_k_grid(eph_ctx* ctx, int n1, int n2, int n3, const double
     }
     for (int d = 0; d < 3; ++d) {
       EPH_TRY(ensure(ctx, *E[d], (size_t)gn[d] * ctx->bext[d] * sizeof(double2)));
-      EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_axis_phase(gn[d], ctx->bext[d], ctx->bmin[d], s[d],
-                                                           as<double2>(*E[d]), ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_PHASE,
+                   eph::launch_axis_phase(gn[d], ctx->bext[d], s[d], as<double2>(*E[d]), ctx->stream));
       ctx->gn[d] = gn[d];
       ctx->gshift[d] = s[d];
     }

@@ -82,12 +82,13 @@ cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, c
 // ---- Re->k contraction on a product k grid (sum factorisation, griddft.cu) ----------------
 // kpts[(j1 n2 + j2) n3 + j3] = (j1/n1, j2/n2, j3/n3) + shift (shift: host array of 3)
 cudaError_t launch_grid_points(int n1, int n2, int n3, const double* shift, double* k, cudaStream_t st);
-// E[j][b] = exp(2 pi i (j/N + shift)(nmin + b)), j < N, b < B
-cudaError_t launch_axis_phase(int N, int B, int nmin, double shift, double2* E, cudaStream_t st);
+// E[j][b] = exp(2 pi i (j/N + shift) n(b)), j < N, b < B; slots n(0) = 0, n(2m - 1) = m, n(2m) = -m
+cudaError_t launch_axis_phase(int N, int B, double shift, double2* E, cudaStream_t st);
 // Wbox[q][box[e]][c] = w_e W[q][e][c]
 cudaError_t launch_box_scatter(const double2* W, long sWq, long ldw, int ne, int ncols, const int* box,
                                const double* we, double2* Wbox, long sBq, int nq, cudaStream_t st);
-// out[a][j - j0][c] = sum_b E[j][b] in[a][b][c], a < A, c < C, b < B <= 32
+// out[a][j - j0][c] = sum_b E[j][b] in[a][b][c], a < A, c < C, b < B <= 33 (paired: whole unshifted
+// axis, B odd)
 cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
                             int nj, int paired, double2* out, long sa_out, cudaStream_t st);
 

@@ -1,22 +1,26 @@
 // Re->k contraction on a product k grid (Eq. 10, and the H(k+q) sum of Eq. 4), by sum
 // factorisation.  On k = (j1/N1 + s1, j2/N2 + s2, j3/N3 + s3) the phase of a lattice vector
 // n = (n1, n2, n3) factorises, e^{2 pi i k.n} = prod_a e^{2 pi i (j_a/N_a + s_a) n_a}, so with
-// the Re list scattered into its bounding box b = (b1, b2, b3), n_a = nmin_a + b_a,
+// the Re list scattered into a box of slots b = (b1, b2, b3) (zeros where no Re vector lies),
 //   Y[j1 j2 j3][c] = sum_b1 E1[j1][b1] sum_b2 E2[j2][b2] sum_b3 E3[j3][b3] Wbox[b1 b2 b3][c]
 // is three small DFTs along one axis each (B_a terms per output instead of |Re|).  Every
 // product of the definition appears once: the result equals the direct sum up to rounding.
+// Slots are symmetric: along an axis of half-width M, slot 0 holds n = 0 and slots 2m - 1,
+// 2m hold n = +m, -m (m = 1..M), so that a whole unshifted axis pairs e^{i t m} with
+// e^{-i t m} (see k_axis_dft).
 #include "eph_kernels.cuh"
 
 namespace eph {
 
-// E[j][b] = exp(2 pi i (j/N + s) (nmin + b)).  The argument is reduced exactly: j n mod N in
-// integers, then frac(s n) (s n exact for the dyadic shifts used on grids is not assumed:
-// it is formed in FP64 and reduced like the k.R argument of k_phase).
-__global__ void k_axis_phase(int N, int B, int nmin, double shift, double2* __restrict__ E) {
+__host__ __device__ __forceinline__ int slot_n(int b) { return b == 0 ? 0 : ((b & 1) ? (b + 1) / 2 : -(b / 2)); }
+
+// E[j][b] = exp(2 pi i (j/N + s) n(b)).  The argument is reduced exactly: j n mod N in
+// integers, then frac(s n) formed in FP64 and reduced like the k.R argument of k_phase.
+__global__ void k_axis_phase(int N, int B, double shift, double2* __restrict__ E) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N * B) return;
   const int j = idx / B, b = idx - j * B;
-  const long n = (long)nmin + b;
+  const long n = slot_n(b);
   long m = ((long)j * n) % N;
   if (m < 0) m += N;
   double t = (double)m / (double)N;
@@ -28,10 +32,10 @@ __global__ void k_axis_phase(int N, int B, int nmin, double shift, double2* __re
   E[idx] = make_double2(c, s);
 }
 
-cudaError_t launch_axis_phase(int N, int B, int nmin, double shift, double2* E, cudaStream_t st) {
+cudaError_t launch_axis_phase(int N, int B, double shift, double2* E, cudaStream_t st) {
   const int total = N * B;
   if (total <= 0) return cudaSuccess;
-  k_axis_phase<<<(total + 255) / 256, 256, 0, st>>>(N, B, nmin, shift, E);
+  k_axis_phase<<<(total + 255) / 256, 256, 0, st>>>(N, B, shift, E);
   return cudaGetLastError();
 }
 
@@ -61,9 +65,11 @@ cudaError_t launch_box_scatter(const double2* W, long sWq, long ldw, int ne, int
 
 // One axis: out[a][j - j0][c] = sum_{b < B} E[j][b] in[a][b][c] for j0 <= j < j0 + nj.
 // One thread per (a, c): the B inputs stay in registers, E (nj x B) is broadcast from shared
-// memory.  paired: the range is the whole axis with no shift, so E[N - j] = conj(E[j]) and one
-// pass over b gives both outputs j and N - j from four real sums (2 FP64 FMA per complex term
-// and output); otherwise the three-multiplication form (3 FMA per complex term).
+// memory.  paired: the range is the whole axis with no shift (B = 2M + 1 symmetric slots), so
+// with u_m = x_{+m} + x_{-m}, w_m = x_{+m} - x_{-m} and (c, s) = E[j][2m - 1],
+//   A = x_0 + sum_m c u_m,  B = sum_m s w_m,  out[j] = A + i B,  out[N - j] = A - i B:
+// 2M + 2 FP64 operations per output instead of 3B (the three-multiplication form used for
+// shifted axes and partial ranges).
 template <int BMAX>
 __global__ void __launch_bounds__(256) k_axis_dft(const double2* __restrict__ in, long sa_in, long C, int B,
                                                   const double2* __restrict__ E, int N, int j0, int nj, int paired,
@@ -89,23 +95,32 @@ __global__ void __launch_bounds__(256) k_axis_dft(const double2* __restrict__ in
   }
   double2* dst = out + (long)a * sa_out + c;
   if (paired) {
-    // j = 0 .. N/2; j and N - j share the four sums
+    constexpr int MM = (BMAX - 1) / 2;  // BMAX odd: slots 2m - 1, 2m < BMAX for m <= MM
+    double ur[MM], ui[MM], wr[MM], wi[MM];
+#pragma unroll
+    for (int m = 1; m <= MM; ++m) {
+      ur[m - 1] = xr[2 * m - 1] + xr[2 * m];
+      ui[m - 1] = xi[2 * m - 1] + xi[2 * m];
+      wr[m - 1] = xr[2 * m - 1] - xr[2 * m];
+      wi[m - 1] = xi[2 * m - 1] - xi[2 * m];
+    }
+    const int M = (B - 1) / 2;
     for (int j = 0; 2 * j <= N; ++j) {
       const double2* e = es + j * B;
-      double p1 = 0.0, p2 = 0.0, p3 = 0.0, p4 = 0.0;  // sum c xr, s xi, c xi, s xr
+      double ar = xr[0], ai = xi[0], br = 0.0, bi = 0.0;
 #pragma unroll
-      for (int b = 0; b < BMAX; ++b) {
-        if (b < B) {
-          const double2 w = e[b];
-          p1 = fma(w.x, xr[b], p1);
-          p2 = fma(w.y, xi[b], p2);
-          p3 = fma(w.x, xi[b], p3);
-          p4 = fma(w.y, xr[b], p4);
+      for (int m = 1; m <= MM; ++m) {
+        if (m <= M) {
+          const double2 w = e[2 * m - 1];
+          ar = fma(w.x, ur[m - 1], ar);
+          ai = fma(w.x, ui[m - 1], ai);
+          br = fma(w.y, wr[m - 1], br);
+          bi = fma(w.y, wi[m - 1], bi);
         }
       }
-      dst[(long)j * C] = make_double2(p1 - p2, p3 + p4);
+      dst[(long)j * C] = make_double2(ar - bi, ai + br);
       const int jm = N - j;
-      if (j != 0 && jm != j) dst[(long)jm * C] = make_double2(p1 + p2, p3 - p4);
+      if (j != 0 && jm != j) dst[(long)jm * C] = make_double2(ar + bi, ai - br);
     }
   } else {
     double xs[BMAX];
@@ -131,8 +146,8 @@ __global__ void __launch_bounds__(256) k_axis_dft(const double2* __restrict__ in
 cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
                             int nj, int paired, double2* out, long sa_out, cudaStream_t st) {
   if (A <= 0 || C <= 0 || nj <= 0) return cudaSuccess;
-  if (B < 1 || B > 32 || A > 65535 || j0 < 0 || j0 + nj > N) return cudaErrorInvalidValue;
-  if (paired && (j0 != 0 || nj != N)) return cudaErrorInvalidValue;
+  if (B < 1 || B > 33 || A > 65535 || j0 < 0 || j0 + nj > N) return cudaErrorInvalidValue;
+  if (paired && (j0 != 0 || nj != N || (B & 1) == 0)) return cudaErrorInvalidValue;
   const size_t smem = (size_t)nj * B * sizeof(double2);
   if (smem > 160 * 1024) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((C + 255) / 256), (unsigned)A, 1);
@@ -144,9 +159,9 @@ cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B,
     kern<<<grid, 256, smem, st>>>(in, sa_in, C, B, E, N, j0, nj, paired, out, sa_out);
     return cudaGetLastError();
   };
-  if (B <= 8) return go(k_axis_dft<8>);
-  if (B <= 16) return go(k_axis_dft<16>);
-  return go(k_axis_dft<32>);
+  if (B <= 9) return go(k_axis_dft<9>);
+  if (B <= 17) return go(k_axis_dft<17>);
+  return go(k_axis_dft<33>);
 }
 
 // kpts[(j1 n2 + j2) n3 + j3] = (j1/n1 + s1, j2/n2 + s2, j3/n3 + s3)
