@@ -42,10 +42,10 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # Keyed by (kernel, workload, q batch).
 # FP64 flops per matrix of the batched H(k+q) eigensolve (2 x DFMA + DADD + DMUL thread
 # instructions executed, from one ncu capture; profiles/k_jacobi_mixed_si_full.md), keyed by (nb, form)
-EIG_FP64_FLOPS = {(8, "fp64"): (2 * 6418943830 + 1816575880 + 181247980) / 256000}
+EIG_FP64_FLOPS = {(8, "fp64"): (2 * 4311850240 + 364618112 + 270336000) / 256000}
 TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 194695936.0 + 740889600.0,
            ("k_zgemm", "si_full", 4): 242432512.0 + 1777470464.0,
-           ("k_jacobi_mixed", "si_full", 4): 263648512.0 + 231078400.0}
+           ("k_jacobi_mixed", "si_full", 4): 263366400.0 + 231316480.0}
 
 
 def parse():
@@ -377,25 +377,28 @@ def run_libeph(args):
     peaks = measured_peaks()
 
     def roof_axis(r):
-        # axis-1 transform of the product-grid path (k_axis_dft, the last and largest of three):
-        # per output element B1 complex terms; paired form 2 FP64 FMA + 1 add per term and output
+        # axis-1 transform of the product-grid path (k_axis_dft, the per-k part; the axis-3 and
+        # axis-2 transforms run per q batch in stage "mode"): on the symmetric slots of half-width
+        # M, an output pair (j, N-j) takes 4M FMA and 4 additions = 4M + 2 flop per output
         ft_ms, ft_n = r["prof"]["ft_k"]
-        B1 = int(wl.Re[:, 0].max() - wl.Re[:, 0].min() + 1)
+        M = int(np.abs(wl.Re[:, 0]).max())
         NW = nb * nb * (1 + nm)
-        outs = float(QB) * nk * NW
-        return {"kernel": "k_axis_dft (axis 1 of the sum-factorised Re->k contraction)",
-                "complex_terms_per_output": B1, "outputs_per_step": outs,
-                "stage_ms_per_step": ft_ms / args.steps,
-                "note": "stage ft_k also holds the scatter and the axis-3, axis-2 transforms"}
+        outs = float(args.steps) * QB * nk * NW / max(ft_n, 1)
+        t = ft_ms / max(ft_n, 1) * 1e-3
+        ach = (4 * M + 2) * outs / t
+        return {"bound": "alu", "kernel": "k_axis_dft (axis 1 of the sum-factorised Re->k contraction)",
+                "achieved": ach / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_FLOPS, "flop_per_output": 4 * M + 2, "outputs_per_launch": outs,
+                "algorithmic_bytes": 16.0 * outs * (1 + (2 * M + 1) / float(wl.kgrid[0]))}
 
     def roof_band(r):
         bd_ms, bd_n = r["prof"]["band"]
         cmac = 2.0 * nb ** 3 * nm * QB * nk          # V_kq^H G3 V_k per (q,k) pair
         t = bd_ms / max(args.steps, 1) * 1e-3
-        ach = 8.0 * cmac / t
-        return {"bound": "alu", "kernel": "k_band_rotate (FP64)", "achieved": ach / 1e12,
-                "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_FLOPS,
-                "flop_per_cmac": 8}
+        ach = 6.0 * cmac / t                         # three-multiplication form: 3 FMA per CMAC
+        return {"bound": "alu", "kernel": "k_band_rotate (FP64, three-multiplication products)",
+                "achieved": ach / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_FLOPS, "flop_per_cmac": 6}
 
     def roof_eig(r):
         eg_ms, eg_n = r["prof"]["eig"]
@@ -404,7 +407,7 @@ def run_libeph(args):
         mats = float(args.steps) * QB * nk / max(eg_n, 1)
         ach = per * mats / t if per else None
         return {"bound": "alu", "kernel": "k_jacobi_mixed<%d> (FP32 sweeps, FP64 Newton-Schulz, V^H A V, FP64 "
-                                          "sweeps)" % (nb + (nb & 1)),
+                                          "polish sweep, first-order finish)" % (nb + (nb & 1)),
                 "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_FLOPS if ach else None,
                 "fp64_flop_per_matrix": per, "matrices_per_launch": mats,

@@ -205,8 +205,10 @@ enum eph_stage {
   EPH_STAGE_PHASE = 0, /* phase factors e^{i k.R} (exact FP64 reduction + sincospi)             */
   EPH_STAGE_FT_Q = 1,  /* Rp->q contraction of g (Eq. 9) and D(q)                              */
   EPH_STAGE_EIG = 2,   /* batched Hermitian Jacobi eigensolves of H(k), H(k+q)                   */
-  EPH_STAGE_MODE = 3,  /* D(q) eigensolve, mode rotation by u(q), per-q operand assembly         */
-  EPH_STAGE_FT_K = 4,  /* Re->k contraction (Eq. 10 Fourier sum) fused with H(k+q)              */
+  EPH_STAGE_MODE = 3,  /* D(q) eigensolve, mode rotation by u(q), per-q operand assembly
+                          (on a product k grid also the axis-3 and axis-2 transforms)        */
+  EPH_STAGE_FT_K = 4,  /* Re->k contraction (Eq. 10 Fourier sum) fused with H(k+q); on a
+                          product k grid its per-k part, the axis-1 transform              */
   EPH_STAGE_BAND = 5,  /* band rotation V_{k+q}^H G V_k                                         */
   EPH_STAGE_ADJ = 6,   /* adjoint (backward) kernels                                            */
   EPH_STAGE_TC = 7,    /* mixed form: tensor-core (tcgen05) Re->k contraction                   */

@@ -678,17 +678,18 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
   }
   if (ctx->has_grid && grid_stages) {
     // sum factorisation of Eq. 10 (and H(k+q)): W_q scattered into the Re box (with w_e),
-    // then the transforms along axes 3 and 2; axis 1 runs per k slab in k_tile_forward
+    // then the transforms along axes 3 and 2 (per-q operand work, profiled with the mode
+    // stage); axis 1, the per-k part, runs per k slab in k_tile_forward (stage ft_k)
     const int B1 = ctx->bext[0], B2 = ctx->bext[1], B3 = ctx->bext[2];
     const int N2 = ctx->gn[1], N3 = ctx->gn[2];
     const long NW = p.NW, vol = (long)B1 * B2 * B3;
     EPH_CK(cudaMemsetAsync(ctx->Wbox.p, 0, (size_t)nqb * vol * NW * sizeof(double2), ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_box_scatter(W, (long)ne * NW, NW, ne, (int)NW, as<int>(ctx->rebox),
+    EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_box_scatter(W, (long)ne * NW, NW, ne, (int)NW, as<int>(ctx->rebox),
                                                          ctx->we, as<double2>(ctx->Wbox), vol * NW, nqb, ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_axis_dft(as<double2>(ctx->Wbox), (long)B3 * NW, nqb * B1 * B2, NW, B3,
+    EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_axis_dft(as<double2>(ctx->Wbox), (long)B3 * NW, nqb * B1 * B2, NW, B3,
                                                       as<double2>(ctx->E3), N3, 0, N3, ctx->gshift[2] == 0.0,
                                                       as<double2>(ctx->S1), (long)N3 * NW, ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_axis_dft(as<double2>(ctx->S1), (long)B2 * N3 * NW, nqb * B1,
+    EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_axis_dft(as<double2>(ctx->S1), (long)B2 * N3 * NW, nqb * B1,
                                                       (long)N3 * NW, B2, as<double2>(ctx->E2), N2, 0, N2,
                                                       ctx->gshift[1] == 0.0, as<double2>(ctx->S2),
                                                       (long)N2 * N3 * NW, ctx->stream));

@@ -475,52 +475,63 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
   bool conv = !valid;
   int sweep = 0;
   double delta = 0.0;  // this column's accumulated scale 1 + delta from unnormalised rotations
-  while (__any_sync(0xffffffffu, !conv) && sweep < max_sweeps) {
+  // first-order finish: once every remaining angle |A_ij / (A_jj - A_ii)| is below theta_max,
+  // v_j += sum_i v_i A_ij / (A_jj - A_ii) completes the eigenvectors to theta_max^2 (the update
+  // is anti-Hermitian to first order, so V stays unitary to the same order) and
+  // A_jj + sum_i |A_ij|^2 / (A_jj - A_ii) the eigenvalues to theta_max^3 ||A||: one pass of
+  // NP-1 column updates instead of a sweep.  theta_max = 1e-8 when polishing to rounding
+  // level (reached after one sweep), 1e-5 when polishing to 1e-12 (usually right after A').
+  const double th2 = polish_tol >= 1e-13 ? 1e-10 : 1e-16;
+  const bool try_before_sweep = polish_tol >= 1e-13;  // angles ~1e-6 after A': worth trying at 1e-5 only
+  for (;;) {
+    if (__all_sync(0xffffffffu, conv)) break;
+    if (sweep > 0 || try_before_sweep) {
+      unit_scale<NP>(a, v, base, delta);
+      double lj = 0.0;
+#pragma unroll
+      for (int r = 0; r < NP; ++r)
+        if (r == j) lj = a[r].x;
+      bool small = true;
+      double li[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        li[i] = shfl_d(lj, base + i);
+        const double gap = lj - li[i];
+        const double m2 = fma(a[i].x, a[i].x, a[i].y * a[i].y);
+        if (i != j && !(m2 <= th2 * (gap * gap))) small = false;
+      }
+      if (__all_sync(0xffffffffu, small)) {
+        double2 dv[NP];
+#pragma unroll
+        for (int r = 0; r < NP; ++r) dv[r] = make_double2(0.0, 0.0);
+        double dl = 0.0;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const bool use = i != j && (a[i].x != 0.0 || a[i].y != 0.0);
+          const double inv = use ? 1.0 / (lj - li[i]) : 0.0;
+          const double2 x = make_double2(a[i].x * inv, a[i].y * inv);
+          dl = fma(a[i].x, x.x, fma(a[i].y, x.y, dl));
+#pragma unroll
+          for (int r = 0; r < NP; ++r) {
+            const double2 w = shfl_d2(v[r], base + i);
+            dv[r].x = fma(w.x, x.x, fma(-w.y, x.y, dv[r].x));
+            dv[r].y = fma(w.x, x.y, fma(w.y, x.x, dv[r].y));
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+          v[r] = make_double2(v[r].x + dv[r].x, v[r].y + dv[r].y);
+          if (r == j) a[r].x = lj + dl;
+        }
+        conv = true;
+        break;
+      }
+    }
+    if (sweep >= max_sweeps) break;
     PolishSweep<NP, 0>::run(a, v, j, base, thresh2, delta);
     ++sweep;
     const double off = group_off2<NP>(a, j, base);  // shuffles: every lane takes part
     if (valid && off <= tol2) conv = true;
-    if (__all_sync(0xffffffffu, conv)) break;
-    // first-order finish: once every remaining angle |A_ij / (A_jj - A_ii)| is below 1e-8, the
-    // eigenvalues have converged (their error is second order, below 1e-16 ||A||) and
-    // v_j += sum_i v_i A_ij / (A_jj - A_ii) completes the eigenvectors to 1e-16 (the update is
-    // anti-Hermitian to first order, so V stays unitary to the same order): one pass of
-    // NP-1 column updates instead of a sweep
-    unit_scale<NP>(a, v, base, delta);
-    double lj = 0.0;
-#pragma unroll
-    for (int r = 0; r < NP; ++r)
-      if (r == j) lj = a[r].x;
-    bool small = true;
-    double li[NP];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      li[i] = shfl_d(lj, base + i);
-      const double gap = lj - li[i];
-      const double m2 = fma(a[i].x, a[i].x, a[i].y * a[i].y);
-      if (i != j && !(m2 <= 1e-16 * (gap * gap))) small = false;
-    }
-    if (__all_sync(0xffffffffu, small)) {
-      double2 dv[NP];
-#pragma unroll
-      for (int r = 0; r < NP; ++r) dv[r] = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        const bool use = i != j && (a[i].x != 0.0 || a[i].y != 0.0);
-        const double inv = use ? 1.0 / (lj - li[i]) : 0.0;
-        const double2 x = make_double2(a[i].x * inv, a[i].y * inv);
-#pragma unroll
-        for (int r = 0; r < NP; ++r) {
-          const double2 w = shfl_d2(v[r], base + i);
-          dv[r].x = fma(w.x, x.x, fma(-w.y, x.y, dv[r].x));
-          dv[r].y = fma(w.x, x.y, fma(w.y, x.x, dv[r].y));
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x + dv[r].x, v[r].y + dv[r].y);
-      conv = true;
-      break;
-    }
   }
   if (valid && j == 0 && !conv) atomicOr(status, 1);
 
