@@ -70,13 +70,14 @@ cudaError_t launch_box_scatter(const double2* W, long sWq, long ldw, int ne, int
 //   A = x_0 + sum_m c u_m,  B = sum_m s w_m,  out[j] = A + i B,  out[N - j] = A - i B:
 // 2M + 2 FP64 operations per output instead of 3B (the three-multiplication form used for
 // shifted axes and partial ranges).
+// BMAX = B exactly (odd: symmetric slots), so no predicated-off FP64 instruction is issued.
 template <int BMAX>
 __global__ void __launch_bounds__(256) k_axis_dft(const double2* __restrict__ in, long sa_in, long C, int B,
                                                   const double2* __restrict__ E, int N, int j0, int nj, int paired,
                                                   double2* __restrict__ out, long sa_out) {
   extern __shared__ double2 es[];  // [nj][B]
   const int a = blockIdx.y;
-  for (int t = threadIdx.x; t < nj * B; t += blockDim.x) es[t] = E[(long)j0 * B + t];
+  for (int t = threadIdx.x; t < nj * BMAX; t += blockDim.x) es[t] = E[(long)j0 * BMAX + t];
   __syncthreads();
   const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
@@ -84,19 +85,14 @@ __global__ void __launch_bounds__(256) k_axis_dft(const double2* __restrict__ in
   const double2* src = in + (long)a * sa_in + c;
 #pragma unroll
   for (int b = 0; b < BMAX; ++b) {
-    if (b < B) {
-      const double2 v = src[(long)b * C];
-      xr[b] = v.x;
-      xi[b] = v.y;
-    } else {
-      xr[b] = 0.0;
-      xi[b] = 0.0;
-    }
+    const double2 v = src[(long)b * C];
+    xr[b] = v.x;
+    xi[b] = v.y;
   }
   double2* dst = out + (long)a * sa_out + c;
   if (paired) {
     constexpr int MM = (BMAX - 1) / 2;  // BMAX odd: slots 2m - 1, 2m < BMAX for m <= MM
-    double ur[MM], ui[MM], wr[MM], wi[MM];
+    double ur[MM + 1], ui[MM + 1], wr[MM + 1], wi[MM + 1];
 #pragma unroll
     for (int m = 1; m <= MM; ++m) {
       ur[m - 1] = xr[2 * m - 1] + xr[2 * m];
@@ -104,19 +100,16 @@ __global__ void __launch_bounds__(256) k_axis_dft(const double2* __restrict__ in
       wr[m - 1] = xr[2 * m - 1] - xr[2 * m];
       wi[m - 1] = xi[2 * m - 1] - xi[2 * m];
     }
-    const int M = (B - 1) / 2;
     for (int j = 0; 2 * j <= N; ++j) {
-      const double2* e = es + j * B;
+      const double2* e = es + j * BMAX;
       double ar = xr[0], ai = xi[0], br = 0.0, bi = 0.0;
 #pragma unroll
       for (int m = 1; m <= MM; ++m) {
-        if (m <= M) {
-          const double2 w = e[2 * m - 1];
-          ar = fma(w.x, ur[m - 1], ar);
-          ai = fma(w.x, ui[m - 1], ai);
-          br = fma(w.y, wr[m - 1], br);
-          bi = fma(w.y, wi[m - 1], bi);
-        }
+        const double2 w = e[2 * m - 1];
+        ar = fma(w.x, ur[m - 1], ar);
+        ai = fma(w.x, ui[m - 1], ai);
+        br = fma(w.y, wr[m - 1], br);
+        bi = fma(w.y, wi[m - 1], bi);
       }
       dst[(long)j * C] = make_double2(ar - bi, ai + br);
       const int jm = N - j;
@@ -127,16 +120,14 @@ __global__ void __launch_bounds__(256) k_axis_dft(const double2* __restrict__ in
 #pragma unroll
     for (int b = 0; b < BMAX; ++b) xs[b] = xr[b] + xi[b];
     for (int j = 0; j < nj; ++j) {
-      const double2* e = es + j * B;
+      const double2* e = es + j * BMAX;
       double t1 = 0.0, t2 = 0.0, t3 = 0.0;  // sum er xr, ei xi, (er + ei)(xr + xi)
 #pragma unroll
       for (int b = 0; b < BMAX; ++b) {
-        if (b < B) {
-          const double2 w = e[b];
-          t1 = fma(w.x, xr[b], t1);
-          t2 = fma(w.y, xi[b], t2);
-          t3 = fma(w.x + w.y, xs[b], t3);
-        }
+        const double2 w = e[b];
+        t1 = fma(w.x, xr[b], t1);
+        t2 = fma(w.y, xi[b], t2);
+        t3 = fma(w.x + w.y, xs[b], t3);
       }
       dst[(long)j * C] = make_double2(t1 - t2, t3 - t1 - t2);
     }
@@ -146,8 +137,8 @@ __global__ void __launch_bounds__(256) k_axis_dft(const double2* __restrict__ in
 cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
                             int nj, int paired, double2* out, long sa_out, cudaStream_t st) {
   if (A <= 0 || C <= 0 || nj <= 0) return cudaSuccess;
-  if (B < 1 || B > 33 || A > 65535 || j0 < 0 || j0 + nj > N) return cudaErrorInvalidValue;
-  if (paired && (j0 != 0 || nj != N || (B & 1) == 0)) return cudaErrorInvalidValue;
+  if (B < 1 || B > 33 || (B & 1) == 0 || A > 65535 || j0 < 0 || j0 + nj > N) return cudaErrorInvalidValue;
+  if (paired && (j0 != 0 || nj != N)) return cudaErrorInvalidValue;
   const size_t smem = (size_t)nj * B * sizeof(double2);
   if (smem > 160 * 1024) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((C + 255) / 256), (unsigned)A, 1);
@@ -159,9 +150,17 @@ cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B,
     kern<<<grid, 256, smem, st>>>(in, sa_in, C, B, E, N, j0, nj, paired, out, sa_out);
     return cudaGetLastError();
   };
-  if (B <= 9) return go(k_axis_dft<9>);
-  if (B <= 17) return go(k_axis_dft<17>);
-  return go(k_axis_dft<33>);
+  switch (B) {
+#define EPH_AXIS_B(V) \
+  case V:             \
+    return go(k_axis_dft<V>);
+    EPH_AXIS_B(1) EPH_AXIS_B(3) EPH_AXIS_B(5) EPH_AXIS_B(7) EPH_AXIS_B(9) EPH_AXIS_B(11) EPH_AXIS_B(13)
+    EPH_AXIS_B(15) EPH_AXIS_B(17) EPH_AXIS_B(19) EPH_AXIS_B(21) EPH_AXIS_B(23) EPH_AXIS_B(25) EPH_AXIS_B(27)
+    EPH_AXIS_B(29) EPH_AXIS_B(31) EPH_AXIS_B(33)
+#undef EPH_AXIS_B
+    default:
+      return cudaErrorInvalidValue;  // the slot box has odd extents only
+  }
 }
 
 // kpts[(j1 n2 + j2) n3 + j3] = (j1/n1 + s1, j2/n2 + s2, j3/n3 + s3)
