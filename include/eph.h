@@ -91,9 +91,10 @@ void eph_default_options(eph_options* opt);
  *   cuda_stream             cudaStream_t to order all work on; NULL = a stream the
  *                           context creates and owns
  * All inputs are HOST pointers; they are copied and may be freed on return.
- * Supported sizes: 1 <= nb, nm <= 16 in both forms (warp-resident Jacobi and
- * rotations); up to 256 in the FP64 form (one CTA per eigensolve, GEMM rotations;
- * forward only); larger sizes, and the mixed form beyond 16, return EPH_ENOTSUP.
+ * Supported sizes: 1 <= nb, nm <= 16 (warp-resident Jacobi and rotations) and up to
+ * 256 (one CTA per eigensolve, GEMM rotations; forward only), in both forms (beyond 16
+ * the mixed form keeps the FP64 contraction and eigensolves and runs the band rotation
+ * as double-float GEMMs); larger sizes return EPH_ENOTSUP.
  * On success *out owns device memory until eph_destroy.
  */
 int eph_create(eph_ctx** out, int nb, int na, int ne, int np,

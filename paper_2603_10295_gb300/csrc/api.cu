@@ -359,10 +359,6 @@ int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re
   // (FP64 form, forward only)
   if (nb > 256 || nm > 256) return bail(EPH_ENOTSUP);
   ctx->big = nb > 16 || nm > 16 || (size_t)(2 * nb * nb + 2 * nm * nb * nb) * 16 > 200 * 1024;
-  if (ctx->big && ctx->opt.form != EPH_FORM_FP64) {
-    fail(ctx, EPH_ENOTSUP, "nb or nm > 16 is supported by the FP64 form only");
-    return bail(EPH_ENOTSUP);
-  }
   for (int i = 0; i < na; ++i)
     if (!(masses[i] > 0.0)) return bail(EPH_EINVAL);
   if (cuda_stream) {
@@ -555,7 +551,7 @@ int set_k_resident(eph_ctx* ctx, int nk, double* eps_k) {
                           1, ctx->stream));
   EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, as<double2>(ctx->Hk_tmp), nb2, nb, nb, nk, as<double>(ctx->eps_k), nb,
                            as<double2>(ctx->Uk), nb2));
-  if (ctx->opt.form == EPH_FORM_MIXED && ctx->opt.mixed_scheme == 0) {
+  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->big && ctx->opt.mixed_scheme == 0) {
     // A operand of the tensor-core Re->k contraction: 3 fixed-point BF16 digits of the phases
     const size_t slice = (size_t)nk * ctx->kpd;
     EPH_TRY(ensure(ctx, ctx->DA, 3 * slice * 2));
@@ -563,7 +559,7 @@ int set_k_resident(eph_ctx* ctx, int nk, double* eps_k) {
                                                   ctx->stream));
     for (int d = 0; d < 3; ++d)
       EPH_CK(make_tc_map_bf16(&ctx->mapDA[d], static_cast<char*>(ctx->DA.p) + d * slice * 2, nk, ctx->kpd, 128));
-  } else if (ctx->opt.form == EPH_FORM_MIXED) {
+  } else if (ctx->opt.form == EPH_FORM_MIXED && !ctx->big) {
     // A operand of the tensor-core Re->k contraction: split-TF32 phases, K-major [nk][kp]
     EPH_TRY(ensure(ctx, ctx->Ahi, (size_t)nk * ctx->kp * sizeof(float)));
     EPH_TRY(ensure(ctx, ctx->Alo, (size_t)nk * ctx->kp * sizeof(float)));
@@ -703,7 +699,8 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
   const int nb = ctx->nb, nm = ctx->nm, nb2 = nb * nb;
   double2* Y = as<double2>(ctx->Y);
   const double2* Uk = as<double2>(ctx->Uk) + k0 * nb2;
-  if (ctx->opt.form == EPH_FORM_MIXED) {  // product-grid path of the mixed form: complex64 g, sgq in elements
+  const bool mixed = ctx->opt.form == EPH_FORM_MIXED;  // complex64 g, sgq in elements
+  if (mixed && !ctx->big) {
     EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_rotate_ff_f64(Y + nb2, p.NW, as<double2>(ctx->Ukq), Uk, nqb, nkt, nm,
                                                                nb, reinterpret_cast<float2*>(out), sgq, ctx->stream));
     return EPH_OK;
@@ -718,13 +715,22 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
   for (int iq = 0; iq < nqb; ++iq)
     for (int kb = 0; kb < nkt; kb += kc) {
       const int nkc = nkt - kb < kc ? nkt - kb : kc;
+      const double2* G3 = Y + ((long)iq * nkt + kb) * p.NW + nb2;
+      const double2* Vkq = as<double2>(ctx->Ukq) + ((long)iq * nkt + kb) * nb2;
+      if (mixed) {  // double-float GEMMs on the FP32 pipe, complex64 g
+        float2* o32 = reinterpret_cast<float2*>(out) + (long)iq * sgq + (long)kb * nm * nb2;
+        EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zgemm_df_b2(nb, nb, nb, G3, nb, p.NW, nb2, Uk + (long)kb * nb2, nb, nb2,
+                                                             0, T, nb, (long)nm * nb2, nb2, nkc, nm, 0, 0,
+                                                             ctx->stream));
+        EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zgemm_df_b2(nb, nb, nb, Vkq, nb, nb2, 0, T, nb, (long)nm * nb2, nb2, o32,
+                                                             nb, (long)nm * nb2, nb2, nkc, nm, 1, 1, ctx->stream));
+        continue;
+      }
       // T[k][nu] = G3[q][k][nu] V_k
-      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zgemm_b2(nb, nb, nb, Y + ((long)iq * nkt + kb) * p.NW + nb2, nb, p.NW,
-                                                        nb2, Uk + (long)kb * nb2, nb, nb2, 0, T, nb, (long)nm * nb2,
-                                                        nb2, nkc, nm, 0, ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zgemm_b2(nb, nb, nb, G3, nb, p.NW, nb2, Uk + (long)kb * nb2, nb, nb2, 0, T,
+                                                        nb, (long)nm * nb2, nb2, nkc, nm, 0, ctx->stream));
       // g[q][k][nu] = V_{k+q}^H T[k][nu]
-      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zgemm_b2(nb, nb, nb, as<double2>(ctx->Ukq) + ((long)iq * nkt + kb) * nb2,
-                                                        nb, nb2, 0, T, nb, (long)nm * nb2, nb2,
+      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zgemm_b2(nb, nb, nb, Vkq, nb, nb2, 0, T, nb, (long)nm * nb2, nb2,
                                                         out + (long)iq * sgq + (long)kb * nm * nb2, nb,
                                                         (long)nm * nb2, nb2, nkc, nm, 1, ctx->stream));
     }
@@ -897,8 +903,10 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
   if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
   if (ctx->opt.async && !ctx->opt.device_ptrs) return fail(ctx, EPH_EINVAL, "async mode needs device pointers");
-  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid) return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
-  // FP64 form, and the mixed form on a product k grid (FP64 Re->k, complex64 band rotation)
+  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && !ctx->big)
+    return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
+  // FP64 form; the mixed form on a product k grid or with nb, nm > 16 (FP64 Re->k and
+  // eigensolves, band rotation in double-float arithmetic, complex64 g)
   const int nb = ctx->nb, nm = ctx->nm, nk = ctx->nk;
   const int nb2 = nb * nb;
   const bool host = !ctx->opt.device_ptrs;
@@ -1102,7 +1110,7 @@ extern "C" int eph_reserve(eph_ctx* ctx, int nq) {
   if (nq < 1) return fail(ctx, EPH_EINVAL, "eph_reserve: nq < 1");
   QPlan p;
   EPH_TRY(ensure(ctx, ctx->qpts, (size_t)nq * 3 * sizeof(double)));
-  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid) return prepare_mixed(ctx, nq, true, &p);
+  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && !ctx->big) return prepare_mixed(ctx, nq, true, &p);
   return prepare_fp64(ctx, nq, true, &p);
 }
 

@@ -34,6 +34,11 @@ cudaError_t launch_transpose(const double2* in, int n, long batch, double2* out,
 // Same product on the FP32 pipe in double-float arithmetic (~1e-13 relative), FP64 in/out.
 cudaError_t launch_zgemm_df(int M, int N, int K, const double2* A, long lda, long sA, const double2* B, long ldb,
                             long sB, double2* C, long ldc, long sC, int batch, cudaStream_t st);
+// double-float C = op(A) B with a two-level batch (b1 < nbat1, b2 < nbat2; offsets b1 s*1 + b2 s*2),
+// op(A) = A^H when adj; C complex64 when out32 (ldc, sC, sC2 in elements of C)
+cudaError_t launch_zgemm_df_b2(int M, int N, int K, const double2* A, long lda, long sA, long sA2, const double2* B,
+                               long ldb, long sB, long sB2, void* C, long ldc, long sC, long sC2, int nbat1, int nbat2,
+                               int adj, int out32, cudaStream_t st);
 // Adjoint form C[b] = A[b]^H * B[b] (A stored M_A x K_A = K x M), accumulate if acc.
 cudaError_t launch_zgemm_ah(int M, int N, int K, const double2* A, long lda, long sA,
                             const double2* B, long ldb, long sB, double2* C, long ldc, long sC,

@@ -282,19 +282,25 @@ __device__ __forceinline__ void dfmac(float& sh, float& sl, float ah, float al, 
 }
 }  // namespace
 
+// C = op(A) B in double-float arithmetic on the FP32 pipe (~1e-14 relative); op(A) = A or
+// A^H (ADJ); C complex128 or complex64 (OUT32); batch index z = b1 * nbat2 + b2 with operand
+// offsets b1 s*1 + b2 s*2.
+template <bool ADJ, bool OUT32>
 __global__ void __launch_bounds__(256, 2) k_zgemm_df(int M, int N, int K, const double2* __restrict__ A, long lda,
                                                   long sA, const double2* __restrict__ B, long ldb, long sB,
-                                                  double2* __restrict__ C, long ldc, long sC) {
+                                                  void* __restrict__ Cv, long ldc, long sC, int nbat2, long sA2,
+                                                  long sB2, long sC2) {
   __shared__ float4 As[BK][BM];
   __shared__ float4 Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int nN = (N + BN - 1) / BN;  // grid.x = (column block, batch), column block fastest
-  const long b = blockIdx.x / nN;
-  const int m0 = blockIdx.y * BM, n0 = (int)(blockIdx.x - b * nN) * BN;
-  A += b * sA;
-  B += b * sB;
-  C += b * sC;
+  const long z = blockIdx.x / nN;
+  const int m0 = blockIdx.y * BM, n0 = (int)(blockIdx.x - z * nN) * BN;
+  const long b1 = z / nbat2, b2 = z - b1 * nbat2;
+  A += b1 * sA + b2 * sA2;
+  B += b1 * sB + b2 * sB2;
+  const long coff = b1 * sC + b2 * sC2;
   ff2 acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -306,7 +312,16 @@ __global__ void __launch_bounds__(256, 2) k_zgemm_df(int M, int N, int K, const 
       const int idx = tid + 256 * l;
       {
         const int m = idx >> 3, kk = idx & 7, gm = m0 + m, gk = k0 + kk;
-        As[kk][m] = to_ff((gm < M && gk < K) ? A[(long)gm * lda + gk] : make_double2(0.0, 0.0));
+        double2 av = make_double2(0.0, 0.0);
+        if (gm < M && gk < K) {
+          if (ADJ) {
+            av = A[(long)gk * lda + gm];
+            av.y = -av.y;
+          } else {
+            av = A[(long)gm * lda + gk];
+          }
+        }
+        As[kk][m] = to_ff(av);
       }
       {
         const int kk = idx >> 6, n = idx & 63, gn = n0 + n, gk = k0 + kk;
@@ -344,7 +359,11 @@ __global__ void __launch_bounds__(256, 2) k_zgemm_df(int M, int N, int K, const 
       const int gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
       const ff2& c = acc[i][j];
-      C[(long)gm * ldc + gn] = make_double2((double)c.rh + (double)c.rl, (double)c.ih + (double)c.il);
+      if (OUT32)
+        static_cast<float2*>(Cv)[coff + (long)gm * ldc + gn] = make_float2(__fadd_rn(c.rh, c.rl), __fadd_rn(c.ih, c.il));
+      else
+        static_cast<double2*>(Cv)[coff + (long)gm * ldc + gn] =
+            make_double2((double)c.rh + (double)c.rl, (double)c.ih + (double)c.il);
     }
   }
 }
@@ -354,7 +373,28 @@ cudaError_t launch_zgemm_df(int M, int N, int K, const double2* A, long lda, lon
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   if (!grid_ok(M, N, batch)) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
-  k_zgemm_df<<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+  k_zgemm_df<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zgemm_df_b2(int M, int N, int K, const double2* A, long lda, long sA, long sA2, const double2* B,
+                               long ldb, long sB, long sB2, void* C, long ldc, long sC, long sC2, int nbat1, int nbat2,
+                               int adj, int out32, cudaStream_t st) {
+  const long batch = (long)nbat1 * nbat2;
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535 || !grid_ok(M, N, 1)) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
+#define EPH_DF(ADJV, O32)                                                                                         \
+  k_zgemm_df<ADJV, O32><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nbat2, sA2, sB2, sC2)
+  if (adj && out32)
+    EPH_DF(true, true);
+  else if (adj)
+    EPH_DF(true, false);
+  else if (out32)
+    EPH_DF(false, true);
+  else
+    EPH_DF(false, false);
+#undef EPH_DF
   return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
 """Batching: materials of different shape (silicon-like Nb=8/Nm=6, MoS2-like
-Nb=11/Nm=9 and, in the FP64 form, a stanene-family ribbon Nb=32/Nm=54) with
-uneven q batches, in both forms, captured into one CUDA graph; replays must reproduce the eager results exactly, also after new q
+Nb=11/Nm=9 and a stanene-family ribbon Nb=32/Nm=54) with uneven q batches, in
+both forms, captured into one CUDA graph; replays must reproduce the eager results exactly, also after new q
 points are copied into the captured inputs.  The autotuner must pick a valid
 decomposition that leaves the results unchanged."""
 import os
@@ -27,9 +27,8 @@ def _materials(form):
     box = (synth.centred_range(6), synth.centred_range(6), range(0, 1))
     mo = synth.make_workload("mos2", nk=120, nq=40, box=box)
     mats = [(si, [3, 5, 1]), (mo, [2, 7])]
-    if form == "fp64":
-        # a stanene-family ribbon (Table 3's narrowest: Nb=32, Nm=54) on the 15-vector 1-D box
-        mats.append((synth.make_workload("stanene", nb=32, na=18, nk=10, nq=40), [1, 2]))
+    # a stanene-family ribbon (Table 3's narrowest: Nb=32, Nm=54) on the 15-vector 1-D box
+    mats.append((synth.make_workload("stanene", nb=32, na=18, nk=10, nq=40), [1, 2]))
     return mats
 
 
