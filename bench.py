@@ -43,7 +43,7 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # FP64 flops per matrix of the batched H(k+q) eigensolve (2 x DFMA + DADD + DMUL thread
 # instructions executed, from one ncu capture; profiles/k_jacobi_mixed_si_full.md), keyed by (nb, form)
 EIG_FP64_FLOPS = {(8, "fp64"): (2 * 4311850240 + 364618112 + 270336000) / 256000}
-TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 194695936.0 + 740889600.0,
+TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
            ("k_zgemm", "si_full", 4): 242432512.0 + 1777470464.0,
            ("k_jacobi_mixed", "si_full", 4): 263366400.0 + 231316480.0}
 

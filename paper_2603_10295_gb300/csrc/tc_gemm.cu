@@ -219,11 +219,22 @@ __global__ void __launch_bounds__(128, 1) k_tc_split_gemm(const __grid_constant_
       tmem_ld16(tl + c0, r0);
       tmem_ld16(tl + 256 + c0, r1);
       tmem_ld_wait();
-      if (row < M) {
+      if (row < M) {  // four 16-byte stores per lane where the row has them
+        const bool vec_ok = (reinterpret_cast<uintptr_t>(crow) & 15) == 0;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < 16; i += 4) {
           const int col = n0 + c0 + i;
-          if (col < Nr) crow[col] = __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
+          if (col + 3 < Nr && vec_ok) {
+            *reinterpret_cast<float4*>(crow + col) =
+                make_float4(__uint_as_float(r0[i]) + __uint_as_float(r1[i]),
+                            __uint_as_float(r0[i + 1]) + __uint_as_float(r1[i + 1]),
+                            __uint_as_float(r0[i + 2]) + __uint_as_float(r1[i + 2]),
+                            __uint_as_float(r0[i + 3]) + __uint_as_float(r1[i + 3]));
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (col + u < Nr) crow[col + u] = __uint_as_float(r0[i + u]) + __uint_as_float(r1[i + u]);
+          }
         }
       }
     }
@@ -440,6 +451,7 @@ __global__ void __launch_bounds__(tcf::THREADS, 1) k_tc_fixed_gemm(const __grid_
       const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
       float* crow = C + (long)q * sC + (long)row * ldc;
       const float* srow = sB + (long)q * Nr;
+      const bool vec_ok = ((reinterpret_cast<uintptr_t>(crow) | reinterpret_cast<uintptr_t>(srow)) & 15) == 0;
       const float sc = sA * 0x1p-16f;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -448,10 +460,26 @@ __global__ void __launch_bounds__(tcf::THREADS, 1) k_tc_fixed_gemm(const __grid_
         tmem_ld16(tl + 128 + c0, r1);
         tmem_ld_wait();
         if (row < M) {
+          // 16 consecutive columns of one row per lane: four 16-byte stores where the row has
+          // them (scalar 4-byte stores, one row per lane, had left most of every 32-byte
+          // sector unused and made the epilogue the limiter)
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
+          for (int i = 0; i < 16; i += 4) {
             const int col = n0 + c0 + i;
-            if (col < Nr) crow[col] = (__uint_as_float(r0[i]) + __uint_as_float(r1[i])) * (sc * srow[col]);
+            if (col + 3 < Nr && vec_ok) {
+              const float4 sv = *reinterpret_cast<const float4*>(srow + col);
+              float4 o;
+              o.x = (__uint_as_float(r0[i]) + __uint_as_float(r1[i])) * (sc * sv.x);
+              o.y = (__uint_as_float(r0[i + 1]) + __uint_as_float(r1[i + 1])) * (sc * sv.y);
+              o.z = (__uint_as_float(r0[i + 2]) + __uint_as_float(r1[i + 2])) * (sc * sv.z);
+              o.w = (__uint_as_float(r0[i + 3]) + __uint_as_float(r1[i + 3])) * (sc * sv.w);
+              *reinterpret_cast<float4*>(crow + col) = o;
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (col + u < Nr)
+                  crow[col + u] = (__uint_as_float(r0[i + u]) + __uint_as_float(r1[i + u])) * (sc * srow[col + u]);
+            }
           }
         }
       }
