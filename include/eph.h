@@ -174,6 +174,22 @@ int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, const doubl
                    double* grad_g_ReRp);
 
 /*
+ * Bloch -> Wannier transform of Eq. 6 (the coarse-grid construction that precedes the
+ * interpolation): for g_mnnu(k',q') given on nk coarse k' and nq coarse q' points in the
+ * gauges this context's H(Re), Phi(Rp) define (U_k', U_k'+q', u_q' as eph_interp_q uses them),
+ *   g(Re,Rp) = 1/(ne np) sum_{k',q'} e^{-i(k'.Re + q'.Rp)} sum_nu u^{-1}_{nu,ka}(q')
+ *              [U_{k'+q'} g_nu(k',q') U_{k'}^H]  (U in the eigenvector-column convention),
+ * the exact inverse of the interpolation when k' and q' run over the Born-von Karman grid
+ * whose supercell vectors are Re = Rp (unit weights; weights are not used here).
+ *   kpts [nk][3], qpts [nq][3]; g [nq][nk][nm][nb][nb] complex128; g_ReRp [np][nm][ne][nb][nb]
+ *   complex128 (overwritten).  Host or device pointers per device_ptrs.  Replaces the
+ *   context's k list (as eph_set_k).  The context's own g(Re,Rp) is not used.
+ * FP64 form with nb, nm <= 16; EPH_ENOTSUP otherwise.
+ */
+int eph_bloch_to_wannier(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts, const void* g,
+                         double* g_ReRp);
+
+/*
  * Electron linewidths from the interpolated couplings without writing g (a fused
  * downstream consumer; the paper's mobility and self-energy workloads consume g this
  * way): for the resident k list and nq q points,

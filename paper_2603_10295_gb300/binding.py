@@ -24,7 +24,7 @@ EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "ep
            "eph_interp_backward", "eph_destroy", "eph_strerror", "eph_last_error", "eph_kernel_launches",
            "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc",
            "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths", "eph_interp_vjp",
-           "eph_set_k_grid")
+           "eph_set_k_grid", "eph_bloch_to_wannier")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -95,6 +95,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_interp_vjp.restype = i
     lib.eph_set_k_grid.argtypes = [vp, i, i, i, dp, dp]
     lib.eph_set_k_grid.restype = i
+    lib.eph_bloch_to_wannier.argtypes = [vp, i, dp, i, dp, vp, dp]
+    lib.eph_bloch_to_wannier.restype = i
     del ip
     if path is None:
         _lib = lib
@@ -234,6 +236,20 @@ class Context:
         grad_g = np.ascontiguousarray(grad_g, dtype=np.complex128)
         out = np.empty((self.np_, self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
         self.eph_interp_vjp(len(kpts), kpts, len(qpts), qpts, grad_g, out)
+        self.nk = len(kpts)   # the call replaces the context's k list
+        return out
+
+    def eph_bloch_to_wannier(self, nk, kpts, nq, qpts, g, g_ReRp):
+        self._check(self.lib.eph_bloch_to_wannier(self.handle, int(nk), _ptr(kpts), int(nq), _ptr(qpts), _ptr(g),
+                                                  _ptr(g_ReRp)))
+
+    def bloch_to_wannier(self, kpts, qpts, g):
+        """Eq. 6: g(Re,Rp) [np][nm][ne][nb][nb] from g(k',q') [nq][nk][nm][nb][nb] on coarse grids."""
+        kpts = np.ascontiguousarray(kpts, dtype=np.float64)
+        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.complex128)
+        out = np.empty((self.np_, self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
+        self.eph_bloch_to_wannier(len(kpts), kpts, len(qpts), qpts, g, out)
         self.nk = len(kpts)   # the call replaces the context's k list
         return out
 

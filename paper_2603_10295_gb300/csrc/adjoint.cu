@@ -155,6 +155,35 @@ cudaError_t launch_band_vjp(double2* Y, long ldy, const double2* gbar, long sgq,
   return cudaGetLastError();
 }
 
+// f[c] = s M_c with M_c = 1 / invsqrtm[c]^2 (the mass of mode index c = 3 kappa + alpha).
+__global__ void k_mass_factors(const double* __restrict__ invsqrtm, int nm, double s, double* __restrict__ f) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nm) f[c] = s / (invsqrtm[c] * invsqrtm[c]);
+}
+
+cudaError_t launch_mass_factors(const double* invsqrtm, int nm, double s, double* f, cudaStream_t st) {
+  if (nm <= 0) return cudaSuccess;
+  k_mass_factors<<<(nm + 127) / 128, 128, 0, st>>>(invsqrtm, nm, s, f);
+  return cudaGetLastError();
+}
+
+// X[q][c][i] *= f[c] for i < blk (in place).
+__global__ void k_scale_modes(double2* __restrict__ X, long per_q, long blk, const double* __restrict__ f, long n) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const long c = (idx % per_q) / blk;
+  const double s = f[c];
+  const double2 v = X[idx];
+  X[idx] = make_double2(v.x * s, v.y * s);
+}
+
+cudaError_t launch_scale_modes(double2* X, int nq, int nm, long blk, const double* f, cudaStream_t st) {
+  const long n = (long)nq * nm * blk;
+  if (n <= 0) return cudaSuccess;
+  k_scale_modes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, (long)nm * blk, blk, f, n);
+  return cudaGetLastError();
+}
+
 // Sum of n partial values into *L (one CTA, fixed order: deterministic).
 __global__ void __launch_bounds__(256) k_sum_into(const double* __restrict__ v, long n, double* __restrict__ L) {
   __shared__ double red[8];

@@ -96,6 +96,8 @@ struct eph_ctx {
   DBuf jwork, ut, Tbuf;
   // linewidth consumer: q weights, per-(q,k) partials, accumulator
   DBuf wqb, lwpart, lwacc;
+  // Eq. 6 (Bloch -> Wannier): unweighted phases and per-mode factors M / (ne np)
+  DBuf Pku, Ppu, mfac;
   // product k grid (sum-factorised Re->k): bounding box of the Re list, axis phase tables,
   // the scattered W_q box and the two partial transforms of a q batch
   bool boxable = false;  // Re vectors distinct, box extents <= 33, box volume <= 8 ne
@@ -306,7 +308,7 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->Lpair, &ctx->Lacc, &ctx->grad, &ctx->Ahi, &ctx->Alo, &ctx->Bhi, &ctx->Blo,
                   &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut,
                   &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc, &ctx->rebox, &ctx->E1,
-                  &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2};
+                  &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -1022,18 +1024,19 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
   return finish(ctx);
 }
 
-extern "C" int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
-                              const void* grad_g, double* grad_g_ReRp) {
-  if (!ctx) return EPH_EINVAL;
-  if (nk < 1 || nq < 1 || !kpts || !qpts || !grad_g || !grad_g_ReRp)
-    return fail(ctx, EPH_EINVAL, "eph_interp_vjp: bad size or NULL pointer");
-  if (ctx->big || ctx->opt.form != EPH_FORM_FP64)
-    return fail(ctx, EPH_ENOTSUP, "eph_interp_vjp: FP64 form with nb, nm <= 16");
+namespace {
+// The adjoint chain of the interpolation applied to a given g-shaped array X [nq][nk][nm][nb][nb]:
+// out = sum_q w(q) conj-phase(q) M(kind) sum_k conj-phase(k) V_{k+q} X V_k^H over the
+// context's gauges.  eq6 = false: the vector-Jacobian product (weighted phases, conj(u));
+// eq6 = true: Eq. 6 (unweighted phases e^{-i k.Re}, e^{-i q.Rp}, u^{-1} = sqrt(M) e^H = M conj(u),
+// and 1/(ne np)).
+int adjoint_chain(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts, const void* xin,
+                  double* out_ReRp, bool eq6) {
   EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
-  const int nb = ctx->nb, ne = ctx->ne, np = ctx->np;
+  const int nb = ctx->nb, ne = ctx->ne, np = ctx->np, nm = ctx->nm;
   const int nb2 = nb * nb;
   const bool host = !ctx->opt.device_ptrs;
-  const long gcols = (long)ctx->nm * nb2;
+  const long gcols = (long)nm * nb2;
   const QPlan p = plan_q(ctx, nq, host ? (size_t)gcols * sizeof(double2) : 0);
   const void* dq = nullptr;
   EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
@@ -1041,22 +1044,39 @@ extern "C" int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, 
   EPH_TRY(ensure(ctx, ctx->G2bar, (size_t)p.QB * p.X * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->G1bar, (size_t)p.QB * p.X * sizeof(double2)));
   if (host) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)p.QB * p.KT * gcols * sizeof(double2)));
+  const double2* Pk = as<double2>(ctx->Pk);
+  if (eq6) {  // unweighted phases of Eq. 6 and the per-mode factors M / (ne np)
+    EPH_TRY(ensure(ctx, ctx->Pku, (size_t)nk * ne * sizeof(double2)));
+    EPH_TRY(ensure(ctx, ctx->Ppu, (size_t)p.QB * np * sizeof(double2)));
+    EPH_TRY(ensure(ctx, ctx->mfac, (size_t)nm * sizeof(double)));
+    EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(as<double>(ctx->kpts), nk, ctx->Re, nullptr, ne, as<double2>(ctx->Pku),
+                                               ne, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_mass_factors(ctx->invsqrtm, nm, 1.0 / ((double)ne * np),
+                                                         as<double>(ctx->mfac), ctx->stream));
+    Pk = as<double2>(ctx->Pku);
+  }
   double2* grad = nullptr;
   const size_t gbytes = (size_t)np * p.X * sizeof(double2);
   if (host) {
     EPH_TRY(ensure(ctx, ctx->grad, gbytes));
     grad = as<double2>(ctx->grad);
   } else {
-    grad = reinterpret_cast<double2*>(grad_g_ReRp);
+    grad = reinterpret_cast<double2*>(out_ReRp);
   }
   EPH_CK(cudaMemsetAsync(grad, 0, gbytes, ctx->stream));
   const double* qdev = static_cast<const double*>(dq);
-  const double2* gin = static_cast<const double2*>(grad_g);
+  const double2* gin = static_cast<const double2*>(xin);
   double2* Y = as<double2>(ctx->Y);
   double2* G2b = as<double2>(ctx->G2bar);
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
     const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
     EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb, false));
+    const double2* Pq = as<double2>(ctx->Pp);
+    if (eq6) {
+      EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(qdev + 3L * q0, nqb, ctx->Rp, nullptr, np, as<double2>(ctx->Ppu), np,
+                                                 ctx->stream));
+      Pq = as<double2>(ctx->Ppu);
+    }
     for (long k0 = 0; k0 < nk; k0 += p.KT) {
       const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
       // only H(k+q) and its eigenvectors: g is linear in g(Re,Rp), so G3 itself is not needed
@@ -1075,18 +1095,42 @@ extern "C" int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, 
         sgq = (long)nkt * gcols;
       }
       EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_band_vjp(Y + nb2, p.NW, gb, sgq, as<double2>(ctx->Ukq),
-                                                  as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, ctx->nm, nb, ctx->stream));
-      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ne, (int)p.gcols, nkt, as<double2>(ctx->Pk) + k0 * ne, ne, 0,
-                                                  Y + nb2, p.NW, (long)nkt * p.NW, G2b, p.gcols, (long)ne * p.gcols,
-                                                  nqb, k0 > 0, ctx->stream));
+                                                  as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb, ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ne, (int)p.gcols, nkt, Pk + k0 * ne, ne, 0, Y + nb2, p.NW,
+                                                  (long)nkt * p.NW, G2b, p.gcols, (long)ne * p.gcols, nqb, k0 > 0,
+                                                  ctx->stream));
     }
-    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_mode_rotate_adj(G2b, as<double2>(ctx->uq), nqb, ctx->nm, ne, nb2,
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_mode_rotate_adj(G2b, as<double2>(ctx->uq), nqb, nm, ne, nb2,
                                                        as<double2>(ctx->G1bar), ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(np, (int)p.X, nqb, as<double2>(ctx->Pp), np, 0,
-                                                as<double2>(ctx->G1bar), p.X, 0, grad, p.X, 0, 1, 1, ctx->stream));
+    if (eq6)
+      EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_scale_modes(as<double2>(ctx->G1bar), nqb, nm, (long)ne * nb2,
+                                                          as<double>(ctx->mfac), ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(np, (int)p.X, nqb, Pq, np, 0, as<double2>(ctx->G1bar), p.X, 0, grad,
+                                                p.X, 0, 1, 1, ctx->stream));
   }
-  if (host) EPH_CK(cudaMemcpyAsync(grad_g_ReRp, grad, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
+  if (host) EPH_CK(cudaMemcpyAsync(out_ReRp, grad, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
   return finish(ctx);
+}
+}  // namespace
+
+extern "C" int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
+                              const void* grad_g, double* grad_g_ReRp) {
+  if (!ctx) return EPH_EINVAL;
+  if (nk < 1 || nq < 1 || !kpts || !qpts || !grad_g || !grad_g_ReRp)
+    return fail(ctx, EPH_EINVAL, "eph_interp_vjp: bad size or NULL pointer");
+  if (ctx->big || ctx->opt.form != EPH_FORM_FP64)
+    return fail(ctx, EPH_ENOTSUP, "eph_interp_vjp: FP64 form with nb, nm <= 16");
+  return adjoint_chain(ctx, nk, kpts, nq, qpts, grad_g, grad_g_ReRp, false);
+}
+
+extern "C" int eph_bloch_to_wannier(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
+                                    const void* g, double* g_ReRp) {
+  if (!ctx) return EPH_EINVAL;
+  if (nk < 1 || nq < 1 || !kpts || !qpts || !g || !g_ReRp)
+    return fail(ctx, EPH_EINVAL, "eph_bloch_to_wannier: bad size or NULL pointer");
+  if (ctx->big || ctx->opt.form != EPH_FORM_FP64)
+    return fail(ctx, EPH_ENOTSUP, "eph_bloch_to_wannier: FP64 form with nb, nm <= 16");
+  return adjoint_chain(ctx, nk, kpts, nq, qpts, g, g_ReRp, true);
 }
 
 extern "C" int eph_sync(eph_ctx* ctx) {

@@ -115,6 +115,10 @@ cudaError_t launch_band_adjoint(double2* Y, long ldy, const double2* Ukq, const 
 // G3bar = V_{k+q} gbar V_k^H over the pair's G3 row, gbar given ([q][k][nu][m][n], q stride sgq)
 cudaError_t launch_band_vjp(double2* Y, long ldy, const double2* gbar, long sgq, const double2* Ukq,
                             const double2* Uk, int nq, int nk, int nm, int nb, cudaStream_t st);
+// f[c] = s / invsqrtm[c]^2 (mass of mode index c times s)
+cudaError_t launch_mass_factors(const double* invsqrtm, int nm, double s, double* f, cudaStream_t st);
+// X[q][c][i] *= f[c], i < blk (in place)
+cudaError_t launch_scale_modes(double2* X, int nq, int nm, long blk, const double* f, cudaStream_t st);
 // *L += sum_i v[i] (one CTA, fixed order).
 cudaError_t launch_sum_into(const double* v, long n, double* L, cudaStream_t st);
 // G1bar[q][c][e][b] = sum_nu conj(u[q][c][nu]) G2bar[q][e][nu][b]
