@@ -190,6 +190,29 @@ int eph_bloch_to_wannier(eph_ctx* ctx, int nk, const double* kpts, int nq, const
                          double* g_ReRp);
 
 /*
+ * Energy-window prescreening of the fine k list (the paper's transport workflow drops the k
+ * points whose states all lie outside a window around the band edge before forming g):
+ * computes eps_nk for all nk points of kpts, keeps the points with some band in
+ * [e_lo, e_hi], and makes the kept points, in their input order, the resident k list (as
+ * eph_set_k with that list would).
+ *   kpts [nk][3]; eps_k [nk_kept][nb] of the kept points (may be NULL); kidx [nk] receives the
+ *   kept indices into kpts (first *nk_kept entries); host or device pointers per
+ *   device_ptrs; *nk_kept on the host.  With nothing in the window *nk_kept = 0 and no k list
+ *   is resident.  Reads the kept count on the host: not available in async mode.
+ */
+int eph_set_k_window(eph_ctx* ctx, int nk, const double* kpts, double e_lo, double e_hi, double* eps_k,
+                     int* kidx, int* nk_kept);
+
+/*
+ * eph_interp_q with pair screening: pairs (q,k) with no eps_{m,k+q} in [e_lo, e_hi] get g = 0
+ * without the band rotation (the only step after eps_{k+q} is known); keep [nq][nk] (int, may
+ * be NULL) receives 1 for the pairs computed and 0 for the screened ones.  eps_kq and omega are
+ * complete.  FP64 form with nb, nm <= 16; EPH_ENOTSUP otherwise.
+ */
+int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, double e_lo, double e_hi, double* eps_kq,
+                        double* omega, void* g, int* keep);
+
+/*
  * Electron linewidths from the interpolated couplings without writing g (a fused
  * downstream consumer; the paper's mobility and self-energy workloads consume g this
  * way): for the resident k list and nq q points,

@@ -24,7 +24,7 @@ EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "ep
            "eph_interp_backward", "eph_destroy", "eph_strerror", "eph_last_error", "eph_kernel_launches",
            "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc",
            "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths", "eph_interp_vjp",
-           "eph_set_k_grid", "eph_bloch_to_wannier")
+           "eph_set_k_grid", "eph_bloch_to_wannier", "eph_set_k_window", "eph_interp_q_window")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -97,6 +97,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_set_k_grid.restype = i
     lib.eph_bloch_to_wannier.argtypes = [vp, i, dp, i, dp, vp, dp]
     lib.eph_bloch_to_wannier.restype = i
+    lib.eph_set_k_window.argtypes = [vp, i, dp, d, d, dp, vp, ctypes.POINTER(i)]
+    lib.eph_set_k_window.restype = i
+    lib.eph_interp_q_window.argtypes = [vp, i, dp, d, d, dp, dp, vp, vp]
+    lib.eph_interp_q_window.restype = i
     del ip
     if path is None:
         _lib = lib
@@ -252,6 +256,36 @@ class Context:
         self.eph_bloch_to_wannier(len(kpts), kpts, len(qpts), qpts, g, out)
         self.nk = len(kpts)   # the call replaces the context's k list
         return out
+
+    def eph_set_k_window(self, nk, kpts, e_lo, e_hi, eps_k, kidx):
+        n = ctypes.c_int(0)
+        self._check(self.lib.eph_set_k_window(self.handle, int(nk), _ptr(kpts), float(e_lo), float(e_hi), _ptr(eps_k),
+                                              _ptr(kidx), ctypes.byref(n)))
+        self.nk = n.value
+        return n.value
+
+    def set_k_window(self, kpts, e_lo, e_hi):
+        """Keeps the k points with a band in [e_lo, e_hi]: (kept indices, their eps_k)."""
+        kpts = np.ascontiguousarray(kpts, dtype=np.float64)
+        kidx = np.empty(len(kpts), dtype=np.int32)
+        eps = np.empty((len(kpts), self.nb))
+        n = self.eph_set_k_window(len(kpts), kpts, e_lo, e_hi, eps, kidx)
+        return kidx[:n].copy(), eps[:n].copy()
+
+    def eph_interp_q_window(self, nq, qpts, e_lo, e_hi, eps_kq=None, omega=None, g=None, keep=None):
+        self._check(self.lib.eph_interp_q_window(self.handle, int(nq), _ptr(qpts), float(e_lo), float(e_hi),
+                                                 _ptr(eps_kq), _ptr(omega), _ptr(g), _ptr(keep)))
+
+    def interp_q_window(self, qpts, e_lo, e_hi):
+        """(eps_kq, omega, g, keep) with g = 0 on the pairs screened out by the window."""
+        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
+        nq = len(qpts)
+        eps_kq = np.empty((nq, self.nk, self.nb))
+        omega = np.empty((nq, self.nm))
+        g = np.empty((nq, self.nk, self.nm, self.nb, self.nb), dtype=np.complex128)
+        keep = np.empty((nq, self.nk), dtype=np.int32)
+        self.eph_interp_q_window(nq, qpts, e_lo, e_hi, eps_kq, omega, g, keep)
+        return eps_kq, omega, g, keep
 
     def eph_linewidths(self, nq, qpts, wq, kT, mu, sigma, omega_min, gamma):
         self._check(self.lib.eph_linewidths(self.handle, int(nq), _ptr(qpts), _ptr(wq), float(kT), float(mu),

@@ -98,6 +98,8 @@ struct eph_ctx {
   DBuf wqb, lwpart, lwacc;
   // Eq. 6 (Bloch -> Wannier): unweighted phases and per-mode factors M / (ne np)
   DBuf Pku, Ppu, mfac;
+  // energy-window prescreening: flags, scan, block totals, kept indices and points, count
+  DBuf scr_flag, scr_pos, scr_tot, scr_idx, scr_k, scr_count;
   // product k grid (sum-factorised Re->k): bounding box of the Re list, axis phase tables,
   // the scattered W_q box and the two partial transforms of a q batch
   bool boxable = false;  // Re vectors distinct, box extents <= 33, box volume <= 8 ne
@@ -308,7 +310,8 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->Lpair, &ctx->Lacc, &ctx->grad, &ctx->Ahi, &ctx->Alo, &ctx->Bhi, &ctx->Blo,
                   &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut,
                   &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc, &ctx->rebox, &ctx->E1,
-                  &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac};
+                  &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
+                  &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -540,6 +543,45 @@ extern "C" int eph_set_k_grid(eph_ctx* ctx, int n1, int n2, int n3, const double
   return EPH_OK;
 }
 
+extern "C" int eph_set_k_window(eph_ctx* ctx, int nk, const double* kpts, double e_lo, double e_hi, double* eps_k,
+                                int* kidx, int* nk_kept) {
+  if (!ctx) return EPH_EINVAL;
+  if (nk < 1 || !kpts || !kidx || !nk_kept || !(e_lo <= e_hi))
+    return fail(ctx, EPH_EINVAL, "eph_set_k_window: nk < 1, NULL pointer or e_lo > e_hi");
+  if (ctx->opt.async) return fail(ctx, EPH_EINVAL, "eph_set_k_window reads the kept count on the host (no async mode)");
+  *nk_kept = 0;
+  // pass 1: the band energies of every k of the list
+  EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
+  ctx->k_ready = false;
+  const int nb = ctx->nb;
+  const long nblk = ((long)nk + 1023) / 1024;
+  EPH_TRY(ensure(ctx, ctx->scr_flag, (size_t)nk * sizeof(int)));
+  EPH_TRY(ensure(ctx, ctx->scr_pos, (size_t)nk * sizeof(int)));
+  EPH_TRY(ensure(ctx, ctx->scr_tot, (size_t)nblk * sizeof(int)));
+  EPH_TRY(ensure(ctx, ctx->scr_idx, (size_t)nk * sizeof(int)));
+  EPH_TRY(ensure(ctx, ctx->scr_count, sizeof(int)));
+  EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_window_select(as<double>(ctx->eps_k), nk, nb, e_lo, e_hi,
+                                                          as<int>(ctx->scr_flag), as<int>(ctx->scr_pos),
+                                                          as<int>(ctx->scr_tot), as<int>(ctx->scr_idx),
+                                                          as<int>(ctx->scr_count), ctx->stream));
+  int count = 0;
+  EPH_CK(cudaMemcpyAsync(&count, ctx->scr_count.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  EPH_CK(cudaStreamSynchronize(ctx->stream));
+  if (count == 0) return EPH_OK;  // nothing in the window: no k list is resident
+  EPH_CK(cudaMemcpyAsync(kidx, ctx->scr_idx.p, (size_t)count * sizeof(int),
+                         ctx->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  // pass 2: the kept points become the resident k list (the same kernels recompute their
+  // H(k) and eigenpairs, bit for bit as on the full list)
+  EPH_TRY(ensure(ctx, ctx->scr_k, (size_t)count * 3 * sizeof(double)));
+  EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_gather_points(as<double>(ctx->kpts), as<int>(ctx->scr_idx), count,
+                                                          as<double>(ctx->scr_k), ctx->stream));
+  EPH_CK(cudaMemcpyAsync(ctx->kpts.p, ctx->scr_k.p, (size_t)count * 3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+  EPH_TRY(set_k_resident(ctx, count, eps_k));
+  *nk_kept = count;
+  return EPH_OK;
+}
+
 namespace {
 // H(k), its eigenpairs and the k-side operands for the k list already in ctx->kpts.
 int set_k_resident(eph_ctx* ctx, int nk, double* eps_k) {
@@ -697,7 +739,8 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
 
 // Band rotation g_nu = V_{k+q}^H G3_nu V_k for one (q batch, k tile): the shared-memory kernel
 // for small shapes, two GEMMs batched over (k, nu) otherwise.
-int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2* out, long sgq) {
+int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2* out, long sgq,
+                const int* keep = nullptr) {
   const int nb = ctx->nb, nm = ctx->nm, nb2 = nb * nb;
   double2* Y = as<double2>(ctx->Y);
   const double2* Uk = as<double2>(ctx->Uk) + k0 * nb2;
@@ -709,7 +752,7 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
   }
   if (!ctx->big) {
     EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, as<double2>(ctx->Ukq), Uk, nqb, nkt, nm, nb, out,
-                                                    sgq, ctx->stream));
+                                                    sgq, ctx->stream, keep));
     return EPH_OK;
   }
   double2* T = as<double2>(ctx->Tbuf);
@@ -900,25 +943,26 @@ int prepare_fp64(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
 
 }  // namespace
 
-extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
-  if (!ctx) return EPH_EINVAL;
-  if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
-  if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
-  if (ctx->opt.async && !ctx->opt.device_ptrs) return fail(ctx, EPH_EINVAL, "async mode needs device pointers");
-  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && !ctx->big)
-    return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
-  // FP64 form; the mixed form on a product k grid or with nb, nm > 16 (FP64 Re->k and
-  // eigensolves, band rotation in double-float arithmetic, complex64 g)
+namespace {
+struct Window {
+  double lo, hi;
+  int* keep;  // [nq][nk] caller buffer, may be NULL
+};
+
+// The forward path of the FP64 form (and of the mixed form on a product k grid or beyond the
+// warp shapes).  win: pairs (q,k) with no eps_{m,k+q} in [lo, hi] are screened out of the band
+// rotation (their g is written as 0) and reported in keep.
+int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g,
+                const Window* win) {
   const int nb = ctx->nb, nm = ctx->nm, nk = ctx->nk;
-  const int nb2 = nb * nb;
   const bool host = !ctx->opt.device_ptrs;
   const size_t esz = ctx->opt.form == EPH_FORM_MIXED ? sizeof(float2) : sizeof(double2);
   QPlan p;
   EPH_TRY(prepare_fp64(ctx, nq, g != nullptr, &p));
+  if (win) EPH_TRY(ensure(ctx, ctx->scr_flag, (size_t)p.QB * p.KT * sizeof(int)));
   const void* dq = nullptr;
   EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
   const double* qdev = static_cast<const double*>(dq);
-  double2* Y = as<double2>(ctx->Y);
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
     const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
     EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
@@ -933,11 +977,21 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
           EPH_CK(cudaMemcpyAsync(eps_kq + ((long)(q0 + iq) * nk + k0) * nb,
                                  as<double>(ctx->eps_tile) + (long)iq * nkt * nb, (size_t)nkt * nb * sizeof(double),
                                  out_kind(ctx), ctx->stream));
+      const int* keep = nullptr;
+      if (win) {  // pair flags from the tile's eps_{k+q}
+        EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_window_flags(as<double>(ctx->eps_tile), (long)nqb * nkt, nb, win->lo,
+                                                              win->hi, as<int>(ctx->scr_flag), ctx->stream));
+        keep = as<int>(ctx->scr_flag);
+        if (win->keep)
+          for (int iq = 0; iq < nqb; ++iq)
+            EPH_CK(cudaMemcpyAsync(win->keep + (long)(q0 + iq) * nk + k0, keep + (long)iq * nkt,
+                                   (size_t)nkt * sizeof(int), out_kind(ctx), ctx->stream));
+      }
       if (g) {
         char* gout = static_cast<char*>(g);
         char* stage = static_cast<char*>(ctx->g_stage.p);
         if (host) {
-          EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0, reinterpret_cast<double2*>(stage), (long)nkt * p.gcols));
+          EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0, reinterpret_cast<double2*>(stage), (long)nkt * p.gcols, keep));
           for (int iq = 0; iq < nqb; ++iq)
             EPH_CK(cudaMemcpyAsync(gout + ((long)(q0 + iq) * nk + k0) * p.gcols * esz,
                                    stage + (long)iq * nkt * p.gcols * esz, (size_t)nkt * p.gcols * esz,
@@ -945,12 +999,37 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
         } else {
           EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0,
                               reinterpret_cast<double2*>(gout + ((long)q0 * nk + k0) * p.gcols * esz),
-                              (long)nk * p.gcols));
+                              (long)nk * p.gcols, keep));
         }
       }
     }
   }
   return finish(ctx);
+}
+}  // namespace
+
+extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
+  if (!ctx) return EPH_EINVAL;
+  if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
+  if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
+  if (ctx->opt.async && !ctx->opt.device_ptrs) return fail(ctx, EPH_EINVAL, "async mode needs device pointers");
+  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && !ctx->big)
+    return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
+  // FP64 form; the mixed form on a product k grid or with nb, nm > 16 (FP64 Re->k and
+  // eigensolves, band rotation in double-float arithmetic, complex64 g)
+  return interp_fp64(ctx, nq, qpts, eps_kq, omega, g, nullptr);
+}
+
+extern "C" int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, double e_lo, double e_hi,
+                                   double* eps_kq, double* omega, void* g, int* keep) {
+  if (!ctx) return EPH_EINVAL;
+  if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q_window before eph_set_k");
+  if (nq < 1 || !qpts || !(e_lo <= e_hi)) return fail(ctx, EPH_EINVAL, "eph_interp_q_window: bad arguments");
+  if (ctx->opt.async && !ctx->opt.device_ptrs) return fail(ctx, EPH_EINVAL, "async mode needs device pointers");
+  if (ctx->opt.form != EPH_FORM_FP64 || ctx->big)
+    return fail(ctx, EPH_ENOTSUP, "eph_interp_q_window: FP64 form with nb, nm <= 16");
+  const Window w{e_lo, e_hi, keep};
+  return interp_fp64(ctx, nq, qpts, eps_kq, omega, g, &w);
 }
 
 extern "C" int eph_interp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts, double* eps_k,

@@ -82,7 +82,8 @@ cudaError_t launch_mode_rotate(const double2* G1, const double2* u, int nq, int 
 // G3 rows: Y + (q*nk + k)*ldy (nm*nb*nb complex per row); Ukq [q][k][nb][nb];
 // Uk [k][nb][nb]; output g + q*sgq + k*nm*nb*nb.
 cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq,
-                               int nk, int nm, int nb, double2* g, long sgq, cudaStream_t st);
+                               int nk, int nm, int nb, double2* g, long sgq, cudaStream_t st,
+                               const int* keep = nullptr);
 
 // ---- Re->k contraction on a product k grid (sum factorisation, griddft.cu) ----------------
 // kpts[(j1 n2 + j2) n3 + j3] = (j1/n1, j2/n2, j3/n3) + shift (shift: host array of 3)
@@ -96,6 +97,16 @@ cudaError_t launch_box_scatter(const double2* W, long sWq, long ldw, int ne, int
 // axis, B odd)
 cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
                             int nj, int paired, double2* out, long sa_out, cudaStream_t st);
+
+// ---- energy-window prescreening (screen.cu) ------------------------------------------------
+// idx[0..*count) = ascending k with some eps[k][n] in [e_lo, e_hi]; flag, pos [nk], tot [ceil(nk/1024)]
+cudaError_t launch_window_select(const double* eps, long nk, int nb, double e_lo, double e_hi, int* flag, int* pos,
+                                 int* tot, int* idx, int* count, cudaStream_t st);
+// flag[i] = 1 if some eps[i][n] lies in [e_lo, e_hi], i < n
+cudaError_t launch_window_flags(const double* eps, long n, int nb, double e_lo, double e_hi, int* flag,
+                                cudaStream_t st);
+// out[j] = kpts[idx[j]] (3 doubles each)
+cudaError_t launch_gather_points(const double* kpts, const int* idx, int n, double* out, cudaStream_t st);
 
 // ---- fused consumer: electron linewidths from each (q,k) tile without writing g -----------
 // part[q][k][n] = pi w_q sum_{m,nu} |g|^2/(2 omega) [(n_B + f) delta(e - e' + omega) + (n_B + 1 - f) delta(e - e' - omega)]

@@ -158,24 +158,30 @@ __device__ __forceinline__ double2 pair_g(const PairSmem& s, int t, int nb) {
   return make_double2(t1 + t2, t3 - t1 + t2);
 }
 
-// One CTA per (q,k) pair: g_nu = V_{k+q}^H G3_nu V_k (2 nb^3 nm CMAC per pair).
+// One CTA per (q,k) pair: g_nu = V_{k+q}^H G3_nu V_k (2 nb^3 nm CMAC per pair).  keep (may be
+// NULL): pairs with keep[q*nk + k] == 0 are screened out and get g = 0 without any arithmetic.
 __global__ void __launch_bounds__(128) k_band_rotate(const double2* __restrict__ Y, long ldy,
                                                      const double2* __restrict__ Ukq,
                                                      const double2* __restrict__ Uk, int nk, int nm, int nb,
-                                                     double2* __restrict__ g, long sgq) {
+                                                     double2* __restrict__ g, long sgq,
+                                                     const int* __restrict__ keep) {
   extern __shared__ double2 sm[];
   const PairSmem s = pair_smem(sm, nb, nm);
   const int nb2 = nb * nb;
   const long pair = blockIdx.x;  // q*nk + k
   const int k = (int)(pair % nk);
   const long q = pair / nk;
-  pair_stage1(s, Y + pair * ldy, Uk + (long)k * nb2, Ukq + pair * nb2, nm, nb);
   double2* out = g + q * sgq + (long)k * nm * nb2;
+  if (keep && !keep[pair]) {  // uniform over the CTA: no barrier is skipped by part of it
+    for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) out[t] = make_double2(0.0, 0.0);
+    return;
+  }
+  pair_stage1(s, Y + pair * ldy, Uk + (long)k * nb2, Ukq + pair * nb2, nm, nb);
   for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) out[t] = pair_g(s, t, nb);
 }
 
 cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
-                               int nm, int nb, double2* g, long sgq, cudaStream_t st) {
+                               int nm, int nb, double2* g, long sgq, cudaStream_t st, const int* keep) {
   long pairs = (long)nq * nk;
   if (pairs <= 0) return cudaSuccess;
   const size_t smem = pair_smem_bytes(nb, nm);
@@ -185,7 +191,7 @@ cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, c
     if (e != cudaSuccess) return e;
   }
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
-  k_band_rotate<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq);
+  k_band_rotate<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq, keep);
   return cudaGetLastError();
 }
 
