@@ -627,14 +627,14 @@ __host__ __device__ inline int rr_partner_rt(int j, int r, int np) {
 }
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_jacobi_big(const double2* __restrict__ A, long sA, long lda, int n,
+__global__ void __launch_bounds__(1024) k_jacobi_big(const double2* __restrict__ A, long sA, long lda, int n,
                                                     double* __restrict__ w, long sw, double2* __restrict__ V, long sV,
                                                     double2* __restrict__ work, int max_sweeps,
                                                     int* __restrict__ status) {
   __shared__ int sp[128], sq[128];
   __shared__ double sc[128], stb[128], sapp[128], saqq[128];
   __shared__ double2 ssg[128];
-  __shared__ double red[8];
+  __shared__ double red[32];
   __shared__ int s_flag;
   __shared__ int srank[256];
   const long mat = blockIdx.x;
@@ -784,7 +784,12 @@ cudaError_t launch_jacobi_big(const double2* A, long sA, long lda, int n, long b
   if (batch <= 0) return cudaSuccess;
   if (n < 1 || n > 256 || sV != (long)n * n) return cudaErrorInvalidValue;
   if (batch > 2147483647L) return cudaErrorInvalidConfiguration;
-  k_jacobi_big<<<(unsigned)batch, 256, 0, st>>>(A, sA, lda, n, w, sw, V, sV, work, max_sweeps, status);
+  // a round's column and row mixes touch n^2 / 2 elements each; with few matrices per SM the
+  // latency of these global (L2-resident) accesses needs many threads in flight: about n^2 / 8
+  // threads (128 .. 1024)
+  int threads = ((n * n / 8 + 31) / 32) * 32;
+  threads = threads < 128 ? 128 : (threads > 1024 ? 1024 : threads);
+  k_jacobi_big<<<(unsigned)batch, threads, 0, st>>>(A, sA, lda, n, w, sw, V, sV, work, max_sweeps, status);
   return cudaGetLastError();
 }
 
