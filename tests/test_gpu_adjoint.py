@@ -108,3 +108,15 @@ def test_device_mode_and_autograd():
     (3.0 * L).backward()
     assert abs(L.item() - L_ref) <= 1e-12 * abs(L_ref)
     assert rel_grad_err(gW.grad.cpu().numpy(), 3.0 * g_ref) <= 1e-12
+
+
+def test_backward_on_mixed_form_context():
+    # a mixed-form context differentiates through the same FP64 adjoint chain; only its
+    # eigensolves are polished to 1e-12 instead of rounding level
+    wl = synth.make_workload("si_tiny", nb=4, nk=24, nq=5)
+    w = weights(wl, wl.kpts)
+    L_ref, g_ref = oracle.loss_and_grad(wl, wl.kpts, wl.qpts, w, 1e-6)
+    ctx = binding.Context.from_workload(wl, form="mixed")
+    L, grad = ctx.loss_and_grad(wl.kpts, wl.qpts, w, 1e-6)
+    assert abs(L - L_ref) <= 1e-9 * abs(L_ref)
+    assert rel_grad_err(grad, g_ref) <= 1e-8
