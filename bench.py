@@ -536,7 +536,8 @@ def run_libeph(args):
         e2e_units = args.steps * QB * nk * nm * nb * nb
         out = {"value": e2e_units / (t_e2e + t_setk * (args.steps * QB) / len(wl.qpts)), "unit": UNIT,
                "h2d_bytes_per_step": QB * 3 * 8,
-               "d2h_bytes_per_step": g_h.numel() * g_h.element_size() + ekq_h.numel() * 8 + om_h.numel() * 8}
+               "d2h_bytes_per_step": g_h.numel() * g_h.element_size() + ekq_h.numel() * 8 + om_h.numel() * 8,
+               "ms_per_step": 1e3 * t_e2e / args.steps, "k_setup_ms": 1e3 * t_setk}
         del g_h
         return out
 

@@ -100,6 +100,11 @@ struct eph_ctx {
   DBuf Pku, Ppu, mfac;
   // energy-window prescreening: flags, scan, block totals, kept indices and points, count
   DBuf scr_flag, scr_pos, scr_tot, scr_idx, scr_k, scr_count;
+  // host-buffer output: device->host copies of g on a second stream, overlapping the band
+  // rotation of the next q of the batch (events: one per q slice, one for all copies)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t slice_ev[16] = {};
+  cudaEvent_t copy_done = nullptr;
   // product k grid (sum-factorised Re->k): bounding box of the Re list, axis phase tables,
   // the scattered W_q box and the two partial transforms of a q batch
   bool boxable = false;  // Re vectors distinct, box extents <= 33, box volume <= 8 ne
@@ -318,6 +323,10 @@ void eph_destroy(eph_ctx* ctx) {
     ctx->pool.push_back(p.b);
   }
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->slice_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -739,20 +748,23 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
 
 // Band rotation g_nu = V_{k+q}^H G3_nu V_k for one (q batch, k tile): the shared-memory kernel
 // for small shapes, two GEMMs batched over (k, nu) otherwise.
+// iq0: the first q of the tile to rotate (nqb of them from there).
 int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2* out, long sgq,
-                const int* keep = nullptr) {
+                const int* keep = nullptr, int iq0 = 0) {
   const int nb = ctx->nb, nm = ctx->nm, nb2 = nb * nb;
-  double2* Y = as<double2>(ctx->Y);
+  double2* Y = as<double2>(ctx->Y) + (long)iq0 * nkt * p.NW;
+  const double2* Ukq = as<double2>(ctx->Ukq) + (long)iq0 * nkt * nb2;
+  if (keep) keep += (long)iq0 * nkt;
   const double2* Uk = as<double2>(ctx->Uk) + k0 * nb2;
   const bool mixed = ctx->opt.form == EPH_FORM_MIXED;  // complex64 g, sgq in elements
   if (mixed && !ctx->big) {
-    EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_rotate_ff_f64(Y + nb2, p.NW, as<double2>(ctx->Ukq), Uk, nqb, nkt, nm,
-                                                               nb, reinterpret_cast<float2*>(out), sgq, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_rotate_ff_f64(Y + nb2, p.NW, Ukq, Uk, nqb, nkt, nm, nb,
+                                                               reinterpret_cast<float2*>(out), sgq, ctx->stream));
     return EPH_OK;
   }
   if (!ctx->big) {
-    EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, as<double2>(ctx->Ukq), Uk, nqb, nkt, nm, nb, out,
-                                                    sgq, ctx->stream, keep));
+    EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, Ukq, Uk, nqb, nkt, nm, nb, out, sgq, ctx->stream,
+                                                    keep));
     return EPH_OK;
   }
   double2* T = as<double2>(ctx->Tbuf);
@@ -761,7 +773,7 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
     for (int kb = 0; kb < nkt; kb += kc) {
       const int nkc = nkt - kb < kc ? nkt - kb : kc;
       const double2* G3 = Y + ((long)iq * nkt + kb) * p.NW + nb2;
-      const double2* Vkq = as<double2>(ctx->Ukq) + ((long)iq * nkt + kb) * nb2;
+      const double2* Vkq = Ukq + ((long)iq * nkt + kb) * nb2;
       if (mixed) {  // double-float GEMMs on the FP32 pipe, complex64 g
         float2* o32 = reinterpret_cast<float2*>(out) + (long)iq * sgq + (long)kb * nm * nb2;
         EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zgemm_df_b2(nb, nb, nb, G3, nb, p.NW, nb2, Uk + (long)kb * nb2, nb, nb2,
@@ -944,6 +956,14 @@ int prepare_fp64(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
 }  // namespace
 
 namespace {
+int ensure_copy_stream(eph_ctx* ctx) {
+  if (ctx->copy_stream) return EPH_OK;
+  EPH_CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : ctx->slice_ev) EPH_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  EPH_CK(cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming));
+  return EPH_OK;
+}
+
 struct Window {
   double lo, hi;
   int* keep;  // [nq][nk] caller buffer, may be NULL
@@ -963,6 +983,8 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
   const void* dq = nullptr;
   EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
   const double* qdev = static_cast<const double*>(dq);
+  bool copies = false;  // device->host copies of g issued on the copy stream
+  if (host && g) EPH_TRY(ensure_copy_stream(ctx));
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
     const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
     EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
@@ -991,11 +1013,18 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
         char* gout = static_cast<char*>(g);
         char* stage = static_cast<char*>(ctx->g_stage.p);
         if (host) {
-          EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0, reinterpret_cast<double2*>(stage), (long)nkt * p.gcols, keep));
-          for (int iq = 0; iq < nqb; ++iq)
-            EPH_CK(cudaMemcpyAsync(gout + ((long)(q0 + iq) * nk + k0) * p.gcols * esz,
-                                   stage + (long)iq * nkt * p.gcols * esz, (size_t)nkt * p.gcols * esz,
-                                   cudaMemcpyDeviceToHost, ctx->stream));
+          // one q at a time: the copy of q overlaps the band rotation of the following ones
+          if (copies) EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));  // stage free again
+          for (int iq = 0; iq < nqb; ++iq) {
+            char* slice = stage + (long)iq * nkt * p.gcols * esz;
+            EPH_TRY(band_rotate(ctx, p, 1, nkt, k0, reinterpret_cast<double2*>(slice), (long)nkt * p.gcols, keep, iq));
+            EPH_CK(cudaEventRecord(ctx->slice_ev[iq], ctx->stream));
+            EPH_CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->slice_ev[iq], 0));
+            EPH_CK(cudaMemcpyAsync(gout + ((long)(q0 + iq) * nk + k0) * p.gcols * esz, slice,
+                                   (size_t)nkt * p.gcols * esz, cudaMemcpyDeviceToHost, ctx->copy_stream));
+          }
+          EPH_CK(cudaEventRecord(ctx->copy_done, ctx->copy_stream));
+          copies = true;
         } else {
           EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0,
                               reinterpret_cast<double2*>(gout + ((long)q0 * nk + k0) * p.gcols * esz),
@@ -1004,6 +1033,7 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
       }
     }
   }
+  if (copies) EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));  // finish() waits for them too
   return finish(ctx);
 }
 }  // namespace
