@@ -66,9 +66,12 @@ typedef struct eph_options {
                         1 = two-term split TF32 (3 products) */
   int eig_plain_fp64; /* 0 (default): Jacobi sweeps preconditioned in FP32, then FP64 sweeps to
                          full FP64 accuracy; 1: FP64 sweeps only */
-  int async;          /* 1: eph_interp_q only enqueues work on the context's stream (device pointers
-                         required, no host synchronisation, no event timing) so that a sequence of
-                         calls can be captured into one CUDA graph; its status is read by eph_sync */
+  int async;          /* 1: eph_interp_q only enqueues work (no host synchronisation, no event
+                         timing); its status is read by eph_sync.  With device pointers a sequence
+                         of calls can be captured into one CUDA graph.  With host pointers (FP64
+                         form, uniform-grid path or nb, nm > 16) the outputs are copied to the host
+                         asynchronously, g on a second stream: the host buffers must stay valid,
+                         and should be pinned, until eph_sync returns */
 } eph_options;
 
 /* Fills *opt with the defaults (FP64 form, host pointers, automatic batching). */
@@ -270,8 +273,9 @@ int eph_profile_reset(eph_ctx* ctx);
  *   eph_reserve   sizes every workspace buffer for calls of up to nq q points with the
  *                 resident k list, so that later eph_interp_q calls allocate nothing
  *                 (a requirement for stream capture).
- *   eph_sync      synchronises the context's stream, reads and clears the device status
- *                 flags of the work enqueued since the last check (async mode).
+ *   eph_sync      synchronises the context's streams (its own and the one that copies g to
+ *                 host buffers), reads and clears the device status flags of the work
+ *                 enqueued since the last check (async mode).
  *   eph_autotune  picks q_batch and k_tile for nq q points by timing candidate
  *                 decompositions (q_batch 1..16, k tiles of nk, nk/2, nk/4) with CUDA
  *                 events on the context's stream; the choice is stored in the context

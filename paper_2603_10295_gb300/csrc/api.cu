@@ -1033,7 +1033,9 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
       }
     }
   }
-  if (copies) EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));  // finish() waits for them too
+  // synchronous calls: finish() also waits for the copies; async mode: eph_sync does, and the
+  // next call's band rotation waits for them before it reuses the staging buffer
+  if (copies && !ctx->opt.async) EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));
   return finish(ctx);
 }
 }  // namespace
@@ -1042,9 +1044,11 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
   if (!ctx) return EPH_EINVAL;
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
   if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
-  if (ctx->opt.async && !ctx->opt.device_ptrs) return fail(ctx, EPH_EINVAL, "async mode needs device pointers");
-  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && !ctx->big)
+  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && !ctx->big) {
+    if (ctx->opt.async && !ctx->opt.device_ptrs)
+      return fail(ctx, EPH_EINVAL, "async mode with host pointers: FP64 form, grid path or nb, nm > 16 only");
     return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
+  }
   // FP64 form; the mixed form on a product k grid or with nb, nm > 16 (FP64 Re->k and
   // eigensolves, band rotation in double-float arithmetic, complex64 g)
   return interp_fp64(ctx, nq, qpts, eps_kq, omega, g, nullptr);
@@ -1055,7 +1059,6 @@ extern "C" int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, dou
   if (!ctx) return EPH_EINVAL;
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q_window before eph_set_k");
   if (nq < 1 || !qpts || !(e_lo <= e_hi)) return fail(ctx, EPH_EINVAL, "eph_interp_q_window: bad arguments");
-  if (ctx->opt.async && !ctx->opt.device_ptrs) return fail(ctx, EPH_EINVAL, "async mode needs device pointers");
   if (ctx->opt.form != EPH_FORM_FP64 || ctx->big)
     return fail(ctx, EPH_ENOTSUP, "eph_interp_q_window: FP64 form with nb, nm <= 16");
   const Window w{e_lo, e_hi, keep};
@@ -1244,6 +1247,7 @@ extern "C" int eph_bloch_to_wannier(eph_ctx* ctx, int nk, const double* kpts, in
 
 extern "C" int eph_sync(eph_ctx* ctx) {
   if (!ctx) return EPH_EINVAL;
+  if (ctx->copy_stream) EPH_CK(cudaStreamSynchronize(ctx->copy_stream));  // host copies of g
   int h[2] = {0, 0};
   EPH_CK(cudaMemcpyAsync(h, ctx->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   EPH_CK(cudaStreamSynchronize(ctx->stream));

@@ -153,3 +153,31 @@ def test_si_full_sampled_fp64():
 def test_mos2_full_sampled_fp64():
     gpu, ref = _sampled_full_size("mos2", nq_check=3, nk_sample=1200, seed=12)
     check(gpu, ref, TOL_FP64, "mos2")
+
+
+@pytest.mark.parametrize("form,grid", [("fp64", False), ("fp64", True), ("mixed", True)])
+def test_async_host_mode_matches_sync(form, grid):
+    # async mode with host buffers: g is copied on a second stream while the next call computes;
+    # after eph_sync every output equals the synchronous call's, bit for bit
+    torch = pytest.importorskip("torch")
+    wl = synth.make_workload("si_tiny", nk=60, nq=9)
+    sync = binding.Context.from_workload(wl, form=form, q_batch=3)
+    asyn = binding.Context.from_workload(wl, form=form, q_batch=3, async_mode=True)
+    if grid:
+        sync.set_k_grid(3, 4, 5)
+        asyn.eph_set_k_grid(3, 4, 5)
+    else:
+        sync.set_k(wl.kpts)
+        asyn.eph_set_k(len(wl.kpts), wl.kpts)
+    nk, nb, nm = sync.nk, wl.nb, wl.nm
+    gdt = torch.complex128 if form == "fp64" else torch.complex64
+    outs = [(torch.empty(3, nk, nb, dtype=torch.float64).pin_memory(), torch.empty(3, nm, dtype=torch.float64).pin_memory(),
+             torch.empty(3, nk, nm, nb, nb, dtype=gdt).pin_memory()) for _ in range(3)]
+    q = torch.from_numpy(wl.qpts.copy()).pin_memory()
+    for i in range(3):
+        asyn.eph_interp_q(3, q[3 * i:3 * i + 3], *outs[i])
+    asyn.eph_sync()
+    for i in range(3):
+        ref = sync.interp_q(wl.qpts[3 * i:3 * i + 3])
+        for a, b in zip(outs[i], ref):
+            assert np.array_equal(a.numpy(), b)
