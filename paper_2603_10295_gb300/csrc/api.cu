@@ -91,6 +91,11 @@ struct eph_ctx {
   double scaleA = 1.0;  // power of two >= 2 max |w_e|
   DBuf DA, DB, sB;
   CUtensorMap mapDA[3]{}, mapDB[4]{};
+  // H(k+q) of the mixed form on the tensor cores: 5 digits of the phases (the first 3 are DA's
+  // planes, read through 64-byte-swizzle maps), 5 of the H columns of W_q, per-column scales,
+  // the (hi, lo) float-pair result
+  DBuf DBH, sBH, Hpair;
+  CUtensorMap mapDA5[5]{}, mapDBH[5]{};
   // shapes beyond the warp kernels (nb or nm > 16): CTA Jacobi work, transposed u, band-rotation temp
   bool big = false;
   DBuf jwork, ut, Tbuf;
@@ -316,7 +321,7 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut,
                   &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc, &ctx->rebox, &ctx->E1,
                   &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
-                  &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count};
+                  &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -605,13 +610,17 @@ int set_k_resident(eph_ctx* ctx, int nk, double* eps_k) {
   EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, as<double2>(ctx->Hk_tmp), nb2, nb, nb, nk, as<double>(ctx->eps_k), nb,
                            as<double2>(ctx->Uk), nb2));
   if (ctx->opt.form == EPH_FORM_MIXED && !ctx->big && ctx->opt.mixed_scheme == 0) {
-    // A operand of the tensor-core Re->k contraction: 3 fixed-point BF16 digits of the phases
+    // A operand of the tensor-core Re->k contractions: 5 fixed-point BF16 digits of the phases
+    // (G3 uses the first 3 through 128-byte-swizzle maps, H(k+q) all 5 through 64-byte ones)
     const size_t slice = (size_t)nk * ctx->kpd;
-    EPH_TRY(ensure(ctx, ctx->DA, 3 * slice * 2));
-    EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_digits_a(as<double2>(ctx->Pk), ne, nk, ne, ctx->kpd, ctx->scaleA, ctx->DA.p,
-                                                  ctx->stream));
+    EPH_TRY(ensure(ctx, ctx->DA, 5 * slice * 2));
+    EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_digits_a(as<double2>(ctx->Pk), ne, nk, ne, ctx->kpd, ctx->scaleA, 5,
+                                                  ctx->DA.p, ctx->stream));
     for (int d = 0; d < 3; ++d)
       EPH_CK(make_tc_map_bf16(&ctx->mapDA[d], static_cast<char*>(ctx->DA.p) + d * slice * 2, nk, ctx->kpd, 128));
+    for (int d = 0; d < 5; ++d)
+      EPH_CK(eph::make_tc_map_bf16_sw64(&ctx->mapDA5[d], static_cast<char*>(ctx->DA.p) + d * slice * 2, nk, ctx->kpd,
+                                        128));
   } else if (ctx->opt.form == EPH_FORM_MIXED && !ctx->big) {
     // A operand of the tensor-core Re->k contraction: split-TF32 phases, K-major [nk][kp]
     EPH_TRY(ensure(ctx, ctx->Ahi, (size_t)nk * ctx->kp * sizeof(float)));
@@ -843,6 +852,10 @@ int prepare_mixed(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
   if (digits) {
     EPH_TRY(ensure(ctx, ctx->DB, 4 * dslice * 2));
     EPH_TRY(ensure(ctx, ctx->sB, (size_t)p.QB * nr * sizeof(float)));
+    const size_t hslice = (size_t)p.QB * 2 * nb2 * kpd;
+    EPH_TRY(ensure(ctx, ctx->DBH, 5 * hslice * 2));
+    EPH_TRY(ensure(ctx, ctx->sBH, (size_t)p.QB * 2 * nb2 * sizeof(float)));
+    EPH_TRY(ensure(ctx, ctx->Hpair, (size_t)p.QB * p.KT * 2 * nb2 * sizeof(float2)));
   } else {
     EPH_TRY(ensure(ctx, ctx->Bhi, (size_t)p.QB * nr * kp * sizeof(float)));
     EPH_TRY(ensure(ctx, ctx->Blo, (size_t)p.QB * nr * kp * sizeof(float)));
@@ -869,10 +882,15 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
   const bool digits = ctx->opt.mixed_scheme == 0;
   const int kpd = ctx->kpd;
   const size_t dslice = (size_t)p.QB * nr * kpd;
-  if (digits)
+  const size_t hslice = (size_t)p.QB * 2 * nb2 * kpd;
+  if (digits) {
     for (int d = 0; d < 4; ++d)
       EPH_CK(make_tc_map_bf16(&ctx->mapDB[d], static_cast<char*>(ctx->DB.p) + d * dslice * 2, (long)p.QB * nr, kpd,
                               128));
+    for (int d = 0; d < 5; ++d)
+      EPH_CK(eph::make_tc_map_bf16_sw64(&ctx->mapDBH[d], static_cast<char*>(ctx->DBH.p) + d * hslice * 2,
+                                        (long)p.QB * 2 * nb2, kpd, 128));
+  }
   if (!digits) {
     EPH_CK(make_tc_map(&ctx->mapBhi, as<float>(ctx->Bhi), (long)p.QB * nr, kp, 256));
     EPH_CK(make_tc_map(&ctx->mapBlo, as<float>(ctx->Blo), (long)p.QB * nr, kp, 256));
@@ -886,19 +904,31 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
       EPH_CK(cudaMemcpyAsync(omega + (long)q0 * nm, ctx->omq.p, (size_t)nqb * nm * sizeof(double), out_kind(ctx),
                              ctx->stream));
     // B operand per q: real embedding of the mode-rotated G2 columns of W_q
-    if (digits)
+    if (digits) {
       EPH_LAUNCH_S(EPH_STAGE_MODE, launch_digits_b(W, p.NW, (long)ne * p.NW, nb2, (int)gcols, ne, kpd, nqb,
-                                                   as<float>(ctx->sB), ctx->DB.p, (long)dslice, ctx->stream));
-    else
+                                                   as<float>(ctx->sB), ctx->DB.p, (long)dslice, 4, ctx->stream));
+      // ... and of its H(k+q) columns, 5 digits
+      EPH_LAUNCH_S(EPH_STAGE_MODE, launch_digits_b(W, p.NW, (long)ne * p.NW, 0, nb2, ne, kpd, nqb, as<float>(ctx->sBH),
+                                                   ctx->DBH.p, (long)hslice, 5, ctx->stream));
+    } else
       EPH_LAUNCH_S(EPH_STAGE_MODE, launch_split_b(W, p.NW, (long)ne * p.NW, nb2, (int)gcols, ne, kp, nqb,
                                                   as<float>(ctx->Bhi), as<float>(ctx->Blo), ctx->stream));
     for (long k0 = 0; k0 < nk; k0 += p.KT) {
       const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
-      // H(k+q) to ~1e-13 (double-float on the FP32 pipe; the eigensolve needs FP64-class input),
-      // then its FP64 Jacobi
-      EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm_df(nkt, nb2, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0, W, p.NW,
-                                                (long)ne * p.NW, as<double2>(ctx->Hkq), nb2, (long)nkt * nb2, nqb,
-                                                ctx->stream));
+      // H(k+q) to ~1e-12 (the eigensolve needs FP64-class input), then its FP64 Jacobi: on the
+      // tensor cores from 5 x 5 digits (digits scheme), else double-float on the FP32 pipe
+      if (digits) {
+        EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_tc_hkq_gemm(ctx->mapDA5, ctx->mapDBH, nkt, (int)k0, 2 * nb2, kpd, nqb,
+                                                             (float)ctx->scaleA, as<float>(ctx->sBH),
+                                                             as<float2>(ctx->Hpair), 2L * nb2, 2L * nkt * nb2,
+                                                             ctx->status + 1, ctx->stream));
+        EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_pairs_to_c128(as<float2>(ctx->Hpair), (long)nqb * nkt * nb2,
+                                                               as<double2>(ctx->Hkq), ctx->stream));
+      } else {
+        EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm_df(nkt, nb2, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0, W, p.NW,
+                                                  (long)ne * p.NW, as<double2>(ctx->Hkq), nb2, (long)nkt * nb2, nqb,
+                                                  ctx->stream));
+      }
       EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, as<double2>(ctx->Hkq), nb2, nb, nb, (long)nqb * nkt,
                                       as<double>(ctx->eps_tile), nb, as<double2>(ctx->Ukq), nb2));
       if (eps_kq)

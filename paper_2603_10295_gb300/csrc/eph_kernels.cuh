@@ -157,10 +157,18 @@ cudaError_t launch_band_rotate_ff_f64(const double2* Y, long ldy, const double2*
                                       int nm, int nb, float2* g, long sgq, cudaStream_t st);
 // Fixed-point BF16 digits (A: 3, B: 4 per value; exact tensor-core accumulation); D slices of n*kp / slice.
 cudaError_t make_tc_map_bf16(void* map_out, const void* base, long rows, int kp, int box_rows);
-cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, double scale, void* D, cudaStream_t st);
+cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, double scale, int ndig, void* D,
+                            cudaStream_t st);
 cudaError_t launch_digits_b(const double2* W, long ldw, long sW, int col0, int ncols, int ne, int kp, int nq,
-                            float* sB, void* D, long slice, cudaStream_t st);
+                            float* sB, void* D, long slice, int ndig, cudaStream_t st);
+// complex128 H[i] = (hi + lo of real output 2i, hi + lo of 2i + 1), i < n
+cudaError_t launch_pairs_to_c128(const float2* Hp, long n, double2* H, cudaStream_t st);
 // C = sA sB[col] 2^-16 sum_l 2^-8l L_l on tcgen05 kind::f16; maps: 3 CUtensorMaps (A), 4 (B).
+// 2-D BF16 tensor map, box 32 x box_rows, 64-byte swizzle (operands of the H(k+q) kernel)
+cudaError_t make_tc_map_bf16_sw64(void* map_out, const void* base, long rows, int kp, int box_rows);
+// H(k+q) on the tensor cores from 5 x 5 BF16 digits: C[q][m][n] = (hi, lo) float pairs, ldc/sC in float2
+cudaError_t launch_tc_hkq_gemm(const void* maps_a5, const void* maps_b5, int M, int a_row0, int Nr, int Kp, int nq,
+                               float sA, const float* sB, float2* C, long ldc, long sC, int* err, cudaStream_t st);
 cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
                                  float sA, const float* sB, float* C, long ldc, long sC, int* err, cudaStream_t st);
 

@@ -85,8 +85,8 @@ cudaError_t launch_split_b(const double2* W, long ldw, long sW, int col0, int nc
 // x/s = sum_i d_i 2^-8(i+1) + O(2^-8n-1), integer digits |d| <= 128, digit i stored as
 // d_i 2^-8i (exact in bf16); s is a power of two with |x| <= s/2 for every x of the row
 // (A: all rows share sA).
-// A digits: P[n][ne] complex128 (row stride ldp) -> D[3][n][kp] bf16 (slice stride n*kp).
-__global__ void k_digits_a(const double2* __restrict__ P, long ldp, int n, int ne, int kp, double inv_s,
+// A digits: P[n][ne] complex128 (row stride ldp) -> D[ndig][n][kp] bf16 (slice stride n*kp).
+__global__ void k_digits_a(const double2* __restrict__ P, long ldp, int n, int ne, int kp, double inv_s, int ndig,
                            __nv_bfloat16* __restrict__ D) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long tot = (long)n * kp;
@@ -100,8 +100,7 @@ __global__ void k_digits_a(const double2* __restrict__ P, long ldp, int n, int n
   }
   // digit i stored pre-scaled by 2^-8i (exact in bf16), so products land at their own scale
   double y = x * inv_s * 256.0, sc = 1.0;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
+  for (int d = 0; d < ndig; ++d) {
     const double a = rint(y);
     D[d * tot + idx] = __float2bfloat16_rn((float)(a * sc));
     y = (y - a) * 256.0;
@@ -109,10 +108,12 @@ __global__ void k_digits_a(const double2* __restrict__ P, long ldp, int n, int n
   }
 }
 
-cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, double scale, void* D, cudaStream_t st) {
+cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, double scale, int ndig, void* D,
+                            cudaStream_t st) {
   const long tot = (long)n * kp;
   if (tot <= 0) return cudaSuccess;
-  k_digits_a<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, ldp, n, ne, kp, 1.0 / scale,
+  if (ndig < 1 || ndig > 5) return cudaErrorInvalidValue;
+  k_digits_a<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, ldp, n, ne, kp, 1.0 / scale, ndig,
                                                           static_cast<__nv_bfloat16*>(D));
   return cudaGetLastError();
 }
@@ -139,9 +140,9 @@ __global__ void k_colscale_b(const double2* __restrict__ W, long ldw, long sW, i
   sB[(long)q * nr_stride + 2 * j + 1] = s;
 }
 
-// B digits: real embedding of the G2 columns of W (as k_split_b) scaled by sB -> D[4][QB*nr][kp].
+// B digits: real embedding of columns col0.. of W (as k_split_b) scaled by sB -> D[ndig][QB*2ncols][kp].
 __global__ void k_digits_b(const double2* __restrict__ W, long ldw, long sW, int col0, int ncols, int ne, int kp,
-                           int nq, const float* __restrict__ sB, long slice, __nv_bfloat16* __restrict__ D) {
+                           int nq, const float* __restrict__ sB, long slice, int ndig, __nv_bfloat16* __restrict__ D) {
   const long per_q = 2L * ncols * kp;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= per_q * nq) return;
@@ -157,8 +158,7 @@ __global__ void k_digits_b(const double2* __restrict__ W, long ldw, long sW, int
   }
   const double inv_s = 1.0 / (double)sB[(long)q * 2 * ncols + row];
   double y = x * inv_s * 256.0, sc = 1.0;
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
+  for (int d = 0; d < ndig; ++d) {
     const double a = rint(y);
     D[d * slice + idx] = __float2bfloat16_rn((float)(a * sc));  // pre-scaled by 2^-8d, exact
     y = (y - a) * 256.0;
@@ -167,15 +167,31 @@ __global__ void k_digits_b(const double2* __restrict__ W, long ldw, long sW, int
 }
 
 cudaError_t launch_digits_b(const double2* W, long ldw, long sW, int col0, int ncols, int ne, int kp, int nq,
-                            float* sB, void* D, long slice, cudaStream_t st) {
+                            float* sB, void* D, long slice, int ndig, cudaStream_t st) {
+  if (ndig < 1 || ndig > 5) return cudaErrorInvalidValue;
   const long cols = (long)ncols * nq;
   if (cols <= 0) return cudaSuccess;
   k_colscale_b<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, nq, sB, 2L * ncols);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long tot = 2L * ncols * kp * nq;
-  k_digits_b<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, kp, nq, sB, slice,
+  k_digits_b<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, kp, nq, sB, slice, ndig,
                                                            static_cast<__nv_bfloat16*>(D));
+  return cudaGetLastError();
+}
+
+// H(k+q) from the float pairs of the high-precision tensor-core contraction: real outputs
+// (hi, lo) at 2j (Re) and 2j + 1 (Im) -> complex128 element j, hi + lo exactly in FP64.
+__global__ void k_pairs_to_c128(const float2* __restrict__ Hp, long n, double2* __restrict__ H) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 v = reinterpret_cast<const float4*>(Hp)[i];
+  H[i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+cudaError_t launch_pairs_to_c128(const float2* Hp, long n, double2* H, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_pairs_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Hp, n, H);
   return cudaGetLastError();
 }
 

@@ -495,6 +495,235 @@ __global__ void __launch_bounds__(tcf::THREADS, 1) k_tc_fixed_gemm(const __grid_
   }
 }
 
+// ----------------------------------------------------------------------------- H(k+q) to FP64 class
+// H(k+q) = P_k (e^{iq.Re} H(Re)) needs ~1e-12 for the eigensolve, so this contraction carries
+// five fixed-point BF16 digits per operand (40 bits) and keeps every product of digit levels
+// i + j <= 4 (15 MMAs per K step).  Levels 0, 1 and 2 accumulate in separate TMEM accumulators,
+// where their integer sums are exact in FP32 (K <= 1024); levels 3 and 4 share one (its FP32
+// rounding is 2^-48 of the result).  The epilogue adds the four with two-sums into a float pair
+// (hi, lo), exact to ~2^-48 relative, scaled by the (power-of-two) operand scales.
+// Tiles 128 x 128 with K slices of 32 bf16 (64-byte rows, 64-byte swizzle) so that the ten
+// digit tiles of a stage (80 KiB) fit twice in shared memory; one accumulator set (512 TMEM
+// columns), so the next tile's MMAs wait for the epilogue.
+namespace tch {
+constexpr int BM = 128, BN = 128, BK = 32, STAGES = 2, ND = 5;
+constexpr int T_BYTES = BM * BK * 2;                           // 8 KiB per digit tile
+constexpr int STAGE_BYTES = 2 * ND * T_BYTES;                  // 80 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 512;                            // L0, L1, L2, L34 x 128 columns
+constexpr int THREADS = 192;
+
+// K-major tile of 64-byte rows with 64-byte swizzle: 8-row groups 512 B apart, descriptor v1.
+__device__ __forceinline__ uint64_t smem_desc64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;  // SWIZZLE_64B
+  return d;
+}
+
+__device__ __forceinline__ void two_sum(float& h, float& l, float x) {
+  const float s = __fadd_rn(h, x);
+  const float bb = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  h = s;
+  l = __fadd_rn(l, e);
+}
+}  // namespace tch
+
+struct TcMaps10 {
+  CUtensorMap a[5];
+  CUtensorMap b[5];
+};
+
+__global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_constant__ TcMaps10 maps, int M,
+                                                                int a_row0, int Nr, int Kp, int nq, float sA,
+                                                                const float* __restrict__ sB, float2* __restrict__ C,
+                                                                long ldc, long sC, int* __restrict__ err) {
+  using namespace tc;
+  using tch::BM;
+  using tch::BN;
+  using tch::BK;
+  using tch::STAGES;
+  using tch::ND;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * tch::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;  // the accumulators hold a finished tile
+  uint64_t* acce = accf + 1;        // the accumulators have been drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkb = Kp / BK;
+  const int ntn = (Nr + BN - 1) / BN, ntm = (M + BM - 1) / BM;
+  const long ntiles = (long)ntn * ntm * nq;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 4);  // one arrival per epilogue warp
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tch::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto tile = [&](int s, int which) -> unsigned char* { return smem + s * tch::STAGE_BYTES + which * tch::T_BYTES; };
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- TMA producer
+      long it = 0;
+      for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        int q, m0, n0;
+        tcf::tile_coords(t, ntn, nq, &q, &m0, &n0);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1))) {
+            *abort_flag = 1;
+            atomicOr(err, 1);
+            break;
+          }
+          if (*abort_flag) break;
+          mbar_arrive_expect_tx(&full[s], tch::STAGE_BYTES);
+#pragma unroll
+          for (int d = 0; d < ND; ++d) tma_load_2d(tile(s, d), &maps.a[d], kb * BK, a_row0 + m0, &full[s]);
+#pragma unroll
+          for (int d = 0; d < ND; ++d) tma_load_2d(tile(s, ND + d), &maps.b[d], kb * BK, q * Nr + n0, &full[s]);
+        }
+      }
+      if (*abort_flag)
+        for (long j = (it > STAGES ? it - STAGES : 0); j < it; ++j) mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      long it = 0, lt = 0;
+      for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++lt) {
+        if (lt >= 1 && !mbar_wait(acce, (uint32_t)((lt - 1) & 1))) {
+          *abort_flag = 1;
+          atomicOr(err, 8);
+          break;
+        }
+        fence_after();
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (*abort_flag || !mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1))) {
+            *abort_flag = 1;
+            atomicOr(err, 2);
+            ok = false;
+            break;
+          }
+          fence_after();
+          uint64_t da[ND], db[ND];
+#pragma unroll
+          for (int d = 0; d < ND; ++d) {
+            da[d] = tch::smem_desc64(smem_u32(tile(s, d)));
+            db[d] = tch::smem_desc64(smem_u32(tile(s, ND + d)));
+          }
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K
+            const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+            const uint32_t t0 = tmem, t1 = tmem + 128, t2 = tmem + 256, t3 = tmem + 384;
+            tcf::mma_bf16(t0, da[0] + o, db[0] + o, first);  // level 0
+            tcf::mma_bf16(t1, da[0] + o, db[1] + o, first);  // level 1
+            tcf::mma_bf16(t1, da[1] + o, db[0] + o, 1u);
+            tcf::mma_bf16(t2, da[0] + o, db[2] + o, first);  // level 2
+            tcf::mma_bf16(t2, da[1] + o, db[1] + o, 1u);
+            tcf::mma_bf16(t2, da[2] + o, db[0] + o, 1u);
+            tcf::mma_bf16(t3, da[0] + o, db[3] + o, first);  // levels 3 and 4
+            tcf::mma_bf16(t3, da[1] + o, db[2] + o, 1u);
+            tcf::mma_bf16(t3, da[2] + o, db[1] + o, 1u);
+            tcf::mma_bf16(t3, da[3] + o, db[0] + o, 1u);
+            tcf::mma_bf16(t3, da[0] + o, db[4] + o, 1u);
+            tcf::mma_bf16(t3, da[1] + o, db[3] + o, 1u);
+            tcf::mma_bf16(t3, da[2] + o, db[2] + o, 1u);
+            tcf::mma_bf16(t3, da[3] + o, db[1] + o, 1u);
+            tcf::mma_bf16(t3, da[4] + o, db[0] + o, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(accf);
+        if (!ok) break;
+      }
+    }
+    __syncwarp();
+  } else {  // ---- epilogue, warps 2..5: TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    long lt = 0;
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const bool ok = mbar_wait(accf, (uint32_t)(lt & 1));
+      if (!ok || *abort_flag) {
+        if (!ok) atomicOr(err, 4);
+        break;
+      }
+      fence_after();
+      int q, m0, n0;
+      tcf::tile_coords(t, ntn, nq, &q, &m0, &n0);
+      const int row = m0 + quarter * 32 + lane;
+      const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+      float2* crow = C + (long)q * sC + (long)row * ldc;
+      const float* srow = sB + (long)q * Nr;
+      const float sc = sA * 0x1p-16f;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r0[16], r1[16], r2[16], r3[16];
+        tmem_ld16(tl + c0, r0);
+        tmem_ld16(tl + 128 + c0, r1);
+        tmem_ld16(tl + 256 + c0, r2);
+        tmem_ld16(tl + 384 + c0, r3);
+        tmem_ld_wait();
+        if (row < M) {
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+            const int col = n0 + c0 + i;
+            float2 v[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              float h = __uint_as_float(r0[i + u]), l = 0.f;
+              tch::two_sum(h, l, __uint_as_float(r1[i + u]));
+              tch::two_sum(h, l, __uint_as_float(r2[i + u]));
+              tch::two_sum(h, l, __uint_as_float(r3[i + u]));
+              const float f = (col + u < Nr) ? sc * srow[col + u] : 0.f;  // powers of two: exact
+              v[u] = make_float2(h * f, l * f);
+            }
+            if (col + 1 < Nr) {
+              *reinterpret_cast<float4*>(crow + col) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+            } else if (col < Nr) {
+              crow[col] = v[0];
+            }
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) tcf::mbar_arrive(acce);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tch::TMEM_COLS) : "memory");
+  }
+}
+
 // ----------------------------------------------------------------------------- host side
 namespace {
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -540,6 +769,41 @@ cudaError_t make_tc_map_bf16(void* map_out, const void* base, long rows, int kp,
                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// 2-D BF16 tensor map over a row-major [rows][kp] array, box 32 x box_rows, 64-byte swizzle.
+cudaError_t make_tc_map_bf16_sw64(void* map_out, const void* base, long rows, int kp, int box_rows) {
+  if (!encode_fn()) return cudaErrorNotSupported;
+  if (kp % tch::BK != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || rows < 1) return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)tch::BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_hkq_gemm(const void* maps_a5, const void* maps_b5, int M, int a_row0, int Nr, int Kp, int nq,
+                               float sA, const float* sB, float2* C, long ldc, long sC, int* err, cudaStream_t st) {
+  if (M <= 0 || Nr <= 0 || nq <= 0) return cudaSuccess;
+  if (Kp % tch::BK != 0 || Kp <= 0 || Kp > 1024) return cudaErrorInvalidValue;  // exact level sums need K <= 1024
+  if ((reinterpret_cast<uintptr_t>(C) & 15) != 0 || (ldc & 1) || (sC & 1)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_hkq_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tch::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorInvalidDevice;
+  TcMaps10 maps;
+  for (int d = 0; d < 5; ++d) {
+    maps.a[d] = static_cast<const CUtensorMap*>(maps_a5)[d];
+    maps.b[d] = static_cast<const CUtensorMap*>(maps_b5)[d];
+  }
+  const long ntiles = (long)((Nr + tch::BN - 1) / tch::BN) * ((M + tch::BM - 1) / tch::BM) * nq;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  k_tc_hkq_gemm<<<grid, tch::THREADS, tch::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
