@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-form measurement")
     ap.add_argument("--no-backward", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-linewidths", action="store_true", help="skip the fused linewidth measurement")
+    ap.add_argument("--no-other", action="store_true", help="skip the MoS2- and stanene-shaped forward lines")
     ap.add_argument("--k-path", default="grid", choices=["grid", "list"],
                     help="FP64 form: sum-factorised Re->k on the workload's uniform k grid, or the dense "
                          "Re->k GEMM on the k list")
@@ -338,6 +339,48 @@ def time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=False):
             "parity": "vs oracle.linewidths <= 1e-10 per k (tests/test_gpu_linewidths.py)"}
 
 
+def time_workload(name, args, dev, legs, QB, warmup, steps):
+    """Forward throughput on another of the paper-shaped workloads (device buffers, CUDA events)."""
+    import torch
+
+    from paper_2603_10295_gb300 import binding, synth
+    wl = synth.make_workload(name)
+    nk, nb, nm = len(wl.kpts), wl.nb, wl.nm
+    q_dev = torch.from_numpy(wl.qpts[:(warmup + steps) * QB].copy()).to(dev)
+    out = {"workload": describe(wl, argparse.Namespace(q_batch=QB))}
+    for form, grid in legs:
+        st = torch.cuda.current_stream()
+        ctx = binding.Context.from_workload(wl, form=form, device_ptrs=True, q_batch=QB, stream=st)
+        if grid:
+            ctx.eph_set_k_grid(*wl.kgrid, None, None)
+        else:
+            ctx.eph_set_k(nk, torch.from_numpy(wl.kpts).to(dev), None)
+        gdt = torch.complex128 if form == "fp64" else torch.complex64
+        e = torch.empty(QB, nk, nb, dtype=torch.float64, device=dev)
+        o = torch.empty(QB, nm, dtype=torch.float64, device=dev)
+        g = torch.empty(QB, nk, nm, nb, nb, dtype=gdt, device=dev)
+        for i in range(warmup):
+            ctx.eph_interp_q(QB, q_dev[i * QB:(i + 1) * QB], e, o, g)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_reset()
+        e0.record(st)
+        for i in range(warmup, warmup + steps):
+            ctx.eph_interp_q(QB, q_dev[i * QB:(i + 1) * QB], e, o, g)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = ctx.profile_read()
+        key = form + ("_grid" if grid else "_list")
+        out[key] = {"value": QB * nk * nm * nb * nb / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                    "stage_ms_per_step": {k: round(v[0] / steps, 3) for k, v in prof.items() if v[0] > 0}}
+        del g, e, o
+        ctx.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_libeph(args):
     import numpy as np
     import torch
@@ -571,6 +614,11 @@ def run_libeph(args):
         line["e2e"] = e2e(forms[0], grid=legs[0][1])
         if "mixed" in line:
             line["mixed"]["e2e"] = e2e("mixed", grid=use_grid)
+    if rank == 0 and not args.no_other:
+        # the MoS2-shaped (200x200 grid, Nb=11, Nm=9) and stanene-shaped (Nb=120, Nm=180) workloads
+        line["other_workloads"] = {
+            "mos2": time_workload("mos2", args, dev, [("fp64", True), ("mixed", True), ("mixed", False)], QB, 2, 5),
+            "stanene": time_workload("stanene", args, dev, [("fp64", False), ("mixed", False)], 1, 1, 1)}
     if rank == 0 and not args.no_linewidths:
         line["linewidths"] = time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=legs[0][1])
     if rank == 0 and not args.no_backward:
