@@ -98,6 +98,9 @@ struct eph_ctx {
   CUtensorMap mapDA5[5]{}, mapDBH[5]{};
   // shapes beyond the warp kernels (nb or nm > 16): CTA Jacobi work, transposed u, band-rotation temp
   bool big = false;
+  bool ws_auto = false;  // workspace_mb left at 0: the k tile may grow to whole eigensolve waves
+  int nsm = 1;           // SM count
+  size_t mem_total = 0;  // device memory
   DBuf jwork, ut, Tbuf;
   // linewidth consumer: q weights, per-(q,k) partials, accumulator
   DBuf wqb, lwpart, lwacc;
@@ -177,9 +180,14 @@ T* as(DBuf& b) {
 // the mixed form, whose g is bound at 1e-6, to 1e-12 ||A|| (eigenvalues still within
 // 1e-12 ||A|| by Weyl's bound), about one FP64 sweep fewer.
 cudaError_t eig(eph_ctx* c, const double2* A, long sA, long lda, int n, long batch, double* w, long sw,
-                double2* V, long sV) {
-  if (n > 16) {  // CTA-per-matrix FP64 Jacobi on a global working copy
-    const size_t need = (size_t)batch * n * n * sizeof(double2);
+                double2* V, long sV, bool full = false) {
+  // full: FP64 eigendecomposition in either form (the dynamical matrices, whose small
+  // eigenvalues set the phonon frequencies' relative accuracy)
+  const bool mixed_tol = c->opt.form == EPH_FORM_MIXED && !full;
+  if (n > 16) {  // CTA per matrix: FP32-preconditioned unless plain FP64 sweeps are requested
+    const bool pre = !c->opt.eig_plain_fp64 && eph::eigh_big_supported(n);
+    const size_t need = pre ? eph::eigh_big_work_bytes(n, batch < 65535 ? batch : 65535)
+                            : (size_t)batch * n * n * sizeof(double2);
     if (c->jwork.n < need) {
       if (c->jwork.p) cudaFree(c->jwork.p);
       c->jwork.p = nullptr;
@@ -187,12 +195,16 @@ cudaError_t eig(eph_ctx* c, const double2* A, long sA, long lda, int n, long bat
       if (cudaMalloc(&c->jwork.p, need) != cudaSuccess) return cudaErrorMemoryAllocation;
       c->jwork.n = need;
     }
+    if (pre)
+      return eph::launch_eigh_big(A, sA, lda, n, batch, w, sw, V, sV, c->jwork.p,
+                                  mixed_tol ? 1e-12 : 1e-15, c->opt.max_sweeps, c->status,
+                                  c->stream);
     return eph::launch_jacobi_big(A, sA, lda, n, batch, w, sw, V, sV, static_cast<double2*>(c->jwork.p),
                                   c->opt.max_sweeps, c->status, c->stream);
   }
   if (c->opt.eig_plain_fp64)
     return eph::launch_jacobi(A, sA, lda, n, batch, w, sw, V, sV, c->opt.max_sweeps, c->status, c->stream);
-  const double tol = c->opt.form == EPH_FORM_MIXED ? 1e-12 : 1e-17;
+  const double tol = mixed_tol ? 1e-12 : 1e-17;
   return eph::launch_jacobi_mixed(A, sA, lda, n, batch, w, sw, V, sV, c->opt.max_sweeps, tol, c->status, c->stream);
 }
 
@@ -354,7 +366,15 @@ int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re
   else
     eph_default_options(&ctx->opt);
   if (ctx->opt.max_sweeps <= 0) ctx->opt.max_sweeps = 20;
+  ctx->ws_auto = ctx->opt.workspace_mb <= 0;
   if (ctx->opt.workspace_mb <= 0) ctx->opt.workspace_mb = 4096;
+  {
+    int dev = 0;
+    size_t fr = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (ctx->nsm < 1) ctx->nsm = 1;
+    if (cudaMemGetInfo(&fr, &ctx->mem_total) != cudaSuccess) ctx->mem_total = 0;
+  }
   int rc = EPH_OK;
   const int nm = ctx->nm, nb2 = nb * nb;
   auto bail = [&](int code) {
@@ -658,10 +678,19 @@ QPlan plan_q(const eph_ctx* ctx, int nq, size_t extra_per_pair) {
   if (p.QB > nq) p.QB = nq;
   // bytes per (q,k) pair in the k stage
   size_t per_pair = (size_t)p.NW * 16 + (size_t)nb2 * 16 + (size_t)ctx->nb * 8 + extra_per_pair;
-  if (ctx->big) per_pair += (size_t)ctx->nm * nb2 * 16 / p.QB + (size_t)nb2 * 16;  // band temp, Jacobi copy
+  if (ctx->big)  // band temp, eigensolver work (A', V, two products, eigenvalues)
+    per_pair += (size_t)ctx->nm * nb2 * 16 / p.QB + (size_t)nb2 * 16 * 4 + (size_t)ctx->nb * 8;
   const size_t budget = (size_t)ctx->opt.workspace_mb << 20;
   long KT = ctx->opt.k_tile > 0 ? ctx->opt.k_tile : (long)(budget / (per_pair * p.QB));
   if (KT > ctx->nk) KT = ctx->nk;
+  if (ctx->big && ctx->opt.k_tile <= 0 && KT < ctx->nk) {
+    // the eigensolve runs a CTA per matrix: a tile of QB x KT matrices should fill whole
+    // waves of the SMs (the automatic budget grows to one wave, up to 1/8 of the device)
+    const long wave = (ctx->nsm + p.QB - 1) / p.QB;
+    if (KT < wave && ctx->ws_auto && per_pair * p.QB * (size_t)wave <= ctx->mem_total / 8) KT = wave;
+    if (KT > wave) KT -= KT % wave;
+    if (KT > ctx->nk) KT = ctx->nk;
+  }
   if (ctx->big && p.QB * KT > 65535) KT = 65535 / p.QB;  // CTA-per-matrix eigensolve grid
   if (ctx->has_grid) {  // whole j1 slabs of the grid
     const long slab = (long)ctx->gn[1] * ctx->gn[2];
@@ -712,7 +741,7 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
   EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny_real(nqb, (long)nm * nm, np, Pp, np, ctx->Phi, (long)nm * nm,
                                                   ctx->dscale, as<double2>(ctx->D), (long)nm * nm, ctx->stream));
   EPH_LAUNCH_S(EPH_STAGE_MODE, eig(ctx, as<double2>(ctx->D), (long)nm * nm, nm, nm, nqb, as<double>(ctx->lamq), nm,
-                                   as<double2>(ctx->evq), (long)nm * nm));
+                                   as<double2>(ctx->evq), (long)nm * nm, true));
   EPH_LAUNCH_S(EPH_STAGE_MODE, launch_phonon_post(as<double>(ctx->lamq), as<double2>(ctx->evq), nqb, nm,
                                                   ctx->invsqrtm, ctx->omega_unit, as<double>(ctx->omq),
                                                   as<double2>(ctx->uq), ctx->stream));

@@ -68,6 +68,15 @@ cudaError_t launch_jacobi_mixed(const double2* A, long sA, long lda, int n, long
 // work [batch][n][n]; V must be packed (sV = n*n).
 cudaError_t launch_jacobi_big(const double2* A, long sA, long lda, int n, long batch, double* w, long sw, double2* V,
                               long sV, double2* work, int max_sweeps, int* status, cudaStream_t st);
+// Same contract, preconditioned: FP32 sweeps on a packed copy in shared memory, Newton-Schulz
+// and A' = V^H A V as batched FP64 GEMMs, FP64 sweeps on A' to a first-order finish
+// (polish_tol 1e-15: FP64 eigendecomposition; >= 1e-13: eigenvectors to ~1e-12).
+// work: eigh_big_work_bytes(n, min(batch, 65535)) bytes.  eigh_big_supported(n): the packed
+// FP32 copy fits in shared memory (n <= ~230 on GB300).
+bool eigh_big_supported(int n);
+size_t eigh_big_work_bytes(int n, long batch);
+cudaError_t launch_eigh_big(const double2* A, long sA, long lda, int n, long batch, double* w, long sw, double2* V,
+                            long sV, void* work, double polish_tol, int max_sweeps, int* status, cudaStream_t st);
 
 // ---- phonon post-processing: omega = sign(l) sqrt|l| * unit; u = e / sqrt(M)
 cudaError_t launch_phonon_post(const double* lam, const double2* e, int nq, int nm, const double* invsqrtm,

@@ -609,188 +609,3 @@ cudaError_t launch_jacobi(const double2* A, long sA, long lda, int n, long batch
 }
 
 }  // namespace eph
-
-namespace eph {
-
-// ----------------------------------------------------------------------------
-// Larger matrices (16 < n <= 256): one CTA per matrix, FP64 parallel Jacobi on a
-// global-memory working copy (too large for registers or shared memory: a complex
-// 120x120 matrix is 230 KB).  Each round rotates the n/2 disjoint pairs of the
-// circle schedule: the CTA computes the pair parameters, mixes columns of A and V
-// (A J, V J), then rows (J^H A), then writes the exact 2x2 block values.  Same
-// rotation formula and stopping rule as the warp kernel (one extra sweep after the
-// off-diagonal norm falls below 1e-15 ||A||_F; cap max_sweeps -> *status |= 1).
-// ----------------------------------------------------------------------------
-namespace {
-__host__ __device__ inline int rr_partner_rt(int j, int r, int np) {
-  return (j == np - 1) ? r : (j == r ? np - 1 : ((2 * r - j) % (np - 1) + (np - 1)) % (np - 1));
-}
-}  // namespace
-
-__global__ void __launch_bounds__(1024) k_jacobi_big(const double2* __restrict__ A, long sA, long lda, int n,
-                                                    double* __restrict__ w, long sw, double2* __restrict__ V, long sV,
-                                                    double2* __restrict__ work, int max_sweeps,
-                                                    int* __restrict__ status) {
-  __shared__ int sp[128], sq[128];
-  __shared__ double sc[128], stb[128], sapp[128], saqq[128];
-  __shared__ double2 ssg[128];
-  __shared__ double red[32];
-  __shared__ int s_flag;
-  __shared__ int srank[256];
-  const long mat = blockIdx.x;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const long nn = (long)n * n;
-  double2* M = work + mat * nn;    // working copy, row-major
-  double2* U = V + mat * sV;       // accumulated eigenvectors, row-major (columns)
-  const double2* Ain = A + mat * sA;
-  for (long i = tid; i < nn; i += nt) {
-    const int r = (int)(i / n), c = (int)(i - (long)r * n);
-    double2 v = Ain[(long)r * lda + c];
-    if (r == c) v.y = 0.0;
-    M[i] = v;
-    U[i] = make_double2(r == c ? 1.0 : 0.0, 0.0);
-  }
-  __syncthreads();
-  auto block_sum = [&](double x) -> double {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if ((tid & 31) == 0) red[tid >> 5] = x;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < (nt >> 5); ++i) t += red[i];
-    __syncthreads();
-    return t;
-  };
-  double part = 0.0;
-  for (long i = tid; i < nn; i += nt) part = fma(M[i].x, M[i].x, fma(M[i].y, M[i].y, part));
-  const double fro2 = block_sum(part);
-  const double thresh2 = 1e-36 * fro2 + 1e-300;
-  const double tol2 = 1e-30 * fro2;
-  const int np = (n + 1) & ~1, npairs = np / 2;
-  bool conv = false;
-  int post = 0, sweep = 0;
-  while (!(conv && post >= 1) && sweep < max_sweeps) {
-    for (int r = 0; r < np - 1; ++r) {
-      // pair parameters
-      for (int i = tid; i < npairs; i += nt) {
-        int p = i == 0 ? r : (r + i) % (np - 1);
-        int q = rr_partner_rt(p, r, np);
-        if (i == 0) q = np - 1;
-        if (p > q) {
-          const int t = p;
-          p = q;
-          q = t;
-        }
-        double c = 1.0, tb = 0.0;
-        double2 sig = make_double2(0.0, 0.0);
-        double app = 0.0, aqq = 0.0;
-        if (q < n) {
-          app = M[(long)p * n + p].x;
-          aqq = M[(long)q * n + q].x;
-          const double2 b = M[(long)p * n + q];
-          const double b2 = fma(b.x, b.x, b.y * b.y);
-          if (b2 > thresh2) {
-            const double dd = aqq - app;
-            const double rr = copysign(2.0, dd) / (fabs(dd) + sqrt(fma(dd, dd, 4.0 * b2)));
-            tb = rr * b2;
-            c = rsqrt(fma(rr * rr, b2, 1.0));
-            sig = make_double2(c * rr * b.x, c * rr * b.y);
-          }
-        }
-        sp[i] = p;
-        sq[i] = q;
-        sc[i] = c;
-        ssg[i] = sig;
-        stb[i] = tb;
-        sapp[i] = app;
-        saqq[i] = aqq;
-      }
-      __syncthreads();
-      // columns of A and V: col_p' = c col_p - conj(sig) col_q, col_q' = sig col_p + c col_q
-      for (long idx = tid; idx < (long)npairs * n; idx += nt) {
-        const int x = (int)(idx / npairs), i = (int)(idx - (long)x * npairs);
-        const int p = sp[i], q = sq[i];
-        if (q >= n) continue;
-        const double c = sc[i];
-        const double2 s = ssg[i];
-        double2* rowA = M + (long)x * n;
-        double2* rowU = U + (long)x * n;
-        const double2 ap = rowA[p], aq = rowA[q], up = rowU[p], uq = rowU[q];
-        rowA[p] = make_double2(fma(c, ap.x, -fma(s.x, aq.x, s.y * aq.y)), fma(c, ap.y, -fma(s.x, aq.y, -s.y * aq.x)));
-        rowA[q] = make_double2(fma(c, aq.x, fma(s.x, ap.x, -s.y * ap.y)), fma(c, aq.y, fma(s.x, ap.y, s.y * ap.x)));
-        rowU[p] = make_double2(fma(c, up.x, -fma(s.x, uq.x, s.y * uq.y)), fma(c, up.y, -fma(s.x, uq.y, -s.y * uq.x)));
-        rowU[q] = make_double2(fma(c, uq.x, fma(s.x, up.x, -s.y * up.y)), fma(c, uq.y, fma(s.x, up.y, s.y * up.x)));
-      }
-      __syncthreads();
-      // rows of A: row_p' = c row_p - sig row_q, row_q' = conj(sig) row_p + c row_q
-      for (long idx = tid; idx < (long)npairs * n; idx += nt) {
-        const int i = (int)(idx / n), y = (int)(idx - (long)i * n);
-        const int p = sp[i], q = sq[i];
-        if (q >= n) continue;
-        const double c = sc[i];
-        const double2 s = ssg[i];
-        double2* a = M + (long)p * n + y;
-        double2* b = M + (long)q * n + y;
-        const double2 xl = *a, xh = *b;
-        *a = make_double2(fma(c, xl.x, -fma(s.x, xh.x, -s.y * xh.y)), fma(c, xl.y, -fma(s.x, xh.y, s.y * xh.x)));
-        *b = make_double2(fma(c, xh.x, fma(s.x, xl.x, s.y * xl.y)), fma(c, xh.y, fma(s.x, xl.y, -s.y * xl.x)));
-      }
-      __syncthreads();
-      // exact values of each rotated 2x2 block
-      for (int i = tid; i < npairs; i += nt) {
-        const int p = sp[i], q = sq[i];
-        if (q >= n) continue;
-        M[(long)p * n + q] = make_double2(0.0, 0.0);
-        M[(long)q * n + p] = make_double2(0.0, 0.0);
-        M[(long)p * n + p] = make_double2(sapp[i] - stb[i], 0.0);
-        M[(long)q * n + q] = make_double2(saqq[i] + stb[i], 0.0);
-      }
-      __syncthreads();
-    }
-    ++sweep;
-    if (conv) ++post;
-    part = 0.0;
-    for (long i = tid; i < nn; i += nt) {
-      const int r = (int)(i / n), c = (int)(i - (long)r * n);
-      if (r != c) part = fma(M[i].x, M[i].x, fma(M[i].y, M[i].y, part));
-    }
-    const double off = block_sum(part);
-    if (off <= tol2) conv = true;
-  }
-  if (tid == 0) s_flag = conv ? 0 : 1;
-  __syncthreads();
-  if (tid == 0 && s_flag) atomicOr(status, 1);
-  // sort ascending (ties by index): ranks from the diagonal, then permute the columns of U
-  for (int j = tid; j < n; j += nt) {
-    const double lam = M[(long)j * n + j].x;
-    int rank = 0;
-    for (int i = 0; i < n; ++i) {
-      const double li = M[(long)i * n + i].x;
-      if (li < lam || (li == lam && i < j)) ++rank;
-    }
-    w[mat * sw + rank] = lam;
-    srank[j] = rank;
-  }
-  __syncthreads();
-  for (long i = tid; i < nn; i += nt) M[i] = U[i];
-  __syncthreads();
-  for (long i = tid; i < nn; i += nt) {
-    const int r = (int)(i / n), j = (int)(i - (long)r * n);
-    U[(long)r * n + srank[j]] = M[i];
-  }
-}
-
-cudaError_t launch_jacobi_big(const double2* A, long sA, long lda, int n, long batch, double* w, long sw, double2* V,
-                              long sV, double2* work, int max_sweeps, int* status, cudaStream_t st) {
-  if (batch <= 0) return cudaSuccess;
-  if (n < 1 || n > 256 || sV != (long)n * n) return cudaErrorInvalidValue;
-  if (batch > 2147483647L) return cudaErrorInvalidConfiguration;
-  // a round's column and row mixes touch n^2 / 2 elements each; with few matrices per SM the
-  // latency of these global (L2-resident) accesses needs many threads in flight: about n^2 / 8
-  // threads (128 .. 1024)
-  int threads = ((n * n / 8 + 31) / 32) * 32;
-  threads = threads < 128 ? 128 : (threads > 1024 ? 1024 : threads);
-  k_jacobi_big<<<(unsigned)batch, threads, 0, st>>>(A, sA, lda, n, w, sw, V, sV, work, max_sweeps, status);
-  return cudaGetLastError();
-}
-
-}  // namespace eph
