@@ -42,10 +42,14 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # Keyed by (kernel, workload, q batch).
 # FP64 flops per matrix of the batched H(k+q) eigensolve (2 x DFMA + DADD + DMUL thread
 # instructions executed, from one ncu capture; profiles/k_jacobi_mixed_si_full.md), keyed by (nb, form)
-EIG_FP64_FLOPS = {(8, "fp64"): (2 * 4311850240 + 364618112 + 270336000) / 256000}
+# FP64 flops per 8x8 eigensolve (2 DFMA + DMUL + DADD thread instructions from one ncu capture of
+# the 256,000-matrix launch: 1.9087e9 DFMA, 2.785e8 DMUL, 4.895e8 DADD)
+EIG_FP64_FLOPS = {(8, "fp64"): (2 * 1908736000 + 278528000 + 489472000) / 256000}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch at one step = 4 q x 64,000 k
 TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
            ("k_zgemm", "si_full", 4): 242432512.0 + 1777470464.0,
-           ("k_jacobi_mixed", "si_full", 4): 263366400.0 + 231316480.0}
+           ("k_jacobi_mixed", "si_full", 4): 262383616.0 + 231961088.0,
+           ("k_band_rotate", "si_full", 4): 2097860096.0 + 1534897664.0}
 
 
 def parse():
@@ -455,9 +459,14 @@ def run_libeph(args):
         cmac = 2.0 * nb ** 3 * nm * QB * nk          # V_kq^H G3 V_k per (q,k) pair
         t = bd_ms / max(args.steps, 1) * 1e-3
         ach = 6.0 * cmac / t                         # three-multiplication form: 3 FMA per CMAC
+        pairs = float(QB) * nk
         return {"bound": "alu", "kernel": "k_band_rotate (FP64, three-multiplication products)",
                 "achieved": ach / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_FLOPS, "flop_per_cmac": 6}
+                "frac": ach / FP64_PEAK_FLOPS, "flop_per_cmac": 6,
+                "traffic": TRAFFIC.get(("k_band_rotate", args.workload, QB)),
+                # G3 rows, V_k and V_{k+q} read, g written (complex128)
+                "algorithmic_bytes": 16.0 * (pairs * (nm * nb * nb + nb * nb + nb * nb) + pairs * nm * nb * nb),
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
 
     def roof_eig(r):
         eg_ms, eg_n = r["prof"]["eig"]
@@ -465,8 +474,8 @@ def run_libeph(args):
         t = eg_ms / max(eg_n, 1) * 1e-3
         mats = float(args.steps) * QB * nk / max(eg_n, 1)
         ach = per * mats / t if per else None
-        return {"bound": "alu", "kernel": "k_jacobi_mixed<%d> (FP32 sweeps, FP64 Newton-Schulz, V^H A V, FP64 "
-                                          "polish sweep, first-order finish)" % (nb + (nb & 1)),
+        return {"bound": "alu", "kernel": "k_jacobi_mixed<%d> (FP32 Jacobi sweeps, two FP64 Ogita-Aishima "
+                                          "refinement steps)" % (nb + (nb & 1)),
                 "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_FLOPS if ach else None,
                 "fp64_flop_per_matrix": per, "matrices_per_launch": mats,
@@ -539,7 +548,7 @@ def run_libeph(args):
                 "roofline": dominant_roofline(head) if forms[0] == "fp64" else roof_tc(head),
                 "gpu_launches": head["launches"], "clocks": head["clocks"]}
         if forms[0] == "fp64":
-            line["stage_rooflines"] = {"band": roof_band(head)}
+            line["stage_rooflines"] = {"band": roof_band(head), "eig": roof_eig(head)}
             if legs[0][1]:
                 line["stage_rooflines"]["ft_k"] = roof_axis(head)
         if ("mixed", use_grid) in res and forms[0] == "fp64":
@@ -547,7 +556,7 @@ def run_libeph(args):
             line["mixed"] = {"value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"],
                              "k_path": line["config"]["k_path"],
                              "gain_vs_fp64": m["value"] / head["value"],
-                             "dtype": "f64 Re->k and eigensolve polish, double-float band rotation, c64 g"
+                             "dtype": "f64 Re->k and eigensolve refinement, double-float band rotation, c64 g"
                                       if use_grid else "bf16 digits / f32 accumulate",
                              "rel_err_bar": "<= 1e-6 on |g|^2 subspace sums (tests/test_gpu_mixed.py, "
                                             "tests/test_gpu_grid.py); eps, omega <= 1e-10",

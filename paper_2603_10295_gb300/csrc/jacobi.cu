@@ -331,21 +331,33 @@ __global__ void __launch_bounds__(128) k_jacobi(const double2* __restrict__ A, l
   }
 }
 
-// FP32-preconditioned variant: the same sweeps first run in FP32 (64x the FP64
-// rate on GB300) to an off-diagonal norm of ~1e-6 ||A||; V is then made unitary
-// to rounding level with two FP64 Newton-Schulz steps V <- V (3I - V^H V)/2 (one step,
-// non-unitarity ~4e-13, when polishing to 1e-12), the FP64
-// matrix is rotated, A' = V^H A V (off-diagonal ~1e-7 ||A||), and FP64 sweeps
-// finish it (quadratic convergence) to an off-diagonal norm below
-// polish_tol ||A||_F: 1e-17 (about two sweeps) gives the FP64 eigendecomposition;
-// 1e-12 (about one sweep) still bounds every eigenvalue error by 1e-12 ||A||
-// (Weyl) and the eigenvector error by 1e-12 ||A|| / gap.
+// FP32-preconditioned variant: the same sweeps first run in FP32 (64x the FP64 rate on
+// GB300) to an off-diagonal norm of ~1e-6 ||A||, then the FP32 eigenvectors X are refined
+// in FP64 by the Ogita-Aishima iteration (Ogita & Aishima, Japan J. Indust. Appl. Math. 35,
+// 2018), written for Hermitian A with the correction split into Hermitian and
+// anti-Hermitian parts:
+//   R = I - X^H X,  S = X^H A X,  lam_j = S_jj / (X^H X)_jj,
+//   K_ij = (S_ij + (lam_i + lam_j) R_ij / 2) / (lam_j - lam_i)  (K^H = -K, one numerator per pair),
+//   X <- X (I + R/2 + K),
+// which makes X unitary and A-diagonal to second order in |R/2 + K| (the quadratic step of
+// Newton's method for the eigendecomposition).  The FP64 work per step is three products
+// of n^3 / 2 to n^3 complex multiply-adds (the Hermitian X^H X and X^H (A X) on half of
+// the pairs); the update X (R/2 + K), a small correction, runs in FP32.  lam_j plus the
+// second-order shift sum_i |K_ij|^2 (lam_j - lam_i) is accurate to third order.
+// A step is final once every |(R/2 + K)_ij| <= th (X then exact to th^2): th = 1e-8 for
+// the FP64 eigendecomposition (two steps from FP32), 1e-4 when eigenvectors are needed to
+// ~1e-8 and eigenvalues to 1e-12 ||A|| (one step).  Pairs whose first-order angle would
+// exceed 1e-3 (near-degenerate relative to the FP32 accuracy) are left out of K; if such a
+// pair still couples above rounding level (4e-15 ||A||_F; 1e-11 for the looser target)
+// after three steps, the warp falls back to the robust sequence: two Newton-Schulz steps,
+// A' = V^H A V and FP64 Jacobi sweeps to polish_tol ||A||_F with a first-order finish.
 template <int NP>
 __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict__ A, long sA, long lda, int n,
                                                       long batch, double* __restrict__ w, long sw,
                                                       double2* __restrict__ V, long sV, int max_sweeps,
                                                       double polish_tol, int* __restrict__ status) {
   constexpr int G = 32 / NP;
+  constexpr int H = NP / 2;
   const int lane = threadIdx.x & 31;
   const int grp0 = lane / NP;
   const bool in_group = grp0 < G;
@@ -368,18 +380,22 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
   double fro2 = 0.0;
 #pragma unroll
   for (int i = 0; i < NP; ++i) fro2 += shfl_d(my2, base + i);
+  // power of two near 1 / ||A||_F: keeps the FP32 copy and the FP32 reciprocals in range
+  int fexp = 0;
+  frexp(sqrt(fro2), &fexp);
+  const double isc = fro2 > 0.0 ? ldexp(1.0, -fexp) : 1.0;
 
-  // ---- FP32 preconditioning sweeps
+  // ---- FP32 preconditioning sweeps (on A scaled to ||A||_F ~ 1)
   double2 v[NP];
-  float2 vf[NP];  // the FP32 eigenvectors, kept for the FP32 part of the Newton-Schulz corrections
   {
+    float2 vf[NP];
     float2 af[NP];
 #pragma unroll
     for (int r = 0; r < NP; ++r) {
-      af[r] = make_float2((float)a[r].x, (float)a[r].y);
+      af[r] = make_float2((float)(a[r].x * isc), (float)(a[r].y * isc));
       vf[r] = make_float2(r == j ? 1.f : 0.f, 0.f);
     }
-    const float fro2f = (float)fro2;
+    const float fro2f = (float)(fro2 * isc * isc);
     const float thr32 = 1e-30f * fro2f + 1e-37f;
     const float tol32 = 1e-12f * fro2f;
     bool c32 = !valid;
@@ -393,158 +409,307 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
 #pragma unroll
     for (int r = 0; r < NP; ++r) v[r] = make_double2((double)vf[r].x, (double)vf[r].y);
   }
-  // ---- Newton-Schulz steps V <- V (3I - V^H V)/2 = V - V E/2, E = V^H V - I: the Gram matrix in
-  // FP64; the correction V E/2 (|E| ~ 1e-7, then ~1e-14) needs only FP32's relative precision
-  // (non-unitarity after the steps: ~1e-14, then rounding level); one step when polishing to 1e-12
-  const int ns_steps = polish_tol >= 1e-13 ? 1 : 2;
-#pragma unroll 1
-  for (int it = 0; it < ns_steps; ++it) {
-    float2 corr[NP];
-#pragma unroll
-    for (int r = 0; r < NP; ++r) corr[r] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      double2 vi[NP];
-      double gx = 0.0, gy = 0.0;
-#pragma unroll
-      for (int r = 0; r < NP; ++r) {
-        vi[r] = shfl_d2(v[r], base + i);
-        gx = fma(vi[r].x, v[r].x, fma(vi[r].y, v[r].y, gx));
-        gy = fma(vi[r].x, v[r].y, fma(-vi[r].y, v[r].x, gy));
-      }
-      if (i == j) gx -= 1.0;
-      const float ex = (float)gx, ey = (float)gy;
-      // V E with V at FP32 precision: the FP32 eigenvectors (within 1e-7 of V) by shuffle,
-      // no FP64 -> FP32 conversions
-#pragma unroll
-      for (int r = 0; r < NP; ++r) {
-        const float2 w = shfl_d2(vf[r], base + i);
-        corr[r].x = fmaf(w.x, ex, fmaf(-w.y, ey, corr[r].x));
-        corr[r].y = fmaf(w.x, ey, fmaf(w.y, ex, corr[r].y));
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < NP; ++r) {
-      v[r].x -= (double)(0.5f * corr[r].x);
-      v[r].y -= (double)(0.5f * corr[r].y);
-    }
-  }
-  double2 (&vn)[NP] = v;
-  // ---- A' = V^H A V:  w = A v_j (columns of A from all lanes), then A'[i][j] = v_i^H w
-  {
-    double2 wv[NP];
-#pragma unroll
-    for (int r = 0; r < NP; ++r) wv[r] = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int s2 = 0; s2 < NP; ++s2) {
-      const double2 vs = vn[s2];
-#pragma unroll
-      for (int r = 0; r < NP; ++r) {
-        const double2 cs = shfl_d2(a[r], base + s2);  // A[r][s2]
-        wv[r].x = fma(cs.x, vs.x, fma(-cs.y, vs.y, wv[r].x));
-        wv[r].y = fma(cs.x, vs.y, fma(cs.y, vs.x, wv[r].y));
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      double ax = 0.0, ay = 0.0;
-#pragma unroll
-      for (int r = 0; r < NP; ++r) {
-        const double2 vi = shfl_d2(vn[r], base + i);
-        ax = fma(vi.x, wv[r].x, fma(vi.y, wv[r].y, ax));
-        ay = fma(vi.x, wv[r].y, fma(-vi.y, wv[r].x, ay));
-      }
-      a[i] = make_double2(ax, (i == j) ? 0.0 : ay);
-    }
-  }
-  // padded columns stay exact unit vectors with zero coupling
-  if (j >= n) {
-#pragma unroll
-    for (int r = 0; r < NP; ++r) {
-      a[r] = make_double2(0.0, 0.0);
-      v[r] = make_double2(r == j ? 1.0 : 0.0, 0.0);
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < NP; ++r)
-    if (r >= n && j < n) a[r] = make_double2(0.0, 0.0);
 
-  // ---- FP64 sweeps until the off-diagonal norm is below polish_tol ||A||_F
-  const double thresh2 = 1e-36 * fro2 + 1e-300;
-  const double tol2 = polish_tol * polish_tol * fro2;
-  bool conv = !valid;
-  int sweep = 0;
-  double delta = 0.0;  // this column's accumulated scale 1 + delta from unnormalised rotations
-  // first-order finish: once every remaining angle |A_ij / (A_jj - A_ii)| is below theta_max,
-  // v_j += sum_i v_i A_ij / (A_jj - A_ii) completes the eigenvectors to theta_max^2 (the update
-  // is anti-Hermitian to first order, so V stays unitary to the same order) and
-  // A_jj + sum_i |A_ij|^2 / (A_jj - A_ii) the eigenvalues to theta_max^3 ||A||: one pass of
-  // NP-1 column updates instead of a sweep.  theta_max = 1e-8 when polishing to rounding
-  // level (reached after one sweep), 1e-5 when polishing to 1e-12 (usually right after A').
-  const double th2 = polish_tol >= 1e-13 ? 1e-10 : 1e-16;
-  const bool try_before_sweep = polish_tol >= 1e-13;  // angles ~1e-6 after A': worth trying at 1e-5 only
-  for (;;) {
-    if (__all_sync(0xffffffffu, conv)) break;
-    if (sweep > 0 || try_before_sweep) {
-      unit_scale<NP>(a, v, base, delta);
-      double lj = 0.0;
+  // ---- refinement
+  const bool loose = polish_tol >= 1e-13;
+  const double th_fin = loose ? 1e-4 : 1e-8;
+  const double tolc2 = (loose ? 1e-22 : 1.6e-29) * fro2;  // (1e-11 ||A||_F)^2, (4e-15 ||A||_F)^2
+  const double thc2 = 1e-6;                                  // (largest first-order angle)^2
+  double pa[NP];  // 3M pre-sums of the own column of A, sent with it
 #pragma unroll
-      for (int r = 0; r < NP; ++r)
-        if (r == j) lj = a[r].x;
-      bool small = true;
-      double li[NP];
+  for (int r = 0; r < NP; ++r) pa[r] = a[r].x + a[r].y;
+  bool done = !valid;
+  double lam = 0.0;
+#pragma unroll 1
+  for (int step = 0; step < 3; ++step) {
+    if (__all_sync(0xffffffffu, done)) break;
+    double xp[NP], xm[NP];
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      xp[r] = v[r].x + v[r].y;
+      xm[r] = v[r].x - v[r].y;
+    }
+    // w = A x_j (three multiplications per complex product)
+    double2 wv[NP];
+    double wp[NP];
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+#pragma unroll
+      for (int s2 = 0; s2 < NP; ++s2) {
+        const double2 ars = shfl_d2(a[r], base + s2);  // A[r][s2]
+        const double prs = shfl_d(pa[r], base + s2);
+        t1 = fma(ars.x, v[s2].x, t1);
+        t2 = fma(ars.y, v[s2].y, t2);
+        t3 = fma(prs, xp[s2], t3);
+      }
+      wv[r] = make_double2(t1 - t2, t3 - t1 - t2);
+      wp[r] = wv[r].x + wv[r].y;
+    }
+    // slot d: the pair (i = j + d mod NP, j); g = x_i^H x_j, s = x_i^H w_j
+    auto pair_products = [&](int src, double2& g, double2& sv) {
+      double g1 = 0.0, g2 = 0.0, g3 = 0.0, s1 = 0.0, s2v = 0.0, s3 = 0.0;
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        const double2 xi = shfl_d2(v[r], src);
+        const double mi = shfl_d(xm[r], src);
+        g1 = fma(xi.x, v[r].x, g1);
+        g2 = fma(xi.y, v[r].y, g2);
+        g3 = fma(mi, xp[r], g3);
+        s1 = fma(xi.x, wv[r].x, s1);
+        s2v = fma(xi.y, wv[r].y, s2v);
+        s3 = fma(mi, wp[r], s3);
+      }
+      g = make_double2(g1 + g2, g3 - g1 + g2);
+      sv = make_double2(s1 + s2v, s3 - s1 + s2v);
+    };
+    double2 g0, s0;
+    pair_products(base + j, g0, s0);
+    // Rayleigh quotient of x_j: 1 / g0 = 1 + e + e^2 + e^3 with e = 1 - g0 (|e| ~ 1e-6, then
+    // ~1e-12; a larger |e| leaves the step unconverged through the diagonal of R/2)
+    const double e0 = 1.0 - g0.x;
+    const double lt = s0.x * fma(e0, fma(e0, e0 + 1.0, 1.0), 1.0);
+    double emx = 0.25 * e0 * e0;  // squared bound on |E_ij| (no square roots on the FP64 pipe)
+    double shift = 0.0;
+    int unres = 0;
+    float2 er[NP];  // er[d] = E_{(j+d) mod NP, j}
+    er[0] = make_float2((float)(0.5 * (1.0 - g0.x)), 0.f);
+    float2 hf[H], kf[H];  // slot d at index d - 1
+#pragma unroll
+    for (int d = 1; d <= H; ++d) {
+      int i = j + d;
+      if (i >= NP) i -= NP;
+      double2 g, sv;
+      pair_products(base + i, g, sv);
+      const double li = shfl_d(lt, base + i);
+      const double hm = 0.5 * (li + lt);
+      const double2 num = make_double2(fma(-hm, g.x, sv.x), fma(-hm, g.y, sv.y));
+      const double gap = lt - li;
+      const double n2 = fma(num.x, num.x, num.y * num.y);
+      const bool own = !(2 * d == NP && j >= H);
+      double2 K = make_double2(0.0, 0.0);
+      if (n2 != 0.0) {
+        if (n2 <= thc2 * (gap * gap)) {
+          // 1 / gap: FP32 reciprocal of the scaled gap and one Newton step (~1e-14 relative)
+          const double gs = gap * isc;
+          double rc;
+          if (fabs(gs) > 1e-30) {
+            rc = (double)__frcp_rn((float)gs);
+            rc = fma(rc, fma(-gs, rc, 1.0), rc) * isc;
+          } else {
+            rc = 1.0 / gap;
+          }
+          K = make_double2(num.x * rc, num.y * rc);
+          if (own) shift = fma(fma(K.x, K.x, K.y * K.y), gap, shift);
+        } else if (n2 > tolc2) {
+          unres = 1;
+        }
+      }
+      const double2 hh = make_double2(-0.5 * g.x, -0.5 * g.y);
+      // |h + K|^2 and |h - K|^2 are both <= 2 (|h|^2 + |K|^2)
+      if (own) emx = fmax(emx, 2.0 * (fma(hh.x, hh.x, hh.y * hh.y) + fma(K.x, K.x, K.y * K.y)));
+      hf[d - 1] = make_float2((float)hh.x, (float)hh.y);
+      kf[d - 1] = make_float2((float)K.x, (float)K.y);
+      if (own) er[d] = make_float2(hf[d - 1].x + kf[d - 1].x, hf[d - 1].y + kf[d - 1].y);
+    }
+    // mirrored half: lane i' = j - d holds the pair (j, i') in its slot d; E_{i'j} = conj(h - k)
+#pragma unroll
+    for (int d = 1; d <= H; ++d) {
+      int ip = j - d;
+      if (ip < 0) ip += NP;
+      const float2 hq = shfl_d2(hf[d - 1], base + ip);
+      const float2 kq = shfl_d2(kf[d - 1], base + ip);
+      const double lq = shfl_d(lt, base + ip);
+      if (2 * d < NP || j >= H) {
+        er[NP - d] = make_float2(hq.x - kq.x, -(hq.y - kq.y));
+        shift = fma((double)fmaf(kq.x, kq.x, kq.y * kq.y), lt - lq, shift);
+      }
+    }
+    // group decisions
+    double emx_g = 0.0;
+    int unres_g = 0;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      emx_g = fmax(emx_g, shfl_d(emx, base + i));
+      unres_g |= __shfl_sync(0xffffffffu, unres, base + i);
+    }
+    // x_j += sum_i x_i E_ij in FP32
+    float2 xf[NP], acc[NP];
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      xf[r] = make_float2((float)v[r].x, (float)v[r].y);
+      acc[r] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int d = 0; d < NP; ++d) {
+      int i = j + d;
+      if (i >= NP) i -= NP;
+      const float2 e = er[d];
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        const float2 xi = shfl_d2(xf[r], base + i);
+        acc[r].x = fmaf(xi.x, e.x, fmaf(-xi.y, e.y, acc[r].x));
+        acc[r].y = fmaf(xi.x, e.y, fmaf(xi.y, e.x, acc[r].y));
+      }
+    }
+    if (!done) {
+#pragma unroll
+      for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x + (double)acc[r].x, v[r].y + (double)acc[r].y);
+      if (emx_g <= th_fin * th_fin && !unres_g) {
+        done = true;
+        lam = lt + shift;
+      }
+    }
+  }
+
+  if (!__all_sync(0xffffffffu, done)) {
+    // ---- robust sequence for this warp, from the refined (or FP32) eigenvectors:
+    // Newton-Schulz V <- V (3I - V^H V)/2 = V - V E/2, E = V^H V - I, with the Gram matrix
+    // in FP64 and the small correction V E/2 at FP32 precision; A' = V^H A V; FP64 sweeps.
+    float2 vf[NP];
+#pragma unroll
+    for (int r = 0; r < NP; ++r) vf[r] = make_float2((float)v[r].x, (float)v[r].y);
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+      float2 corr[NP];
+#pragma unroll
+      for (int r = 0; r < NP; ++r) corr[r] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
-        li[i] = shfl_d(lj, base + i);
-        const double gap = lj - li[i];
-        const double m2 = fma(a[i].x, a[i].x, a[i].y * a[i].y);
-        if (i != j && !(m2 <= th2 * (gap * gap))) small = false;
-      }
-      if (__all_sync(0xffffffffu, small)) {
-        double2 dv[NP];
-#pragma unroll
-        for (int r = 0; r < NP; ++r) dv[r] = make_double2(0.0, 0.0);
-        double dl = 0.0;
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          const bool use = i != j && (a[i].x != 0.0 || a[i].y != 0.0);
-          const double inv = use ? 1.0 / (lj - li[i]) : 0.0;
-          const double2 x = make_double2(a[i].x * inv, a[i].y * inv);
-          dl = fma(a[i].x, x.x, fma(a[i].y, x.y, dl));
-#pragma unroll
-          for (int r = 0; r < NP; ++r) {
-            const double2 w = shfl_d2(v[r], base + i);
-            dv[r].x = fma(w.x, x.x, fma(-w.y, x.y, dv[r].x));
-            dv[r].y = fma(w.x, x.y, fma(w.y, x.x, dv[r].y));
-          }
-        }
+        double2 vi[NP];
+        double gx = 0.0, gy = 0.0;
 #pragma unroll
         for (int r = 0; r < NP; ++r) {
-          v[r] = make_double2(v[r].x + dv[r].x, v[r].y + dv[r].y);
-          if (r == j) a[r].x = lj + dl;
+          vi[r] = shfl_d2(v[r], base + i);
+          gx = fma(vi[r].x, v[r].x, fma(vi[r].y, v[r].y, gx));
+          gy = fma(vi[r].x, v[r].y, fma(-vi[r].y, v[r].x, gy));
         }
-        conv = true;
-        break;
+        if (i == j) gx -= 1.0;
+        const float ex = (float)gx, ey = (float)gy;
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+          const float2 wq = shfl_d2(vf[r], base + i);
+          corr[r].x = fmaf(wq.x, ex, fmaf(-wq.y, ey, corr[r].x));
+          corr[r].y = fmaf(wq.x, ey, fmaf(wq.y, ex, corr[r].y));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        v[r].x -= (double)(0.5f * corr[r].x);
+        v[r].y -= (double)(0.5f * corr[r].y);
       }
     }
-    if (sweep >= max_sweeps) break;
-    PolishSweep<NP, 0>::run(a, v, j, base, thresh2, delta);
-    ++sweep;
-    const double off = group_off2<NP>(a, j, base);  // shuffles: every lane takes part
-    if (valid && off <= tol2) conv = true;
-  }
-  if (valid && j == 0 && !conv) atomicOr(status, 1);
+    // A' = V^H A V: wv = A v_j (columns of A from all lanes), then A'[i][j] = v_i^H wv
+    double2 ap[NP];
+    {
+      double2 wv[NP];
+#pragma unroll
+      for (int r = 0; r < NP; ++r) wv[r] = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int s2 = 0; s2 < NP; ++s2) {
+        const double2 vs = v[s2];
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+          const double2 cs = shfl_d2(a[r], base + s2);  // A[r][s2]
+          wv[r].x = fma(cs.x, vs.x, fma(-cs.y, vs.y, wv[r].x));
+          wv[r].y = fma(cs.x, vs.y, fma(cs.y, vs.x, wv[r].y));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        double ax = 0.0, ay = 0.0;
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+          const double2 vi = shfl_d2(v[r], base + i);
+          ax = fma(vi.x, wv[r].x, fma(vi.y, wv[r].y, ax));
+          ay = fma(vi.x, wv[r].y, fma(-vi.y, wv[r].x, ay));
+        }
+        ap[i] = make_double2(ax, (i == j) ? 0.0 : ay);
+      }
+    }
+    // padded columns stay exact unit vectors with zero coupling
+    if (j >= n) {
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        ap[r] = make_double2(0.0, 0.0);
+        v[r] = make_double2(r == j ? 1.0 : 0.0, 0.0);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NP; ++r)
+      if (r >= n && j < n) ap[r] = make_double2(0.0, 0.0);
 
-  // undo the scales: column j of V carries sqrt(1 + delta), diagonal entry j carries 1 + delta
-  // (delta < 1e-9: the second-order series are exact to rounding)
-  double lam = 0.0;
+    const double thresh2 = 1e-36 * fro2 + 1e-300;
+    const double tol2 = polish_tol * polish_tol * fro2;
+    bool conv = !valid;
+    int sweep = 0;
+    double delta = 0.0;  // this column's accumulated scale 1 + delta from unnormalised rotations
+    // first-order finish: once every remaining angle |A_ij / (A_jj - A_ii)| is below theta_max,
+    // v_j += sum_i v_i A_ij / (A_jj - A_ii) completes the eigenvectors to theta_max^2 and
+    // A_jj + sum_i |A_ij|^2 / (A_jj - A_ii) the eigenvalues to theta_max^3 ||A||.
+    const double th2 = loose ? 1e-10 : 1e-16;
+    for (;;) {
+      if (__all_sync(0xffffffffu, conv)) break;
+      if (sweep > 0 || loose) {
+        unit_scale<NP>(ap, v, base, delta);
+        double lj = 0.0;
 #pragma unroll
-  for (int r = 0; r < NP; ++r)
-    if (r == j) lam = a[r].x;
-  lam = fma(-lam, delta * (1.0 - delta), lam);
-  const double vs = fma(delta, fma(0.375, delta, -0.5), 1.0);
+        for (int r = 0; r < NP; ++r)
+          if (r == j) lj = ap[r].x;
+        bool small = true;
+        double li[NP];
 #pragma unroll
-  for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x * vs, v[r].y * vs);
+        for (int i = 0; i < NP; ++i) {
+          li[i] = shfl_d(lj, base + i);
+          const double gap = lj - li[i];
+          const double m2 = fma(ap[i].x, ap[i].x, ap[i].y * ap[i].y);
+          if (i != j && !(m2 <= th2 * (gap * gap))) small = false;
+        }
+        if (__all_sync(0xffffffffu, small)) {
+          double2 dv[NP];
+#pragma unroll
+          for (int r = 0; r < NP; ++r) dv[r] = make_double2(0.0, 0.0);
+          double dl = 0.0;
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            const bool use = i != j && (ap[i].x != 0.0 || ap[i].y != 0.0);
+            const double inv = use ? 1.0 / (lj - li[i]) : 0.0;
+            const double2 x = make_double2(ap[i].x * inv, ap[i].y * inv);
+            dl = fma(ap[i].x, x.x, fma(ap[i].y, x.y, dl));
+#pragma unroll
+            for (int r = 0; r < NP; ++r) {
+              const double2 wq = shfl_d2(v[r], base + i);
+              dv[r].x = fma(wq.x, x.x, fma(-wq.y, x.y, dv[r].x));
+              dv[r].y = fma(wq.x, x.y, fma(wq.y, x.x, dv[r].y));
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < NP; ++r) {
+            v[r] = make_double2(v[r].x + dv[r].x, v[r].y + dv[r].y);
+            if (r == j) ap[r].x = lj + dl;
+          }
+          conv = true;
+          break;
+        }
+      }
+      if (sweep >= max_sweeps) break;
+      PolishSweep<NP, 0>::run(ap, v, j, base, thresh2, delta);
+      ++sweep;
+      const double off = group_off2<NP>(ap, j, base);  // shuffles: every lane takes part
+      if (valid && off <= tol2) conv = true;
+    }
+    if (valid && j == 0 && !conv) atomicOr(status, 1);
+    // undo the scales: column j of V carries sqrt(1 + delta), diagonal entry j carries 1 + delta
+    // (delta < 1e-9: the second-order series are exact to rounding)
+#pragma unroll
+    for (int r = 0; r < NP; ++r)
+      if (r == j) lam = ap[r].x;
+    lam = fma(-lam, delta * (1.0 - delta), lam);
+    const double vs = fma(delta, fma(0.375, delta, -0.5), 1.0);
+#pragma unroll
+    for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x * vs, v[r].y * vs);
+  }
+
   int rank = 0;
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
