@@ -287,6 +287,24 @@ int eph_sync(eph_ctx* ctx);
 int eph_autotune(eph_ctx* ctx, int nq, const double* qpts, int* q_batch_out, int* k_tile_out);
 
 /*
+ * The batched Hermitian eigensolver of the interpolation, on caller matrices: the
+ * diagonalisations of Eq. 4 (H(k), H(k+q) -> eigenvalues eps and the gauge columns U) and
+ * Eq. 5 (D(q) -> omega^2 and the mode eigenvectors) as one call.
+ *   A     [batch][n][n] complex128 (re, im), row-major; only the Hermitian part is used
+ *         (the imaginary parts of the diagonal are ignored).
+ *   w     [batch][n] eigenvalues, ascending (ties in input order).
+ *   V     [batch][n][n] complex128, column j the unit eigenvector of w[j] (V^H A V = diag w).
+ * Host or device pointers per the context's device_ptrs option; the call runs on the
+ * context's stream and is synchronous unless the context is in async mode.
+ * 1 <= n <= 256, batch >= 1.  Precision follows the context's form: FP64 eigenvalues and
+ * eigenvectors (residual ~1e-15 ||A||) for EPH_FORM_FP64; for EPH_FORM_MIXED eigenvalues
+ * within ~1e-12 ||A|| and eigenvectors within ~1e-8.  eig_plain_fp64 selects the plain FP64
+ * Jacobi sweeps.  Errors: EPH_EINVAL (sizes, NULL pointers), EPH_ENOTCONV (a matrix reached
+ * max_sweeps; results still written), EPH_ENOMEM, EPH_ECUDA.
+ */
+int eph_eigh(eph_ctx* ctx, int n, int batch, const void* A, double* w, void* V);
+
+/*
  * Band energies and eigenvectors of H(k) = sum_Re w_e e^{i k.Re} H(Re) for a
  * k list, computed without any device allocation by the library.  The paper
  * has no counterpart: this entry point exists for callers that cannot call

@@ -24,7 +24,7 @@ EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "ep
            "eph_interp_backward", "eph_destroy", "eph_strerror", "eph_last_error", "eph_kernel_launches",
            "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc",
            "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths", "eph_interp_vjp",
-           "eph_set_k_grid", "eph_bloch_to_wannier", "eph_set_k_window", "eph_interp_q_window")
+           "eph_set_k_grid", "eph_bloch_to_wannier", "eph_set_k_window", "eph_interp_q_window", "eph_eigh")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -101,6 +101,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_set_k_window.restype = i
     lib.eph_interp_q_window.argtypes = [vp, i, dp, d, d, dp, dp, vp, vp]
     lib.eph_interp_q_window.restype = i
+    lib.eph_eigh.argtypes = [vp, i, i, vp, dp, vp]
+    lib.eph_eigh.restype = i
     del ip
     if path is None:
         _lib = lib
@@ -290,6 +292,18 @@ class Context:
     def eph_linewidths(self, nq, qpts, wq, kT, mu, sigma, omega_min, gamma):
         self._check(self.lib.eph_linewidths(self.handle, int(nq), _ptr(qpts), _ptr(wq), float(kT), float(mu),
                                             float(sigma), float(omega_min), _ptr(gamma)))
+
+    def eph_eigh(self, n, batch, A, w, V):
+        self._check(self.lib.eph_eigh(self.handle, int(n), int(batch), _ptr(A), _ptr(w), _ptr(V)))
+
+    def eigh(self, A):
+        """Batched Hermitian eigendecomposition of A [batch][n][n] (host mode): (w, V), ascending."""
+        A = np.ascontiguousarray(A, dtype=np.complex128)
+        batch, n = A.shape[0], A.shape[1]
+        w = np.empty((batch, n))
+        V = np.empty((batch, n, n), dtype=np.complex128)
+        self.eph_eigh(n, batch, A, w, V)
+        return w, V
 
     def linewidths(self, qpts, wq=None, kT=0.025852, mu=0.0, sigma=0.05, omega_min=1e-6):
         qpts = np.ascontiguousarray(qpts, dtype=np.float64)

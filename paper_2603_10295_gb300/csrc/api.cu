@@ -102,6 +102,7 @@ struct eph_ctx {
   int nsm = 1;           // SM count
   size_t mem_total = 0;  // device memory
   DBuf jwork, ut, Tbuf;
+  DBuf eigA, eigW, eigV;  // eph_eigh staging (host-pointer mode)
   // linewidth consumer: q weights, per-(q,k) partials, accumulator
   DBuf wqb, lwpart, lwacc;
   // Eq. 6 (Bloch -> Wannier): unweighted phases and per-mode factors M / (ne np)
@@ -330,7 +331,7 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->D, &ctx->lamq, &ctx->evq, &ctx->omq, &ctx->uq, &ctx->G1, &ctx->W, &ctx->Y,
                   &ctx->eps_tile, &ctx->Ukq, &ctx->g_stage, &ctx->wk, &ctx->G2bar, &ctx->G1bar,
                   &ctx->Lpair, &ctx->Lacc, &ctx->grad, &ctx->Ahi, &ctx->Alo, &ctx->Bhi, &ctx->Blo,
-                  &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut,
+                  &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut, &ctx->eigA, &ctx->eigW, &ctx->eigV,
                   &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc, &ctx->rebox, &ctx->E1,
                   &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
                   &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair};
@@ -1302,6 +1303,29 @@ extern "C" int eph_bloch_to_wannier(eph_ctx* ctx, int nk, const double* kpts, in
   if (ctx->big || ctx->opt.form != EPH_FORM_FP64)
     return fail(ctx, EPH_ENOTSUP, "eph_bloch_to_wannier: FP64 form with nb, nm <= 16");
   return adjoint_chain(ctx, nk, kpts, nq, qpts, g, g_ReRp, true);
+}
+
+extern "C" int eph_eigh(eph_ctx* ctx, int n, int batch, const void* A, double* w, void* V) {
+  if (!ctx) return EPH_EINVAL;
+  if (n < 1 || n > 256 || batch < 1 || !A || !w || !V) return fail(ctx, EPH_EINVAL, "eph_eigh: bad size or NULL pointer");
+  const size_t nn = (size_t)n * n, abytes = (size_t)batch * nn * sizeof(double2);
+  const void* dA = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->eigA, A, abytes, &dA));
+  double* dw = w;
+  double2* dV = static_cast<double2*>(V);
+  if (!ctx->opt.device_ptrs) {
+    EPH_TRY(ensure(ctx, ctx->eigW, (size_t)batch * n * sizeof(double)));
+    EPH_TRY(ensure(ctx, ctx->eigV, abytes));
+    dw = as<double>(ctx->eigW);
+    dV = as<double2>(ctx->eigV);
+  }
+  EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, static_cast<const double2*>(dA), (long)nn, n, n, batch, dw, n, dV, (long)nn,
+                                  ctx->opt.form == EPH_FORM_FP64));
+  if (!ctx->opt.device_ptrs) {
+    EPH_CK(cudaMemcpyAsync(w, dw, (size_t)batch * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    EPH_CK(cudaMemcpyAsync(V, dV, abytes, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return finish(ctx);
 }
 
 extern "C" int eph_sync(eph_ctx* ctx) {
