@@ -380,22 +380,26 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
   double fro2 = 0.0;
 #pragma unroll
   for (int i = 0; i < NP; ++i) fro2 += shfl_d(my2, base + i);
-  // power of two near 1 / ||A||_F: keeps the FP32 copy and the FP32 reciprocals in range
+  // the solve runs on A scaled by a power of two to ||A||_F in [0.5, 1) (exact), which keeps
+  // every FP32 quantity in range; the eigenvalues are scaled back at the end
   int fexp = 0;
   frexp(sqrt(fro2), &fexp);
   const double isc = fro2 > 0.0 ? ldexp(1.0, -fexp) : 1.0;
+#pragma unroll
+  for (int r = 0; r < NP; ++r) a[r] = make_double2(a[r].x * isc, a[r].y * isc);
+  fro2 *= isc * isc;
 
-  // ---- FP32 preconditioning sweeps (on A scaled to ||A||_F ~ 1)
+  // ---- FP32 preconditioning sweeps
   double2 v[NP];
   {
     float2 vf[NP];
     float2 af[NP];
 #pragma unroll
     for (int r = 0; r < NP; ++r) {
-      af[r] = make_float2((float)(a[r].x * isc), (float)(a[r].y * isc));
+      af[r] = make_float2((float)a[r].x, (float)a[r].y);
       vf[r] = make_float2(r == j ? 1.f : 0.f, 0.f);
     }
-    const float fro2f = (float)(fro2 * isc * isc);
+    const float fro2f = (float)fro2;
     const float thr32 = 1e-30f * fro2f + 1e-37f;
     const float tol32 = 1e-12f * fro2f;
     bool c32 = !valid;
@@ -412,12 +416,23 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
 
   // ---- refinement
   const bool loose = polish_tol >= 1e-13;
-  const double th_fin = loose ? 1e-4 : 1e-8;
-  const double tolc2 = (loose ? 1e-22 : 1.6e-29) * fro2;  // (1e-11 ||A||_F)^2, (4e-15 ||A||_F)^2
-  const double thc2 = 1e-6;                                  // (largest first-order angle)^2
-  double pa[NP];  // 3M pre-sums of the own column of A, sent with it
+  const float th2f = loose ? 1e-8f : 1e-16f;  // (final |E_ij|)^2
+  const float tolc2f = (float)((loose ? 1e-22 : 1.6e-29) * fro2);  // (1e-11 ||A||_F)^2, (4e-15 ||A||_F)^2
+  const float thc2f = 1e-6f;  // (largest first-order angle)^2
+  // A and its 3M pre-sums in shared memory (per warp; element (r, s) of group g at
+  // [(r NP + s) G + g], so the groups of a warp read consecutive words): frees the registers
+  // of the column copy for the refinement
+  __shared__ double2 shA[4][NP * NP * G];
+  __shared__ double shP[4][NP * NP * G];
+  const int wib = (threadIdx.x >> 5) & 3;
+  if (in_group) {
 #pragma unroll
-  for (int r = 0; r < NP; ++r) pa[r] = a[r].x + a[r].y;
+    for (int r = 0; r < NP; ++r) {
+      shA[wib][(r * NP + j) * G + grp] = a[r];
+      shP[wib][(r * NP + j) * G + grp] = a[r].x + a[r].y;
+    }
+  }
+  __syncwarp();
   bool done = !valid;
   double lam = 0.0;
 #pragma unroll 1
@@ -437,8 +452,8 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       double t1 = 0.0, t2 = 0.0, t3 = 0.0;
 #pragma unroll
       for (int s2 = 0; s2 < NP; ++s2) {
-        const double2 ars = shfl_d2(a[r], base + s2);  // A[r][s2]
-        const double prs = shfl_d(pa[r], base + s2);
+        const double2 ars = shA[wib][(r * NP + s2) * G + grp];  // A[r][s2]
+        const double prs = shP[wib][(r * NP + s2) * G + grp];
         t1 = fma(ars.x, v[s2].x, t1);
         t2 = fma(ars.y, v[s2].y, t2);
         t3 = fma(prs, xp[s2], t3);
@@ -469,11 +484,15 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     // ~1e-12; a larger |e| leaves the step unconverged through the diagonal of R/2)
     const double e0 = 1.0 - g0.x;
     const double lt = s0.x * fma(e0, fma(e0, e0 + 1.0, 1.0), 1.0);
-    double emx = 0.25 * e0 * e0;  // squared bound on |E_ij| (no square roots on the FP64 pipe)
-    double shift = 0.0;
+    // The bookkeeping of the correction runs in FP32: K, the angle tests and the eigenvalue
+    // shift need ~1e-7 relative precision only.  Their inputs S_ij, G_ij and the gap
+    // lam_j - lam_i are formed in FP64 (they are small differences).
+    const float ltf = (float)lt;
+    float emx = 0.25f * (float)e0 * (float)e0;  // squared bound on |E_ij|
+    float shift = 0.f;
     int unres = 0;
     float2 er[NP];  // er[d] = E_{(j+d) mod NP, j}
-    er[0] = make_float2((float)(0.5 * (1.0 - g0.x)), 0.f);
+    er[0] = make_float2(0.5f * (float)e0, 0.f);
     float2 hf[H], kf[H];  // slot d at index d - 1
 #pragma unroll
     for (int d = 1; d <= H; ++d) {
@@ -482,35 +501,28 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       double2 g, sv;
       pair_products(base + i, g, sv);
       const double li = shfl_d(lt, base + i);
-      const double hm = 0.5 * (li + lt);
-      const double2 num = make_double2(fma(-hm, g.x, sv.x), fma(-hm, g.y, sv.y));
-      const double gap = lt - li;
-      const double n2 = fma(num.x, num.x, num.y * num.y);
+      const float lif = shfl_d(ltf, base + i);
+      const float gap = (float)(lt - li);
+      const float hm = 0.5f * (lif + ltf);
+      const float2 gf = make_float2((float)g.x, (float)g.y);
+      const float2 num = make_float2(fmaf(-hm, gf.x, (float)sv.x), fmaf(-hm, gf.y, (float)sv.y));
+      const float n2 = fmaf(num.x, num.x, num.y * num.y);
       const bool own = !(2 * d == NP && j >= H);
-      double2 K = make_double2(0.0, 0.0);
-      if (n2 != 0.0) {
-        if (n2 <= thc2 * (gap * gap)) {
-          // 1 / gap: FP32 reciprocal of the scaled gap and one Newton step (~1e-14 relative)
-          const double gs = gap * isc;
-          double rc;
-          if (fabs(gs) > 1e-30) {
-            rc = (double)__frcp_rn((float)gs);
-            rc = fma(rc, fma(-gs, rc, 1.0), rc) * isc;
-          } else {
-            rc = 1.0 / gap;
-          }
-          K = make_double2(num.x * rc, num.y * rc);
-          if (own) shift = fma(fma(K.x, K.x, K.y * K.y), gap, shift);
-        } else if (n2 > tolc2) {
+      float2 K = make_float2(0.f, 0.f);
+      if (n2 != 0.f) {
+        if (n2 <= thc2f * (gap * gap)) {
+          K = make_float2(__fdiv_rn(num.x, gap), __fdiv_rn(num.y, gap));
+          if (own) shift = fmaf(fmaf(K.x, K.x, K.y * K.y), gap, shift);
+        } else if (n2 > tolc2f) {
           unres = 1;
         }
       }
-      const double2 hh = make_double2(-0.5 * g.x, -0.5 * g.y);
+      const float2 hh = make_float2(-0.5f * gf.x, -0.5f * gf.y);
       // |h + K|^2 and |h - K|^2 are both <= 2 (|h|^2 + |K|^2)
-      if (own) emx = fmax(emx, 2.0 * (fma(hh.x, hh.x, hh.y * hh.y) + fma(K.x, K.x, K.y * K.y)));
-      hf[d - 1] = make_float2((float)hh.x, (float)hh.y);
-      kf[d - 1] = make_float2((float)K.x, (float)K.y);
-      if (own) er[d] = make_float2(hf[d - 1].x + kf[d - 1].x, hf[d - 1].y + kf[d - 1].y);
+      if (own) emx = fmaxf(emx, 2.f * (fmaf(hh.x, hh.x, hh.y * hh.y) + fmaf(K.x, K.x, K.y * K.y)));
+      hf[d - 1] = hh;
+      kf[d - 1] = K;
+      if (own) er[d] = make_float2(hh.x + K.x, hh.y + K.y);
     }
     // mirrored half: lane i' = j - d holds the pair (j, i') in its slot d; E_{i'j} = conj(h - k)
 #pragma unroll
@@ -519,18 +531,18 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       if (ip < 0) ip += NP;
       const float2 hq = shfl_d2(hf[d - 1], base + ip);
       const float2 kq = shfl_d2(kf[d - 1], base + ip);
-      const double lq = shfl_d(lt, base + ip);
+      const float lq = shfl_d(ltf, base + ip);
       if (2 * d < NP || j >= H) {
         er[NP - d] = make_float2(hq.x - kq.x, -(hq.y - kq.y));
-        shift = fma((double)fmaf(kq.x, kq.x, kq.y * kq.y), lt - lq, shift);
+        shift = fmaf(fmaf(kq.x, kq.x, kq.y * kq.y), ltf - lq, shift);
       }
     }
     // group decisions
-    double emx_g = 0.0;
+    float emx_g = 0.f;
     int unres_g = 0;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      emx_g = fmax(emx_g, shfl_d(emx, base + i));
+      emx_g = fmaxf(emx_g, shfl_d(emx, base + i));
       unres_g |= __shfl_sync(0xffffffffu, unres, base + i);
     }
     // x_j += sum_i x_i E_ij in FP32
@@ -555,9 +567,9 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     if (!done) {
 #pragma unroll
       for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x + (double)acc[r].x, v[r].y + (double)acc[r].y);
-      if (emx_g <= th_fin * th_fin && !unres_g) {
+      if (emx_g <= th2f && !unres_g) {
         done = true;
-        lam = lt + shift;
+        lam = lt + (double)shift;
       }
     }
   }
@@ -610,7 +622,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
         const double2 vs = v[s2];
 #pragma unroll
         for (int r = 0; r < NP; ++r) {
-          const double2 cs = shfl_d2(a[r], base + s2);  // A[r][s2]
+          const double2 cs = shA[wib][(r * NP + s2) * G + grp];  // A[r][s2]
           wv[r].x = fma(cs.x, vs.x, fma(-cs.y, vs.y, wv[r].x));
           wv[r].y = fma(cs.x, vs.y, fma(cs.y, vs.x, wv[r].y));
         }
@@ -717,7 +729,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     if (i < n && (li < lam || (li == lam && i < j))) ++rank;
   }
   if (valid && j < n) {
-    w[mat * sw + rank] = lam;
+    w[mat * sw + rank] = lam / isc;
     double2* out = V + mat * sV;
 #pragma unroll
     for (int r = 0; r < NP; ++r)
