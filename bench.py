@@ -43,13 +43,13 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # FP64 flops per matrix of the batched H(k+q) eigensolve (2 x DFMA + DADD + DMUL thread
 # instructions executed, from one ncu capture; profiles/k_jacobi_mixed_si_full.md), keyed by (nb, form)
 # FP64 flops per 8x8 eigensolve (2 DFMA + DMUL + DADD thread instructions from one ncu capture of
-# the 256,000-matrix launch: 1.9087e9 DFMA, 2.785e8 DMUL, 4.895e8 DADD)
-EIG_FP64_FLOPS = {(8, "fp64"): (2 * 1908736000 + 278528000 + 489472000) / 256000}
+# the 256,000-matrix launch: 1.7695e9 DFMA, 5.94e7 DMUL, 5.489e8 DADD)
+EIG_FP64_FLOPS = {(8, "fp64"): (2 * 1769472000 + 59392000 + 548864000) / 256000}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at one step = 4 q x 64,000 k
 TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
            ("k_zgemm", "si_full", 4): 242432512.0 + 1777470464.0,
-           ("k_jacobi_mixed", "si_full", 4): 262383616.0 + 231961088.0,
-           ("k_band_rotate", "si_full", 4): 2097860096.0 + 1534897664.0}
+           ("k_jacobi_mixed", "si_full", 4): 263503872.0 + 230582272.0,
+           ("k_band_rotate", "si_full", 4): 2098326016.0 + 1534963712.0}
 
 
 def parse():
