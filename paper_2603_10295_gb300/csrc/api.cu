@@ -103,6 +103,7 @@ struct eph_ctx {
   size_t mem_total = 0;  // device memory
   DBuf jwork, ut, Tbuf;
   DBuf eigA, eigW, eigV;  // eph_eigh staging (host-pointer mode)
+  DBuf tcband;            // tensor-core band rotation of large shapes (mixed form)
   // linewidth consumer: q weights, per-(q,k) partials, accumulator
   DBuf wqb, lwpart, lwacc;
   // Eq. 6 (Bloch -> Wannier): unweighted phases and per-mode factors M / (ne np)
@@ -180,6 +181,14 @@ T* as(DBuf& b) {
 // The FP64 form polishes to an off-diagonal norm of 1e-17 ||A|| (full FP64 eigenvectors);
 // the mixed form, whose g is bound at 1e-6, to 1e-12 ||A|| (eigenvalues still within
 // 1e-12 ||A|| by Weyl's bound), about one FP64 sweep fewer.
+// device workspace eig() needs for a batch of n x n matrices
+size_t eig_work_bytes(const eph_ctx* c, int n, long batch) {
+  if (n <= 16) return 0;
+  if (!c->opt.eig_plain_fp64 && eph::eigh_big_supported(n))
+    return eph::eigh_big_work_bytes(n, batch < 65535 ? batch : 65535);
+  return (size_t)batch * n * n * sizeof(double2);
+}
+
 cudaError_t eig(eph_ctx* c, const double2* A, long sA, long lda, int n, long batch, double* w, long sw,
                 double2* V, long sV, bool full = false) {
   // full: FP64 eigendecomposition in either form (the dynamical matrices, whose small
@@ -331,7 +340,7 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->D, &ctx->lamq, &ctx->evq, &ctx->omq, &ctx->uq, &ctx->G1, &ctx->W, &ctx->Y,
                   &ctx->eps_tile, &ctx->Ukq, &ctx->g_stage, &ctx->wk, &ctx->G2bar, &ctx->G1bar,
                   &ctx->Lpair, &ctx->Lacc, &ctx->grad, &ctx->Ahi, &ctx->Alo, &ctx->Bhi, &ctx->Blo,
-                  &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut, &ctx->eigA, &ctx->eigW, &ctx->eigV,
+                  &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut, &ctx->eigA, &ctx->eigW, &ctx->eigV, &ctx->tcband,
                   &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc, &ctx->rebox, &ctx->E1,
                   &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
                   &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair};
@@ -788,6 +797,22 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
 // Band rotation g_nu = V_{k+q}^H G3_nu V_k for one (q batch, k tile): the shared-memory kernel
 // for small shapes, two GEMMs batched over (k, nu) otherwise.
 // iq0: the first q of the tile to rotate (nqb of them from there).
+bool use_band_tc(const eph_ctx* ctx) {
+  return ctx->opt.form == EPH_FORM_MIXED && ctx->big && ctx->opt.mixed_scheme == 0 &&
+         eph::band_tc_supported(ctx->nm, ctx->nb);
+}
+
+// workspace of the tensor-core band rotation for npairs pairs of a tile of nkt k points: the
+// pairs go in chunks of at most ~6 GB of digit and product buffers
+size_t band_tc_bytes(const eph_ctx* ctx, long npairs, int nkt) {
+  const size_t b0 = eph::band_tc_work_bytes(nkt, ctx->nm, ctx->nb, 0);
+  const size_t per = eph::band_tc_work_bytes(nkt, ctx->nm, ctx->nb, 1) - b0;
+  long pb = (long)(((size_t)6 << 30) / per);
+  if (pb > npairs) pb = npairs;
+  if (pb < 1) pb = 1;
+  return eph::band_tc_work_bytes(nkt, ctx->nm, ctx->nb, pb);
+}
+
 int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2* out, long sgq,
                 const int* keep = nullptr, int iq0 = 0) {
   const int nb = ctx->nb, nm = ctx->nm, nb2 = nb * nb;
@@ -804,6 +829,12 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
   if (!ctx->big) {
     EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, Ukq, Uk, nqb, nkt, nm, nb, out, sgq, ctx->stream,
                                                     keep));
+    return EPH_OK;
+  }
+  if (use_band_tc(ctx)) {  // mixed form: two batched five-digit tensor-core products
+    EPH_TRY(ensure(ctx, ctx->tcband, band_tc_bytes(ctx, (long)nqb * nkt, nkt)));
+    EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc(Y, p.NW, Ukq, Uk, nqb, nkt, nm, nb, reinterpret_cast<float2*>(out),
+                                                     sgq, ctx->tcband.p, ctx->tcband.n, ctx->status + 1, ctx->stream));
     return EPH_OK;
   }
   double2* T = as<double2>(ctx->Tbuf);
@@ -1006,7 +1037,14 @@ int prepare_fp64(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
     EPH_TRY(ensure(ctx, ctx->Tbuf, (size_t)p.KT * ctx->nm * nb2 * sizeof(double2)));
     EPH_TRY(ensure(ctx, ctx->ut, (size_t)p.QB * ctx->nm * ctx->nm * sizeof(double2)));
     const size_t jw = (size_t)(p.QB * p.KT > ctx->nk ? p.QB * p.KT : ctx->nk) * nmax * nmax * sizeof(double2);
-    EPH_TRY(ensure(ctx, ctx->jwork, jw));
+    size_t need = jw;
+    const size_t e1 = eig_work_bytes(ctx, ctx->nb, (long)p.QB * p.KT), e2 = eig_work_bytes(ctx, ctx->nb, ctx->nk),
+                 e3 = eig_work_bytes(ctx, ctx->nm, p.QB);
+    need = need > e1 ? need : e1;
+    need = need > e2 ? need : e2;
+    need = need > e3 ? need : e3;
+    EPH_TRY(ensure(ctx, ctx->jwork, need));
+    if (use_band_tc(ctx)) EPH_TRY(ensure(ctx, ctx->tcband, band_tc_bytes(ctx, (long)p.QB * p.KT, (int)p.KT)));
   }
   if (host && want_g) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)p.QB * p.KT * p.gcols * sizeof(double2)));
   *out = p;

@@ -1,0 +1,242 @@
+// Band rotation g_nu = V_{k+q}^H G3_nu V_k (the last step of Eq. 7's evaluation, Eqs. 4-5
+// gauges) for shapes beyond the shared-memory kernels, on the tcgen05 tensor cores: the mixed
+// form's large-Nb path.  Two batched products of the five-digit fixed-point scheme of the H(k+q)
+// contraction (float-pair results, ~1e-12 relative), on the real embedding of the complex
+// matrices (K = 2 Nb, re/im interleaved):
+//   stage 1, per pair:  C1[2n' + c][nu Nb + a] = (re, im)_c of T[(nu, a)][n'],  T = G3_nu V_k,
+//                       A = V_k embedded (rows 2n' + c, K = 2b + t), B = the G3 rows (nu, a);
+//   stage 2, per pair:  C2[2m + c][nu Nb + n'] = (re, im)_c of g_nu[m][n'],
+//                       A = V_{k+q}^H embedded (rows 2m + c, K = 2a + t),
+//                       B rows (nu, n') with K = 2a + t gathered from C1.
+// Every B row carries its own power-of-two scale (fixed point relative to the row maximum);
+// V is unitary, so its scale is 2.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "eph_kernels.cuh"
+
+namespace eph {
+namespace {
+
+constexpr int MAXKL = 16;  // K values per lane in the row kernels (Kp <= 512, Nb <= 256)
+
+// Five signed base-256 digits of y = x / s (|y| <= 1/2): y = sum_i d_i 2^-8(i+1) + O(2^-41),
+// |d_i| <= 128; digit i is stored pre-scaled by 2^-8i (exact in bf16).
+__device__ __forceinline__ void put_digits5(double y, __nv_bfloat16* __restrict__ D, long slice, long idx) {
+  long long R = __double2ll_rn(y * 0x1p40);
+  float scale = 1.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int sh = 32 - 8 * i;
+    const long long d = (R + (1LL << (sh - 1))) >> sh;  // round to nearest (arithmetic shift)
+    R -= d * (1LL << sh);
+    D[i * slice + idx] = __float2bfloat16_rn((float)d * scale);
+    scale *= 0x1p-8f;
+  }
+  D[4 * slice + idx] = __float2bfloat16_rn((float)R * scale);
+}
+
+// power of two s >= 2 max|x| (1 for an all-zero row)
+__device__ __forceinline__ double row_scale(double mx) {
+  if (!(mx > 0.0)) return 1.0;
+  int e;
+  frexp(mx, &e);
+  return ldexp(1.0, e + 1);
+}
+
+// A digits of embedded unitary matrices V[b] (nb x nb, stride sV): rows r = 2i + c, K = 2j + t;
+// mode 0: [[Vr, -Vi], [Vi, Vr]][c][t] of V[j][i] (V^T applied to G3 rows), mode 1:
+// [[Vr, Vi], [-Vi, Vr]][c][t] of V[j][i] (V^H applied to T).  s = 2.
+__global__ void k_vdigits(const double2* __restrict__ V, long sV, int nb, long nmat, int kp, int mode,
+                          __nv_bfloat16* __restrict__ D, long slice) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long per = 2L * nb * kp;
+  if (idx >= per * nmat) return;
+  const long b = idx / per;
+  const long rem = idx - b * per;
+  const int r = (int)(rem / kp), kk = (int)(rem - (long)r * kp);
+  double x = 0.0;
+  if (kk < 2 * nb) {
+    const int i = r >> 1, c = r & 1, j = kk >> 1, t = kk & 1;
+    const double2 v = V[b * sV + (long)j * nb + i];
+    if (mode == 0)
+      x = (c == t) ? v.x : (c == 0 ? -v.y : v.y);
+    else
+      x = (c == t) ? v.x : (c == 0 ? v.y : -v.y);
+  }
+  put_digits5(0.5 * x, D, slice, idx);
+}
+
+// Stage-1 B digits, one warp per row w = p nrow + j: K = 2b + t of G3[p][j][b] (complex128 row of
+// nb elements at Y + p ldy + off + j nb); sB[w] = the row's scale.
+__global__ void k_gdigits(const double2* __restrict__ Y, long ldy, long off, int nrow, int nb, long rows, int kp,
+                          float* __restrict__ sB, __nv_bfloat16* __restrict__ D, long slice) {
+  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= rows) return;  // whole warps
+  const long p = w / nrow;
+  const int j = (int)(w - p * nrow);
+  const double* src = reinterpret_cast<const double*>(Y + p * ldy + off + (long)j * nb);
+  double x[MAXKL];
+  double mx = 0.0;
+#pragma unroll
+  for (int i = 0; i < MAXKL; ++i) {
+    const int kk = lane + 32 * i;
+    x[i] = kk < 2 * nb ? src[kk] : 0.0;
+    mx = fmax(mx, fabs(x[i]));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const double s = row_scale(mx);
+  if (lane == 0) sB[w] = (float)s;
+  const double inv = 1.0 / s;
+#pragma unroll
+  for (int i = 0; i < MAXKL; ++i) {
+    const int kk = lane + 32 * i;
+    if (kk < kp) put_digits5(x[i] * inv, D, slice, w * kp + kk);
+  }
+}
+
+// Stage-2 B digits, one warp per row w = p nrow + j, j = nu nb + n': K = 2a + t of
+// T[(nu, a)][n'] part t = C1[p][2n' + t][nu nb + a] (float pair hi + lo).
+__global__ void k_tdigits(const float2* __restrict__ C1, long sC, int nrow, int nb, long rows, int kp,
+                          float* __restrict__ sB, __nv_bfloat16* __restrict__ D, long slice) {
+  const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  const long p = w / nrow;
+  const int j = (int)(w - p * nrow);
+  const int nu = j / nb, np_ = j - nu * nb;
+  const float2* src = C1 + p * sC + (long)nu * nb;
+  double x[MAXKL];
+  double mx = 0.0;
+#pragma unroll
+  for (int i = 0; i < MAXKL; ++i) {
+    const int kk = lane + 32 * i;
+    double v = 0.0;
+    if (kk < 2 * nb) {
+      const float2 h = src[(long)(2 * np_ + (kk & 1)) * nrow + (kk >> 1)];
+      v = (double)h.x + (double)h.y;
+    }
+    x[i] = v;
+    mx = fmax(mx, fabs(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const double s = row_scale(mx);
+  if (lane == 0) sB[w] = (float)s;
+  const double inv = 1.0 / s;
+#pragma unroll
+  for (int i = 0; i < MAXKL; ++i) {
+    const int kk = lane + 32 * i;
+    if (kk < kp) put_digits5(x[i] * inv, D, slice, w * kp + kk);
+  }
+}
+
+// g[iq][kk][nu][m][n'] = complex64 of C2[p][2m + c][nu nb + n'] (hi + lo), pair p0 + p = iq nk + kk.
+__global__ void k_gout(const float2* __restrict__ C2, long sC, int nrow, int nb, int nm, long npairs, int nk, long p0,
+                       float2* __restrict__ g, long sgq) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long per = (long)nm * nb * nb;
+  if (idx >= per * npairs) return;
+  const long p = idx / per;
+  const long rem = idx - p * per;
+  const int nu = (int)(rem / (nb * nb));
+  const int r2 = (int)(rem - (long)nu * nb * nb);
+  const int m = r2 / nb, n = r2 - m * nb;
+  const float2* src = C2 + p * sC + (long)nu * nb + n;
+  const float2 re = src[(long)(2 * m) * nrow], im = src[(long)(2 * m + 1) * nrow];
+  const long P = p0 + p;
+  const long iq = P / nk, kk = P - iq * nk;
+  g[iq * sgq + kk * per + rem] = make_float2(__fadd_rn(re.x, re.y), __fadd_rn(im.x, im.y));
+}
+
+size_t align_up(size_t x) { return (x + 1023) & ~(size_t)1023; }
+
+struct BandTcShape {
+  int kp, M;
+  long Nr;
+  size_t a1, per_pair;
+};
+
+BandTcShape band_tc_shape(int nk, int nm, int nb) {
+  BandTcShape s;
+  s.kp = ((2 * nb + 31) / 32) * 32;
+  s.M = 2 * nb;
+  s.Nr = (long)nm * nb;
+  s.a1 = align_up((size_t)5 * nk * s.M * s.kp * 2);
+  // B digits (shared by both stages), C float pairs (C1 then C2), A2 digits, B row scales
+  s.per_pair = (size_t)5 * s.Nr * s.kp * 2 + (size_t)s.M * s.Nr * 8 + (size_t)5 * s.M * s.kp * 2 + (size_t)s.Nr * 4;
+  return s;
+}
+
+}  // namespace
+
+bool band_tc_supported(int nm, int nb) {
+  // exact level sums need K = 2 Nb <= 1024; the epilogue's paired stores need an even row length
+  return nb >= 1 && nb <= 256 && ((long)nm * nb) % 2 == 0;
+}
+
+size_t band_tc_work_bytes(int nk, int nm, int nb, long pairs) {
+  const BandTcShape s = band_tc_shape(nk, nm, nb);
+  return s.a1 + (size_t)pairs * s.per_pair + 4 * 1024;
+}
+
+cudaError_t launch_band_tc(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk, int nm,
+                           int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err, cudaStream_t st) {
+  const long npairs = (long)nq * nk;
+  if (npairs <= 0) return cudaSuccess;
+  if (!band_tc_supported(nm, nb) || nk < 1) return cudaErrorInvalidValue;
+  const BandTcShape sh = band_tc_shape(nk, nm, nb);
+  if (work_bytes < band_tc_work_bytes(nk, nm, nb, 1)) return cudaErrorInvalidValue;
+  long PB = (long)((work_bytes - sh.a1 - 4 * 1024) / sh.per_pair);
+  if (PB > npairs) PB = npairs;
+  const int kp = sh.kp, M = sh.M;
+  const long Nr = sh.Nr;
+  char* base = static_cast<char*>(work);
+  __nv_bfloat16* A1 = reinterpret_cast<__nv_bfloat16*>(base);
+  char* chunk = base + sh.a1;
+  __nv_bfloat16* Bd = reinterpret_cast<__nv_bfloat16*>(chunk);
+  float2* C = reinterpret_cast<float2*>(chunk + align_up((size_t)5 * PB * Nr * kp * 2));
+  __nv_bfloat16* A2 = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(C) + align_up((size_t)PB * M * Nr * 8));
+  float* sB = reinterpret_cast<float*>(reinterpret_cast<char*>(A2) + align_up((size_t)5 * PB * M * kp * 2));
+  cudaError_t e;
+  // A digits of V_k for every k of the tile (stage 1)
+  {
+    const long slice = (long)nk * M * kp;
+    k_vdigits<<<(unsigned)((slice + 255) / 256), 256, 0, st>>>(Uk, (long)nb * nb, nb, nk, kp, 0, A1, slice);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  CUtensorMap mA1[5], mA2[5], mB[5];
+  for (int d = 0; d < 5; ++d)
+    if ((e = make_tc_map_bf16_sw64(&mA1[d], A1 + (long)d * nk * M * kp, (long)nk * M, kp, 128)) != cudaSuccess) return e;
+  for (long p0 = 0; p0 < npairs; p0 += PB) {
+    const long pb = npairs - p0 < PB ? npairs - p0 : PB;
+    const long rows = pb * Nr, bslice = rows * kp, aslice = pb * M * kp;
+    for (int d = 0; d < 5; ++d) {
+      if ((e = make_tc_map_bf16_sw64(&mB[d], Bd + d * bslice, rows, kp, 128)) != cudaSuccess) return e;
+      if ((e = make_tc_map_bf16_sw64(&mA2[d], A2 + d * aslice, pb * M, kp, 128)) != cudaSuccess) return e;
+    }
+    // stage 1: T^T = V_k^T G3^T per pair
+    k_gdigits<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(Y + p0 * ldy, ldy, (long)nb * nb, (int)Nr, nb,
+                                                                   rows, kp, sB, Bd, bslice);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_tc_hkq_gemm_b(mA1, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, nk,
+                                  (int)(p0 % nk), M, 1, st)) != cudaSuccess)
+      return e;
+    // stage 2: g = V_{k+q}^H T per pair
+    k_tdigits<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(C, (long)M * Nr, (int)Nr, nb, rows, kp, sB, Bd,
+                                                                   bslice);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_vdigits<<<(unsigned)((aslice + 255) / 256), 256, 0, st>>>(Ukq + p0 * nb * nb, (long)nb * nb, nb, pb, kp, 1, A2,
+                                                                aslice);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_tc_hkq_gemm_b(mA2, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, (int)pb, 0,
+                                  M, 1, st)) != cudaSuccess)
+      return e;
+    const long tot = pb * nm * nb * nb;
+    k_gout<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, (long)M * Nr, (int)Nr, nb, nm, pb, nk, p0, g, sgq);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace eph

@@ -178,7 +178,20 @@ cudaError_t make_tc_map_bf16_sw64(void* map_out, const void* base, long rows, in
 // H(k+q) on the tensor cores from 5 x 5 BF16 digits: C[q][m][n] = (hi, lo) float pairs, ldc/sC in float2
 cudaError_t launch_tc_hkq_gemm(const void* maps_a5, const void* maps_b5, int M, int a_row0, int Nr, int Kp, int nq,
                                float sA, const float* sB, float2* C, long ldc, long sC, int* err, cudaStream_t st);
+// Same product batched over q with A rows a_row0 + ((q + a_qoff) mod a_mod) a_stride + m; morder = 1
+// takes the m tiles fastest (M of a few tiles sharing each B tile).
+cudaError_t launch_tc_hkq_gemm_b(const void* maps_a5, const void* maps_b5, int M, int a_row0, int Nr, int Kp, int nq,
+                                 float sA, const float* sB, float2* C, long ldc, long sC, int* err, int a_mod,
+                                 int a_qoff, int a_stride, int morder, cudaStream_t st);
 cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
                                  float sA, const float* sB, float* C, long ldc, long sC, int* err, cudaStream_t st);
+// Band rotation of large shapes on the tensor cores (mixed form): g[iq][kk] (complex64, rows iq
+// sgq apart, pair (iq, kk) at kk nm nb^2) = V_{k+q}^H G3_nu V_k for the nq x nk pairs of a tile,
+// G3 at Y + (iq nk + kk) ldy + nb^2, V_{k+q} at Ukq + (iq nk + kk) nb^2, V_k at Uk + kk nb^2.
+// work: at least band_tc_work_bytes(nk, nm, nb, 1) bytes; more lets more pairs go per chunk.
+size_t band_tc_work_bytes(int nk, int nm, int nb, long pairs);
+bool band_tc_supported(int nm, int nb);
+cudaError_t launch_band_tc(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk, int nm,
+                           int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err, cudaStream_t st);
 
 }  // namespace eph

@@ -524,6 +524,17 @@ __device__ __forceinline__ uint64_t smem_desc64(uint32_t addr) {
   return d;
 }
 
+// Tile order with the m tile fastest: the m tiles that share one B tile run back to back
+// (batched products with M <= 2 BM rows per batch read each B tile from DRAM once).
+__device__ __forceinline__ void tile_coords_mfast(long t, int ntm, int ntn, int* q, int* m0, int* n0) {
+  const int m = (int)(t % ntm);
+  const long r = t / ntm;
+  const int n = (int)(r % ntn);
+  *q = (int)(r / ntn);
+  *m0 = m * BM;
+  *n0 = n * BN;
+}
+
 __device__ __forceinline__ void two_sum(float& h, float& l, float x) {
   const float s = __fadd_rn(h, x);
   const float bb = __fsub_rn(s, h);
@@ -538,10 +549,13 @@ struct TcMaps10 {
   CUtensorMap b[5];
 };
 
+// Batch q reads A rows a_row0 + ((q + a_qoff) mod a_mod) a_stride + m (a_mod = 1: A shared by
+// every batch); morder = 1 takes the m tiles fastest.
 __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_constant__ TcMaps10 maps, int M,
                                                                 int a_row0, int Nr, int Kp, int nq, float sA,
                                                                 const float* __restrict__ sB, float2* __restrict__ C,
-                                                                long ldc, long sC, int* __restrict__ err) {
+                                                                long ldc, long sC, int* __restrict__ err, int a_mod,
+                                                                int a_qoff, int a_stride, int morder) {
   using namespace tc;
   using tch::BM;
   using tch::BN;
@@ -591,7 +605,11 @@ __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_co
       long it = 0;
       for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
         int q, m0, n0;
-        tcf::tile_coords(t, ntn, nq, &q, &m0, &n0);
+        if (morder)
+          tch::tile_coords_mfast(t, ntm, ntn, &q, &m0, &n0);
+        else
+          tcf::tile_coords(t, ntn, nq, &q, &m0, &n0);
+        const int arow = a_row0 + ((q + a_qoff) % a_mod) * a_stride + m0;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = (int)(it % STAGES);
           if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1))) {
@@ -602,7 +620,7 @@ __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_co
           if (*abort_flag) break;
           mbar_arrive_expect_tx(&full[s], tch::STAGE_BYTES);
 #pragma unroll
-          for (int d = 0; d < ND; ++d) tma_load_2d(tile(s, d), &maps.a[d], kb * BK, a_row0 + m0, &full[s]);
+          for (int d = 0; d < ND; ++d) tma_load_2d(tile(s, d), &maps.a[d], kb * BK, arow, &full[s]);
 #pragma unroll
           for (int d = 0; d < ND; ++d) tma_load_2d(tile(s, ND + d), &maps.b[d], kb * BK, q * Nr + n0, &full[s]);
         }
@@ -676,7 +694,10 @@ __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_co
       }
       fence_after();
       int q, m0, n0;
-      tcf::tile_coords(t, ntn, nq, &q, &m0, &n0);
+      if (morder)
+        tch::tile_coords_mfast(t, ntm, ntn, &q, &m0, &n0);
+      else
+        tcf::tile_coords(t, ntn, nq, &q, &m0, &n0);
       const int row = m0 + quarter * 32 + lane;
       const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
       float2* crow = C + (long)q * sC + (long)row * ldc;
@@ -787,7 +808,14 @@ cudaError_t make_tc_map_bf16_sw64(void* map_out, const void* base, long rows, in
 
 cudaError_t launch_tc_hkq_gemm(const void* maps_a5, const void* maps_b5, int M, int a_row0, int Nr, int Kp, int nq,
                                float sA, const float* sB, float2* C, long ldc, long sC, int* err, cudaStream_t st) {
+  return launch_tc_hkq_gemm_b(maps_a5, maps_b5, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err, 1, 0, 0, 0, st);
+}
+
+cudaError_t launch_tc_hkq_gemm_b(const void* maps_a5, const void* maps_b5, int M, int a_row0, int Nr, int Kp, int nq,
+                                 float sA, const float* sB, float2* C, long ldc, long sC, int* err, int a_mod,
+                                 int a_qoff, int a_stride, int morder, cudaStream_t st) {
   if (M <= 0 || Nr <= 0 || nq <= 0) return cudaSuccess;
+  if (a_mod < 1 || a_qoff < 0 || a_stride < 0) return cudaErrorInvalidValue;
   if (Kp % tch::BK != 0 || Kp <= 0 || Kp > 1024) return cudaErrorInvalidValue;  // exact level sums need K <= 1024
   if ((reinterpret_cast<uintptr_t>(C) & 15) != 0 || (ldc & 1) || (sC & 1)) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_tc_hkq_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tch::SMEM_BYTES);
@@ -802,7 +830,8 @@ cudaError_t launch_tc_hkq_gemm(const void* maps_a5, const void* maps_b5, int M, 
   }
   const long ntiles = (long)((Nr + tch::BN - 1) / tch::BN) * ((M + tch::BM - 1) / tch::BM) * nq;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
-  k_tc_hkq_gemm<<<grid, tch::THREADS, tch::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err);
+  k_tc_hkq_gemm<<<grid, tch::THREADS, tch::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err,
+                                                             a_mod, a_qoff, a_stride, morder);
   return cudaGetLastError();
 }
 
