@@ -20,28 +20,60 @@ namespace {
 
 constexpr int MAXKL = 16;  // K values per lane in the row kernels (Kp <= 512, Nb <= 256)
 
-// Five signed base-256 digits of y = x / s (|y| <= 1/2): y = sum_i d_i 2^-8(i+1) + O(2^-41),
-// |d_i| <= 128; digit i is stored pre-scaled by 2^-8i (exact in bf16).
-__device__ __forceinline__ void put_digits5(double y, __nv_bfloat16* __restrict__ D, long slice, long idx) {
-  long long R = __double2ll_rn(y * 0x1p40);
+// The digit kernels run on the integer pipe: FP64 arithmetic (and FP64 <-> integer conversion)
+// is ~1/64 of the FP32 rate on GB300, so the fixed-point value round(x 2^(40 - es)) of
+// x / s (s = 2^es) is formed from the IEEE bits.
+__device__ __forceinline__ long long fixed40_d(double x, int es) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return 0;  // zero or subnormal: below the row's last digit
+  const long long m = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+  const int sh = (e - 1023) - 52 + 40 - es;  // x 2^(40 - es) = m 2^sh
+  long long X;
+  if (sh >= 0)
+    X = m << sh;  // |x / s| <= 1/2 keeps this below 2^40
+  else if (sh > -63)
+    X = (m + (1LL << (-sh - 1))) >> (-sh);
+  else
+    X = 0;
+  return (long long)(b >> 63) ? -X : X;
+}
+__device__ __forceinline__ long long fixed40_f(float x, int es) {
+  const unsigned int b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xFF);
+  if (e == 0) return 0;
+  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = (e - 127) - 23 + 40 - es;
+  long long X;
+  if (sh >= 0)
+    X = m << sh;
+  else if (sh > -40)
+    X = (m + (1LL << (-sh - 1))) >> (-sh);
+  else
+    X = 0;
+  return (b >> 31) ? -X : X;
+}
+
+// Five signed base-256 digits of X = round(y 2^40), |y| <= 1/2 (+ 2^-24): y = sum_i d_i
+// 2^-8(i+1) + O(2^-41), |d_i| <= 128; digit i stored pre-scaled by 2^-8i (exact in bf16).
+__device__ __forceinline__ void put_digits5(long long R, __nv_bfloat16* __restrict__ D, long slice, long idx) {
   float scale = 1.f;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int sh = 32 - 8 * i;
     const long long d = (R + (1LL << (sh - 1))) >> sh;  // round to nearest (arithmetic shift)
     R -= d * (1LL << sh);
-    D[i * slice + idx] = __float2bfloat16_rn((float)d * scale);
+    D[i * slice + idx] = __float2bfloat16_rn((float)(int)d * scale);
     scale *= 0x1p-8f;
   }
-  D[4 * slice + idx] = __float2bfloat16_rn((float)R * scale);
+  D[4 * slice + idx] = __float2bfloat16_rn((float)(int)R * scale);
 }
 
-// power of two s >= 2 max|x| (1 for an all-zero row)
-__device__ __forceinline__ double row_scale(double mx) {
-  if (!(mx > 0.0)) return 1.0;
-  int e;
-  frexp(mx, &e);
-  return ldexp(1.0, e + 1);
+// exponent es of the row scale s = 2^es >= 2 max|x| from the largest biased exponent eb of the
+// row (max|x| in [2^(eb - bias), 2^(eb - bias + 1))): es = eb - bias + 2; an all-zero row gets 0
+__device__ __forceinline__ int warp_max_int(int v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
 // A digits of embedded unitary matrices V[b] (nb x nb, stride sV): rows r = 2i + c, K = 2j + t;
@@ -64,7 +96,7 @@ __global__ void k_vdigits(const double2* __restrict__ V, long sV, int nb, long n
     else
       x = (c == t) ? v.x : (c == 0 ? v.y : -v.y);
   }
-  put_digits5(0.5 * x, D, slice, idx);
+  put_digits5(fixed40_d(x, 1), D, slice, idx);
 }
 
 // Stage-1 B digits, one warp per row w = p nrow + j: K = 2b + t of G3[p][j][b] (complex128 row of
@@ -78,21 +110,20 @@ __global__ void k_gdigits(const double2* __restrict__ Y, long ldy, long off, int
   const int j = (int)(w - p * nrow);
   const double* src = reinterpret_cast<const double*>(Y + p * ldy + off + (long)j * nb);
   double x[MAXKL];
-  double mx = 0.0;
+  int eb = 0;
 #pragma unroll
   for (int i = 0; i < MAXKL; ++i) {
     const int kk = lane + 32 * i;
     x[i] = kk < 2 * nb ? src[kk] : 0.0;
-    mx = fmax(mx, fabs(x[i]));
+    eb = max(eb, (int)((__double_as_longlong(x[i]) >> 52) & 0x7FF));
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const double s = row_scale(mx);
-  if (lane == 0) sB[w] = (float)s;
-  const double inv = 1.0 / s;
+  eb = warp_max_int(eb);
+  const int es = eb ? eb - 1023 + 2 : 0;
+  if (lane == 0) sB[w] = ldexpf(1.f, es);
 #pragma unroll
   for (int i = 0; i < MAXKL; ++i) {
     const int kk = lane + 32 * i;
-    if (kk < kp) put_digits5(x[i] * inv, D, slice, w * kp + kk);
+    if (kk < kp) put_digits5(fixed40_d(x[i], es), D, slice, w * kp + kk);
   }
 }
 
@@ -107,27 +138,21 @@ __global__ void k_tdigits(const float2* __restrict__ C1, long sC, int nrow, int 
   const int j = (int)(w - p * nrow);
   const int nu = j / nb, np_ = j - nu * nb;
   const float2* src = C1 + p * sC + (long)nu * nb;
-  double x[MAXKL];
-  double mx = 0.0;
+  float2 x[MAXKL];
+  int eb = 0;
 #pragma unroll
   for (int i = 0; i < MAXKL; ++i) {
     const int kk = lane + 32 * i;
-    double v = 0.0;
-    if (kk < 2 * nb) {
-      const float2 h = src[(long)(2 * np_ + (kk & 1)) * nrow + (kk >> 1)];
-      v = (double)h.x + (double)h.y;
-    }
-    x[i] = v;
-    mx = fmax(mx, fabs(v));
+    x[i] = kk < 2 * nb ? src[(long)(2 * np_ + (kk & 1)) * nrow + (kk >> 1)] : make_float2(0.f, 0.f);
+    eb = max(eb, (int)((__float_as_uint(x[i].x) >> 23) & 0xFF));
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const double s = row_scale(mx);
-  if (lane == 0) sB[w] = (float)s;
-  const double inv = 1.0 / s;
+  eb = warp_max_int(eb);
+  const int es = eb ? eb - 127 + 2 : 0;  // |hi + lo| <= |hi| (1 + 2^-24): still within s / 2 + 2^-25 s
+  if (lane == 0) sB[w] = ldexpf(1.f, es);
 #pragma unroll
   for (int i = 0; i < MAXKL; ++i) {
     const int kk = lane + 32 * i;
-    if (kk < kp) put_digits5(x[i] * inv, D, slice, w * kp + kk);
+    if (kk < kp) put_digits5(fixed40_f(x[i].x, es) + fixed40_f(x[i].y, es), D, slice, w * kp + kk);
   }
 }
 

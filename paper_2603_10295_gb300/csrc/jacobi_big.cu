@@ -54,14 +54,18 @@ __device__ T block_sum(T x, T* red) {
 // col_p' = c col_p - conj(sigma) col_q, col_q' = sigma col_p + c col_q; rows (J^H) as
 // row_p' = c row_p - sigma row_q, row_q' = conj(sigma) row_p + c row_q.
 struct Round64 {
-  int sp[128], sq[128];
+  int sp[128], sq[128], son[128];
   double sc[128], stb[128], sapp[128], saqq[128];
   double2 ssg[128];
 };
 
 // One round of FP64 rotations on M (n x n, row-major, global) accumulating V <- V J.
+// Threshold form: a pair is rotated only if |A_pq|^2 > max(thresh2, th2 (A_qq - A_pp)^2), i.e.
+// if its angle is above sqrt(th2) (th2 = 0: every pair above thresh2); the rest is left to
+// the first-order finish.
 __device__ void fp64_round(double2* __restrict__ M, double2* __restrict__ U, int n, int np, int r, double thresh2,
-                           Round64& s) {
+                           double th2, Round64& s) {
+  // (thresh2 also carries the rounding-level coupling that the polish accepts without rotation)
   const int tid = threadIdx.x, nt = blockDim.x, npairs = np / 2;
   for (int i = tid; i < npairs; i += nt) {
     int p, q;
@@ -69,13 +73,15 @@ __device__ void fp64_round(double2* __restrict__ M, double2* __restrict__ U, int
     double c = 1.0, tb = 0.0;
     double2 sig = make_double2(0.0, 0.0);
     double app = 0.0, aqq = 0.0;
+    int on = 0;
     if (q < n) {
       app = M[(long)p * n + p].x;
       aqq = M[(long)q * n + q].x;
       const double2 b = M[(long)p * n + q];
       const double b2 = fma(b.x, b.x, b.y * b.y);
-      if (b2 > thresh2) {
-        const double dd = aqq - app;
+      const double dd = aqq - app;
+      if (b2 > thresh2 && b2 > th2 * (dd * dd)) {
+        on = 1;
         const double rr = copysign(2.0, dd) / (fabs(dd) + sqrt(fma(dd, dd, 4.0 * b2)));
         tb = rr * b2;
         c = rsqrt(fma(rr * rr, b2, 1.0));
@@ -84,6 +90,7 @@ __device__ void fp64_round(double2* __restrict__ M, double2* __restrict__ U, int
     }
     s.sp[i] = p;
     s.sq[i] = q;
+    s.son[i] = on;
     s.sc[i] = c;
     s.ssg[i] = sig;
     s.stb[i] = tb;
@@ -94,8 +101,8 @@ __device__ void fp64_round(double2* __restrict__ M, double2* __restrict__ U, int
   // columns of A and V
   for (long idx = tid; idx < (long)npairs * n; idx += nt) {
     const int x = (int)(idx / npairs), i = (int)(idx - (long)x * npairs);
+    if (!s.son[i]) continue;
     const int p = s.sp[i], q = s.sq[i];
-    if (q >= n) continue;
     const double c = s.sc[i];
     const double2 g = s.ssg[i];
     double2* rowA = M + (long)x * n;
@@ -110,8 +117,8 @@ __device__ void fp64_round(double2* __restrict__ M, double2* __restrict__ U, int
   // rows of A
   for (long idx = tid; idx < (long)npairs * n; idx += nt) {
     const int i = (int)(idx / n), y = (int)(idx - (long)i * n);
+    if (!s.son[i]) continue;
     const int p = s.sp[i], q = s.sq[i];
-    if (q >= n) continue;
     const double c = s.sc[i];
     const double2 g = s.ssg[i];
     double2* a = M + (long)p * n + y;
@@ -123,8 +130,8 @@ __device__ void fp64_round(double2* __restrict__ M, double2* __restrict__ U, int
   __syncthreads();
   // exact values of each rotated 2x2 block
   for (int i = tid; i < npairs; i += nt) {
+    if (!s.son[i]) continue;
     const int p = s.sp[i], q = s.sq[i];
-    if (q >= n) continue;
     M[(long)p * n + q] = make_double2(0.0, 0.0);
     M[(long)q * n + p] = make_double2(0.0, 0.0);
     M[(long)p * n + p] = make_double2(s.sapp[i] - s.stb[i], 0.0);
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_big(const double2* __restrict__
   bool conv = false;
   int post = 0, sweep = 0;
   while (!(conv && post >= 1) && sweep < max_sweeps) {
-    for (int r = 0; r < np - 1; ++r) fp64_round(M, U, n, np, r, thresh2, rs);
+    for (int r = 0; r < np - 1; ++r) fp64_round(M, U, n, np, r, thresh2, 0.0, rs);
     ++sweep;
     if (conv) ++post;
     part = 0.0;
@@ -392,9 +399,11 @@ __global__ void k_ns_update(double2* __restrict__ V, const double2* __restrict__
   V[i] = make_double2(fma(1.5, v.x, -0.5 * t.x), fma(1.5, v.y, -0.5 * t.y));
 }
 
-// FP64 sweeps on A' = V^H A V (Mw, its Hermitian part taken first), accumulating into U, until
-// every remaining angle |A'_ij / (A'_jj - A'_ii)|^2 is below th2 (tested before the first sweep
-// when try_before), or the off-diagonal norm is below polish_tol ||A||_F.  On the angle exit the
+// FP64 threshold sweeps on A' = V^H A V (Mw, its Hermitian part taken first; only pairs whose
+// angle is above sqrt(th2) and whose coupling is above polish_tol ||A||_F are rotated),
+// accumulating into U, until every remaining coupling has an angle |A'_ij / (A'_jj - A'_ii)|^2
+// below th2 or is below polish_tol ||A||_F (tested before the first sweep when try_before), or
+// the off-diagonal norm is below polish_tol ||A||_F.  On the angle exit the
 // first-order finish is prepared: Mw becomes X with X_ij = A'_ij / (A'_jj - A'_ii) (zero diagonal),
 // so that V = U (I + X) completes the eigenvectors to th2 (the update is anti-Hermitian to first
 // order), and lam_j = A'_jj + sum_i |A'_ij|^2 / (A'_jj - A'_ii) the eigenvalues; otherwise X = 0.
@@ -438,7 +447,9 @@ __global__ void __launch_bounds__(1024) k_jacobi_polish_big(double2* __restrict_
         if (r < c) {
           const double2 m = M[idx];
           const double gap = M[(long)c * n + c].x - M[(long)r * n + r].x;
-          if (!(fma(m.x, m.x, m.y * m.y) <= th2 * (gap * gap))) bad = 1;
+          const double m2 = fma(m.x, m.x, m.y * m.y);
+          // a small angle (first-order finish) or a coupling at the polish tolerance
+          if (!(m2 <= th2 * (gap * gap)) && !(m2 <= tol2)) bad = 1;
         }
       }
       if (!__syncthreads_or(bad)) {
@@ -447,7 +458,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_polish_big(double2* __restrict_
       }
     }
     if (conv || sweep >= max_sweeps) break;
-    for (int r = 0; r < np - 1; ++r) fp64_round(M, U, n, np, r, thresh2, rs);
+    for (int r = 0; r < np - 1; ++r) fp64_round(M, U, n, np, r, thresh2 > tol2 ? thresh2 : tol2, th2, rs);
     ++sweep;
     part = 0.0;
     for (long idx = tid; idx < nn; idx += nt) {
@@ -463,7 +474,8 @@ __global__ void __launch_bounds__(1024) k_jacobi_polish_big(double2* __restrict_
     if (fin) {
       for (int i = 0; i < n; ++i) {
         const double2 m = M[(long)i * n + j];
-        if (i != j && (m.x != 0.0 || m.y != 0.0)) dl += fma(m.x, m.x, m.y * m.y) / (lj - M[(long)i * n + i].x);
+        const double gap = lj - M[(long)i * n + i].x, m2 = fma(m.x, m.x, m.y * m.y);
+        if (i != j && m2 != 0.0 && m2 <= th2 * (gap * gap)) dl += m2 / gap;
       }
     }
     slam[j] = lj + dl;
@@ -474,8 +486,9 @@ __global__ void __launch_bounds__(1024) k_jacobi_polish_big(double2* __restrict_
     if (i == j) continue;
     const double2 m = M[idx];
     double2 x = make_double2(0.0, 0.0);
-    if (fin && (m.x != 0.0 || m.y != 0.0)) {
-      const double inv = 1.0 / (M[(long)j * n + j].x - M[(long)i * n + i].x);
+    const double gap = M[(long)j * n + j].x - M[(long)i * n + i].x, m2 = fma(m.x, m.x, m.y * m.y);
+    if (fin && m2 != 0.0 && m2 <= th2 * (gap * gap)) {  // couplings left at tolerance level stay unrotated
+      const double inv = 1.0 / gap;
       x = make_double2(m.x * inv, m.y * inv);
     }
     M[idx] = x;
