@@ -639,7 +639,8 @@ int set_k_resident(eph_ctx* ctx, int nk, double* eps_k) {
                           1, ctx->stream));
   EPH_LAUNCH_S(EPH_STAGE_EIG, eig(ctx, as<double2>(ctx->Hk_tmp), nb2, nb, nb, nk, as<double>(ctx->eps_k), nb,
                            as<double2>(ctx->Uk), nb2));
-  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->big && ctx->opt.mixed_scheme == 0) {
+  if (ctx->opt.form == EPH_FORM_MIXED && ctx->opt.mixed_scheme == 0 &&
+      (!ctx->big || eph::band_tc_supported(ctx->nm, ctx->nb))) {
     // A operand of the tensor-core Re->k contractions: 5 fixed-point BF16 digits of the phases
     // (G3 uses the first 3 through 128-byte-swizzle maps, H(k+q) all 5 through 64-byte ones)
     const size_t slice = (size_t)nk * ctx->kpd;
@@ -677,6 +678,17 @@ struct QPlan {
   long KT, NW, gcols, X;
 };
 
+// Large shapes: the eigensolve runs a CTA per matrix, so a tile of QB x KT matrices should fill
+// whole waves of the SMs (the automatic budget grows to one wave, up to 1/8 of the device).
+long fit_waves(const eph_ctx* ctx, long KT, int QB, size_t per_pair) {
+  if (ctx->opt.k_tile > 0 || KT >= ctx->nk) return KT;
+  const long wave = (ctx->nsm + QB - 1) / QB;
+  if (KT < wave && ctx->ws_auto && per_pair * QB * (size_t)wave <= ctx->mem_total / 8) KT = wave;
+  if (KT > wave) KT -= KT % wave;
+  if (KT > ctx->nk) KT = ctx->nk;
+  return KT;
+}
+
 QPlan plan_q(const eph_ctx* ctx, int nq, size_t extra_per_pair) {
   QPlan p;
   const int nb2 = ctx->nb * ctx->nb;
@@ -693,14 +705,7 @@ QPlan plan_q(const eph_ctx* ctx, int nq, size_t extra_per_pair) {
   const size_t budget = (size_t)ctx->opt.workspace_mb << 20;
   long KT = ctx->opt.k_tile > 0 ? ctx->opt.k_tile : (long)(budget / (per_pair * p.QB));
   if (KT > ctx->nk) KT = ctx->nk;
-  if (ctx->big && ctx->opt.k_tile <= 0 && KT < ctx->nk) {
-    // the eigensolve runs a CTA per matrix: a tile of QB x KT matrices should fill whole
-    // waves of the SMs (the automatic budget grows to one wave, up to 1/8 of the device)
-    const long wave = (ctx->nsm + p.QB - 1) / p.QB;
-    if (KT < wave && ctx->ws_auto && per_pair * p.QB * (size_t)wave <= ctx->mem_total / 8) KT = wave;
-    if (KT > wave) KT -= KT % wave;
-    if (KT > ctx->nk) KT = ctx->nk;
-  }
+  if (ctx->big) KT = fit_waves(ctx, KT, p.QB, per_pair);
   if (ctx->big && p.QB * KT > 65535) KT = 65535 / p.QB;  // CTA-per-matrix eigensolve grid
   if (ctx->has_grid) {  // whole j1 slabs of the grid
     const long slab = (long)ctx->gn[1] * ctx->gn[2];
@@ -802,6 +807,12 @@ bool use_band_tc(const eph_ctx* ctx) {
          eph::band_tc_supported(ctx->nm, ctx->nb);
 }
 
+// the mixed form's k-list path with the tensor-core contractions (small shapes, and large ones
+// whose band rotation also runs on the tensor cores)
+bool mixed_list(const eph_ctx* ctx) {
+  return ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && (!ctx->big || use_band_tc(ctx));
+}
+
 // workspace of the tensor-core band rotation for npairs pairs of a tile of nkt k points: the
 // pairs go in chunks of at most ~6 GB of digit and product buffers
 size_t band_tc_bytes(const eph_ctx* ctx, long npairs, int nkt) {
@@ -833,8 +844,9 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
   }
   if (use_band_tc(ctx)) {  // mixed form: two batched five-digit tensor-core products
     EPH_TRY(ensure(ctx, ctx->tcband, band_tc_bytes(ctx, (long)nqb * nkt, nkt)));
-    EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc(Y, p.NW, Ukq, Uk, nqb, nkt, nm, nb, reinterpret_cast<float2*>(out),
-                                                     sgq, ctx->tcband.p, ctx->tcband.n, ctx->status + 1, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc(Y, 0, p.NW, nb2, Ukq, Uk, nqb, nkt, nm, nb,
+                                                     reinterpret_cast<float2*>(out), sgq, ctx->tcband.p, ctx->tcband.n,
+                                                     ctx->status + 1, ctx->stream));
     return EPH_OK;
   }
   double2* T = as<double2>(ctx->Tbuf);
@@ -898,11 +910,15 @@ int prepare_mixed(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
   // per (q,k): H(k+q) + V_{k+q} (FP64), eigenvalues, G3 (FP32 real embedding), host staging of g
   QPlan p = plan_q(ctx, nq, 0);
   {
-    const size_t per_pair = (size_t)nb2 * 16 * 2 + (size_t)nb * 8 + (size_t)nr * 4 + (host && want_g ? (size_t)gcols * 8 : 0);
+    size_t per_pair = (size_t)nb2 * 16 * 2 + (size_t)nb * 8 + (size_t)nr * 4 + (host && want_g ? (size_t)gcols * 8 : 0);
+    if (ctx->big) per_pair += (size_t)nb2 * 16 * 4 + (size_t)nb * 8;  // CTA eigensolver work
     const size_t budget = (size_t)ctx->opt.workspace_mb << 20;
     long KT = ctx->opt.k_tile > 0 ? ctx->opt.k_tile : (long)(budget / (per_pair * p.QB));
     if (KT > nk) KT = nk;
-    if (KT > 128) KT -= KT % 128;
+    if (ctx->big)
+      KT = fit_waves(ctx, KT, p.QB, per_pair);
+    else if (KT > 128)
+      KT -= KT % 128;
     if (KT < 1) KT = 1;
     p.KT = KT;
   }
@@ -923,6 +939,15 @@ int prepare_mixed(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
   }
   EPH_TRY(ensure(ctx, ctx->G3f, (size_t)p.QB * p.KT * nr * sizeof(float)));
   EPH_TRY(ensure(ctx, ctx->Hkq, (size_t)p.QB * p.KT * nb2 * sizeof(double2)));
+  if (ctx->big) {  // CTA eigensolver and tensor-core band rotation workspaces
+    size_t need = eig_work_bytes(ctx, nb, (long)p.QB * p.KT);
+    const size_t e2 = eig_work_bytes(ctx, nb, nk), e3 = eig_work_bytes(ctx, nm, p.QB);
+    need = need > e2 ? need : e2;
+    need = need > e3 ? need : e3;
+    EPH_TRY(ensure(ctx, ctx->jwork, need));
+    EPH_TRY(ensure(ctx, ctx->tcband, band_tc_bytes(ctx, (long)p.QB * p.KT, (int)p.KT)));
+    EPH_TRY(ensure(ctx, ctx->ut, (size_t)p.QB * nm * nm * sizeof(double2)));
+  }
   if (host && want_g) EPH_TRY(ensure(ctx, ctx->g_stage32, (size_t)p.QB * p.KT * gcols * 2 * sizeof(float)));
   *out = p;
   return EPH_OK;
@@ -1008,7 +1033,18 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
                                                           (int)k0, (int)nr, kp, nqb, as<float>(ctx->G3f), nr,
                                                           (long)nkt * nr, ctx->status + 1, ctx->stream));
       float* gout = static_cast<float*>(g);
-      if (host) {
+      if (ctx->big) {  // two five-digit tensor-core products per pair
+        float2* dst = host ? as<float2>(ctx->g_stage32) : reinterpret_cast<float2*>(gout) + ((long)q0 * nk + k0) * gcols;
+        EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc(ctx->G3f.p, 1, nr / 2, 0, as<double2>(ctx->Ukq),
+                                                         as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb, dst,
+                                                         host ? (long)nkt * gcols : (long)nk * gcols, ctx->tcband.p,
+                                                         ctx->tcband.n, ctx->status + 1, ctx->stream));
+        if (host)
+          for (int iq = 0; iq < nqb; ++iq)
+            EPH_CK(cudaMemcpyAsync(gout + 2L * ((long)(q0 + iq) * nk + k0) * gcols,
+                                   as<float>(ctx->g_stage32) + 2L * iq * nkt * gcols,
+                                   (size_t)nkt * gcols * 2 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+      } else if (host) {
         EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate_ff(as<float>(ctx->G3f), nr, as<double2>(ctx->Ukq),
                                                             as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
                                                             as<float>(ctx->g_stage32), 2L * nkt * gcols, ctx->stream));
@@ -1142,10 +1178,13 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
   if (!ctx) return EPH_EINVAL;
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
   if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
-  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && !ctx->big) {
-    if (ctx->opt.async && !ctx->opt.device_ptrs)
-      return fail(ctx, EPH_EINVAL, "async mode with host pointers: FP64 form, grid path or nb, nm > 16 only");
-    return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
+  if (mixed_list(ctx)) {
+    if (ctx->opt.async && !ctx->opt.device_ptrs) {
+      if (!ctx->big)
+        return fail(ctx, EPH_EINVAL, "async mode with host pointers: FP64 form, grid path or nb, nm > 16 only");
+    } else {
+      return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g);
+    }
   }
   // FP64 form; the mixed form on a product k grid or with nb, nm > 16 (FP64 Re->k and
   // eigensolves, band rotation in double-float arithmetic, complex64 g)
@@ -1388,7 +1427,7 @@ extern "C" int eph_reserve(eph_ctx* ctx, int nq) {
   if (nq < 1) return fail(ctx, EPH_EINVAL, "eph_reserve: nq < 1");
   QPlan p;
   EPH_TRY(ensure(ctx, ctx->qpts, (size_t)nq * 3 * sizeof(double)));
-  if (ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && !ctx->big) return prepare_mixed(ctx, nq, true, &p);
+  if (mixed_list(ctx) && !(ctx->big && ctx->opt.async && !ctx->opt.device_ptrs)) return prepare_mixed(ctx, nq, true, &p);
   return prepare_fp64(ctx, nq, true, &p);
 }
 

@@ -99,31 +99,40 @@ __global__ void k_vdigits(const double2* __restrict__ V, long sV, int nb, long n
   put_digits5(fixed40_d(x, 1), D, slice, idx);
 }
 
-// Stage-1 B digits, one warp per row w = p nrow + j: K = 2b + t of G3[p][j][b] (complex128 row of
-// nb elements at Y + p ldy + off + j nb); sB[w] = the row's scale.
-__global__ void k_gdigits(const double2* __restrict__ Y, long ldy, long off, int nrow, int nb, long rows, int kp,
+// Stage-1 B digits, one warp per row w = p nrow + j: K = 2b + t of G3[p][j][b] (complex row of nb
+// elements at Y + p ldy + off + j nb: complex128 from the FP64 contraction or complex64 from the
+// tensor-core one); sB[w] = the row's scale.
+__device__ __forceinline__ int biased_exp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+__device__ __forceinline__ int biased_exp(float x) { return (int)((__float_as_uint(x) >> 23) & 0xFF); }
+__device__ __forceinline__ long long fixed40(double x, int es) { return fixed40_d(x, es); }
+__device__ __forceinline__ long long fixed40(float x, int es) { return fixed40_f(x, es); }
+
+template <typename TC>  // double2 or float2
+__global__ void k_gdigits(const TC* __restrict__ Y, long ldy, long off, int nrow, int nb, long rows, int kp,
                           float* __restrict__ sB, __nv_bfloat16* __restrict__ D, long slice) {
+  using T = decltype(TC::x);
+  constexpr int bias = sizeof(T) == 8 ? 1023 : 127;
   const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= rows) return;  // whole warps
   const long p = w / nrow;
   const int j = (int)(w - p * nrow);
-  const double* src = reinterpret_cast<const double*>(Y + p * ldy + off + (long)j * nb);
-  double x[MAXKL];
+  const T* src = reinterpret_cast<const T*>(Y + p * ldy + off + (long)j * nb);
+  T x[MAXKL];
   int eb = 0;
 #pragma unroll
   for (int i = 0; i < MAXKL; ++i) {
     const int kk = lane + 32 * i;
-    x[i] = kk < 2 * nb ? src[kk] : 0.0;
-    eb = max(eb, (int)((__double_as_longlong(x[i]) >> 52) & 0x7FF));
+    x[i] = kk < 2 * nb ? src[kk] : (T)0;
+    eb = max(eb, biased_exp(x[i]));
   }
   eb = warp_max_int(eb);
-  const int es = eb ? eb - 1023 + 2 : 0;
+  const int es = eb ? eb - bias + 2 : 0;
   if (lane == 0) sB[w] = ldexpf(1.f, es);
 #pragma unroll
   for (int i = 0; i < MAXKL; ++i) {
     const int kk = lane + 32 * i;
-    if (kk < kp) put_digits5(fixed40_d(x[i], es), D, slice, w * kp + kk);
+    if (kk < kp) put_digits5(fixed40(x[i], es), D, slice, w * kp + kk);
   }
 }
 
@@ -205,8 +214,9 @@ size_t band_tc_work_bytes(int nk, int nm, int nb, long pairs) {
   return s.a1 + (size_t)pairs * s.per_pair + 4 * 1024;
 }
 
-cudaError_t launch_band_tc(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk, int nm,
-                           int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err, cudaStream_t st) {
+cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const double2* Ukq, const double2* Uk, int nq,
+                           int nk, int nm, int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err,
+                           cudaStream_t st) {
   const long npairs = (long)nq * nk;
   if (npairs <= 0) return cudaSuccess;
   if (!band_tc_supported(nm, nb) || nk < 1) return cudaErrorInvalidValue;
@@ -241,8 +251,13 @@ cudaError_t launch_band_tc(const double2* Y, long ldy, const double2* Ukq, const
       if ((e = make_tc_map_bf16_sw64(&mA2[d], A2 + d * aslice, pb * M, kp, 128)) != cudaSuccess) return e;
     }
     // stage 1: T^T = V_k^T G3^T per pair
-    k_gdigits<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(Y + p0 * ldy, ldy, (long)nb * nb, (int)Nr, nb,
-                                                                   rows, kp, sB, Bd, bslice);
+    const unsigned gblocks = (unsigned)((rows * 32 + 255) / 256);
+    if (y_f32)
+      k_gdigits<float2><<<gblocks, 256, 0, st>>>(static_cast<const float2*>(Y) + p0 * ldy, ldy, y_off, (int)Nr, nb,
+                                                 rows, kp, sB, Bd, bslice);
+    else
+      k_gdigits<double2><<<gblocks, 256, 0, st>>>(static_cast<const double2*>(Y) + p0 * ldy, ldy, y_off, (int)Nr, nb,
+                                                  rows, kp, sB, Bd, bslice);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_tc_hkq_gemm_b(mA1, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, nk,
                                   (int)(p0 % nk), M, 1, st)) != cudaSuccess)

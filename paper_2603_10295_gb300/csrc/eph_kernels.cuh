@@ -187,11 +187,13 @@ cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M
                                  float sA, const float* sB, float* C, long ldc, long sC, int* err, cudaStream_t st);
 // Band rotation of large shapes on the tensor cores (mixed form): g[iq][kk] (complex64, rows iq
 // sgq apart, pair (iq, kk) at kk nm nb^2) = V_{k+q}^H G3_nu V_k for the nq x nk pairs of a tile,
-// G3 at Y + (iq nk + kk) ldy + nb^2, V_{k+q} at Ukq + (iq nk + kk) nb^2, V_k at Uk + kk nb^2.
+// G3 at Y + (iq nk + kk) ldy + y_off (complex128, or complex64 when y_f32; ldy, y_off in complex
+// elements), V_{k+q} at Ukq + (iq nk + kk) nb^2, V_k at Uk + kk nb^2.
 // work: at least band_tc_work_bytes(nk, nm, nb, 1) bytes; more lets more pairs go per chunk.
 size_t band_tc_work_bytes(int nk, int nm, int nb, long pairs);
 bool band_tc_supported(int nm, int nb);
-cudaError_t launch_band_tc(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk, int nm,
-                           int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err, cudaStream_t st);
+cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const double2* Ukq, const double2* Uk, int nq,
+                           int nk, int nm, int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err,
+                           cudaStream_t st);
 
 }  // namespace eph
