@@ -343,16 +343,17 @@ def time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=False):
             "parity": "vs oracle.linewidths <= 1e-10 per k (tests/test_gpu_linewidths.py)"}
 
 
-def time_workload(name, args, dev, legs, QB, warmup, steps):
-    """Forward throughput on another of the paper-shaped workloads (device buffers, CUDA events)."""
+def time_workload(name, args, dev, legs, warmup, steps):
+    """Forward throughput on another of the paper-shaped workloads (device buffers, CUDA events).
+    legs: (form, uniform-grid path, q points per call)."""
     import torch
 
     from paper_2603_10295_gb300 import binding, synth
     wl = synth.make_workload(name)
     nk, nb, nm = len(wl.kpts), wl.nb, wl.nm
-    q_dev = torch.from_numpy(wl.qpts[:(warmup + steps) * QB].copy()).to(dev)
-    out = {"workload": describe(wl, argparse.Namespace(q_batch=QB))}
-    for form, grid in legs:
+    out = {"workload": describe(wl, argparse.Namespace(q_batch=legs[0][2]))}
+    for form, grid, QB in legs:
+        q_dev = torch.from_numpy(wl.qpts[:(warmup + steps) * QB].copy()).to(dev)
         st = torch.cuda.current_stream()
         ctx = binding.Context.from_workload(wl, form=form, device_ptrs=True, q_batch=QB, stream=st)
         if grid:
@@ -377,7 +378,7 @@ def time_workload(name, args, dev, legs, QB, warmup, steps):
         ms = e0.elapsed_time(e1) / steps
         prof = ctx.profile_read()
         key = form + ("_grid" if grid else "_list")
-        out[key] = {"value": QB * nk * nm * nb * nb / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+        out[key] = {"value": QB * nk * nm * nb * nb / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "q_per_step": QB,
                     "stage_ms_per_step": {k: round(v[0] / steps, 3) for k, v in prof.items() if v[0] > 0}}
         del g, e, o
         ctx.close()
@@ -626,8 +627,10 @@ def run_libeph(args):
     if rank == 0 and not args.no_other:
         # the MoS2-shaped (200x200 grid, Nb=11, Nm=9) and stanene-shaped (Nb=120, Nm=180) workloads
         line["other_workloads"] = {
-            "mos2": time_workload("mos2", args, dev, [("fp64", True), ("mixed", True), ("mixed", False)], QB, 2, 5),
-            "stanene": time_workload("stanene", args, dev, [("fp64", False), ("mixed", False)], 1, 1, 1)}
+            "mos2": time_workload("mos2", args, dev, [("fp64", True, QB), ("mixed", True, QB), ("mixed", False, QB)], 2, 5),
+            # FP64: one q per call keeps the Re->k GEMM's k tiles whole waves of 152 rows; the mixed
+            # form batches 4 q so that their dynamical-matrix eigensolves run side by side
+            "stanene": time_workload("stanene", args, dev, [("fp64", False, 1), ("mixed", False, 4)], 1, 1)}
     if rank == 0 and not args.no_linewidths:
         line["linewidths"] = time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=legs[0][1])
     if rank == 0 and not args.no_backward:

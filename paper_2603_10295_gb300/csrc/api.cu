@@ -772,11 +772,17 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
     // G2[e][nu][b] = sum_c u[c][nu] G1[c][e][b]: one GEMM per q, batched over Re (u^T from a transpose)
     EPH_TRY(ensure(ctx, ctx->ut, (size_t)nqb * nm * nm * sizeof(double2)));
     EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_transpose(as<double2>(ctx->uq), nm, nqb, as<double2>(ctx->ut), ctx->stream));
-    for (int iq = 0; iq < nqb; ++iq)
-      EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_zgemm_b2(nm, nb2, nm, as<double2>(ctx->ut) + (long)iq * nm * nm, nm, 0, 0,
-                                                        as<double2>(ctx->G1) + (long)iq * p.X, (long)ne * nb2, nb2, 0,
-                                                        W + (long)iq * ne * p.NW + nb2, nb2, p.NW, 0, ne, 1, 0,
-                                                        ctx->stream));
+    for (int iq = 0; iq < nqb; ++iq) {
+      const double2* ut = as<double2>(ctx->ut) + (long)iq * nm * nm;
+      const double2* G1 = as<double2>(ctx->G1) + (long)iq * p.X;
+      double2* Wq = W + (long)iq * ne * p.NW + nb2;
+      if (ctx->opt.form == EPH_FORM_MIXED)  // double-float on the FP32 pipe (~1e-13): the g of this form is c64
+        EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_zgemm_df_b2(nm, nb2, nm, ut, nm, 0, 0, G1, (long)ne * nb2, nb2, 0, Wq,
+                                                             nb2, p.NW, 0, ne, 1, 0, 0, ctx->stream));
+      else
+        EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_zgemm_b2(nm, nb2, nm, ut, nm, 0, 0, G1, (long)ne * nb2, nb2, 0, Wq, nb2,
+                                                          p.NW, 0, ne, 1, 0, ctx->stream));
+    }
   }
   if (ctx->has_grid && grid_stages) {
     // sum factorisation of Eq. 10 (and H(k+q)): W_q scattered into the Re box (with w_e),
