@@ -591,19 +591,30 @@ cudaError_t launch_eigh_big(const double2* A, long sA, long lda, int n, long bat
     k_jacobi32_big<<<(unsigned)nb, threads_for((long)sh.np * sh.np / 4), sh.smem, st>>>(
         Ab, sA, lda, n, sh.np, sh.lds, sh.vsm, reinterpret_cast<float2*>(G), Vw, 12);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // The products: FP64 for the FP64 eigendecomposition; double-float on the FP32 pipe (~1e-13
+    // relative) when eigenvalues are needed to ~1e-12 ||A|| (polish_tol >= 1e-13)
+    const bool df = polish_tol >= 1e-13;
+    auto mm = [&](const double2* A_, long lda_, long sA_, const double2* B_, double2* C_) {  // C = A B
+      return df ? launch_zgemm_df(n, n, n, A_, lda_, sA_, B_, n, nn, C_, n, nn, nb, st)
+                : launch_zgemm(n, n, n, A_, lda_, sA_, B_, n, nn, C_, n, nn, nb, st);
+    };
+    auto mh = [&](const double2* A_, const double2* B_, double2* C_) {  // C = A^H B
+      return df ? launch_zgemm_df_b2(n, n, n, A_, n, nn, 0, B_, n, nn, 0, C_, n, nn, 0, nb, 1, 1, 0, st)
+                : launch_zgemm_ah(n, n, n, A_, n, nn, B_, n, nn, C_, n, nn, nb, 0, st);
+    };
     // Newton-Schulz: V = Q (I + E) with |E| = d becomes Q (I - 1.5 E^2 + ...): the FP32
     // eigenvectors of an n ~ 100 matrix after a dozen sweeps are unitary only to d ~ 1e-5, so
     // two steps (d^2 ~ 1e-10, then rounding) in either form
     for (int it = 0; it < 2; ++it) {
-      if ((e = launch_zgemm_ah(n, n, n, Vw, n, nn, Vw, n, nn, G, n, nn, nb, 0, st)) != cudaSuccess) return e;
-      if ((e = launch_zgemm(n, n, n, Vw, n, nn, G, n, nn, T, n, nn, nb, st)) != cudaSuccess) return e;
+      if ((e = mh(Vw, Vw, G)) != cudaSuccess) return e;
+      if ((e = mm(Vw, n, nn, G, T)) != cudaSuccess) return e;
       const long tot = (long)nb * nn;
       k_ns_update<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Vw, T, tot);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // A' = V^H (A V)
-    if ((e = launch_zgemm(n, n, n, Ab, lda, sA, Vw, n, nn, T, n, nn, nb, st)) != cudaSuccess) return e;
-    if ((e = launch_zgemm_ah(n, n, n, Vw, n, nn, T, n, nn, M, n, nn, nb, 0, st)) != cudaSuccess) return e;
+    if ((e = mm(Ab, lda, sA, Vw, T)) != cudaSuccess) return e;
+    if ((e = mh(Vw, T, M)) != cudaSuccess) return e;
     // FP64 sweeps to the first-order finish: angles^2 <= 1e-16 for the FP64 eigendecomposition,
     // 1e-10 (tried right after A') when the eigenvectors are needed to 1e-12
     const double th2 = polish_tol >= 1e-13 ? 1e-10 : 1e-16;
@@ -611,7 +622,7 @@ cudaError_t launch_eigh_big(const double2* A, long sA, long lda, int n, long bat
                                                                        polish_tol >= 1e-13 ? 1 : 0, max_sweeps,
                                                                        status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_zgemm(n, n, n, Vw, n, nn, M, n, nn, T, n, nn, nb, st)) != cudaSuccess) return e;
+    if ((e = mm(Vw, n, nn, M, T)) != cudaSuccess) return e;
     k_eig_sort_big<<<(unsigned)nb, threads_for(nn / 4), 0, st>>>(Vw, T, lam, n, w + b0 * sw, sw, V + b0 * sV, sV);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -156,14 +156,33 @@ __global__ void k_digits_b(const double2* __restrict__ W, long ldw, long sW, int
     const double2 g = W[(long)q * sW + (long)e * ldw + col0 + j];
     x = (sgn == t) ? g.x : (sgn == 0 ? -g.y : g.y);
   }
-  const double inv_s = 1.0 / (double)sB[(long)q * 2 * ncols + row];
-  double y = x * inv_s * 256.0, sc = 1.0;
-  for (int d = 0; d < ndig; ++d) {
-    const double a = rint(y);
-    D[d * slice + idx] = __float2bfloat16_rn((float)(a * sc));  // pre-scaled by 2^-8d, exact
-    y = (y - a) * 256.0;
-    sc *= 0x1p-8;
+  // fixed point X = round(x / s 2^(8 ndig)) from the IEEE bits (integer pipe; s = 2^es), then
+  // signed base-256 digits from the top, each rounded to nearest (|d| <= 128)
+  const int es = (int)((__float_as_uint(sB[(long)q * 2 * ncols + row]) >> 23) & 0xFF) - 127;
+  const int F = 8 * ndig;
+  long long R = 0;
+  {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e != 0) {
+      const long long m = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+      const int sh = (e - 1023) - 52 + F - es;  // |x / s| <= 1/2: m 2^sh < 2^(F - 1)
+      if (sh >= 0)
+        R = m << sh;
+      else if (sh > -63)
+        R = (m + (1LL << (-sh - 1))) >> (-sh);
+      if (b >> 63) R = -R;
+    }
   }
+  float sc = 1.f;
+  for (int d = 0; d < ndig - 1; ++d) {
+    const int sh = 8 * (ndig - 1 - d);
+    const long long a = (R + (1LL << (sh - 1))) >> sh;
+    R -= a * (1LL << sh);
+    D[d * slice + idx] = __float2bfloat16_rn((float)(int)a * sc);  // pre-scaled by 2^-8d, exact
+    sc *= 0x1p-8f;
+  }
+  D[(ndig - 1) * slice + idx] = __float2bfloat16_rn((float)(int)R * sc);
 }
 
 cudaError_t launch_digits_b(const double2* W, long ldw, long sW, int col0, int ncols, int ne, int kp, int nq,
