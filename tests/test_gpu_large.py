@@ -67,6 +67,15 @@ def test_mixed_form_small_and_large(nb, na):
     check_mixed(ctx.interp(wl.kpts, wl.qpts), oracle.interpolate(wl), f"mixed nb={nb} nm={3 * na}")
 
 
+def test_mixed_large_odd_row_length():
+    # Nm Nb odd (17 x 3): the tensor-core band rotation needs an even row length, so this shape
+    # takes the FP64 Re->k flow with the double-float band rotation
+    wl = synth.make_workload("si_tiny", nb=17, na=1, nk=6, nq=3)
+    assert (wl.nm * wl.nb) % 2 == 1
+    ctx = binding.Context.from_workload(wl, form="mixed", q_batch=2)
+    check_mixed(ctx.interp(wl.kpts, wl.qpts), oracle.interpolate(wl), "mixed nb=17 nm=3")
+
+
 def test_large_shapes_rejected_where_not_supported():
     wl = synth.make_workload("si_tiny", nb=20, nk=4, nq=2)
     ctx = binding.Context.from_workload(wl)
