@@ -80,32 +80,39 @@ cudaError_t launch_mode_rotate(const double2* G1, const double2* u, int nq, int 
 }
 
 // One (q,k) pair of the band rotation in shared memory, three-multiplication complex
-// products (3 FMA per complex multiply-add instead of 4): V_k and G3 are staged with the
-// sums re + im, V_{k+q} with re - im, so that
-//   T = G3_nu V_k:          t1 = sum x.re y.re, t2 = sum x.im y.im, t3 = sum (x.re + x.im)(y.re + y.im),
-//                           T = (t1 - t2, t3 - t1 - t2);
-//   g = V_{k+q}^H T (conj): t3 = sum (x.re - x.im)(y.re + y.im), g = (t1 + t2, t3 - t1 + t2).
+// products (3 FMA per complex multiply-add instead of 4) in the form that needs one pre-sum of
+// the left operand and two of the right one: for x = a + ib, y = c + id,
+//   k1 = c (a + b),  k2 = a (d - c),  k3 = b (c + d),   x y = (k1 - k3) + i (k1 + k2),
+// summed over the contraction index with two final additions per output.
+//   T = G3_nu V_k:        x = G3 (pre-sum Gr + Gi), y = V_k (pre-sums Vi - Vr, Vr + Vi);
+//   g = V_{k+q}^H T:      x = T (pre-sum Tr + Ti), y = conj(V_{k+q}) (pre-sums -Vi - Vr, Vr - Vi).
+// Per pair 2 Nb^2 Nm (Nb + 1) + 2 Nb^2 (2 + Nm) + ... : 2,560 additions beside the 18,432 FMA at
+// the Si shapes (3,200 with the (re + im) sums of both operands).
 struct PairSmem {
-  double2 *uk, *ukq, *G, *T;
-  double *uks, *ukqd, *Gs, *Ts;
+  double *ukr, *ukd, *uks;   // V_k: Re, Im - Re, Re + Im
+  double *uqr, *uqm, *uqp;   // V_{k+q}: Re, -Im - Re, Re - Im
+  double2 *G, *T;
+  double *Gs, *Ts;
 };
 
 __device__ __forceinline__ PairSmem pair_smem(void* base, int nb, int nm) {
   const int nb2 = nb * nb, x = nm * nb2;
   PairSmem p;
-  p.uk = static_cast<double2*>(base);
-  p.ukq = p.uk + nb2;
-  p.G = p.ukq + nb2;
+  p.G = static_cast<double2*>(base);
   p.T = p.G + x;
-  p.uks = reinterpret_cast<double*>(p.T + x);
-  p.ukqd = p.uks + nb2;
-  p.Gs = p.ukqd + nb2;
+  p.Gs = reinterpret_cast<double*>(p.T + x);
   p.Ts = p.Gs + x;
+  p.ukr = p.Ts + x;
+  p.ukd = p.ukr + nb2;
+  p.uks = p.ukd + nb2;
+  p.uqr = p.uks + nb2;
+  p.uqm = p.uqr + nb2;
+  p.uqp = p.uqm + nb2;
   return p;
 }
 
 __host__ __device__ constexpr size_t pair_smem_bytes(int nb, int nm) {
-  return (size_t)(2 * nb * nb + 2 * nm * nb * nb) * (sizeof(double2) + sizeof(double));
+  return (size_t)(2 * nm * nb * nb) * (sizeof(double2) + sizeof(double)) + (size_t)6 * nb * nb * sizeof(double);
 }
 
 // Stages the pair and forms T = G3 V_k (all threads of the CTA; ends with a barrier).
@@ -115,10 +122,12 @@ __device__ __forceinline__ void pair_stage1(const PairSmem& s, const double2* __
   const int nb2 = nb * nb;
   for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
     const double2 a = ukg[t], b = ukqg[t];
-    s.uk[t] = a;
+    s.ukr[t] = a.x;
+    s.ukd[t] = a.y - a.x;
     s.uks[t] = a.x + a.y;
-    s.ukq[t] = b;
-    s.ukqd[t] = b.x - b.y;
+    s.uqr[t] = b.x;
+    s.uqm[t] = -b.y - b.x;
+    s.uqp[t] = b.x - b.y;
   }
   for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
     const double2 a = grow[t];
@@ -129,16 +138,17 @@ __device__ __forceinline__ void pair_stage1(const PairSmem& s, const double2* __
   for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) {
     const int nu = t / nb2, rem = t - nu * nb2, a = rem / nb, n = rem - a * nb;
     const int g0 = nu * nb2 + a * nb;
-    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    double k1 = 0.0, k2 = 0.0, k3 = 0.0;
     for (int b = 0; b < nb; ++b) {
-      const double2 x = s.G[g0 + b], y = s.uk[b * nb + n];
-      t1 = fma(x.x, y.x, t1);
-      t2 = fma(x.y, y.y, t2);
-      t3 = fma(s.Gs[g0 + b], s.uks[b * nb + n], t3);
+      const double2 x = s.G[g0 + b];
+      const int v = b * nb + n;
+      k1 = fma(s.ukr[v], s.Gs[g0 + b], k1);
+      k2 = fma(x.x, s.ukd[v], k2);
+      k3 = fma(x.y, s.uks[v], k3);
     }
-    const double2 v = make_double2(t1 - t2, t3 - t1 - t2);
-    s.T[t] = v;
-    s.Ts[t] = v.x + v.y;
+    const double2 tv = make_double2(k1 - k3, k1 + k2);
+    s.T[t] = tv;
+    s.Ts[t] = tv.x + tv.y;
   }
   __syncthreads();
 }
@@ -148,14 +158,15 @@ __device__ __forceinline__ double2 pair_g(const PairSmem& s, int t, int nb) {
   const int nb2 = nb * nb;
   const int nu = t / nb2, rem = t - nu * nb2, m = rem / nb, n = rem - m * nb;
   const int t0 = nu * nb2 + n;
-  double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+  double k1 = 0.0, k2 = 0.0, k3 = 0.0;
   for (int a = 0; a < nb; ++a) {
-    const double2 x = s.ukq[a * nb + m], y = s.T[t0 + a * nb];
-    t1 = fma(x.x, y.x, t1);
-    t2 = fma(x.y, y.y, t2);
-    t3 = fma(s.ukqd[a * nb + m], s.Ts[t0 + a * nb], t3);
+    const int v = a * nb + m, ti = t0 + a * nb;
+    const double2 y = s.T[ti];
+    k1 = fma(s.uqr[v], s.Ts[ti], k1);
+    k2 = fma(y.x, s.uqm[v], k2);
+    k3 = fma(y.y, s.uqp[v], k3);
   }
-  return make_double2(t1 + t2, t3 - t1 + t2);
+  return make_double2(k1 - k3, k1 + k2);
 }
 
 // One CTA per (q,k) pair: g_nu = V_{k+q}^H G3_nu V_k (2 nb^3 nm CMAC per pair).  keep (may be
