@@ -48,8 +48,8 @@ EIG_FP64_FLOPS = {(8, "fp64"): (2 * 1769472000 + 59392000 + 548864000) / 256000}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at one step = 4 q x 64,000 k
 TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
            ("k_zgemm", "si_full", 4): 242432512.0 + 1777470464.0,
-           ("k_jacobi_mixed", "si_full", 4): 263503872.0 + 230582272.0,
-           ("k_band_rotate", "si_full", 4): 2098326016.0 + 1534963712.0}
+           ("k_jacobi_mixed", "si_full", 4): 263387136.0 + 230558208.0,
+           ("k_band_rotate", "si_full", 4): 2097285888.0 + 1534482688.0}
 
 
 def parse():
