@@ -1,8 +1,8 @@
 // Band rotation g_nu = V_{k+q}^H G3_nu V_k (the last step of Eq. 7's evaluation, Eqs. 4-5
 // gauges) for shapes beyond the shared-memory kernels, on the tcgen05 tensor cores: the mixed
-// form's large-Nb path.  Two batched products of the five-digit fixed-point scheme of the H(k+q)
-// contraction (float-pair results, ~1e-12 relative), on the real embedding of the complex
-// matrices (K = 2 Nb, re/im interleaved):
+// form's large-Nb path.  Two batched products of the fixed-point digit scheme of the H(k+q)
+// contraction with four digits per operand (levels <= 3, ~2^-32 of each row's scale; float-pair
+// results), on the real embedding of the complex matrices (K = 2 Nb, re/im interleaved):
 //   stage 1, per pair:  C1[2n' + c][nu Nb + a] = (re, im)_c of T[(nu, a)][n'],  T = G3_nu V_k,
 //                       A = V_k embedded (rows 2n' + c, K = 2b + t), B = the G3 rows (nu, a);
 //   stage 2, per pair:  C2[2m + c][nu Nb + n'] = (re, im)_c of g_nu[m][n'],
@@ -19,54 +19,56 @@ namespace eph {
 namespace {
 
 constexpr int MAXKL = 16;  // K values per lane in the row kernels (Kp <= 512, Nb <= 256)
+constexpr int NDIG = 4;    // digits per operand: 32 bits, ~2^-32 of each row's scale (complex64 g)
+constexpr int FBITS = 8 * NDIG;
 
 // The digit kernels run on the integer pipe: FP64 arithmetic (and FP64 <-> integer conversion)
-// is ~1/64 of the FP32 rate on GB300, so the fixed-point value round(x 2^(40 - es)) of
-// x / s (s = 2^es) is formed from the IEEE bits.
-__device__ __forceinline__ long long fixed40_d(double x, int es) {
+// is ~1/64 of the FP32 rate on GB300, so the fixed-point value round(x 2^(F - es)) of
+// x / s (s = 2^es, F = 8 NDIG bits) is formed from the IEEE bits.
+__device__ __forceinline__ long long fixedF_d(double x, int es) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7FF);
   if (e == 0) return 0;  // zero or subnormal: below the row's last digit
   const long long m = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
-  const int sh = (e - 1023) - 52 + 40 - es;  // x 2^(40 - es) = m 2^sh
+  const int sh = (e - 1023) - 52 + FBITS - es;  // x 2^(F - es) = m 2^sh
   long long X;
   if (sh >= 0)
-    X = m << sh;  // |x / s| <= 1/2 keeps this below 2^40
+    X = m << sh;  // |x / s| <= 1/2 keeps this below 2^F
   else if (sh > -63)
     X = (m + (1LL << (-sh - 1))) >> (-sh);
   else
     X = 0;
   return (long long)(b >> 63) ? -X : X;
 }
-__device__ __forceinline__ long long fixed40_f(float x, int es) {
+__device__ __forceinline__ long long fixedF_f(float x, int es) {
   const unsigned int b = __float_as_uint(x);
   const int e = (int)((b >> 23) & 0xFF);
   if (e == 0) return 0;
   const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
-  const int sh = (e - 127) - 23 + 40 - es;
+  const int sh = (e - 127) - 23 + FBITS - es;
   long long X;
   if (sh >= 0)
     X = m << sh;
-  else if (sh > -40)
+  else if (sh > -62)
     X = (m + (1LL << (-sh - 1))) >> (-sh);
   else
     X = 0;
   return (b >> 31) ? -X : X;
 }
 
-// Five signed base-256 digits of X = round(y 2^40), |y| <= 1/2 (+ 2^-24): y = sum_i d_i
-// 2^-8(i+1) + O(2^-41), |d_i| <= 128; digit i stored pre-scaled by 2^-8i (exact in bf16).
-__device__ __forceinline__ void put_digits5(long long R, __nv_bfloat16* __restrict__ D, long slice, long idx) {
+// NDIG signed base-256 digits of X = round(y 2^F), |y| <= 1/2 (+ 2^-24): y = sum_i d_i
+// 2^-8(i+1) + O(2^-(F+1)), |d_i| <= 128; digit i stored pre-scaled by 2^-8i (exact in bf16).
+__device__ __forceinline__ void put_digits(long long R, __nv_bfloat16* __restrict__ D, long slice, long idx) {
   float scale = 1.f;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int sh = 32 - 8 * i;
+  for (int i = 0; i < NDIG - 1; ++i) {
+    const int sh = FBITS - 8 - 8 * i;
     const long long d = (R + (1LL << (sh - 1))) >> sh;  // round to nearest (arithmetic shift)
     R -= d * (1LL << sh);
     D[i * slice + idx] = __float2bfloat16_rn((float)(int)d * scale);
     scale *= 0x1p-8f;
   }
-  D[4 * slice + idx] = __float2bfloat16_rn((float)(int)R * scale);
+  D[(NDIG - 1) * slice + idx] = __float2bfloat16_rn((float)(int)R * scale);
 }
 
 // exponent es of the row scale s = 2^es >= 2 max|x| from the largest biased exponent eb of the
@@ -96,7 +98,7 @@ __global__ void k_vdigits(const double2* __restrict__ V, long sV, int nb, long n
     else
       x = (c == t) ? v.x : (c == 0 ? v.y : -v.y);
   }
-  put_digits5(fixed40_d(x, 1), D, slice, idx);
+  put_digits(fixedF_d(x, 1), D, slice, idx);
 }
 
 // Stage-1 B digits, one warp per row w = p nrow + j: K = 2b + t of G3[p][j][b] (complex row of nb
@@ -104,8 +106,8 @@ __global__ void k_vdigits(const double2* __restrict__ V, long sV, int nb, long n
 // tensor-core one); sB[w] = the row's scale.
 __device__ __forceinline__ int biased_exp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
 __device__ __forceinline__ int biased_exp(float x) { return (int)((__float_as_uint(x) >> 23) & 0xFF); }
-__device__ __forceinline__ long long fixed40(double x, int es) { return fixed40_d(x, es); }
-__device__ __forceinline__ long long fixed40(float x, int es) { return fixed40_f(x, es); }
+__device__ __forceinline__ long long fixedF(double x, int es) { return fixedF_d(x, es); }
+__device__ __forceinline__ long long fixedF(float x, int es) { return fixedF_f(x, es); }
 
 template <typename TC>  // double2 or float2
 __global__ void k_gdigits(const TC* __restrict__ Y, long ldy, long off, int nrow, int nb, long rows, int kp,
@@ -132,7 +134,7 @@ __global__ void k_gdigits(const TC* __restrict__ Y, long ldy, long off, int nrow
 #pragma unroll
   for (int i = 0; i < MAXKL; ++i) {
     const int kk = lane + 32 * i;
-    if (kk < kp) put_digits5(fixed40(x[i], es), D, slice, w * kp + kk);
+    if (kk < kp) put_digits(fixedF(x[i], es), D, slice, w * kp + kk);
   }
 }
 
@@ -161,7 +163,7 @@ __global__ void k_tdigits(const float2* __restrict__ C1, long sC, int nrow, int 
 #pragma unroll
   for (int i = 0; i < MAXKL; ++i) {
     const int kk = lane + 32 * i;
-    if (kk < kp) put_digits5(fixed40_f(x[i].x, es) + fixed40_f(x[i].y, es), D, slice, w * kp + kk);
+    if (kk < kp) put_digits(fixedF_f(x[i].x, es) + fixedF_f(x[i].y, es), D, slice, w * kp + kk);
   }
 }
 
@@ -196,9 +198,10 @@ BandTcShape band_tc_shape(int nk, int nm, int nb) {
   s.kp = ((2 * nb + 31) / 32) * 32;
   s.M = 2 * nb;
   s.Nr = (long)nm * nb;
-  s.a1 = align_up((size_t)5 * nk * s.M * s.kp * 2);
+  s.a1 = align_up((size_t)NDIG * nk * s.M * s.kp * 2);
   // B digits (shared by both stages), C float pairs (C1 then C2), A2 digits, B row scales
-  s.per_pair = (size_t)5 * s.Nr * s.kp * 2 + (size_t)s.M * s.Nr * 8 + (size_t)5 * s.M * s.kp * 2 + (size_t)s.Nr * 4;
+  s.per_pair =
+      (size_t)NDIG * s.Nr * s.kp * 2 + (size_t)s.M * s.Nr * 8 + (size_t)NDIG * s.M * s.kp * 2 + (size_t)s.Nr * 4;
   return s;
 }
 
@@ -230,9 +233,9 @@ cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const
   __nv_bfloat16* A1 = reinterpret_cast<__nv_bfloat16*>(base);
   char* chunk = base + sh.a1;
   __nv_bfloat16* Bd = reinterpret_cast<__nv_bfloat16*>(chunk);
-  float2* C = reinterpret_cast<float2*>(chunk + align_up((size_t)5 * PB * Nr * kp * 2));
+  float2* C = reinterpret_cast<float2*>(chunk + align_up((size_t)NDIG * PB * Nr * kp * 2));
   __nv_bfloat16* A2 = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(C) + align_up((size_t)PB * M * Nr * 8));
-  float* sB = reinterpret_cast<float*>(reinterpret_cast<char*>(A2) + align_up((size_t)5 * PB * M * kp * 2));
+  float* sB = reinterpret_cast<float*>(reinterpret_cast<char*>(A2) + align_up((size_t)NDIG * PB * M * kp * 2));
   cudaError_t e;
   // A digits of V_k for every k of the tile (stage 1)
   {
@@ -241,12 +244,12 @@ cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   CUtensorMap mA1[5], mA2[5], mB[5];
-  for (int d = 0; d < 5; ++d)
+  for (int d = 0; d < NDIG; ++d)
     if ((e = make_tc_map_bf16_sw64(&mA1[d], A1 + (long)d * nk * M * kp, (long)nk * M, kp, 128)) != cudaSuccess) return e;
   for (long p0 = 0; p0 < npairs; p0 += PB) {
     const long pb = npairs - p0 < PB ? npairs - p0 : PB;
     const long rows = pb * Nr, bslice = rows * kp, aslice = pb * M * kp;
-    for (int d = 0; d < 5; ++d) {
+    for (int d = 0; d < NDIG; ++d) {
       if ((e = make_tc_map_bf16_sw64(&mB[d], Bd + d * bslice, rows, kp, 128)) != cudaSuccess) return e;
       if ((e = make_tc_map_bf16_sw64(&mA2[d], A2 + d * aslice, pb * M, kp, 128)) != cudaSuccess) return e;
     }
@@ -260,7 +263,7 @@ cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const
                                                   rows, kp, sB, Bd, bslice);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_tc_hkq_gemm_b(mA1, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, nk,
-                                  (int)(p0 % nk), M, 1, st)) != cudaSuccess)
+                                  (int)(p0 % nk), M, 1, NDIG, st)) != cudaSuccess)
       return e;
     // stage 2: g = V_{k+q}^H T per pair
     k_tdigits<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(C, (long)M * Nr, (int)Nr, nb, rows, kp, sB, Bd,
@@ -270,7 +273,7 @@ cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const
                                                                 aslice);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_tc_hkq_gemm_b(mA2, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, (int)pb, 0,
-                                  M, 1, st)) != cudaSuccess)
+                                  M, 1, NDIG, st)) != cudaSuccess)
       return e;
     const long tot = pb * nm * nb * nb;
     k_gout<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, (long)M * Nr, (int)Nr, nb, nm, pb, nk, p0, g, sgq);

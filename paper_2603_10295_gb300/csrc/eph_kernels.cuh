@@ -179,10 +179,11 @@ cudaError_t make_tc_map_bf16_sw64(void* map_out, const void* base, long rows, in
 cudaError_t launch_tc_hkq_gemm(const void* maps_a5, const void* maps_b5, int M, int a_row0, int Nr, int Kp, int nq,
                                float sA, const float* sB, float2* C, long ldc, long sC, int* err, cudaStream_t st);
 // Same product batched over q with A rows a_row0 + ((q + a_qoff) mod a_mod) a_stride + m; morder = 1
-// takes the m tiles fastest (M of a few tiles sharing each B tile).
+// takes the m tiles fastest (M of a few tiles sharing each B tile); ndig = 4 or 5 digits per
+// operand (the first ndig maps of each array are read).
 cudaError_t launch_tc_hkq_gemm_b(const void* maps_a5, const void* maps_b5, int M, int a_row0, int Nr, int Kp, int nq,
                                  float sA, const float* sB, float2* C, long ldc, long sC, int* err, int a_mod,
-                                 int a_qoff, int a_stride, int morder, cudaStream_t st);
+                                 int a_qoff, int a_stride, int morder, int ndig, cudaStream_t st);
 cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
                                  float sA, const float* sB, float* C, long ldc, long sC, int* err, cudaStream_t st);
 // Band rotation of large shapes on the tensor cores (mixed form): g[iq][kk] (complex64, rows iq

@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(tcf::THREADS, 1) k_tc_fixed_gemm(const __grid_
 namespace tch {
 constexpr int BM = 128, BN = 128, BK = 32, STAGES = 2, ND = 5;
 constexpr int T_BYTES = BM * BK * 2;                           // 8 KiB per digit tile
-constexpr int STAGE_BYTES = 2 * ND * T_BYTES;                  // 80 KiB
+constexpr int STAGE_BYTES = 2 * ND * T_BYTES;                  // 80 KiB (five digits; four use 64)
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 512;                            // L0, L1, L2, L34 x 128 columns
 constexpr int THREADS = 192;
@@ -551,6 +551,9 @@ struct TcMaps10 {
 
 // Batch q reads A rows a_row0 + ((q + a_qoff) mod a_mod) a_stride + m (a_mod = 1: A shared by
 // every batch); morder = 1 takes the m tiles fastest.
+// NDG = 5: the scheme above; NDG = 4: four digits (32 bits) per operand, levels <= 3 kept
+// (10 MMAs per K step into the same four accumulators L0, L1, L2, L3), ~2^-32 relative.
+template <int NDG>
 __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_constant__ TcMaps10 maps, int M,
                                                                 int a_row0, int Nr, int Kp, int nq, float sA,
                                                                 const float* __restrict__ sB, float2* __restrict__ C,
@@ -564,6 +567,7 @@ __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_co
   using tch::ND;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr int SBYTES = 2 * NDG * tch::T_BYTES;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * tch::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* accf = empty + STAGES;  // the accumulators hold a finished tile
@@ -598,7 +602,7 @@ __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_co
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  auto tile = [&](int s, int which) -> unsigned char* { return smem + s * tch::STAGE_BYTES + which * tch::T_BYTES; };
+  auto tile = [&](int s, int which) -> unsigned char* { return smem + s * SBYTES + which * tch::T_BYTES; };
 
   if (warp == 0) {
     if (lane == 0) {  // ---- TMA producer
@@ -618,11 +622,11 @@ __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_co
             break;
           }
           if (*abort_flag) break;
-          mbar_arrive_expect_tx(&full[s], tch::STAGE_BYTES);
+          mbar_arrive_expect_tx(&full[s], SBYTES);
 #pragma unroll
-          for (int d = 0; d < ND; ++d) tma_load_2d(tile(s, d), &maps.a[d], kb * BK, arow, &full[s]);
+          for (int d = 0; d < NDG; ++d) tma_load_2d(tile(s, d), &maps.a[d], kb * BK, arow, &full[s]);
 #pragma unroll
-          for (int d = 0; d < ND; ++d) tma_load_2d(tile(s, ND + d), &maps.b[d], kb * BK, q * Nr + n0, &full[s]);
+          for (int d = 0; d < NDG; ++d) tma_load_2d(tile(s, NDG + d), &maps.b[d], kb * BK, q * Nr + n0, &full[s]);
         }
       }
       if (*abort_flag)
@@ -649,11 +653,11 @@ __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_co
             break;
           }
           fence_after();
-          uint64_t da[ND], db[ND];
+          uint64_t da[NDG], db[NDG];
 #pragma unroll
-          for (int d = 0; d < ND; ++d) {
+          for (int d = 0; d < NDG; ++d) {
             da[d] = tch::smem_desc64(smem_u32(tile(s, d)));
-            db[d] = tch::smem_desc64(smem_u32(tile(s, ND + d)));
+            db[d] = tch::smem_desc64(smem_u32(tile(s, NDG + d)));
           }
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
@@ -666,15 +670,17 @@ __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_co
             tcf::mma_bf16(t2, da[0] + o, db[2] + o, first);  // level 2
             tcf::mma_bf16(t2, da[1] + o, db[1] + o, 1u);
             tcf::mma_bf16(t2, da[2] + o, db[0] + o, 1u);
-            tcf::mma_bf16(t3, da[0] + o, db[3] + o, first);  // levels 3 and 4
+            tcf::mma_bf16(t3, da[0] + o, db[3] + o, first);  // level 3 (and 4)
             tcf::mma_bf16(t3, da[1] + o, db[2] + o, 1u);
             tcf::mma_bf16(t3, da[2] + o, db[1] + o, 1u);
             tcf::mma_bf16(t3, da[3] + o, db[0] + o, 1u);
-            tcf::mma_bf16(t3, da[0] + o, db[4] + o, 1u);
-            tcf::mma_bf16(t3, da[1] + o, db[3] + o, 1u);
-            tcf::mma_bf16(t3, da[2] + o, db[2] + o, 1u);
-            tcf::mma_bf16(t3, da[3] + o, db[1] + o, 1u);
-            tcf::mma_bf16(t3, da[4] + o, db[0] + o, 1u);
+            if constexpr (NDG == 5) {
+              tcf::mma_bf16(t3, da[0] + o, db[4] + o, 1u);
+              tcf::mma_bf16(t3, da[1] + o, db[3] + o, 1u);
+              tcf::mma_bf16(t3, da[2] + o, db[2] + o, 1u);
+              tcf::mma_bf16(t3, da[3] + o, db[1] + o, 1u);
+              tcf::mma_bf16(t3, da[4] + o, db[0] + o, 1u);
+            }
           }
           mma_commit(&empty[s]);
         }
@@ -808,30 +814,31 @@ cudaError_t make_tc_map_bf16_sw64(void* map_out, const void* base, long rows, in
 
 cudaError_t launch_tc_hkq_gemm(const void* maps_a5, const void* maps_b5, int M, int a_row0, int Nr, int Kp, int nq,
                                float sA, const float* sB, float2* C, long ldc, long sC, int* err, cudaStream_t st) {
-  return launch_tc_hkq_gemm_b(maps_a5, maps_b5, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err, 1, 0, 0, 0, st);
+  return launch_tc_hkq_gemm_b(maps_a5, maps_b5, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err, 1, 0, 0, 0, 5, st);
 }
 
 cudaError_t launch_tc_hkq_gemm_b(const void* maps_a5, const void* maps_b5, int M, int a_row0, int Nr, int Kp, int nq,
                                  float sA, const float* sB, float2* C, long ldc, long sC, int* err, int a_mod,
-                                 int a_qoff, int a_stride, int morder, cudaStream_t st) {
+                                 int a_qoff, int a_stride, int morder, int ndig, cudaStream_t st) {
   if (M <= 0 || Nr <= 0 || nq <= 0) return cudaSuccess;
-  if (a_mod < 1 || a_qoff < 0 || a_stride < 0) return cudaErrorInvalidValue;
+  if (a_mod < 1 || a_qoff < 0 || a_stride < 0 || (ndig != 4 && ndig != 5)) return cudaErrorInvalidValue;
   if (Kp % tch::BK != 0 || Kp <= 0 || Kp > 1024) return cudaErrorInvalidValue;  // exact level sums need K <= 1024
   if ((reinterpret_cast<uintptr_t>(C) & 15) != 0 || (ldc & 1) || (sC & 1)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_hkq_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tch::SMEM_BYTES);
+  auto kern = ndig == 5 ? k_tc_hkq_gemm<5> : k_tc_hkq_gemm<4>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tch::SMEM_BYTES);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return cudaErrorInvalidDevice;
   TcMaps10 maps;
-  for (int d = 0; d < 5; ++d) {
+  for (int d = 0; d < ndig; ++d) {
     maps.a[d] = static_cast<const CUtensorMap*>(maps_a5)[d];
     maps.b[d] = static_cast<const CUtensorMap*>(maps_b5)[d];
   }
   const long ntiles = (long)((Nr + tch::BN - 1) / tch::BN) * ((M + tch::BM - 1) / tch::BM) * nq;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
-  k_tc_hkq_gemm<<<grid, tch::THREADS, tch::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err,
-                                                             a_mod, a_qoff, a_stride, morder);
+  kern<<<grid, tch::THREADS, tch::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err, a_mod, a_qoff,
+                                                    a_stride, morder);
   return cudaGetLastError();
 }
 
