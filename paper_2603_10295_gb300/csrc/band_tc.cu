@@ -262,8 +262,8 @@ cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const
       k_gdigits<double2><<<gblocks, 256, 0, st>>>(static_cast<const double2*>(Y) + p0 * ldy, ldy, y_off, (int)Nr, nb,
                                                   rows, kp, sB, Bd, bslice);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_tc_hkq_gemm_b(mA1, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, nk,
-                                  (int)(p0 % nk), M, 1, NDIG, st)) != cudaSuccess)
+    if ((e = launch_tc_band_gemm(mA1, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, nk,
+                                 (int)(p0 % nk), M, st)) != cudaSuccess)
       return e;
     // stage 2: g = V_{k+q}^H T per pair
     k_tdigits<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(C, (long)M * Nr, (int)Nr, nb, rows, kp, sB, Bd,
@@ -272,8 +272,8 @@ cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const
     k_vdigits<<<(unsigned)((aslice + 255) / 256), 256, 0, st>>>(Ukq + p0 * nb * nb, (long)nb * nb, nb, pb, kp, 1, A2,
                                                                 aslice);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_tc_hkq_gemm_b(mA2, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, (int)pb, 0,
-                                  M, 1, NDIG, st)) != cudaSuccess)
+    if ((e = launch_tc_band_gemm(mA2, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, (int)pb, 0, M,
+                                 st)) != cudaSuccess)
       return e;
     const long tot = pb * nm * nb * nb;
     k_gout<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, (long)M * Nr, (int)Nr, nb, nm, pb, nk, p0, g, sgq);

@@ -186,6 +186,12 @@ cudaError_t launch_tc_hkq_gemm_b(const void* maps_a5, const void* maps_b5, int M
                                  int a_qoff, int a_stride, int morder, int ndig, cudaStream_t st);
 cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
                                  float sA, const float* sB, float* C, long ldc, long sC, int* err, cudaStream_t st);
+// Batched products of the band rotation: four digits per operand (maps: 4 CUtensorMaps each,
+// 64-byte swizzle), levels <= 3 in two accumulators (level 0 exact), two accumulator sets so the
+// epilogue overlaps the next tile; C float pairs; A rows as launch_tc_hkq_gemm_b, m tiles fastest.
+cudaError_t launch_tc_band_gemm(const void* maps_a4, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
+                                float sA, const float* sB, float2* C, long ldc, long sC, int* err, int a_mod,
+                                int a_qoff, int a_stride, cudaStream_t st);
 // Band rotation of large shapes on the tensor cores (mixed form): g[iq][kk] (complex64, rows iq
 // sgq apart, pair (iq, kk) at kk nm nb^2) = V_{k+q}^H G3_nu V_k for the nq x nk pairs of a tile,
 // G3 at Y + (iq nk + kk) ldy + y_off (complex128, or complex64 when y_f32; ldy, y_off in complex

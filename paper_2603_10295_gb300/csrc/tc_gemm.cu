@@ -751,6 +751,208 @@ __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_co
   }
 }
 
+// ----------------------------------------------------------------------------- batched band products
+// The band rotation's products (complex64 result, ~2^-31 relative suffices): four digits per
+// operand, levels <= 3, with level 0 exact in its own accumulator and levels 1-3 in a second one
+// (their sum is at most 2^-7 of level 0, so its FP32 rounding is ~2^-31 of the result), which
+// leaves room for two accumulator sets: the epilogue of one tile runs under the MMAs of the next.
+// 32-wide K slices (64-byte swizzle), three 64 KiB stages.  Batch q reads A rows
+// a_row0 + ((q + a_qoff) mod a_mod) a_stride + m; tiles (m fastest, then n, then q).
+namespace tcb {
+constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3, ND = 4;
+constexpr int T_BYTES = BM * BK * 2;                       // 8 KiB per digit tile
+constexpr int STAGE_BYTES = 2 * ND * T_BYTES;              // 64 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 512;                        // 2 sets x (L0, L123) x 128 columns
+constexpr int THREADS = 192;
+}  // namespace tcb
+
+__global__ void __launch_bounds__(tcb::THREADS, 1) k_tc_band_gemm(const __grid_constant__ TcMaps10 maps, int M,
+                                                                 int a_row0, int Nr, int Kp, int nq, float sA,
+                                                                 const float* __restrict__ sB, float2* __restrict__ C,
+                                                                 long ldc, long sC, int* __restrict__ err, int a_mod,
+                                                                 int a_qoff, int a_stride) {
+  using namespace tc;
+  using tcb::BM;
+  using tcb::BN;
+  using tcb::BK;
+  using tcb::STAGES;
+  using tcb::ND;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * tcb::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;  // [2] accumulator set b holds a finished tile
+  uint64_t* acce = accf + 2;        // [2] accumulator set b has been drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkb = Kp / BK;
+  const int ntn = (Nr + BN - 1) / BN, ntm = (M + BM - 1) / BM;
+  const long ntiles = (long)ntn * ntm * nq;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tcb::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto tile = [&](int s, int which) -> unsigned char* { return smem + s * tcb::STAGE_BYTES + which * tcb::T_BYTES; };
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- TMA producer
+      long it = 0;
+      for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        int q, m0, n0;
+        tch::tile_coords_mfast(t, ntm, ntn, &q, &m0, &n0);
+        const int arow = a_row0 + ((q + a_qoff) % a_mod) * a_stride + m0;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1))) {
+            *abort_flag = 1;
+            atomicOr(err, 1);
+            break;
+          }
+          if (*abort_flag) break;
+          mbar_arrive_expect_tx(&full[s], tcb::STAGE_BYTES);
+#pragma unroll
+          for (int d = 0; d < ND; ++d) tma_load_2d(tile(s, d), &maps.a[d], kb * BK, arow, &full[s]);
+#pragma unroll
+          for (int d = 0; d < ND; ++d) tma_load_2d(tile(s, ND + d), &maps.b[d], kb * BK, q * Nr + n0, &full[s]);
+        }
+      }
+      // after an abort: wait (bounded) for the loads still in flight
+      if (*abort_flag)
+        for (long j = (it > STAGES ? it - STAGES : 0); j < it; ++j) mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      long it = 0, lt = 0;
+      for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++lt) {
+        const int b = (int)(lt & 1);
+        if (lt >= 2 && !mbar_wait(&acce[b], (uint32_t)(((lt / 2) - 1) & 1))) {
+          *abort_flag = 1;
+          atomicOr(err, 8);
+          break;
+        }
+        fence_after();
+        const uint32_t d0 = tmem + (uint32_t)(b * 256), d1 = d0 + 128;
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (*abort_flag || !mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1))) {
+            *abort_flag = 1;
+            atomicOr(err, 2);
+            ok = false;
+            break;
+          }
+          fence_after();
+          uint64_t da[ND], db[ND];
+#pragma unroll
+          for (int d = 0; d < ND; ++d) {
+            da[d] = tch::smem_desc64(smem_u32(tile(s, d)));
+            db[d] = tch::smem_desc64(smem_u32(tile(s, ND + d)));
+          }
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K
+            const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+            tcf::mma_bf16(d0, da[0] + o, db[0] + o, first);  // level 0 (exact)
+            tcf::mma_bf16(d1, da[0] + o, db[1] + o, first);  // levels 1-3
+            tcf::mma_bf16(d1, da[1] + o, db[0] + o, 1u);
+            tcf::mma_bf16(d1, da[0] + o, db[2] + o, 1u);
+            tcf::mma_bf16(d1, da[1] + o, db[1] + o, 1u);
+            tcf::mma_bf16(d1, da[2] + o, db[0] + o, 1u);
+            tcf::mma_bf16(d1, da[0] + o, db[3] + o, 1u);
+            tcf::mma_bf16(d1, da[1] + o, db[2] + o, 1u);
+            tcf::mma_bf16(d1, da[2] + o, db[1] + o, 1u);
+            tcf::mma_bf16(d1, da[3] + o, db[0] + o, 1u);
+          }
+          mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+        }
+        mma_commit(&accf[b]);  // the tile's accumulators are complete (or the loop was aborted)
+        if (!ok) break;
+      }
+    }
+    __syncwarp();
+  } else {  // ---- epilogue, warps 2..5: TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    long lt = 0;
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const int b = (int)(lt & 1);
+      const bool ok = mbar_wait(&accf[b], (uint32_t)((lt / 2) & 1));
+      if (!ok || *abort_flag) {
+        if (!ok) atomicOr(err, 4);
+        break;
+      }
+      fence_after();
+      int q, m0, n0;
+      tch::tile_coords_mfast(t, ntm, ntn, &q, &m0, &n0);
+      const int row = m0 + quarter * 32 + lane;
+      const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+      float2* crow = C + (long)q * sC + (long)row * ldc;
+      const float* srow = sB + (long)q * Nr;
+      const float sc = sA * 0x1p-16f;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r0[16], r1[16];
+        tmem_ld16(tl + c0, r0);
+        tmem_ld16(tl + 128 + c0, r1);
+        tmem_ld_wait();
+        if (row < M) {
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+            const int col = n0 + c0 + i;
+            float2 v[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              float h = __uint_as_float(r0[i + u]), l = 0.f;
+              tch::two_sum(h, l, __uint_as_float(r1[i + u]));
+              const float f = (col + u < Nr) ? sc * srow[col + u] : 0.f;  // powers of two: exact
+              v[u] = make_float2(h * f, l * f);
+            }
+            if (col + 1 < Nr) {
+              *reinterpret_cast<float4*>(crow + col) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+            } else if (col < Nr) {
+              crow[col] = v[0];
+            }
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) tcf::mbar_arrive(&acce[b]);
+    }
+  }
+  // drain: after an abort the producer waits (bounded) for its last loads (above); every warp
+  // then meets here before the TMEM is released
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcb::TMEM_COLS) : "memory");
+  }
+}
+
 // ----------------------------------------------------------------------------- host side
 namespace {
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -839,6 +1041,30 @@ cudaError_t launch_tc_hkq_gemm_b(const void* maps_a5, const void* maps_b5, int M
   const int grid = (int)(ntiles < sms ? ntiles : sms);
   kern<<<grid, tch::THREADS, tch::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err, a_mod, a_qoff,
                                                     a_stride, morder);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_band_gemm(const void* maps_a4, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
+                                float sA, const float* sB, float2* C, long ldc, long sC, int* err, int a_mod,
+                                int a_qoff, int a_stride, cudaStream_t st) {
+  if (M <= 0 || Nr <= 0 || nq <= 0) return cudaSuccess;
+  if (Kp % tcb::BK != 0 || Kp <= 0 || Kp > 1024) return cudaErrorInvalidValue;  // exact level-0 sums need K <= 1024
+  if (a_mod < 1 || a_qoff < 0 || a_stride < 0) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(C) & 15) != 0 || (ldc & 1) || (sC & 1)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_band_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tcb::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorInvalidDevice;
+  TcMaps10 maps;
+  for (int d = 0; d < tcb::ND; ++d) {
+    maps.a[d] = static_cast<const CUtensorMap*>(maps_a4)[d];
+    maps.b[d] = static_cast<const CUtensorMap*>(maps_b4)[d];
+  }
+  const long ntiles = (long)((Nr + tcb::BN - 1) / tcb::BN) * ((M + tcb::BM - 1) / tcb::BM) * nq;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  k_tc_band_gemm<<<grid, tcb::THREADS, tcb::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err,
+                                                               a_mod, a_qoff, a_stride);
   return cudaGetLastError();
 }
 
