@@ -208,56 +208,76 @@ def measured_peaks():
 
 
 def time_form(wl, form, args, q_dev, k_dev, rank, world, local, dev, QB, use_grid=False):
-    """Times args.steps q batches of one form on the device (inputs resident in HBM)."""
+    """Times args.steps q batches of one form on the device (inputs resident in HBM).
+
+    The timed steps run through an asynchronous context (no host synchronisation between calls,
+    as a pipelined caller would run it); the per-stage breakdown comes from the same steps
+    repeated through a synchronous context with CUDA-event profiling."""
     import torch
 
     from paper_2603_10295_gb300 import binding
     nk, nb, nm = len(wl.kpts), wl.nb, wl.nm
-    st = torch.cuda.current_stream()
-    ctx = binding.Context.from_workload(wl, form=form, device_ptrs=True, q_batch=QB, stream=st)
+    # an explicit stream: the library enqueues on it and the timing events bracket its work
+    # (torch's legacy default stream would leave the library on a stream of its own)
+    st = torch.cuda.Stream()
     eps_k = torch.empty(nk, nb, dtype=torch.float64, device=dev)
     gdt = torch.complex128 if form == "fp64" else torch.complex64
     eps_kq = torch.empty(QB, nk, nb, dtype=torch.float64, device=dev)
     om = torch.empty(QB, nm, dtype=torch.float64, device=dev)
     g = torch.empty(QB, nk, nm, nb, nb, dtype=gdt, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(st)
-    if use_grid:
-        ctx.eph_set_k_grid(*wl.kgrid, None, eps_k)
-    else:
-        ctx.eph_set_k(nk, k_dev, eps_k)
-    e1.record(st)
-    torch.cuda.synchronize()
-    setk_ms = e0.elapsed_time(e1)
     nsteps = args.warmup + args.steps
 
-    def step(i):
-        ctx.eph_interp_q(QB, q_dev[i * QB:(i + 1) * QB], eps_kq, om, g)
+    def context(asyn):
+        c = binding.Context.from_workload(wl, form=form, device_ptrs=True, q_batch=QB, stream=st, async_mode=asyn)
+        torch.cuda.synchronize()
+        e0.record(st)
+        if use_grid:
+            c.eph_set_k_grid(*wl.kgrid, None, eps_k)
+        else:
+            c.eph_set_k(nk, k_dev, eps_k)
+        e1.record(st)
+        torch.cuda.synchronize()
+        c.eph_sync()
+        return c, e0.elapsed_time(e1)
+
+    ctx, setk_ms = context(True)
+
+    def step(c, i):
+        c.eph_interp_q(QB, q_dev[i * QB:(i + 1) * QB], eps_kq, om, g)
 
     for i in range(args.warmup):
-        step(i)
+        step(ctx, i)
+    ctx.eph_sync()
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    ctx.profile(True)
-    ctx.profile_reset()
     launches0 = ctx.launches()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     e0.record(st)
     for i in range(args.warmup, nsteps):
-        step(i)
+        step(ctx, i)
     e1.record(st)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    ctx.eph_sync()  # device status flags of the timed calls
     el_ms = e0.elapsed_time(e1)
     launches = ctx.launches() - launches0
-    prof = ctx.profile_read()
-    ctx.profile(False)
+    ctx.close()
+    # stage breakdown: the same steps, synchronous calls with CUDA-event profiling
+    pctx, _ = context(False)
+    step(pctx, 0)
+    pctx.profile(True)
+    pctx.profile_reset()
+    for i in range(args.warmup, nsteps):
+        step(pctx, i)
+    prof = pctx.profile_read()
+    pctx.profile(False)
+    pctx.close()
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([el_ms], device=dev, dtype=torch.float64)
@@ -270,7 +290,6 @@ def time_form(wl, form, args, q_dev, k_dev, rank, world, local, dev, QB, use_gri
                setk_ms=setk_ms, setk_share_ms=setk_share_ms, launches=launches, prof=prof, clocks=clk,
                g_bytes=g.numel() * g.element_size())
     del g, eps_kq, om
-    ctx.close()
     torch.cuda.empty_cache()
     return out
 
