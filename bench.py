@@ -624,14 +624,22 @@ def run_libeph(args):
         for i in range(args.warmup):
             hctx.eph_interp_q(QB, q_h[i * QB:(i + 1) * QB], *outs[i % len(outs)])
         hctx.eph_sync()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(args.warmup, nsteps):
             hctx.eph_interp_q(QB, q_h[i * QB:(i + 1) * QB], *outs[i % len(outs)])
         hctx.eph_sync()
         t_e2e = time.perf_counter() - t0
         hctx.close()
+        if world > 1:  # whole job: every rank's units over the slowest rank's time
+            t = torch.tensor([t_e2e, t_setk], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e, t_setk = (float(x) for x in t.tolist())
         ekq_h, om_h, g_h = outs[0]
-        e2e_units = args.steps * QB * nk * nm * nb * nb
+        e2e_units = world * args.steps * QB * nk * nm * nb * nb
         out = {"value": e2e_units / (t_e2e + t_setk * (args.steps * QB) / len(wl.qpts)), "unit": UNIT,
                "h2d_bytes_per_step": QB * 3 * 8,
                "d2h_bytes_per_step": g_h.numel() * g_h.element_size() + ekq_h.numel() * 8 + om_h.numel() * 8,
@@ -639,22 +647,28 @@ def run_libeph(args):
         del g_h
         return out
 
-    if rank == 0 and not args.no_e2e:
-        line["e2e"] = e2e(forms[0], grid=legs[0][1])
-        if "mixed" in line:
-            line["mixed"]["e2e"] = e2e("mixed", grid=use_grid)
-    if rank == 0 and not args.no_other:
+    # every rank runs the end-to-end leg (the whole job's rate); the other workloads, linewidths,
+    # adjoint and CPU baseline are single-GPU extras, run at N=1 only
+    if not args.no_e2e:
+        e2e_head = e2e(forms[0], grid=legs[0][1])
+        e2e_mixed = e2e("mixed", grid=use_grid) if ("mixed", use_grid) in res and forms[0] == "fp64" else None
+        if rank == 0:
+            line["e2e"] = e2e_head
+            if e2e_mixed is not None:
+                line["mixed"]["e2e"] = e2e_mixed
+    single = rank == 0 and world == 1
+    if single and not args.no_other:
         # the MoS2-shaped (200x200 grid, Nb=11, Nm=9) and stanene-shaped (Nb=120, Nm=180) workloads
         line["other_workloads"] = {
             "mos2": time_workload("mos2", args, dev, [("fp64", True, QB), ("mixed", True, QB), ("mixed", False, QB)], 2, 5),
             # FP64: one q per call keeps the Re->k GEMM's k tiles whole waves of 152 rows; the mixed
             # form batches 4 q so that their dynamical-matrix eigensolves run side by side
             "stanene": time_workload("stanene", args, dev, [("fp64", False, 1), ("mixed", False, 4)], 1, 1)}
-    if rank == 0 and not args.no_linewidths:
+    if single and not args.no_linewidths:
         line["linewidths"] = time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=legs[0][1])
-    if rank == 0 and not args.no_backward:
+    if single and not args.no_backward:
         line["backward"] = time_backward(args)
-    if rank == 0 and not args.no_cpu_baseline:
+    if single and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_k)
     if rank == 0:
         print(json.dumps(line), flush=True)
