@@ -124,6 +124,22 @@ def _ptr(x):
     raise TypeError(f"unsupported buffer type {type(x)}")
 
 
+def _points(x, name):
+    """A (n, 3) C-contiguous float64 copy (or view) of a list of points in crystal coordinates."""
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    if a.ndim != 2 or a.shape[1] != 3:
+        raise ValueError(f"{name} must have shape (n, 3), got {a.shape}")
+    return a
+
+
+def _shaped(x, shape, dtype, name):
+    """A C-contiguous array of exactly `shape` (host-mode inputs whose size the library assumes)."""
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if a.shape != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {a.shape}")
+    return a
+
+
 class Context:
     """One eph_ctx: Wannier data resident on the current CUDA device.
 
@@ -237,9 +253,8 @@ class Context:
 
     def vjp(self, kpts, qpts, grad_g):
         """dL/dg(Re,Rp) for an upstream gradient grad_g [nq][nk][nm][nb][nb] (complex128)."""
-        kpts = np.ascontiguousarray(kpts, dtype=np.float64)
-        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
-        grad_g = np.ascontiguousarray(grad_g, dtype=np.complex128)
+        kpts, qpts = _points(kpts, "kpts"), _points(qpts, "qpts")
+        grad_g = _shaped(grad_g, (len(qpts), len(kpts), self.nm, self.nb, self.nb), np.complex128, "grad_g")
         out = np.empty((self.np_, self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
         self.eph_interp_vjp(len(kpts), kpts, len(qpts), qpts, grad_g, out)
         self.nk = len(kpts)   # the call replaces the context's k list
@@ -251,9 +266,8 @@ class Context:
 
     def bloch_to_wannier(self, kpts, qpts, g):
         """Eq. 6: g(Re,Rp) [np][nm][ne][nb][nb] from g(k',q') [nq][nk][nm][nb][nb] on coarse grids."""
-        kpts = np.ascontiguousarray(kpts, dtype=np.float64)
-        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
-        g = np.ascontiguousarray(g, dtype=np.complex128)
+        kpts, qpts = _points(kpts, "kpts"), _points(qpts, "qpts")
+        g = _shaped(g, (len(qpts), len(kpts), self.nm, self.nb, self.nb), np.complex128, "g")
         out = np.empty((self.np_, self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
         self.eph_bloch_to_wannier(len(kpts), kpts, len(qpts), qpts, g, out)
         self.nk = len(kpts)   # the call replaces the context's k list
@@ -268,7 +282,7 @@ class Context:
 
     def set_k_window(self, kpts, e_lo, e_hi):
         """Keeps the k points with a band in [e_lo, e_hi]: (kept indices, their eps_k)."""
-        kpts = np.ascontiguousarray(kpts, dtype=np.float64)
+        kpts = _points(kpts, "kpts")
         kidx = np.empty(len(kpts), dtype=np.int32)
         eps = np.empty((len(kpts), self.nb))
         n = self.eph_set_k_window(len(kpts), kpts, e_lo, e_hi, eps, kidx)
@@ -280,7 +294,7 @@ class Context:
 
     def interp_q_window(self, qpts, e_lo, e_hi):
         """(eps_kq, omega, g, keep) with g = 0 on the pairs screened out by the window."""
-        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
+        qpts = _points(qpts, "qpts")
         nq = len(qpts)
         eps_kq = np.empty((nq, self.nk, self.nb))
         omega = np.empty((nq, self.nm))
@@ -299,6 +313,8 @@ class Context:
     def eigh(self, A):
         """Batched Hermitian eigendecomposition of A [batch][n][n] (host mode): (w, V), ascending."""
         A = np.ascontiguousarray(A, dtype=np.complex128)
+        if A.ndim != 3 or A.shape[1] != A.shape[2]:
+            raise ValueError(f"A must have shape (batch, n, n), got {A.shape}")
         batch, n = A.shape[0], A.shape[1]
         w = np.empty((batch, n))
         V = np.empty((batch, n, n), dtype=np.complex128)
@@ -306,8 +322,8 @@ class Context:
         return w, V
 
     def linewidths(self, qpts, wq=None, kT=0.025852, mu=0.0, sigma=0.05, omega_min=1e-6):
-        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
-        wq = None if wq is None else np.ascontiguousarray(wq, dtype=np.float64)
+        qpts = _points(qpts, "qpts")
+        wq = None if wq is None else _shaped(wq, (len(qpts),), np.float64, "wq")
         gamma = np.empty((self.nk, self.nb))
         self.eph_linewidths(len(qpts), qpts, wq, kT, mu, sigma, omega_min, gamma)
         return gamma
@@ -318,7 +334,7 @@ class Context:
 
     # -- host-mode conveniences (numpy in, numpy out) ----------------------
     def set_k(self, kpts):
-        kpts = np.ascontiguousarray(kpts, dtype=np.float64)
+        kpts = _points(kpts, "kpts")
         eps_k = np.empty((len(kpts), self.nb))
         self.eph_set_k(len(kpts), kpts, eps_k)
         return eps_k
@@ -329,7 +345,7 @@ class Context:
         return eps_k
 
     def interp_q(self, qpts, want_g=True):
-        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
+        qpts = _points(qpts, "qpts")
         nq = len(qpts)
         eps_kq = np.empty((nq, self.nk, self.nb))
         omega = np.empty((nq, self.nm))
@@ -346,9 +362,8 @@ class Context:
         return eps_k, eps_kq, omega, g
 
     def loss_and_grad(self, kpts, qpts, w_nk, omega_min):
-        kpts = np.ascontiguousarray(kpts, dtype=np.float64)
-        qpts = np.ascontiguousarray(qpts, dtype=np.float64)
-        w_nk = np.ascontiguousarray(w_nk, dtype=np.float64)
+        kpts, qpts = _points(kpts, "kpts"), _points(qpts, "qpts")
+        w_nk = _shaped(w_nk, (len(kpts), self.nb), np.float64, "w_nk")
         L = np.zeros(1)
         grad = np.empty((self.np_, self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
         self.eph_interp_backward(len(kpts), kpts, len(qpts), qpts, w_nk, omega_min, L, grad)

@@ -65,3 +65,30 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
 def test_product_path_has_no_fallback(tmp_path):
     with pytest.raises(RuntimeError):
         binding.load_library(str(tmp_path / "missing.so"))
+
+
+def test_binding_rejects_misshaped_host_arrays():
+    # the host-mode conveniences check shapes before any library call, so a (n,) point list or
+    # a gradient of the wrong size never reaches the C side as an out-of-range read
+    import numpy as np
+    assert binding._points([[0.0, 0.5, 0.25]], "kpts").shape == (1, 3)
+    assert binding._points(np.zeros((0, 3)), "kpts").shape == (0, 3)
+    for bad in (np.zeros(3), np.zeros((4, 2)), np.zeros((2, 3, 1))):
+        with pytest.raises(ValueError):
+            binding._points(bad, "kpts")
+    with pytest.raises(ValueError):
+        binding._shaped(np.zeros((2, 3)), (3, 2), np.float64, "w_nk")
+    ctx = object.__new__(binding.Context)   # no library handle: any C call would fail differently
+    ctx.nb, ctx.nm, ctx.nk, ctx.np_, ctx.ne, ctx.form = 2, 3, 4, 5, 6, "fp64"
+    with pytest.raises(ValueError):
+        ctx.set_k(np.zeros(3))
+    with pytest.raises(ValueError):
+        ctx.interp_q(np.zeros((2, 2)))
+    with pytest.raises(ValueError):
+        ctx.vjp(np.zeros((4, 3)), np.zeros((2, 3)), np.zeros((2, 4, 3, 2)))
+    with pytest.raises(ValueError):
+        ctx.loss_and_grad(np.zeros((4, 3)), np.zeros((2, 3)), np.zeros((4, 3)), 1e-6)
+    with pytest.raises(ValueError):
+        ctx.linewidths(np.zeros((2, 3)), wq=np.ones(3))
+    with pytest.raises(ValueError):
+        ctx.eigh(np.zeros((2, 3, 4)))
