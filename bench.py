@@ -68,10 +68,48 @@ def parse():
     ap.add_argument("--no-backward", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-linewidths", action="store_true", help="skip the fused linewidth measurement")
     ap.add_argument("--no-other", action="store_true", help="skip the MoS2- and stanene-shaped forward lines")
+    ap.add_argument("--capture", default=None, choices=sorted(CAPTURES),
+                    help="run one small untimed case for an ncu capture and exit (no JSON line)")
     ap.add_argument("--k-path", default="grid", choices=["grid", "list"],
                     help="FP64 form: sum-factorised Re->k on the workload's uniform k grid, or the dense "
                          "Re->k GEMM on the k list")
     return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- ncu capture cases
+# name -> (workload, its overrides, form, q points per call, calls).  Each runs eph_set_k and
+# `calls` eph_interp_q calls on device buffers, untimed: the programs the stanene-shaped
+# profiles were taken from (a 120-band, 180-mode case small enough for a full-section
+# capture of the band-rotation tensor-core product, and the bench's stanene mixed leg).
+CAPTURES = {
+    "stanene-band-tc": ("stanene", dict(nk=16, nq=2, box=(range(0, 1), range(-1, 2), range(0, 1))), "mixed", 1, 2),
+    "stanene-mixed": ("stanene", dict(nk=512, nq=8), "mixed", 4, 2),
+}
+
+
+def run_capture(args):
+    import torch
+
+    from paper_2603_10295_gb300 import binding, synth
+    name, over, form, QB, calls = CAPTURES[args.capture]
+    dev = torch.device("cuda:0")
+    wl = synth.make_workload(name, **over)
+    nk, nb, nm = len(wl.kpts), wl.nb, wl.nm
+    ctx = binding.Context.from_workload(wl, form=form, device_ptrs=True, stream=torch.cuda.current_stream(),
+                                        q_batch=QB)
+    ctx.eph_set_k(nk, torch.from_numpy(wl.kpts).to(dev))
+    gdt = torch.complex128 if form == "fp64" else torch.complex64
+    e = torch.empty(QB, nk, nb, dtype=torch.float64, device=dev)
+    o = torch.empty(QB, nm, dtype=torch.float64, device=dev)
+    g = torch.empty(QB, nk, nm, nb, nb, dtype=gdt, device=dev)
+    q_d = torch.from_numpy(wl.qpts).to(dev)
+    for i in range(calls):
+        ctx.eph_interp_q(QB, q_d[i * QB:(i + 1) * QB], e, o, g)
+    torch.cuda.synchronize()
+    print(f"capture {args.capture}: {wl.name} Nb={nb} Nm={nm} Ne={wl.ne}, {nk} k, {calls} x {QB} q, "
+          f"{ctx.launches()} kernel launches", flush=True)
+    ctx.close()
+    return 0
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -680,6 +718,8 @@ def run_libeph(args):
 
 def main():
     args = parse()
+    if args.capture:
+        return run_capture(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_libeph(args)
