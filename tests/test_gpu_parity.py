@@ -181,3 +181,45 @@ def test_async_host_mode_matches_sync(form, grid):
         ref = sync.interp_q(wl.qpts[3 * i:3 * i + 3])
         for a, b in zip(outs[i], ref):
             assert np.array_equal(a.numpy(), b)
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_phase_reduction_exact_far_from_the_cell(form):
+    # k and q on a 1/8 grid plus integer offsets up to 2^20: every product k_i n_i and their
+    # sum t are exact in FP64, so the exact reduction t - rint(t) gives the phases of the points
+    # inside the cell (cell-based phases are periodic); a phase formed in lower precision, or
+    # from a rounded 2 pi t, is off by ~1e-9 there.  Both lists match the oracle at the in-cell
+    # points (eigenvalues and frequencies directly, g through the subspace sums).
+    rng = np.random.default_rng(21)
+    wl = synth.make_workload("si_tiny", nk=9, nq=3)
+    k0 = rng.integers(0, 8, (9, 3)) / 8.0
+    q0 = rng.integers(0, 8, (3, 3)) / 8.0
+    kf = k0 + rng.integers(-(1 << 20), 1 << 20, (9, 3))
+    qf = q0 + rng.integers(-(1 << 20), 1 << 20, (3, 3))
+    ref = oracle.interpolate(wl, k0, q0)
+    for pts in ((k0, q0), (kf, qf)):
+        got = binding.Context.from_workload(wl, form=form).interp(*pts)
+        if form == "fp64":
+            check(got, ref, TOL_FP64, "far points")
+        else:
+            e_k, e_kq, om, g = got
+            assert max(gauge.max_rel_eps(e_k, ref[0]), gauge.max_rel_eps(e_kq, ref[1]),
+                       gauge.max_rel_omega(om, ref[2])) <= 1e-10
+            assert gauge.max_rel_S(g, ref[3], ref[0], ref[1], ref[2]) <= 1e-6
+
+
+def test_phase_reduction_grid_shift_far_from_the_cell():
+    # the uniform-grid path with an integer-plus-dyadic shift of 2^19: the same points as the
+    # unshifted grid after reduction, so the oracle at the in-cell points is the reference
+    wl = synth.make_workload("si_tiny", nk=2, nq=3)
+    n = (4, 2, 8)
+    base = (0.125, 0.0, -0.25)
+    far = (0.125 + (1 << 19), -3.0 * (1 << 17), -0.25 - 12345.0)
+    a = binding.Context.from_workload(wl)
+    near = (a.set_k_grid(*n, shift=base),) + a.interp_q(wl.qpts)
+    b = binding.Context.from_workload(wl)
+    shifted = (b.set_k_grid(*n, shift=far),) + b.interp_q(wl.qpts)
+    k = synth.uniform_grid(*n) + np.asarray(base)[None, :]
+    ref = oracle.interpolate(wl, k, wl.qpts)
+    check(near, ref, TOL_FP64, "grid, in-cell shift")
+    check(shifted, ref, TOL_FP64, "grid, far shift")

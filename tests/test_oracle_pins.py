@@ -41,6 +41,12 @@ def test_phase_properties():
     assert np.abs(oracle.phases(k + G, R) - P).max() < 1e-12
     k2 = rng.random((50, 3))
     assert np.abs(oracle.phases(k, R) * oracle.phases(k2, R) - oracle.phases(k + k2, R)).max() < 1e-12
+    # dyadic points 2^20 cells away: k.R is exact in FP64, so the exact reduction t - rint(t)
+    # returns the in-cell argument up to the sign of r = +-1/2 (rint rounds half to even), i.e.
+    # the in-cell phases to the last bit of sin(pi) (an unreduced sin(2 pi t) is off by ~1e-8)
+    kd = rng.integers(0, 8, size=(50, 3)) / 8.0
+    Gd = rng.integers(-(1 << 20), 1 << 20, size=(50, 3))
+    assert np.abs(oracle.phases(kd + Gd, R) - oracle.phases(kd, R)).max() <= 1e-15
     # explicit value: k=(1/4,0,0), R=(1,0,0) -> i
     assert abs(oracle.phases(np.array([[0.25, 0, 0]]), np.array([[1, 0, 0]]))[0, 0] - 1j) < 1e-15
 
