@@ -2,7 +2,7 @@
 
 Each mutation replaces one oracle function (on the CPU) by a plausible wrong
 variant: a flipped phase sign, a missing conjugate, a transposed operand, a
-dropped mass factor.  The pins in test_oracle_pins.py are then run against the
+dropped mass factor or weight, a wrong eigenvalue order or sign, k - q for k + q.  The pins in test_oracle_pins.py are then run against the
 mutated oracle and at least one of them has to fail.
 """
 import numpy as np
@@ -21,12 +21,18 @@ PIN_FUNCS = [
     pins.test_wannier_round_trip,
     pins.test_unitarity_invariant_and_periodicity,
     pins.test_vjp_is_the_adjoint_of_the_interpolation,
+    pins.test_unstable_spring_chain_negative_frequency,
+    pins.test_complex_hopping_and_diatomic_chain_closed_forms,
 ]
 
 _orig_phases = eo.phases
 _orig_g_req = eo.g_req_to_bloch
 _orig_phonon = eo.phonon_eigen
 _orig_vjp = eo.vjp
+_orig_hk = eo.hamiltonian_k
+_orig_dq = eo.dynamical_matrix
+_orig_eig = eo.electron_eigen
+_orig_g1 = eo.g_rp_to_q
 
 
 def _phase_sign(pts, R, w=None):
@@ -66,6 +72,68 @@ def _vjp_kq_gauge_conjugated(a, kpts, qpts, gbar, ev):
     return _orig_vjp(a, kpts, qpts, gbar, dict(ev, V_kq=ev["V_kq"].conj()))
 
 
+def _hk_minus_k(kpts, Re, we, H_Re):
+    # e^{-ik.R} in H(k): the same spectrum only with time-reversal symmetry
+    return _orig_hk(-np.asarray(kpts), Re, we, H_Re)
+
+
+def _hk_transposed(kpts, Re, we, H_Re):
+    return _orig_hk(kpts, Re, we, np.ascontiguousarray(np.swapaxes(H_Re, 1, 2)))
+
+
+def _hk_no_weight(kpts, Re, we, H_Re):
+    return _orig_hk(kpts, Re, None, H_Re)
+
+
+def _dq_minus_q(qpts, Rp, wp, Phi_Rp, masses):
+    # e^{-iq.Rp} in D(q): same frequencies (real force constants), conjugated mode vectors
+    return _orig_dq(-np.asarray(qpts), Rp, wp, Phi_Rp, masses)
+
+
+def _dq_without_masses(qpts, Rp, wp, Phi_Rp, masses):
+    return _orig_dq(qpts, Rp, wp, Phi_Rp, np.ones(len(masses)))
+
+
+def _eig_descending(Hk):
+    e, V = _orig_eig(Hk)
+    return e[..., ::-1], V[..., ::-1]
+
+
+def _omega_unsigned(Dq, masses):
+    om, e, u = _orig_phonon(Dq, masses)
+    return np.abs(om), e, u
+
+
+def _mode_vector_times_mass(Dq, masses):
+    om, e, u = _orig_phonon(Dq, masses)
+    return om, e, e * np.sqrt(np.repeat(np.asarray(masses, dtype=np.float64), 3))[None, :, None]
+
+
+def _g1_no_weight(qpts, Rp, wp, g_ReRp):
+    return _orig_g1(qpts, Rp, None, g_ReRp)
+
+
+def _g_req_bands_swapped(kpts, Re, we, G1q, V_k, V_kq, u_q):
+    return np.swapaxes(_orig_g_req(kpts, Re, we, G1q, V_k, V_kq, u_q), 2, 3)
+
+
+def _interpolate_k_minus_q(a, kpts=None, qpts=None, return_eigvecs=False):
+    # the oracle's steps with H(k - q) in place of H(k + q)
+    kpts = a.kpts if kpts is None else np.asarray(kpts, dtype=np.float64)
+    qpts = a.qpts if qpts is None else np.asarray(qpts, dtype=np.float64)
+    eps_k, V_k = eo.electron_eigen(eo.hamiltonian_k(kpts, a.Re, a.we, a.H_Re))
+    omega, _, u = eo.phonon_eigen(eo.dynamical_matrix(qpts, a.Rp, a.wp, a.Phi_Rp, a.masses), a.masses)
+    G1 = eo.g_rp_to_q(qpts, a.Rp, a.wp, a.g_ReRp)
+    eps_kq, g, vkq = [], [], []
+    for iq in range(len(qpts)):
+        e_kq, V_kq = eo.electron_eigen(eo.hamiltonian_k(kpts - qpts[iq][None, :], a.Re, a.we, a.H_Re))
+        eps_kq.append(e_kq)
+        vkq.append(V_kq)
+        g.append(eo.g_req_to_bloch(kpts, a.Re, a.we, G1[iq], V_k, V_kq, u[iq]))
+    out = (eps_k, np.stack(eps_kq), omega, np.stack(g))
+    return out + (dict(V_k=V_k, V_kq=np.stack(vkq), u=u),) if return_eigvecs else out
+
+
 MUTATIONS = {
     "phase_sign": ("phases", _phase_sign),
     "phase_missing_2pi": ("phases", _phase_unreduced_wrong_scale),
@@ -75,6 +143,17 @@ MUTATIONS = {
     "mode_vector_without_mass": ("phonon_eigen", _phonon_no_mass),
     "vjp_mode_rotation_unconjugated": ("vjp", _vjp_u_unconjugated),
     "vjp_band_gauge_conjugated": ("vjp", _vjp_kq_gauge_conjugated),
+    "hamiltonian_phase_sign": ("hamiltonian_k", _hk_minus_k),
+    "hamiltonian_transposed": ("hamiltonian_k", _hk_transposed),
+    "hamiltonian_without_weights": ("hamiltonian_k", _hk_no_weight),
+    "dynamical_matrix_phase_sign": ("dynamical_matrix", _dq_minus_q),
+    "dynamical_matrix_without_masses": ("dynamical_matrix", _dq_without_masses),
+    "eigenvalues_descending": ("electron_eigen", _eig_descending),
+    "unstable_mode_sign_dropped": ("phonon_eigen", _omega_unsigned),
+    "mode_vector_times_mass": ("phonon_eigen", _mode_vector_times_mass),
+    "eq9_without_weights": ("g_rp_to_q", _g1_no_weight),
+    "band_indices_swapped": ("g_req_to_bloch", _g_req_bands_swapped),
+    "k_minus_q": ("interpolate", _interpolate_k_minus_q),
 }
 
 
@@ -89,4 +168,5 @@ def test_planted_mistake_is_caught(name, monkeypatch):
             pin()
         except AssertionError:
             caught.append(pin.__name__)
+            break
     assert caught, f"mutation {name} passed every pin"

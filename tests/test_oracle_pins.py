@@ -101,6 +101,75 @@ def test_spring_chain_closed_form():
     assert np.abs(om[:, :2]).max() < 1e-12
 
 
+
+def test_unstable_spring_chain_negative_frequency():
+    # a negative spring constant: lambda(q) = 4K/M sin^2(pi q) < 0, reported as
+    # omega = -sqrt(|lambda|) (the sign convention for unstable modes)
+    K, M = -2.3, 28.0855
+    R = np.array([[-1, 0, 0], [0, 0, 0], [1, 0, 0]], np.int32)
+    Phi = np.zeros((3, 3, 3))
+    Phi[1, 0, 0] = 2 * K
+    Phi[0, 0, 0] = Phi[2, 0, 0] = -K
+    q = np.stack([np.linspace(0.05, 0.95, 19), np.zeros(19), np.zeros(19)], -1)
+    om, _, _ = oracle.phonon_eigen(oracle.dynamical_matrix(q, R, np.ones(3), Phi, [M]), [M])
+    expect = -2 * np.sqrt(-K / M) * np.abs(np.sin(np.pi * q[:, 0])) * 0.0646541513
+    assert np.abs(om[:, 0] - expect).max() < 1e-9 * np.abs(expect).max()
+    assert np.abs(om[:, 1:]).max() < 1e-12
+
+
+class _Arrays:
+    pass
+
+
+def _chain_model(eps0, t, K1, K2, M, Gt):
+    """One band with complex hopping t on the bond to the next cell (t* back), two equal
+    masses M per cell with x springs K1 inside the cell and K2 to the next cell, and a
+    coupling Gt[6] at Re = Rp = 0 only.  R list: -x, 0, +x."""
+    R = np.array([[-1, 0, 0], [0, 0, 0], [1, 0, 0]], np.int32)
+    H = np.array([np.conj(t), eps0, t], dtype=np.complex128).reshape(3, 1, 1)
+    Phi = np.zeros((3, 6, 6))
+    Phi[1, 0, 0] = Phi[1, 3, 3] = K1 + K2
+    Phi[1, 0, 3] = Phi[1, 3, 0] = -K1
+    Phi[2, 3, 0] = -K2      # atom 1 of the home cell to atom 0 of the cell at +x
+    Phi[0, 0, 3] = -K2      # its transpose at -x
+    gW = np.zeros((3, 6, 3, 1, 1), np.complex128)
+    gW[1, :, 1, 0, 0] = Gt
+    a = _Arrays()
+    a.H_Re, a.Phi_Rp, a.g_ReRp, a.Re, a.Rp = H, Phi, gW, R, R
+    a.we, a.wp, a.masses = np.ones(3), np.ones(3), np.array([M, M])
+    return a
+
+
+def test_complex_hopping_and_diatomic_chain_closed_forms():
+    # electrons: eps(k) = eps0 + 2|t| cos(2 pi k + arg t) for the e^{+ik.R} convention
+    # (distinguishes k from -k), at k and at k+q.  Phonons: the diatomic chain,
+    # D(q) = [[a, b], [conj(b), a]] on the two x displacements with a = (K1+K2)/M and
+    # b = -(K1 + K2 e^{-2 pi i q})/M; branches a -+ |b| with eigenvectors
+    # (1, -+e^{-i beta})/sqrt(2), beta = arg b.  With one band, V = 1 and g_nu = u_nu^T Gt,
+    # so |g| of the two x branches is |Gt_0 -+ e^{-i beta} Gt_3| / sqrt(2M) (the sign of
+    # the phase convention, the mass factor and the mode index all enter).
+    eps0, t = 0.4, 0.9 * np.exp(0.7j)
+    K1, K2, M = 3.1, 1.2, 20.0
+    rng = np.random.default_rng(8)
+    Gt = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    a = _chain_model(eps0, t, K1, K2, M, Gt)
+    k = np.stack([rng.random(7), rng.random(7), rng.random(7)], -1)
+    q = np.stack([np.linspace(0.07, 0.93, 9), rng.random(9), rng.random(9)], -1)
+    eps_k, eps_kq, omega, g = oracle.interpolate(a, k, q)
+    band = lambda x: eps0 + 2 * abs(t) * np.cos(2 * np.pi * x + np.angle(t))
+    assert np.abs(eps_k[:, 0] - band(k[:, 0])).max() < 1e-14
+    assert np.abs(eps_kq[:, :, 0] - band(k[None, :, 0] + q[:, None, 0])).max() < 1e-14
+    av = (K1 + K2) / M
+    b = -(K1 + K2 * np.exp(-2j * np.pi * q[:, 0])) / M
+    beta = np.angle(b)
+    unit = 0.0646541513
+    assert (omega[:, :4] ** 2).max() < 1e-14 * av * unit ** 2      # y, z: no springs (lambda at rounding level)
+    assert np.abs(omega[:, 4] - np.sqrt(av - np.abs(b)) * unit).max() < 1e-9
+    assert np.abs(omega[:, 5] - np.sqrt(av + np.abs(b)) * unit).max() < 1e-9
+    for s, nu in ((-1, 4), (1, 5)):
+        expect = np.abs(Gt[0] + s * np.exp(-1j * beta) * Gt[3]) / np.sqrt(2 * M)
+        assert np.abs(np.abs(g[:, :, nu, 0, 0]) - expect[:, None]).max() < 1e-12
+
 def _plane_wave_inputs(nb=4, na=2, seed=3):
     rng = np.random.default_rng(seed)
     R = synth.box_vectors(range(-1, 2), range(-1, 2), range(0, 1))
