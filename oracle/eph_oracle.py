@@ -24,6 +24,24 @@ Conventions (readings of the paper where it is silent):
   * u_{kappa alpha, nu}(q) = e_{kappa alpha, nu}(q)/sqrt(M_kappa) (mass-scaled
     phonon eigenvector; no sqrt(hbar/2 omega) factor), index kappa alpha = 3 kappa + alpha.
   * omega = sign(lambda) sqrt(|lambda|) * hbar sqrt(eV/(A^2 amu)), in eV.
+
+Pins (tests/test_oracle_pins.py; tests/test_oracle_mutations.py plants a mistake in each
+function below and checks that a pin fails):
+  * phases: unit modulus, R = 0, periodicity (bit-level 2^20 cells out), product rule, e^{i pi/2}.
+  * hamiltonian_k, electron_eigen: one-band chain and complex-hopping chain dispersions (the
+    latter fixes the sign of the phase, at k and at k+q); plane-wave case with a DFT-matrix H0.
+  * dynamical_matrix, phonon_eigen: hermiticity and the three zero modes at Gamma (acoustic sum
+    rule); monatomic spring chain (stable and unstable: the sign of omega); diatomic chain mode
+    vectors (the sign of the phase and u = e/sqrt(M), seen through |g|); the eV unit against
+    the textbook THz factor.
+  * g_rp_to_q, g_req_to_bloch, interpolate: single-(Re,Rp) plane-wave closed form; Eq. 7 by
+    brute force on tiny inputs; the Wannier round trip through Eq. 6; the gauge-free norm
+    identity, periodicity and linearity.
+  * loss_and_grad, vjp: central differences (exact for a quadratic form), Euler's identity,
+    the dot-product identity <vjp(gbar), dg> = <gbar, g(dg)>.
+  * linewidths: the closed form for one band, one mode and a constant coupling, and its
+    symmetries.
+  * g_bloch_to_wannier (Eq. 6): the round trip above.
 """
 from __future__ import annotations
 
