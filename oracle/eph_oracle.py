@@ -37,8 +37,9 @@ function below and checks that a pin fails):
   * g_rp_to_q, g_req_to_bloch, interpolate: single-(Re,Rp) plane-wave closed form; Eq. 7 by
     brute force on tiny inputs; the Wannier round trip through Eq. 6; the gauge-free norm
     identity, periodicity and linearity.
-  * loss_and_grad, vjp: central differences (exact for a quadratic form), Euler's identity,
-    the dot-product identity <vjp(gbar), dg> = <gbar, g(dg)>.
+  * loss_weights, loss, loss_and_grad, vjp: L in closed form on the plane-wave inputs (1/omega,
+    the weight on the k-side band n, the omega_min cut); central differences (exact for a
+    quadratic form), Euler's identity, the dot-product identity <vjp(gbar), dg> = <gbar, g(dg)>.
   * linewidths: the closed form for one band, one mode and a constant coupling, and its
     symmetries.
   * g_bloch_to_wannier (Eq. 6): the round trip above.

@@ -23,6 +23,7 @@ PIN_FUNCS = [
     pins.test_vjp_is_the_adjoint_of_the_interpolation,
     pins.test_unstable_spring_chain_negative_frequency,
     pins.test_complex_hopping_and_diatomic_chain_closed_forms,
+    pins.test_loss_closed_form_on_plane_wave,
 ]
 
 _orig_phases = eo.phases
@@ -33,6 +34,7 @@ _orig_hk = eo.hamiltonian_k
 _orig_dq = eo.dynamical_matrix
 _orig_eig = eo.electron_eigen
 _orig_g1 = eo.g_rp_to_q
+_orig_loss_weights = eo.loss_weights
 
 
 def _phase_sign(pts, R, w=None):
@@ -134,6 +136,17 @@ def _interpolate_k_minus_q(a, kpts=None, qpts=None, return_eigvecs=False):
     return out + (dict(V_k=V_k, V_kq=np.stack(vkq), u=u),) if return_eigvecs else out
 
 
+def _loss_weights_omega_squared(omega, w_nk, omega_min):
+    c = _orig_loss_weights(omega, w_nk, omega_min)
+    return c / np.where(omega > omega_min, omega, 1.0)[:, None, :, None]
+
+
+def _loss_k_plus_q_band(g, omega, w_nk, omega_min):
+    # the weight w_nk applied on the band index of the k+q side (m) instead of the k side (n)
+    c = eo.loss_weights(omega, w_nk, omega_min)
+    return float(np.sum(c[:, :, :, :, None] * np.abs(g) ** 2))
+
+
 MUTATIONS = {
     "phase_sign": ("phases", _phase_sign),
     "phase_missing_2pi": ("phases", _phase_unreduced_wrong_scale),
@@ -154,6 +167,8 @@ MUTATIONS = {
     "eq9_without_weights": ("g_rp_to_q", _g1_no_weight),
     "band_indices_swapped": ("g_req_to_bloch", _g_req_bands_swapped),
     "k_minus_q": ("interpolate", _interpolate_k_minus_q),
+    "loss_over_omega_squared": ("loss_weights", _loss_weights_omega_squared),
+    "loss_weight_on_wrong_band": ("loss", _loss_k_plus_q_band),
 }
 
 

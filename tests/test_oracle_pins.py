@@ -308,6 +308,30 @@ def test_adjoint_central_differences_and_euler():
             assert abs(d - ref) <= 1e-6 * max(1.0, np.abs(grad).max())
 
 
+
+def test_loss_closed_form_on_plane_wave():
+    # on the plane-wave inputs |g_mn nu| and omega_nu are known in closed form and the same at
+    # every (k, q), so L = nq sum_k sum_n w_nk sum_nu (sum_m |g_mn nu|^2) / omega_nu, with the
+    # weight on the band index n of the k side and modes at or below omega_min left out; the
+    # oracle's L (and, by Euler's identity, its gradient) must give exactly this
+    a, Q, Gt, e0, p0, dvals, i0 = _plane_wave_inputs()
+    rng = np.random.default_rng(9)
+    k = rng.random((5, 3))
+    q = rng.random((4, 3))
+    nb = Q.shape[0]
+    w_nk = rng.uniform(0.0, 1.0, (len(k), nb))
+    m = np.repeat(a.masses, 3)
+    QGQ = np.einsum("am,vab,bn->vmn", Q.conj(), Gt, Q)
+    g2 = (a.we[e0] * a.wp[p0]) ** 2 * np.abs(QGQ) ** 2 / m[:, None, None]      # [nu][m][n]
+    om = np.sqrt(a.wp[i0] * dvals) * oracle.OMEGA_UNIT_EV     # [nu], ascending (unit pinned above)
+    for omega_min in (1e-6, 0.5 * (om[2] + om[3])):
+        keep = om > omega_min
+        per_n = (g2.sum(axis=1)[keep] / om[keep][:, None]).sum(axis=0)         # [n]
+        expect = len(q) * float((w_nk * per_n[None, :]).sum())
+        L, grad = oracle.loss_and_grad(a, k, q, w_nk, omega_min)
+        assert abs(L - expect) < 1e-12 * expect
+        assert abs(np.real(np.vdot(grad, a.g_ReRp)) - 2 * expect) < 1e-12 * expect
+
 def test_vjp_is_the_adjoint_of_the_interpolation():
     # g(k,q) is linear in g(Re,Rp) at fixed H, Phi (fixed gauges), so for any upstream gbar
     # and direction d: Re<vjp(gbar), d> = Re<gbar, A(d)>, A(d) = interpolation of d.
