@@ -48,9 +48,14 @@ enum eph_status {
 
 enum eph_form {
   EPH_FORM_FP64 = 0,  /* every contraction in FP64 (DFMA) */
-  EPH_FORM_MIXED = 1  /* Re->k contraction of g as split-precision tcgen05 tensor-core products with
-                         FP32 accumulation, g as complex64; phases, H(k)/H(k+q)/D(q), their
-                         eigensolves and the Rp->q contraction stay FP64 */
+  EPH_FORM_MIXED = 1  /* split precision on the large contractions, g as complex64: on k lists the
+                         Re->k contraction of g and H(k+q) are tcgen05 tensor-core products of
+                         fixed-point BF16 digits with FP32 accumulation; the band rotation runs in
+                         double-float FP32 (nb, nm <= 16) or on the tensor cores (larger shapes);
+                         the eigensolves stop at eigenvalues within ~1e-12 ||A|| and eigenvectors
+                         within ~1e-8.  Phases (exact FP64 reduction), D(q) and its eigensolve,
+                         the Rp->q contraction and, on uniform grids, the Re->k transforms stay
+                         FP64 */
 };
 
 typedef struct eph_options {
@@ -64,8 +69,10 @@ typedef struct eph_options {
   int mixed_scheme;  /* mixed form only: 0 = fixed-point BF16 digits (3 for the phases, 4 for g)
                         with exact FP32 tensor-core accumulation (default; needs 2*ne <= 1024),
                         1 = two-term split TF32 (3 products) */
-  int eig_plain_fp64; /* 0 (default): Jacobi sweeps preconditioned in FP32, then FP64 sweeps to
-                         full FP64 accuracy; 1: FP64 sweeps only */
+  int eig_plain_fp64; /* 0 (default): FP32 Jacobi sweeps, then FP64 refinement to full FP64
+                         accuracy (Ogita-Aishima steps for n <= 12; plain FP64 sweeps for n = 13..16;
+                         Newton-Schulz, A' = V^H A V and FP64 polish sweeps for n > 16);
+                         1: plain FP64 Jacobi sweeps only */
   int async;          /* 1: eph_interp_q only enqueues work (no host synchronisation, no event
                          timing); its status is read by eph_sync.  With device pointers a sequence
                          of calls can be captured into one CUDA graph.  With host pointers (FP64
