@@ -103,8 +103,10 @@ void eph_default_options(eph_options* opt);
  * All inputs are HOST pointers; they are copied and may be freed on return.
  * Supported sizes: 1 <= nb, nm <= 16 (warp-resident Jacobi and rotations) and up to
  * 256 (one CTA per eigensolve, GEMM rotations; forward only), in both forms (beyond 16
- * the mixed form keeps the FP64 contraction and eigensolves and runs the band rotation
- * as double-float GEMMs); larger sizes return EPH_ENOTSUP.
+ * the FP64 form rotates with batched FP64 GEMMs; the mixed form runs the Re->k contraction,
+ * H(k+q) and the band rotation on the tensor cores, the mode rotation and the eigensolves'
+ * products in double-float); larger sizes return EPH_ENOTSUP.  The mixed form's digit
+ * scheme (mixed_scheme 0) needs 2*ne <= 1024 (EPH_ENOTSUP otherwise).
  * On success *out owns device memory until eph_destroy.
  */
 int eph_create(eph_ctx** out, int nb, int na, int ne, int np,
@@ -129,8 +131,9 @@ int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k);
  * the bounding box of the Re list (B_a terms per output instead of ne): the same sum,
  * term for term, to rounding.  Used when nb, nm <= 16, the Re vectors are distinct and
  * their box has extents <= 32 and volume <= 8 ne; otherwise the general path runs on the
- * generated k list.  In the mixed form the contraction is then FP64 as well and only the
- * band rotation runs in double-float arithmetic on the FP32 pipe (g complex64).
+ * generated k list.  In the mixed form the transforms are FP64 as well; the band rotation
+ * runs in double-float arithmetic on the FP32 pipe and the eigensolves stop at the mixed
+ * form's accuracy (g complex64).
  *   shift [3] HOST pointer (NULL = 0); eps_k [nk][nb] as in eph_set_k (may be NULL).
  * EPH_EINVAL for n_a < 1 or nk > 2^31 - 1.
  */
