@@ -448,7 +448,7 @@ def run_libeph(args):
     import torch
 
     from paper_2603_10295_gb300 import binding, synth
-    from paper_2603_10295_gb300.sharding import q_shard
+    from paper_2603_10295_gb300.sharding import step_q_indices
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -461,8 +461,7 @@ def run_libeph(args):
     QB = args.q_batch
     # this rank's q points: a contiguous block of the (cyclically extended) q list
     nsteps = args.warmup + args.steps
-    a, _ = q_shard(world * nsteps * QB, rank, world)
-    qidx = (np.arange(nsteps * QB) + a) % len(wl.qpts)
+    qidx = step_q_indices(len(wl.qpts), nsteps, QB, rank, world)
     q_dev = torch.from_numpy(np.ascontiguousarray(wl.qpts[qidx])).to(dev)
     k_dev = torch.from_numpy(wl.kpts).to(dev)
 

@@ -17,6 +17,19 @@ def q_shard(nq: int, rank: int, world: int) -> tuple[int, int]:
     return start, start + base + (1 if rank < extra else 0)
 
 
+def step_q_indices(nq: int, nsteps: int, q_batch: int, rank: int, world: int):
+    """Indices into a list of nq q points for this rank's nsteps batches of q_batch points.
+
+    The ranks take consecutive blocks of the list extended cyclically, so that every rank has
+    the same amount of work (weak scaling) and, while world * nsteps * q_batch <= nq, no q
+    point is processed twice."""
+    import numpy as np
+    if nq < 1 or nsteps < 0 or q_batch < 1:
+        raise ValueError("bad step request")
+    start, _ = q_shard(world * nsteps * q_batch, rank, world)
+    return (np.arange(nsteps * q_batch) + start) % nq
+
+
 def allreduce_loss_and_grad(L, grad, group=None):
     """Sums a rank-local scalar L and gradient tensor over all ranks (in place for grad)."""
     import torch

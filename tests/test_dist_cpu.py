@@ -8,7 +8,7 @@ import socket
 import numpy as np
 import pytest
 
-from paper_2603_10295_gb300.sharding import q_shard
+from paper_2603_10295_gb300.sharding import q_shard, step_q_indices
 
 
 @pytest.mark.parametrize("nq,world", [(1, 1), (7, 2), (256, 3), (5, 8), (0, 2)])
@@ -21,6 +21,19 @@ def test_q_shard_partitions(nq, world):
     assert seen == list(range(nq))
     sizes = [q_shard(nq, r, world)[1] - q_shard(nq, r, world)[0] for r in range(world)]
     assert max(sizes) - min(sizes) <= 1
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
+def test_bench_step_indices_disjoint_equal_work(world):
+    # the bench's per-rank q points: equal counts, and disjoint while the list is long enough
+    nq, nsteps, qb = 1000, 13, 4
+    blocks = [step_q_indices(nq, nsteps, qb, r, world) for r in range(world)]
+    assert all(len(b) == nsteps * qb for b in blocks)
+    allq = np.concatenate(blocks)
+    assert np.array_equal(np.sort(allq), np.arange(world * nsteps * qb))
+    # a longer run wraps around the list; every rank still gets nsteps * qb valid indices
+    wrap = [step_q_indices(7, nsteps, qb, r, world) for r in range(world)]
+    assert all(len(b) == nsteps * qb and b.min() >= 0 and b.max() < 7 for b in wrap)
 
 
 def _free_port():
