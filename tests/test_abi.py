@@ -92,3 +92,33 @@ def test_binding_rejects_misshaped_host_arrays():
         ctx.linewidths(np.zeros((2, 3)), wq=np.ones(3))
     with pytest.raises(ValueError):
         ctx.eigh(np.zeros((2, 3, 4)))
+
+
+def test_every_entry_point_rejects_a_null_context_without_gpu(lib):
+    # a NULL context (and, for the context-free entry point, a bad size) is an argument error
+    # reported before any CUDA call: these run on a host without a GPU
+    E = binding.EPH_EINVAL
+    i = ctypes.c_int()
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    assert lib.eph_set_k_grid(None, 2, 2, 2, None, None) == E
+    assert lib.eph_set_k_window(None, 1, None, 0.0, 1.0, None, None, ctypes.byref(i)) == E
+    assert lib.eph_interp(None, 1, None, 1, None, None, None, None, None) == E
+    assert lib.eph_interp_q_window(None, 1, None, 0.0, 1.0, None, None, None, None) == E
+    assert lib.eph_interp_backward(None, 1, None, 1, None, None, 0.0, None, None) == E
+    assert lib.eph_interp_vjp(None, 1, None, 1, None, None, None) == E
+    assert lib.eph_bloch_to_wannier(None, 1, None, 1, None, None, None) == E
+    assert lib.eph_linewidths(None, 1, None, None, 0.025, 0.0, 0.1, 1e-6, None) == E
+    assert lib.eph_eigh(None, 4, 1, None, None, None) == E
+    assert lib.eph_reserve(None, 4) == E
+    assert lib.eph_sync(None) == E
+    assert lib.eph_autotune(None, 4, None, ctypes.byref(i), ctypes.byref(i)) == E
+    assert lib.eph_profile(None, 1) == E
+    assert lib.eph_profile_read(None, 0, ctypes.byref(ms), ctypes.byref(n)) == E
+    assert lib.eph_profile_reset(None) == E
+    assert lib.eph_kernel_launches(None) == 0
+    # the allocation-free entry point: sizes beyond its fixed scratch, nb > 16, NULL pointers
+    dummy = ctypes.c_void_p(16)   # never dereferenced: every call below fails its checks first
+    assert lib.eph_bands_noalloc(0, dummy, 4, 8, dummy, None, dummy, dummy, dummy, 0, None) == E
+    assert lib.eph_bands_noalloc(10, dummy, 17, 8, dummy, None, dummy, dummy, dummy, 0, None) == E
+    assert lib.eph_bands_noalloc(100000, dummy, 8, 216, dummy, None, dummy, dummy, dummy, 0, None) == E
+    assert lib.eph_bands_noalloc(10, None, 4, 8, dummy, None, dummy, dummy, dummy, 0, None) == E
