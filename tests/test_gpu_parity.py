@@ -223,3 +223,18 @@ def test_phase_reduction_grid_shift_far_from_the_cell():
     ref = oracle.interpolate(wl, k, wl.qpts)
     check(near, ref, TOL_FP64, "grid, in-cell shift")
     check(shifted, ref, TOL_FP64, "grid, far shift")
+
+
+def test_empty_inputs_rejected_and_context_kept():
+    # empty k, q and matrix batches are argument errors; the resident k list survives them
+    wl = synth.make_workload("si_tiny", nk=4, nq=2)
+    ctx = binding.Context.from_workload(wl)
+    ref = ctx.interp(wl.kpts, wl.qpts)
+    for call in (lambda: ctx.set_k(np.zeros((0, 3))), lambda: ctx.interp_q(np.zeros((0, 3))),
+                 lambda: ctx.eigh(np.zeros((0, 4, 4), dtype=np.complex128))):
+        with pytest.raises(binding.EphError) as ei:
+            call()
+        assert ei.value.code == binding.EPH_EINVAL
+    again = ctx.interp_q(wl.qpts)
+    for a, b in zip(ref[1:], again):
+        assert np.array_equal(a, b)
