@@ -24,6 +24,7 @@ PIN_FUNCS = [
     pins.test_unstable_spring_chain_negative_frequency,
     pins.test_complex_hopping_and_diatomic_chain_closed_forms,
     pins.test_loss_closed_form_on_plane_wave,
+    pins.test_linewidths_closed_form_and_properties,
 ]
 
 _orig_phases = eo.phases
@@ -35,6 +36,8 @@ _orig_dq = eo.dynamical_matrix
 _orig_eig = eo.electron_eigen
 _orig_g1 = eo.g_rp_to_q
 _orig_loss_weights = eo.loss_weights
+_orig_b2w = eo.g_bloch_to_wannier
+_orig_linewidths = eo.linewidths
 
 
 def _phase_sign(pts, R, w=None):
@@ -147,6 +150,29 @@ def _loss_k_plus_q_band(g, omega, w_nk, omega_min):
     return float(np.sum(c[:, :, :, :, None] * np.abs(g) ** 2))
 
 
+def _eq6_unnormalised(kc, qc, Re, Rp, g_bloch, V_k, V_kq, u_q):
+    # Eq. 6 without its 1/(Ne Np)
+    return _orig_b2w(kc, qc, Re, Rp, g_bloch, V_k, V_kq, u_q) * (len(Re) * len(Rp))
+
+
+def _eq6_forward_phases(kc, qc, Re, Rp, g_bloch, V_k, V_kq, u_q):
+    # e^{+i(k'.Re + q'.Rp)} in the back transform: the same grid read as -k', -q'
+    return _orig_b2w(-np.asarray(kc), -np.asarray(qc), Re, Rp, g_bloch, V_k, V_kq, u_q)
+
+
+def _swap_terms(eps_k, eps_kq, omega, g, wq, kT, mu, sigma, omega_min):
+    # phonon absorption weighted at the emission energy and vice versa
+    om = np.asarray(omega)[:, None, :, None, None]
+    ok = om > omega_min
+    w = np.where(ok, om, 1.0)
+    nB = eo.bose(w, kT)
+    f = eo.fermi(np.asarray(eps_kq)[:, :, None, :, None], mu, kT)
+    de = np.asarray(eps_k)[None, :, None, None, :] - np.asarray(eps_kq)[:, :, None, :, None]
+    term = (nB + f) * eo.gaussian(de - w, sigma) + (nB + 1.0 - f) * eo.gaussian(de + w, sigma)
+    c = np.where(ok, np.pi * np.abs(g) ** 2 / (2.0 * w), 0.0) * term
+    return np.einsum("q,qkvmn->kn", np.ones(len(omega)) if wq is None else np.asarray(wq), c)
+
+
 MUTATIONS = {
     "phase_sign": ("phases", _phase_sign),
     "phase_missing_2pi": ("phases", _phase_unreduced_wrong_scale),
@@ -169,6 +195,9 @@ MUTATIONS = {
     "k_minus_q": ("interpolate", _interpolate_k_minus_q),
     "loss_over_omega_squared": ("loss_weights", _loss_weights_omega_squared),
     "loss_weight_on_wrong_band": ("loss", _loss_k_plus_q_band),
+    "eq6_without_normalisation": ("g_bloch_to_wannier", _eq6_unnormalised),
+    "eq6_forward_phases": ("g_bloch_to_wannier", _eq6_forward_phases),
+    "linewidth_terms_swapped": ("linewidths", _swap_terms),
 }
 
 
