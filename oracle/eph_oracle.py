@@ -40,8 +40,11 @@ function below and checks that a pin fails):
   * loss_weights, loss, loss_and_grad, vjp: L in closed form on the plane-wave inputs (1/omega,
     the weight on the k-side band n, the omega_min cut); central differences (exact for a
     quadratic form), Euler's identity, the dot-product identity <vjp(gbar), dg> = <gbar, g(dg)>.
-  * linewidths: the closed form for one band, one mode and a constant coupling, and its
-    symmetries.
+  * linewidths (with bose, fermi, gaussian): the sigma -> 0 limit on two tight-binding chain
+    bands with degenerate Einstein modes and a constant coupling, against the analytic chain
+    density of states; detailed balance at eps = mu (both weights equal csch(omega/kT)); the
+    zero-temperature limit (emission only above mu, absorption only below); the omega_min cut,
+    positivity and linearity in the q weights.
   * g_bloch_to_wannier (Eq. 6): the round trip above.
 """
 from __future__ import annotations

@@ -24,7 +24,10 @@ PIN_FUNCS = [
     pins.test_unstable_spring_chain_negative_frequency,
     pins.test_complex_hopping_and_diatomic_chain_closed_forms,
     pins.test_loss_closed_form_on_plane_wave,
-    pins.test_linewidths_closed_form_and_properties,
+    pins.test_linewidths_sigma_to_zero_limit_on_chain_bands,
+    pins.test_linewidths_detailed_balance_at_the_chemical_potential,
+    pins.test_linewidths_zero_temperature_limit,
+    pins.test_linewidths_properties,
 ]
 
 _orig_phases = eo.phases
@@ -173,6 +176,31 @@ def _swap_terms(eps_k, eps_kq, omega, g, wq, kT, mu, sigma, omega_min):
     return np.einsum("q,qkvmn->kn", np.ones(len(omega)) if wq is None else np.asarray(wq), c)
 
 
+def _lw_no_half_omega(eps_k, eps_kq, omega, g, wq, kT, mu, sigma, omega_min):
+    # drops the 1/(2 omega) of the coupling's zero-point amplitude (|g|^2 scaled by 2 omega
+    # cancels it)
+    scale = np.sqrt(2.0 * np.abs(np.asarray(omega)))[:, None, :, None, None]
+    return _orig_linewidths(eps_k, eps_kq, omega, g * scale, wq, kT, mu, sigma, omega_min)
+
+
+def _lw_g_transposed(eps_k, eps_kq, omega, g, wq, kT, mu, sigma, omega_min):
+    # |g_nm| in place of |g_mn| (the k-side and k+q-side band indices exchanged)
+    return _orig_linewidths(eps_k, eps_kq, omega, np.swapaxes(g, -1, -2), wq, kT, mu, sigma, omega_min)
+
+
+def _lw_fermi_at_k(eps_k, eps_kq, omega, g, wq, kT, mu, sigma, omega_min):
+    # occupation of the initial state n,k in place of the final state m,k+q
+    om = np.asarray(omega)[:, None, :, None, None]
+    ok = om > omega_min
+    w = np.where(ok, om, 1.0)
+    nB = eo.bose(w, kT)
+    f = eo.fermi(np.asarray(eps_k)[None, :, None, None, :], mu, kT)
+    de = np.asarray(eps_k)[None, :, None, None, :] - np.asarray(eps_kq)[:, :, None, :, None]
+    term = (nB + f) * eo.gaussian(de + w, sigma) + (nB + 1.0 - f) * eo.gaussian(de - w, sigma)
+    c = np.where(ok, np.pi * np.abs(g) ** 2 / (2.0 * w), 0.0) * term
+    return np.einsum("q,qkvmn->kn", np.asarray(wq, dtype=np.float64), c)
+
+
 MUTATIONS = {
     "phase_sign": ("phases", _phase_sign),
     "phase_missing_2pi": ("phases", _phase_unreduced_wrong_scale),
@@ -198,6 +226,9 @@ MUTATIONS = {
     "eq6_without_normalisation": ("g_bloch_to_wannier", _eq6_unnormalised),
     "eq6_forward_phases": ("g_bloch_to_wannier", _eq6_forward_phases),
     "linewidth_terms_swapped": ("linewidths", _swap_terms),
+    "linewidth_without_1_over_2omega": ("linewidths", _lw_no_half_omega),
+    "linewidth_coupling_band_indices_swapped": ("linewidths", _lw_g_transposed),
+    "linewidth_occupation_at_k": ("linewidths", _lw_fermi_at_k),
 }
 
 

@@ -372,22 +372,98 @@ def test_table3_sizes_and_cost_ratio():
 
 
 # ---------------------------------------------------------------- linewidth consumer
-def test_linewidths_closed_form_and_properties():
-    # one band, one mode, constant coupling: Gamma is pi |g|^2/(2w) times the two
-    # Gaussian-weighted occupation terms, written out by hand here
-    kT, mu, sig, w, g0 = 0.025852, 0.1, 0.02, 0.05, 0.3 + 0.4j
+# Two one-band chains eps_m(k) = e0_m + 2 t_m cos(2 pi k) (textbook tight-binding bands) and
+# three degenerate Einstein modes omega0 (one atom, on-site springs only: D(q) = K/M for every
+# q), with a coupling that does not depend on k or q: g_mn,nu = G_mn e_{x,nu}(q)/sqrt(M), e a
+# random unitary basis of the degenerate mode space at every q (sum_nu |e_{x,nu}|^2 = 1).  On a
+# uniform q grid with w_q = 1/Nq, sum_q w_q delta(E - eps_m(k+q)) tends to the chain density of
+# states rho_m(E) = 1/(pi sqrt(4 t_m^2 - (E - e0_m)^2)) as sigma -> 0, so the Fan-Migdal
+# linewidth has the closed form
+#   Gamma_nk = pi/(2 omega0 M) sum_m |G_mn|^2 [ (n_B + f(E+)) rho_m(E+) + (n_B + 1 - f(E-)) rho_m(E-) ],
+# E+- = eps_nk +- omega0 (absorption lands at E+, emission at E-).  The Gaussian delta converges
+# as sigma^2 (Gamma(sigma) = Gamma_0 + c sigma^2 + O(sigma^4)), so two widths and one Richardson
+# step reach the limit to ~1e-6.
+_LW_BANDS = ((0.0, 0.5), (0.3, -0.4))
+_LW_G = np.array([[0.3 + 0.2j, -0.5 + 0.1j], [0.7j, 0.25]])
+_LW_W0, _LW_M = 0.06, 20.0
+
+
+def _chain_dos(E, e0, t):
+    return 1.0 / (np.pi * np.sqrt(4.0 * t * t - (E - e0) ** 2))
+
+
+def _einstein_chain_linewidths(kx, kT, mu, sigmas, nq=20000, seed=5):
+    rng = np.random.default_rng(seed)
+    q = np.arange(nq) / nq
+    eps_k = np.stack([e0 + 2 * t * np.cos(2 * np.pi * kx) for e0, t in _LW_BANDS], -1)
+    eps_kq = np.stack([e0 + 2 * t * np.cos(2 * np.pi * (kx[None, :] + q[:, None])) for e0, t in _LW_BANDS], -1)
+    omega = np.full((nq, 3), _LW_W0)
+    e, _ = np.linalg.qr(rng.standard_normal((nq, 3, 3)) + 1j * rng.standard_normal((nq, 3, 3)))
+    g = _LW_G[None, None, None] * (e[:, 0, :] / np.sqrt(_LW_M))[:, None, :, None, None]
+    g = np.broadcast_to(g, (nq, len(kx), 3, 2, 2)).copy()
+    wq = np.full(nq, 1.0 / nq)
+    return eps_k, [oracle.linewidths(eps_k, eps_kq, omega, g, wq, kT, mu, s, 1e-6) for s in sigmas]
+
+
+def test_linewidths_sigma_to_zero_limit_on_chain_bands():
+    kx = np.array([0.13, 0.23, 0.29])
+    kT, mu = 0.025852, 0.1
+    eps_k, (g1, g2) = _einstein_chain_linewidths(kx, kT, mu, (0.004, 0.002))
+    gamma0 = (4.0 * g2 - g1) / 3.0  # Richardson: removes the sigma^2 term
+    nB = 1.0 / (math.exp(_LW_W0 / kT) - 1.0)
+    occ = lambda E: 1.0 / (np.exp((E - mu) / kT) + 1.0)
+    expect = np.zeros_like(gamma0)
+    for n in range(2):
+        Ep, Em = eps_k[:, n] + _LW_W0, eps_k[:, n] - _LW_W0
+        for m, (e0, t) in enumerate(_LW_BANDS):
+            expect[:, n] += np.pi * abs(_LW_G[m, n]) ** 2 / (2 * _LW_W0 * _LW_M) * (
+                (nB + occ(Ep)) * _chain_dos(Ep, e0, t) + (nB + 1.0 - occ(Em)) * _chain_dos(Em, e0, t))
+    assert np.abs(gamma0 / expect - 1.0).max() < 2e-5
+
+
+def test_linewidths_detailed_balance_at_the_chemical_potential():
+    # For eps_nk = mu the absorption weight n_B + f(mu + w) and the emission weight
+    # n_B + 1 - f(mu - w) are both 1/(e^x - 1) + 1/(e^x + 1) = 1/sinh(x), x = w/kT, so
+    # Gamma = pi/(2 w M) csch(w/kT) sum_m |G_mn|^2 [rho_m(mu + w) + rho_m(mu - w)].
+    kx = np.array([0.23])
+    kT = 0.025852
+    mu = _LW_BANDS[0][0] + 2 * _LW_BANDS[0][1] * math.cos(2 * math.pi * 0.23)  # eps of band 0 at k = 0.23
+    eps_k, (g1, g2) = _einstein_chain_linewidths(kx, kT, mu, (0.004, 0.002))
+    assert abs(eps_k[0, 0] - mu) < 1e-15
+    gamma0 = (4.0 * g2 - g1) / 3.0
+    expect = sum(np.pi * abs(_LW_G[m, 0]) ** 2 / (2 * _LW_W0 * _LW_M) / math.sinh(_LW_W0 / kT)
+                 * (_chain_dos(mu + _LW_W0, e0, t) + _chain_dos(mu - _LW_W0, e0, t))
+                 for m, (e0, t) in enumerate(_LW_BANDS))
+    assert abs(gamma0[0, 0] / expect - 1.0) < 2e-5
+
+
+def test_linewidths_zero_temperature_limit():
+    # kT -> 0: no thermal phonons (n_B -> 0) and step occupations.  An electron above mu + w
+    # can only emit (Gamma ~ rho(eps - w)); a hole below mu - w is filled only through the
+    # absorption term, whose final states at eps + w are occupied (Gamma ~ rho(eps + w)).
+    kx = np.array([0.13, 0.23, 0.29])
+    kT, mu = 0.003, 0.0
+    eps_k, (g1, g2) = _einstein_chain_linewidths(kx, kT, mu, (0.004, 0.002))
+    gamma0 = (4.0 * g2 - g1) / 3.0
+    expect = np.zeros_like(gamma0)
+    for i in range(len(kx)):
+        for n in range(2):
+            e = eps_k[i, n]
+            assert abs(e - mu) > _LW_W0 + 20 * kT  # occupations are 0 or 1 to e^-20
+            E = e - _LW_W0 if e > mu else e + _LW_W0
+            expect[i, n] = sum(np.pi * abs(_LW_G[m, n]) ** 2 / (2 * _LW_W0 * _LW_M) * _chain_dos(E, e0, t)
+                               for m, (e0, t) in enumerate(_LW_BANDS))
+    assert np.abs(gamma0 / expect - 1.0).max() < 2e-5
+
+
+def test_linewidths_properties():
+    # modes at or below omega_min contribute nothing; Gamma >= 0 and linear in the q weights
+    kT = 0.025852
     eps_k = np.array([[0.17]])
     eps_kq = np.array([[[0.13]]])
-    omega = np.array([[w]])
-    g = np.full((1, 1, 1, 1, 1), g0)
-    nB = 1.0 / (np.exp(w / kT) - 1.0)
-    f = 1.0 / (np.exp((0.13 - mu) / kT) + 1.0)
-    gau = lambda x: np.exp(-x * x / (2 * sig * sig)) / (sig * np.sqrt(2 * np.pi))
-    expect = np.pi * abs(g0) ** 2 / (2 * w) * ((nB + f) * gau(0.04 + w) + (nB + 1 - f) * gau(0.04 - w))
-    got = oracle.linewidths(eps_k, eps_kq, omega, g, [1.0], kT, mu, sig, 1e-6)
-    assert abs(got[0, 0] - expect) < 1e-14 * expect
-    # modes below omega_min contribute nothing; Gamma >= 0 and linear in the q weights
-    assert oracle.linewidths(eps_k, eps_kq, omega, g, [1.0], kT, mu, sig, 0.06)[0, 0] == 0.0
+    g = np.full((1, 1, 1, 1, 1), 0.3 + 0.4j)
+    assert oracle.linewidths(eps_k, eps_kq, np.array([[0.05]]), g, [1.0], kT, 0.1, 0.02, 0.06)[0, 0] == 0.0
+    assert oracle.linewidths(eps_k, eps_kq, np.array([[0.05]]), g, [1.0], kT, 0.1, 0.02, 0.04)[0, 0] > 0.0
     wl = synth.make_workload("si_tiny", nk=5, nq=3)
     ek, ekq, om, gg = oracle.interpolate(wl)
     G1 = oracle.linewidths(ek, ekq, om, gg, [1.0, 2.0, 0.5], kT, 0.0, 0.1, 1e-6)
