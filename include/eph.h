@@ -151,6 +151,43 @@ int eph_set_k_grid(eph_ctx* ctx, int n1, int n2, int n3, const double* shift, do
  */
 int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g);
 
+/*
+ * Rp-partitioned g(Re,Rp) (the paper's "Workload distribution": pools split the Rp vectors of
+ * g(Re,Rp) and sum the partial Eq. 9 results over the pool before the k stage).  For a
+ * g(Re,Rp) larger than one GPU's memory (Table 3's widest ribbons: 353-458 GiB), each GPU holds
+ * the slice Rp[rp_begin .. rp_begin + rp_count - 1]:
+ *
+ *   eph_create_rp_slice  as eph_create, but g_ReRp_slice is [rp_count][nm][ne][nb][nb]
+ *                        complex128, the rows of g(Re,Rp) for that Rp range.  Phi_Rp, Rp and wp
+ *                        still cover all np vectors (D(q) needs every force constant).
+ *                        EPH_EINVAL unless 0 <= rp_begin, 1 <= rp_count, rp_begin + rp_count <= np.
+ *   eph_g1_partial       G1 [nq][nm][ne][nb][nb] complex128 = sum over the slice's Rp of
+ *                        w_p e^{i q.Rp} g(Re,Rp) (Eq. 9 restricted to the slice); the sum of
+ *                        the partials of all slices (an allreduce across the GPUs) is Eq. 9.
+ *   eph_interp_q_g1      eph_interp_q with G1 [nq][nm][ne][nb][nb] complex128 supplied by the
+ *                        caller (the summed partials) in place of Eq. 9: outputs as eph_interp_q.
+ *                        Works on any context (also a whole one).
+ * qpts, G1 and the outputs are host or device pointers per device_ptrs.  On an Rp-slice context
+ * (rp_count < np) eph_interp_q, eph_interp_q_window, eph_interp_backward and eph_linewidths,
+ * which would need the whole Eq. 9, return EPH_ESTATE; eph_interp_vjp and eph_bloch_to_wannier
+ * do not read g(Re,Rp) and return the whole [np] result.
+ */
+int eph_create_rp_slice(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re, const double* Phi_Rp,
+                        const double* g_ReRp_slice, const int* Re, const double* we, const int* Rp, const double* wp,
+                        const double* masses, int rp_begin, int rp_count, const eph_options* opt, void* cuda_stream);
+int eph_g1_partial(eph_ctx* ctx, int nq, const double* qpts, double* G1);
+int eph_interp_q_g1(eph_ctx* ctx, int nq, const double* qpts, const double* G1, double* eps_kq, double* omega,
+                    void* g);
+
+/*
+ * Replaces the resident g(Re,Rp) (or the context's Rp slice of it) by g_ReRp, same layout as at
+ * creation ([nrp][nm][ne][nb][nb] complex128), host or device pointer per device_ptrs; the
+ * Hamiltonians, force constants and the resident k list are kept.  A device-to-device copy in
+ * device mode: this is how a training loop feeds an updated g(Re,Rp) tensor back to the same
+ * context without a host round trip.
+ */
+int eph_set_gw(eph_ctx* ctx, const double* g_ReRp);
+
 /* eph_set_k followed by eph_interp_q. */
 int eph_interp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
                double* eps_k, double* eps_kq, double* omega, void* g);
@@ -335,9 +372,12 @@ int eph_eigh(eph_ctx* ctx, int n, int batch, const void* A, double* w, void* V);
  * Limits: 1 <= nb <= 16 and scratch = round_up(16*nk*ne, 256) + 16*nk*nb*nb
  * bytes <= EPH_NOALLOC_SCRATCH_BYTES, else EPH_EINVAL before any GPU work.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, once per device, with that device current); make
+ * (cudaGetSymbolAddress, once per device, with that device current; again
+ * if the current CUDA context changed, e.g. after cudaDeviceReset); make
  * that first call before any stream capture.  The call synchronises the
- * stream to report the eigensolver status (EPH_ENOTCONV at the sweep cap).
+ * stream to report the eigensolver status (EPH_ENOTCONV at the sweep cap):
+ * it blocks the calling host thread until all work queued on that stream,
+ * including work queued before the call, has finished.
  * All calls share the one array and it keeps the last call's contents: calls
  * that overlap on the GPU (other streams or host threads on the same device)
  * race and must be serialised by the caller.

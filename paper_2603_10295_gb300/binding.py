@@ -24,7 +24,8 @@ EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "ep
            "eph_interp_backward", "eph_destroy", "eph_strerror", "eph_last_error", "eph_kernel_launches",
            "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc",
            "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths", "eph_interp_vjp",
-           "eph_set_k_grid", "eph_bloch_to_wannier", "eph_set_k_window", "eph_interp_q_window", "eph_eigh")
+           "eph_set_k_grid", "eph_bloch_to_wannier", "eph_set_k_window", "eph_interp_q_window", "eph_eigh",
+           "eph_create_rp_slice", "eph_g1_partial", "eph_interp_q_g1", "eph_set_gw")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -103,6 +104,15 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_interp_q_window.restype = i
     lib.eph_eigh.argtypes = [vp, i, i, vp, dp, vp]
     lib.eph_eigh.restype = i
+    lib.eph_create_rp_slice.argtypes = [ctypes.POINTER(vp), i, i, i, i, dp, dp, dp, vp, dp, vp, dp, dp, i, i,
+                                        ctypes.POINTER(EphOptions), vp]
+    lib.eph_create_rp_slice.restype = i
+    lib.eph_g1_partial.argtypes = [vp, i, dp, dp]
+    lib.eph_g1_partial.restype = i
+    lib.eph_interp_q_g1.argtypes = [vp, i, dp, dp, dp, dp, vp]
+    lib.eph_interp_q_g1.restype = i
+    lib.eph_set_gw.argtypes = [vp, dp]
+    lib.eph_set_gw.restype = i
     del ip
     if path is None:
         _lib = lib
@@ -150,7 +160,8 @@ class Context:
 
     def __init__(self, nb, na, H_Re, Phi_Rp, g_ReRp, Re, Rp, masses, we=None, wp=None, form="fp64",
                  device_ptrs=False, q_batch=0, k_tile=0, max_sweeps=0, workspace_mb=0, stream=None,
-                 mixed_scheme="digits", eig_plain_fp64=False, async_mode=False):
+                 mixed_scheme="digits", eig_plain_fp64=False, async_mode=False, rp_slice=None):
+        """rp_slice = (rp_begin, rp_count): g_ReRp holds only those Rp rows (eph_create_rp_slice)."""
         self.lib = load_library()
         self.nb, self.na, self.nm = int(nb), int(na), 3 * int(na)
         H_Re = np.ascontiguousarray(H_Re, dtype=np.complex128)
@@ -177,9 +188,17 @@ class Context:
         st = None
         if stream is not None:
             st = stream if isinstance(stream, int) else int(stream.cuda_stream)
-        rc = self.lib.eph_create(ctypes.byref(handle), self.nb, self.na, self.ne, self.np_, _ptr(H_Re),
-                                 _ptr(Phi_Rp), _ptr(g_ReRp), _ptr(Re), _ptr(we), _ptr(Rp), _ptr(wp), _ptr(masses),
-                                 ctypes.byref(opt), st)
+        self.rp_slice = (0, self.np_) if rp_slice is None else (int(rp_slice[0]), int(rp_slice[1]))
+        if rp_slice is None:
+            rc = self.lib.eph_create(ctypes.byref(handle), self.nb, self.na, self.ne, self.np_, _ptr(H_Re),
+                                     _ptr(Phi_Rp), _ptr(g_ReRp), _ptr(Re), _ptr(we), _ptr(Rp), _ptr(wp), _ptr(masses),
+                                     ctypes.byref(opt), st)
+        else:
+            if g_ReRp.shape[0] != self.rp_slice[1]:
+                raise ValueError(f"g_ReRp holds {g_ReRp.shape[0]} Rp rows, the slice {self.rp_slice[1]}")
+            rc = self.lib.eph_create_rp_slice(ctypes.byref(handle), self.nb, self.na, self.ne, self.np_, _ptr(H_Re),
+                                              _ptr(Phi_Rp), _ptr(g_ReRp), _ptr(Re), _ptr(we), _ptr(Rp), _ptr(wp),
+                                              _ptr(masses), self.rp_slice[0], self.rp_slice[1], ctypes.byref(opt), st)
         if rc != EPH_OK:
             raise EphError(rc, self.lib.eph_strerror(rc).decode())
         self.handle = handle
@@ -235,6 +254,37 @@ class Context:
 
     def eph_interp_q(self, nq, qpts, eps_kq=None, omega=None, g=None):
         self._check(self.lib.eph_interp_q(self.handle, int(nq), _ptr(qpts), _ptr(eps_kq), _ptr(omega), _ptr(g)))
+
+    def eph_g1_partial(self, nq, qpts, G1):
+        self._check(self.lib.eph_g1_partial(self.handle, int(nq), _ptr(qpts), _ptr(G1)))
+
+    def eph_interp_q_g1(self, nq, qpts, G1, eps_kq=None, omega=None, g=None):
+        self._check(self.lib.eph_interp_q_g1(self.handle, int(nq), _ptr(qpts), _ptr(G1), _ptr(eps_kq), _ptr(omega),
+                                             _ptr(g)))
+
+    def eph_set_gw(self, g_ReRp):
+        self._check(self.lib.eph_set_gw(self.handle, _ptr(g_ReRp)))
+
+    def g1_partial(self, qpts):
+        """Eq. 9 over this context's Rp slice: G1 [nq][nm][ne][nb][nb] (host mode)."""
+        qpts = _points(qpts, "qpts")
+        G1 = np.empty((len(qpts), self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
+        self.eph_g1_partial(len(qpts), qpts, G1)
+        return G1
+
+    def interp_q_g1(self, qpts, G1, want_g=True):
+        """eph_interp_q with a given G1 (host mode): (eps_kq, omega, g)."""
+        qpts = _points(qpts, "qpts")
+        nq = len(qpts)
+        G1 = _shaped(G1, (nq, self.nm, self.ne, self.nb, self.nb), np.complex128, "G1")
+        eps_kq = np.empty((nq, self.nk, self.nb))
+        omega = np.empty((nq, self.nm))
+        g = None
+        if want_g:
+            dt = np.complex128 if self.form == "fp64" else np.complex64
+            g = np.empty((nq, self.nk, self.nm, self.nb, self.nb), dtype=dt)
+        self.eph_interp_q_g1(nq, qpts, G1, eps_kq, omega, g)
+        return eps_kq, omega, g
 
     def eph_reserve(self, nq):
         self._check(self.lib.eph_reserve(self.handle, int(nq)))

@@ -67,7 +67,11 @@ struct eph_ctx {
   double* Phi = nullptr;       // [np][nm*nm]
   double* dscale = nullptr;    // [nm*nm]  1/sqrt(M_k M_k')
   double* invsqrtm = nullptr;  // [nm]
-  double2* gW = nullptr;       // [np][nm*ne*nb*nb]
+  double2* gW = nullptr;       // [nrp][nm*ne*nb*nb]: the Rp vectors rp0 .. rp0 + nrp - 1
+  int rp0 = 0, nrp = 0;        // Rp slice of g(Re,Rp) held here (the whole list unless created
+                               // by eph_create_rp_slice); Phi(Rp) always covers all np vectors
+  const double2* g1_ext = nullptr;  // eph_interp_q_g1: caller's G1 [nq][nm*ne*nb*nb] for this call
+  DBuf g1in;                   // host-mode staging of that G1
   int* Re = nullptr;
   int* Rp = nullptr;
   double* we = nullptr;
@@ -115,6 +119,10 @@ struct eph_ctx {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t slice_ev[16] = {};
   cudaEvent_t copy_done = nullptr;
+  // copies of g out of g_stage may still be in flight (set when they are issued, cleared once the
+  // copy stream is known to have drained): the next band rotation into g_stage, in this call or
+  // a later one, first waits on copy_done
+  bool copies_pending = false;
   // product k grid (sum-factorised Re->k): bounding box of the Re list, axis phase tables,
   // the scattered W_q box and the two partial transforms of a q batch
   bool boxable = false;  // Re vectors distinct, box extents <= 33, box volume <= 8 ne
@@ -343,7 +351,7 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut, &ctx->eigA, &ctx->eigW, &ctx->eigV, &ctx->tcband,
                   &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc, &ctx->rebox, &ctx->E1,
                   &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
-                  &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair};
+                  &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair, &ctx->g1in};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -358,19 +366,25 @@ void eph_destroy(eph_ctx* ctx) {
   delete ctx;
 }
 
-int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re, const double* Phi_Rp,
-               const double* g_ReRp, const int* Re, const double* we, const int* Rp, const double* wp,
-               const double* masses, const eph_options* opt, void* cuda_stream) {
+}  // extern "C"
+
+namespace {
+int create_impl(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re, const double* Phi_Rp,
+                const double* g_ReRp, const int* Re, const double* we, const int* Rp, const double* wp,
+                const double* masses, int rp0, int nrp, const eph_options* opt, void* cuda_stream) {
   if (!out) return EPH_EINVAL;
   *out = nullptr;
   if (nb < 1 || na < 1 || ne < 1 || np < 1 || !H_Re || !Phi_Rp || !g_ReRp || !Re || !Rp || !masses)
     return EPH_EINVAL;
+  if (rp0 < 0 || nrp < 1 || (long)rp0 + nrp > np) return EPH_EINVAL;
   eph_ctx* ctx = new eph_ctx();
   ctx->nb = nb;
   ctx->na = na;
   ctx->nm = 3 * na;
   ctx->ne = ne;
   ctx->np = np;
+  ctx->rp0 = rp0;
+  ctx->nrp = nrp;
   if (opt)
     ctx->opt = *opt;
   else
@@ -419,7 +433,7 @@ int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re
   ctx->omega_unit = omega_unit_ev();
   const size_t szH = (size_t)ne * nb2 * sizeof(double2);
   const size_t szPhi = (size_t)np * nm * nm * sizeof(double);
-  const size_t szG = (size_t)np * nm * ne * nb2 * sizeof(double2);
+  const size_t szG = (size_t)nrp * nm * ne * nb2 * sizeof(double2);
   struct Up {
     void** dst;
     const void* src;
@@ -499,6 +513,23 @@ int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re
     return bail(EPH_ENOMEM);
   *out = ctx;
   return EPH_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int eph_create(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re, const double* Phi_Rp,
+               const double* g_ReRp, const int* Re, const double* we, const int* Rp, const double* wp,
+               const double* masses, const eph_options* opt, void* cuda_stream) {
+  return create_impl(out, nb, na, ne, np, H_Re, Phi_Rp, g_ReRp, Re, we, Rp, wp, masses, 0, np, opt, cuda_stream);
+}
+
+int eph_create_rp_slice(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re, const double* Phi_Rp,
+                        const double* g_ReRp_slice, const int* Re, const double* we, const int* Rp, const double* wp,
+                        const double* masses, int rp_begin, int rp_count, const eph_options* opt,
+                        void* cuda_stream) {
+  return create_impl(out, nb, na, ne, np, H_Re, Phi_Rp, g_ReRp_slice, Re, we, Rp, wp, masses, rp_begin, rp_count,
+                     opt, cuda_stream);
 }
 
 }  // extern "C"
@@ -744,7 +775,9 @@ int ensure_q_workspace(eph_ctx* ctx, const QPlan& p, bool with_y = true) {
 
 // Per q batch, before the k loop: phases, D(q) -> omega, u; Eq. 9; W_q; on a product k grid
 // (grid_stages) also the first two axis transforms of W_q.
-int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid_stages = true) {
+// g1_in: the caller's G1 of these q points (eph_interp_q_g1), else Eq. 9 runs on the resident slice.
+int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid_stages = true,
+              const double2* g1_in = nullptr) {
   const int nm = ctx->nm, ne = ctx->ne, np = ctx->np, nb2 = ctx->nb * ctx->nb;
   double2* Qe = as<double2>(ctx->Qe);
   double2* Pp = as<double2>(ctx->Pp);
@@ -760,13 +793,17 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
   EPH_LAUNCH_S(EPH_STAGE_MODE, launch_phonon_post(as<double>(ctx->lamq), as<double2>(ctx->evq), nqb, nm,
                                                   ctx->invsqrtm, ctx->omega_unit, as<double>(ctx->omq),
                                                   as<double2>(ctx->uq), ctx->stream));
-  // Eq. 9: G1 = sum_Rp w_p e^{i q.Rp} g(Re,Rp)
-  EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, p.X, np, Pp, np, ctx->gW, p.X, as<double2>(ctx->G1), p.X,
-                                             ctx->stream));
+  // Eq. 9: G1 = sum_Rp w_p e^{i q.Rp} g(Re,Rp) over the Rp vectors of the resident slice
+  const double2* G1src = g1_in;
+  if (!G1src) {
+    EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, p.X, ctx->nrp, Pp + ctx->rp0, np, ctx->gW, p.X,
+                                               as<double2>(ctx->G1), p.X, ctx->stream));
+    G1src = as<double2>(ctx->G1);
+  }
   // W_q = [ e^{i q.Re} H(Re) | mode-rotated G1 ], row e of length NW
   EPH_LAUNCH_S(EPH_STAGE_MODE, launch_scale_rows(Qe, nqb, ctx->H, ne, nb2, W, p.NW, (long)ne * p.NW, ctx->stream));
   if (nm <= 16) {
-    EPH_LAUNCH_S(EPH_STAGE_MODE, launch_mode_rotate(as<double2>(ctx->G1), as<double2>(ctx->uq), nqb, nm, ne, nb2,
+    EPH_LAUNCH_S(EPH_STAGE_MODE, launch_mode_rotate(G1src, as<double2>(ctx->uq), nqb, nm, ne, nb2,
                                                     W + nb2, p.NW, (long)ne * p.NW, ctx->stream));
   } else {
     // G2[e][nu][b] = sum_c u[c][nu] G1[c][e][b]: one GEMM per q, batched over Re (u^T from a transpose)
@@ -774,7 +811,7 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
     EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_transpose(as<double2>(ctx->uq), nm, nqb, as<double2>(ctx->ut), ctx->stream));
     for (int iq = 0; iq < nqb; ++iq) {
       const double2* ut = as<double2>(ctx->ut) + (long)iq * nm * nm;
-      const double2* G1 = as<double2>(ctx->G1) + (long)iq * p.X;
+      const double2* G1 = G1src + (long)iq * p.X;
       double2* Wq = W + (long)iq * ne * p.NW + nb2;
       if (ctx->opt.form == EPH_FORM_MIXED)  // double-float on the FP32 pipe (~1e-13): the g of this form is c64
         EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_zgemm_df_b2(nm, nb2, nm, ut, nm, 0, 0, G1, (long)ne * nb2, nb2, 0, Wq,
@@ -991,7 +1028,7 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
   double2* W = as<double2>(ctx->W);
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
     const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
-    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb, true, ctx->g1_ext ? ctx->g1_ext + (long)q0 * p.X : nullptr));
     if (omega)
       EPH_CK(cudaMemcpyAsync(omega + (long)q0 * nm, ctx->omq.p, (size_t)nqb * nm * sizeof(double), out_kind(ctx),
                              ctx->stream));
@@ -1123,11 +1160,10 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
   const void* dq = nullptr;
   EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
   const double* qdev = static_cast<const double*>(dq);
-  bool copies = false;  // device->host copies of g issued on the copy stream
   if (host && g) EPH_TRY(ensure_copy_stream(ctx));
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
     const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
-    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb, true, ctx->g1_ext ? ctx->g1_ext + (long)q0 * p.X : nullptr));
     if (omega)
       EPH_CK(cudaMemcpyAsync(omega + (long)q0 * nm, ctx->omq.p, (size_t)nqb * nm * sizeof(double), out_kind(ctx),
                              ctx->stream));
@@ -1153,8 +1189,10 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
         char* gout = static_cast<char*>(g);
         char* stage = static_cast<char*>(ctx->g_stage.p);
         if (host) {
-          // one q at a time: the copy of q overlaps the band rotation of the following ones
-          if (copies) EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));  // stage free again
+          // one q at a time: the copy of q overlaps the band rotation of the following ones; the
+          // staging buffer is free again once the copies of the previous tile (of this call or,
+          // in async mode, of an earlier one) are done
+          if (ctx->copies_pending) EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));
           for (int iq = 0; iq < nqb; ++iq) {
             char* slice = stage + (long)iq * nkt * p.gcols * esz;
             EPH_TRY(band_rotate(ctx, p, 1, nkt, k0, reinterpret_cast<double2*>(slice), (long)nkt * p.gcols, keep, iq));
@@ -1164,7 +1202,7 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
                                    (size_t)nkt * p.gcols * esz, cudaMemcpyDeviceToHost, ctx->copy_stream));
           }
           EPH_CK(cudaEventRecord(ctx->copy_done, ctx->copy_stream));
-          copies = true;
+          ctx->copies_pending = true;
         } else {
           EPH_TRY(band_rotate(ctx, p, nqb, nkt, k0,
                               reinterpret_cast<double2*>(gout + ((long)q0 * nk + k0) * p.gcols * esz),
@@ -1174,16 +1212,86 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
     }
   }
   // synchronous calls: finish() also waits for the copies; async mode: eph_sync does, and the
-  // next call's band rotation waits for them before it reuses the staging buffer
-  if (copies && !ctx->opt.async) EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));
+  // next call's band rotation waits for them (copies_pending) before it reuses the staging buffer
+  if (ctx->copies_pending && !ctx->opt.async) {
+    EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));
+    const int rc = finish(ctx);  // synchronises the stream, hence the copies it waited for
+    if (rc == EPH_OK || rc == EPH_ENOTCONV) ctx->copies_pending = false;
+    return rc;
+  }
   return finish(ctx);
 }
+}  // namespace
+
+namespace {
+// true if the context holds g(Re,Rp) for every Rp vector (not an Rp slice)
+bool whole_g(const eph_ctx* ctx) { return ctx->rp0 == 0 && ctx->nrp == ctx->np; }
+
+int interp_q_dispatch(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g);
 }  // namespace
 
 extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
   if (!ctx) return EPH_EINVAL;
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q before eph_set_k");
   if (nq < 1 || !qpts) return fail(ctx, EPH_EINVAL, "eph_interp_q: nq < 1 or qpts NULL");
+  if (!whole_g(ctx))
+    return fail(ctx, EPH_ESTATE, "eph_interp_q on an Rp-slice context: sum eph_g1_partial over the slices, then "
+                                 "call eph_interp_q_g1");
+  return interp_q_dispatch(ctx, nq, qpts, eps_kq, omega, g);
+}
+
+extern "C" int eph_g1_partial(eph_ctx* ctx, int nq, const double* qpts, double* G1) {
+  if (!ctx) return EPH_EINVAL;
+  if (nq < 1 || !qpts || !G1) return fail(ctx, EPH_EINVAL, "eph_g1_partial: nq < 1 or NULL pointer");
+  const int np = ctx->np, ne = ctx->ne, nm = ctx->nm, nb2 = ctx->nb * ctx->nb;
+  const long X = (long)nm * ne * nb2;
+  const int QB = 16;
+  const void* dq = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
+  EPH_TRY(ensure(ctx, ctx->Pp, (size_t)(nq < QB ? nq : QB) * np * sizeof(double2)));
+  if (!ctx->opt.device_ptrs) EPH_TRY(ensure(ctx, ctx->G1, (size_t)(nq < QB ? nq : QB) * X * sizeof(double2)));
+  const double* qdev = static_cast<const double*>(dq);
+  for (int q0 = 0; q0 < nq; q0 += QB) {
+    const int nqb = nq - q0 < QB ? nq - q0 : QB;
+    double2* dst = ctx->opt.device_ptrs ? reinterpret_cast<double2*>(G1) + (long)q0 * X : as<double2>(ctx->G1);
+    EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(qdev + 3L * q0, nqb, ctx->Rp, ctx->wp, np, as<double2>(ctx->Pp), np,
+                                               ctx->stream));
+    // Eq. 9 over the Rp vectors of this slice only: the partial sums of all slices add up to G1
+    EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, X, ctx->nrp, as<double2>(ctx->Pp) + ctx->rp0, np, ctx->gW, X, dst,
+                                               X, ctx->stream));
+    if (!ctx->opt.device_ptrs)
+      EPH_CK(cudaMemcpyAsync(reinterpret_cast<double2*>(G1) + (long)q0 * X, dst, (size_t)nqb * X * sizeof(double2),
+                             cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return finish(ctx);
+}
+
+extern "C" int eph_interp_q_g1(eph_ctx* ctx, int nq, const double* qpts, const double* G1, double* eps_kq,
+                               double* omega, void* g) {
+  if (!ctx) return EPH_EINVAL;
+  if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q_g1 before eph_set_k");
+  if (nq < 1 || !qpts || !G1) return fail(ctx, EPH_EINVAL, "eph_interp_q_g1: nq < 1 or NULL pointer");
+  const size_t bytes = (size_t)nq * ctx->nm * ctx->ne * ctx->nb * ctx->nb * sizeof(double2);
+  const void* dg1 = nullptr;
+  EPH_TRY(stage_in(ctx, ctx->g1in, G1, bytes, &dg1));
+  ctx->g1_ext = static_cast<const double2*>(dg1);
+  const int rc = interp_q_dispatch(ctx, nq, qpts, eps_kq, omega, g);
+  ctx->g1_ext = nullptr;
+  return rc;
+}
+
+extern "C" int eph_set_gw(eph_ctx* ctx, const double* g_ReRp) {
+  if (!ctx) return EPH_EINVAL;
+  if (!g_ReRp) return fail(ctx, EPH_EINVAL, "eph_set_gw: NULL pointer");
+  const size_t bytes = (size_t)ctx->nrp * ctx->nm * ctx->ne * ctx->nb * ctx->nb * sizeof(double2);
+  EPH_CK(cudaMemcpyAsync(ctx->gW, g_ReRp, bytes, ctx->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         ctx->stream));
+  if (!ctx->opt.device_ptrs) EPH_CK(cudaStreamSynchronize(ctx->stream));  // the host buffer may go on return
+  return finish(ctx);
+}
+
+namespace {
+int interp_q_dispatch(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
   if (mixed_list(ctx)) {
     if (ctx->opt.async && !ctx->opt.device_ptrs) {
       if (!ctx->big)
@@ -1196,6 +1304,7 @@ extern "C" int eph_interp_q(eph_ctx* ctx, int nq, const double* qpts, double* ep
   // eigensolves, band rotation in double-float arithmetic, complex64 g)
   return interp_fp64(ctx, nq, qpts, eps_kq, omega, g, nullptr);
 }
+}  // namespace
 
 extern "C" int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, double e_lo, double e_hi,
                                    double* eps_kq, double* omega, void* g, int* keep) {
@@ -1204,6 +1313,7 @@ extern "C" int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, dou
   if (nq < 1 || !qpts || !(e_lo <= e_hi)) return fail(ctx, EPH_EINVAL, "eph_interp_q_window: bad arguments");
   if (ctx->opt.form != EPH_FORM_FP64 || ctx->big)
     return fail(ctx, EPH_ENOTSUP, "eph_interp_q_window: FP64 form with nb, nm <= 16");
+  if (!whole_g(ctx)) return fail(ctx, EPH_ESTATE, "eph_interp_q_window on an Rp-slice context");
   const Window w{e_lo, e_hi, keep};
   return interp_fp64(ctx, nq, qpts, eps_kq, omega, g, &w);
 }
@@ -1221,6 +1331,7 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
   if (nk < 1 || nq < 1 || !kpts || !qpts || !w_nk || !L_out || !grad_g_ReRp)
     return fail(ctx, EPH_EINVAL, "eph_interp_backward: bad size or NULL pointer");
   if (ctx->big) return fail(ctx, EPH_ENOTSUP, "eph_interp_backward supports nb, nm <= 16");
+  if (!whole_g(ctx)) return fail(ctx, EPH_ESTATE, "eph_interp_backward on an Rp-slice context");
   EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
   const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, np = ctx->np;
   const int nb2 = nb * nb;
@@ -1343,6 +1454,8 @@ int adjoint_chain(eph_ctx* ctx, int nk, const double* kpts, int nq, const double
       const double2* gb = gin + ((long)q0 * nk + k0) * gcols;
       long sgq = (long)nk * gcols;
       if (host) {
+        // g_stage may still be read by copies of an earlier asynchronous eph_interp_q
+        if (ctx->copies_pending) EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));
         for (int iq = 0; iq < nqb; ++iq)
           EPH_CK(cudaMemcpyAsync(as<double2>(ctx->g_stage) + (long)iq * nkt * gcols, gb + (long)iq * nk * gcols,
                                  (size_t)nkt * gcols * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
@@ -1413,7 +1526,10 @@ extern "C" int eph_eigh(eph_ctx* ctx, int n, int batch, const void* A, double* w
 
 extern "C" int eph_sync(eph_ctx* ctx) {
   if (!ctx) return EPH_EINVAL;
-  if (ctx->copy_stream) EPH_CK(cudaStreamSynchronize(ctx->copy_stream));  // host copies of g
+  if (ctx->copy_stream) {  // host copies of g
+    EPH_CK(cudaStreamSynchronize(ctx->copy_stream));
+    ctx->copies_pending = false;
+  }
   int h[2] = {0, 0};
   EPH_CK(cudaMemcpyAsync(h, ctx->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   EPH_CK(cudaStreamSynchronize(ctx->stream));
@@ -1538,6 +1654,7 @@ extern "C" int eph_linewidths(eph_ctx* ctx, int nq, const double* qpts, const do
     return fail(ctx, EPH_EINVAL, "eph_linewidths: nq < 1, NULL pointer, or kT/sigma not positive");
   if (ctx->opt.form != EPH_FORM_FP64 || ctx->big)
     return fail(ctx, EPH_ENOTSUP, "eph_linewidths: FP64 form with nb, nm <= 16");
+  if (!whole_g(ctx)) return fail(ctx, EPH_ESTATE, "eph_linewidths on an Rp-slice context");
   const int nb = ctx->nb, nm = ctx->nm, nk = ctx->nk, nb2 = nb * nb;
   QPlan p;
   EPH_TRY(prepare_fp64(ctx, nq, false, &p));

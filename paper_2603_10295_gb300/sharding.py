@@ -41,3 +41,35 @@ def allreduce_loss_and_grad(L, grad, group=None):
     else:
         dist.all_reduce(grad, group=group)
     return float(t.item()), grad
+
+
+# ---------------------------------------------------------------------------------------------
+# Rp partition of g(Re,Rp) (the paper's pools): for a g(Re,Rp) that does not fit one GPU, each
+# rank holds a contiguous block of the Rp vectors (eph_create_rp_slice), forms the partial Eq. 9
+# sum over its block (eph_g1_partial), and one all-reduce of G1 per q batch gives every rank the
+# whole G1, from which it runs the rest of the path for its own k points (eph_interp_q_g1).
+# ---------------------------------------------------------------------------------------------
+def rp_slice(np_total: int, rank: int, world: int) -> tuple[int, int]:
+    """(rp_begin, rp_count) of this rank's block of the Rp list; every block holds >= 1 vector."""
+    if np_total < world:
+        raise ValueError(f"{np_total} Rp vectors cannot be split over {world} ranks")
+    a, b = q_shard(np_total, rank, world)
+    return a, b - a
+
+
+def allreduce_g1(G1, group=None):
+    """Sums the ranks' partial G1 tensors in place (complex tensors as their real views)."""
+    import torch
+    import torch.distributed as dist
+    dist.all_reduce(torch.view_as_real(G1) if torch.is_complex(G1) else G1, group=group)
+    return G1
+
+
+def interp_q_rp_partitioned(ctx, nq, qpts, G1, eps_kq=None, omega=None, g=None, group=None):
+    """One q batch on an Rp-partitioned g(Re,Rp): partial Eq. 9 on this rank's slice, all-reduce
+    of G1 over `group`, then the k stage from the summed G1.  `ctx` is a device-pointer
+    binding.Context on torch's current stream (so the collective is ordered after the partial
+    sum); G1 is a caller tensor [nq][nm][ne][nb][nb] complex128 on the same device."""
+    ctx.eph_g1_partial(nq, qpts, G1)
+    allreduce_g1(G1, group)
+    ctx.eph_interp_q_g1(nq, qpts, G1, eps_kq, omega, g)

@@ -23,7 +23,7 @@ def lib():
 def header_functions():
     text = open(os.path.join(ROOT, "include", "eph.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(eph_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(eph_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_binding_exports():
@@ -122,3 +122,26 @@ def test_every_entry_point_rejects_a_null_context_without_gpu(lib):
     assert lib.eph_bands_noalloc(10, dummy, 17, 8, dummy, None, dummy, dummy, dummy, 0, None) == E
     assert lib.eph_bands_noalloc(100000, dummy, 8, 216, dummy, None, dummy, dummy, dummy, 0, None) == E
     assert lib.eph_bands_noalloc(10, None, 4, 8, dummy, None, dummy, dummy, dummy, 0, None) == E
+    # the Rp-partition and g(Re,Rp)-update entry points
+    assert lib.eph_g1_partial(None, 1, dummy, dummy) == E
+    assert lib.eph_interp_q_g1(None, 1, dummy, dummy, None, None, None) == E
+    assert lib.eph_set_gw(None, dummy) == E
+
+
+def test_rp_slice_bounds_checked_without_gpu(lib):
+    # an Rp slice outside [0, np) is rejected before the context touches the device
+    import numpy as np
+    h = ctypes.c_void_p()
+    opt = binding.EphOptions()
+    lib.eph_default_options(ctypes.byref(opt))
+    nb, na, ne, np_ = 2, 1, 3, 3
+    H = np.zeros((ne, nb, nb), np.complex128)
+    Phi = np.zeros((np_, 3, 3))
+    g = np.zeros((np_, 3, ne, nb, nb), np.complex128)
+    R = np.zeros((3, 3), np.int32)
+    m = np.ones(1)
+    for begin, count in ((-1, 1), (0, 0), (2, 2), (3, 1)):
+        assert lib.eph_create_rp_slice(ctypes.byref(h), nb, na, ne, np_, H.ctypes.data, Phi.ctypes.data,
+                                       g.ctypes.data, R.ctypes.data, None, R.ctypes.data, None, m.ctypes.data,
+                                       begin, count, ctypes.byref(opt), None) == binding.EPH_EINVAL
+        assert not h.value

@@ -82,3 +82,68 @@ def test_gloo_two_ranks_sum_equals_single_process(tmp_path):
     g = np.load(tmp_path / "grad.npy")
     assert abs(L - L_ref) <= 1e-12 * abs(L_ref)
     assert np.abs(g - g_ref).max() <= 1e-12 * np.abs(g_ref).max()
+
+
+@pytest.mark.parametrize("np_total,world", [(27, 2), (216, 3), (15, 8), (8, 8)])
+def test_rp_slices_cover_the_list(np_total, world):
+    from paper_2603_10295_gb300.sharding import rp_slice
+    blocks = [rp_slice(np_total, r, world) for r in range(world)]
+    covered = [i for b, c in blocks for i in range(b, b + c)]
+    assert covered == list(range(np_total)) and min(c for _, c in blocks) >= 1
+    with pytest.raises(ValueError):
+        rp_slice(world - 1, 0, world)
+
+
+class _OracleSliceContext:
+    """Stands in for a device context on CPU ranks: eph_g1_partial is the oracle's Eq. 9 over
+    the rank's Rp block; eph_interp_q_g1 records the G1 it is given."""
+
+    def __init__(self, wl, begin, count):
+        self.wl, self.b, self.c = wl, begin, count
+        self.seen = None
+
+    def eph_g1_partial(self, nq, qpts, G1):
+        import torch
+
+        import oracle
+        part = oracle.g_rp_to_q(qpts[:nq], self.wl.Rp[self.b:self.b + self.c], self.wl.wp[self.b:self.b + self.c],
+                                self.wl.g_ReRp[self.b:self.b + self.c])
+        G1.copy_(torch.from_numpy(part.reshape(G1.shape)))
+
+    def eph_interp_q_g1(self, nq, qpts, G1, eps_kq, omega, g):
+        self.seen = G1.clone()
+
+
+def _rp_worker(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_10295_gb300 import synth
+    from paper_2603_10295_gb300.sharding import interp_q_rp_partitioned, rp_slice
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    wl = synth.make_workload("si_tiny", nb=3, nk=4, nq=5)
+    b, c = rp_slice(wl.np_, rank, world)
+    ctx = _OracleSliceContext(wl, b, c)
+    G1 = torch.empty((5, wl.nm, wl.ne, wl.nb, wl.nb), dtype=torch.complex128)
+    interp_q_rp_partitioned(ctx, 5, wl.qpts, G1)
+    np.save(os.path.join(out_dir, f"g1_{rank}.npy"), ctx.seen.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_rp_partition_sums_to_eq9(tmp_path, world):
+    # every rank ends with the whole Eq. 9 result although it holds only its Rp block of g(Re,Rp)
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+
+    import oracle
+    from paper_2603_10295_gb300 import synth
+    mp.spawn(_rp_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    wl = synth.make_workload("si_tiny", nb=3, nk=4, nq=5)
+    ref = oracle.g_rp_to_q(wl.qpts, wl.Rp, wl.wp, wl.g_ReRp)
+    for r in range(world):
+        got = np.load(tmp_path / f"g1_{r}.npy").reshape(ref.shape)
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()

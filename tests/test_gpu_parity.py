@@ -183,6 +183,35 @@ def test_async_host_mode_matches_sync(form, grid):
             assert np.array_equal(a.numpy(), b)
 
 
+@pytest.mark.parametrize("grid", [False, True])
+def test_async_host_mode_back_to_back_large_copies(grid):
+    # g of one q is ~120 MB here, so its device->host copy (on the copy stream) is still running
+    # when the next asynchronous call reaches its band rotation into the same staging buffer;
+    # that rotation has to wait for the copy.  Four calls in a row, one q each, into distinct
+    # pinned buffers, must equal the synchronous calls bit for bit.
+    torch = pytest.importorskip("torch")
+    wl = synth.make_workload("si_tiny", nk=20000, nq=4)
+    sync = binding.Context.from_workload(wl, q_batch=1)
+    asyn = binding.Context.from_workload(wl, q_batch=1, async_mode=True)
+    if grid:
+        sync.set_k_grid(25, 20, 40)
+        asyn.eph_set_k_grid(25, 20, 40)
+    else:
+        sync.set_k(wl.kpts)
+        asyn.eph_set_k(len(wl.kpts), wl.kpts)
+    nk, nb, nm = sync.nk, wl.nb, wl.nm
+    outs = [(torch.empty(1, nk, nb, dtype=torch.float64).pin_memory(), torch.empty(1, nm, dtype=torch.float64).pin_memory(),
+             torch.empty(1, nk, nm, nb, nb, dtype=torch.complex128).pin_memory()) for _ in range(4)]
+    q = torch.from_numpy(wl.qpts.copy()).pin_memory()
+    for i in range(4):
+        asyn.eph_interp_q(1, q[i:i + 1], *outs[i])
+    asyn.eph_sync()
+    for i in range(4):
+        ref = sync.interp_q(wl.qpts[i:i + 1])
+        for a, b in zip(outs[i], ref):
+            assert np.array_equal(a.numpy(), b)
+
+
 @pytest.mark.parametrize("form", ["fp64", "mixed"])
 def test_phase_reduction_exact_far_from_the_cell(form):
     # k and q on a 1/8 grid plus integer offsets up to 2^20: every product k_i n_i and their

@@ -126,6 +126,38 @@ def test_autograd_arbitrary_loss():
     assert abs(fd - an) <= 1e-8 * abs(an)
 
 
+def test_autograd_device_path_and_retain_graph():
+    # CUDA tensors in and out (the model's context stays on the device; g(Re,Rp) is copied into it
+    # on the device), and a second backward through the same graph gives the same gradient
+    torch = pytest.importorskip("torch")
+    from paper_2603_10295_gb300.autograd import EphInterp, EphLoss, model_context
+    dev = torch.device("cuda:0")
+    wl = synth.make_workload("si_tiny", nb=4, nk=16, nq=3)
+    rng = np.random.default_rng(9)
+    w = rng.uniform(0.0, 1.0, (len(wl.kpts), wl.nb))
+    kd, qd = torch.from_numpy(wl.kpts).to(dev), torch.from_numpy(wl.qpts).to(dev)
+    gW = torch.from_numpy(wl.g_ReRp.copy()).to(dev).requires_grad_(True)
+    g = EphInterp.apply(gW, wl, kd, qd)
+    assert g.is_cuda
+    om = binding.Context.from_workload(wl).interp(wl.kpts, wl.qpts)[2]
+    c = torch.from_numpy(oracle.loss_weights(om, w, 1e-6)).to(dev)[:, :, :, None, :]
+    loss = (c * g.abs() ** 2).sum()
+    loss.backward(retain_graph=True)
+    first = gW.grad.clone()
+    gW.grad = None
+    loss.backward()
+    assert torch.equal(gW.grad, first)
+    # the loss path on the same cached context, after a different g(Re,Rp) went through it
+    gW2 = torch.from_numpy(1.5 * wl.g_ReRp).to(dev).requires_grad_(True)
+    EphLoss.apply(gW2, wl, kd, qd, torch.from_numpy(w).to(dev), 1e-6).backward()
+    _, g_ref = oracle.loss_and_grad(wl, wl.kpts, wl.qpts, w, 1e-6)
+    assert rel(gW2.grad.cpu().numpy(), 1.5 * g_ref) <= 1e-12
+    gW3 = torch.from_numpy(wl.g_ReRp.copy()).to(dev).requires_grad_(True)
+    EphLoss.apply(gW3, wl, kd, qd, torch.from_numpy(w).to(dev), 1e-6).backward()
+    assert rel(first.cpu().numpy(), gW3.grad.cpu().numpy()) <= 1e-12
+    assert model_context(wl, dev) is model_context(wl, dev)
+
+
 def test_vjp_errors():
     wl = synth.make_workload("si_tiny", nk=4, nq=2)
     gbar = np.zeros((2, 4, wl.nm, wl.nb, wl.nb), dtype=np.complex128)
