@@ -28,33 +28,62 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[EPH_NOALLOC_SCRATCH_BY
 __device__ __align__(256) int g_noalloc_status;
 
 constexpr int kMaxDevices = 256;
-void* g_scratch_addr[kMaxDevices] = {};
-int* g_status_addr[kMaxDevices] = {};
+struct Addr {
+  void* ctx = nullptr;  // the CUDA context the addresses belong to
+  void* scratch = nullptr;
+  int* status = nullptr;
+};
+Addr g_addr[kMaxDevices];
 std::mutex g_setup_mutex;
+
+// cuCtxGetCurrent through the runtime's driver entry point (the library links only the runtime)
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
+}
 
 // Host code cannot use the array's name as a device address: it is a
 // host-side stand-in.  Look the device address up once per device, with that
-// device current.
+// device current.  The cached address is tied to the CUDA context that was
+// current at the lookup: after cudaDeviceReset, or under another context on
+// the same device, the next call looks it up again.
 int device_addresses(void** scratch, int** status) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return EPH_ECUDA;
   }
+  void* cur = nullptr;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get || get(&cur) != 0) return EPH_ECUDA;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  Addr& a = g_addr[dev];
+  if (!cur || a.ctx != cur || !a.scratch) {
     void* s = nullptr;
     void* f = nullptr;
+    // (the lookup also makes the device's primary context current if no context was)
     if (cudaGetSymbolAddress(&s, g_noalloc_scratch) != cudaSuccess ||
         cudaGetSymbolAddress(&f, g_noalloc_status) != cudaSuccess || !s || !f) {
       cudaGetLastError();
       return EPH_ECUDA;
     }
-    g_scratch_addr[dev] = s;
-    g_status_addr[dev] = static_cast<int*>(f);
+    if (!cur && (get(&cur) != 0 || !cur)) return EPH_ECUDA;
+    a.ctx = cur;
+    a.scratch = s;
+    a.status = static_cast<int*>(f);
   }
-  *scratch = g_scratch_addr[dev];
-  *status = g_status_addr[dev];
+  *scratch = a.scratch;
+  *status = a.status;
   return EPH_OK;
 }
 

@@ -60,6 +60,18 @@ def test_bands_noalloc_matches_set_k_on_two_calls(lib):
         assert np.abs(rec - Hk).max() <= TOL * np.abs(Hk).max()
         eye = np.einsum("kam,kan->kmn", Uh.conj(), Uh)
         assert np.abs(eye - np.eye(nb)[None]).max() <= 1e-13
+    # the property the entry point exists for: once the first call has resolved the scratch
+    # address, further calls leave the device's free memory unchanged (any cudaMalloc would
+    # map at least one 2 MiB page; outputs and inputs here are allocated beforehand)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rc = lib.eph_bands_noalloc(nk, k_d.data_ptr(), nb, ne, Re_d.data_ptr(), we_d.data_ptr(), H_d.data_ptr(),
+                                   eps.data_ptr(), U.data_ptr(), 0, st.cuda_stream)
+        assert rc == binding.EPH_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_bands_noalloc_rejects_sizes_beyond_scratch(lib):
