@@ -52,6 +52,57 @@ TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
            ("k_band_rotate", "si_full", 4): 2097285888.0 + 1534482688.0}
 
 
+def fp64_peak_probe(dev):
+    """Measured FP64 rates of this GPU: a DFMA loop (four independent FMA chains per element,
+    compiled at run time by torch's jiterator, 4,096 flop per element over 2^24 elements) and
+    cuBLAS DGEMM (torch.matmul, float64 8192^3); best of 5 each, CUDA events.  The rooflines'
+    FP64 denominator stays the unit count x max clock; these numbers are printed beside it."""
+    import torch
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def best(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return min(t) * 1e-3
+
+    try:
+        from torch.cuda.jiterator import _create_jit_fn
+        code = """
+template <typename T> T dfma_chains(T x, T y) {
+  T a0 = x, a1 = y, a2 = x + y, a3 = x - y;
+  for (int i = 0; i < 512; ++i) {
+    a0 = fma(a0, y, x); a1 = fma(a1, y, x); a2 = fma(a2, y, x); a3 = fma(a3, y, x);
+  }
+  return a0 + a1 + a2 + a3;
+}"""
+        fn = _create_jit_fn(code)
+        x = torch.rand(1 << 24, dtype=torch.float64, device=dev)
+        y = torch.full_like(x, 0.999)
+        t = best(lambda: fn(x, y))
+        out["dfma_loop_tflops"] = 4096.0 * x.numel() / t / 1e12
+        del x, y
+    except Exception as exc:  # noqa: BLE001 - a probe that cannot compile is reported, not fatal
+        out["dfma_loop_error"] = str(exc).splitlines()[0][:200]
+    a = torch.rand(8192, 8192, dtype=torch.float64, device=dev)
+    b = torch.rand(8192, 8192, dtype=torch.float64, device=dev)
+    t = best(lambda: torch.matmul(a, b), reps=3)
+    out["dgemm_tflops"] = 2.0 * 8192 ** 3 / t / 1e12
+    out["unit_count_tflops"] = FP64_PEAK_FLOPS / 1e12
+    out["how"] = ("DFMA loop: jiterator elementwise kernel, 4 x 512 dependent FMA chains per element, 2^24 "
+                  "elements; DGEMM: torch.matmul float64 8192^3; best of 5 / 3, CUDA events")
+    del a, b
+    torch.cuda.empty_cache()
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -70,6 +121,9 @@ def parse():
     ap.add_argument("--no-other", action="store_true", help="skip the MoS2- and stanene-shaped forward lines")
     ap.add_argument("--capture", default=None, choices=sorted(CAPTURES),
                     help="run one small untimed case for an ncu capture and exit (no JSON line)")
+    ap.add_argument("--graph-full", action="store_true",
+                    help="time only the batching workload with the stanene context's q batches as written "
+                         "(1400 q, mixed form; minutes per replay) and print its JSON object")
     ap.add_argument("--k-path", default="grid", choices=["grid", "list"],
                     help="FP64 form: sum-factorised Re->k on the workload's uniform k grid, or the dense "
                          "Re->k GEMM on the k list")
@@ -333,39 +387,69 @@ def time_form(wl, form, args, q_dev, k_dev, rank, world, local, dev, QB, use_gri
 
 
 def time_backward(args):
-    """eph_interp_backward on the differentiation workload (mos2_diff: 48x48 k x 256 q, FP64)."""
+    """eph_interp_backward on the differentiation workload (mos2_diff: 48x48 k grid x 256 q, FP64):
+    the library call on the resident grid (forward Re->k sum and its adjoint sum-factorised), its
+    stage breakdown, the same call on the points as a plain k list (dense GEMMs), and one
+    optimisation step through torch.autograd (EphLoss forward + backward on device tensors)."""
     import numpy as np
     import torch
 
     from paper_2603_10295_gb300 import binding, synth
+    from paper_2603_10295_gb300.autograd import EphLoss
     wl = synth.make_workload("mos2_diff")
     dev = torch.device("cuda", torch.cuda.current_device())
     st = torch.cuda.current_stream()
-    ctx = binding.Context.from_workload(wl, device_ptrs=True, stream=st)
-    nk, nq, nb = len(wl.kpts), len(wl.qpts), wl.nb
+    nk, nq, nb, nm = len(wl.kpts), len(wl.qpts), wl.nb, wl.nm
     k_d = torch.from_numpy(wl.kpts).to(dev)
     q_d = torch.from_numpy(wl.qpts).to(dev)
     e_d = torch.empty(nk, nb, dtype=torch.float64, device=dev)
-    ctx.eph_set_k(nk, k_d, e_d)
+    ctx = binding.Context.from_workload(wl, device_ptrs=True, stream=st)
+    ctx.eph_set_k_grid(*wl.kgrid, None, e_d)
     # Fermi weights at 300 K around the median of band 3 (1-based) over the k grid
     e = e_d.cpu().numpy()
     mu = float(np.median(e[:, 2]))
-    w_d = torch.from_numpy(1.0 / (np.exp((e - mu) / 0.025852) + 1.0)).to(dev)
+    w_np = 1.0 / (np.exp((e - mu) / 0.025852) + 1.0)
+    w_d = torch.from_numpy(w_np).to(dev)
     L = torch.zeros(1, dtype=torch.float64, device=dev)
     grad = torch.empty(wl.g_ReRp.shape, dtype=torch.complex128, device=dev)
-    ctx.eph_interp_backward(nk, k_d, nq, q_d, w_d, 1e-6, L, grad)      # warm-up
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 2
-    torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(reps):
-        ctx.eph_interp_backward(nk, k_d, nq, q_d, w_d, 1e-6, L, grad)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+
+    def timed(fn, reps):
+        fn()                                   # warm-up
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_grid = timed(lambda: ctx.eph_interp_backward(nk, None, nq, q_d, w_d, 1e-6, L, grad), 3)
+    ctx.profile(True)
+    ctx.profile_reset()
+    ctx.eph_interp_backward(nk, None, nq, q_d, w_d, 1e-6, L, grad)
+    prof = ctx.profile_read()
+    ctx.profile(False)
     ctx.close()
-    return {"workload": "mos2_diff: Nb=11 Nm=9 Ne=Np=144, 48x48 k x 256 q, FP64 adjoint (forward recomputed)",
-            "ms_per_call": ms, "g_elements_per_s": nk * nq * wl.nm * nb * nb / (ms * 1e-3),
+    lctx = binding.Context.from_workload(wl, device_ptrs=True, stream=st)
+    ms_list = timed(lambda: lctx.eph_interp_backward(nk, k_d, nq, q_d, w_d, 1e-6, L, grad), 1)
+    lctx.close()
+    # one optimisation step through torch.autograd (the model's cached device context)
+    gW = torch.from_numpy(wl.g_ReRp.copy()).to(dev).requires_grad_(True)
+
+    def step():
+        gW.grad = None
+        EphLoss.apply(gW, wl, None, q_d, w_d, 1e-6).backward()
+
+    ms_autograd = timed(step, 3)
+    el = nk * nq * nm * nb * nb
+    return {"workload": "mos2_diff: Nb=11 Nm=9 Ne=Np=144, 48x48 k grid x 256 q, FP64 adjoint (forward recomputed)",
+            "ms_per_call": ms_grid, "g_elements_per_s": el / (ms_grid * 1e-3), "k_path": "grid (kpts NULL)",
+            "stage_ms_per_call": {k: round(v[0], 3) for k, v in prof.items() if v[0] > 0},
+            "k_list": {"ms_per_call": ms_list, "g_elements_per_s": el / (ms_list * 1e-3)},
+            "autograd_step": {"what": "EphLoss.apply + backward() on CUDA tensors: eph_set_gw (device copy of "
+                                      "g(Re,Rp)), eph_interp_backward on the grid, grad scaling",
+                              "ms_per_step": ms_autograd, "host_round_trips": 0},
             "parity": "vs FP64 CPU adjoint <= 1e-12, central differences <= 1e-6 (tests/test_gpu_adjoint.py)"}
 
 
@@ -443,6 +527,64 @@ def time_workload(name, args, dev, legs, warmup, steps):
     return out
 
 
+# the batching workload: stanene-shaped (full shapes, 512 k) with uneven q batches in one CUDA graph
+# with a silicon-shaped (Nb=8) and a MoS2-shaped (Nb=11) context.  The silicon- and MoS2-shaped
+# contexts take the batch sizes as written (1400 q); the stanene context the first batches of
+# the list, scaled so that a replay stays ~10 s (one stanene q costs ~0.17 s mixed, ~2.1 s FP64).
+GRAPH_STANENE = {"mixed": ([17, 40, 11], 4), "fp64": ([1, 2], 1)}
+
+
+def time_batched_graph(form, dev, replays=3, full=False):
+    """One captured graph over three materials (GraphBatcher), autotuned tiles; total g el/s over
+    the replays and each material's share (its calls timed eagerly, one after the other)."""
+    import torch
+
+    from paper_2603_10295_gb300 import synth
+    from paper_2603_10295_gb300.batching import graph_of_materials
+    batches = list(synth.STANENE_Q_BATCHES)
+    si = synth.make_workload("si_tiny", nk=1024, nq=sum(batches))
+    mo = synth.make_workload("mos2_diff", nq=sum(batches))
+    st = synth.make_workload("stanene")
+    sb, sch = (batches, 4) if full else GRAPH_STANENE[form]
+    specs = [(si, batches, 16, False), (mo, batches, 16, True), (st, sb, sch, False)]
+    gb, mats = graph_of_materials(specs, form, dev, autotune=True)
+    gb.replay()                     # warm replay (the capture's eager pass ran before it)
+    gb.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(gb.stream)
+    for _ in range(replays):
+        gb.replay()
+    e1.record(gb.stream)
+    gb.check()
+    ms = e0.elapsed_time(e1) / replays
+    # each material's calls alone, eagerly (the per-material share of the work)
+    eager = []
+    for m in mats:
+        with torch.cuda.stream(gb.stream):
+            e0.record(gb.stream)
+            for ctx, q, e, o, g in gb.items:
+                if ctx is m.ctx:
+                    ctx.eph_interp_q(q.shape[0], q, e, o, g)
+            e1.record(gb.stream)
+        gb.check()
+        eager.append(e0.elapsed_time(e1))
+    total_el = sum(m.g_elements() for m in mats)
+    out = {"value": total_el / (ms * 1e-3), "unit": UNIT, "ms_per_replay": ms, "replays": replays,
+           "graph_launches_per_replay": 1, "library_calls_per_replay": len(gb.items),
+           "eager_sum_ms": sum(eager), "materials": []}
+    for m, t in zip(mats, eager):
+        out["materials"].append({"workload": m.wl.name, "nb": m.wl.nb, "nm": m.wl.nm, "ne": m.wl.ne, "nk": m.nk,
+                                 "k_path": "grid" if m.grid else "list", "q_batches": m.batches,
+                                 "q_per_call": m.chunk, "autotuned_q_batch_k_tile": list(m.tuned),
+                                 "g_elements": m.g_elements(), "eager_ms": t, "time_share": t / sum(eager),
+                                 "g_el_per_s_eager": m.g_elements() / (t * 1e-3)})
+        m.ctx.close()
+    del gb, mats
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_libeph(args):
     import numpy as np
     import torch
@@ -506,20 +648,27 @@ def run_libeph(args):
         issued = 15 * 2.0 * mpad * npad * kpd * QB
         t = ft_ms / max(args.steps, 1) * 1e-3
         peak = peaks.get("bf16_tflops")
+        useful = 8.0 * nk * nb * nb * ne * QB
         return {"bound": "tensor", "kernel": "k_tc_hkq_gemm (tcgen05 kind::f16, 5 x 5 BF16 digits) + conversion",
-                "achieved": issued / t / 1e12 if t else None, "peak": peak, "unit": "TFLOP/s",
-                "frac": (issued / t / 1e12 / peak) if (t and peak) else None, "ms_per_step": ft_ms / args.steps,
-                "useful_tflops": 8.0 * nk * nb * nb * ne * QB / t / 1e12 if t else None}
+                "achieved": useful / t / 1e12 if t else None, "peak": peak, "unit": "TFLOP/s",
+                "frac": (useful / t / 1e12 / peak) if (t and peak) else None,
+                "achieved_issued": issued / t / 1e12 if t else None,
+                "frac_issued": (issued / t / 1e12 / peak) if (t and peak) else None, "ms_per_step": ft_ms / args.steps,
+                "useful_tflops": useful / t / 1e12 if t else None}
 
     def roof_band(r):
         bd_ms, bd_n = r["prof"]["band"]
         cmac = 2.0 * nb ** 3 * nm * QB * nk          # V_kq^H G3 V_k per (q,k) pair
         t = bd_ms / max(args.steps, 1) * 1e-3
-        ach = 6.0 * cmac / t                         # three-multiplication form: 3 FMA per CMAC
+        ach = 8.0 * cmac / t                         # the method's work: 8 flop per complex multiply-add
+        issued = 6.0 * cmac / t                      # three-multiplication form: 3 FMA per CMAC
         pairs = float(QB) * nk
         return {"bound": "alu", "kernel": "k_band_rotate (FP64, three-multiplication products)",
                 "achieved": ach / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_FLOPS, "flop_per_cmac": 6,
+                "frac": ach / FP64_PEAK_FLOPS, "flop_per_cmac": 8,
+                "frac_issued": issued / FP64_PEAK_FLOPS, "issued_flop_per_cmac": 6,
+                "note": "frac counts 8 flop per complex multiply-add of 2 Nb^3 Nm per pair; the kernel issues "
+                        "3 DFMA (6 flop) per one in the three-multiplication form, hence frac > frac_issued",
                 "traffic": TRAFFIC.get(("k_band_rotate", args.workload, QB)),
                 # G3 rows, V_k and V_{k+q} read, g written (complex128)
                 "algorithmic_bytes": 16.0 * (pairs * (nm * nb * nb + nb * nb + nb * nb) + pairs * nm * nb * nb),
@@ -558,12 +707,13 @@ def run_libeph(args):
         nkt = -(-nk // max(ft_n // max(args.steps, 1), 1))
         # P_k tile read, W_q read, Y = [H(k+q) | G3] written once (complex128)
         algo_bytes = 16.0 * (nkt * ne + QB * ne * NW + QB * nkt * NW)
-        # the kernel's algorithm (3M complex product) spends 3 DFMA = 6 flop per complex multiply-add
-        ach = 6.0 * cmac_launch / t if t else None
+        # the method's work: 8 flop per complex multiply-add; the kernel (3M) issues 3 DFMA = 6 flop
+        ach = 8.0 * cmac_launch / t if t else None
+        issued = 6.0 * cmac_launch / t if t else None
         return {"bound": "alu", "kernel": "k_zgemm (Re->k contraction fused with H(k+q), FP64 DFMA, 3M)",
                 "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                "frac": (ach / FP64_PEAK_FLOPS) if ach else None,
-                "flop_per_cmac": 6, "complex_equiv_tflops": 8.0 * cmac_launch / t / 1e12 if t else None,
+                "frac": (ach / FP64_PEAK_FLOPS) if ach else None, "flop_per_cmac": 8,
+                "frac_issued": (issued / FP64_PEAK_FLOPS) if issued else None, "issued_flop_per_cmac": 6,
                 "traffic": TRAFFIC.get(("k_zgemm", args.workload, QB)), "algorithmic_bytes": algo_bytes,
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
 
@@ -581,8 +731,12 @@ def run_libeph(args):
         algo_bytes = 2.0 * (3 * mpad * kpd + 4 * QB * npad * kpd) + 4.0 * QB * min(mpad, nk) * nr
         peak = peaks.get("bf16_tflops")
         return {"bound": "tensor", "kernel": "k_tc_fixed_gemm (tcgen05 kind::f16, fixed-point BF16 digits)",
-                "achieved": issued / t / 1e12 if t else None, "peak": peak, "unit": "TFLOP/s",
-                "frac": (issued / t / 1e12 / peak) if (t and peak) else None,
+                "achieved": useful / t / 1e12 if t else None, "peak": peak, "unit": "TFLOP/s",
+                "frac": (useful / t / 1e12 / peak) if (t and peak) else None,
+                "achieved_issued": issued / t / 1e12 if t else None,
+                "frac_issued": (issued / t / 1e12 / peak) if (t and peak) else None,
+                "note": "frac: the complex Re->k contraction at 8 flop per complex multiply-add; frac_issued: the "
+                        "nine bf16 digit products the kernel issues per K step on the real embedding",
                 "useful_tflops": useful / t / 1e12 if t else None, "ms_per_launch": tc_ms / max(tc_n, 1),
                 "traffic": TRAFFIC.get(("k_tc_fixed_gemm", args.workload, QB)), "algorithmic_bytes": algo_bytes,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), measured" if peak else "unavailable"}
@@ -700,11 +854,22 @@ def run_libeph(args):
             "mos2": time_workload("mos2", args, dev, [("fp64", True, QB), ("mixed", True, QB), ("mixed", False, QB)], 2, 5),
             # FP64: one q per call keeps the Re->k GEMM's k tiles whole waves of 152 rows; the mixed
             # form batches 4 q so that their dynamical-matrix eigensolves run side by side
-            "stanene": time_workload("stanene", args, dev, [("fp64", False, 1), ("mixed", False, 4)], 1, 1)}
+            "stanene": time_workload("stanene", args, dev, [("fp64", False, 1), ("mixed", False, 4)], 2, 3)}
+        line["other_workloads"]["batched_graph"] = {
+            "what": "one CUDA graph: stanene-shaped (Nb=120, Nm=180, Ne=Np=15, 512 k) + si_tiny-shaped "
+                    "(Nb=8, 1024 k) + MoS2-shaped (Nb=11, 48x48 k grid) contexts, uneven q batches "
+                    f"{list(synth.STANENE_Q_BATCHES)} (stanene: the first batches, scaled: "
+                    f"mixed {GRAPH_STANENE['mixed'][0]}, FP64 {GRAPH_STANENE['fp64'][0]}), eph_autotune's "
+                    "(q_batch, k_tile) per context, g through a per-material ring buffer",
+            "parity": "sampled (k,q) of every material after a replay vs the oracle "
+                      "(tests/test_gpu_config5_graph.py)",
+            "mixed": time_batched_graph("mixed", dev), "fp64": time_batched_graph("fp64", dev)}
     if single and not args.no_linewidths:
         line["linewidths"] = time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=legs[0][1])
     if single and not args.no_backward:
         line["backward"] = time_backward(args)
+    if single:
+        line["fp64_peak_probe"] = fp64_peak_probe(dev)
     if single and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_k)
     if rank == 0:
@@ -721,6 +886,12 @@ def main():
         return run_capture(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.graph_full:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"batched_graph_full": time_batched_graph("mixed", torch.device("cuda", 0),
+                                                                   replays=max(1, args.steps), full=True)}))
+        return 0
     return run_libeph(args)
 
 
