@@ -201,7 +201,10 @@ int eph_interp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* q
  *   L_out        one double (host or device)
  *   grad_g_ReRp  [np][nm][ne][nb][nb] complex128, dL/dRe(g) + i dL/dIm(g)
  *                (the PyTorch convention for a real scalar of complex inputs)
- * Uses the k list given here (it replaces the resident one).
+ * Uses the k list given here (it replaces the resident one).  kpts = NULL: the resident k
+ * list (nk must equal its size); after eph_set_k_grid both Re->k sums -- the recomputed
+ * forward one and its adjoint -- then run sum-factorised, as three one-axis transforms
+ * (the adjoint applies the conjugate axis phases in reverse order and gathers the Re rows).
  */
 int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
                         const double* w_nk, double omega_min, double* L_out, double* grad_g_ReRp);
@@ -217,7 +220,8 @@ int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int nq, const 
  * as this context returned it.
  *   kpts [nk][3], qpts [nq][3]; grad_g [nq][nk][nm][nb][nb] complex128; grad_g_ReRp
  *   [np][nm][ne][nb][nb] complex128 (overwritten).  Host or device pointers per
- *   device_ptrs.  Replaces the context's k list (as eph_set_k).
+ *   device_ptrs.  Replaces the context's k list (as eph_set_k); kpts = NULL keeps the
+ *   resident one (sum-factorised on a uniform grid, as in eph_interp_backward).
  * FP64 form with nb, nm <= 16; EPH_ENOTSUP otherwise.
  */
 int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts, const void* grad_g,
@@ -233,7 +237,9 @@ int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, const doubl
  * whose supercell vectors are Re = Rp (unit weights; weights are not used here).
  *   kpts [nk][3], qpts [nq][3]; g [nq][nk][nm][nb][nb] complex128; g_ReRp [np][nm][ne][nb][nb]
  *   complex128 (overwritten).  Host or device pointers per device_ptrs.  Replaces the
- *   context's k list (as eph_set_k).  The context's own g(Re,Rp) is not used.
+ *   context's k list (as eph_set_k); kpts = NULL keeps the resident one (e.g. the coarse grid
+ *   set by eph_set_k_grid, whose sums over k' then run sum-factorised).  The context's own
+ *   g(Re,Rp) is not used.
  * FP64 form with nb, nm <= 16; EPH_ENOTSUP otherwise.
  */
 int eph_bloch_to_wannier(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts, const void* g,
@@ -254,10 +260,30 @@ int eph_set_k_window(eph_ctx* ctx, int nk, const double* kpts, double e_lo, doub
                      int* kidx, int* nk_kept);
 
 /*
+ * Irreducible k list of a uniform grid under time reversal (the paper's transport workflow
+ * interpolates on the irreducible wedge of the fine k grid with weights, then prescreens it by
+ * the energy window): for Hamiltonians whose H(Re) are real (H(-Re) = H(Re)^T), H(-k) =
+ * conj H(k), so eps(-k) = eps(k) and a k-sum over the grid equals the weighted sum over one
+ * point of each pair {k, -k}.  Grid point i = (j1 n2 + j2) n3 + j3 at k = j/n + shift; its
+ * partner -k is grid point (-j_a - 2 shift_a n_a) mod n_a; i is kept if i <= its partner,
+ * with weight 2 (1 if it is its own partner).  The kept points, ascending, become the resident
+ * k list (a plain list: later Re->k sums use the general path).
+ *   shift [3] HOST pointer (NULL = 0); 2 shift_a n_a must be an integer on every axis (else
+ *   EPH_EINVAL).  eps_k [nk_kept][nb] (may be NULL), kidx [n1 n2 n3] receives the kept grid
+ *   indices (first *nk_kept entries), wk [n1 n2 n3] their weights (sum = n1 n2 n3); host or
+ *   device pointers per device_ptrs; *nk_kept on the host.  Not available in async mode.
+ * The reduction is pure index arithmetic (bit-exact); whether H(Re) has the symmetry is the
+ * caller's to know (the library does not check it).
+ */
+int eph_set_k_grid_ibz(eph_ctx* ctx, int n1, int n2, int n3, const double* shift, double* eps_k, int* kidx,
+                       double* wk, int* nk_kept);
+
+/*
  * eph_interp_q with pair screening: pairs (q,k) with no eps_{m,k+q} in [e_lo, e_hi] get g = 0
  * without the band rotation (the only step after eps_{k+q} is known); keep [nq][nk] (int, may
  * be NULL) receives 1 for the pairs computed and 0 for the screened ones.  eps_kq and omega are
- * complete.  FP64 form with nb, nm <= 16; EPH_ENOTSUP otherwise.
+ * complete.  Both forms (in the mixed form the screened pairs skip its double-float band
+ * rotation; g complex64) with nb, nm <= 16; EPH_ENOTSUP otherwise.
  */
 int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, double e_lo, double e_hi, double* eps_kq,
                         double* omega, void* g, int* keep);

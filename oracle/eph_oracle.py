@@ -46,6 +46,10 @@ function below and checks that a pin fails):
     zero-temperature limit (emission only above mu, absorption only below); the omega_min cut,
     positivity and linearity in the q weights.
   * g_bloch_to_wannier (Eq. 6): the round trip above.
+  * grid_points, ibz_time_reversal: the number of kept points (N + N_self)/2 with N_self, the
+    points that are their own partner, counted axis by axis in closed form; weights summing to
+    N; on real-H(Re) inputs eps(partner) = eps(k) and weighted sums over the kept points equal
+    the sums over the whole grid.
 """
 from __future__ import annotations
 
@@ -309,3 +313,35 @@ def linewidths(eps_k, eps_kq, omega, g, wq, kT, mu, sigma, omega_min):
     term = (nB + fm) * gaussian(de + oms, sigma) + (nB + 1.0 - fm) * gaussian(de - oms, sigma)
     contrib = np.where(ok, np.abs(g) ** 2 / (2.0 * oms) * term, 0.0)  # [q][k][nu][m][n]
     return np.pi * np.einsum("q,qkvmn->kn", np.asarray(wq, dtype=np.float64), contrib)
+
+
+# ----------------------------------------------------------------------------
+# Irreducible k list under time reversal (the transport workflow's reduced fine k grid).
+# ----------------------------------------------------------------------------
+def grid_points(n, shift=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """k = (j1/n1, j2/n2, j3/n3) + shift in the order (j1 n2 + j2) n3 + j3 -> [n1 n2 n3][3]."""
+    n1, n2, n3 = n
+    j = np.stack(np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij"), -1).reshape(-1, 3)
+    return j / np.array([n1, n2, n3], dtype=np.float64) + np.asarray(shift, dtype=np.float64)[None, :]
+
+
+def ibz_time_reversal(n, shift=(0.0, 0.0, 0.0)):
+    """(kept grid indices ascending, weights) of the reduction k ~ -k of a uniform grid.
+
+    With real H(Re), H(-k) = conj H(k) and eps(-k) = eps(k), so a grid sum is the weighted sum
+    over one point of each pair {k, -k} (-k taken modulo reciprocal lattice vectors).  Brute
+    force: the partner of each point is the grid point whose coordinates add to an integer
+    vector with it; a point is kept if its index is not above its partner's, with weight 2, or 1
+    if it is its own partner.  Small grids only (all pairs are compared).
+    """
+    pts = grid_points(n, shift)
+    s = pts[:, None, :] + pts[None, :, :]
+    d = np.abs(s - np.rint(s)).max(-1)
+    match = d < 1e-9
+    if not np.all(match.sum(1) == 1):
+        raise ValueError("-k is not on the grid (2 shift n must be an integer on every axis)")
+    partner = match.argmax(1)
+    idx = np.arange(len(pts))
+    keep = idx <= partner
+    w = np.where(partner == idx, 1.0, 2.0)
+    return idx[keep], w[keep]

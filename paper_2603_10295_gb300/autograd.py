@@ -2,6 +2,7 @@
 
     L = EphLoss.apply(g_ReRp, model, kpts, qpts, w_nk, omega_min)
     L.backward()            # g_ReRp.grad = dL/dRe(g) + i dL/dIm(g)
+    # kpts=None: the model's uniform k grid (model.kgrid), sum-factorised Re->k in both directions
 
     g = EphInterp.apply(g_ReRp, model, kpts, qpts)    # [nq][nk][nm][nb][nb]
     any_loss(g).backward()  # through eph_interp_vjp
@@ -63,19 +64,37 @@ def _dev(x, device, dtype):
     return torch.as_tensor(x, dtype=dtype).to(device).contiguous()
 
 
+def _k_points(ctx, model, kpts, dev):
+    """(nk, device k list or None).  kpts None: the model's uniform grid (model.kgrid), made the
+    context's resident k list once, so that the Re->k sums run sum-factorised."""
+    if kpts is not None:
+        kd = _dev(kpts, dev, torch.float64)
+        return kd.shape[0], kd
+    grid = tuple(getattr(model, "kgrid", None) or ())
+    if len(grid) != 3:
+        raise ValueError("kpts=None needs a model with a uniform k grid (model.kgrid)")
+    if getattr(ctx, "_grid", None) != grid or ctx.nk != grid[0] * grid[1] * grid[2]:
+        ctx.eph_set_k_grid(*grid)
+        ctx._grid = grid
+    return ctx.nk, None
+
+
 class EphLoss(torch.autograd.Function):
     @staticmethod
     def forward(fctx, g_ReRp, model, kpts, qpts, w_nk, omega_min):
         dev = _device_of(g_ReRp)
         ctx = model_context(model, dev)
         gW = g_ReRp.detach().to(dev, torch.complex128).contiguous()
-        kd, qd = _dev(kpts, dev, torch.float64), _dev(qpts, dev, torch.float64)
+        qd = _dev(qpts, dev, torch.float64)
         wd = _dev(w_nk, dev, torch.float64)
         L = torch.zeros(1, dtype=torch.float64, device=dev)
         grad = torch.empty(gW.shape, dtype=torch.complex128, device=dev)
         with torch.cuda.device(dev):
             ctx.eph_set_gw(gW)
-            ctx.eph_interp_backward(kd.shape[0], kd, qd.shape[0], qd, wd, float(omega_min), L, grad)
+            nk, kd = _k_points(ctx, model, kpts, dev)
+            ctx.eph_interp_backward(nk, kd, qd.shape[0], qd, wd, float(omega_min), L, grad)
+            if kd is not None:
+                ctx._grid = None   # the call made kpts the resident list
         fctx.save_for_backward(grad.to(g_ReRp.device))
         return L[0].to(g_ReRp.device)
 
@@ -104,6 +123,7 @@ class EphInterp(torch.autograd.Function):
         with torch.cuda.device(dev):
             ctx.eph_set_gw(gW)
             ctx.eph_set_k(nk, kd)
+            ctx._grid = None
             ctx.eph_interp_q(nq, qd, None, None, g)
         fctx.model, fctx.dev, fctx.in_device = model, dev, g_ReRp.device
         fctx.save_for_backward(kd, qd)
@@ -118,4 +138,5 @@ class EphInterp(torch.autograd.Function):
         out = torch.empty((ctx.np_, ctx.nm, ctx.ne, ctx.nb, ctx.nb), dtype=torch.complex128, device=dev)
         with torch.cuda.device(dev):
             ctx.eph_interp_vjp(kd.shape[0], kd, qd.shape[0], qd, gin, out)
+            ctx._grid = None
         return out.to(fctx.in_device), None, None, None

@@ -25,7 +25,7 @@ EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "ep
            "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc",
            "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths", "eph_interp_vjp",
            "eph_set_k_grid", "eph_bloch_to_wannier", "eph_set_k_window", "eph_interp_q_window", "eph_eigh",
-           "eph_create_rp_slice", "eph_g1_partial", "eph_interp_q_g1", "eph_set_gw")
+           "eph_create_rp_slice", "eph_g1_partial", "eph_interp_q_g1", "eph_set_gw", "eph_set_k_grid_ibz")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -113,6 +113,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_interp_q_g1.restype = i
     lib.eph_set_gw.argtypes = [vp, dp]
     lib.eph_set_gw.restype = i
+    lib.eph_set_k_grid_ibz.argtypes = [vp, i, i, i, dp, dp, vp, dp, ctypes.POINTER(i)]
+    lib.eph_set_k_grid_ibz.restype = i
     del ip
     if path is None:
         _lib = lib
@@ -302,12 +304,14 @@ class Context:
                                             _ptr(grad_g_ReRp)))
 
     def vjp(self, kpts, qpts, grad_g):
-        """dL/dg(Re,Rp) for an upstream gradient grad_g [nq][nk][nm][nb][nb] (complex128)."""
-        kpts, qpts = _points(kpts, "kpts"), _points(qpts, "qpts")
-        grad_g = _shaped(grad_g, (len(qpts), len(kpts), self.nm, self.nb, self.nb), np.complex128, "grad_g")
+        """dL/dg(Re,Rp) for an upstream gradient grad_g [nq][nk][nm][nb][nb] (complex128).
+        kpts = None: the resident k list (a uniform grid runs sum-factorised)."""
+        kpts, nk = (None, self.nk) if kpts is None else (_points(kpts, "kpts"), len(kpts))
+        qpts = _points(qpts, "qpts")
+        grad_g = _shaped(grad_g, (len(qpts), nk, self.nm, self.nb, self.nb), np.complex128, "grad_g")
         out = np.empty((self.np_, self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
-        self.eph_interp_vjp(len(kpts), kpts, len(qpts), qpts, grad_g, out)
-        self.nk = len(kpts)   # the call replaces the context's k list
+        self.eph_interp_vjp(nk, kpts, len(qpts), qpts, grad_g, out)
+        self.nk = nk   # the call replaces the context's k list
         return out
 
     def eph_bloch_to_wannier(self, nk, kpts, nq, qpts, g, g_ReRp):
@@ -315,12 +319,14 @@ class Context:
                                                   _ptr(g_ReRp)))
 
     def bloch_to_wannier(self, kpts, qpts, g):
-        """Eq. 6: g(Re,Rp) [np][nm][ne][nb][nb] from g(k',q') [nq][nk][nm][nb][nb] on coarse grids."""
-        kpts, qpts = _points(kpts, "kpts"), _points(qpts, "qpts")
-        g = _shaped(g, (len(qpts), len(kpts), self.nm, self.nb, self.nb), np.complex128, "g")
+        """Eq. 6: g(Re,Rp) [np][nm][ne][nb][nb] from g(k',q') [nq][nk][nm][nb][nb] on coarse grids.
+        kpts = None: the resident k list (e.g. the coarse grid of set_k_grid)."""
+        kpts, nk = (None, self.nk) if kpts is None else (_points(kpts, "kpts"), len(kpts))
+        qpts = _points(qpts, "qpts")
+        g = _shaped(g, (len(qpts), nk, self.nm, self.nb, self.nb), np.complex128, "g")
         out = np.empty((self.np_, self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
-        self.eph_bloch_to_wannier(len(kpts), kpts, len(qpts), qpts, g, out)
-        self.nk = len(kpts)   # the call replaces the context's k list
+        self.eph_bloch_to_wannier(nk, kpts, len(qpts), qpts, g, out)
+        self.nk = nk   # the call replaces the context's k list
         return out
 
     def eph_set_k_window(self, nk, kpts, e_lo, e_hi, eps_k, kidx):
@@ -329,6 +335,23 @@ class Context:
                                               _ptr(kidx), ctypes.byref(n)))
         self.nk = n.value
         return n.value
+
+    def eph_set_k_grid_ibz(self, n1, n2, n3, shift, eps_k, kidx, wk):
+        n = ctypes.c_int(0)
+        sh = None if shift is None else np.ascontiguousarray(shift, dtype=np.float64)
+        self._check(self.lib.eph_set_k_grid_ibz(self.handle, int(n1), int(n2), int(n3), _ptr(sh), _ptr(eps_k),
+                                                _ptr(kidx), _ptr(wk), ctypes.byref(n)))
+        self.nk = n.value
+        return n.value
+
+    def set_k_grid_ibz(self, n1, n2, n3, shift=None):
+        """Time-reversal irreducible half of a uniform grid: (kept grid indices, weights, eps_k)."""
+        nk = int(n1) * int(n2) * int(n3)
+        kidx = np.empty(nk, dtype=np.int32)
+        wk = np.empty(nk)
+        eps = np.empty((nk, self.nb))
+        n = self.eph_set_k_grid_ibz(n1, n2, n3, shift, eps, kidx, wk)
+        return kidx[:n].copy(), wk[:n].copy(), eps[:n].copy()
 
     def set_k_window(self, kpts, e_lo, e_hi):
         """Keeps the k points with a band in [e_lo, e_hi]: (kept indices, their eps_k)."""
@@ -348,7 +371,8 @@ class Context:
         nq = len(qpts)
         eps_kq = np.empty((nq, self.nk, self.nb))
         omega = np.empty((nq, self.nm))
-        g = np.empty((nq, self.nk, self.nm, self.nb, self.nb), dtype=np.complex128)
+        dt = np.complex128 if self.form == "fp64" else np.complex64
+        g = np.empty((nq, self.nk, self.nm, self.nb, self.nb), dtype=dt)
         keep = np.empty((nq, self.nk), dtype=np.int32)
         self.eph_interp_q_window(nq, qpts, e_lo, e_hi, eps_kq, omega, g, keep)
         return eps_kq, omega, g, keep
@@ -412,9 +436,12 @@ class Context:
         return eps_k, eps_kq, omega, g
 
     def loss_and_grad(self, kpts, qpts, w_nk, omega_min):
-        kpts, qpts = _points(kpts, "kpts"), _points(qpts, "qpts")
-        w_nk = _shaped(w_nk, (len(kpts), self.nb), np.float64, "w_nk")
+        """(L, dL/dg(Re,Rp)); kpts = None: the resident k list (a uniform grid runs sum-factorised)."""
+        kpts, nk = (None, self.nk) if kpts is None else (_points(kpts, "kpts"), len(kpts))
+        qpts = _points(qpts, "qpts")
+        w_nk = _shaped(w_nk, (nk, self.nb), np.float64, "w_nk")
         L = np.zeros(1)
         grad = np.empty((self.np_, self.nm, self.ne, self.nb, self.nb), dtype=np.complex128)
-        self.eph_interp_backward(len(kpts), kpts, len(qpts), qpts, w_nk, omega_min, L, grad)
+        self.eph_interp_backward(nk, kpts, len(qpts), qpts, w_nk, omega_min, L, grad)
+        self.nk = nk
         return float(L[0]), grad

@@ -100,6 +100,14 @@ struct eph_ctx {
   // the (hi, lo) float-pair result
   DBuf DBH, sBH, Hpair;
   CUtensorMap mapDA5[5]{}, mapDBH[5]{};
+  // Eq. 9 of the mixed form on the tensor cores: 4 fixed-point BF16 digits of the resident
+  // g(Re,Rp) (real embedding, rows 2X, K = 2 nrp padded to kpp; per-row scales sG), formed once
+  // per g(Re,Rp); 3 digits of the q phases of a batch (128 rows, zero beyond the batch)
+  bool eq9_tc = false;
+  int kpp = 0;          // 2*nrp rounded up to a multiple of 64
+  double scaleP = 1.0;  // power of two >= 2 max |w_p|
+  DBuf DG, sG, DP, G1f;
+  CUtensorMap mapDG[4]{}, mapDP[3]{};
   // shapes beyond the warp kernels (nb or nm > 16): CTA Jacobi work, transposed u, band-rotation temp
   bool big = false;
   bool ws_auto = false;  // workspace_mb left at 0: the k tile may grow to whole eigensolve waves
@@ -131,6 +139,7 @@ struct eph_ctx {
   int gn[3] = {0, 0, 0};
   double gshift[3] = {0.0, 0.0, 0.0};
   DBuf rebox, E1, E2, E3, Wbox, S1, S2;
+  DBuf aS2, aS1, aS0;  // adjoint of the product-grid transforms: after axis 1, axis 2, axis 3
   long long launches = 0;
   std::string err;
   // per-stage event timing
@@ -351,7 +360,8 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut, &ctx->eigA, &ctx->eigW, &ctx->eigV, &ctx->tcband,
                   &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc, &ctx->rebox, &ctx->E1,
                   &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
-                  &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair, &ctx->g1in};
+                  &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair, &ctx->g1in,
+                  &ctx->aS2, &ctx->aS1, &ctx->aS0, &ctx->DG, &ctx->sG, &ctx->DP, &ctx->G1f};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -369,6 +379,19 @@ void eph_destroy(eph_ctx* ctx) {
 }  // extern "C"
 
 namespace {
+// Digits of the resident g(Re,Rp) for the mixed form's tensor-core Eq. 9 (after creation and
+// after eph_set_gw).
+int form_gw_digits(eph_ctx* ctx) {
+  if (!ctx->eq9_tc) return EPH_OK;
+  const long X = (long)ctx->nm * ctx->ne * ctx->nb * ctx->nb;
+  const size_t slice = (size_t)2 * X * ctx->kpp;
+  cudaError_t e = eph::launch_digits_b(ctx->gW, X, 0, 0, (int)X, ctx->nrp, ctx->kpp, 1, static_cast<float*>(ctx->sG.p),
+                                       ctx->DG.p, (long)slice, 4, ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, EPH_ECUDA, "g(Re,Rp) digits", e);
+  ++ctx->launches;
+  return EPH_OK;
+}
+
 int create_impl(eph_ctx** out, int nb, int na, int ne, int np, const double* H_Re, const double* Phi_Rp,
                 const double* g_ReRp, const int* Re, const double* we, const int* Rp, const double* wp,
                 const double* masses, int rp0, int nrp, const eph_options* opt, void* cuda_stream) {
@@ -506,6 +529,38 @@ int create_impl(eph_ctx** out, int nb, int na, int ne, int np, const double* H_R
       }
     }
     ctx->boxable = ok;
+  }
+  // mixed form: Eq. 9 on the tensor cores when the digit planes of g(Re,Rp) stay modest
+  // (4 x 2 bytes per real element of the embedding: 16 X kpp bytes, ~2 x g(Re,Rp) at Si and MoS2
+  // shapes; not for the stanene ribbons' 9.3 GB couplings, whose 15-term sums stay FP64)
+  if (ctx->opt.form == EPH_FORM_MIXED && ctx->opt.mixed_scheme == 0) {
+    const long X = (long)nm * ne * nb2;
+    const int kpp = ((2 * nrp + 63) / 64) * 64;
+    const size_t dbytes = (size_t)16 * X * kpp;
+    const size_t cap = std::min((size_t)4 << 30, ctx->mem_total ? ctx->mem_total / 16 : (size_t)4 << 30);
+    if (kpp <= 1024 && dbytes <= cap && 2 * X <= 2147483647L) {
+      double wmax = 0.0;
+      for (int i = 0; i < np; ++i) wmax = std::fmax(wmax, std::fabs(wp ? wp[i] : 1.0));
+      int ex = 0;
+      const double f = std::frexp(wmax > 0.0 ? wmax : 1.0, &ex);
+      ctx->scaleP = std::ldexp(1.0, f == 0.5 ? ex : ex + 1);  // the least power of two >= 2 max |w_p|
+      ctx->kpp = kpp;
+      ctx->eq9_tc = true;
+      if (ensure(ctx, ctx->DG, dbytes) != EPH_OK || ensure(ctx, ctx->sG, (size_t)2 * X * sizeof(float)) != EPH_OK ||
+          ensure(ctx, ctx->DP, (size_t)3 * 128 * kpp * 2) != EPH_OK ||
+          ensure(ctx, ctx->G1f, (size_t)16 * 2 * X * sizeof(float)) != EPH_OK)
+        return bail(EPH_ENOMEM);
+      if (cudaMemsetAsync(ctx->DP.p, 0, (size_t)3 * 128 * kpp * 2, ctx->stream) != cudaSuccess) return bail(EPH_ECUDA);
+      for (int d = 0; d < 4; ++d)
+        if (eph::make_tc_map_bf16(&ctx->mapDG[d], static_cast<char*>(ctx->DG.p) + (size_t)d * 2 * X * kpp * 2, 2 * X,
+                                  kpp, 128) != cudaSuccess)
+          return bail(EPH_ECUDA);
+      for (int d = 0; d < 3; ++d)
+        if (eph::make_tc_map_bf16(&ctx->mapDP[d], static_cast<char*>(ctx->DP.p) + (size_t)d * 128 * kpp * 2, 128, kpp,
+                                  128) != cudaSuccess)
+          return bail(EPH_ECUDA);
+      if (form_gw_digits(ctx) != EPH_OK) return bail(EPH_ECUDA);
+    }
   }
   // status[0]: Jacobi sweep cap reached; status[1]: tensor-core pipeline wait timed out
   if (cudaMalloc(&ctx->status, 2 * sizeof(int)) != cudaSuccess ||
@@ -657,6 +712,64 @@ extern "C" int eph_set_k_window(eph_ctx* ctx, int nk, const double* kpts, double
   return EPH_OK;
 }
 
+extern "C" int eph_set_k_grid_ibz(eph_ctx* ctx, int n1, int n2, int n3, const double* shift, double* eps_k,
+                                  int* kidx, double* wk, int* nk_kept) {
+  if (!ctx) return EPH_EINVAL;
+  if (n1 < 1 || n2 < 1 || n3 < 1 || (long)n1 * n2 * n3 > 2147483647L || !kidx || !wk || !nk_kept)
+    return fail(ctx, EPH_EINVAL, "eph_set_k_grid_ibz: bad grid size or NULL pointer");
+  if (ctx->opt.async) return fail(ctx, EPH_EINVAL, "eph_set_k_grid_ibz reads the kept count on the host (no async mode)");
+  const int gn[3] = {n1, n2, n3};
+  const double s[3] = {shift ? shift[0] : 0.0, shift ? shift[1] : 0.0, shift ? shift[2] : 0.0};
+  int t[3];
+  for (int d = 0; d < 3; ++d) {  // -k must lie on the grid: 2 s_a n_a an integer
+    const double x = 2.0 * s[d] * gn[d];
+    if (std::fabs(x - std::rint(x)) > 1e-9)
+      return fail(ctx, EPH_EINVAL, "eph_set_k_grid_ibz: 2 * shift * n must be an integer on every axis");
+    t[d] = (int)std::rint(x);
+  }
+  *nk_kept = 0;
+  ctx->k_ready = false;
+  ctx->has_grid = false;
+  const long nk = (long)n1 * n2 * n3;
+  const long nblk = (nk + 1023) / 1024;
+  EPH_TRY(ensure(ctx, ctx->kpts, (size_t)nk * 3 * sizeof(double)));
+  EPH_TRY(ensure(ctx, ctx->scr_flag, (size_t)nk * sizeof(int)));
+  EPH_TRY(ensure(ctx, ctx->scr_pos, (size_t)nk * sizeof(int)));
+  EPH_TRY(ensure(ctx, ctx->scr_tot, (size_t)nblk * sizeof(int)));
+  EPH_TRY(ensure(ctx, ctx->scr_idx, (size_t)nk * sizeof(int)));
+  EPH_TRY(ensure(ctx, ctx->scr_count, sizeof(int)));
+  EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_grid_points(n1, n2, n3, s, as<double>(ctx->kpts), ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_ibz_select(n1, n2, n3, t, as<int>(ctx->scr_flag), as<int>(ctx->scr_pos),
+                                                       as<int>(ctx->scr_tot), as<int>(ctx->scr_idx),
+                                                       as<int>(ctx->scr_count), ctx->stream));
+  int count = 0;
+  EPH_CK(cudaMemcpyAsync(&count, ctx->scr_count.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  EPH_CK(cudaStreamSynchronize(ctx->stream));
+  if (count < 1) return fail(ctx, EPH_ECUDA, "eph_set_k_grid_ibz: empty reduction");
+  // weights next to the kept indices (scr_pos is free again after the compaction)
+  double* wdev = ctx->opt.device_ptrs ? wk : nullptr;
+  DBuf& wbuf = ctx->scr_pos;
+  if (!wdev) {
+    EPH_TRY(ensure(ctx, wbuf, (size_t)count * sizeof(double)));
+    wdev = as<double>(wbuf);
+  }
+  EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_ibz_weights(as<int>(ctx->scr_idx), as<int>(ctx->scr_count), count, n1, n2,
+                                                        n3, t, wdev, ctx->stream));
+  const cudaMemcpyKind kind = ctx->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  EPH_CK(cudaMemcpyAsync(kidx, ctx->scr_idx.p, (size_t)count * sizeof(int), kind, ctx->stream));
+  if (!ctx->opt.device_ptrs)
+    EPH_CK(cudaMemcpyAsync(wk, wdev, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  // the kept points become the resident k list
+  EPH_TRY(ensure(ctx, ctx->scr_k, (size_t)count * 3 * sizeof(double)));
+  EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_gather_points(as<double>(ctx->kpts), as<int>(ctx->scr_idx), count,
+                                                          as<double>(ctx->scr_k), ctx->stream));
+  EPH_CK(cudaMemcpyAsync(ctx->kpts.p, ctx->scr_k.p, (size_t)count * 3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+  EPH_TRY(set_k_resident(ctx, count, eps_k));
+  *nk_kept = count;
+  return EPH_OK;
+}
+
 namespace {
 // H(k), its eigenpairs and the k-side operands for the k list already in ctx->kpts.
 int set_k_resident(eph_ctx* ctx, int nk, double* eps_k) {
@@ -795,7 +908,18 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
                                                   as<double2>(ctx->uq), ctx->stream));
   // Eq. 9: G1 = sum_Rp w_p e^{i q.Rp} g(Re,Rp) over the Rp vectors of the resident slice
   const double2* G1src = g1_in;
-  if (!G1src) {
+  if (!G1src && ctx->eq9_tc) {
+    // mixed form: G1 = P_q g as a tensor-core product of 3 phase digits and 4 digits of g(Re,Rp)
+    // (rows of the real embedding of g, per-row scales), FP32 accumulation, then to complex128
+    EPH_LAUNCH_S(EPH_STAGE_FT_Q, eph::launch_digits_a(Pp + ctx->rp0, np, nqb, ctx->nrp, ctx->kpp, ctx->scaleP, 3,
+                                                      ctx->DP.p, ctx->stream, 128));
+    EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_tc_fixed_gemm(ctx->mapDP, ctx->mapDG, nqb, 0, (int)(2 * p.X), ctx->kpp, 1,
+                                                      (float)ctx->scaleP, as<float>(ctx->sG), as<float>(ctx->G1f),
+                                                      2 * p.X, 0, ctx->status + 1, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_FT_Q, eph::launch_f32pairs_to_c128(as<float2>(ctx->G1f), (long)nqb * p.X,
+                                                              as<double2>(ctx->G1), ctx->stream));
+    G1src = as<double2>(ctx->G1);
+  } else if (!G1src) {
     EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, p.X, ctx->nrp, Pp + ctx->rp0, np, ctx->gW, p.X,
                                                as<double2>(ctx->G1), p.X, ctx->stream));
     G1src = as<double2>(ctx->G1);
@@ -877,7 +1001,7 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
   const bool mixed = ctx->opt.form == EPH_FORM_MIXED;  // complex64 g, sgq in elements
   if (mixed && !ctx->big) {
     EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_rotate_ff_f64(Y + nb2, p.NW, Ukq, Uk, nqb, nkt, nm, nb,
-                                                               reinterpret_cast<float2*>(out), sgq, ctx->stream));
+                                                               reinterpret_cast<float2*>(out), sgq, ctx->stream, keep));
     return EPH_OK;
   }
   if (!ctx->big) {
@@ -998,7 +1122,19 @@ int prepare_mixed(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
 
 // Mixed form: H(k+q) and every eigensolve in FP64; the Re->k contraction of g as a
 // split-TF32 tensor-core GEMM with FP32 accumulation; FP32 band rotation; complex64 g.
-int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g) {
+struct Window;
+int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g,
+                   const Window* win = nullptr);
+}  // namespace
+
+namespace {
+struct Window {
+  double lo, hi;
+  int* keep;  // [nq][nk] caller buffer, may be NULL
+};
+
+int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double* omega, void* g,
+                   const Window* win) {
   const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, nk = ctx->nk, kp = ctx->kp;
   const int nb2 = nb * nb;
   const long nr = ctx->nr;
@@ -1006,6 +1142,7 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
   const long gcols = (long)nm * nb2;
   QPlan p;
   EPH_TRY(prepare_mixed(ctx, nq, g != nullptr, &p));
+  if (win) EPH_TRY(ensure(ctx, ctx->scr_flag, (size_t)p.QB * p.KT * sizeof(int)));
   const void* dq = nullptr;
   EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
   const bool digits = ctx->opt.mixed_scheme == 0;
@@ -1065,6 +1202,16 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
           EPH_CK(cudaMemcpyAsync(eps_kq + ((long)(q0 + iq) * nk + k0) * nb,
                                  as<double>(ctx->eps_tile) + (long)iq * nkt * nb, (size_t)nkt * nb * sizeof(double),
                                  out_kind(ctx), ctx->stream));
+      const int* keep = nullptr;
+      if (win) {  // pair flags from the tile's eps_{k+q}: screened pairs skip the band rotation
+        EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_window_flags(as<double>(ctx->eps_tile), (long)nqb * nkt, nb, win->lo,
+                                                              win->hi, as<int>(ctx->scr_flag), ctx->stream));
+        keep = as<int>(ctx->scr_flag);
+        if (win->keep)
+          for (int iq = 0; iq < nqb; ++iq)
+            EPH_CK(cudaMemcpyAsync(win->keep + (long)(q0 + iq) * nk + k0, keep + (long)iq * nkt,
+                                   (size_t)nkt * sizeof(int), out_kind(ctx), ctx->stream));
+      }
       if (!g) continue;
       // G3 = P_k G2 on the tensor cores (FP32 result)
       if (digits)
@@ -1090,7 +1237,8 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
       } else if (host) {
         EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate_ff(as<float>(ctx->G3f), nr, as<double2>(ctx->Ukq),
                                                             as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
-                                                            as<float>(ctx->g_stage32), 2L * nkt * gcols, ctx->stream));
+                                                            as<float>(ctx->g_stage32), 2L * nkt * gcols, ctx->stream,
+                                                            keep));
         for (int iq = 0; iq < nqb; ++iq)
           EPH_CK(cudaMemcpyAsync(gout + 2L * ((long)(q0 + iq) * nk + k0) * gcols,
                                  as<float>(ctx->g_stage32) + 2L * iq * nkt * gcols,
@@ -1099,7 +1247,7 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
         EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate_ff(as<float>(ctx->G3f), nr, as<double2>(ctx->Ukq),
                                                             as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
                                                             gout + 2L * ((long)q0 * nk + k0) * gcols, 2L * nk * gcols,
-                                                            ctx->stream));
+                                                            ctx->stream, keep));
       }
     }
   }
@@ -1140,11 +1288,6 @@ int ensure_copy_stream(eph_ctx* ctx) {
   EPH_CK(cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming));
   return EPH_OK;
 }
-
-struct Window {
-  double lo, hi;
-  int* keep;  // [nq][nk] caller buffer, may be NULL
-};
 
 // The forward path of the FP64 form (and of the mixed form on a product k grid or beyond the
 // warp shapes).  win: pairs (q,k) with no eps_{m,k+q} in [lo, hi] are screened out of the band
@@ -1287,6 +1430,7 @@ extern "C" int eph_set_gw(eph_ctx* ctx, const double* g_ReRp) {
   EPH_CK(cudaMemcpyAsync(ctx->gW, g_ReRp, bytes, ctx->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          ctx->stream));
   if (!ctx->opt.device_ptrs) EPH_CK(cudaStreamSynchronize(ctx->stream));  // the host buffer may go on return
+  EPH_TRY(form_gw_digits(ctx));
   return finish(ctx);
 }
 
@@ -1311,10 +1455,14 @@ extern "C" int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, dou
   if (!ctx) return EPH_EINVAL;
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q_window before eph_set_k");
   if (nq < 1 || !qpts || !(e_lo <= e_hi)) return fail(ctx, EPH_EINVAL, "eph_interp_q_window: bad arguments");
-  if (ctx->opt.form != EPH_FORM_FP64 || ctx->big)
-    return fail(ctx, EPH_ENOTSUP, "eph_interp_q_window: FP64 form with nb, nm <= 16");
+  if (ctx->big) return fail(ctx, EPH_ENOTSUP, "eph_interp_q_window: nb, nm <= 16");
   if (!whole_g(ctx)) return fail(ctx, EPH_ESTATE, "eph_interp_q_window on an Rp-slice context");
   const Window w{e_lo, e_hi, keep};
+  if (mixed_list(ctx)) {  // the mixed form's tensor-core k-list path
+    if (ctx->opt.async && !ctx->opt.device_ptrs)
+      return fail(ctx, EPH_EINVAL, "async mode with host pointers: FP64 form or grid path only");
+    return interp_q_mixed(ctx, nq, qpts, eps_kq, omega, g, &w);
+  }
   return interp_fp64(ctx, nq, qpts, eps_kq, omega, g, &w);
 }
 
@@ -1325,14 +1473,73 @@ extern "C" int eph_interp(eph_ctx* ctx, int nk, const double* kpts, int nq, cons
   return eph_interp_q(ctx, nq, qpts, eps_kq, omega, g);
 }
 
+namespace {
+// Adjoint of the Re->k contraction of one k tile, accumulated over the tiles of a q batch:
+//   G2bar[q][e][c] (+)= sum_{k in tile} conj(Pk[k][e]) G3bar[q][k][c],
+// with G3bar in the G part of Y (row stride NW).  On a product k grid the sum is the transpose of
+// the three axis transforms: the axis-1 part runs per tile (slabs of j1) into aS2, and
+// adj_k_finish adds axes 2 and 3 and gathers the Re rows; on a k list it is one GEMM per tile.
+int adj_workspace(eph_ctx* ctx, const QPlan& p) {
+  if (!ctx->has_grid) return EPH_OK;
+  const long B1 = ctx->bext[0], B2 = ctx->bext[1], B3 = ctx->bext[2];
+  const long N2 = ctx->gn[1], N3 = ctx->gn[2];
+  EPH_TRY(ensure(ctx, ctx->aS2, (size_t)p.QB * B1 * N2 * N3 * p.gcols * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->aS1, (size_t)p.QB * B1 * B2 * N3 * p.gcols * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->aS0, (size_t)p.QB * B1 * B2 * B3 * p.gcols * sizeof(double2)));
+  return EPH_OK;
+}
+
+int adj_k_tile(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt, const double2* Pk, double2* G2b) {
+  double2* Y = as<double2>(ctx->Y);
+  const int nb2 = ctx->nb * ctx->nb, ne = ctx->ne;
+  if (ctx->has_grid) {
+    const long slab = (long)ctx->gn[1] * ctx->gn[2];
+    const int j0 = (int)(k0 / slab), nj = (int)(nkt / slab), B1 = ctx->bext[0];
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_axis_adj(Y + nb2, (long)nkt * p.NW, slab * p.NW, p.NW, nqb, (int)slab,
+                                                     (int)p.gcols, B1, as<double2>(ctx->E1), j0, nj,
+                                                     as<double2>(ctx->aS2), (long)B1 * slab * p.gcols,
+                                                     slab * p.gcols, p.gcols, k0 > 0, ctx->stream));
+    return EPH_OK;
+  }
+  EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ne, (int)p.gcols, nkt, Pk + k0 * ne, ne, 0, Y + nb2, p.NW,
+                                              (long)nkt * p.NW, G2b, p.gcols, (long)ne * p.gcols, nqb, k0 > 0,
+                                              ctx->stream));
+  return EPH_OK;
+}
+
+// weighted: multiply by w_e (the weighted phases of the interpolation); else weights 1 (Eq. 6)
+int adj_k_finish(eph_ctx* ctx, const QPlan& p, int nqb, double2* G2b, bool weighted) {
+  if (!ctx->has_grid) return EPH_OK;
+  const int B1 = ctx->bext[0], B2 = ctx->bext[1], B3 = ctx->bext[2];
+  const int N2 = ctx->gn[1], N3 = ctx->gn[2];
+  const long C = p.gcols;
+  EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_axis_adj(as<double2>(ctx->aS2), (long)N2 * N3 * C, (long)N3 * C, 0,
+                                                   nqb * B1, 1, (int)(N3 * C), B2, as<double2>(ctx->E2), 0, N2,
+                                                   as<double2>(ctx->aS1), (long)B2 * N3 * C, (long)N3 * C, 0, 0,
+                                                   ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_axis_adj(as<double2>(ctx->aS1), (long)N3 * C, C, 0, nqb * B1 * B2, 1,
+                                                   (int)C, B3, as<double2>(ctx->E3), 0, N3, as<double2>(ctx->aS0),
+                                                   (long)B3 * C, C, 0, 0, ctx->stream));
+  const long vol = (long)B1 * B2 * B3;
+  EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_box_gather(as<double2>(ctx->aS0), vol * C, (int)C, as<int>(ctx->rebox),
+                                                     weighted ? ctx->we : nullptr, ctx->ne, G2b, (long)ctx->ne * C,
+                                                     nqb, ctx->stream));
+  return EPH_OK;
+}
+}  // namespace
+
 extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
                                    const double* w_nk, double omega_min, double* L_out, double* grad_g_ReRp) {
   if (!ctx) return EPH_EINVAL;
-  if (nk < 1 || nq < 1 || !kpts || !qpts || !w_nk || !L_out || !grad_g_ReRp)
+  if (nk < 1 || nq < 1 || !qpts || !w_nk || !L_out || !grad_g_ReRp)
     return fail(ctx, EPH_EINVAL, "eph_interp_backward: bad size or NULL pointer");
   if (ctx->big) return fail(ctx, EPH_ENOTSUP, "eph_interp_backward supports nb, nm <= 16");
   if (!whole_g(ctx)) return fail(ctx, EPH_ESTATE, "eph_interp_backward on an Rp-slice context");
-  EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
+  if (kpts) {
+    EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
+  } else if (!ctx->k_ready || nk != ctx->nk) {
+    return fail(ctx, EPH_ESTATE, "eph_interp_backward with kpts NULL needs the resident k list (nk = its size)");
+  }
   const int nb = ctx->nb, nm = ctx->nm, ne = ctx->ne, np = ctx->np;
   const int nb2 = nb * nb;
   const bool host = !ctx->opt.device_ptrs;
@@ -1346,6 +1553,7 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
   EPH_TRY(ensure(ctx, ctx->G1bar, (size_t)p.QB * p.X * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->Lpair, (size_t)p.QB * p.KT * sizeof(double)));
   EPH_TRY(ensure(ctx, ctx->Lacc, sizeof(double)));
+  EPH_TRY(adj_workspace(ctx, p));
   double2* grad = nullptr;
   const size_t gbytes = (size_t)np * p.X * sizeof(double2);
   if (host) {
@@ -1375,10 +1583,9 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
       EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_sum_into(as<double>(ctx->Lpair), (long)nqb * nkt, as<double>(ctx->Lacc),
                                                   ctx->stream));
       // G2bar[q] (+)= P_k^H G3bar  over this k tile
-      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ne, (int)p.gcols, nkt, as<double2>(ctx->Pk) + k0 * ne, ne, 0,
-                                                  Y + nb2, p.NW, (long)nkt * p.NW, G2b, p.gcols, (long)ne * p.gcols,
-                                                  nqb, k0 > 0, ctx->stream));
+      EPH_TRY(adj_k_tile(ctx, p, nqb, k0, nkt, as<double2>(ctx->Pk), G2b));
     }
+    EPH_TRY(adj_k_finish(ctx, p, nqb, G2b, true));
     // G1bar = conj(u) G2bar (mode rotation adjoint), then grad += P_q(Rp)^H G1bar
     EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_mode_rotate_adj(G2b, as<double2>(ctx->uq), nqb, nm, ne, nb2,
                                                        as<double2>(ctx->G1bar), ctx->stream));
@@ -1398,7 +1605,11 @@ namespace {
 // and 1/(ne np)).
 int adjoint_chain(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts, const void* xin,
                   double* out_ReRp, bool eq6) {
-  EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
+  if (kpts) {
+    EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
+  } else if (!ctx->k_ready || nk != ctx->nk) {
+    return fail(ctx, EPH_ESTATE, "kpts NULL needs the resident k list (nk = its size)");
+  }
   const int nb = ctx->nb, ne = ctx->ne, np = ctx->np, nm = ctx->nm;
   const int nb2 = nb * nb;
   const bool host = !ctx->opt.device_ptrs;
@@ -1409,6 +1620,7 @@ int adjoint_chain(eph_ctx* ctx, int nk, const double* kpts, int nq, const double
   EPH_TRY(ensure_q_workspace(ctx, p));
   EPH_TRY(ensure(ctx, ctx->G2bar, (size_t)p.QB * p.X * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->G1bar, (size_t)p.QB * p.X * sizeof(double2)));
+  EPH_TRY(adj_workspace(ctx, p));
   if (host) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)p.QB * p.KT * gcols * sizeof(double2)));
   const double2* Pk = as<double2>(ctx->Pk);
   if (eq6) {  // unweighted phases of Eq. 6 and the per-mode factors M / (ne np)
@@ -1464,10 +1676,9 @@ int adjoint_chain(eph_ctx* ctx, int nk, const double* kpts, int nq, const double
       }
       EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_band_vjp(Y + nb2, p.NW, gb, sgq, as<double2>(ctx->Ukq),
                                                   as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb, ctx->stream));
-      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ne, (int)p.gcols, nkt, Pk + k0 * ne, ne, 0, Y + nb2, p.NW,
-                                                  (long)nkt * p.NW, G2b, p.gcols, (long)ne * p.gcols, nqb, k0 > 0,
-                                                  ctx->stream));
+      EPH_TRY(adj_k_tile(ctx, p, nqb, k0, nkt, Pk, G2b));
     }
+    EPH_TRY(adj_k_finish(ctx, p, nqb, G2b, !eq6));
     EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_mode_rotate_adj(G2b, as<double2>(ctx->uq), nqb, nm, ne, nb2,
                                                        as<double2>(ctx->G1bar), ctx->stream));
     if (eq6)
@@ -1484,7 +1695,7 @@ int adjoint_chain(eph_ctx* ctx, int nk, const double* kpts, int nq, const double
 extern "C" int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
                               const void* grad_g, double* grad_g_ReRp) {
   if (!ctx) return EPH_EINVAL;
-  if (nk < 1 || nq < 1 || !kpts || !qpts || !grad_g || !grad_g_ReRp)
+  if (nk < 1 || nq < 1 || !qpts || !grad_g || !grad_g_ReRp)
     return fail(ctx, EPH_EINVAL, "eph_interp_vjp: bad size or NULL pointer");
   if (ctx->big || ctx->opt.form != EPH_FORM_FP64)
     return fail(ctx, EPH_ENOTSUP, "eph_interp_vjp: FP64 form with nb, nm <= 16");
@@ -1494,7 +1705,7 @@ extern "C" int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, 
 extern "C" int eph_bloch_to_wannier(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
                                     const void* g, double* g_ReRp) {
   if (!ctx) return EPH_EINVAL;
-  if (nk < 1 || nq < 1 || !kpts || !qpts || !g || !g_ReRp)
+  if (nk < 1 || nq < 1 || !qpts || !g || !g_ReRp)
     return fail(ctx, EPH_EINVAL, "eph_bloch_to_wannier: bad size or NULL pointer");
   if (ctx->big || ctx->opt.form != EPH_FORM_FP64)
     return fail(ctx, EPH_ENOTSUP, "eph_bloch_to_wannier: FP64 form with nb, nm <= 16");

@@ -104,6 +104,13 @@ cudaError_t launch_box_scatter(const double2* W, long sWq, long ldw, int ne, int
                                const double* we, double2* Wbox, long sBq, int nq, cudaStream_t st);
 // out[a][j - j0][c] = sum_b E[j][b] in[a][b][c], a < A, c < C, b < B <= 33 (paired: whole unshifted
 // axis, B odd)
+// out[a][b][r][c] (+)= sum_j conj(E[j0 + j][b]) in[a][j][r][c]  (adjoint of one axis transform)
+cudaError_t launch_axis_adj(const double2* in, long sa_in, long sj_in, long ldr_in, int A, int R, int CC, int B,
+                            const double2* E, int j0, int nj, double2* out, long sa_out, long sb_out, long ldr_out,
+                            int accumulate, cudaStream_t st);
+// G[q][e][c] = w_e Sbox[q][box[e]][c]  (adjoint of the box scatter; we = NULL: weights 1)
+cudaError_t launch_box_gather(const double2* Sbox, long sBq, int ncols, const int* box, const double* we, int ne,
+                              double2* G, long sGq, int nq, cudaStream_t st);
 cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
                             int nj, int paired, double2* out, long sa_out, cudaStream_t st);
 
@@ -115,6 +122,11 @@ cudaError_t launch_window_select(const double* eps, long nk, int nb, double e_lo
 cudaError_t launch_window_flags(const double* eps, long n, int nb, double e_lo, double e_hi, int* flag,
                                 cudaStream_t st);
 // out[j] = kpts[idx[j]] (3 doubles each)
+// time-reversal reduction of a uniform grid: kept indices (ascending) and their weights (1 or 2)
+cudaError_t launch_ibz_select(int n1, int n2, int n3, const int* t, int* flag, int* pos, int* tot, int* idx,
+                              int* count, cudaStream_t st);
+cudaError_t launch_ibz_weights(const int* idx, const int* count, int n_max, int n1, int n2, int n3, const int* t,
+                               double* w, cudaStream_t st);
 cudaError_t launch_gather_points(const double* kpts, const int* idx, int n, double* out, cudaStream_t st);
 
 // ---- fused consumer: electron linewidths from each (q,k) tile without writing g -----------
@@ -160,14 +172,16 @@ cudaError_t launch_split_b(const double2* W, long ldw, long sW, int col0, int nc
                            float* Bhi, float* Blo, cudaStream_t st);
 // Band rotation with double-float accumulation (FP64 gauges as float pairs), complex64 out.
 cudaError_t launch_band_rotate_ff(const float* Y, long ldy_floats, const double2* Ukq, const double2* Uk, int nq,
-                                  int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st);
+                                  int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st, const int* keep = nullptr);
 // the same from complex128 G3 rows (product-grid path of the mixed form); g complex64, sgq in elements
 cudaError_t launch_band_rotate_ff_f64(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
-                                      int nm, int nb, float2* g, long sgq, cudaStream_t st);
+                                      int nm, int nb, float2* g, long sgq, cudaStream_t st, const int* keep = nullptr);
 // Fixed-point BF16 digits (A: 3, B: 4 per value; exact tensor-core accumulation); D slices of n*kp / slice.
 cudaError_t make_tc_map_bf16(void* map_out, const void* base, long rows, int kp, int box_rows);
 cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, double scale, int ndig, void* D,
-                            cudaStream_t st);
+                            cudaStream_t st, int plane_rows = 0);
+// complex64 as float pairs -> complex128
+cudaError_t launch_f32pairs_to_c128(const float2* X, long n, double2* Y, cudaStream_t st);
 cudaError_t launch_digits_b(const double2* W, long ldw, long sW, int col0, int ncols, int ne, int kp, int nq,
                             float* sB, void* D, long slice, int ndig, cudaStream_t st);
 // complex128 H[i] = (hi + lo of real output 2i, hi + lo of 2i + 1), i < n

@@ -163,6 +163,108 @@ cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B,
   }
 }
 
+// Adjoint of one axis transform (the Re <- k direction of the backward pass, Eq. 10 transposed):
+//   out[a][b][r][c] (+)= sum_{j0 <= j < j0 + nj} conj(E[j][b]) in[a][j - j0][r][c]
+// for every slot b < B, row r < R and column c < CC.  One thread per (a, r, c) keeps the B
+// complex accumulators in registers and streams the nj inputs once; conj(E) comes from shared
+// memory.  Four DFMA per (j, b) and output column.
+template <int BMAX>
+__global__ void __launch_bounds__(256) k_axis_adj(const double2* __restrict__ in, long sa_in, long sj_in, long ldr_in,
+                                                  int R, int CC, const double2* __restrict__ E, int j0, int nj,
+                                                  double2* __restrict__ out, long sa_out, long sb_out, long ldr_out,
+                                                  int accumulate) {
+  extern __shared__ double2 es[];  // [nj][BMAX]
+  const int a = blockIdx.y;
+  for (int t = threadIdx.x; t < nj * BMAX; t += blockDim.x) es[t] = E[(long)j0 * BMAX + t];
+  __syncthreads();
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)R * CC) return;
+  const int r = (int)(idx / CC), c = (int)(idx - (long)r * CC);
+  double ar[BMAX], ai[BMAX];
+  double2* dst = out + (long)a * sa_out + (long)r * ldr_out + c;
+#pragma unroll
+  for (int b = 0; b < BMAX; ++b) {
+    if (accumulate) {
+      const double2 v = dst[(long)b * sb_out];
+      ar[b] = v.x;
+      ai[b] = v.y;
+    } else {
+      ar[b] = 0.0;
+      ai[b] = 0.0;
+    }
+  }
+  const double2* src = in + (long)a * sa_in + (long)r * ldr_in + c;
+  for (int j = 0; j < nj; ++j) {
+    const double2 x = src[(long)j * sj_in];
+    const double2* e = es + j * BMAX;
+#pragma unroll
+    for (int b = 0; b < BMAX; ++b) {  // conj(e) x
+      const double2 w = e[b];
+      ar[b] = fma(w.x, x.x, ar[b]);
+      ar[b] = fma(w.y, x.y, ar[b]);
+      ai[b] = fma(w.x, x.y, ai[b]);
+      ai[b] = fma(-w.y, x.x, ai[b]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < BMAX; ++b) dst[(long)b * sb_out] = make_double2(ar[b], ai[b]);
+}
+
+cudaError_t launch_axis_adj(const double2* in, long sa_in, long sj_in, long ldr_in, int A, int R, int CC, int B,
+                            const double2* E, int j0, int nj, double2* out, long sa_out, long sb_out, long ldr_out,
+                            int accumulate, cudaStream_t st) {
+  if (A <= 0 || R <= 0 || CC <= 0 || nj <= 0) return cudaSuccess;
+  if (B < 1 || B > 33 || (B & 1) == 0 || A > 65535 || j0 < 0) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)nj * B * sizeof(double2);
+  if (smem > 160 * 1024) return cudaErrorInvalidValue;
+  const long cols = (long)R * CC;
+  const dim3 grid((unsigned)((cols + 255) / 256), (unsigned)A, 1);
+  auto go = [&](auto kern) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, 256, smem, st>>>(in, sa_in, sj_in, ldr_in, R, CC, E, j0, nj, out, sa_out, sb_out, ldr_out,
+                                  accumulate);
+    return cudaGetLastError();
+  };
+  switch (B) {
+#define EPH_AXIS_ADJ_B(V) \
+  case V:                 \
+    return go(k_axis_adj<V>);
+    EPH_AXIS_ADJ_B(1) EPH_AXIS_ADJ_B(3) EPH_AXIS_ADJ_B(5) EPH_AXIS_ADJ_B(7) EPH_AXIS_ADJ_B(9) EPH_AXIS_ADJ_B(11)
+    EPH_AXIS_ADJ_B(13) EPH_AXIS_ADJ_B(15) EPH_AXIS_ADJ_B(17) EPH_AXIS_ADJ_B(19) EPH_AXIS_ADJ_B(21)
+    EPH_AXIS_ADJ_B(23) EPH_AXIS_ADJ_B(25) EPH_AXIS_ADJ_B(27) EPH_AXIS_ADJ_B(29) EPH_AXIS_ADJ_B(31)
+    EPH_AXIS_ADJ_B(33)
+#undef EPH_AXIS_ADJ_B
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+// The adjoint of the box scatter: G[q][e][c] = w_e Sbox[q][box[e]][c] (w = NULL: 1).
+__global__ void k_box_gather(const double2* __restrict__ Sbox, long sBq, int ncols, const int* __restrict__ box,
+                             const double* __restrict__ we, int ne, double2* __restrict__ G, long sGq, int nq) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long per_q = (long)ne * ncols;
+  if (idx >= per_q * nq) return;
+  const int q = (int)(idx / per_q);
+  const long rem = idx - (long)q * per_q;
+  const int e = (int)(rem / ncols);
+  const int c = (int)(rem - (long)e * ncols);
+  const double2 v = Sbox[q * sBq + (long)box[e] * ncols + c];
+  const double w = we ? we[e] : 1.0;
+  G[q * sGq + rem] = make_double2(w * v.x, w * v.y);
+}
+
+cudaError_t launch_box_gather(const double2* Sbox, long sBq, int ncols, const int* box, const double* we, int ne,
+                              double2* G, long sGq, int nq, cudaStream_t st) {
+  const long total = (long)nq * ne * ncols;
+  if (total <= 0) return cudaSuccess;
+  k_box_gather<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Sbox, sBq, ncols, box, we, ne, G, sGq, nq);
+  return cudaGetLastError();
+}
+
 // kpts[(j1 n2 + j2) n3 + j3] = (j1/n1 + s1, j2/n2 + s2, j3/n3 + s3)
 __global__ void k_grid_points(int n1, int n2, int n3, double s1, double s2, double s3, double* __restrict__ k) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -87,7 +87,7 @@ cudaError_t launch_split_b(const double2* W, long ldw, long sW, int col0, int nc
 // (A: all rows share sA).
 // A digits: P[n][ne] complex128 (row stride ldp) -> D[ndig][n][kp] bf16 (slice stride n*kp).
 __global__ void k_digits_a(const double2* __restrict__ P, long ldp, int n, int ne, int kp, double inv_s, int ndig,
-                           __nv_bfloat16* __restrict__ D) {
+                           __nv_bfloat16* __restrict__ D, long plane) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long tot = (long)n * kp;
   if (idx >= tot) return;
@@ -102,19 +102,34 @@ __global__ void k_digits_a(const double2* __restrict__ P, long ldp, int n, int n
   double y = x * inv_s * 256.0, sc = 1.0;
   for (int d = 0; d < ndig; ++d) {
     const double a = rint(y);
-    D[d * tot + idx] = __float2bfloat16_rn((float)(a * sc));
+    D[d * plane + idx] = __float2bfloat16_rn((float)(a * sc));
     y = (y - a) * 256.0;
     sc *= 0x1p-8;
   }
 }
 
 cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, double scale, int ndig, void* D,
-                            cudaStream_t st) {
+                            cudaStream_t st, int plane_rows) {
   const long tot = (long)n * kp;
   if (tot <= 0) return cudaSuccess;
-  if (ndig < 1 || ndig > 5) return cudaErrorInvalidValue;
+  if (ndig < 1 || ndig > 5 || (plane_rows > 0 && plane_rows < n)) return cudaErrorInvalidValue;
+  const long plane = plane_rows > 0 ? (long)plane_rows * kp : tot;
   k_digits_a<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, ldp, n, ne, kp, 1.0 / scale, ndig,
-                                                          static_cast<__nv_bfloat16*>(D));
+                                                          static_cast<__nv_bfloat16*>(D), plane);
+  return cudaGetLastError();
+}
+
+// complex64 stored as float pairs (re, im) -> complex128
+__global__ void k_f32pairs_to_c128(const float2* __restrict__ X, long n, double2* __restrict__ Y) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float2 v = X[i];
+  Y[i] = make_double2((double)v.x, (double)v.y);
+}
+
+cudaError_t launch_f32pairs_to_c128(const float2* X, long n, double2* Y, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_f32pairs_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, n, Y);
   return cudaGetLastError();
 }
 
@@ -257,9 +272,15 @@ template <typename TIn>
 __global__ void __launch_bounds__(128) k_band_rotate_ff(const TIn* __restrict__ Y, long ldy,
                                                         const double2* __restrict__ Ukq,
                                                         const double2* __restrict__ Uk, int nk, int nm, int nb,
-                                                        float2* __restrict__ g, long sgq) {
+                                                        float2* __restrict__ g, long sgq,
+                                                        const int* __restrict__ keep) {
   extern __shared__ float2 smf2[];
   const int nb2 = nb * nb;
+  if (keep && !keep[blockIdx.x]) {  // screened pair (uniform over the CTA): g = 0, no arithmetic
+    float2* out = g + (long)(blockIdx.x / nk) * sgq + (long)(blockIdx.x % nk) * nm * nb2;
+    for (int t = threadIdx.x; t < nm * nb2; t += blockDim.x) out[t] = make_float2(0.f, 0.f);
+    return;
+  }
   float2* ukr = smf2;            // [nb2] (hi, lo) of Re V_k
   float2* uki = ukr + nb2;       // [nb2] (hi, lo) of Im V_k
   float2* uqr = uki + nb2;
@@ -315,7 +336,7 @@ __global__ void __launch_bounds__(128) k_band_rotate_ff(const TIn* __restrict__ 
 }
 
 cudaError_t launch_band_rotate_ff(const float* Y, long ldy_floats, const double2* Ukq, const double2* Uk, int nq,
-                                  int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st) {
+                                  int nk, int nm, int nb, float* g, long sgq_floats, cudaStream_t st, const int* keep) {
   const long pairs = (long)nq * nk;
   if (pairs <= 0) return cudaSuccess;
   const size_t smem = (size_t)(4 * nb * nb + 3 * nm * nb * nb) * sizeof(float2);
@@ -328,12 +349,12 @@ cudaError_t launch_band_rotate_ff(const float* Y, long ldy_floats, const double2
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
   k_band_rotate_ff<float2><<<(unsigned)pairs, 128, smem, st>>>(reinterpret_cast<const float2*>(Y), ldy_floats / 2, Ukq,
                                                                 Uk, nk, nm, nb, reinterpret_cast<float2*>(g),
-                                                                sgq_floats / 2);
+                                                                sgq_floats / 2, keep);
   return cudaGetLastError();
 }
 
 cudaError_t launch_band_rotate_ff_f64(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
-                                      int nm, int nb, float2* g, long sgq, cudaStream_t st) {
+                                      int nm, int nb, float2* g, long sgq, cudaStream_t st, const int* keep) {
   const long pairs = (long)nq * nk;
   if (pairs <= 0) return cudaSuccess;
   const size_t smem = (size_t)(4 * nb * nb + 3 * nm * nb * nb) * sizeof(float2);
@@ -344,7 +365,7 @@ cudaError_t launch_band_rotate_ff_f64(const double2* Y, long ldy, const double2*
     if (e != cudaSuccess) return e;
   }
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
-  k_band_rotate_ff<double2><<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq);
+  k_band_rotate_ff<double2><<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq, keep);
   return cudaGetLastError();
 }
 

@@ -83,6 +83,56 @@ __global__ void k_gather_points(const double* __restrict__ kpts, const int* __re
   out[3L * j + 2] = kpts[3 * s + 2];
 }
 
+// Time-reversal reduction of a uniform k grid (the irreducible k list of the paper's transport
+// workflow, for Hamiltonians with real H(Re), where H(-k) = conj H(k) and eps(-k) = eps(k)).
+// Grid point i = (j1 n2 + j2) n3 + j3 at k = j/n + s; its partner -k lies on the grid at
+// j'_a = (-j_a - t_a) mod n_a, t_a = 2 s_a n_a (an integer).  i is kept if i <= partner(i); a kept
+// point stands for itself and its partner: weight 2, or 1 if it is its own partner.
+__device__ __forceinline__ long ibz_partner(long i, int n1, int n2, int n3, int t1, int t2, int t3) {
+  const int j3 = (int)(i % n3);
+  const long r = i / n3;
+  const int j2 = (int)(r % n2), j1 = (int)(r / n2);
+  auto neg = [](int j, int t, int n) {
+    int m = (-j - t) % n;
+    return m < 0 ? m + n : m;
+  };
+  return ((long)neg(j1, t1, n1) * n2 + neg(j2, t2, n2)) * n3 + neg(j3, t3, n3);
+}
+
+__global__ void k_ibz_flags(int n1, int n2, int n3, int t1, int t2, int t3, int* __restrict__ flag) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long nk = (long)n1 * n2 * n3;
+  if (i >= nk) return;
+  flag[i] = i <= ibz_partner(i, n1, n2, n3, t1, t2, t3) ? 1 : 0;
+}
+
+__global__ void k_ibz_weights(const int* __restrict__ idx, const int* __restrict__ count, int n1, int n2, int n3,
+                              int t1, int t2, int t3, double* __restrict__ w) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= *count) return;
+  const long i = idx[j];
+  w[j] = ibz_partner(i, n1, n2, n3, t1, t2, t3) == i ? 1.0 : 2.0;
+}
+
+cudaError_t launch_ibz_select(int n1, int n2, int n3, const int* t, int* flag, int* pos, int* tot, int* idx,
+                              int* count, cudaStream_t st) {
+  const long nk = (long)n1 * n2 * n3;
+  if (nk <= 0) return cudaSuccess;
+  const long nblk = (nk + 1023) / 1024;
+  k_ibz_flags<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(n1, n2, n3, t[0], t[1], t[2], flag);
+  k_scan_blocks<<<(unsigned)nblk, 1024, 0, st>>>(flag, nk, pos, tot);
+  k_scan_totals<<<1, 32, 0, st>>>(tot, (int)nblk, count);
+  k_compact<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(flag, pos, tot, nk, idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ibz_weights(const int* idx, const int* count, int n_max, int n1, int n2, int n3, const int* t,
+                               double* w, cudaStream_t st) {
+  if (n_max <= 0) return cudaSuccess;
+  k_ibz_weights<<<(n_max + 255) / 256, 256, 0, st>>>(idx, count, n1, n2, n3, t[0], t[1], t[2], w);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_window_select(const double* eps, long nk, int nb, double e_lo, double e_hi, int* flag, int* pos,
                                  int* tot, int* idx, int* count, cudaStream_t st) {
   if (nk <= 0) return cudaSuccess;

@@ -101,21 +101,29 @@ def _positive(r) -> bool:
     return False
 
 
-def draw_hamiltonian(rng, R, lattice, nb, lam):
+def draw_hamiltonian(rng, R, lattice, nb, lam, real=False):
+    """H(R) with H(-R) = H(R)^H.  real: H(R) real (H(-R) = H(R)^T), i.e. a Hamiltonian with
+    time-reversal symmetry, H(-k) = conj H(k) (draws one real matrix per +-R pair)."""
     ne = len(R)
     H = np.zeros((ne, nb, nb), dtype=np.complex128)
     idx = _index_of(R)
     L = cart_length(R, lattice)
+
+    def draw():
+        if real:
+            return rng.standard_normal((nb, nb)).astype(np.complex128)
+        return rng.standard_normal((nb, nb)) + 1j * rng.standard_normal((nb, nb))
+
     for i, r in enumerate(R):
         r = tuple(int(x) for x in r)
         j = idx.get(tuple(-x for x in r))
         if j is None:
             continue
         if i == j:
-            A = rng.standard_normal((nb, nb)) + 1j * rng.standard_normal((nb, nb))
+            A = draw()
             H[i] = 0.5 * (A + A.conj().T)
         elif _positive(r):
-            A = (rng.standard_normal((nb, nb)) + 1j * rng.standard_normal((nb, nb))) * math.exp(-L[i] / lam)
+            A = draw() * math.exp(-L[i] / lam)
             H[i] = A
             H[j] = A.conj().T
     return H
@@ -215,8 +223,10 @@ def _lattice(spec):
 
 
 def make_workload(name: str, seed: int = 0, nq: int | None = None, nk: int | None = None,
-                  nb: int | None = None, box=None, with_coupling: bool = True, na: int | None = None) -> Workload:
-    """Build a named workload.  nq/nk/nb/na/box override the config (smaller cases for tests)."""
+                  nb: int | None = None, box=None, with_coupling: bool = True, na: int | None = None,
+                  real_h: bool = False) -> Workload:
+    """Build a named workload.  nq/nk/nb/na/box override the config (smaller cases for tests);
+    real_h draws real H(R) (time-reversal symmetric bands, eps(-k) = eps(k))."""
     cfg = dict(CONFIGS[name])
     rng = np.random.default_rng(seed)
     lat = _lattice(cfg["lattice"])
@@ -227,7 +237,7 @@ def make_workload(name: str, seed: int = 0, nq: int | None = None, nk: int | Non
     na = len(masses)
     R = box_vectors(*(box if box is not None else cfg["box"]))
     lamH, lamP, lamG = cfg["lam"]
-    H = draw_hamiltonian(rng, R, lat, nb, lamH)
+    H = draw_hamiltonian(rng, R, lat, nb, lamH, real=real_h)
     Phi = draw_force_constants(rng, R, lat, na, lamP)
     g = draw_coupling(rng, R, R, lat, na, nb, lamG) if with_coupling else None
     kspec, qspec = cfg["k"], cfg["q"]

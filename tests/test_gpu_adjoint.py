@@ -51,6 +51,29 @@ def test_backward_mos2_diff_subset():
     assert rel_grad_err(grad, g_ref) <= 1e-12
 
 
+@pytest.mark.parametrize("name,grid,k_tile", [("si_tiny", (3, 4, 5), 0), ("si_tiny", (3, 4, 5), 20),
+                                               ("mos2_diff", (48, 48, 1), 0)])
+def test_backward_on_a_uniform_grid_sum_factorised(name, grid, k_tile):
+    # kpts = NULL after eph_set_k_grid: the forward Re->k sum and its adjoint both run as three
+    # one-axis transforms (k_tile 20 = one j1 slab: the axis-1 adjoint accumulates over tiles)
+    wl = synth.make_workload(name, nq=3) if name == "mos2_diff" else synth.make_workload(name, nb=4, nq=3)
+    kpts = synth.uniform_grid(*grid)
+    w = weights(wl, kpts)
+    L_ref, g_ref = oracle.loss_and_grad(wl, kpts, wl.qpts, w, 1e-6)
+    ctx = binding.Context.from_workload(wl, k_tile=k_tile)
+    ctx.set_k_grid(*grid)
+    L, grad = ctx.loss_and_grad(None, wl.qpts, w, 1e-6)
+    assert abs(L - L_ref) <= 1e-12 * abs(L_ref)
+    assert rel_grad_err(grad, g_ref) <= 1e-12
+    # the vector-Jacobian product on the grid equals the one on the same points as a list
+    rng = np.random.default_rng(12)
+    shape_g = (len(wl.qpts), len(kpts), wl.nm, wl.nb, wl.nb)
+    gbar = rng.standard_normal(shape_g) + 1j * rng.standard_normal(shape_g)
+    v_grid = ctx.vjp(None, wl.qpts, gbar)
+    v_list = binding.Context.from_workload(wl).vjp(kpts, wl.qpts, gbar)
+    assert rel_grad_err(v_grid, v_list) <= 1e-12
+
+
 def test_backward_central_differences():
     wl = synth.make_workload("si_tiny", nb=4, nk=16, nq=3)
     w = weights(wl, wl.kpts)

@@ -62,6 +62,22 @@ def test_round_trip_mos2_shaped_2d():
     assert rel(ctx.bloch_to_wannier(coarse, coarse, g), wl.g_ReRp) <= 1e-12
 
 
+@pytest.mark.parametrize("name,grid", [("si_tiny", (3, 3, 3)), ("mos2", (4, 4, 1))])
+def test_round_trip_on_the_resident_grid(name, grid):
+    # Eq. 6 over the coarse grid set by eph_set_k_grid (kpts = NULL): the k' sum runs as the
+    # adjoint of the three axis transforms, with unit weights
+    if name == "mos2":
+        wl = synth.make_workload("mos2", box=(synth.centred_range(4), synth.centred_range(4), range(0, 1)),
+                                 nk=1, nq=1)
+    else:
+        wl = synth.make_workload(name)
+    coarse = synth.uniform_grid(*grid)
+    ctx = binding.Context.from_workload(wl)
+    ctx.set_k_grid(*grid)
+    g = ctx.interp_q(coarse)[2]
+    assert rel(ctx.bloch_to_wannier(None, coarse, g), wl.g_ReRp) <= 1e-12
+
+
 def test_device_mode_matches_host_mode():
     torch = pytest.importorskip("torch")
     wl = synth.make_workload("si_tiny")

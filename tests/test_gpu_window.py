@@ -84,14 +84,88 @@ def test_pair_screening(q_batch, k_tile):
     assert not np.any(g[~m])
 
 
+@pytest.mark.parametrize("grid", [False, True])
+def test_pair_screening_mixed_form(grid):
+    # the mixed form: tensor-core k-list path (grid False) or the sum-factorised grid path; the
+    # screened pairs skip the double-float band rotation.  The mask is decided on FP64 eps_{k+q}
+    # that agree with the oracle to 1e-10 (windows sit in gaps wider than that)
+    wl = synth.make_workload("si_tiny", nk=60, nq=5)
+    kpts = synth.uniform_grid(3, 4, 5) if grid else wl.kpts
+    ref = oracle.interpolate(wl, kpts, wl.qpts)
+    lo, hi = gap_window(np.concatenate([ref[0].ravel(), ref[1].ravel()]), 30, 36, min_gap=1e-8)
+    expect = ((ref[1] >= lo) & (ref[1] <= hi)).any(axis=2).astype(np.int32)
+    assert 0 < expect.sum() < expect.size
+    ctx = binding.Context.from_workload(wl, form="mixed", q_batch=2)
+    full = binding.Context.from_workload(wl, form="mixed", q_batch=2)
+    if grid:
+        ctx.set_k_grid(3, 4, 5)
+        full.set_k_grid(3, 4, 5)
+    else:
+        ctx.set_k(kpts)
+        full.set_k(kpts)
+    e_kq, om, g, keep = ctx.interp_q_window(wl.qpts, lo, hi)
+    assert g.dtype == np.complex64
+    assert np.array_equal(keep, expect)
+    e_f, om_f, g_f = full.interp_q(wl.qpts)
+    assert np.array_equal(e_kq, e_f) and np.array_equal(om, om_f)
+    m = keep.astype(bool)
+    assert np.array_equal(g[m], g_f[m])
+    assert not np.any(g[~m])
+
+
+@pytest.mark.parametrize("n,shift", [((4, 4, 4), None), ((6, 4, 2), (0.5 / 6, 0.0, 0.25)), ((5, 3, 1), None)])
+def test_time_reversal_ibz_bit_exact(n, shift):
+    # kept grid indices and weights are index arithmetic: equal to the oracle's brute-force
+    # reduction; eps_k of the kept points equal eph_set_k on those points bit for bit
+    wl = synth.make_workload("si_tiny", nb=6, nq=3, real_h=True)
+    sh = (0.0, 0.0, 0.0) if shift is None else shift
+    idx_ref, w_ref = oracle.ibz_time_reversal(n, sh)
+    ctx = binding.Context.from_workload(wl)
+    kidx, wk, eps = ctx.set_k_grid_ibz(*n, shift=shift)
+    assert np.array_equal(kidx, idx_ref.astype(np.int32)) and np.array_equal(wk, w_ref)
+    pts = oracle.grid_points(n, sh)[idx_ref]
+    ref = binding.Context.from_workload(wl)
+    assert np.array_equal(eps, ref.set_k(pts))
+    # a weighted k-sum over the kept points equals the sum over the whole grid
+    full = binding.Context.from_workload(wl).set_k_grid(*n, shift=shift)
+    f = lambda e: 1.0 / (np.exp((e - 0.2) / 0.05) + 1.0)
+    assert abs((wk[:, None] * f(eps)).sum() - f(full).sum()) <= 1e-12 * f(full).sum()
+    # the resident list is the kept points: the interpolation matches the oracle there
+    ge = ctx.interp_q(wl.qpts)
+    from tests import gauge
+    r = oracle.interpolate(wl, pts, wl.qpts)
+    assert gauge.max_rel_S(ge[2], r[3], r[0], r[1], r[2]) <= 1e-12
+
+
+def test_time_reversal_ibz_device_mode_and_errors():
+    torch = pytest.importorskip("torch")
+    wl = synth.make_workload("si_tiny", nb=4, nq=2, real_h=True)
+    dev = torch.device("cuda:0")
+    ctx = binding.Context.from_workload(wl, device_ptrs=True, stream=torch.cuda.current_stream())
+    n = (4, 6, 2)
+    N = 48
+    kidx = torch.empty(N, dtype=torch.int32, device=dev)
+    wk = torch.empty(N, dtype=torch.float64, device=dev)
+    eps = torch.empty(N, wl.nb, dtype=torch.float64, device=dev)
+    cnt = ctx.eph_set_k_grid_ibz(*n, None, eps, kidx, wk)
+    torch.cuda.synchronize()
+    idx_ref, w_ref = oracle.ibz_time_reversal(n)
+    assert cnt == len(idx_ref)
+    assert np.array_equal(kidx[:cnt].cpu().numpy(), idx_ref) and np.array_equal(wk[:cnt].cpu().numpy(), w_ref)
+    host = binding.Context.from_workload(wl)
+    with pytest.raises(binding.EphError) as ei:
+        host.set_k_grid_ibz(4, 4, 4, shift=(0.1, 0.0, 0.0))    # -k off the grid
+    assert ei.value.code == binding.EPH_EINVAL
+
+
 def test_window_errors():
     wl = synth.make_workload("si_tiny", nk=6, nq=2)
     ctx = binding.Context.from_workload(wl)
     with pytest.raises(binding.EphError) as ei:
         ctx.set_k_window(wl.kpts, 1.0, 0.0)
     assert ei.value.code == binding.EPH_EINVAL
-    mixed = binding.Context.from_workload(wl, form="mixed")
-    mixed.set_k(wl.kpts)
+    big = binding.Context.from_workload(synth.make_workload("si_tiny", nb=20, nk=4, nq=2), form="mixed")
+    big.set_k(wl.kpts[:4])
     with pytest.raises(binding.EphError) as ei:
-        mixed.interp_q_window(wl.qpts, -1.0, 1.0)
+        big.interp_q_window(wl.qpts, -1.0, 1.0)
     assert ei.value.code == binding.EPH_ENOTSUP

@@ -28,6 +28,8 @@ PIN_FUNCS = [
     pins.test_linewidths_detailed_balance_at_the_chemical_potential,
     pins.test_linewidths_zero_temperature_limit,
     pins.test_linewidths_properties,
+    lambda: pins.test_ibz_time_reversal_counts_and_weights((4, 4, 4), (0, 0, 0)),
+    pins.test_ibz_time_reversal_preserves_grid_sums_for_real_hamiltonians,
 ]
 
 _orig_phases = eo.phases
@@ -41,6 +43,7 @@ _orig_g1 = eo.g_rp_to_q
 _orig_loss_weights = eo.loss_weights
 _orig_b2w = eo.g_bloch_to_wannier
 _orig_linewidths = eo.linewidths
+_orig_ibz = eo.ibz_time_reversal
 
 
 def _phase_sign(pts, R, w=None):
@@ -201,6 +204,17 @@ def _lw_fermi_at_k(eps_k, eps_kq, omega, g, wq, kT, mu, sigma, omega_min):
     return np.einsum("q,qkvmn->kn", np.asarray(wq, dtype=np.float64), c)
 
 
+def _ibz_partner_is_itself(n, shift=(0.0, 0.0, 0.0)):
+    # forgets the negation: every point "pairs" with itself (nothing reduced, weights 1)
+    N = n[0] * n[1] * n[2]
+    return np.arange(N), np.ones(N)
+
+
+def _ibz_weights_one(n, shift=(0.0, 0.0, 0.0)):
+    idx, w = _orig_ibz(n, shift)
+    return idx, np.ones_like(w)
+
+
 MUTATIONS = {
     "phase_sign": ("phases", _phase_sign),
     "phase_missing_2pi": ("phases", _phase_unreduced_wrong_scale),
@@ -229,6 +243,8 @@ MUTATIONS = {
     "linewidth_without_1_over_2omega": ("linewidths", _lw_no_half_omega),
     "linewidth_coupling_band_indices_swapped": ("linewidths", _lw_g_transposed),
     "linewidth_occupation_at_k": ("linewidths", _lw_fermi_at_k),
+    "ibz_without_negation": ("ibz_time_reversal", _ibz_partner_is_itself),
+    "ibz_unit_weights": ("ibz_time_reversal", _ibz_weights_one),
 }
 
 

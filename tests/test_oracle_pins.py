@@ -469,3 +469,37 @@ def test_linewidths_properties():
     G1 = oracle.linewidths(ek, ekq, om, gg, [1.0, 2.0, 0.5], kT, 0.0, 0.1, 1e-6)
     G2 = oracle.linewidths(ek, ekq, om, gg, [2.0, 4.0, 1.0], kT, 0.0, 0.1, 1e-6)
     assert np.all(G1 >= 0) and np.abs(G2 - 2 * G1).max() < 1e-13 * np.abs(G1).max()
+
+
+# ---------------------------------------------------------------- time-reversal k reduction
+@pytest.mark.parametrize("n,shift", [((4, 4, 4), (0, 0, 0)), ((5, 3, 1), (0, 0, 0)), ((6, 4, 2), (0.5 / 6, 0, 0.25)),
+                                     ((2, 2, 2), (0, 0, 0)), ((7, 1, 1), (0.5 / 7, 0, 0))])
+def test_ibz_time_reversal_counts_and_weights(n, shift):
+    idx, w = oracle.ibz_time_reversal(n, shift)
+    N = n[0] * n[1] * n[2]
+    # points equal to their own partner: 2 j_a + t_a = 0 mod n_a on every axis (t_a = 2 s_a n_a)
+    nself = 1
+    for na, sa in zip(n, shift):
+        t = int(round(2 * sa * na))
+        nself *= sum(1 for j in range(na) if (2 * j + t) % na == 0)
+    assert len(idx) == (N + nself) // 2
+    assert w.sum() == N and set(np.unique(w)) <= {1.0, 2.0} and (w == 1.0).sum() == nself
+    assert np.all(np.diff(idx) > 0)
+
+
+def test_ibz_time_reversal_preserves_grid_sums_for_real_hamiltonians():
+    wl = synth.make_workload("si_tiny", nb=5, real_h=True)
+    n = (4, 3, 5)
+    k = oracle.grid_points(n)
+    eps, _ = oracle.electron_eigen(oracle.hamiltonian_k(k, wl.Re, wl.we, wl.H_Re))
+    epm, _ = oracle.electron_eigen(oracle.hamiltonian_k(-k, wl.Re, wl.we, wl.H_Re))
+    assert np.abs(eps - epm).max() < 1e-13 * np.abs(eps).max()        # eps(-k) = eps(k)
+    idx, w = oracle.ibz_time_reversal(n)
+    f = 1.0 / (np.exp((eps - 0.3) / 0.05) + 1.0)
+    assert abs((w[:, None] * f[idx]).sum() - f.sum()) < 1e-12 * f.sum()
+    assert abs((w[:, None] * eps[idx] ** 2).sum() - (eps ** 2).sum()) < 1e-12 * (eps ** 2).sum()
+    # a complex H(R) has no such symmetry: the reduction would be wrong there
+    wc = synth.make_workload("si_tiny", nb=5)
+    ec, _ = oracle.electron_eigen(oracle.hamiltonian_k(k, wc.Re, wc.we, wc.H_Re))
+    ecm, _ = oracle.electron_eigen(oracle.hamiltonian_k(-k, wc.Re, wc.we, wc.H_Re))
+    assert np.abs(ec - ecm).max() > 1e-3
