@@ -52,6 +52,29 @@ TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
            ("k_band_rotate", "si_full", 4): 2097285888.0 + 1534482688.0}
 
 
+def gpu_local_cpus(gpu_index):
+    """CPUs of the NUMA node the GPU hangs off (sysfs, via the GPU's PCI bus id), or None.  Pinned
+    host buffers first touched from those CPUs sit in the memory next to the GPU's link, so that
+    device->host copies do not cross to the other CPU's memory."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i", str(gpu_index)],
+                             capture_output=True, text=True, timeout=20).stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/numa_node"
+        node = int(open(path).read().strip())
+        if node < 0:
+            return None, None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            if not part:
+                continue
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return (cpus or None), node
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return None, None
+
+
 def fp64_peak_probe(dev):
     """Measured FP64 rates of this GPU: a DFMA loop (four independent FMA chains per element,
     compiled at run time by torch's jiterator, 4,096 flop per element over 2^24 elements) and
@@ -131,36 +154,56 @@ def parse():
 
 
 # ----------------------------------------------------------------------------- ncu capture cases
-# name -> (workload, its overrides, form, q points per call, calls).  Each runs eph_set_k and
-# `calls` eph_interp_q calls on device buffers, untimed: the programs the stanene-shaped
-# profiles were taken from (a 120-band, 180-mode case small enough for a full-section
-# capture of the band-rotation tensor-core product, and the bench's stanene mixed leg).
+# name -> (workload, its overrides, form, q points per call, calls, kind).  Each sets the k list
+# (kind "list": eph_set_k; "grid": eph_set_k_grid on the workload's grid) and makes `calls`
+# eph_interp_q calls on device buffers, untimed; kind "backward" makes `calls` eph_interp_backward
+# calls on the grid instead.  These are the programs the small-case profiles were taken from: a
+# 120-band, 180-mode case small enough for a full-section capture of the band-rotation
+# tensor-core product, the bench's stanene mixed leg, a silicon-shaped grid (Ne = 216) for the
+# mixed form's double-float band rotation, and the MoS2-shaped differentiation workload on 8 q.
 CAPTURES = {
-    "stanene-band-tc": ("stanene", dict(nk=16, nq=2, box=(range(0, 1), range(-1, 2), range(0, 1))), "mixed", 1, 2),
-    "stanene-mixed": ("stanene", dict(nk=512, nq=8), "mixed", 4, 2),
+    "stanene-band-tc": ("stanene", dict(nk=16, nq=2, box=(range(0, 1), range(-1, 2), range(0, 1))), "mixed", 1, 2,
+                        "list"),
+    "stanene-mixed": ("stanene", dict(nk=512, nq=8), "mixed", 4, 2, "list"),
+    "si-mixed-grid": ("si_full", dict(nq=8), "mixed", 4, 2, "grid24"),
+    "mos2-diff-backward": ("mos2_diff", dict(nq=8), "fp64", 4, 1, "backward"),
 }
 
 
 def run_capture(args):
+    import numpy as np
     import torch
 
     from paper_2603_10295_gb300 import binding, synth
-    name, over, form, QB, calls = CAPTURES[args.capture]
+    name, over, form, QB, calls, kind = CAPTURES[args.capture]
     dev = torch.device("cuda:0")
     wl = synth.make_workload(name, **over)
+    if kind == "grid24":   # a 24^3 grid of the silicon-shaped workload: 13,824 k
+        wl.kgrid = (24, 24, 24)
+        wl.kpts = synth.uniform_grid(24, 24, 24)
     nk, nb, nm = len(wl.kpts), wl.nb, wl.nm
     ctx = binding.Context.from_workload(wl, form=form, device_ptrs=True, stream=torch.cuda.current_stream(),
                                         q_batch=QB)
-    ctx.eph_set_k(nk, torch.from_numpy(wl.kpts).to(dev))
-    gdt = torch.complex128 if form == "fp64" else torch.complex64
-    e = torch.empty(QB, nk, nb, dtype=torch.float64, device=dev)
-    o = torch.empty(QB, nm, dtype=torch.float64, device=dev)
-    g = torch.empty(QB, nk, nm, nb, nb, dtype=gdt, device=dev)
+    if kind == "list":
+        ctx.eph_set_k(nk, torch.from_numpy(wl.kpts).to(dev))
+    else:
+        ctx.eph_set_k_grid(*wl.kgrid, None, None)
     q_d = torch.from_numpy(wl.qpts).to(dev)
-    for i in range(calls):
-        ctx.eph_interp_q(QB, q_d[i * QB:(i + 1) * QB], e, o, g)
+    if kind == "backward":
+        w = torch.from_numpy(np.full((nk, nb), 0.5)).to(dev)
+        L = torch.zeros(1, dtype=torch.float64, device=dev)
+        grad = torch.empty(wl.g_ReRp.shape, dtype=torch.complex128, device=dev)
+        for i in range(calls):
+            ctx.eph_interp_backward(nk, None, len(wl.qpts), q_d, w, 1e-6, L, grad)
+    else:
+        gdt = torch.complex128 if form == "fp64" else torch.complex64
+        e = torch.empty(QB, nk, nb, dtype=torch.float64, device=dev)
+        o = torch.empty(QB, nm, dtype=torch.float64, device=dev)
+        g = torch.empty(QB, nk, nm, nb, nb, dtype=gdt, device=dev)
+        for i in range(calls):
+            ctx.eph_interp_q(QB, q_d[i * QB:(i + 1) * QB], e, o, g)
     torch.cuda.synchronize()
-    print(f"capture {args.capture}: {wl.name} Nb={nb} Nm={nm} Ne={wl.ne}, {nk} k, {calls} x {QB} q, "
+    print(f"capture {args.capture}: {wl.name} Nb={nb} Nm={nm} Ne={wl.ne}, {nk} k, {calls} call(s), "
           f"{ctx.launches()} kernel launches", flush=True)
     ctx.close()
     return 0
@@ -585,6 +628,68 @@ def time_batched_graph(form, dev, replays=3, full=False):
     return out
 
 
+def time_multi_material(dev, replays=5):
+    """Three FP64 materials with uneven q batches (Si-shaped Nb=8, MoS2-shaped Nb=11 on a 12x12
+    grid, a 3-band one-atom Si box), few k points each so that one (q batch, k tile) of one material
+    fills well under one wave of the SMs: one CUDA graph of separate eph_interp_q calls against one
+    graph of a single eph_interp_q_multi call, whose band rotations run as one persistent launch
+    per round over every material's pairs."""
+    import torch
+
+    from paper_2603_10295_gb300 import binding, synth
+    from paper_2603_10295_gb300.batching import GraphBatcher
+    mo = synth.make_workload("mos2_diff", nq=40)
+    mo.kgrid, mo.kpts = (12, 12, 1), synth.uniform_grid(12, 12, 1)
+    mats = [(synth.make_workload("si_tiny", nk=256, nq=40), 17, False), (mo, 11, True),
+            (synth.make_workload("si_tiny", nb=3, na=1, nk=128, nq=40), 25, False)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for mode in ("separate", "multi"):
+        gb = GraphBatcher(dev)
+        ctxs, qs, bufs = [], [], []
+        for wl, nq, grid in mats:
+            c = binding.Context.from_workload(wl, device_ptrs=True, async_mode=True, stream=gb.stream, q_batch=4)
+            with torch.cuda.stream(gb.stream):
+                if grid:
+                    c.eph_set_k_grid(*wl.kgrid, None, None)
+                else:
+                    c.eph_set_k(len(wl.kpts), torch.from_numpy(wl.kpts).to(dev))
+            nk, nb, nm = c.nk, wl.nb, wl.nm
+            q = torch.from_numpy(wl.qpts[:nq].copy()).to(dev)
+            b = (torch.empty(nq, nk, nb, dtype=torch.float64, device=dev),
+                 torch.empty(nq, nm, dtype=torch.float64, device=dev),
+                 torch.empty(nq, nk, nm, nb, nb, dtype=torch.complex128, device=dev))
+            ctxs.append(c)
+            qs.append(q)
+            bufs.append(b)
+            if mode == "separate":
+                gb.add(c, q, *b)
+        if mode == "multi":
+            gb.add_multi(ctxs, qs, [b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs])
+        gb.capture()
+        gb.replay()
+        gb.check()
+        torch.cuda.synchronize()
+        e0.record(gb.stream)
+        for _ in range(replays):
+            gb.replay()
+        e1.record(gb.stream)
+        gb.check()
+        ms = e0.elapsed_time(e1) / replays
+        el = sum(nq * c.nk * wl.nm * wl.nb * wl.nb for (wl, nq, _), c in zip(mats, ctxs))
+        launches = sum(c.launches() for c in ctxs)
+        out[mode] = {"ms_per_replay": ms, "value": el / (ms * 1e-3), "unit": UNIT,
+                     "kernel_launches_total": launches}
+        for c in ctxs:
+            c.close()
+        del gb, bufs
+        torch.cuda.empty_cache()
+    out["materials"] = [{"workload": wl.name, "nb": wl.nb, "nm": wl.nm, "q": nq, "k_path": "grid" if g else "list"}
+                        for wl, nq, g in mats]
+    out["multi_over_separate"] = out["separate"]["ms_per_replay"] / out["multi"]["ms_per_replay"]
+    return out
+
+
 def run_libeph(args):
     import numpy as np
     import torch
@@ -798,6 +903,14 @@ def run_libeph(args):
         # every copy.  The tensor-core k-list path of the mixed form runs synchronously.
         gdt = torch.complex128 if form == "fp64" else torch.complex64
         asyn = form == "fp64" or grid
+        # host thread and pinned buffers on the GPU's own NUMA node (restored after the leg)
+        cpus, node = gpu_local_cpus(local)
+        old_aff = os.sched_getaffinity(0) if hasattr(os, "sched_getaffinity") else None
+        if cpus and old_aff is not None:
+            try:
+                os.sched_setaffinity(0, cpus & old_aff or cpus)
+            except OSError:
+                node = None
         hctx = binding.Context.from_workload(wl, form=form, device_ptrs=False, q_batch=QB, async_mode=asyn)
         kp_h = torch.from_numpy(wl.kpts).pin_memory()
         epsk_h = torch.empty(nk, nb, dtype=torch.float64).pin_memory()
@@ -825,6 +938,11 @@ def run_libeph(args):
         hctx.eph_sync()
         t_e2e = time.perf_counter() - t0
         hctx.close()
+        if cpus and old_aff is not None:
+            try:
+                os.sched_setaffinity(0, old_aff)
+            except OSError:
+                pass
         if world > 1:  # whole job: every rank's units over the slowest rank's time
             t = torch.tensor([t_e2e, t_setk], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -834,7 +952,9 @@ def run_libeph(args):
         out = {"value": e2e_units / (t_e2e + t_setk * (args.steps * QB) / len(wl.qpts)), "unit": UNIT,
                "h2d_bytes_per_step": QB * 3 * 8,
                "d2h_bytes_per_step": g_h.numel() * g_h.element_size() + ekq_h.numel() * 8 + om_h.numel() * 8,
-               "ms_per_step": 1e3 * t_e2e / args.steps, "k_setup_ms": 1e3 * t_setk}
+               "ms_per_step": 1e3 * t_e2e / args.steps, "k_setup_ms": 1e3 * t_setk,
+               "host_numa_node": node, "d2h_gbs_effective": (g_h.numel() * g_h.element_size() + ekq_h.numel() * 8)
+               * args.steps / t_e2e / 1e9}
         del g_h
         return out
 
@@ -864,6 +984,7 @@ def run_libeph(args):
             "parity": "sampled (k,q) of every material after a replay vs the oracle "
                       "(tests/test_gpu_config5_graph.py)",
             "mixed": time_batched_graph("mixed", dev), "fp64": time_batched_graph("fp64", dev)}
+        line["other_workloads"]["multi_material_persistent"] = time_multi_material(dev)
     if single and not args.no_linewidths:
         line["linewidths"] = time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=legs[0][1])
     if single and not args.no_backward:

@@ -188,6 +188,25 @@ int eph_interp_q_g1(eph_ctx* ctx, int nq, const double* qpts, const double* G1, 
  */
 int eph_set_gw(eph_ctx* ctx, const double* g_ReRp);
 
+/*
+ * eph_interp_q for several contexts (materials of different nb, nm, each with its own q batch of
+ * any size) in one call whose band rotations run as persistent kernels over a mixed work list:
+ * the calls proceed in rounds, each context contributing its next (q batch, k tile) unit (phases,
+ * D(q), Eq. 9 and the mode rotation at the start of a q batch; the Re->k contraction and the
+ * H(k+q) eigensolves per tile), and one launch per round rotates the pairs of every context's
+ * unit, its CTAs walking the concatenated pair list (k_band_rotate_multi).  Results are bit for
+ * bit those of separate eph_interp_q calls.
+ *   ctxs[nctx] distinct contexts, 1 <= nctx <= 32, each with a resident k list, FP64 form,
+ *   nb, nm <= 16, device pointers, whole g(Re,Rp) (else EPH_ENOTSUP); nq[i], qpts[i], eps_kq[i],
+ *   omega[i], g[i] as eph_interp_q's arguments for context i (eps_kq, omega, g and their
+ *   entries may be NULL).
+ * All the work runs on ctxs[0]'s stream (it first waits for the work queued on the other
+ * contexts' streams, which wait for the call at its end); with every context on one stream the
+ * call can be captured into a CUDA graph (async mode).  Errors are reported on ctxs[0].
+ */
+int eph_interp_q_multi(int nctx, eph_ctx* const* ctxs, const int* nq, const double* const* qpts,
+                       double* const* eps_kq, double* const* omega, void* const* g);
+
 /* eph_set_k followed by eph_interp_q. */
 int eph_interp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
                double* eps_k, double* eps_kq, double* omega, void* g);

@@ -19,6 +19,7 @@ class GraphBatcher:
         self.device = torch.device(device or "cuda")
         self.stream = torch.cuda.Stream(device=self.device)
         self.items = []      # (ctx, q_dev, eps_kq, omega, g)
+        self.multi = []      # (ctxs, [q_dev], [eps_kq], [omega], [g]): one eph_interp_q_multi call each
         self.graph = None
 
     def add(self, ctx, q_dev, eps_kq=None, omega=None, g=None):
@@ -41,13 +42,33 @@ class GraphBatcher:
             calls += 1
         return calls
 
+    def add_multi(self, ctxs, qs, eps_kq=None, omega=None, g=None):
+        """One eph_interp_q_multi call over several contexts (FP64 form, nb, nm <= 16): their band
+        rotations run as one persistent launch per round over the pairs of every context."""
+        for ctx in ctxs:
+            if not (ctx.device_ptrs and getattr(ctx, "async_mode", False)):
+                raise ValueError("contexts in a graph batch need device_ptrs=True and async_mode=True")
+        n = len(ctxs)
+        self.multi.append((list(ctxs), list(qs), list(eps_kq or [None] * n), list(omega or [None] * n),
+                           list(g or [None] * n)))
+
+    def contexts(self):
+        out = {id(i[0]): i[0] for i in self.items}
+        for cs, *_ in self.multi:
+            out.update({id(c): c for c in cs})
+        return list(out.values())
+
     def _run_all(self):
+        from .binding import interp_q_multi
         for ctx, q, e, o, g in self.items:
             ctx.eph_interp_q(q.shape[0], q, e, o, g)
+        for cs, qs, es, os_, gs in self.multi:
+            interp_q_multi(cs, [q.shape[0] for q in qs], qs, es, os_, gs)
 
     def capture(self):
-        for ctx in {id(i[0]): i[0] for i in self.items}.values():
-            nq_max = max(q.shape[0] for c, q, *_ in self.items if c is ctx)
+        for ctx in self.contexts():
+            nq_max = max([q.shape[0] for c, q, *_ in self.items if c is ctx] +
+                         [q.shape[0] for cs, qs, *_ in self.multi for c, q in zip(cs, qs) if c is ctx])
             ctx.eph_reserve(nq_max)
         with torch.cuda.stream(self.stream):
             self._run_all()              # eager pass: primes function attributes and tensor maps
@@ -64,7 +85,7 @@ class GraphBatcher:
 
     def check(self):
         self.stream.synchronize()
-        for ctx in {id(i[0]): i[0] for i in self.items}.values():
+        for ctx in self.contexts():
             ctx.eph_sync()
 
 

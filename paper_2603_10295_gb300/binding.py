@@ -25,7 +25,8 @@ EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "ep
            "eph_profile", "eph_profile_read", "eph_profile_reset", "eph_bands_noalloc",
            "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths", "eph_interp_vjp",
            "eph_set_k_grid", "eph_bloch_to_wannier", "eph_set_k_window", "eph_interp_q_window", "eph_eigh",
-           "eph_create_rp_slice", "eph_g1_partial", "eph_interp_q_g1", "eph_set_gw", "eph_set_k_grid_ibz")
+           "eph_create_rp_slice", "eph_g1_partial", "eph_interp_q_g1", "eph_set_gw", "eph_set_k_grid_ibz",
+           "eph_interp_q_multi")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -115,6 +116,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_set_gw.restype = i
     lib.eph_set_k_grid_ibz.argtypes = [vp, i, i, i, dp, dp, vp, dp, ctypes.POINTER(i)]
     lib.eph_set_k_grid_ibz.restype = i
+    lib.eph_interp_q_multi.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    lib.eph_interp_q_multi.restype = i
     del ip
     if path is None:
         _lib = lib
@@ -445,3 +449,16 @@ class Context:
         self.eph_interp_backward(nk, kpts, len(qpts), qpts, w_nk, omega_min, L, grad)
         self.nk = nk
         return float(L[0]), grad
+
+
+def interp_q_multi(ctxs, nqs, qpts, eps_kq=None, omega=None, g=None):
+    """eph_interp_q_multi over device-pointer contexts: list arguments per context (entries may
+    be None).  Errors are raised from the first context."""
+    n = len(ctxs)
+    lib = ctxs[0].lib
+    vp = ctypes.c_void_p
+    arr = lambda xs: (vp * n)(*[_ptr(x) for x in (xs if xs is not None else [None] * n)])
+    handles = (vp * n)(*[c.handle for c in ctxs])
+    nq_arr = (ctypes.c_int * n)(*[int(x) for x in nqs])
+    ctxs[0]._check(lib.eph_interp_q_multi(n, handles, nq_arr, arr(qpts), arr(eps_kq), arr(omega), arr(g)))
+

@@ -294,6 +294,11 @@ double omega_unit_ev() {
       ctx->pending.push_back({(stage), ea_, eb_});                \
     }                                                             \
   } while (0)
+#define EPH_CK_C(c, call)                                        \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return fail((c), EPH_ECUDA, #call, e_); \
+  } while (0)
 #define EPH_TRY(call)           \
   do {                          \
     int r_ = (call);            \
@@ -1449,6 +1454,134 @@ int interp_q_dispatch(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, 
   return interp_fp64(ctx, nq, qpts, eps_kq, omega, g, nullptr);
 }
 }  // namespace
+
+extern "C" int eph_interp_q_multi(int nctx, eph_ctx* const* ctxs, const int* nq, const double* const* qpts,
+                                  double* const* eps_kq, double* const* omega, void* const* g) {
+  if (nctx < 1 || nctx > eph::kMaxBandSegs || !ctxs || !nq || !qpts) return EPH_EINVAL;
+  eph_ctx* c0 = ctxs[0];
+  if (!c0) return EPH_EINVAL;
+  for (int i = 0; i < nctx; ++i) {
+    eph_ctx* c = ctxs[i];
+    if (!c || nq[i] < 1 || !qpts[i]) return fail(c0, EPH_EINVAL, "eph_interp_q_multi: NULL context, nq < 1 or qpts NULL");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(c0, EPH_EINVAL, "eph_interp_q_multi: a context appears twice");
+    if (!c->k_ready) return fail(c0, EPH_ESTATE, "eph_interp_q_multi before eph_set_k");
+    if (c->opt.form != EPH_FORM_FP64 || c->big || !c->opt.device_ptrs || !whole_g(c))
+      return fail(c0, EPH_ENOTSUP, "eph_interp_q_multi: FP64 form, nb, nm <= 16, device pointers, whole g(Re,Rp)");
+  }
+  // every context runs on the first one's stream for the duration of the call: its stream first
+  // waits for the work already queued on the others, and they wait for this call at the end
+  std::vector<cudaStream_t> saved((size_t)nctx);
+  cudaEvent_t ev = nullptr;
+  EPH_CK_C(c0, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  for (int i = 0; i < nctx; ++i) {
+    saved[i] = ctxs[i]->stream;
+    if (saved[i] != c0->stream) {
+      EPH_CK_C(c0, cudaEventRecord(ev, saved[i]));
+      EPH_CK_C(c0, cudaStreamWaitEvent(c0->stream, ev, 0));
+    }
+  }
+  struct Unit {
+    int q0, nqb;
+    long k0;
+    int nkt;
+  };
+  std::vector<QPlan> plans((size_t)nctx);
+  std::vector<std::vector<Unit>> units((size_t)nctx);
+  size_t rounds = 0;
+  int rc = EPH_OK;
+  for (int i = 0; i < nctx && rc == EPH_OK; ++i) {
+    eph_ctx* c = ctxs[i];
+    c->stream = c0->stream;
+    rc = prepare_fp64(c, nq[i], g && g[i], &plans[i]);
+    if (rc != EPH_OK) break;
+    const QPlan& p = plans[i];
+    for (int q0 = 0; q0 < nq[i]; q0 += p.QB)
+      for (long k0 = 0; k0 < c->nk; k0 += p.KT)
+        units[i].push_back({q0, nq[i] - q0 < p.QB ? nq[i] - q0 : p.QB, k0, (int)(c->nk - k0 < p.KT ? c->nk - k0 : p.KT)});
+    rounds = std::max(rounds, units[i].size());
+  }
+  int nsm = 1;
+  for (size_t r = 0; r < rounds && rc == EPH_OK; ++r) {
+    eph::BandSegs segs{};
+    int nseg = 0, mnb = 1, mnm = 1;
+    long total = 0;
+    for (int i = 0; i < nctx && rc == EPH_OK; ++i) {
+      if (r >= units[i].size()) continue;
+      eph_ctx* ctx = ctxs[i];
+      const QPlan& p = plans[i];
+      const Unit u = units[i][r];
+      const int nb = ctx->nb, nm = ctx->nm, nb2 = nb * nb;
+      const double* qdev = qpts[i] + 3L * u.q0;
+      if (u.k0 == 0) {  // a new q batch of this context
+        rc = q_prelude(ctx, p, qdev, u.nqb);
+        if (rc != EPH_OK) break;
+        if (omega && omega[i] && cudaMemcpyAsync(omega[i] + (long)u.q0 * nm, ctx->omq.p, (size_t)u.nqb * nm * sizeof(double),
+                                                 cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+          rc = fail(c0, EPH_ECUDA, "eph_interp_q_multi: omega copy");
+          break;
+        }
+      }
+      rc = k_tile_forward(ctx, p, u.nqb, u.k0, u.nkt);
+      if (rc != EPH_OK) break;
+      if (eps_kq && eps_kq[i])
+        for (int iq = 0; iq < u.nqb && rc == EPH_OK; ++iq)
+          if (cudaMemcpyAsync(eps_kq[i] + ((long)(u.q0 + iq) * ctx->nk + u.k0) * nb,
+                              as<double>(ctx->eps_tile) + (long)iq * u.nkt * nb, (size_t)u.nkt * nb * sizeof(double),
+                              cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+            rc = fail(c0, EPH_ECUDA, "eph_interp_q_multi: eps copy");
+      if (rc != EPH_OK || !(g && g[i])) continue;
+      eph::BandSeg& sg = segs.s[nseg++];
+      sg.Y = as<double2>(ctx->Y) + nb2;
+      sg.ldy = p.NW;
+      sg.Ukq = as<double2>(ctx->Ukq);
+      sg.Uk = as<double2>(ctx->Uk) + u.k0 * nb2;
+      sg.g = static_cast<double2*>(g[i]) + ((long)u.q0 * ctx->nk + u.k0) * p.gcols;
+      sg.sgq = (long)ctx->nk * p.gcols;
+      sg.pair0 = total;
+      sg.nk = u.nkt;
+      sg.nm = nm;
+      sg.nb = nb;
+      total += (long)u.nqb * u.nkt;
+      mnb = std::max(mnb, nb);
+      mnm = std::max(mnm, nm);
+      nsm = std::max(nsm, ctx->nsm);
+    }
+    if (rc != EPH_OK) break;
+    // one persistent launch for this round's tiles of every context
+    if (nseg > 0) {
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (c0->prof && !c0->opt.async) {
+        ea = take_event(c0);
+        eb = take_event(c0);
+        if (ea) cudaEventRecord(ea, c0->stream);
+      }
+      const cudaError_t e = eph::launch_band_rotate_multi(segs, nseg, total, mnb, mnm, nsm, c0->stream);
+      if (e != cudaSuccess) {
+        rc = fail(c0, EPH_ECUDA, "launch_band_rotate_multi", e);
+        break;
+      }
+      ++c0->launches;
+      if (ea && eb) {
+        cudaEventRecord(eb, c0->stream);
+        c0->pending.push_back({EPH_STAGE_BAND, ea, eb});
+      }
+    }
+  }
+  for (int i = 0; i < nctx; ++i) ctxs[i]->stream = saved[i];
+  for (int i = 0; i < nctx && rc == EPH_OK; ++i)
+    if (saved[i] != c0->stream) {
+      if (cudaEventRecord(ev, c0->stream) != cudaSuccess || cudaStreamWaitEvent(saved[i], ev, 0) != cudaSuccess)
+        rc = fail(c0, EPH_ECUDA, "eph_interp_q_multi: stream ordering");
+    }
+  cudaEventDestroy(ev);
+  if (rc != EPH_OK) return rc;
+  for (int i = 1; i < nctx; ++i) {  // status flags and profiles of the other contexts
+    const int r2 = finish(ctxs[i]);
+    if (r2 != EPH_OK) return r2;
+  }
+  return finish(c0);
+}
 
 extern "C" int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, double e_lo, double e_hi,
                                    double* eps_kq, double* omega, void* g, int* keep) {

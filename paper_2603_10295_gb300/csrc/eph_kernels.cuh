@@ -96,6 +96,24 @@ cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, c
 
 // ---- Re->k contraction on a product k grid (sum factorisation, griddft.cu) ----------------
 // kpts[(j1 n2 + j2) n3 + j3] = (j1/n1, j2/n2, j3/n3) + shift (shift: host array of 3)
+// One segment of the persistent multi-material band rotation: pairs (q,k) of one (context,
+// q batch, k tile), q-major with k fastest, first pair at global index pair0.
+struct BandSeg {
+  const double2* Y;    // G3 rows of the tile (pair p at Y + p * ldy)
+  long ldy;
+  const double2* Ukq;  // [pairs][nb][nb]
+  const double2* Uk;   // [nk][nb][nb] of the tile's k points
+  double2* g;          // output of the tile: q stride sgq, k stride nm nb nb
+  long sgq;
+  long pair0;
+  int nk, nm, nb, pad;
+};
+constexpr int kMaxBandSegs = 32;
+struct BandSegs {
+  BandSeg s[kMaxBandSegs];
+};
+cudaError_t launch_band_rotate_multi(const BandSegs& segs, int nseg, long total, int max_nb, int max_nm, int nsm,
+                                     cudaStream_t st);
 cudaError_t launch_grid_points(int n1, int n2, int n3, const double* shift, double* k, cudaStream_t st);
 // E[j][b] = exp(2 pi i (j/N + shift) n(b)), j < N, b < B; slots n(0) = 0, n(2m - 1) = m, n(2m) = -m
 cudaError_t launch_axis_phase(int N, int B, double shift, double2* E, cudaStream_t st);

@@ -3,6 +3,8 @@
 //                  (applied once per q, before the Re sum, with which it commutes)
 //   band rotation  g[q][k][nu] = V_{k+q}^H G3[q][k][nu] V_k   (U_{mm',k+q} U*_{nn',k})
 //   phonons        omega = sign(l) sqrt|l| * hbar sqrt(eV/(A^2 amu)), u = e / sqrt(M)
+#include <algorithm>
+
 #include "eph_kernels.cuh"
 
 namespace eph {
@@ -203,6 +205,53 @@ cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, c
   }
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
   k_band_rotate<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq, keep);
+  return cudaGetLastError();
+}
+
+// Persistent band rotation over a mixed work list: segments of (q,k) pairs from several
+// contexts (materials of different nb, nm; uneven q batches and k tiles), one launch.  CTAs
+// walk the concatenated pair index with a grid stride; each pair finds its segment by binary
+// search over the segments' first-pair offsets and runs the same per-pair arithmetic as
+// k_band_rotate (bit-identical results), with shared memory sized for the largest segment.
+// The segment table travels as a kernel parameter (no host-to-device copy, so the launch can be
+// captured in a CUDA graph).
+__global__ void __launch_bounds__(128) k_band_rotate_multi(const __grid_constant__ BandSegs segs, int nseg, long total) {
+  extern __shared__ double2 sm[];
+  for (long t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {  // last segment with pair0 <= t
+      const int mid = (lo + hi + 1) >> 1;
+      if (segs.s[mid].pair0 <= t) lo = mid; else hi = mid - 1;
+    }
+    const BandSeg& sg = segs.s[lo];
+    const int nb = sg.nb, nm = sg.nm, nb2 = nb * nb;
+    const PairSmem s = pair_smem(sm, nb, nm);
+    const long pair = t - sg.pair0;
+    const int k = (int)(pair % sg.nk);
+    const long q = pair / sg.nk;
+    pair_stage1(s, sg.Y + pair * sg.ldy, sg.Uk + (long)k * nb2, sg.Ukq + pair * nb2, nm, nb);
+    double2* out = sg.g + q * sg.sgq + (long)k * nm * nb2;
+    for (int e = threadIdx.x; e < nm * nb2; e += blockDim.x) out[e] = pair_g(s, e, nb);
+    __syncthreads();  // shared memory is reused by the next pair
+  }
+}
+
+cudaError_t launch_band_rotate_multi(const BandSegs& segs, int nseg, long total, int max_nb, int max_nm, int nsm,
+                                     cudaStream_t st) {
+  if (total <= 0 || nseg <= 0) return cudaSuccess;
+  if (nseg > kMaxBandSegs || segs.s[0].pair0 != 0) return cudaErrorInvalidValue;
+  const size_t smem = pair_smem_bytes(max_nb, max_nm);
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_band_rotate_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_rotate_multi, 128, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const long grid = std::min<long>(total, (long)nsm * per_sm);
+  k_band_rotate_multi<<<(unsigned)grid, 128, smem, st>>>(segs, nseg, total);
   return cudaGetLastError();
 }
 

@@ -126,6 +126,8 @@ def test_every_entry_point_rejects_a_null_context_without_gpu(lib):
     assert lib.eph_g1_partial(None, 1, dummy, dummy) == E
     assert lib.eph_interp_q_g1(None, 1, dummy, dummy, None, None, None) == E
     assert lib.eph_set_gw(None, dummy) == E
+    assert lib.eph_interp_q_multi(0, None, None, None, None, None, None) == E
+    assert lib.eph_interp_q_multi(1, None, None, None, None, None, None) == E
 
 
 def test_rp_slice_bounds_checked_without_gpu(lib):

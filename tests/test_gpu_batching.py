@@ -97,3 +97,76 @@ def test_autotune_picks_valid_tiles_and_keeps_results():
     # and the results still match the oracle
     ref = oracle.interpolate(wl)
     assert gauge.max_rel_S(bufs1[2].cpu().numpy(), ref[3], ref[0], ref[1], ref[2]) <= 1e-12
+
+
+def _multi_materials():
+    box = (synth.centred_range(6), synth.centred_range(6), range(0, 1))
+    return [(synth.make_workload("si_tiny", nk=150, nq=9), 5),
+            (synth.make_workload("mos2", nk=120, nq=9, box=box), 9),
+            (synth.make_workload("si_tiny", nb=3, na=1, nk=64, nq=9), 2)]
+
+
+def test_multi_material_persistent_call_matches_separate_calls():
+    # eph_interp_q_multi: three materials (nb 8/11/3, nm 6/9/3) with uneven q batches, their band
+    # rotations as one persistent launch per round; bit-identical to separate eph_interp_q calls,
+    # and on the oracle for every material
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream()
+    ctxs, qs, outs, refs = [], [], [], []
+    for wl, nq in _multi_materials():
+        c = binding.Context.from_workload(wl, device_ptrs=True, stream=st, q_batch=4, k_tile=48)
+        c.eph_set_k(len(wl.kpts), torch.from_numpy(wl.kpts).to(dev))
+        q = torch.from_numpy(wl.qpts[:nq].copy()).to(dev)
+        ctxs.append(c)
+        qs.append(q)
+        outs.append(_buffers(torch, wl, nq, "fp64", dev))
+        r = binding.Context.from_workload(wl, q_batch=4, k_tile=48)
+        r.set_k(wl.kpts)
+        refs.append(r.interp_q(wl.qpts[:nq]))
+    binding.interp_q_multi(ctxs, [q.shape[0] for q in qs], qs, [o[0] for o in outs], [o[1] for o in outs],
+                           [o[2] for o in outs])
+    torch.cuda.synchronize()
+    for (wl, nq), o, r in zip(_multi_materials(), outs, refs):
+        for a, b in zip(o, r):
+            assert np.array_equal(a.cpu().numpy(), b)
+        ref = oracle.interpolate(wl, wl.kpts, wl.qpts[:nq])
+        assert gauge.max_rel_S(o[2].cpu().numpy(), ref[3], ref[0], ref[1], ref[2]) <= 1e-12
+
+
+def test_multi_material_call_in_a_graph_and_errors():
+    torch = pytest.importorskip("torch")
+    from paper_2603_10295_gb300.batching import GraphBatcher
+    dev = torch.device("cuda:0")
+    gb = GraphBatcher(dev)
+    ctxs, qs, outs, eager = [], [], [], []
+    for wl, nq in _multi_materials():
+        c = binding.Context.from_workload(wl, device_ptrs=True, async_mode=True, stream=gb.stream, q_batch=4)
+        with torch.cuda.stream(gb.stream):
+            c.eph_set_k(len(wl.kpts), torch.from_numpy(wl.kpts).to(dev))
+        ctxs.append(c)
+        qs.append(torch.from_numpy(wl.qpts[:nq].copy()).to(dev))
+        outs.append(_buffers(torch, wl, nq, "fp64", dev))
+        r = binding.Context.from_workload(wl, q_batch=4)
+        r.set_k(wl.kpts)
+        eager.append(r.interp_q(wl.qpts[:nq]))
+    gb.add_multi(ctxs, qs, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+    gb.capture()
+    for o in outs:
+        o[2].zero_()
+    gb.replay()
+    gb.check()
+    for o, r in zip(outs, eager):
+        for a, b in zip(o, r):
+            assert np.array_equal(a.cpu().numpy(), b)
+    # contexts the persistent rotation does not cover are rejected on the first context
+    wl = synth.make_workload("si_tiny", nk=8, nq=2)
+    m = binding.Context.from_workload(wl, form="mixed", device_ptrs=True)
+    m.eph_set_k(8, torch.from_numpy(wl.kpts).to(dev))
+    q = torch.from_numpy(wl.qpts).to(dev)
+    with pytest.raises(binding.EphError) as ei:
+        binding.interp_q_multi([ctxs[0], m], [2, 2], [q, q])
+    assert ei.value.code == binding.EPH_ENOTSUP
+    with pytest.raises(binding.EphError) as ei:
+        binding.interp_q_multi([ctxs[0], ctxs[0]], [2, 2], [q, q])
+    assert ei.value.code == binding.EPH_EINVAL
