@@ -894,8 +894,10 @@ int ensure_q_workspace(eph_ctx* ctx, const QPlan& p, bool with_y = true) {
 // Per q batch, before the k loop: phases, D(q) -> omega, u; Eq. 9; W_q; on a product k grid
 // (grid_stages) also the first two axis transforms of W_q.
 // g1_in: the caller's G1 of these q points (eph_interp_q_g1), else Eq. 9 runs on the resident slice.
+// fp64_eq9: Eq. 9 in FP64 even where the mixed form has it on the tensor cores (the adjoint, whose
+// chain stays FP64 in both forms).
 int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid_stages = true,
-              const double2* g1_in = nullptr) {
+              const double2* g1_in = nullptr, bool fp64_eq9 = false) {
   const int nm = ctx->nm, ne = ctx->ne, np = ctx->np, nb2 = ctx->nb * ctx->nb;
   double2* Qe = as<double2>(ctx->Qe);
   double2* Pp = as<double2>(ctx->Pp);
@@ -913,7 +915,7 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
                                                   as<double2>(ctx->uq), ctx->stream));
   // Eq. 9: G1 = sum_Rp w_p e^{i q.Rp} g(Re,Rp) over the Rp vectors of the resident slice
   const double2* G1src = g1_in;
-  if (!G1src && ctx->eq9_tc) {
+  if (!G1src && ctx->eq9_tc && !fp64_eq9) {
     // mixed form: G1 = P_q g as a tensor-core product of 3 phase digits and 4 digits of g(Re,Rp)
     // (rows of the real embedding of g, per-row scales), FP32 accumulation, then to complex128
     EPH_LAUNCH_S(EPH_STAGE_FT_Q, eph::launch_digits_a(Pp + ctx->rp0, np, nqb, ctx->nrp, ctx->kpp, ctx->scaleP, 3,
@@ -1703,7 +1705,7 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
   double2* G2b = as<double2>(ctx->G2bar);
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
     const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
-    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb, true, nullptr, true));
     for (long k0 = 0; k0 < nk; k0 += p.KT) {
       const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
       // recompute the Re->k stage and the gauges for this tile (never stored across tiles)
