@@ -160,12 +160,14 @@ def parse():
 # calls on the grid instead.  These are the programs the small-case profiles were taken from: a
 # 120-band, 180-mode case small enough for a full-section capture of the band-rotation
 # tensor-core product, the bench's stanene mixed leg, a silicon-shaped grid (Ne = 216) for the
-# mixed form's double-float band rotation, and the MoS2-shaped differentiation workload on 8 q.
+# mixed form's band rotation (tensor cores; "-ff": the double-float kernel), and the MoS2-shaped
+# differentiation workload on 8 q.
 CAPTURES = {
     "stanene-band-tc": ("stanene", dict(nk=16, nq=2, box=(range(0, 1), range(-1, 2), range(0, 1))), "mixed", 1, 2,
                         "list"),
     "stanene-mixed": ("stanene", dict(nk=512, nq=8), "mixed", 4, 2, "list"),
     "si-mixed-grid": ("si_full", dict(nq=8), "mixed", 4, 2, "grid24"),
+    "si-mixed-grid-ff": ("si_full", dict(nq=8), "mixed", 4, 2, "grid24", dict(band_ff=True)),
     "mos2-diff-backward": ("mos2_diff", dict(nq=8), "fp64", 4, 1, "backward"),
 }
 
@@ -175,7 +177,8 @@ def run_capture(args):
     import torch
 
     from paper_2603_10295_gb300 import binding, synth
-    name, over, form, QB, calls, kind = CAPTURES[args.capture]
+    name, over, form, QB, calls, kind, *extra = CAPTURES[args.capture]
+    extra = extra[0] if extra else {}
     dev = torch.device("cuda:0")
     wl = synth.make_workload(name, **over)
     if kind == "grid24":   # a 24^3 grid of the silicon-shaped workload: 13,824 k
@@ -183,7 +186,7 @@ def run_capture(args):
         wl.kpts = synth.uniform_grid(24, 24, 24)
     nk, nb, nm = len(wl.kpts), wl.nb, wl.nm
     ctx = binding.Context.from_workload(wl, form=form, device_ptrs=True, stream=torch.cuda.current_stream(),
-                                        q_batch=QB)
+                                        q_batch=QB, **extra)
     if kind == "list":
         ctx.eph_set_k(nk, torch.from_numpy(wl.kpts).to(dev))
     else:

@@ -50,12 +50,14 @@ enum eph_form {
   EPH_FORM_FP64 = 0,  /* every contraction in FP64 (DFMA) */
   EPH_FORM_MIXED = 1  /* split precision on the large contractions, g as complex64: on k lists the
                          Re->k contraction of g and H(k+q) are tcgen05 tensor-core products of
-                         fixed-point BF16 digits with FP32 accumulation; the band rotation runs in
-                         double-float FP32 (nb, nm <= 16) or on the tensor cores (larger shapes);
+                         fixed-point BF16 digits with FP32 accumulation; the Rp->q contraction
+                         (Eq. 9) is one too while its digit planes stay below ~4 GB (Si- and
+                         MoS2-shaped inputs; FP64 otherwise); the band rotation runs on the tensor
+                         cores (fused two-product kernel for nb <= 16, nm*nb <= 128; batched
+                         products beyond; option band_ff selects double-float FP32 for the former);
                          the eigensolves stop at eigenvalues within ~1e-12 ||A|| and eigenvectors
-                         within ~1e-8.  Phases (exact FP64 reduction), D(q) and its eigensolve,
-                         the Rp->q contraction and, on uniform grids, the Re->k transforms stay
-                         FP64 */
+                         within ~1e-8.  Phases (exact FP64 reduction), D(q) and its eigensolve and,
+                         on uniform grids, the Re->k transforms stay FP64 */
 };
 
 typedef struct eph_options {
@@ -79,6 +81,10 @@ typedef struct eph_options {
                          form, uniform-grid path or nb, nm > 16) the outputs are copied to the host
                          asynchronously, g on a second stream: the host buffers must stay valid,
                          and should be pinned, until eph_sync returns */
+  int band_ff;        /* mixed form, nb <= 16 and nm*nb <= 128: 0 (default) = band rotation on the
+                         tensor cores (four fixed-point BF16 digits per operand, exact level-0
+                         accumulation, ~2^-31 of each pair's largest element); 1 = double-float
+                         FP32 arithmetic on the CUDA cores */
 } eph_options;
 
 /* Fills *opt with the defaults (FP64 form, host pointers, automatic batching). */
@@ -132,8 +138,8 @@ int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k);
  * term for term, to rounding.  Used when nb, nm <= 16, the Re vectors are distinct and
  * their box has extents <= 32 and volume <= 8 ne; otherwise the general path runs on the
  * generated k list.  In the mixed form the transforms are FP64 as well; the band rotation
- * runs in double-float arithmetic on the FP32 pipe and the eigensolves stop at the mixed
- * form's accuracy (g complex64).
+ * runs on the tensor cores from these FP64 sums (rounded to FP32) and the eigensolves stop at
+ * the mixed form's accuracy (g complex64).
  *   shift [3] HOST pointer (NULL = 0); eps_k [nk][nb] as in eph_set_k (may be NULL).
  * EPH_EINVAL for n_a < 1 or nk > 2^31 - 1.
  */
@@ -301,8 +307,8 @@ int eph_set_k_grid_ibz(eph_ctx* ctx, int n1, int n2, int n3, const double* shift
  * eph_interp_q with pair screening: pairs (q,k) with no eps_{m,k+q} in [e_lo, e_hi] get g = 0
  * without the band rotation (the only step after eps_{k+q} is known); keep [nq][nk] (int, may
  * be NULL) receives 1 for the pairs computed and 0 for the screened ones.  eps_kq and omega are
- * complete.  Both forms (in the mixed form the screened pairs skip its double-float band
- * rotation; g complex64) with nb, nm <= 16; EPH_ENOTSUP otherwise.
+ * complete.  Both forms (in the mixed form the screened pairs get g = 0 from its band
+ * rotation kernel; g complex64) with nb, nm <= 16; EPH_ENOTSUP otherwise.
  */
 int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, double e_lo, double e_hi, double* eps_kq,
                         double* omega, void* g, int* keep);

@@ -987,6 +987,11 @@ bool mixed_list(const eph_ctx* ctx) {
   return ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && (!ctx->big || use_band_tc(ctx));
 }
 
+// mixed form, small shapes: the fused tensor-core band rotation unless the double-float one is asked for
+bool small_band_tc(const eph_ctx* ctx) {
+  return !ctx->opt.band_ff && eph::band_tc_small_supported(ctx->nm, ctx->nb);
+}
+
 // workspace of the tensor-core band rotation for npairs pairs of a tile of nkt k points: the
 // pairs go in chunks of at most ~6 GB of digit and product buffers
 size_t band_tc_bytes(const eph_ctx* ctx, long npairs, int nkt) {
@@ -1007,8 +1012,14 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
   const double2* Uk = as<double2>(ctx->Uk) + k0 * nb2;
   const bool mixed = ctx->opt.form == EPH_FORM_MIXED;  // complex64 g, sgq in elements
   if (mixed && !ctx->big) {
-    EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_rotate_ff_f64(Y + nb2, p.NW, Ukq, Uk, nqb, nkt, nm, nb,
-                                                               reinterpret_cast<float2*>(out), sgq, ctx->stream, keep));
+    if (small_band_tc(ctx))
+      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc_small(Y + nb2, 0, p.NW, Ukq, Uk, nqb, nkt, nm, nb,
+                                                             reinterpret_cast<float2*>(out), sgq, keep,
+                                                             ctx->status + 1, ctx->stream));
+    else
+      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_rotate_ff_f64(Y + nb2, p.NW, Ukq, Uk, nqb, nkt, nm, nb,
+                                                                 reinterpret_cast<float2*>(out), sgq, ctx->stream,
+                                                                 keep));
     return EPH_OK;
   }
   if (!ctx->big) {
@@ -1242,14 +1253,25 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
                                    as<float>(ctx->g_stage32) + 2L * iq * nkt * gcols,
                                    (size_t)nkt * gcols * 2 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
       } else if (host) {
-        EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate_ff(as<float>(ctx->G3f), nr, as<double2>(ctx->Ukq),
-                                                            as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
-                                                            as<float>(ctx->g_stage32), 2L * nkt * gcols, ctx->stream,
-                                                            keep));
+        if (small_band_tc(ctx))
+          EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc_small(ctx->G3f.p, 1, nr / 2, as<double2>(ctx->Ukq),
+                                                                 as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
+                                                                 as<float2>(ctx->g_stage32), (long)nkt * gcols, keep,
+                                                                 ctx->status + 1, ctx->stream));
+        else
+          EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate_ff(as<float>(ctx->G3f), nr, as<double2>(ctx->Ukq),
+                                                              as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,
+                                                              as<float>(ctx->g_stage32), 2L * nkt * gcols, ctx->stream,
+                                                              keep));
         for (int iq = 0; iq < nqb; ++iq)
           EPH_CK(cudaMemcpyAsync(gout + 2L * ((long)(q0 + iq) * nk + k0) * gcols,
                                  as<float>(ctx->g_stage32) + 2L * iq * nkt * gcols,
                                  (size_t)nkt * gcols * 2 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+      } else if (small_band_tc(ctx)) {
+        EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc_small(
+                                         ctx->G3f.p, 1, nr / 2, as<double2>(ctx->Ukq), as<double2>(ctx->Uk) + k0 * nb2,
+                                         nqb, nkt, nm, nb, reinterpret_cast<float2*>(gout) + ((long)q0 * nk + k0) * gcols,
+                                         (long)nk * gcols, keep, ctx->status + 1, ctx->stream));
       } else {
         EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate_ff(as<float>(ctx->G3f), nr, as<double2>(ctx->Ukq),
                                                             as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb,

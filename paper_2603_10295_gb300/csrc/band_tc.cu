@@ -10,6 +10,10 @@
 //                       B rows (nu, n') with K = 2a + t gathered from C1.
 // Every B row carries its own power-of-two scale (fixed point relative to the row maximum);
 // V is unitary, so its scale is 2.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -280,6 +284,580 @@ cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Band rotation for Nb <= 16 and Nm Nb <= 128 (the Si- and MoS2-shaped workloads of the mixed
+// form), both products of a tile of pairs fused in one CTA on the tcgen05 tensor cores.  A tile
+// holds PPT pairs (q, k) with one k:
+//   stage 1, per pair:  U_nu = V_{k+q}^H G3_nu     A rows (nu, n'), K = (a, re/im); B = conj(V_{k+q})
+//                       on the real embedding, columns (m, re/im), one column block per pair (the
+//                       cross products of one pair's rows with another's block are never read);
+//   stage 2, per tile:  g_nu = U_nu V_k            A rows (m, nu), K = (n', re/im); B = V_k on the
+//                       real embedding, columns (n, re/im), shared by the tile's pairs.
+// Pair j takes the accumulator rows j*RS .. j*RS + Nm Nb - 1 (RS a multiple of 32: each warp's TMEM
+// lanes belong to one pair).  Operands are four fixed-point BF16 digits (32 bits; levels i + j <= 3,
+// 10 MMAs per K step): level 0 in its own accumulator, where its sum is exact, levels 1-3 in a second
+// one (~2^-31 of the result).  G3 (rounded to FP32 when it comes in FP64) carries a
+// power-of-two scale per row, U one per pair (errors are measured against each pair's largest
+// |g|^2), V scale 2.  Digits of FP32 values come from FP32 arithmetic: adding and subtracting
+// 1.5 * 2^23 rounds to an integer and each remainder is exact.  V (FP64) goes through an exact
+// 32-bit fixed-point integer.  The threads write the digits straight into shared memory in the
+// no-swizzle K-major layout (8-row x 16-byte core matrices); U never leaves the SM.
+// Every wait on the MMA completion barrier is bounded: on a timeout the CTA sets *err and stops.
+namespace {
+namespace bts {
+constexpr int THREADS = 128, ND = 4;
+constexpr long long WAIT_LIMIT = 2000000000LL;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// byte offset of element (r, k) in a K-major tile with KP columns, no swizzle: core matrices of
+// 8 rows x 8 bf16 (128 contiguous bytes), K-adjacent ones 128 B apart (LBO), 8-row groups
+// KP/8 x 128 B apart (SBO)
+template <int KP>
+__device__ __forceinline__ uint32_t off(int r, int k) {
+  return (uint32_t)((r >> 3) * (KP * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+template <int KP>
+__device__ __forceinline__ uint64_t desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;       // LBO: next core matrix along K
+  d |= (uint64_t)((KP * 16) >> 4) << 32;  // SBO: next 8-row group
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  return d;                               // swizzle mode 0: none
+}
+// kind::f16 instruction descriptor: D f32, A/B bf16, both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+// the ten digit products of levels <= 3 over KP/16 K steps: level 0 into d0, levels 1-3 into d1
+template <int KP>
+__device__ __forceinline__ void mma_levels(uint32_t d0, uint32_t d1, uint32_t sA, int a_tile, uint32_t sB, int b_tile,
+                                           uint32_t id) {
+#pragma unroll
+  for (int ks = 0; ks < KP / 16; ++ks) {
+    uint64_t da[ND], db[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      da[d] = desc<KP>(sA + d * a_tile + ks * 256);
+      db[d] = desc<KP>(sB + d * b_tile + ks * 256);
+    }
+    const uint32_t f = ks > 0 ? 1u : 0u;
+    mma(d0, da[0], db[0], id, f);
+    mma(d1, da[0], db[1], id, f);
+    mma(d1, da[1], db[0], id, 1u);
+    mma(d1, da[0], db[2], id, 1u);
+    mma(d1, da[1], db[1], id, 1u);
+    mma(d1, da[2], db[0], id, 1u);
+    mma(d1, da[0], db[3], id, 1u);
+    mma(d1, da[1], db[2], id, 1u);
+    mma(d1, da[2], db[1], id, 1u);
+    mma(d1, da[3], db[0], id, 1u);
+  }
+}
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > WAIT_LIMIT) return false;
+  }
+}
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src) {
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void st32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+// the bf16 pair (lo, hi) of two FP32 values that are exact in bf16 (digits), lo at the lower address
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+// Digits e_i = D_i 2^-8(i+1), integers |D_i| <= 128, of y + yl with |y + yl| <= 1/2 (y and yl two
+// parts of one value): y + yl = e_0 + e_1 + e_2 + e_3 + O(2^-31).  Adding and subtracting
+// 1.5 * 2^(23 - 8(i+1)) rounds to a multiple of 2^-8(i+1); the remainders are exact up to the one
+// rounding that folds yl in.  Level-0 products e_0 f_0 are multiples of 2^-16 below 2^-2, so their
+// sums over K <= 32 stay exact in FP32.
+constexpr float MG0 = 0x1.8p15f, MG1 = 0x1.8p7f, MG2 = 0x1.8p-1f, MG3 = 0x1.8p-9f;
+__device__ __forceinline__ float rnd_at(float y, float M) { return __fsub_rn(__fadd_rn(y, M), M); }
+__device__ __forceinline__ void fdigits(float y, float yl, float (&e)[ND]) {
+  float q = rnd_at(__fadd_rn(y, yl), MG0);
+  e[0] = q;
+  y = __fadd_rn(__fsub_rn(y, q), yl);
+  q = rnd_at(y, MG1);
+  e[1] = q;
+  y = __fsub_rn(y, q);
+  q = rnd_at(y, MG2);
+  e[2] = q;
+  e[3] = rnd_at(__fsub_rn(y, q), MG3);
+}
+__device__ __forceinline__ float i2f(int q) { return __fsub_rn(__int_as_float(0x4B400000 + q), 12582912.0f); }  // |q| < 2^22
+// the same digits of X 2^-32 for an integer X = round(y 2^32), |X| <= 2^31, from integer arithmetic
+__device__ __forceinline__ void idigits(long long X, float (&d)[ND]) {
+  const int q0 = (int)((X + (1LL << 23)) >> 24);
+  int r = (int)(X - ((long long)q0 << 24));
+  const int q1 = (r + (1 << 15)) >> 16;
+  r -= q1 << 16;
+  const int q2 = (r + (1 << 7)) >> 8;
+  r -= q2 << 8;
+  d[0] = __fmul_rn(i2f(q0), 0x1p-8f);
+  d[1] = __fmul_rn(i2f(q1), 0x1p-16f);
+  d[2] = __fmul_rn(i2f(q2), 0x1p-24f);
+  d[3] = __fmul_rn(i2f(r), 0x1p-32f);
+}
+// FP64 -> FP32, rounded to nearest (ties away), by integer operations (normal FP32 range; smaller
+// magnitudes give 0)
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) + (1ULL << 28);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned mag = __funnelshift_l(lo, hi, 3) - (896u << 23);
+  return (e > 896u && e < 1151u) ? __uint_as_float(mag | (hi & 0x80000000u)) : 0.f;
+}
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(double x) { return d2f_int(x); }
+__device__ __forceinline__ float pow2f(int e) { return ldexpf(1.f, e); }  // once per row and tile
+__device__ __forceinline__ int fexp(float x) { return (int)((__float_as_uint(x) >> 23) & 0xFF); }
+}  // namespace bts
+
+template <typename TC, int KP>  // TC: double2 (FP64 contraction) or float2 (tensor-core contraction)
+__global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 6 : 4) k_band_tc_small(const TC* __restrict__ Y, long ldy,
+                                                                   const double2* __restrict__ Ukq,
+                                                                   const double2* __restrict__ Uk, int nq, int nk,
+                                                                   int nm, int nb, int RS, int PPT,
+                                                                   float2* __restrict__ g, long sgq,
+                                                                   const int* __restrict__ keep, int* __restrict__ err,
+                                                                   uint32_t tmem_cols, int vec16) {
+  using namespace bts;
+  constexpr int A_TILE = 128 * KP * 2;
+  constexpr int B2_TILE = KP * KP * 2;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int N1 = PPT * KP;  // stage-1 MMA N: PPT column blocks of KP
+  const int B1_TILE = N1 * KP * 2;
+  unsigned char* A = sm;                    // [ND][128 x KP] (stage 1, then stage 2)
+  unsigned char* B1 = A + ND * A_TILE;      // [ND][N1 x KP]
+  unsigned char* B2 = B1 + ND * B1_TILE;    // [ND][KP x KP]
+  const int per = nm * nb * nb;             // G3 elements of one pair
+  // raw inputs of the next tile, copied asynchronously while the current one computes:
+  // G3 of each pair [PPT][per], then V_{k+q} of each pair and V_k [PPT + 1][nb2]
+  unsigned char* rawG = B2 + ND * B2_TILE;
+  unsigned char* rawV = rawG + (((size_t)PPT * per * sizeof(TC) + 15) & ~(size_t)15);
+  int* smax = reinterpret_cast<int*>(rawV + (size_t)(PPT + 1) * nb * nb * sizeof(double2));  // [4] exponent of U
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smax + 4);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nb2 = nb * nb, R = nm * nb, K2 = 2 * nb;
+  const uint32_t sA = smem_u32(A), sB1 = smem_u32(B1), sB2 = smem_u32(B2);
+  const uint32_t sRawG = smem_u32(rawG), sRawV = smem_u32(rawV);
+  const TC* gsm = reinterpret_cast<const TC*>(rawG);
+  const double2* vsm = reinterpret_cast<const double2*>(rawV);
+
+  // zero the operand tiles once: K padding and unused rows stay zero
+  for (int i = tid; i < (ND * (A_TILE + B1_TILE + B2_TILE)) / 16; i += THREADS)
+    reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t acc0 = tmem, acc1 = tmem + (uint32_t)N1;  // L0 | L123 (stage 2 uses their first KP columns)
+  // this thread's accumulator row: pair j of the tile, row rr of that pair
+  const int j = tid / RS, rr = tid - j * RS;
+  const bool row_ok = j < PPT && rr < R;
+  const int nu1 = rr / nb, x1 = rr - nu1 * nb;  // stage 1 row (nu, n')
+  const int m2 = rr / nm, nu2 = rr - m2 * nm;   // stage 2 row (m, nu)
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tl1 = lane_base + (uint32_t)(j < PPT ? j * KP : 0);
+  uint32_t phase = 0;
+  const unsigned div_nb = (65536u + nb - 1) / nb, div_nb2 = (65536u + nb2 - 1) / nb2;
+  const int nqg = (nq + PPT - 1) / PPT;
+  const long ntiles = (long)nqg * nk;
+  const bool vec_out = (nb % 2 == 0) && ((reinterpret_cast<uintptr_t>(g) & 15) == 0) && (sgq % 2 == 0);
+  // asynchronous copies of tile tt's inputs into rawG / rawV (one commit group)
+  auto prefetch = [&](long tt) {
+    if (tt >= ntiles) return;
+    const int kk = (int)(tt % nk), qg = (int)(tt / nk);
+    for (int jj = 0; jj < PPT; ++jj) {
+      const int iq = qg * PPT + jj;
+      if (iq >= nq) break;
+      const long P = (long)iq * nk + kk;
+      const TC* src = Y + P * ldy;
+      const uint32_t dst = sRawG + (uint32_t)((size_t)jj * per * sizeof(TC));
+      if (sizeof(TC) == 16 || !vec16) {
+        for (int i = tid; i < per; i += THREADS) cp_async<(int)sizeof(TC)>(dst + (uint32_t)(i * sizeof(TC)), src + i);
+      } else {  // complex64 rows 16-byte aligned, even length: two elements per copy
+        for (int i = tid; 2 * i < per; i += THREADS) cp_async<16>(dst + (uint32_t)(i * 16), src + 2 * i);
+      }
+      const double2* vs = Ukq + P * nb2;
+      for (int i = tid; i < nb2; i += THREADS) cp_async<16>(sRawV + (uint32_t)((jj * nb2 + i) * 16), vs + i);
+    }
+    const double2* vk = Uk + (long)kk * nb2;
+    for (int i = tid; i < nb2; i += THREADS) cp_async<16>(sRawV + (uint32_t)((PPT * nb2 + i) * 16), vk + i);
+    cp_async_commit();
+  };
+  prefetch(blockIdx.x);
+
+  for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int kk = (int)(t % nk), qg = (int)(t / nk);
+    // ---- stage-1 A (digits of the G3 rows) and both B operands, from this tile's raw inputs
+    if (tid < 4) smax[tid] = 0;
+    cp_async_wait_all();
+    __syncthreads();
+    const int iq = qg * PPT + j;
+    const bool live = row_ok && iq < nq;
+    const long P = (long)iq * nk + kk;
+    int es = 0;  // row scale 2^es of this thread's G3 row
+    if (live) {
+      const TC* src = gsm + (long)j * per + (long)nu1 * nb2 + x1;
+      float v[KP];
+      float mx = 0.f;
+#pragma unroll
+      for (int a = 0; a < KP / 2; ++a) {
+        if (a < nb) {
+          const TC z = src[(long)a * nb];
+          v[2 * a] = to_f(z.x);
+          v[2 * a + 1] = to_f(z.y);
+          mx = fmaxf(mx, fmaxf(fabsf(v[2 * a]), fabsf(v[2 * a + 1])));
+        } else {
+          v[2 * a] = 0.f;
+          v[2 * a + 1] = 0.f;
+        }
+      }
+      const int eb = fexp(mx);
+      es = eb ? eb - 127 + 2 : 0;
+      const float sc = pow2f(-es);
+#pragma unroll
+      for (int c = 0; c < KP / 8; ++c) {  // 16-byte chunk c: K = 8c .. 8c + 7, i.e. a = 4c .. 4c + 3
+        uint32_t w[ND][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          float dr[ND], di[ND];
+          fdigits(__fmul_rn(v[8 * c + 2 * i], sc), 0.f, dr);
+          fdigits(__fmul_rn(v[8 * c + 2 * i + 1], sc), 0.f, di);
+#pragma unroll
+          for (int d = 0; d < ND; ++d) w[d][i] = pack2(dr[d], di[d]);
+        }
+        const uint32_t o = off<KP>(tid, 8 * c);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) st128(sA + d * A_TILE + o, w[d][0], w[d][1], w[d][2], w[d][3]);
+      }
+    }
+    for (int e = tid; e < (PPT + 1) * nb2; e += THREADS) {
+      // e / nb2 and r2 / nb by multiply-shift (exact for e < 2^16 / nb2, r2 < 2^16 / nb)
+      const int jj = (int)(((unsigned)e * div_nb2) >> 16), r2 = e - jj * nb2;
+      const int a = (int)(((unsigned)r2 * div_nb) >> 16), c = r2 - a * nb;
+      float vr[ND], vi[ND];
+      if (jj < PPT) {
+        // stage 1, block jj: conj(V_{k+q})[a][m = c]; rows (m, re) = (Vr, Vi), (m, im) = (-Vi, Vr) along K = (a, re/im)
+        const int iqj = qg * PPT + jj;
+        if (iqj >= nq) continue;
+        const double2 u = vsm[jj * nb2 + r2];
+        idigits(fixedF_d(u.x, 1), vr);
+        idigits(fixedF_d(u.y, 1), vi);
+        const uint32_t o0 = off<KP>(jj * KP + 2 * c, 2 * a), o1 = off<KP>(jj * KP + 2 * c + 1, 2 * a);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          st32(sB1 + d * B1_TILE + o0, pack2(vr[d], vi[d]));
+          st32(sB1 + d * B1_TILE + o1, pack2(-vi[d], vr[d]));
+        }
+      } else {
+        // stage 2: V_k[n' = a][n = c]; rows (n, re) = (Vr, -Vi), (n, im) = (Vi, Vr) along K = (n', re/im)
+        const double2 u = vsm[PPT * nb2 + r2];
+        idigits(fixedF_d(u.x, 1), vr);
+        idigits(fixedF_d(u.y, 1), vi);
+        const uint32_t o0 = off<KP>(2 * c, 2 * a), o1 = off<KP>(2 * c + 1, 2 * a);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          st32(sB2 + d * B2_TILE + o0, pack2(vr[d], -vi[d]));
+          st32(sB2 + d * B2_TILE + o1, pack2(vi[d], vr[d]));
+        }
+      }
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    prefetch(t + gridDim.x);  // the raw buffers are free again
+    if (tid == 0) {  // ---- stage 1 MMAs
+      fence_after();
+      mma_levels<KP>(acc0, acc1, sA, A_TILE, sB1, B1_TILE, idesc(N1));
+      commit(bar);
+    }
+    bool ok = wait(bar, phase & 1);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(err, 16);
+        wait(bar, phase & 1);  // bounded: the MMAs must be done before the TMEM is released
+      }
+      break;
+    }
+    ++phase;
+    fence_after();
+    // ---- epilogue 1: this thread's U row (nu, n'), columns (m, re/im): U = 2^(es + 1) (L0 + L123)
+    // (h: L0, l: L123); pair maximum of the exponents of U
+    float h[KP], l[KP];
+#pragma unroll
+    for (int c = 0; c < KP; c += 16) {
+      ld16(tl1 + c, h + c);
+      ld16(tl1 + (uint32_t)N1 + c, l + c);
+    }
+    ld_wait();
+    {
+      float mx = 0.f;
+#pragma unroll
+      for (int c = 0; c < KP; ++c)
+        if (c < K2) mx = fmaxf(mx, fabsf(__fadd_rn(h[c], l[c])));
+      const int eb = fexp(mx);
+      if (live && eb) atomicMax(&smax[j], eb + es + 1);  // biased exponent of 2^(es + 1) max|L0 + L123|
+    }
+    fence_before();
+    __syncthreads();
+    // ---- stage-2 A: digits of U / 2^esu at rows (m, nu), K = (n', re/im) (overwrites stage 1's A)
+    const int ebu = j < PPT ? smax[j] : 0;
+    const int esu = ebu ? ebu - 127 + 2 : 0;
+    if (live) {
+      const float sc = pow2f(es + 1 - esu);
+#pragma unroll
+      for (int m = 0; m < KP / 2; ++m) {
+        if (m < nb) {
+          float dr[ND], di[ND];
+          fdigits(__fmul_rn(h[2 * m], sc), __fmul_rn(l[2 * m], sc), dr);
+          fdigits(__fmul_rn(h[2 * m + 1], sc), __fmul_rn(l[2 * m + 1], sc), di);
+          const uint32_t o = off<KP>(j * RS + m * nm + nu1, 2 * x1);
+#pragma unroll
+          for (int d = 0; d < ND; ++d) st32(sA + d * A_TILE + o, pack2(dr[d], di[d]));
+        }
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {  // ---- stage 2 MMAs (into the first KP columns of the same accumulators)
+      fence_after();
+      mma_levels<KP>(acc0, acc1, sA, A_TILE, sB2, B2_TILE, idesc(KP));
+      commit(bar);
+    }
+    ok = wait(bar, phase & 1);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(err, 16);
+        wait(bar, phase & 1);
+      }
+      break;
+    }
+    ++phase;
+    fence_after();
+    // ---- epilogue 2: g rows (m, nu), columns (n, re/im)
+#pragma unroll
+    for (int c = 0; c < KP; c += 16) {
+      ld16(lane_base + c, h + c);
+      ld16(lane_base + (uint32_t)N1 + c, l + c);
+    }
+    ld_wait();
+    if (live) {
+      float2* out = g + (long)iq * sgq + (long)kk * nm * nb2 + (long)nu2 * nb2 + (long)m2 * nb;
+      const bool zero = keep && !keep[P];
+      const float f = zero ? 0.f : pow2f(esu + 1);  // g = 2^(esu + 1) (L0 + L123), one rounding
+#pragma unroll
+      for (int c = 0; c < KP; ++c) h[c] = __fmul_rn(__fadd_rn(h[c], l[c]), f);
+      if (vec_out) {
+#pragma unroll
+        for (int n = 0; n < KP / 2; n += 2)
+          if (n < nb) reinterpret_cast<float4*>(out)[n / 2] = make_float4(h[2 * n], h[2 * n + 1], h[2 * n + 2], h[2 * n + 3]);
+      } else {
+#pragma unroll
+        for (int n = 0; n < KP / 2; ++n)
+          if (n < nb) out[n] = make_float2(h[2 * n], h[2 * n + 1]);
+      }
+    }
+    fence_before();
+    __syncthreads();
+  }
+  cp_async_wait_all();  // no copy may land in shared memory after the CTA has left
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  }
+}
+
+struct SmallShape {
+  int kp, rs, ppt, n1;
+  uint32_t cols;
+  size_t smem;
+};
+
+SmallShape small_shape(int nm, int nb) {
+  SmallShape s{};
+  const int R = nm * nb;
+  s.kp = 2 * nb <= 16 ? 16 : 32;
+  s.rs = ((R + 31) / 32) * 32;
+  s.ppt = s.rs > 0 ? 128 / s.rs : 0;
+  if (s.ppt > 4) s.ppt = 4;
+  s.n1 = s.ppt * s.kp;
+  uint32_t c = 32;
+  while (c < (uint32_t)(2 * s.n1)) c <<= 1;
+  s.cols = c;
+  s.smem = (size_t)bts::ND * (128 * s.kp * 2 + (size_t)s.n1 * s.kp * 2 + (size_t)s.kp * s.kp * 2) + 64;
+  return s;
+}
+
+// shared memory of one CTA: operand tiles, raw inputs of a tile (G3 in elem_bytes, V), scalars
+size_t small_smem(const SmallShape& s, int nm, int nb, size_t elem_bytes) {
+  const size_t g3 = (((size_t)s.ppt * nm * nb * nb * elem_bytes) + 15) & ~(size_t)15;
+  return s.smem + g3 + (size_t)(s.ppt + 1) * nb * nb * 16;
+}
+
+// Shared-memory request and CTAs per SM of a launch: what the registers, threads and shared memory
+// allow, at most tmem_cap; a larger request enforces the cap, so that no CTA's TMEM allocation waits
+// on another.  Shared memory is counted in 256-byte units plus the per-CTA reserve.  Cached per
+// (kernel, need, cap, device).
+cudaError_t small_occupancy(const void* kern, size_t need, int tmem_cap, size_t* smem_out, int* occ_out) {
+  struct Entry {
+    const void* kern;
+    size_t need;
+    int cap, dev;
+    size_t smem;
+    int occ;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  // set on every launch: the attribute belongs to the current context
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& c : cache)
+      if (c.kern == kern && c.need == need && c.cap == tmem_cap && c.dev == dev) {
+        *smem_out = c.smem;
+        *occ_out = c.occ;
+        return cudaSuccess;
+      }
+  }
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+  int sm_smem = 0, reserve = 0, sm_regs = 0;
+  if ((e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  auto unit = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t static_smem = fa.sharedSizeBytes;
+  const int warp_regs = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;
+  const int by_regs = sm_regs / (warp_regs * (bts::THREADS / 32));
+  const int by_threads = 2048 / bts::THREADS;
+  auto by_smem = [&](size_t dyn) { return (int)((size_t)sm_smem / (unit(dyn + static_smem) + (size_t)reserve)); };
+  int occ = std::min(std::min(by_regs, by_threads), by_smem(need));
+  size_t smem = need;
+  if (occ > tmem_cap) {  // request more shared memory so that at most tmem_cap CTAs fit
+    occ = tmem_cap;
+    smem = ((size_t)sm_smem / (size_t)tmem_cap - (size_t)reserve - static_smem) & ~(size_t)255;
+    if (smem < need) smem = need;
+    while (by_smem(smem) > tmem_cap) smem += 256;
+  }
+  if (occ < 1 || smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  std::lock_guard<std::mutex> lock(mu);
+  cache.push_back(Entry{kern, need, tmem_cap, dev, smem, occ});
+  *smem_out = smem;
+  *occ_out = occ;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+bool band_tc_small_supported(int nm, int nb) {
+  return nb >= 1 && nb <= 16 && nm >= 1 && nm * nb <= 128;
+}
+
+cudaError_t launch_band_tc_small(const void* Y, int y_f32, long ldy, const double2* Ukq, const double2* Uk, int nq,
+                                 int nk, int nm, int nb, float2* g, long sgq, const int* keep, int* err,
+                                 cudaStream_t st) {
+  if ((long)nq * nk <= 0) return cudaSuccess;
+  if (!band_tc_small_supported(nm, nb) || nk < 1) return cudaErrorInvalidValue;
+  const SmallShape s = small_shape(nm, nb);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorInvalidDevice;
+  const long ntiles = (long)((nq + s.ppt - 1) / s.ppt) * nk;
+  // complex64 G3 in 16-byte copies when every pair's rows start 16-byte aligned and have even length
+  const int vec16 = !y_f32 || ((reinterpret_cast<uintptr_t>(Y) & 15) == 0 && ldy % 2 == 0 && (nm * nb * nb) % 2 == 0);
+  cudaError_t e;
+  // CTAs per SM: what the registers and shared memory allow (occupancy calculator), at most what the
+  // TMEM columns allow; a larger shared-memory request enforces the latter, so that no CTA's TMEM
+  // allocation waits on another.  The grid is that many CTAs per SM (one wave).
+#define EPH_SMALL_LAUNCH(TCT, KPV)                                                                                    \
+  do {                                                                                                                \
+    auto kern = k_band_tc_small<TCT, KPV>;                                                                            \
+    size_t smem = 0;                                                                                                  \
+    int occ = 0;                                                                                                      \
+    if ((e = small_occupancy(reinterpret_cast<const void*>(kern), small_smem(s, nm, nb, sizeof(TCT)),                 \
+                             (int)(512 / s.cols), &smem, &occ)) != cudaSuccess)                                       \
+      return e;                                                                                                       \
+    const long grid = std::min(ntiles, (long)sms * occ);                                                              \
+    kern<<<(unsigned)grid, bts::THREADS, smem, st>>>(static_cast<const TCT*>(Y), ldy, Ukq, Uk, nq, nk, nm, nb, s.rs,  \
+                                                     s.ppt, g, sgq, keep, err, s.cols, vec16);                        \
+  } while (0)
+  if (y_f32) {
+    if (s.kp == 16) EPH_SMALL_LAUNCH(float2, 16); else EPH_SMALL_LAUNCH(float2, 32);
+  } else {
+    if (s.kp == 16) EPH_SMALL_LAUNCH(double2, 16); else EPH_SMALL_LAUNCH(double2, 32);
+  }
+#undef EPH_SMALL_LAUNCH
+  return cudaGetLastError();
 }
 
 }  // namespace eph

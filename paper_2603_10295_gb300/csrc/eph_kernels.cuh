@@ -231,6 +231,13 @@ cudaError_t launch_tc_band_gemm(const void* maps_a4, const void* maps_b4, int M,
 // work: at least band_tc_work_bytes(nk, nm, nb, 1) bytes; more lets more pairs go per chunk.
 size_t band_tc_work_bytes(int nk, int nm, int nb, long pairs);
 bool band_tc_supported(int nm, int nb);
+// Fused tensor-core band rotation for nb <= 16, nm nb <= 128 (complex64 g, ~2^-31 relative to each
+// pair's largest element): Y rows of G3 per pair (complex128 or, y_f32, complex64), ldy complex
+// elements apart; keep (optional) zeroes screened pairs; *err |= 16 on a barrier timeout.
+bool band_tc_small_supported(int nm, int nb);
+cudaError_t launch_band_tc_small(const void* Y, int y_f32, long ldy, const double2* Ukq, const double2* Uk, int nq,
+                                 int nk, int nm, int nb, float2* g, long sgq, const int* keep, int* err,
+                                 cudaStream_t st);
 cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const double2* Ukq, const double2* Uk, int nq,
                            int nk, int nm, int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err,
                            cudaStream_t st);

@@ -1,0 +1,92 @@
+"""Fused tensor-core band rotation of the mixed form (nb <= 16, nm nb <= 128): g = V_{k+q}^H G3 V_k
+as two tcgen05 products of four-digit fixed-point BF16 operands per tile of (k,q) pairs.
+
+Checked against the FP64 CPU oracle on gauge-invariant quantities (|g|^2 subspace sums within the
+mixed form's 1e-6) and element by element against the double-float FP32 rotation of the same
+context (same G3, same eigenvectors): both round g once to complex64, so they agree to a few
+FP32 ulps of each pair's largest element.  Shapes cover every tile arrangement: one, two and four
+pairs per tile, K = 16 and 32, ragged last tiles; both inputs: complex64 G3 from the tensor-core
+Re->k contraction (k list) and complex128 G3 from the sum-factorised FP64 transforms (uniform grid)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_10295_gb300 import binding, build_lib, synth
+from tests import gauge
+
+pytestmark = pytest.mark.gpu
+
+TOL_S = 1e-6     # mixed form: |g|^2 subspace sums against the FP64 oracle
+TOL_FF = 3e-7    # element-wise, relative to the pair's largest |g|: tensor-core vs double-float rotation
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not os.path.exists(binding.LIB_PATH):
+        build_lib.build()
+    return binding.load_library()
+
+
+def pair_rel(g, gref):
+    nq, nk = g.shape[:2]
+    d = np.abs(g - gref).reshape(nq, nk, -1).max(axis=2)
+    m = np.abs(gref).reshape(nq, nk, -1).max(axis=2)
+    return float((d / np.where(m > 0, m, 1.0)).max())
+
+
+def check(gpu, ref, gff):
+    e_k, e_kq, om, g = gpu
+    r_k, r_kq, r_om, r_g = ref
+    assert g.dtype == np.complex64
+    S = gauge.max_rel_S(g, r_g, r_k, r_kq, r_om)
+    ff = pair_rel(g, gff)
+    print(f"S {S:.3g}  vs double-float {ff:.3g}")
+    assert S <= TOL_S
+    assert ff <= TOL_FF
+    return S, ff
+
+
+# (nb, na): pairs per tile and K of the tile arrangement
+SHAPES = [(8, 2),    # Si-shaped: 48 rows, two pairs per tile, K = 16
+          (11, 3),   # MoS2-shaped: 99 rows, one pair, K = 32
+          (3, 1),    # 9 rows: four pairs, K = 16
+          (9, 1),    # 27 rows: four pairs, K = 32 (N = 128)
+          (5, 3),    # 45 rows: two pairs
+          (16, 2),   # 96 rows: one pair, K = 32 at its limit
+          (1, 1)]    # a single band
+
+
+@pytest.mark.parametrize("nb,na", SHAPES)
+def test_band_small_k_list(nb, na):
+    wl = synth.make_workload("si_tiny", nb=nb, na=na, nk=37, nq=5)
+    ref = oracle.interpolate(wl)
+    ctx = binding.Context.from_workload(wl, form="mixed", q_batch=3, k_tile=17)
+    gpu = ctx.interp(wl.kpts, wl.qpts)
+    ff = binding.Context.from_workload(wl, form="mixed", q_batch=3, k_tile=17, band_ff=True)
+    gff = ff.interp(wl.kpts, wl.qpts)[3]
+    check(gpu, ref, gff)
+
+
+@pytest.mark.parametrize("nb,na", [(8, 2), (11, 3), (3, 1), (16, 2)])
+def test_band_small_grid(nb, na):
+    wl = synth.make_workload("si_tiny", nb=nb, na=na, nq=3)
+    grid = (3, 4, 5)
+    kpts = synth.uniform_grid(*grid)
+    ref = oracle.interpolate(wl, kpts, wl.qpts)
+    out = []
+    for band_ff in (False, True):
+        ctx = binding.Context.from_workload(wl, form="mixed", q_batch=2, band_ff=band_ff)
+        eps_k = ctx.set_k_grid(*grid)
+        out.append((eps_k,) + ctx.interp_q(wl.qpts))
+    check(out[0], ref, out[1][3])
+
+
+def test_band_small_repeated_calls_identical():
+    # the tiles are independent of the launch's grid and of earlier calls: same input, same bits
+    wl = synth.make_workload("si_tiny", nk=101, nq=4)
+    ctx = binding.Context.from_workload(wl, form="mixed")
+    a = ctx.interp(wl.kpts, wl.qpts)[3]
+    b = ctx.interp(wl.kpts, wl.qpts)[3]
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
