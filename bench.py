@@ -44,7 +44,9 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # instructions executed, from one ncu capture; profiles/k_jacobi_mixed_si_full.md), keyed by (nb, form)
 # FP64 flops per 8x8 eigensolve (2 DFMA + DMUL + DADD thread instructions from one ncu capture of
 # the 256,000-matrix launch: 1.7695e9 DFMA, 5.94e7 DMUL, 5.489e8 DADD)
-EIG_FP64_FLOPS = {(8, "fp64"): (2 * 1769472000 + 59392000 + 548864000) / 256000}
+EIG_FP64_FLOPS = {(8, "fp64"): (2 * 1769472000 + 59392000 + 548864000) / 256000,
+                  # mixed form (eigensolves stop at ~1e-12 ||A||): one launch of 55,296 matrices
+                  (8, "mixed"): (2 * 197296128 + 62816256 + 12386304) / 55296}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at one step = 4 q x 64,000 k
 TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
            ("k_zgemm", "si_full", 4): 242432512.0 + 1777470464.0,
@@ -160,14 +162,16 @@ def parse():
 # calls on the grid instead.  These are the programs the small-case profiles were taken from: a
 # 120-band, 180-mode case small enough for a full-section capture of the band-rotation
 # tensor-core product, the bench's stanene mixed leg, a silicon-shaped grid (Ne = 216) for the
-# mixed form's band rotation (tensor cores; "-ff": the double-float kernel), and the MoS2-shaped
-# differentiation workload on 8 q.
+# mixed and FP64 forms' band rotation (tensor cores; "-ff" / "-dfma": the CUDA-core kernels), and
+# the MoS2-shaped differentiation workload on 8 q.
 CAPTURES = {
     "stanene-band-tc": ("stanene", dict(nk=16, nq=2, box=(range(0, 1), range(-1, 2), range(0, 1))), "mixed", 1, 2,
                         "list"),
     "stanene-mixed": ("stanene", dict(nk=512, nq=8), "mixed", 4, 2, "list"),
     "si-mixed-grid": ("si_full", dict(nq=8), "mixed", 4, 2, "grid24"),
-    "si-mixed-grid-ff": ("si_full", dict(nq=8), "mixed", 4, 2, "grid24", dict(band_ff=True)),
+    "si-mixed-grid-ff": ("si_full", dict(nq=8), "mixed", 4, 2, "grid24", dict(band_alu=True)),
+    "si-fp64-grid": ("si_full", dict(nq=8), "fp64", 4, 2, "grid24"),
+    "si-fp64-grid-dfma": ("si_full", dict(nq=8), "fp64", 4, 2, "grid24", dict(band_alu=True)),
     "mos2-diff-backward": ("mos2_diff", dict(nq=8), "fp64", 4, 1, "backward"),
 }
 
@@ -489,9 +493,23 @@ def time_backward(args):
 
     ms_autograd = timed(step, 3)
     el = nk * nq * nm * nb * nb
+    # dominant kernel: k_band_adjoint (stage "band" of the backward call), V_{k+q} (2 c g) V_k^H
+    # with the loss terms: 2 Nb^3 Nm complex multiply-adds per (k,q) pair at 8 flop each
+    band_ms, band_n = prof.get("band", (0.0, 0))
+    cmac = 2.0 * nb ** 3 * nm * nk * nq
+    ach = 8.0 * cmac / (band_ms * 1e-3) if band_ms else None
+    roof = {"bound": "alu", "kernel": "k_band_adjoint (FP64, V_{k+q} (2 c g) V_k^H and the loss terms)",
+            "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_FLOPS if ach else None, "flop_per_cmac": 8, "launches": band_n,
+            "ms_per_launch": band_ms / max(band_n, 1),
+            # G3 rows and V_k, V_{k+q} read, G3bar written (complex128), w and omega
+            "algorithmic_bytes_per_launch": 16.0 * nk * nq * (2 * nm * nb * nb + 2 * nb * nb) / max(band_n, 1),
+            "share_of_call": band_ms / ms_grid if ms_grid else None,
+            "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
     return {"workload": "mos2_diff: Nb=11 Nm=9 Ne=Np=144, 48x48 k grid x 256 q, FP64 adjoint (forward recomputed)",
             "ms_per_call": ms_grid, "g_elements_per_s": el / (ms_grid * 1e-3), "k_path": "grid (kpts NULL)",
             "stage_ms_per_call": {k: round(v[0], 3) for k, v in prof.items() if v[0] > 0},
+            "roofline": roof,
             "k_list": {"ms_per_call": ms_list, "g_elements_per_s": el / (ms_list * 1e-3)},
             "autograd_step": {"what": "EphLoss.apply + backward() on CUDA tensors: eph_set_gw (device copy of "
                                       "g(Re,Rp)), eph_interp_backward on the grid, grad scaling",
@@ -782,9 +800,9 @@ def run_libeph(args):
                 "algorithmic_bytes": 16.0 * (pairs * (nm * nb * nb + nb * nb + nb * nb) + pairs * nm * nb * nb),
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
 
-    def roof_eig(r):
+    def roof_eig(r, form="fp64"):
         eg_ms, eg_n = r["prof"]["eig"]
-        per = EIG_FP64_FLOPS.get((nb, "fp64"))
+        per = EIG_FP64_FLOPS.get((nb, form))
         t = eg_ms / max(eg_n, 1) * 1e-3
         mats = float(args.steps) * QB * nk / max(eg_n, 1)
         ach = per * mats / t if per else None
@@ -793,9 +811,30 @@ def run_libeph(args):
                 "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_FLOPS if ach else None,
                 "fp64_flop_per_matrix": per, "matrices_per_launch": mats,
-                "traffic": TRAFFIC.get(("k_jacobi_mixed", args.workload, QB)),
+                "traffic": TRAFFIC.get(("k_jacobi_mixed", args.workload, QB)) if form == "fp64" else None,
                 "algorithmic_bytes": mats * (nb * nb * 16 + nb * nb * 16 + nb * 8),
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
+
+    def roof_band_tc(r, g3_bytes):
+        # the mixed form's fused tensor-core band rotation (k_band_tc_small) against HBM: G3 rows in
+        # (complex128 from the FP64 grid transforms, complex64 from the tensor-core contraction),
+        # V_{k+q} per pair and V_k per tile of pairs (two q at one k for these shapes) in, g out
+        bd_ms, bd_n = r["prof"]["band"]
+        pairs = float(args.steps) * QB * nk
+        ppt = max(1, min(4, 128 // (((nm * nb + 31) // 32) * 32)))
+        per_pair = g3_bytes * nm * nb * nb + 16.0 * nb * nb + 16.0 * nb * nb / ppt + 8.0 * nm * nb * nb
+        t = bd_ms * 1e-3
+        ach = per_pair * pairs / t if t else None
+        peak = peaks.get("hbm_gbs")
+        return {"bound": "hbm", "kernel": "k_band_tc_small (tcgen05 kind::f16, four-digit fixed-point BF16 operands)",
+                "achieved": ach / 1e9 if ach else None, "peak": peak, "unit": "GB/s",
+                "frac": (ach / 1e9 / peak) if (ach and peak) else None,
+                "algorithmic_bytes_per_pair": per_pair, "pairs_per_launch": pairs / max(bd_n, 1),
+                "traffic": None,
+                "cmac_per_pair": 2 * nb ** 3 * nm,
+                "note": "issue-bound on the digit arithmetic (ncu: 63 % issue, tensor pipe 9 %, DRAM 26 %); "
+                        "profiles/k_band_tc_small_si_mixed_grid24.md",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs, measured" if peak else "unavailable"}
 
     def dominant_roofline(r):
         st = {k: v[0] for k, v in r["prof"].items()}
@@ -875,13 +914,18 @@ def run_libeph(args):
             line["mixed"] = {"value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"],
                              "k_path": line["config"]["k_path"],
                              "gain_vs_fp64": m["value"] / head["value"],
-                             "dtype": "f64 Re->k and eigensolve refinement, double-float band rotation, c64 g"
-                                      if use_grid else "bf16 digits / f32 accumulate",
+                             "dtype": "f64 Re->k and eigensolve refinement, tensor-core (bf16 digit) band rotation "
+                                      "and Eq. 9, c64 g" if use_grid else "bf16 digits / f32 accumulate",
                              "rel_err_bar": "<= 1e-6 on |g|^2 subspace sums (tests/test_gpu_mixed.py, "
                                             "tests/test_gpu_grid.py); eps, omega <= 1e-10",
                              "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in m["prof"].items()},
                              "gpu_launches": m["launches"], "clocks": m["clocks"]}
-            if not use_grid:
+            mst = {k: v[0] for k, v in m["prof"].items()}
+            if use_grid:
+                sr = {"eig": roof_eig(m, "mixed"), "ft_k": roof_axis(m), "band": roof_band_tc(m, 16.0)}
+                line["mixed"]["roofline"] = sr[max(("eig", "ft_k", "band"), key=lambda k: mst.get(k, 0.0))]
+                line["mixed"]["stage_rooflines"] = sr
+            else:
                 line["mixed"]["roofline_tensor_kernel"] = roof_tc(m)
         if use_grid and ("fp64", False) in res:
             fl, ml = res[("fp64", False)], res[("mixed", False)]
@@ -892,10 +936,11 @@ def run_libeph(args):
                          "roofline": roof_fp64(fl), "gpu_launches": fl["launches"], "clocks": fl["clocks"]},
                 "mixed": {"value": ml["value"], "unit": UNIT, "ms_per_step": ml["ms_per_step"],
                           "gain_vs_fp64": ml["value"] / fl["value"], "dtype": "bf16 digits / f32 accumulate",
-                          "rel_err_bar": "<= 1e-6 on |g|^2 subspace sums (measured 3.2e-7 si_full); eps_kq <= 1e-10 "
+                          "rel_err_bar": "<= 1e-6 on |g|^2 subspace sums (measured 4.1e-7 si_full); eps_kq <= 1e-10 "
                                          "(measured 2.1e-11)",
                           "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in ml["prof"].items()},
                           "roofline_tensor_kernel": roof_tc(ml), "roofline_hkq_kernel": roof_hkq(ml),
+                          "roofline_band_kernel": roof_band_tc(ml, 8.0),
                           "gpu_launches": ml["launches"], "clocks": ml["clocks"]}}
 
     # end to end through the public C-ABI with HOST buffers (pinned), copies inside the timed region

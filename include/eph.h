@@ -54,7 +54,7 @@ enum eph_form {
                          (Eq. 9) is one too while its digit planes stay below ~4 GB (Si- and
                          MoS2-shaped inputs; FP64 otherwise); the band rotation runs on the tensor
                          cores (fused two-product kernel for nb <= 16, nm*nb <= 128; batched
-                         products beyond; option band_ff selects double-float FP32 for the former);
+                         products beyond; option band_alu selects double-float FP32 for the former);
                          the eigensolves stop at eigenvalues within ~1e-12 ||A|| and eigenvectors
                          within ~1e-8.  Phases (exact FP64 reduction), D(q) and its eigensolve and,
                          on uniform grids, the Re->k transforms stay FP64 */
@@ -81,10 +81,12 @@ typedef struct eph_options {
                          form, uniform-grid path or nb, nm > 16) the outputs are copied to the host
                          asynchronously, g on a second stream: the host buffers must stay valid,
                          and should be pinned, until eph_sync returns */
-  int band_ff;        /* mixed form, nb <= 16 and nm*nb <= 128: 0 (default) = band rotation on the
-                         tensor cores (four fixed-point BF16 digits per operand, exact level-0
-                         accumulation, ~2^-31 of each pair's largest element); 1 = double-float
-                         FP32 arithmetic on the CUDA cores */
+  int band_alu;       /* nb <= 16 and nm*nb <= 128: 0 (default) = band rotation on the tensor cores,
+                         fixed-point BF16 digit products with exact level sums (mixed form: four
+                         digits per operand, ~2^-31 of each pair's largest element; FP64 form: six
+                         digits, levels <= 6, integer assembly of the doubles, ~1e-14); 1 = on the
+                         CUDA cores (double-float FP32 in the mixed form, FP64 DFMA in the FP64
+                         form) */
 } eph_options;
 
 /* Fills *opt with the defaults (FP64 form, host pointers, automatic batching). */
@@ -350,8 +352,9 @@ enum eph_stage {
                           (on a product k grid also the axis-3 and axis-2 transforms)        */
   EPH_STAGE_FT_K = 4,  /* Re->k contraction (Eq. 10 Fourier sum) fused with H(k+q); on a
                           product k grid its per-k part, the axis-1 transform              */
-  EPH_STAGE_BAND = 5,  /* band rotation V_{k+q}^H G V_k                                         */
-  EPH_STAGE_ADJ = 6,   /* adjoint (backward) kernels                                            */
+  EPH_STAGE_BAND = 5,  /* band rotation V_{k+q}^H G V_k (in eph_interp_backward: its adjoint
+                          V_{k+q} (2 c g) V_k^H with the loss terms)                       */
+  EPH_STAGE_ADJ = 6,   /* the other adjoint (backward) kernels                                  */
   EPH_STAGE_TC = 7,    /* mixed form: tensor-core (tcgen05) Re->k contraction                   */
   EPH_NSTAGES = 8
 };

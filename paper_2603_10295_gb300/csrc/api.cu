@@ -987,9 +987,9 @@ bool mixed_list(const eph_ctx* ctx) {
   return ctx->opt.form == EPH_FORM_MIXED && !ctx->has_grid && (!ctx->big || use_band_tc(ctx));
 }
 
-// mixed form, small shapes: the fused tensor-core band rotation unless the double-float one is asked for
+// small shapes: the fused tensor-core band rotation (both forms) unless the CUDA-core one is asked for
 bool small_band_tc(const eph_ctx* ctx) {
-  return !ctx->opt.band_ff && eph::band_tc_small_supported(ctx->nm, ctx->nb);
+  return !ctx->opt.band_alu && eph::band_tc_small_supported(ctx->nm, ctx->nb);
 }
 
 // workspace of the tensor-core band rotation for npairs pairs of a tile of nkt k points: the
@@ -1023,8 +1023,12 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
     return EPH_OK;
   }
   if (!ctx->big) {
-    EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, Ukq, Uk, nqb, nkt, nm, nb, out, sgq, ctx->stream,
-                                                    keep));
+    if (small_band_tc(ctx))  // FP64 accuracy from six-digit tensor-core products, no FP64 instruction
+      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc_small64(Y + nb2, p.NW, Ukq, Uk, nqb, nkt, nm, nb, out, sgq, keep,
+                                                               ctx->status + 1, ctx->stream));
+    else
+      EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_rotate(Y + nb2, p.NW, Ukq, Uk, nqb, nkt, nm, nb, out, sgq, ctx->stream,
+                                                      keep));
     return EPH_OK;
   }
   if (use_band_tc(ctx)) {  // mixed form: two batched five-digit tensor-core products
@@ -1733,7 +1737,7 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
       // recompute the Re->k stage and the gauges for this tile (never stored across tiles)
       EPH_TRY(k_tile_forward(ctx, p, nqb, k0, nkt));
       // g, L and G3bar = V_{k+q} (2 c g) V_k^H in place of G3
-      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_band_adjoint(Y + nb2, p.NW, as<double2>(ctx->Ukq),
+      EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_adjoint(Y + nb2, p.NW, as<double2>(ctx->Ukq),
                                                       as<double2>(ctx->Uk) + k0 * nb2, wdev + k0 * nb,
                                                       as<double>(ctx->omq), omega_min, nqb, nkt, nm, nb,
                                                       as<double>(ctx->Lpair), ctx->stream));

@@ -739,13 +739,15 @@ struct SmallShape {
   size_t smem;
 };
 
-SmallShape small_shape(int nm, int nb) {
+// nacc accumulators of PPT * KP columns each must fit the 512 TMEM columns
+SmallShape small_shape(int nm, int nb, int nacc = 2) {
   SmallShape s{};
   const int R = nm * nb;
   s.kp = 2 * nb <= 16 ? 16 : 32;
   s.rs = ((R + 31) / 32) * 32;
   s.ppt = s.rs > 0 ? 128 / s.rs : 0;
   if (s.ppt > 4) s.ppt = 4;
+  while (s.ppt > 1 && nacc * s.ppt * s.kp > 512) --s.ppt;
   s.n1 = s.ppt * s.kp;
   uint32_t c = 32;
   while (c < (uint32_t)(2 * s.n1)) c <<= 1;
@@ -758,6 +760,367 @@ SmallShape small_shape(int nm, int nb) {
 size_t small_smem(const SmallShape& s, int nm, int nb, size_t elem_bytes) {
   const size_t g3 = (((size_t)s.ppt * nm * nb * nb * elem_bytes) + 15) & ~(size_t)15;
   return s.smem + g3 + (size_t)(s.ppt + 1) * nb * nb * 16;
+}
+
+// ---------------------------------------------------------------------------------------------
+// The same fused band rotation at FP64 accuracy (the FP64 form, complex128 g), still on the
+// tensor cores: every operand is six balanced base-256 digits (48 bits, |D| <= 128, exact in bf16)
+// of a fixed-point value relative to a power-of-two scale (G3 and U: one scale per pair; V: 2).
+// Digit products of levels i + j <= 6 (26 MMAs per K step) go to five accumulators: levels 0-3
+// each alone, where their sums are exact integers in FP32 (|sum| < 2^22 for K <= 32), levels 4-6
+// together (2^-32 below level 0: the tensor core's per-instruction FP32 rounding of that sum, ~2^-23
+// of it, is ~2^-55 of the result).  The five sums become integers on a 2^-48 grid (adding
+// 1.5 * 2^23 after scaling; the combined levels in two exact pieces) combined in 64-bit integers; U
+// is re-digitised from that integer and g is assembled from it as an IEEE double with integer
+// operations.  No FP64 instruction runs; the error is the digits' rounding (2^-49 of the scale) and
+// the dropped levels >= 7: ~5e-14 of each pair's largest |g|^2 (an exact integer model of these
+// steps on random inputs).
+namespace bt64 {
+constexpr int ND = 6;
+constexpr int NACC = 5;
+// balanced digits of X (|X| <= 2^47), value X 2^-48 = sum_i e_i, e_i = D_i 2^-8(i+1)
+__device__ __forceinline__ void xdigits(long long X, float (&e)[ND]) {
+  const long long d0 = (X + (1LL << 39)) >> 40;
+  X -= d0 << 40;
+  const long long d1 = (X + (1LL << 31)) >> 32;
+  int x = (int)(X - (d1 << 32));  // |x| <= 2^31 - 1 after rounding: [-2^31, 2^31)
+  const int d2 = (int)(((long long)x + (1 << 23)) >> 24);
+  x = (int)((unsigned)x - ((unsigned)d2 << 24));  // exact: the remainder fits (wrap-around arithmetic)
+  const int d3 = (x + (1 << 15)) >> 16;
+  x -= d3 << 16;
+  const int d4 = (x + (1 << 7)) >> 8;
+  x -= d4 << 8;
+  using bts::i2f;
+  e[0] = __fmul_rn(i2f((int)d0), 0x1p-8f);
+  e[1] = __fmul_rn(i2f((int)d1), 0x1p-16f);
+  e[2] = __fmul_rn(i2f(d2), 0x1p-24f);
+  e[3] = __fmul_rn(i2f(d3), 0x1p-32f);
+  e[4] = __fmul_rn(i2f(d4), 0x1p-40f);
+  e[5] = __fmul_rn(i2f(x), 0x1p-48f);
+}
+// x / 2^(emax - 1021) as a signed 48-bit fixed-point integer (rounded), emax >= the biased
+// exponent of x, so that |x| / 2^(emax - 1021) < 1/2
+__device__ __forceinline__ long long dfixed48(double x, int emax) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return 0LL;
+  const long long m = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+  const int sh = emax + 6 - e;  // X = m 2^(e - 1075) 2^(48 - (emax - 1021)) = m >> (emax + 6 - e), rounded
+  const long long M = sh < 53 ? ((m + (1LL << (sh - 1))) >> sh) : 0LL;
+  return (b >> 63) ? -M : M;
+}
+__device__ __forceinline__ int dexp(double x) { return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF); }
+// the integer n = L 2^k of a level sum (|n| < 2^22; rounded for the combined levels)
+__device__ __forceinline__ long long lvl(float L, float twok) {
+  return (long long)(__float_as_int(__fmaf_rn(L, twok, 12582912.0f)) - 0x4B400000);
+}
+// X = n0 2^32 + n1 2^24 + n2 2^16 + n3 2^8 + n4, in units of 2^-48 of the product of the operand
+// scales: n0..n3 exact; n4 = the combined levels 4-6 rounded to 2^-48
+__device__ __forceinline__ long long combine(float l0, float l1, float l2, float l3, float l4) {
+  return (lvl(l0, 0x1p16f) << 32) + (lvl(l1, 0x1p24f) << 24) + (lvl(l2, 0x1p32f) << 16) + (lvl(l3, 0x1p40f) << 8) +
+         lvl(l4, 0x1p48f);
+}
+// X 2^E as an IEEE double, exactly (|X| < 2^53), from integer operations
+__device__ __forceinline__ double i2d_scaled(long long X, int E) {
+  if (X == 0) return 0.0;
+  const unsigned long long sgn = X < 0 ? (1ULL << 63) : 0ULL;
+  const unsigned long long M = X < 0 ? (unsigned long long)(-X) : (unsigned long long)X;
+  const int lz = __clzll((long long)M);
+  const int bl = 64 - lz;  // bit length
+  const unsigned long long mant = (M << (lz + 1)) >> 12;
+  const long long ex = (long long)(bl - 1 + E + 1023);
+  if (ex <= 0) return 0.0;  // below the normal range
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | mant));
+}
+// the 26 digit products of levels <= 6 over KP/16 K steps into accumulator min(level, 4)
+template <int KP>
+__device__ __forceinline__ void mma_levels64(uint32_t acc, int ncol, uint32_t sA, int a_tile, uint32_t sB, int b_tile,
+                                             uint32_t id) {
+#pragma unroll
+  for (int ks = 0; ks < KP / 16; ++ks) {
+    bool first[NACC] = {ks == 0, ks == 0, ks == 0, ks == 0, ks == 0};
+#pragma unroll
+    for (int lv = 0; lv <= ND; ++lv) {
+      const int a_i = lv < NACC ? lv : NACC - 1;
+#pragma unroll
+      for (int i = (lv > ND - 1 ? lv - (ND - 1) : 0); i <= (lv < ND - 1 ? lv : ND - 1); ++i) {
+        const uint64_t da = bts::desc<KP>(sA + i * a_tile + ks * 256);
+        const uint64_t db = bts::desc<KP>(sB + (lv - i) * b_tile + ks * 256);
+        bts::mma(acc + (uint32_t)(a_i * ncol), da, db, id, first[a_i] ? 0u : 1u);
+        first[a_i] = false;
+      }
+    }
+  }
+}
+}  // namespace bt64
+
+template <int KP>
+__global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_small64(
+    const double2* __restrict__ Y, long ldy, const double2* __restrict__ Ukq, const double2* __restrict__ Uk, int nq,
+    int nk, int nm, int nb, int RS, int PPT, double2* __restrict__ g, long sgq, const int* __restrict__ keep,
+    int* __restrict__ err, uint32_t tmem_cols) {
+  using namespace bts;
+  using bt64::ND;
+  using bt64::NACC;
+  constexpr int A_TILE = 128 * KP * 2;
+  constexpr int B2_TILE = KP * KP * 2;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int N1 = PPT * KP;
+  const int B1_TILE = N1 * KP * 2;
+  unsigned char* A = sm;                  // [ND][128 x KP]
+  unsigned char* B1 = A + ND * A_TILE;    // [ND][N1 x KP]
+  unsigned char* B2 = B1 + ND * B1_TILE;  // [ND][KP x KP]
+  const int per = nm * nb * nb;
+  unsigned char* rawG = B2 + ND * B2_TILE;                                   // [PPT][per] complex128
+  unsigned char* rawV = rawG + (size_t)PPT * per * sizeof(double2);          // [PPT + 1][nb2]
+  int* gmax = reinterpret_cast<int*>(rawV + (size_t)(PPT + 1) * nb * nb * sizeof(double2));  // [4] G3 exponent
+  int* umax = gmax + 4;                                                      // [4] bit length of U
+  uint64_t* bar = reinterpret_cast<uint64_t*>(umax + 4);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nb2 = nb * nb, R = nm * nb;
+  const uint32_t sA = smem_u32(A), sB1 = smem_u32(B1), sB2 = smem_u32(B2);
+  const uint32_t sRawG = smem_u32(rawG), sRawV = smem_u32(rawV);
+  const double2* gsm = reinterpret_cast<const double2*>(rawG);
+  const double2* vsm = reinterpret_cast<const double2*>(rawV);
+
+  for (int i = tid; i < (ND * (A_TILE + B1_TILE + B2_TILE)) / 16; i += THREADS)
+    reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;  // accumulator a (level a, 4: levels 4-6) at columns a * N1 .. a * N1 + N1 - 1
+  const int j = tid / RS, rr = tid - j * RS;
+  const bool row_ok = j < PPT && rr < R;
+  const int nu1 = rr / nb, x1 = rr - nu1 * nb;  // stage 1 row (nu, n')
+  const int m2 = rr / nm, nu2 = rr - m2 * nm;   // stage 2 row (m, nu)
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tl1 = lane_base + (uint32_t)(j < PPT ? j * KP : 0);
+  const unsigned div_nb = (65536u + nb - 1) / nb, div_nb2 = (65536u + nb2 - 1) / nb2;
+  uint32_t phase = 0;
+  const int nqg = (nq + PPT - 1) / PPT;
+  const long ntiles = (long)nqg * nk;
+  auto prefetch = [&](long tt) {
+    if (tt >= ntiles) return;
+    const int kk = (int)(tt % nk), qg = (int)(tt / nk);
+    for (int jj = 0; jj < PPT; ++jj) {
+      const int iq = qg * PPT + jj;
+      if (iq >= nq) break;
+      const long P = (long)iq * nk + kk;
+      const double2* src = Y + P * ldy;
+      const uint32_t dst = sRawG + (uint32_t)((size_t)jj * per * sizeof(double2));
+      for (int i = tid; i < per; i += THREADS) cp_async<16>(dst + (uint32_t)(i * 16), src + i);
+      const double2* vs = Ukq + P * nb2;
+      for (int i = tid; i < nb2; i += THREADS) cp_async<16>(sRawV + (uint32_t)((jj * nb2 + i) * 16), vs + i);
+    }
+    const double2* vk = Uk + (long)kk * nb2;
+    for (int i = tid; i < nb2; i += THREADS) cp_async<16>(sRawV + (uint32_t)((PPT * nb2 + i) * 16), vk + i);
+    cp_async_commit();
+  };
+  auto wait_mma = [&]() -> bool {
+    const bool ok = wait(bar, phase & 1);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(err, 16);
+        wait(bar, phase & 1);  // bounded: the MMAs must be done before the TMEM is released
+      }
+      return false;
+    }
+    ++phase;
+    fence_after();
+    return true;
+  };
+  prefetch(blockIdx.x);
+
+  for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int kk = (int)(t % nk), qg = (int)(t / nk);
+    if (tid < 4) {
+      gmax[tid] = 0;
+      umax[tid] = 0;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int iq = qg * PPT + j;
+    const bool live = row_ok && iq < nq;
+    const long P = (long)iq * nk + kk;
+    const double2* src = gsm + (long)j * per + (long)nu1 * nb2 + x1;
+    // ---- pair maximum of the G3 exponents
+    if (live) {
+      int eb = 0;
+#pragma unroll
+      for (int a = 0; a < KP / 2; ++a)
+        if (a < nb) {
+          const double2 z = src[(long)a * nb];
+          eb = max(eb, max(bt64::dexp(z.x), bt64::dexp(z.y)));
+        }
+      atomicMax(&gmax[j], eb);
+    }
+    // ---- B operands: digits of conj(V_{k+q}) (stage 1, block per pair) and V_k (stage 2), scale 2
+    // (|v| <= 1 for unitary V)
+    for (int e = tid; e < (PPT + 1) * nb2; e += THREADS) {
+      const int jj = (int)(((unsigned)e * div_nb2) >> 16), r2 = e - jj * nb2;
+      const int a = (int)(((unsigned)r2 * div_nb) >> 16), c = r2 - a * nb;
+      float vr[ND], vi[ND];
+      if (jj < PPT) {
+        if (qg * PPT + jj >= nq) continue;
+        const double2 u = vsm[jj * nb2 + r2];
+        bt64::xdigits(bt64::dfixed48(u.x, 1022), vr);
+        bt64::xdigits(bt64::dfixed48(u.y, 1022), vi);
+        const uint32_t o0 = off<KP>(jj * KP + 2 * c, 2 * a), o1 = off<KP>(jj * KP + 2 * c + 1, 2 * a);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          st32(sB1 + d * B1_TILE + o0, pack2(vr[d], vi[d]));
+          st32(sB1 + d * B1_TILE + o1, pack2(-vi[d], vr[d]));
+        }
+      } else {
+        const double2 u = vsm[PPT * nb2 + r2];
+        bt64::xdigits(bt64::dfixed48(u.x, 1022), vr);
+        bt64::xdigits(bt64::dfixed48(u.y, 1022), vi);
+        const uint32_t o0 = off<KP>(2 * c, 2 * a), o1 = off<KP>(2 * c + 1, 2 * a);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          st32(sB2 + d * B2_TILE + o0, pack2(vr[d], -vi[d]));
+          st32(sB2 + d * B2_TILE + o1, pack2(vi[d], vr[d]));
+        }
+      }
+    }
+    __syncthreads();
+    // ---- stage-1 A: digits of the G3 rows relative to 2^(emax - 1021) of the pair
+    const int gex = j < PPT ? gmax[j] : 0;
+    if (live) {
+#pragma unroll
+      for (int c = 0; c < KP / 8; ++c) {
+        uint32_t w[ND][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int a = 4 * c + i;
+          float dr[ND], di[ND];
+          if (a < nb) {
+            const double2 z = src[(long)a * nb];
+            bt64::xdigits(bt64::dfixed48(z.x, gex), dr);
+            bt64::xdigits(bt64::dfixed48(z.y, gex), di);
+          } else {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) dr[d] = di[d] = 0.f;
+          }
+#pragma unroll
+          for (int d = 0; d < ND; ++d) w[d][i] = pack2(dr[d], di[d]);
+        }
+        const uint32_t o = off<KP>(tid, 8 * c);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) st128(sA + d * A_TILE + o, w[d][0], w[d][1], w[d][2], w[d][3]);
+      }
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    prefetch(t + gridDim.x);
+    if (tid == 0) {
+      fence_after();
+      bt64::mma_levels64<KP>(tmem, N1, sA, A_TILE, sB1, B1_TILE, idesc(N1));
+      commit(bar);
+    }
+    if (!wait_mma()) break;
+    // ---- epilogue 1: U (row (nu, n'), columns (m, re/im)) as integers X in units of
+    // 2^-48 * 2^(gex - 1021) * 2 (the G3 and V scales); pair maximum of the bit lengths
+    long long X[KP];
+    {
+      float l0[KP], l1[KP], l2[KP], l3[KP], l4[KP];
+#pragma unroll
+      for (int c = 0; c < KP; c += 16) {
+        ld16(tl1 + c, l0 + c);
+        ld16(tl1 + (uint32_t)N1 + c, l1 + c);
+        ld16(tl1 + (uint32_t)(2 * N1) + c, l2 + c);
+        ld16(tl1 + (uint32_t)(3 * N1) + c, l3 + c);
+        ld16(tl1 + (uint32_t)(4 * N1) + c, l4 + c);
+      }
+      ld_wait();
+      int bl = 0;
+#pragma unroll
+      for (int c = 0; c < KP; ++c) {
+        X[c] = bt64::combine(l0[c], l1[c], l2[c], l3[c], l4[c]);
+        const unsigned long long M = X[c] < 0 ? (unsigned long long)(-X[c]) : (unsigned long long)X[c];
+        if (c < 2 * nb) bl = max(bl, 64 - __clzll((long long)M));
+      }
+      if (live) atomicMax(&umax[j], bl);
+    }
+    fence_before();
+    __syncthreads();
+    // ---- stage-2 A: digits of U relative to 2^B (B = the pair's largest bit length + 1), rows (m, nu)
+    const int B = (j < PPT ? umax[j] : 0) + 1;
+    if (live) {
+#pragma unroll
+      for (int m = 0; m < KP / 2; ++m) {
+        if (m < nb) {
+          float dr[ND], di[ND];
+#pragma unroll
+          for (int t2 = 0; t2 < 2; ++t2) {
+            const long long x = X[2 * m + t2];
+            // x / 2^B as a 48-bit fraction (|x| < 2^(B - 1)); shifts of the magnitude keep the sign exact
+            const unsigned long long M = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+            const long long F = (long long)(B <= 48 ? (M << (48 - B)) : (M >> (B - 48)));
+            bt64::xdigits(x < 0 ? -F : F, t2 == 0 ? dr : di);
+          }
+          const uint32_t o = off<KP>(j * RS + m * nm + nu1, 2 * x1);
+#pragma unroll
+          for (int d = 0; d < ND; ++d) st32(sA + d * A_TILE + o, pack2(dr[d], di[d]));
+        }
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after();
+      bt64::mma_levels64<KP>(tmem, N1, sA, A_TILE, sB2, B2_TILE, idesc(KP));
+      commit(bar);
+    }
+    if (!wait_mma()) break;
+    // ---- epilogue 2: g rows (m, nu), columns (n, re/im) = X_g 2^-48 * 2 * (2^B 2^-48 2^(gex - 1021) 2)
+    {
+      float l0[KP], l1[KP], l2[KP], l3[KP], l4[KP];
+#pragma unroll
+      for (int c = 0; c < KP; c += 16) {
+        ld16(lane_base + c, l0 + c);
+        ld16(lane_base + (uint32_t)N1 + c, l1 + c);
+        ld16(lane_base + (uint32_t)(2 * N1) + c, l2 + c);
+        ld16(lane_base + (uint32_t)(3 * N1) + c, l3 + c);
+        ld16(lane_base + (uint32_t)(4 * N1) + c, l4 + c);
+      }
+      ld_wait();
+      if (live) {
+        double2* out = g + (long)iq * sgq + (long)kk * nm * nb2 + (long)nu2 * nb2 + (long)m2 * nb;
+        const bool zero = keep && !keep[P];
+        // U = X_U 2^-48 2^(gex - 1021) 2; stage-2 A holds U / (2^B 2^-48 2^(gex - 1021) 2)
+        const int E = B - 48 + (gex - 1021) + 1 + 1 - 48;
+#pragma unroll
+        for (int n = 0; n < KP / 2; ++n) {
+          if (n < nb) {
+            const long long xr = bt64::combine(l0[2 * n], l1[2 * n], l2[2 * n], l3[2 * n], l4[2 * n]);
+            const long long xi = bt64::combine(l0[2 * n + 1], l1[2 * n + 1], l2[2 * n + 1], l3[2 * n + 1], l4[2 * n + 1]);
+            out[n] = zero ? make_double2(0.0, 0.0) : make_double2(bt64::i2d_scaled(xr, E), bt64::i2d_scaled(xi, E));
+          }
+        }
+      }
+    }
+    fence_before();
+    __syncthreads();
+  }
+  cp_async_wait_all();
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  }
 }
 
 // Shared-memory request and CTAs per SM of a launch: what the registers, threads and shared memory
@@ -857,6 +1220,36 @@ cudaError_t launch_band_tc_small(const void* Y, int y_f32, long ldy, const doubl
     if (s.kp == 16) EPH_SMALL_LAUNCH(double2, 16); else EPH_SMALL_LAUNCH(double2, 32);
   }
 #undef EPH_SMALL_LAUNCH
+  return cudaGetLastError();
+}
+
+// FP64-accurate variant (complex128 G3 in, complex128 g out)
+cudaError_t launch_band_tc_small64(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
+                                   int nm, int nb, double2* g, long sgq, const int* keep, int* err, cudaStream_t st) {
+  if ((long)nq * nk <= 0) return cudaSuccess;
+  if (!band_tc_small_supported(nm, nb) || nk < 1) return cudaErrorInvalidValue;
+  const SmallShape s = small_shape(nm, nb, bt64::NACC);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorInvalidDevice;
+  const long ntiles = (long)((nq + s.ppt - 1) / s.ppt) * nk;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(bt64::NACC * s.n1)) cols <<= 1;
+  const size_t need = (size_t)bt64::ND * (128 * s.kp * 2 + (size_t)s.n1 * s.kp * 2 + (size_t)s.kp * s.kp * 2) +
+                      (size_t)s.ppt * nm * nb * nb * 16 + (size_t)(s.ppt + 1) * nb * nb * 16 + 64;
+  cudaError_t e;
+  const void* kern = s.kp == 16 ? reinterpret_cast<const void*>(k_band_tc_small64<16>)
+                                : reinterpret_cast<const void*>(k_band_tc_small64<32>);
+  size_t smem = 0;
+  int occ = 0;
+  if ((e = small_occupancy(kern, need, (int)(512 / cols), &smem, &occ)) != cudaSuccess) return e;
+  const long grid = std::min(ntiles, (long)sms * occ);
+  if (s.kp == 16)
+    k_band_tc_small64<16><<<(unsigned)grid, bts::THREADS, smem, st>>>(Y, ldy, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, g,
+                                                                      sgq, keep, err, cols);
+  else
+    k_band_tc_small64<32><<<(unsigned)grid, bts::THREADS, smem, st>>>(Y, ldy, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, g,
+                                                                      sgq, keep, err, cols);
   return cudaGetLastError();
 }
 

@@ -238,6 +238,10 @@ bool band_tc_small_supported(int nm, int nb);
 cudaError_t launch_band_tc_small(const void* Y, int y_f32, long ldy, const double2* Ukq, const double2* Uk, int nq,
                                  int nk, int nm, int nb, float2* g, long sgq, const int* keep, int* err,
                                  cudaStream_t st);
+// The same rotation at FP64 accuracy (seven-digit operands, exact level sums, integer assembly of
+// the doubles): complex128 G3 in, complex128 g out, ~1e-14 of each pair's largest element.
+cudaError_t launch_band_tc_small64(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
+                                   int nm, int nb, double2* g, long sgq, const int* keep, int* err, cudaStream_t st);
 cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const double2* Ukq, const double2* Uk, int nq,
                            int nk, int nm, int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err,
                            cudaStream_t st);

@@ -1,5 +1,6 @@
-"""Fused tensor-core band rotation of the mixed form (nb <= 16, nm nb <= 128): g = V_{k+q}^H G3 V_k
-as two tcgen05 products of four-digit fixed-point BF16 operands per tile of (k,q) pairs.
+"""Fused tensor-core band rotation (nb <= 16, nm nb <= 128): g = V_{k+q}^H G3 V_k as two tcgen05
+products of fixed-point BF16 digit operands per tile of (k,q) pairs; four digits in the mixed form,
+six digits with exact level sums and integer-assembled doubles in the FP64 form.
 
 Checked against the FP64 CPU oracle on gauge-invariant quantities (|g|^2 subspace sums within the
 mixed form's 1e-6) and element by element against the double-float FP32 rotation of the same
@@ -20,6 +21,8 @@ pytestmark = pytest.mark.gpu
 
 TOL_S = 1e-6     # mixed form: |g|^2 subspace sums against the FP64 oracle
 TOL_FF = 3e-7    # element-wise, relative to the pair's largest |g|: tensor-core vs double-float rotation
+TOL_S64 = 1e-12  # FP64 form: |g|^2 subspace sums against the FP64 oracle
+TOL_DFMA = 1e-13  # FP64 form, element-wise relative to the pair's largest |g|: six-digit vs DFMA rotation
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -64,7 +67,7 @@ def test_band_small_k_list(nb, na):
     ref = oracle.interpolate(wl)
     ctx = binding.Context.from_workload(wl, form="mixed", q_batch=3, k_tile=17)
     gpu = ctx.interp(wl.kpts, wl.qpts)
-    ff = binding.Context.from_workload(wl, form="mixed", q_batch=3, k_tile=17, band_ff=True)
+    ff = binding.Context.from_workload(wl, form="mixed", q_batch=3, k_tile=17, band_alu=True)
     gff = ff.interp(wl.kpts, wl.qpts)[3]
     check(gpu, ref, gff)
 
@@ -76,8 +79,8 @@ def test_band_small_grid(nb, na):
     kpts = synth.uniform_grid(*grid)
     ref = oracle.interpolate(wl, kpts, wl.qpts)
     out = []
-    for band_ff in (False, True):
-        ctx = binding.Context.from_workload(wl, form="mixed", q_batch=2, band_ff=band_ff)
+    for band_alu in (False, True):
+        ctx = binding.Context.from_workload(wl, form="mixed", q_batch=2, band_alu=band_alu)
         eps_k = ctx.set_k_grid(*grid)
         out.append((eps_k,) + ctx.interp_q(wl.qpts))
     check(out[0], ref, out[1][3])
@@ -90,3 +93,53 @@ def test_band_small_repeated_calls_identical():
     a = ctx.interp(wl.kpts, wl.qpts)[3]
     b = ctx.interp(wl.kpts, wl.qpts)[3]
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def check64(gpu, ref, gd):
+    e_k, e_kq, om, g = gpu
+    r_k, r_kq, r_om, r_g = ref
+    assert g.dtype == np.complex128
+    S = gauge.max_rel_S(g, r_g, r_k, r_kq, r_om)
+    d = pair_rel(g, gd)
+    print(f"FP64 S {S:.3g}  vs DFMA {d:.3g}")
+    assert S <= TOL_S64
+    assert d <= TOL_DFMA
+    return S, d
+
+
+@pytest.mark.parametrize("nb,na", SHAPES)
+def test_band_small_fp64_k_list(nb, na):
+    wl = synth.make_workload("si_tiny", nb=nb, na=na, nk=37, nq=5)
+    ref = oracle.interpolate(wl)
+    gpu = binding.Context.from_workload(wl, q_batch=3, k_tile=17).interp(wl.kpts, wl.qpts)
+    gd = binding.Context.from_workload(wl, q_batch=3, k_tile=17, band_alu=True).interp(wl.kpts, wl.qpts)[3]
+    check64(gpu, ref, gd)
+
+
+@pytest.mark.parametrize("nb,na", [(8, 2), (11, 3), (3, 1), (16, 2)])
+def test_band_small_fp64_grid(nb, na):
+    wl = synth.make_workload("si_tiny", nb=nb, na=na, nq=3)
+    grid = (3, 4, 5)
+    ref = oracle.interpolate(wl, synth.uniform_grid(*grid), wl.qpts)
+    out = []
+    for band_alu in (False, True):
+        ctx = binding.Context.from_workload(wl, q_batch=2, band_alu=band_alu)
+        eps_k = ctx.set_k_grid(*grid)
+        out.append((eps_k,) + ctx.interp_q(wl.qpts))
+    check64(out[0], ref, out[1][3])
+
+
+def test_band_small_fp64_scaled_and_zero_inputs():
+    # the fixed point is relative to each pair's own scale: couplings scaled by 2^+-200 give the
+    # same digits, g scales exactly; an all-zero coupling gives g = 0 exactly
+    wl = synth.make_workload("si_tiny", nk=23, nq=3)
+    base = binding.Context.from_workload(wl).interp(wl.kpts, wl.qpts)[3]
+    for f in (2.0 ** 200, 2.0 ** -200):
+        w2 = synth.make_workload("si_tiny", nk=23, nq=3)
+        w2.g_ReRp = wl.g_ReRp * f
+        g = binding.Context.from_workload(w2).interp(w2.kpts, w2.qpts)[3]
+        assert np.array_equal(g, base * f)
+    w0 = synth.make_workload("si_tiny", nk=23, nq=3)
+    w0.g_ReRp = np.zeros_like(wl.g_ReRp)
+    g0 = binding.Context.from_workload(w0).interp(w0.kpts, w0.qpts)[3]
+    assert not np.any(g0)

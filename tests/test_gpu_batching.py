@@ -121,7 +121,8 @@ def test_multi_material_persistent_call_matches_separate_calls():
         ctxs.append(c)
         qs.append(q)
         outs.append(_buffers(torch, wl, nq, "fp64", dev))
-        r = binding.Context.from_workload(wl, q_batch=4, k_tile=48)
+        # the persistent kernel is the FP64 DFMA rotation: compare with separate calls that use it
+        r = binding.Context.from_workload(wl, q_batch=4, k_tile=48, band_alu=True)
         r.set_k(wl.kpts)
         refs.append(r.interp_q(wl.qpts[:nq]))
     binding.interp_q_multi(ctxs, [q.shape[0] for q in qs], qs, [o[0] for o in outs], [o[1] for o in outs],
@@ -147,7 +148,7 @@ def test_multi_material_call_in_a_graph_and_errors():
         ctxs.append(c)
         qs.append(torch.from_numpy(wl.qpts[:nq].copy()).to(dev))
         outs.append(_buffers(torch, wl, nq, "fp64", dev))
-        r = binding.Context.from_workload(wl, q_batch=4)
+        r = binding.Context.from_workload(wl, q_batch=4, band_alu=True)
         r.set_k(wl.kpts)
         eager.append(r.interp_q(wl.qpts[:nq]))
     gb.add_multi(ctxs, qs, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
