@@ -202,8 +202,10 @@ int eph_set_gw(eph_ctx* ctx, const double* g_ReRp);
  * the calls proceed in rounds, each context contributing its next (q batch, k tile) unit (phases,
  * D(q), Eq. 9 and the mode rotation at the start of a q batch; the Re->k contraction and the
  * H(k+q) eigensolves per tile), and one launch per round rotates the pairs of every context's
- * unit, its CTAs walking the concatenated pair list (k_band_rotate_multi).  Results are bit for
- * bit those of separate eph_interp_q calls.
+ * unit, its CTAs walking the concatenated pair list (k_band_rotate_multi, the FP64 DFMA rotation).
+ * Results are bit for bit those of separate eph_interp_q calls on contexts created with
+ * band_alu = 1; the default separate calls rotate on the tensor cores and agree to ~5e-14 of each
+ * pair's largest |g|.
  *   ctxs[nctx] distinct contexts, 1 <= nctx <= 32, each with a resident k list, FP64 form,
  *   nb, nm <= 16, device pointers, whole g(Re,Rp) (else EPH_ENOTSUP); nq[i], qpts[i], eps_kq[i],
  *   omega[i], g[i] as eph_interp_q's arguments for context i (eps_kq, omega, g and their
