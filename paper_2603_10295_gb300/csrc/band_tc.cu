@@ -778,25 +778,23 @@ size_t small_smem(const SmallShape& s, int nm, int nb, size_t elem_bytes) {
 namespace bt64 {
 constexpr int ND = 6;
 constexpr int NACC = 5;
-// balanced digits of X (|X| <= 2^47), value X 2^-48 = sum_i e_i, e_i = D_i 2^-8(i+1)
+// balanced digits of X (|X| < 2^47), value X 2^-48 = sum_i e_i, e_i = D_i 2^-8(i+1), |D_i| <= 128:
+// Y = X + 0x808080808080 is in [0, 2^48 + 2^40] and gives D = b - 128 from its bytes b_i (the added
+// 128 in every byte position is the carry-free offset of balanced base-256 digits); the top digit
+// takes bits 40..48 (b up to 256, D up to +128).  Each digit: one byte permute (or a shift) builds
+// the FP32 bits of 2^23 + b, one FMA subtracts 2^23 + 128 and scales, exactly.
+__device__ __forceinline__ float dig(uint32_t w, uint32_t sel, float s) {
+  return __fmaf_rn(__uint_as_float(__byte_perm(w, 0x4B000000u, sel)), s, -8388736.0f * s);
+}
 __device__ __forceinline__ void xdigits(long long X, float (&e)[ND]) {
-  const long long d0 = (X + (1LL << 39)) >> 40;
-  X -= d0 << 40;
-  const long long d1 = (X + (1LL << 31)) >> 32;
-  int x = (int)(X - (d1 << 32));  // |x| <= 2^31 - 1 after rounding: [-2^31, 2^31)
-  const int d2 = (int)(((long long)x + (1 << 23)) >> 24);
-  x = (int)((unsigned)x - ((unsigned)d2 << 24));  // exact: the remainder fits (wrap-around arithmetic)
-  const int d3 = (x + (1 << 15)) >> 16;
-  x -= d3 << 16;
-  const int d4 = (x + (1 << 7)) >> 8;
-  x -= d4 << 8;
-  using bts::i2f;
-  e[0] = __fmul_rn(i2f((int)d0), 0x1p-8f);
-  e[1] = __fmul_rn(i2f((int)d1), 0x1p-16f);
-  e[2] = __fmul_rn(i2f(d2), 0x1p-24f);
-  e[3] = __fmul_rn(i2f(d3), 0x1p-32f);
-  e[4] = __fmul_rn(i2f(d4), 0x1p-40f);
-  e[5] = __fmul_rn(i2f(x), 0x1p-48f);
+  const unsigned long long Y = (unsigned long long)X + 0x808080808080ULL;
+  const uint32_t hi = (uint32_t)(Y >> 32), lo = (uint32_t)Y;
+  e[0] = __fmaf_rn(__uint_as_float(0x4B000000u | (hi >> 8)), 0x1p-8f, -8388736.0f * 0x1p-8f);  // bits 40..48
+  e[1] = dig(hi, 0x7540, 0x1p-16f);  // byte 4
+  e[2] = dig(lo, 0x7543, 0x1p-24f);
+  e[3] = dig(lo, 0x7542, 0x1p-32f);
+  e[4] = dig(lo, 0x7541, 0x1p-40f);
+  e[5] = dig(lo, 0x7540, 0x1p-48f);
 }
 // x / 2^(emax - 1021) as a signed 48-bit fixed-point integer (rounded), emax >= the biased
 // exponent of x, so that |x| / 2^(emax - 1021) < 1/2
@@ -811,14 +809,17 @@ __device__ __forceinline__ long long dfixed48(double x, int emax) {
 }
 __device__ __forceinline__ int dexp(double x) { return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF); }
 // the integer n = L 2^k of a level sum (|n| < 2^22; rounded for the combined levels)
-__device__ __forceinline__ long long lvl(float L, float twok) {
-  return (long long)(__float_as_int(__fmaf_rn(L, twok, 12582912.0f)) - 0x4B400000);
-}
 // X = n0 2^32 + n1 2^24 + n2 2^16 + n3 2^8 + n4, in units of 2^-48 of the product of the operand
 // scales: n0..n3 exact; n4 = the combined levels 4-6 rounded to 2^-48
+__device__ __forceinline__ int lvl32(float L, float twok) {
+  return __float_as_int(__fmaf_rn(L, twok, 12582912.0f)) - 0x4B400000;
+}
 __device__ __forceinline__ long long combine(float l0, float l1, float l2, float l3, float l4) {
-  return (lvl(l0, 0x1p16f) << 32) + (lvl(l1, 0x1p24f) << 24) + (lvl(l2, 0x1p32f) << 16) + (lvl(l3, 0x1p40f) << 8) +
-         lvl(l4, 0x1p48f);
+  long long X = (long long)lvl32(l4, 0x1p48f);
+  X += (long long)lvl32(l3, 0x1p40f) * 256;  // widening multiply-adds
+  X += (long long)lvl32(l2, 0x1p32f) * 65536;
+  X += (long long)lvl32(l1, 0x1p24f) * 16777216;
+  return X + ((long long)lvl32(l0, 0x1p16f) << 32);
 }
 // X 2^E as an IEEE double, exactly (|X| < 2^53), from integer operations
 __device__ __forceinline__ double i2d_scaled(long long X, int E) {
@@ -854,17 +855,23 @@ __device__ __forceinline__ void mma_levels64(uint32_t acc, int ncol, uint32_t sA
 }
 }  // namespace bt64
 
+// One CTA per SM holds nslots independent tile slots of four warps (128 threads, TMEM lanes 0-127),
+// each with its own shared memory (slot_bytes), TMEM columns (slot_cols), mbarrier and named
+// barrier (1 + slot): the five accumulators of a slot take 160 columns at the Si shapes, so
+// three slots share one 512-column allocation where separate CTAs would each round up to 256.
 template <int KP>
-__global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_small64(
+__global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_tc_small64(
     const double2* __restrict__ Y, long ldy, const double2* __restrict__ Ukq, const double2* __restrict__ Uk, int nq,
     int nk, int nm, int nb, int RS, int PPT, double2* __restrict__ g, long sgq, const int* __restrict__ keep,
-    int* __restrict__ err, uint32_t tmem_cols) {
+    int* __restrict__ err, uint32_t tmem_cols, int nslots, unsigned slot_bytes, unsigned slot_cols) {
   using namespace bts;
   using bt64::ND;
   using bt64::NACC;
   constexpr int A_TILE = 128 * KP * 2;
   constexpr int B2_TILE = KP * KP * 2;
-  extern __shared__ __align__(1024) unsigned char sm[];
+  extern __shared__ __align__(1024) unsigned char sm_all[];
+  const int slot = threadIdx.x >> 7;
+  unsigned char* sm = sm_all + (size_t)slot * slot_bytes;
   const int N1 = PPT * KP;
   const int B1_TILE = N1 * KP * 2;
   unsigned char* A = sm;                  // [ND][128 x KP]
@@ -876,8 +883,18 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
   int* gmax = reinterpret_cast<int*>(rawV + (size_t)(PPT + 1) * nb * nb * sizeof(double2));  // [4] G3 exponent
   int* umax = gmax + 4;                                                      // [4] bit length of U
   uint64_t* bar = reinterpret_cast<uint64_t*>(umax + 4);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm_all + (size_t)nslots * slot_bytes);  // CTA-wide
+  const int tid = threadIdx.x & 127, warp = tid >> 5;  // within the slot; warp = TMEM lane quarter
+  auto slot_sync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(1 + slot) : "memory"); };
+  auto slot_or = [&](bool v) -> bool {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(1 + slot)
+        : "memory");
+    return r != 0;
+  };
   const int nb2 = nb * nb, R = nm * nb;
   const uint32_t sA = smem_u32(A), sB1 = smem_u32(B1), sB2 = smem_u32(B2);
   const uint32_t sRawG = smem_u32(rawG), sRawV = smem_u32(rawV);
@@ -890,7 +907,7 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(tmem_cols)
                  : "memory");
@@ -899,7 +916,8 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = *tslot;  // accumulator a (level a, 4: levels 4-6) at columns a * N1 .. a * N1 + N1 - 1
+  // this slot's accumulator a (level a, 4: levels 4-6) at columns a * N1 .. a * N1 + N1 - 1 of its range
+  const uint32_t tmem = *tslot + (uint32_t)slot * slot_cols;
   const int j = tid / RS, rr = tid - j * RS;
   const bool row_ok = j < PPT && rr < R;
   const int nu1 = rr / nb, x1 = rr - nu1 * nb;  // stage 1 row (nu, n')
@@ -910,6 +928,7 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
   uint32_t phase = 0;
   const int nqg = (nq + PPT - 1) / PPT;
   const long ntiles = (long)nqg * nk;
+  const long t0 = (long)blockIdx.x * nslots + slot, tstep = (long)gridDim.x * nslots;
   auto prefetch = [&](long tt) {
     if (tt >= ntiles) return;
     const int kk = (int)(tt % nk), qg = (int)(tt / nk);
@@ -929,7 +948,7 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
   };
   auto wait_mma = [&]() -> bool {
     const bool ok = wait(bar, phase & 1);
-    if (__syncthreads_or(!ok)) {
+    if (slot_or(!ok)) {
       if (tid == 0) {
         atomicOr(err, 16);
         wait(bar, phase & 1);  // bounded: the MMAs must be done before the TMEM is released
@@ -940,16 +959,16 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
     fence_after();
     return true;
   };
-  prefetch(blockIdx.x);
+  prefetch(t0);
 
-  for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (long t = t0; t < ntiles; t += tstep) {
     const int kk = (int)(t % nk), qg = (int)(t / nk);
     if (tid < 4) {
       gmax[tid] = 0;
       umax[tid] = 0;
     }
     cp_async_wait_all();
-    __syncthreads();
+    slot_sync();
     const int iq = qg * PPT + j;
     const bool live = row_ok && iq < nq;
     const long P = (long)iq * nk + kk;
@@ -994,7 +1013,7 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
         }
       }
     }
-    __syncthreads();
+    slot_sync();
     // ---- stage-1 A: digits of the G3 rows relative to 2^(emax - 1021) of the pair
     const int gex = j < PPT ? gmax[j] : 0;
     if (live) {
@@ -1023,8 +1042,8 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
     }
     fence_async_smem();
     fence_before();
-    __syncthreads();
-    prefetch(t + gridDim.x);
+    slot_sync();
+    prefetch(t + tstep);
     if (tid == 0) {
       fence_after();
       bt64::mma_levels64<KP>(tmem, N1, sA, A_TILE, sB1, B1_TILE, idesc(N1));
@@ -1045,17 +1064,17 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
         ld16(tl1 + (uint32_t)(4 * N1) + c, l4 + c);
       }
       ld_wait();
-      int bl = 0;
+      unsigned long long mx = 0;
 #pragma unroll
       for (int c = 0; c < KP; ++c) {
         X[c] = bt64::combine(l0[c], l1[c], l2[c], l3[c], l4[c]);
         const unsigned long long M = X[c] < 0 ? (unsigned long long)(-X[c]) : (unsigned long long)X[c];
-        if (c < 2 * nb) bl = max(bl, 64 - __clzll((long long)M));
+        if (c < 2 * nb) mx = M > mx ? M : mx;
       }
-      if (live) atomicMax(&umax[j], bl);
+      if (live) atomicMax(&umax[j], 64 - __clzll((long long)mx));
     }
     fence_before();
-    __syncthreads();
+    slot_sync();
     // ---- stage-2 A: digits of U relative to 2^B (B = the pair's largest bit length + 1), rows (m, nu)
     const int B = (j < PPT ? umax[j] : 0) + 1;
     if (live) {
@@ -1078,7 +1097,7 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
       }
     }
     fence_async_smem();
-    __syncthreads();
+    slot_sync();
     if (tid == 0) {
       fence_after();
       bt64::mma_levels64<KP>(tmem, N1, sA, A_TILE, sB2, B2_TILE, idesc(KP));
@@ -1113,13 +1132,13 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
       }
     }
     fence_before();
-    __syncthreads();
+    slot_sync();
   }
   cp_async_wait_all();
   fence_before();
   __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(tmem_cols) : "memory");
   }
 }
 
@@ -1127,11 +1146,12 @@ __global__ void __launch_bounds__(bts::THREADS, KP == 16 ? 4 : 2) k_band_tc_smal
 // allow, at most tmem_cap; a larger request enforces the cap, so that no CTA's TMEM allocation waits
 // on another.  Shared memory is counted in 256-byte units plus the per-CTA reserve.  Cached per
 // (kernel, need, cap, device).
-cudaError_t small_occupancy(const void* kern, size_t need, int tmem_cap, size_t* smem_out, int* occ_out) {
+cudaError_t small_occupancy(const void* kern, size_t need, int tmem_cap, size_t* smem_out, int* occ_out,
+                            int threads = bts::THREADS) {
   struct Entry {
     const void* kern;
     size_t need;
-    int cap, dev;
+    int cap, dev, threads;
     size_t smem;
     int occ;
   };
@@ -1145,7 +1165,7 @@ cudaError_t small_occupancy(const void* kern, size_t need, int tmem_cap, size_t*
   {
     std::lock_guard<std::mutex> lock(mu);
     for (const Entry& c : cache)
-      if (c.kern == kern && c.need == need && c.cap == tmem_cap && c.dev == dev) {
+      if (c.kern == kern && c.need == need && c.cap == tmem_cap && c.dev == dev && c.threads == threads) {
         *smem_out = c.smem;
         *occ_out = c.occ;
         return cudaSuccess;
@@ -1161,8 +1181,8 @@ cudaError_t small_occupancy(const void* kern, size_t need, int tmem_cap, size_t*
   auto unit = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t static_smem = fa.sharedSizeBytes;
   const int warp_regs = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;
-  const int by_regs = sm_regs / (warp_regs * (bts::THREADS / 32));
-  const int by_threads = 2048 / bts::THREADS;
+  const int by_regs = sm_regs / (warp_regs * (threads / 32));
+  const int by_threads = 2048 / threads;
   auto by_smem = [&](size_t dyn) { return (int)((size_t)sm_smem / (unit(dyn + static_smem) + (size_t)reserve)); };
   int occ = std::min(std::min(by_regs, by_threads), by_smem(need));
   size_t smem = need;
@@ -1174,7 +1194,7 @@ cudaError_t small_occupancy(const void* kern, size_t need, int tmem_cap, size_t*
   }
   if (occ < 1 || smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   std::lock_guard<std::mutex> lock(mu);
-  cache.push_back(Entry{kern, need, tmem_cap, dev, smem, occ});
+  cache.push_back(Entry{kern, need, tmem_cap, dev, threads, smem, occ});
   *smem_out = smem;
   *occ_out = occ;
   return cudaSuccess;
@@ -1223,7 +1243,8 @@ cudaError_t launch_band_tc_small(const void* Y, int y_f32, long ldy, const doubl
   return cudaGetLastError();
 }
 
-// FP64-accurate variant (complex128 G3 in, complex128 g out)
+// FP64-accurate variant (complex128 G3 in, complex128 g out): one CTA per SM with up to three tile
+// slots (as many as the 512 TMEM columns and the shared memory hold)
 cudaError_t launch_band_tc_small64(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
                                    int nm, int nb, double2* g, long sgq, const int* keep, int* err, cudaStream_t st) {
   if ((long)nq * nk <= 0) return cudaSuccess;
@@ -1233,23 +1254,31 @@ cudaError_t launch_band_tc_small64(const double2* Y, long ldy, const double2* Uk
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return cudaErrorInvalidDevice;
   const long ntiles = (long)((nq + s.ppt - 1) / s.ppt) * nk;
+  const unsigned slot_cols = (unsigned)(((bt64::NACC * s.n1) + 31) / 32 * 32);
+  const size_t slot_need = (size_t)bt64::ND * (128 * s.kp * 2 + (size_t)s.n1 * s.kp * 2 + (size_t)s.kp * s.kp * 2) +
+                           (size_t)s.ppt * nm * nb * nb * 16 + (size_t)(s.ppt + 1) * nb * nb * 16 + 64;
+  const unsigned slot_bytes = (unsigned)((slot_need + 1023) & ~(size_t)1023);
+  int nslots = (int)(512 / slot_cols);
+  nslots = std::min(nslots, (int)((220 * 1024 - 64) / slot_bytes));
+  nslots = std::min(nslots, s.kp == 16 ? 3 : 2);  // the kernels' launch bounds
+  if (nslots < 1) return cudaErrorInvalidConfiguration;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(bt64::NACC * s.n1)) cols <<= 1;
-  const size_t need = (size_t)bt64::ND * (128 * s.kp * 2 + (size_t)s.n1 * s.kp * 2 + (size_t)s.kp * s.kp * 2) +
-                      (size_t)s.ppt * nm * nb * nb * 16 + (size_t)(s.ppt + 1) * nb * nb * 16 + 64;
-  cudaError_t e;
+  while (cols < (uint32_t)(nslots * slot_cols)) cols <<= 1;
   const void* kern = s.kp == 16 ? reinterpret_cast<const void*>(k_band_tc_small64<16>)
                                 : reinterpret_cast<const void*>(k_band_tc_small64<32>);
+  cudaError_t e;
   size_t smem = 0;
   int occ = 0;
-  if ((e = small_occupancy(kern, need, (int)(512 / cols), &smem, &occ)) != cudaSuccess) return e;
-  const long grid = std::min(ntiles, (long)sms * occ);
+  if ((e = small_occupancy(kern, (size_t)nslots * slot_bytes + 64, (int)(512 / cols), &smem, &occ,
+                           nslots * bts::THREADS)) != cudaSuccess)
+    return e;
+  const long grid = std::min((ntiles + nslots - 1) / nslots, (long)sms * occ);
   if (s.kp == 16)
-    k_band_tc_small64<16><<<(unsigned)grid, bts::THREADS, smem, st>>>(Y, ldy, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, g,
-                                                                      sgq, keep, err, cols);
+    k_band_tc_small64<16><<<(unsigned)grid, nslots * bts::THREADS, smem, st>>>(
+        Y, ldy, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, g, sgq, keep, err, cols, nslots, slot_bytes, slot_cols);
   else
-    k_band_tc_small64<32><<<(unsigned)grid, bts::THREADS, smem, st>>>(Y, ldy, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, g,
-                                                                      sgq, keep, err, cols);
+    k_band_tc_small64<32><<<(unsigned)grid, nslots * bts::THREADS, smem, st>>>(
+        Y, ldy, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, g, sgq, keep, err, cols, nslots, slot_bytes, slot_cols);
   return cudaGetLastError();
 }
 
