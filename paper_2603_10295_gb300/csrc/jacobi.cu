@@ -38,6 +38,25 @@ __device__ __forceinline__ float2 shfl_d2(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
+// FP64 <-> FP32 conversions by integer operations: on GB300 the conversion instructions share the
+// FP64 pipe, which the refinement keeps busy, while the integer pipe is idle.  d2f rounds to
+// nearest (ties away); both map magnitudes outside FP32's normal range below 2^-126 to 0 (only the
+// small FP32 corrections of the refinement go through them).
+__device__ __forceinline__ float d2f_i(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) + (1ULL << 28);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned mag = __funnelshift_l(lo, hi, 3) - (896u << 23);
+  return (e > 896u && e < 1151u) ? __uint_as_float(mag | (hi & 0x80000000u)) : 0.f;
+}
+__device__ __forceinline__ double f2d_i(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u) return 0.0;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 template <typename T>
 struct Cx;
 template <>
@@ -396,7 +415,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     float2 af[NP];
 #pragma unroll
     for (int r = 0; r < NP; ++r) {
-      af[r] = make_float2((float)a[r].x, (float)a[r].y);
+      af[r] = make_float2(d2f_i(a[r].x), d2f_i(a[r].y));
       vf[r] = make_float2(r == j ? 1.f : 0.f, 0.f);
     }
     const float fro2f = (float)fro2;
@@ -411,7 +430,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       if (valid && off <= tol32) c32 = true;
     }
 #pragma unroll
-    for (int r = 0; r < NP; ++r) v[r] = make_double2((double)vf[r].x, (double)vf[r].y);
+    for (int r = 0; r < NP; ++r) v[r] = make_double2(f2d_i(vf[r].x), f2d_i(vf[r].y));
   }
 
   // ---- refinement
@@ -487,12 +506,13 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     // The bookkeeping of the correction runs in FP32: K, the angle tests and the eigenvalue
     // shift need ~1e-7 relative precision only.  Their inputs S_ij, G_ij and the gap
     // lam_j - lam_i are formed in FP64 (they are small differences).
-    const float ltf = (float)lt;
-    float emx = 0.25f * (float)e0 * (float)e0;  // squared bound on |E_ij|
+    const float ltf = d2f_i(lt);
+    const float e0f = d2f_i(e0);
+    float emx = 0.25f * e0f * e0f;  // squared bound on |E_ij|
     float shift = 0.f;
     int unres = 0;
     float2 er[NP];  // er[d] = E_{(j+d) mod NP, j}
-    er[0] = make_float2(0.5f * (float)e0, 0.f);
+    er[0] = make_float2(0.5f * e0f, 0.f);
     float2 hf[H], kf[H];  // slot d at index d - 1
 #pragma unroll
     for (int d = 1; d <= H; ++d) {
@@ -502,10 +522,10 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       pair_products(base + i, g, sv);
       const double li = shfl_d(lt, base + i);
       const float lif = shfl_d(ltf, base + i);
-      const float gap = (float)(lt - li);
+      const float gap = d2f_i(lt - li);
       const float hm = 0.5f * (lif + ltf);
-      const float2 gf = make_float2((float)g.x, (float)g.y);
-      const float2 num = make_float2(fmaf(-hm, gf.x, (float)sv.x), fmaf(-hm, gf.y, (float)sv.y));
+      const float2 gf = make_float2(d2f_i(g.x), d2f_i(g.y));
+      const float2 num = make_float2(fmaf(-hm, gf.x, d2f_i(sv.x)), fmaf(-hm, gf.y, d2f_i(sv.y)));
       const float n2 = fmaf(num.x, num.x, num.y * num.y);
       const bool own = !(2 * d == NP && j >= H);
       float2 K = make_float2(0.f, 0.f);
@@ -549,7 +569,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     float2 xf[NP], acc[NP];
 #pragma unroll
     for (int r = 0; r < NP; ++r) {
-      xf[r] = make_float2((float)v[r].x, (float)v[r].y);
+      xf[r] = make_float2(d2f_i(v[r].x), d2f_i(v[r].y));
       acc[r] = make_float2(0.f, 0.f);
     }
 #pragma unroll
@@ -566,10 +586,10 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     }
     if (!done) {
 #pragma unroll
-      for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x + (double)acc[r].x, v[r].y + (double)acc[r].y);
+      for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x + f2d_i(acc[r].x), v[r].y + f2d_i(acc[r].y));
       if (emx_g <= th2f && !unres_g) {
         done = true;
-        lam = lt + (double)shift;
+        lam = lt + f2d_i(shift);
       }
     }
   }
