@@ -131,6 +131,14 @@ struct eph_ctx {
   // copy stream is known to have drained): the next band rotation into g_stage, in this call or
   // a later one, first waits on copy_done
   bool copies_pending = false;
+  // the FP64 path with host buffers stages each k tile's g, eps_{k+q} and omega in one of two sets
+  // (g_stage / g_stage2, est, ost), alternating per tile: a tile's band rotation waits only for the
+  // copies out of its own set (set_done), so the copy stream is never starved by the band rotation
+  // of the next tile, and no device->host copy runs on the compute stream
+  DBuf g_stage2, est[2], ost[2];
+  cudaEvent_t set_done[2] = {};
+  bool set_pending[2] = {false, false};
+  int stage_set = 0;
   // product k grid (sum-factorised Re->k): bounding box of the Re list, axis phase tables,
   // the scattered W_q box and the two partial transforms of a q batch
   bool boxable = false;  // Re vectors distinct, box extents <= 33, box volume <= 8 ne
@@ -366,7 +374,8 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc, &ctx->rebox, &ctx->E1,
                   &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
                   &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair, &ctx->g1in,
-                  &ctx->aS2, &ctx->aS1, &ctx->aS0, &ctx->DG, &ctx->sG, &ctx->DP, &ctx->G1f};
+                  &ctx->aS2, &ctx->aS1, &ctx->aS0, &ctx->DG, &ctx->sG, &ctx->DP, &ctx->G1f, &ctx->g_stage2,
+                  &ctx->est[0], &ctx->est[1], &ctx->ost[0], &ctx->ost[1]};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -376,6 +385,8 @@ void eph_destroy(eph_ctx* ctx) {
   for (cudaEvent_t e : ctx->slice_ev)
     if (e) cudaEventDestroy(e);
   if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
+  for (cudaEvent_t e : ctx->set_done)
+    if (e) cudaEventDestroy(e);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -1290,6 +1301,9 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
 // Workspace plan of the FP64 form for nq q points (allocates; nothing is launched).
 int prepare_fp64(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
   const bool host = !ctx->opt.device_ptrs;
+  // host buffers: the k tile is planned for one staging set of g; the second set (and the small
+  // eps / omega staging) sits outside the soft workspace cap, since splitting the tile to fit it
+  // cost more than the copy overlap it buys (si_full: 19.3 against 14.9 ms per step)
   const QPlan p = plan_q(ctx, nq, host && want_g ? (size_t)ctx->nm * ctx->nb * ctx->nb * 16 : 0);
   EPH_TRY(ensure_q_workspace(ctx, p));
   if (ctx->big) {
@@ -1306,7 +1320,15 @@ int prepare_fp64(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
     EPH_TRY(ensure(ctx, ctx->jwork, need));
     if (use_band_tc(ctx)) EPH_TRY(ensure(ctx, ctx->tcband, band_tc_bytes(ctx, (long)p.QB * p.KT, (int)p.KT)));
   }
-  if (host && want_g) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)p.QB * p.KT * p.gcols * sizeof(double2)));
+  if (host && want_g) {
+    const size_t gb = (size_t)p.QB * p.KT * p.gcols * sizeof(double2);
+    EPH_TRY(ensure(ctx, ctx->g_stage, gb));
+    EPH_TRY(ensure(ctx, ctx->g_stage2, gb));
+    for (int s2 = 0; s2 < 2; ++s2) {
+      EPH_TRY(ensure(ctx, ctx->est[s2], (size_t)p.QB * p.KT * ctx->nb * sizeof(double)));
+      EPH_TRY(ensure(ctx, ctx->ost[s2], (size_t)p.QB * ctx->nm * sizeof(double)));
+    }
+  }
   *out = p;
   return EPH_OK;
 }
@@ -1319,6 +1341,7 @@ int ensure_copy_stream(eph_ctx* ctx) {
   EPH_CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
   for (cudaEvent_t& e : ctx->slice_ev) EPH_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   EPH_CK(cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming));
+  for (cudaEvent_t& e : ctx->set_done) EPH_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   return EPH_OK;
 }
 
@@ -1336,17 +1359,19 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
   const void* dq = nullptr;
   EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
   const double* qdev = static_cast<const double*>(dq);
-  if (host && g) EPH_TRY(ensure_copy_stream(ctx));
+  // host buffers with g: every device->host copy goes through the tile's staging set on the copy stream
+  const bool staged = host && g;
+  if (staged) EPH_TRY(ensure_copy_stream(ctx));
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
     const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
     EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb, true, ctx->g1_ext ? ctx->g1_ext + (long)q0 * p.X : nullptr));
-    if (omega)
+    if (omega && !staged)
       EPH_CK(cudaMemcpyAsync(omega + (long)q0 * nm, ctx->omq.p, (size_t)nqb * nm * sizeof(double), out_kind(ctx),
                              ctx->stream));
     for (long k0 = 0; k0 < nk; k0 += p.KT) {
       const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
       EPH_TRY(k_tile_forward(ctx, p, nqb, k0, nkt));
-      if (eps_kq)
+      if (eps_kq && !staged)
         for (int iq = 0; iq < nqb; ++iq)  // one contiguous copy per q (rows of the tile)
           EPH_CK(cudaMemcpyAsync(eps_kq + ((long)(q0 + iq) * nk + k0) * nb,
                                  as<double>(ctx->eps_tile) + (long)iq * nkt * nb, (size_t)nkt * nb * sizeof(double),
@@ -1365,10 +1390,21 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
         char* gout = static_cast<char*>(g);
         char* stage = static_cast<char*>(ctx->g_stage.p);
         if (host) {
-          // one q at a time: the copy of q overlaps the band rotation of the following ones; the
-          // staging buffer is free again once the copies of the previous tile (of this call or,
-          // in async mode, of an earlier one) are done
-          if (ctx->copies_pending) EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));
+          // one q at a time: the copy of q overlaps the band rotation of the following ones.  The
+          // tile uses the staging set the previous tile did not; it waits only for the copies out
+          // of that set (two tiles back, of this call or, in async mode, of an earlier one)
+          const int set = ctx->stage_set;
+          ctx->stage_set ^= 1;
+          stage = static_cast<char*>(set ? ctx->g_stage2.p : ctx->g_stage.p);
+          if (ctx->set_pending[set]) EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->set_done[set], 0));
+          double* est = as<double>(ctx->est[set]);
+          double* ost = as<double>(ctx->ost[set]);
+          if (eps_kq)
+            EPH_CK(cudaMemcpyAsync(est, ctx->eps_tile.p, (size_t)nqb * nkt * nb * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+          if (omega && k0 == 0)
+            EPH_CK(cudaMemcpyAsync(ost, ctx->omq.p, (size_t)nqb * nm * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
           for (int iq = 0; iq < nqb; ++iq) {
             char* slice = stage + (long)iq * nkt * p.gcols * esz;
             EPH_TRY(band_rotate(ctx, p, 1, nkt, k0, reinterpret_cast<double2*>(slice), (long)nkt * p.gcols, keep, iq));
@@ -1376,7 +1412,15 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
             EPH_CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->slice_ev[iq], 0));
             EPH_CK(cudaMemcpyAsync(gout + ((long)(q0 + iq) * nk + k0) * p.gcols * esz, slice,
                                    (size_t)nkt * p.gcols * esz, cudaMemcpyDeviceToHost, ctx->copy_stream));
+            if (eps_kq)
+              EPH_CK(cudaMemcpyAsync(eps_kq + ((long)(q0 + iq) * nk + k0) * nb, est + (long)iq * nkt * nb,
+                                     (size_t)nkt * nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->copy_stream));
           }
+          if (omega && k0 == 0)
+            EPH_CK(cudaMemcpyAsync(omega + (long)q0 * nm, ost, (size_t)nqb * nm * sizeof(double),
+                                   cudaMemcpyDeviceToHost, ctx->copy_stream));
+          EPH_CK(cudaEventRecord(ctx->set_done[set], ctx->copy_stream));
+          ctx->set_pending[set] = true;
           EPH_CK(cudaEventRecord(ctx->copy_done, ctx->copy_stream));
           ctx->copies_pending = true;
         } else {
@@ -1392,7 +1436,7 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
   if (ctx->copies_pending && !ctx->opt.async) {
     EPH_CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_done, 0));
     const int rc = finish(ctx);  // synchronises the stream, hence the copies it waited for
-    if (rc == EPH_OK || rc == EPH_ENOTCONV) ctx->copies_pending = false;
+    if (rc == EPH_OK || rc == EPH_ENOTCONV) ctx->copies_pending = ctx->set_pending[0] = ctx->set_pending[1] = false;
     return rc;
   }
   return finish(ctx);
@@ -1900,7 +1944,7 @@ extern "C" int eph_sync(eph_ctx* ctx) {
   if (!ctx) return EPH_EINVAL;
   if (ctx->copy_stream) {  // host copies of g
     EPH_CK(cudaStreamSynchronize(ctx->copy_stream));
-    ctx->copies_pending = false;
+    ctx->copies_pending = ctx->set_pending[0] = ctx->set_pending[1] = false;
   }
   int h[2] = {0, 0};
   EPH_CK(cudaMemcpyAsync(h, ctx->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
