@@ -50,8 +50,14 @@ EIG_FP64_FLOPS = {(8, "fp64"): (2 * 1769472000 + 59392000 + 548864000) / 256000,
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at one step = 4 q x 64,000 k
 TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
            ("k_zgemm", "si_full", 4): 242432512.0 + 1777470464.0,
-           ("k_jacobi_mixed", "si_full", 4): 263387136.0 + 230558208.0,
            ("k_band_rotate", "si_full", 4): 2097285888.0 + 1534482688.0}
+# DRAM bytes per unit (pair or matrix) of the current kernels from the 24^3-grid captures
+# (bench.py --capture si-fp64-grid / si-mixed-grid, 55,296 pairs per launch), scaled to a launch
+# by its units: these kernels stream their inputs once, so traffic grows in proportion
+TRAFFIC_PER_UNIT = {("k_jacobi_mixed", "si_full", 4, "fp64"): (56772608.0 + 10082304.0) / 55296,
+                    ("k_jacobi_mixed", "si_full", 4, "mixed"): (56966912.0 + 10144256.0) / 55296,
+                    ("k_band_tc_small64", "si_full", 4, "grid"): (424918528.0 + 287893248.0) / 55296,
+                    ("k_band_tc_small", "si_full", 4, "grid"): (424756224.0 + 136090112.0) / 55296}
 
 
 def gpu_local_cpus(gpu_index):
@@ -783,6 +789,8 @@ def run_libeph(args):
                 "useful_tflops": useful / t / 1e12 if t else None}
 
     def roof_band(r):
+        if nb <= 16 and nm * nb <= 128:  # the default FP64 rotation: six-digit tensor-core products
+            return roof_band_tc(r, 16.0, fp64=True)
         bd_ms, bd_n = r["prof"]["band"]
         cmac = 2.0 * nb ** 3 * nm * QB * nk          # V_kq^H G3 V_k per (q,k) pair
         t = bd_ms / max(args.steps, 1) * 1e-3
@@ -811,29 +819,39 @@ def run_libeph(args):
                 "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_FLOPS if ach else None,
                 "fp64_flop_per_matrix": per, "matrices_per_launch": mats,
-                "traffic": TRAFFIC.get(("k_jacobi_mixed", args.workload, QB)) if form == "fp64" else None,
+                "traffic": (TRAFFIC_PER_UNIT.get(("k_jacobi_mixed", args.workload, QB, form), 0.0) * mats) or None,
                 "algorithmic_bytes": mats * (nb * nb * 16 + nb * nb * 16 + nb * 8),
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
 
-    def roof_band_tc(r, g3_bytes):
-        # the mixed form's fused tensor-core band rotation (k_band_tc_small) against HBM: G3 rows in
-        # (complex128 from the FP64 grid transforms, complex64 from the tensor-core contraction),
-        # V_{k+q} per pair and V_k per tile of pairs (two q at one k for these shapes) in, g out
+    def roof_band_tc(r, g3_bytes, fp64=False):
+        # the fused tensor-core band rotation (k_band_tc_small, mixed; k_band_tc_small64, FP64 form)
+        # against HBM: G3 rows in (complex128 from the FP64 grid transforms, complex64 from the
+        # tensor-core contraction), V_{k+q} per pair and V_k per tile of pairs (two q at one k for
+        # these shapes) in, g out (complex64 mixed, complex128 FP64)
         bd_ms, bd_n = r["prof"]["band"]
         pairs = float(args.steps) * QB * nk
         ppt = max(1, min(4, 128 // (((nm * nb + 31) // 32) * 32)))
-        per_pair = g3_bytes * nm * nb * nb + 16.0 * nb * nb + 16.0 * nb * nb / ppt + 8.0 * nm * nb * nb
+        gbytes = 16.0 if fp64 else 8.0
+        per_pair = g3_bytes * nm * nb * nb + 16.0 * nb * nb + 16.0 * nb * nb / ppt + gbytes * nm * nb * nb
         t = bd_ms * 1e-3
         ach = per_pair * pairs / t if t else None
         peak = peaks.get("hbm_gbs")
-        return {"bound": "hbm", "kernel": "k_band_tc_small (tcgen05 kind::f16, four-digit fixed-point BF16 operands)",
+        key = ("k_band_tc_small64" if fp64 else "k_band_tc_small", args.workload, QB, "grid" if g3_bytes == 16.0 else "list")
+        tr = TRAFFIC_PER_UNIT.get(key)
+        return {"bound": "hbm",
+                "kernel": "k_band_tc_small64 (tcgen05 kind::f16, six-digit operands, exact level sums, FP64 accuracy, "
+                          "no FP64 instruction)" if fp64 else
+                          "k_band_tc_small (tcgen05 kind::f16, four-digit fixed-point BF16 operands)",
                 "achieved": ach / 1e9 if ach else None, "peak": peak, "unit": "GB/s",
                 "frac": (ach / 1e9 / peak) if (ach and peak) else None,
                 "algorithmic_bytes_per_pair": per_pair, "pairs_per_launch": pairs / max(bd_n, 1),
-                "traffic": None,
+                "traffic": tr * pairs / max(bd_n, 1) if tr else None,
                 "cmac_per_pair": 2 * nb ** 3 * nm,
-                "note": "issue-bound on the digit arithmetic (ncu: 63 % issue, tensor pipe 9 %, DRAM 26 %); "
-                        "profiles/k_band_tc_small_si_mixed_grid24.md",
+                "note": ("issue-bound on integer digit arithmetic (ncu: 48 % issue, ALU pipe 49 %, tensor pipe 8 %); "
+                         "profiles/k_band_tc_small64_si_fp64_grid24.md" if fp64 else
+                         "issue-bound on the digit arithmetic (ncu: 63 % issue, tensor pipe 9 %, DRAM 26 %); "
+                         "profiles/k_band_tc_small_si_mixed_grid24.md")
+                + "; traffic = DRAM bytes per pair of the 24^3 capture x pairs per launch",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs, measured" if peak else "unavailable"}
 
     def dominant_roofline(r):
