@@ -86,7 +86,9 @@ typedef struct eph_options {
                          digits per operand, ~2^-31 of each pair's largest element; FP64 form: six
                          digits, levels <= 6, integer assembly of the doubles, ~1e-14); 1 = on the
                          CUDA cores (double-float FP32 in the mixed form, FP64 DFMA in the FP64
-                         form) */
+                         form).  The same switch applies to the FP64 band products of
+                         eph_interp_backward, eph_interp_vjp, eph_bloch_to_wannier and
+                         eph_linewidths (six-digit tensor-core products, or FP64 DFMA) */
 } eph_options;
 
 /* Fills *opt with the defaults (FP64 form, host pointers, automatic batching). */
@@ -234,6 +236,12 @@ int eph_interp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* q
  * list (nk must equal its size); after eph_set_k_grid both Re->k sums -- the recomputed
  * forward one and its adjoint -- then run sum-factorised, as three one-axis transforms
  * (the adjoint applies the conjugate axis phases in reverse order and gathers the Re rows).
+ * Every supported shape and both forms: the chain is FP64 (a mixed-form context recomputes
+ * the forward with the FP64 Eq. 9, its electron eigensolves polished to 1e-12).  The band
+ * rotation and its adjoint run on the tensor cores at FP64 accuracy (six-digit operands,
+ * ~5e-14 of each pair's largest element) for nb <= 16, nm nb <= 128 unless band_alu is set,
+ * as FP64 GEMMs batched over (k, nu) for larger shapes.  An Rp-slice context returns
+ * EPH_ESTATE.
  */
 int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
                         const double* w_nk, double omega_min, double* L_out, double* grad_g_ReRp);
@@ -251,7 +259,8 @@ int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int nq, const 
  *   [np][nm][ne][nb][nb] complex128 (overwritten).  Host or device pointers per
  *   device_ptrs.  Replaces the context's k list (as eph_set_k); kpts = NULL keeps the
  *   resident one (sum-factorised on a uniform grid, as in eph_interp_backward).
- * FP64 form with nb, nm <= 16; EPH_ENOTSUP otherwise.
+ * Every supported shape and both forms (an FP64 chain, as eph_interp_backward; in a mixed-form
+ * context the gauges are that context's, its electron eigensolves polished to 1e-12).
  */
 int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts, const void* grad_g,
                    double* grad_g_ReRp);
@@ -269,7 +278,7 @@ int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, const doubl
  *   context's k list (as eph_set_k); kpts = NULL keeps the resident one (e.g. the coarse grid
  *   set by eph_set_k_grid, whose sums over k' then run sum-factorised).  The context's own
  *   g(Re,Rp) is not used.
- * FP64 form with nb, nm <= 16; EPH_ENOTSUP otherwise.
+ * Every supported shape and both forms (an FP64 chain, as eph_interp_vjp).
  */
 int eph_bloch_to_wannier(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts, const void* g,
                          double* g_ReRp);
@@ -328,7 +337,11 @@ int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, double e_lo, d
  * width sigma (all in eV); g as eph_interp_q defines it.  Units: |g|^2 / eV^2.
  *   qpts [nq][3], wq [nq] q weights (NULL = all 1), gamma [nk][nb] (overwritten with the
  *   sum over these q points); host or device pointers per device_ptrs.
- * FP64 form with nb, nm <= 16; EPH_ENOTSUP otherwise.
+ * Every supported shape and both forms, in FP64 (a mixed-form context runs the FP64 chain with
+ * its electron eigensolves polished to 1e-12).  g is formed over the context's k-tile
+ * workspace and reduced there: by the FP64-accuracy tensor-core rotation for nb <= 16,
+ * nm nb <= 128 (the fused CUDA-core kernel with band_alu), by FP64 GEMMs for larger shapes.
+ * An Rp-slice context returns EPH_ESTATE.
  */
 int eph_linewidths(eph_ctx* ctx, int nq, const double* qpts, const double* wq, double kT, double mu,
                    double sigma, double omega_min, double* gamma);

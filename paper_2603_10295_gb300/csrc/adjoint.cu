@@ -155,6 +155,66 @@ cudaError_t launch_band_vjp(double2* Y, long ldy, const double2* gbar, long sgq,
   return cudaGetLastError();
 }
 
+// Loss terms of the adjoint for large shapes, one CTA per (q,k) pair over the pair's g row
+// [nu][m][n] (row stride ldy): Lpair = sum c |g|^2 in a fixed order, and 2 c g written in place,
+// c = w_nk / omega_qnu (0 for omega <= omega_min).
+__global__ void __launch_bounds__(256) k_loss_terms(double2* __restrict__ Y, long ldy, const double* __restrict__ wk,
+                                                    const double* __restrict__ om, double omega_min, int nk, int nm,
+                                                    int nb, double* __restrict__ Lpair) {
+  __shared__ double red[8];
+  const long pair = blockIdx.x;
+  const int k = (int)(pair % nk);
+  const long q = pair / nk;
+  const int nb2 = nb * nb;
+  double2* row = Y + pair * ldy;
+  double lsum = 0.0;
+  for (int nu = 0; nu < nm; ++nu) {
+    const double w = om[q * nm + nu];
+    const double inv = w > omega_min ? 1.0 / w : 0.0;
+    for (int t = threadIdx.x; t < nb2; t += blockDim.x) {
+      const int n = t % nb;
+      const double c = wk[(long)k * nb + n] * inv;
+      const double2 g = row[(long)nu * nb2 + t];
+      lsum = fma(c, fma(g.x, g.x, g.y * g.y), lsum);
+      row[(long)nu * nb2 + t] = make_double2(2.0 * c * g.x, 2.0 * c * g.y);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    Lpair[pair] = t;
+  }
+}
+
+cudaError_t launch_loss_terms(double2* Y, long ldy, const double* wk, const double* om, double omega_min, int nq,
+                              int nk, int nm, int nb, double* Lpair, cudaStream_t st) {
+  const long pairs = (long)nq * nk;
+  if (pairs <= 0) return cudaSuccess;
+  if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
+  k_loss_terms<<<(unsigned)pairs, 256, 0, st>>>(Y, ldy, wk, om, omega_min, nk, nm, nb, Lpair);
+  return cudaGetLastError();
+}
+
+// out[b][j][i] = conj(in[b][i][j]) for a batch of n x n complex matrices (V^H of eigenvector sets)
+__global__ void k_conj_transpose(const double2* __restrict__ in, int n, long total, double2* __restrict__ out) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const long nn = (long)n * n, b = t / nn;
+  const int r = (int)(t - b * nn), i = r / n, j = r - i * n;
+  const double2 v = in[t];
+  out[b * nn + (long)j * n + i] = make_double2(v.x, -v.y);
+}
+
+cudaError_t launch_conj_transpose(const double2* in, int n, long batch, double2* out, cudaStream_t st) {
+  const long total = batch * n * n;
+  if (total <= 0) return cudaSuccess;
+  k_conj_transpose<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(in, n, total, out);
+  return cudaGetLastError();
+}
+
 // f[c] = s M_c with M_c = 1 / invsqrtm[c]^2 (the mass of mode index c = 3 kappa + alpha).
 __global__ void k_mass_factors(const double* __restrict__ invsqrtm, int nm, double s, double* __restrict__ f) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;

@@ -136,6 +136,8 @@ struct eph_ctx {
   // copies out of its own set (set_done), so the copy stream is never starved by the band rotation
   // of the next tile, and no device->host copy runs on the compute stream
   DBuf g_stage2, est[2], ost[2];
+  DBuf Pacc;  // adjoint: phase rows of the q batches whose G1bar rows await the gradient GEMM
+  DBuf UkH;   // adjoint of large shapes: V_k^H of the k tile
   cudaEvent_t set_done[2] = {};
   bool set_pending[2] = {false, false};
   int stage_set = 0;
@@ -375,7 +377,7 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
                   &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair, &ctx->g1in,
                   &ctx->aS2, &ctx->aS1, &ctx->aS0, &ctx->DG, &ctx->sG, &ctx->DP, &ctx->G1f, &ctx->g_stage2,
-                  &ctx->est[0], &ctx->est[1], &ctx->ost[0], &ctx->ost[1]};
+                  &ctx->est[0], &ctx->est[1], &ctx->ost[0], &ctx->ost[1], &ctx->Pacc, &ctx->UkH};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -1298,6 +1300,22 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
   return finish(ctx);
 }
 
+// Large shapes: the band products' temporary, u^T of the q batch and the eigensolver work.
+int big_workspace(eph_ctx* ctx, const QPlan& p) {
+  const int nb2 = ctx->nb * ctx->nb, nmax = ctx->nb > ctx->nm ? ctx->nb : ctx->nm;
+  EPH_TRY(ensure(ctx, ctx->Tbuf, (size_t)p.KT * ctx->nm * nb2 * sizeof(double2)));
+  EPH_TRY(ensure(ctx, ctx->ut, (size_t)p.QB * ctx->nm * ctx->nm * sizeof(double2)));
+  const size_t jw = (size_t)(p.QB * p.KT > ctx->nk ? p.QB * p.KT : ctx->nk) * nmax * nmax * sizeof(double2);
+  size_t need = jw;
+  const size_t e1 = eig_work_bytes(ctx, ctx->nb, (long)p.QB * p.KT), e2 = eig_work_bytes(ctx, ctx->nb, ctx->nk),
+               e3 = eig_work_bytes(ctx, ctx->nm, p.QB);
+  need = need > e1 ? need : e1;
+  need = need > e2 ? need : e2;
+  need = need > e3 ? need : e3;
+  EPH_TRY(ensure(ctx, ctx->jwork, need));
+  return EPH_OK;
+}
+
 // Workspace plan of the FP64 form for nq q points (allocates; nothing is launched).
 int prepare_fp64(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
   const bool host = !ctx->opt.device_ptrs;
@@ -1307,17 +1325,7 @@ int prepare_fp64(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
   const QPlan p = plan_q(ctx, nq, host && want_g ? (size_t)ctx->nm * ctx->nb * ctx->nb * 16 : 0);
   EPH_TRY(ensure_q_workspace(ctx, p));
   if (ctx->big) {
-    const int nb2 = ctx->nb * ctx->nb, nmax = ctx->nb > ctx->nm ? ctx->nb : ctx->nm;
-    EPH_TRY(ensure(ctx, ctx->Tbuf, (size_t)p.KT * ctx->nm * nb2 * sizeof(double2)));
-    EPH_TRY(ensure(ctx, ctx->ut, (size_t)p.QB * ctx->nm * ctx->nm * sizeof(double2)));
-    const size_t jw = (size_t)(p.QB * p.KT > ctx->nk ? p.QB * p.KT : ctx->nk) * nmax * nmax * sizeof(double2);
-    size_t need = jw;
-    const size_t e1 = eig_work_bytes(ctx, ctx->nb, (long)p.QB * p.KT), e2 = eig_work_bytes(ctx, ctx->nb, ctx->nk),
-                 e3 = eig_work_bytes(ctx, ctx->nm, p.QB);
-    need = need > e1 ? need : e1;
-    need = need > e2 ? need : e2;
-    need = need > e3 ? need : e3;
-    EPH_TRY(ensure(ctx, ctx->jwork, need));
+    EPH_TRY(big_workspace(ctx, p));
     if (use_band_tc(ctx)) EPH_TRY(ensure(ctx, ctx->tcband, band_tc_bytes(ctx, (long)p.QB * p.KT, (int)p.KT)));
   }
   if (host && want_g) {
@@ -1733,12 +1741,126 @@ int adj_k_finish(eph_ctx* ctx, const QPlan& p, int nqb, double2* G2b, bool weigh
 }
 }  // namespace
 
+namespace {
+// Large shapes, FP64: g = V_{k+q}^H (G3 V_k) written over the G3 rows of Y (GEMMs batched over
+// (k, nu) through the band temporary).
+int band_rotate_big_inplace(eph_ctx* ctx, const QPlan& p, int stage, int nqb, long k0, int nkt) {
+  const int nb = ctx->nb, nm = ctx->nm, nb2 = nb * nb;
+  const long NW = p.NW, gcols = (long)nm * nb2;
+  double2* Y = as<double2>(ctx->Y);
+  double2* T = as<double2>(ctx->Tbuf);
+  const double2* Uk = as<double2>(ctx->Uk) + k0 * nb2;
+  const double2* Ukq = as<double2>(ctx->Ukq);
+  const int kc = 65535 / nm;  // batch-size limit of one launch
+  for (int iq = 0; iq < nqb; ++iq)
+    for (int kb = 0; kb < nkt; kb += kc) {
+      const int nkc = nkt - kb < kc ? nkt - kb : kc;
+      double2* G3 = Y + ((long)iq * nkt + kb) * NW + nb2;
+      const double2* Vkq = Ukq + ((long)iq * nkt + kb) * nb2;
+      EPH_LAUNCH_S(stage, eph::launch_zgemm_b2(nb, nb, nb, G3, nb, NW, nb2, Uk + (long)kb * nb2, nb, nb2, 0, T, nb,
+                                               gcols, nb2, nkc, nm, 0, ctx->stream));
+      EPH_LAUNCH_S(stage, eph::launch_zgemm_b2(nb, nb, nb, Vkq, nb, nb2, 0, T, nb, gcols, nb2, G3, nb, NW, nb2, nkc,
+                                               nm, 1, ctx->stream));
+    }
+  return EPH_OK;
+}
+
+// Large shapes: the band rotation's adjoint as FP64 GEMMs batched over (k, nu), like the forward.
+// gbar NULL: g = V_{k+q}^H (G3 V_k) over the G3 rows of Y, then the loss terms (Lpair, 2 c g in
+// place); else the upstream gradient rows gbar[q][k] (q stride sgq, k stride gcols).  Then
+// G3bar = V_{k+q} (gbar V_k^H) over the G3 rows of Y.
+int band_adjoint_big(eph_ctx* ctx, const QPlan& p, int stage, int nqb, long k0, int nkt, const double* wk,
+                     double omega_min, const double2* gbar, long sgq) {
+  const int nb = ctx->nb, nm = ctx->nm, nb2 = nb * nb;
+  const long NW = p.NW, gcols = (long)nm * nb2;
+  double2* Y = as<double2>(ctx->Y);
+  double2* T = as<double2>(ctx->Tbuf);
+  const double2* Uk = as<double2>(ctx->Uk) + k0 * nb2;
+  const double2* Ukq = as<double2>(ctx->Ukq);
+  EPH_TRY(ensure(ctx, ctx->UkH, (size_t)p.KT * nb2 * sizeof(double2)));
+  double2* UkH = as<double2>(ctx->UkH);
+  EPH_LAUNCH_S(stage, eph::launch_conj_transpose(Uk, nb, nkt, UkH, ctx->stream));
+  const int kc = 65535 / nm;  // batch-size limit of one launch
+  if (!gbar) {
+    EPH_TRY(band_rotate_big_inplace(ctx, p, stage, nqb, k0, nkt));
+    EPH_LAUNCH_S(stage, eph::launch_loss_terms(Y + nb2, NW, wk, as<double>(ctx->omq), omega_min, nqb, nkt, nm, nb,
+                                               as<double>(ctx->Lpair), ctx->stream));
+  }
+  for (int iq = 0; iq < nqb; ++iq)
+    for (int kb = 0; kb < nkt; kb += kc) {
+      const int nkc = nkt - kb < kc ? nkt - kb : kc;
+      double2* G3 = Y + ((long)iq * nkt + kb) * NW + nb2;
+      const double2* Vkq = Ukq + ((long)iq * nkt + kb) * nb2;
+      const double2* src = gbar ? gbar + (long)iq * sgq + (long)kb * gcols : G3;
+      const long sk = gbar ? gcols : NW;
+      EPH_LAUNCH_S(stage, eph::launch_zgemm_b2(nb, nb, nb, src, nb, sk, nb2, UkH + (long)kb * nb2, nb, nb2, 0, T, nb,
+                                               gcols, nb2, nkc, nm, 0, ctx->stream));
+      EPH_LAUNCH_S(stage, eph::launch_zgemm_b2(nb, nb, nb, Vkq, nb, nb2, 0, T, nb, gcols, nb2, G3, nb, NW, nb2, nkc,
+                                               nm, 0, ctx->stream));
+    }
+  return EPH_OK;
+}
+
+// G1bar[q][c] = sum_nu conj(u[q][c][nu]) G2bar[q][nu]: the shared-memory kernel for nm <= 16, else
+// per q one GEMM batched over Re with op(A) = (u^T)^H = conj(u) (u^T from the q batch's prelude)
+int mode_rotate_adj(eph_ctx* ctx, const QPlan& p, int nqb, const double2* G2b, double2* rows) {
+  const int nm = ctx->nm, ne = ctx->ne, nb2 = ctx->nb * ctx->nb;
+  if (nm <= 16) {
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_mode_rotate_adj(G2b, as<double2>(ctx->uq), nqb, nm, ne, nb2, rows, ctx->stream));
+    return EPH_OK;
+  }
+  for (int iq = 0; iq < nqb; ++iq)
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_zgemm_b2(nm, nb2, nm, as<double2>(ctx->ut) + (long)iq * nm * nm, nm, 0, 0,
+                                                     G2b + (long)iq * p.X, nb2, (long)nm * nb2, 0, rows + (long)iq * p.X,
+                                                     (long)ne * nb2, nb2, 0, ne, 1, 1, ctx->stream));
+  return EPH_OK;
+}
+
+// The gradient GEMM grad += P_q(Rp)^H G1bar takes the G1bar rows of several q batches at once (up
+// to 64 q, within an eighth of the workspace budget): the same multiply-adds, but a reduction
+// length of 64 instead of one q batch, and grad read and written once per 64 q.
+struct GradAcc {
+  long cap = 0;  // G1bar rows (q points) held
+  long n = 0;    // rows waiting
+};
+int grad_acc_init(eph_ctx* ctx, const QPlan& p, GradAcc* a) {
+  const size_t row = (size_t)p.X * sizeof(double2);
+  long cap = (long)(((size_t)ctx->opt.workspace_mb << 20) / 8 / row);
+  if (cap > 64) cap = 64;
+  if (cap < p.QB) cap = p.QB;
+  a->cap = cap;
+  a->n = 0;
+  EPH_TRY(ensure(ctx, ctx->G1bar, (size_t)cap * row));
+  EPH_TRY(ensure(ctx, ctx->Pacc, (size_t)cap * ctx->np * sizeof(double2)));
+  return EPH_OK;
+}
+// rows for the next batch of nqb q points (flushing first if they would not fit)
+int grad_acc_flush(eph_ctx* ctx, const QPlan& p, GradAcc* a, double2* grad) {
+  if (a->n == 0) return EPH_OK;
+  EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ctx->np, (int)p.X, (int)a->n, as<double2>(ctx->Pacc), ctx->np, 0,
+                                              as<double2>(ctx->G1bar), p.X, 0, grad, p.X, 0, 1, 1, ctx->stream));
+  a->n = 0;
+  return EPH_OK;
+}
+int grad_acc_rows(eph_ctx* ctx, const QPlan& p, GradAcc* a, int nqb, double2* grad, double2** rows) {
+  if (a->n + nqb > a->cap) EPH_TRY(grad_acc_flush(ctx, p, a, grad));
+  *rows = as<double2>(ctx->G1bar) + a->n * p.X;
+  return EPH_OK;
+}
+// the batch's phase rows join the waiting rows
+int grad_acc_push(eph_ctx* ctx, GradAcc* a, int nqb, const double2* Pq) {
+  EPH_CK(cudaMemcpyAsync(as<double2>(ctx->Pacc) + a->n * ctx->np, Pq, (size_t)nqb * ctx->np * sizeof(double2),
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+  a->n += nqb;
+  return EPH_OK;
+}
+}  // namespace
+
 extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int nq, const double* qpts,
                                    const double* w_nk, double omega_min, double* L_out, double* grad_g_ReRp) {
   if (!ctx) return EPH_EINVAL;
   if (nk < 1 || nq < 1 || !qpts || !w_nk || !L_out || !grad_g_ReRp)
     return fail(ctx, EPH_EINVAL, "eph_interp_backward: bad size or NULL pointer");
-  if (ctx->big) return fail(ctx, EPH_ENOTSUP, "eph_interp_backward supports nb, nm <= 16");
   if (!whole_g(ctx)) return fail(ctx, EPH_ESTATE, "eph_interp_backward on an Rp-slice context");
   if (kpts) {
     EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
@@ -1754,8 +1876,10 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
   EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
   EPH_TRY(stage_in(ctx, ctx->wk, w_nk, (size_t)nk * nb * sizeof(double), &dw));
   EPH_TRY(ensure_q_workspace(ctx, p));
+  if (ctx->big) EPH_TRY(big_workspace(ctx, p));
   EPH_TRY(ensure(ctx, ctx->G2bar, (size_t)p.QB * p.X * sizeof(double2)));
-  EPH_TRY(ensure(ctx, ctx->G1bar, (size_t)p.QB * p.X * sizeof(double2)));
+  GradAcc acc;
+  EPH_TRY(grad_acc_init(ctx, p, &acc));
   EPH_TRY(ensure(ctx, ctx->Lpair, (size_t)p.QB * p.KT * sizeof(double)));
   EPH_TRY(ensure(ctx, ctx->Lacc, sizeof(double)));
   EPH_TRY(adj_workspace(ctx, p));
@@ -1781,22 +1905,41 @@ extern "C" int eph_interp_backward(eph_ctx* ctx, int nk, const double* kpts, int
       // recompute the Re->k stage and the gauges for this tile (never stored across tiles)
       EPH_TRY(k_tile_forward(ctx, p, nqb, k0, nkt));
       // g, L and G3bar = V_{k+q} (2 c g) V_k^H in place of G3
-      EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_adjoint(Y + nb2, p.NW, as<double2>(ctx->Ukq),
-                                                      as<double2>(ctx->Uk) + k0 * nb2, wdev + k0 * nb,
-                                                      as<double>(ctx->omq), omega_min, nqb, nkt, nm, nb,
-                                                      as<double>(ctx->Lpair), ctx->stream));
+      if (ctx->big) {
+        EPH_TRY(band_adjoint_big(ctx, p, EPH_STAGE_BAND, nqb, k0, nkt, wdev + k0 * nb, omega_min, nullptr, 0));
+      } else if (small_band_tc(ctx)) {
+        // on the tensor cores at FP64 accuracy: 2 c g (and L per pair) over G3, then its adjoint
+        // rotation in place
+        const long rq = (long)nkt * p.NW;
+        const double2* Uk = as<double2>(ctx->Uk) + k0 * nb2;
+        EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc_small64_ex(
+                                         Y + nb2, rq, p.NW, as<double2>(ctx->Ukq), Uk, nqb, nkt, nm, nb, Y + nb2, rq,
+                                         p.NW, nullptr, false, wdev + k0 * nb, as<double>(ctx->omq), omega_min,
+                                         as<double>(ctx->Lpair), ctx->status + 1, ctx->stream));
+        EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc_small64_ex(
+                                         Y + nb2, rq, p.NW, as<double2>(ctx->Ukq), Uk, nqb, nkt, nm, nb, Y + nb2, rq,
+                                         p.NW, nullptr, true, nullptr, nullptr, 0.0, nullptr, ctx->status + 1,
+                                         ctx->stream));
+      } else {
+        EPH_LAUNCH_S(EPH_STAGE_BAND, launch_band_adjoint(Y + nb2, p.NW, as<double2>(ctx->Ukq),
+                                                        as<double2>(ctx->Uk) + k0 * nb2, wdev + k0 * nb,
+                                                        as<double>(ctx->omq), omega_min, nqb, nkt, nm, nb,
+                                                        as<double>(ctx->Lpair), ctx->stream));
+      }
       EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_sum_into(as<double>(ctx->Lpair), (long)nqb * nkt, as<double>(ctx->Lacc),
                                                   ctx->stream));
       // G2bar[q] (+)= P_k^H G3bar  over this k tile
       EPH_TRY(adj_k_tile(ctx, p, nqb, k0, nkt, as<double2>(ctx->Pk), G2b));
     }
     EPH_TRY(adj_k_finish(ctx, p, nqb, G2b, true));
-    // G1bar = conj(u) G2bar (mode rotation adjoint), then grad += P_q(Rp)^H G1bar
-    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_mode_rotate_adj(G2b, as<double2>(ctx->uq), nqb, nm, ne, nb2,
-                                                       as<double2>(ctx->G1bar), ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(np, (int)p.X, nqb, as<double2>(ctx->Pp), np, 0,
-                                                as<double2>(ctx->G1bar), p.X, 0, grad, p.X, 0, 1, 1, ctx->stream));
+    // G1bar = conj(u) G2bar (mode rotation adjoint) into the accumulated rows; grad += P_q(Rp)^H G1bar
+    // once enough q are waiting
+    double2* rows = nullptr;
+    EPH_TRY(grad_acc_rows(ctx, p, &acc, nqb, grad, &rows));
+    EPH_TRY(mode_rotate_adj(ctx, p, nqb, G2b, rows));
+    EPH_TRY(grad_acc_push(ctx, &acc, nqb, as<double2>(ctx->Pp)));
   }
+  EPH_TRY(grad_acc_flush(ctx, p, &acc, grad));
   EPH_CK(cudaMemcpyAsync(L_out, ctx->Lacc.p, sizeof(double), out_kind(ctx), ctx->stream));
   if (host) EPH_CK(cudaMemcpyAsync(grad_g_ReRp, grad, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
   return finish(ctx);
@@ -1823,8 +1966,10 @@ int adjoint_chain(eph_ctx* ctx, int nk, const double* kpts, int nq, const double
   const void* dq = nullptr;
   EPH_TRY(stage_in(ctx, ctx->qpts, qpts, (size_t)nq * 3 * sizeof(double), &dq));
   EPH_TRY(ensure_q_workspace(ctx, p));
+  if (ctx->big) EPH_TRY(big_workspace(ctx, p));
   EPH_TRY(ensure(ctx, ctx->G2bar, (size_t)p.QB * p.X * sizeof(double2)));
-  EPH_TRY(ensure(ctx, ctx->G1bar, (size_t)p.QB * p.X * sizeof(double2)));
+  GradAcc acc;
+  EPH_TRY(grad_acc_init(ctx, p, &acc));
   EPH_TRY(adj_workspace(ctx, p));
   if (host) EPH_TRY(ensure(ctx, ctx->g_stage, (size_t)p.QB * p.KT * gcols * sizeof(double2)));
   const double2* Pk = as<double2>(ctx->Pk);
@@ -1853,7 +1998,7 @@ int adjoint_chain(eph_ctx* ctx, int nk, const double* kpts, int nq, const double
   double2* G2b = as<double2>(ctx->G2bar);
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
     const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
-    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb, false));
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb, false, nullptr, true));
     const double2* Pq = as<double2>(ctx->Pp);
     if (eq6) {
       EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(qdev + 3L * q0, nqb, ctx->Rp, nullptr, np, as<double2>(ctx->Ppu), np,
@@ -1879,19 +2024,28 @@ int adjoint_chain(eph_ctx* ctx, int nk, const double* kpts, int nq, const double
         gb = as<double2>(ctx->g_stage);
         sgq = (long)nkt * gcols;
       }
-      EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_band_vjp(Y + nb2, p.NW, gb, sgq, as<double2>(ctx->Ukq),
-                                                  as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb, ctx->stream));
+      if (ctx->big)
+        EPH_TRY(band_adjoint_big(ctx, p, EPH_STAGE_ADJ, nqb, k0, nkt, nullptr, 0.0, gb, sgq));
+      else if (small_band_tc(ctx))  // G3bar = V_{k+q} gbar V_k^H on the tensor cores at FP64 accuracy
+        EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_band_tc_small64_ex(
+                                        gb, sgq, gcols, as<double2>(ctx->Ukq), as<double2>(ctx->Uk) + k0 * nb2, nqb,
+                                        nkt, nm, nb, Y + nb2, (long)nkt * p.NW, p.NW, nullptr, true, nullptr, nullptr,
+                                        0.0, nullptr, ctx->status + 1, ctx->stream));
+      else
+        EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_band_vjp(Y + nb2, p.NW, gb, sgq, as<double2>(ctx->Ukq),
+                                                    as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb, ctx->stream));
       EPH_TRY(adj_k_tile(ctx, p, nqb, k0, nkt, Pk, G2b));
     }
     EPH_TRY(adj_k_finish(ctx, p, nqb, G2b, !eq6));
-    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_mode_rotate_adj(G2b, as<double2>(ctx->uq), nqb, nm, ne, nb2,
-                                                       as<double2>(ctx->G1bar), ctx->stream));
+    double2* rows = nullptr;
+    EPH_TRY(grad_acc_rows(ctx, p, &acc, nqb, grad, &rows));
+    EPH_TRY(mode_rotate_adj(ctx, p, nqb, G2b, rows));
     if (eq6)
-      EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_scale_modes(as<double2>(ctx->G1bar), nqb, nm, (long)ne * nb2,
-                                                          as<double>(ctx->mfac), ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(np, (int)p.X, nqb, Pq, np, 0, as<double2>(ctx->G1bar), p.X, 0, grad,
-                                                p.X, 0, 1, 1, ctx->stream));
+      EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_scale_modes(rows, nqb, nm, (long)ne * nb2, as<double>(ctx->mfac),
+                                                          ctx->stream));
+    EPH_TRY(grad_acc_push(ctx, &acc, nqb, Pq));
   }
+  EPH_TRY(grad_acc_flush(ctx, p, &acc, grad));
   if (host) EPH_CK(cudaMemcpyAsync(out_ReRp, grad, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
   return finish(ctx);
 }
@@ -1902,8 +2056,6 @@ extern "C" int eph_interp_vjp(eph_ctx* ctx, int nk, const double* kpts, int nq, 
   if (!ctx) return EPH_EINVAL;
   if (nk < 1 || nq < 1 || !qpts || !grad_g || !grad_g_ReRp)
     return fail(ctx, EPH_EINVAL, "eph_interp_vjp: bad size or NULL pointer");
-  if (ctx->big || ctx->opt.form != EPH_FORM_FP64)
-    return fail(ctx, EPH_ENOTSUP, "eph_interp_vjp: FP64 form with nb, nm <= 16");
   return adjoint_chain(ctx, nk, kpts, nq, qpts, grad_g, grad_g_ReRp, false);
 }
 
@@ -1912,8 +2064,6 @@ extern "C" int eph_bloch_to_wannier(eph_ctx* ctx, int nk, const double* kpts, in
   if (!ctx) return EPH_EINVAL;
   if (nk < 1 || nq < 1 || !qpts || !g || !g_ReRp)
     return fail(ctx, EPH_EINVAL, "eph_bloch_to_wannier: bad size or NULL pointer");
-  if (ctx->big || ctx->opt.form != EPH_FORM_FP64)
-    return fail(ctx, EPH_ENOTSUP, "eph_bloch_to_wannier: FP64 form with nb, nm <= 16");
   return adjoint_chain(ctx, nk, kpts, nq, qpts, g, g_ReRp, true);
 }
 
@@ -2068,8 +2218,6 @@ extern "C" int eph_linewidths(eph_ctx* ctx, int nq, const double* qpts, const do
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_linewidths before eph_set_k");
   if (nq < 1 || !qpts || !gamma || !(kT > 0.0) || !(sigma > 0.0))
     return fail(ctx, EPH_EINVAL, "eph_linewidths: nq < 1, NULL pointer, or kT/sigma not positive");
-  if (ctx->opt.form != EPH_FORM_FP64 || ctx->big)
-    return fail(ctx, EPH_ENOTSUP, "eph_linewidths: FP64 form with nb, nm <= 16");
   if (!whole_g(ctx)) return fail(ctx, EPH_ESTATE, "eph_linewidths on an Rp-slice context");
   const int nb = ctx->nb, nm = ctx->nm, nk = ctx->nk, nb2 = nb * nb;
   QPlan p;
@@ -2092,11 +2240,27 @@ extern "C" int eph_linewidths(eph_ctx* ctx, int nq, const double* qpts, const do
   double2* Y = as<double2>(ctx->Y);
   for (int q0 = 0; q0 < nq; q0 += p.QB) {
     const int nqb = (nq - q0 < p.QB) ? nq - q0 : p.QB;
-    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb));
+    EPH_TRY(q_prelude(ctx, p, qdev + 3L * q0, nqb, true, nullptr, true));
     for (long k0 = 0; k0 < nk; k0 += p.KT) {
       const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
       EPH_TRY(k_tile_forward(ctx, p, nqb, k0, nkt));
-      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_linewidth(
+      if (ctx->big || small_band_tc(ctx)) {
+        // g over the G3 rows (GEMMs for large shapes, the FP64-accuracy tensor-core rotation for
+        // small ones), then the linewidth terms from those rows
+        if (ctx->big) {
+          EPH_TRY(band_rotate_big_inplace(ctx, p, EPH_STAGE_BAND, nqb, k0, nkt));
+        } else {
+          const long rq = (long)nkt * p.NW;
+          EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc_small64_ex(
+                                           Y + nb2, rq, p.NW, as<double2>(ctx->Ukq), as<double2>(ctx->Uk) + k0 * nb2,
+                                           nqb, nkt, nm, nb, Y + nb2, rq, p.NW, nullptr, false, nullptr, nullptr, 0.0,
+                                           nullptr, ctx->status + 1, ctx->stream));
+        }
+        EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_linewidth_terms(
+                                         Y + nb2, p.NW, as<double>(ctx->eps_k) + k0 * nb, as<double>(ctx->eps_tile),
+                                         as<double>(ctx->omq), as<double>(ctx->wqb) + q0, nqb, nkt, nm, nb, kT, mu,
+                                         sigma, omega_min, as<double>(ctx->lwpart), ctx->stream));
+      } else EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_linewidth(
                                        Y + nb2, p.NW, as<double2>(ctx->Ukq), as<double2>(ctx->Uk) + k0 * nb2,
                                        as<double>(ctx->eps_k) + k0 * nb, as<double>(ctx->eps_tile),
                                        as<double>(ctx->omq), as<double>(ctx->wqb) + q0, nqb, nkt, nm, nb, kT, mu, sigma,

@@ -859,10 +859,18 @@ __device__ __forceinline__ void mma_levels64(uint32_t acc, int ncol, uint32_t sA
 // each with its own shared memory (slot_bytes), TMEM columns (slot_cols), mbarrier and named
 // barrier (1 + slot): the five accumulators of a slot take 160 columns at the Si shapes, so
 // three slots share one 512-column allocation where separate CTAs would each round up to 256.
+//
+// Pair (iq, kk) reads its rows [nu][a][b] at X + iq xq + kk xk and writes [nu][m][n] at
+// out + iq oq + kk ok; the two may be the same rows (a tile's input is in shared memory before its
+// output is written, and no two tiles share a pair).  adj = 0: V_{k+q}^H X V_k (the band rotation);
+// adj = 1: V_{k+q} X V_k^H (its adjoint, the same products with both V conjugate-transposed).
+// wk non-NULL: the loss terms of the adjoint, c = w_nk / omega_qnu (0 for omega <= omega_min):
+// Lpair[iq nk + kk] = sum c |g|^2 (fixed order) and 2 c g written instead of g.
 template <int KP>
 __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_tc_small64(
-    const double2* __restrict__ Y, long ldy, const double2* __restrict__ Ukq, const double2* __restrict__ Uk, int nq,
-    int nk, int nm, int nb, int RS, int PPT, double2* __restrict__ g, long sgq, const int* __restrict__ keep,
+    const double2* X, long xq, long xk, const double2* __restrict__ Ukq, const double2* __restrict__ Uk, int nq,
+    int nk, int nm, int nb, int RS, int PPT, double2* g, long oq, long ok, const int* __restrict__ keep, int adj,
+    const double* __restrict__ wk, const double* __restrict__ om, double omega_min, double* __restrict__ Lpair,
     int* __restrict__ err, uint32_t tmem_cols, int nslots, unsigned slot_bytes, unsigned slot_cols) {
   using namespace bts;
   using bt64::ND;
@@ -883,6 +891,7 @@ __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_t
   int* gmax = reinterpret_cast<int*>(rawV + (size_t)(PPT + 1) * nb * nb * sizeof(double2));  // [4] G3 exponent
   int* umax = gmax + 4;                                                      // [4] bit length of U
   uint64_t* bar = reinterpret_cast<uint64_t*>(umax + 4);
+  double* lred = reinterpret_cast<double*>(bar + 1);                         // [4] loss per warp
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm_all + (size_t)nslots * slot_bytes);  // CTA-wide
   const int tid = threadIdx.x & 127, warp = tid >> 5;  // within the slot; warp = TMEM lane quarter
   auto slot_sync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(1 + slot) : "memory"); };
@@ -936,7 +945,7 @@ __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_t
       const int iq = qg * PPT + jj;
       if (iq >= nq) break;
       const long P = (long)iq * nk + kk;
-      const double2* src = Y + P * ldy;
+      const double2* src = X + (long)iq * xq + (long)kk * xk;
       const uint32_t dst = sRawG + (uint32_t)((size_t)jj * per * sizeof(double2));
       for (int i = tid; i < per; i += THREADS) cp_async<16>(dst + (uint32_t)(i * 16), src + i);
       const double2* vs = Ukq + P * nb2;
@@ -985,14 +994,16 @@ __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_t
       atomicMax(&gmax[j], eb);
     }
     // ---- B operands: digits of conj(V_{k+q}) (stage 1, block per pair) and V_k (stage 2), scale 2
-    // (|v| <= 1 for unitary V)
+    // (|v| <= 1 for unitary V); the adjoint takes conj(V[c][a]) in place of V[a][c]
     for (int e = tid; e < (PPT + 1) * nb2; e += THREADS) {
       const int jj = (int)(((unsigned)e * div_nb2) >> 16), r2 = e - jj * nb2;
       const int a = (int)(((unsigned)r2 * div_nb) >> 16), c = r2 - a * nb;
+      const int rv = adj ? c * nb + a : r2;
       float vr[ND], vi[ND];
       if (jj < PPT) {
         if (qg * PPT + jj >= nq) continue;
-        const double2 u = vsm[jj * nb2 + r2];
+        double2 u = vsm[jj * nb2 + rv];
+        if (adj) u.y = -u.y;
         bt64::xdigits(bt64::dfixed48(u.x, 1022), vr);
         bt64::xdigits(bt64::dfixed48(u.y, 1022), vi);
         const uint32_t o0 = off<KP>(jj * KP + 2 * c, 2 * a), o1 = off<KP>(jj * KP + 2 * c + 1, 2 * a);
@@ -1002,7 +1013,8 @@ __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_t
           st32(sB1 + d * B1_TILE + o1, pack2(-vi[d], vr[d]));
         }
       } else {
-        const double2 u = vsm[PPT * nb2 + r2];
+        double2 u = vsm[PPT * nb2 + rv];
+        if (adj) u.y = -u.y;
         bt64::xdigits(bt64::dfixed48(u.x, 1022), vr);
         bt64::xdigits(bt64::dfixed48(u.y, 1022), vi);
         const uint32_t o0 = off<KP>(2 * c, 2 * a), o1 = off<KP>(2 * c + 1, 2 * a);
@@ -1116,18 +1128,42 @@ __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_t
         ld16(lane_base + (uint32_t)(4 * N1) + c, l4 + c);
       }
       ld_wait();
+      double lsum = 0.0;
       if (live) {
-        double2* out = g + (long)iq * sgq + (long)kk * nm * nb2 + (long)nu2 * nb2 + (long)m2 * nb;
+        double2* out = g + (long)iq * oq + (long)kk * ok + (long)nu2 * nb2 + (long)m2 * nb;
         const bool zero = keep && !keep[P];
         // U = X_U 2^-48 2^(gex - 1021) 2; stage-2 A holds U / (2^B 2^-48 2^(gex - 1021) 2)
         const int E = B - 48 + (gex - 1021) + 1 + 1 - 48;
+        double inv = 0.0;  // loss: 1 / omega of the row's mode, 0 at or below omega_min
+        if (wk) {
+          const double w = om[(long)iq * nm + nu2];
+          inv = w > omega_min ? 1.0 / w : 0.0;
+        }
 #pragma unroll
         for (int n = 0; n < KP / 2; ++n) {
           if (n < nb) {
             const long long xr = bt64::combine(l0[2 * n], l1[2 * n], l2[2 * n], l3[2 * n], l4[2 * n]);
             const long long xi = bt64::combine(l0[2 * n + 1], l1[2 * n + 1], l2[2 * n + 1], l3[2 * n + 1], l4[2 * n + 1]);
-            out[n] = zero ? make_double2(0.0, 0.0) : make_double2(bt64::i2d_scaled(xr, E), bt64::i2d_scaled(xi, E));
+            double2 v = zero ? make_double2(0.0, 0.0) : make_double2(bt64::i2d_scaled(xr, E), bt64::i2d_scaled(xi, E));
+            if (wk) {
+              const double c = wk[(long)kk * nb + n] * inv;
+              lsum = fma(c, fma(v.x, v.x, v.y * v.y), lsum);
+              v = make_double2(2.0 * c * v.x, 2.0 * c * v.y);
+            }
+            out[n] = v;
           }
+        }
+      }
+      if (wk) {
+        // a pair's rows are whole warps (RS is a multiple of 32): warp sums, then the pair's warps in order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if ((tid & 31) == 0) lred[warp] = lsum;
+        slot_sync();
+        if (live && rr == 0) {
+          double sum = 0.0;
+          for (int w = j * (RS / 32); w < (j + 1) * (RS / 32); ++w) sum += lred[w];
+          Lpair[P] = sum;
         }
       }
     }
@@ -1247,7 +1283,16 @@ cudaError_t launch_band_tc_small(const void* Y, int y_f32, long ldy, const doubl
 // slots (as many as the 512 TMEM columns and the shared memory hold)
 cudaError_t launch_band_tc_small64(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
                                    int nm, int nb, double2* g, long sgq, const int* keep, int* err, cudaStream_t st) {
+  return launch_band_tc_small64_ex(Y, (long)nk * ldy, ldy, Ukq, Uk, nq, nk, nm, nb, g, sgq, (long)nm * nb * nb, keep,
+                                   false, nullptr, nullptr, 0.0, nullptr, err, st);
+}
+
+cudaError_t launch_band_tc_small64_ex(const double2* X, long xq, long xk, const double2* Ukq, const double2* Uk, int nq,
+                                      int nk, int nm, int nb, double2* out, long oq, long ok, const int* keep, bool adj,
+                                      const double* wk, const double* om, double omega_min, double* Lpair, int* err,
+                                      cudaStream_t st) {
   if ((long)nq * nk <= 0) return cudaSuccess;
+  if (wk && (!om || !Lpair)) return cudaErrorInvalidValue;
   if (!band_tc_small_supported(nm, nb) || nk < 1) return cudaErrorInvalidValue;
   const SmallShape s = small_shape(nm, nb, bt64::NACC);
   int dev = 0, sms = 0;
@@ -1256,7 +1301,7 @@ cudaError_t launch_band_tc_small64(const double2* Y, long ldy, const double2* Uk
   const long ntiles = (long)((nq + s.ppt - 1) / s.ppt) * nk;
   const unsigned slot_cols = (unsigned)(((bt64::NACC * s.n1) + 31) / 32 * 32);
   const size_t slot_need = (size_t)bt64::ND * (128 * s.kp * 2 + (size_t)s.n1 * s.kp * 2 + (size_t)s.kp * s.kp * 2) +
-                           (size_t)s.ppt * nm * nb * nb * 16 + (size_t)(s.ppt + 1) * nb * nb * 16 + 64;
+                           (size_t)s.ppt * nm * nb * nb * 16 + (size_t)(s.ppt + 1) * nb * nb * 16 + 128;
   const unsigned slot_bytes = (unsigned)((slot_need + 1023) & ~(size_t)1023);
   int nslots = (int)(512 / slot_cols);
   nslots = std::min(nslots, (int)((220 * 1024 - 64) / slot_bytes));
@@ -1275,10 +1320,12 @@ cudaError_t launch_band_tc_small64(const double2* Y, long ldy, const double2* Uk
   const long grid = std::min((ntiles + nslots - 1) / nslots, (long)sms * occ);
   if (s.kp == 16)
     k_band_tc_small64<16><<<(unsigned)grid, nslots * bts::THREADS, smem, st>>>(
-        Y, ldy, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, g, sgq, keep, err, cols, nslots, slot_bytes, slot_cols);
+        X, xq, xk, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, out, oq, ok, keep, adj ? 1 : 0, wk, om, omega_min, Lpair, err,
+        cols, nslots, slot_bytes, slot_cols);
   else
     k_band_tc_small64<32><<<(unsigned)grid, nslots * bts::THREADS, smem, st>>>(
-        Y, ldy, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, g, sgq, keep, err, cols, nslots, slot_bytes, slot_cols);
+        X, xq, xk, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, out, oq, ok, keep, adj ? 1 : 0, wk, om, omega_min, Lpair, err,
+        cols, nslots, slot_bytes, slot_cols);
   return cudaGetLastError();
 }
 

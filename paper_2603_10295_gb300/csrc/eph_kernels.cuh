@@ -153,6 +153,10 @@ cudaError_t launch_band_linewidth(const double2* Y, long ldy, const double2* Ukq
                                   const double* epskq, const double* om, const double* wq, int nq, int nk, int nm,
                                   int nb, double kT, double mu, double sigma, double omega_min, double* part,
                                   cudaStream_t st);
+// The same terms from g rows already formed ([nu][m][n] per pair, pair stride ldg): any nb, nm.
+cudaError_t launch_linewidth_terms(const double2* G, long ldg, const double* epsk, const double* epskq,
+                                   const double* om, const double* wq, int nq, int nk, int nm, int nb, double kT,
+                                   double mu, double sigma, double omega_min, double* part, cudaStream_t st);
 // acc[k][n] += sum_q part[q][k][n]
 cudaError_t launch_sum_over_q(const double* part, int nq, long per_q, double* acc, cudaStream_t st);
 
@@ -174,6 +178,12 @@ cudaError_t launch_sum_into(const double* v, long n, double* L, cudaStream_t st)
 // G1bar[q][c][e][b] = sum_nu conj(u[q][c][nu]) G2bar[q][e][nu][b]
 cudaError_t launch_mode_rotate_adj(const double2* G2b, const double2* u, int nq, int nm, int ne, int nb2,
                                    double2* G1b, cudaStream_t st);
+// Large shapes: L per pair and 2 c g in place over the g rows [nu][m][n] (row stride ldy) of a
+// (q batch, k tile); c = wk[k][n] / om[q][nu], 0 for om <= omega_min.
+cudaError_t launch_loss_terms(double2* Y, long ldy, const double* wk, const double* om, double omega_min, int nq,
+                              int nk, int nm, int nb, double* Lpair, cudaStream_t st);
+// out[b] = in[b]^H for a batch of n x n complex matrices.
+cudaError_t launch_conj_transpose(const double2* in, int n, long batch, double2* out, cudaStream_t st);
 
 // ---- mixed form (split-TF32 tensor-core Re->k contraction) -------------------------
 // TMA descriptor (CUtensorMap, 128 bytes) over a row-major FP32 [rows][kp] array:
@@ -238,10 +248,18 @@ bool band_tc_small_supported(int nm, int nb);
 cudaError_t launch_band_tc_small(const void* Y, int y_f32, long ldy, const double2* Ukq, const double2* Uk, int nq,
                                  int nk, int nm, int nb, float2* g, long sgq, const int* keep, int* err,
                                  cudaStream_t st);
-// The same rotation at FP64 accuracy (seven-digit operands, exact level sums, integer assembly of
-// the doubles): complex128 G3 in, complex128 g out, ~1e-14 of each pair's largest element.
+// The same rotation at FP64 accuracy (six-digit operands, exact level sums, integer assembly of
+// the doubles): complex128 G3 in, complex128 g out, ~5e-14 of each pair's largest element.
 cudaError_t launch_band_tc_small64(const double2* Y, long ldy, const double2* Ukq, const double2* Uk, int nq, int nk,
                                    int nm, int nb, double2* g, long sgq, const int* keep, int* err, cudaStream_t st);
+// General form: pair (iq, kk) reads X + iq xq + kk xk and writes out + iq oq + kk ok (may be the
+// same rows); adj: V_{k+q} X V_k^H instead of V_{k+q}^H X V_k; wk non-NULL: the adjoint's loss
+// terms, Lpair[iq nk + kk] = sum c |g|^2 and 2 c g written (c = wk[kk][n] / om[iq][nu], 0 for
+// om <= omega_min).
+cudaError_t launch_band_tc_small64_ex(const double2* X, long xq, long xk, const double2* Ukq, const double2* Uk, int nq,
+                                      int nk, int nm, int nb, double2* out, long oq, long ok, const int* keep, bool adj,
+                                      const double* wk, const double* om, double omega_min, double* Lpair, int* err,
+                                      cudaStream_t st);
 cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const double2* Ukq, const double2* Uk, int nq,
                            int nk, int nm, int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err,
                            cudaStream_t st);

@@ -327,6 +327,75 @@ cudaError_t launch_band_linewidth(const double2* Y, long ldy, const double2* Ukq
   return cudaGetLastError();
 }
 
+// The same linewidth terms from g rows already formed ([nu][m][n] of a pair at G + pair ldg): one
+// CTA per pair; thread t takes column n = n0 + t % cols and every rpp-th row (nu, m) from t / cols,
+// its partial sums then combine in a fixed order (deterministic for any nb, nm).
+__global__ void __launch_bounds__(128) k_linewidth_terms(const double2* __restrict__ G, long ldg,
+                                                         const double* __restrict__ epsk,
+                                                         const double* __restrict__ epskq,
+                                                         const double* __restrict__ om, const double* __restrict__ wq,
+                                                         int nk, int nm, int nb, double kT, double mu, double sigma,
+                                                         double omega_min, double* __restrict__ part) {
+  extern __shared__ double lw_sm[];
+  double* fm = lw_sm;         // [nb] Fermi factors at k+q
+  double* nbose = fm + nb;    // [nm] Bose factors (0 for excluded modes)
+  double* red = nbose + nm;   // [blockDim.x] partial sums
+  const long pair = blockIdx.x;
+  const int k = (int)(pair % nk);
+  const long q = pair / nk;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) fm[t] = 1.0 / (exp((epskq[pair * nb + t] - mu) / kT) + 1.0);
+  for (int t = threadIdx.x; t < nm; t += blockDim.x) {
+    const double w = om[q * nm + t];
+    nbose[t] = (w > omega_min) ? 1.0 / expm1(w / kT) : 0.0;
+  }
+  __syncthreads();
+  const double inv = 1.0 / (sigma * sqrt(2.0 * 3.141592653589793238));
+  const double c = -0.5 / (sigma * sigma);
+  const double2* g = G + pair * ldg;
+  const int R = nm * nb;  // rows (nu, m)
+  for (int n0 = 0; n0 < nb; n0 += blockDim.x) {
+    const int cols = min(nb - n0, (int)blockDim.x);
+    const int rpp = blockDim.x / cols;
+    const int n = n0 + threadIdx.x % cols, r1 = threadIdx.x / cols;
+    double sum = 0.0;
+    if (r1 < rpp) {
+      const double en = epsk[(long)k * nb + n];
+      for (int r = r1; r < R; r += rpp) {
+        const int nu = r / nb, m = r - nu * nb;
+        const double w = om[q * nm + nu];
+        if (w > omega_min) {
+          const double2 gv = g[(long)r * nb + n];
+          const double nB = nbose[nu], f = fm[m];
+          const double de = en - epskq[pair * nb + m];
+          const double xa = de + w, xe = de - w;
+          const double d = (nB + f) * exp(c * xa * xa) + (nB + 1.0 - f) * exp(c * xe * xe);
+          sum += fma(gv.x, gv.x, gv.y * gv.y) / (2.0 * w) * d;
+        }
+      }
+    }
+    red[threadIdx.x] = sum;
+    __syncthreads();
+    if ((int)threadIdx.x < cols) {
+      double tot = 0.0;
+      for (int i = 0; i < rpp; ++i) tot += red[i * cols + threadIdx.x];
+      part[pair * nb + n] = 3.141592653589793238 * wq[q] * inv * tot;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_linewidth_terms(const double2* G, long ldg, const double* epsk, const double* epskq,
+                                   const double* om, const double* wq, int nq, int nk, int nm, int nb, double kT,
+                                   double mu, double sigma, double omega_min, double* part, cudaStream_t st) {
+  const long pairs = (long)nq * nk;
+  if (pairs <= 0) return cudaSuccess;
+  if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
+  const size_t smem = (size_t)(nb + nm + 128) * sizeof(double);
+  k_linewidth_terms<<<(unsigned)pairs, 128, smem, st>>>(G, ldg, epsk, epskq, om, wq, nk, nm, nb, kT, mu, sigma,
+                                                        omega_min, part);
+  return cudaGetLastError();
+}
+
 // acc[k][n] += sum_{q < nq} part[q][k][n] (fixed order over q).
 __global__ void k_sum_over_q(const double* __restrict__ part, int nq, long per_q, double* __restrict__ acc) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -8,6 +8,7 @@ context (same G3, same eigenvectors): both round g once to complex64, so they ag
 FP32 ulps of each pair's largest element.  Shapes cover every tile arrangement: one, two and four
 pairs per tile, K = 16 and 32, ragged last tiles; both inputs: complex64 G3 from the tensor-core
 Re->k contraction (k list) and complex128 G3 from the sum-factorised FP64 transforms (uniform grid)."""
+import copy
 import os
 
 import numpy as np
@@ -143,3 +144,49 @@ def test_band_small_fp64_scaled_and_zero_inputs():
     w0.g_ReRp = np.zeros_like(wl.g_ReRp)
     g0 = binding.Context.from_workload(w0).interp(w0.kpts, w0.qpts)[3]
     assert not np.any(g0)
+
+
+# the adjoint and the VJP take the same FP64 tensor-core rotation, conjugate-transposed, with the
+# loss terms in the epilogue of the forward product
+TOL_ADJ = 1e-12   # against the FP64 oracle's loss and gradient (relative to the largest element)
+TOL_ADJ_ALU = 2e-13  # against the CUDA-core FP64 adjoint of the same context
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("nb,na", [(8, 2), (11, 3), (3, 1), (9, 1), (16, 2), (1, 1)])
+def test_band_small_fp64_adjoint(nb, na):
+    wl = synth.make_workload("si_tiny", nb=nb, na=na, nk=29, nq=5)
+    rng = np.random.default_rng(nb)
+    w = rng.uniform(0.0, 1.0, (len(wl.kpts), wl.nb))
+    L, grad = binding.Context.from_workload(wl, q_batch=3, k_tile=13).loss_and_grad(wl.kpts, wl.qpts, w, 1e-6)
+    La, ga = binding.Context.from_workload(wl, q_batch=3, k_tile=13, band_alu=True).loss_and_grad(
+        wl.kpts, wl.qpts, w, 1e-6)
+    Lr, gr = oracle.loss_and_grad(wl, wl.kpts, wl.qpts, w, 1e-6)
+    print(f"L {abs(L - Lr) / abs(Lr):.3g}  grad {_rel(grad, gr):.3g}  vs ALU {_rel(grad, ga):.3g}")
+    assert abs(L - Lr) <= TOL_ADJ * abs(Lr)
+    assert _rel(grad, gr) <= TOL_ADJ
+    assert abs(L - La) <= TOL_ADJ_ALU * abs(La)
+    assert _rel(grad, ga) <= TOL_ADJ_ALU
+
+
+@pytest.mark.parametrize("nb,na", [(8, 2), (11, 3), (5, 3)])
+def test_band_small_fp64_vjp(nb, na):
+    wl = synth.make_workload("si_tiny", nb=nb, na=na, nk=31, nq=4)
+    rng = np.random.default_rng(7 + nb)
+    shape_g = (len(wl.qpts), len(wl.kpts), wl.nm, wl.nb, wl.nb)
+    gbar = rng.standard_normal(shape_g) + 1j * rng.standard_normal(shape_g)
+    v = binding.Context.from_workload(wl, q_batch=3, k_tile=11).vjp(wl.kpts, wl.qpts, gbar)
+    va = binding.Context.from_workload(wl, q_batch=3, k_tile=11, band_alu=True).vjp(wl.kpts, wl.qpts, gbar)
+    # an arbitrary gbar is not gauge covariant: the oracle's eigenvectors give another VJP, so the
+    # check is <v, d> = <gbar, A d> with A d from the same context's eigenvectors
+    d = rng.standard_normal(wl.g_ReRp.shape) + 1j * rng.standard_normal(wl.g_ReRp.shape)
+    wd = copy.copy(wl)
+    wd.g_ReRp = d
+    Ad = binding.Context.from_workload(wd, q_batch=3, k_tile=11, band_alu=True).interp(wl.kpts, wl.qpts)[3]
+    lhs, rhs = np.real(np.vdot(v, d)), np.real(np.vdot(gbar, Ad))
+    print(f"vjp dot identity {abs(lhs - rhs) / np.sum(np.abs(gbar) * np.abs(Ad)):.3g}  vs ALU {_rel(v, va):.3g}")
+    assert abs(lhs - rhs) <= 1e-12 * np.sum(np.abs(gbar) * np.abs(Ad))
+    assert _rel(v, va) <= TOL_ADJ_ALU

@@ -95,7 +95,11 @@ def test_device_mode_matches_host_mode():
 
 def test_eq6_errors():
     wl = synth.make_workload("si_tiny", nk=2, nq=2)
-    mixed = binding.Context.from_workload(wl, form="mixed")
+    ctx = binding.Context.from_workload(wl)
     with pytest.raises(binding.EphError) as ei:
-        mixed.bloch_to_wannier(wl.kpts, wl.qpts, np.zeros((2, 2, wl.nm, wl.nb, wl.nb), dtype=np.complex128))
-    assert ei.value.code == binding.EPH_ENOTSUP
+        ctx.eph_bloch_to_wannier(2, wl.kpts, 2, wl.qpts, None, np.empty(wl.g_ReRp.shape, dtype=np.complex128))
+    assert ei.value.code == binding.EPH_EINVAL
+    # a mixed-form context runs the same FP64 chain: zero g gives zero g(Re,Rp)
+    mixed = binding.Context.from_workload(wl, form="mixed")
+    rec = mixed.bloch_to_wannier(wl.kpts, wl.qpts, np.zeros((2, 2, wl.nm, wl.nb, wl.nb), dtype=np.complex128))
+    assert not np.any(rec)

@@ -77,10 +77,12 @@ def test_mixed_large_odd_row_length():
 
 
 def test_large_shapes_rejected_where_not_supported():
+    # the energy-window call keeps its warp-resident kernels: nb, nm <= 16
     wl = synth.make_workload("si_tiny", nb=20, nk=4, nq=2)
     ctx = binding.Context.from_workload(wl)
+    ctx.set_k_window(wl.kpts, -1e3, 1e3)
     with pytest.raises(binding.EphError) as ei:
-        ctx.loss_and_grad(wl.kpts, wl.qpts, np.ones((len(wl.kpts), wl.nb)), 1e-6)
+        ctx.interp_q_window(wl.qpts, -1e3, 1e3)
     assert ei.value.code == binding.EPH_ENOTSUP
 
 

@@ -1,7 +1,8 @@
-"""GPU parity of the fused linewidth consumer (eph_linewidths) against the oracle.
+"""GPU parity of the linewidth consumer (eph_linewidths) against the oracle.
 
 The oracle forms g (oracle.interpolate) and then the imaginary Fan-Migdal
-self-energy (oracle.linewidths); libeph does both in one pass without writing g.
+self-energy (oracle.linewidths); libeph forms g in its k-tile workspace (over the
+G3 rows) and reduces it to Gamma there, never writing g out.
 Inside a group of degenerate bands at k only the group sum of Gamma is gauge
 invariant, so Gamma is compared through those sums (groups as in tests/gauge.py).
 Bar: max |dGamma| / max Gamma per k <= 1e-10.  The Gaussian delta turns an
@@ -104,10 +105,49 @@ def test_linewidth_errors():
     with pytest.raises(binding.EphError) as ei:
         ctx.linewidths(wl.qpts, sigma=0.0)
     assert ei.value.code == binding.EPH_EINVAL
-    mixed = binding.Context.from_workload(wl, form="mixed")
-    mixed.set_k(wl.kpts)
-    with pytest.raises(binding.EphError) as ei:
-        mixed.linewidths(wl.qpts)
-    assert ei.value.code == binding.EPH_ENOTSUP
     # the context still works afterwards
     ctx.linewidths(wl.qpts)
+
+
+def test_tensor_core_rotation_matches_fused_fp64_kernel():
+    # g from the FP64-accuracy tensor-core rotation (in place over G3, then the terms) against the
+    # fused CUDA-core kernel (band_alu): ~5e-14 of each pair's largest |g| apart
+    wl = synth.make_workload("si_tiny", nk=40, nq=5)
+    out = []
+    for band_alu in (False, True):
+        ctx = binding.Context.from_workload(wl, q_batch=2, k_tile=16, band_alu=band_alu)
+        ctx.set_k(wl.kpts)
+        out.append(ctx.linewidths(wl.qpts, None, kT=KT, mu=0.0, sigma=0.3, omega_min=1e-6))
+    e_k = oracle.interpolate(wl, wl.kpts, wl.qpts[:1])[0]
+    assert grouped_err(out[0], out[1], e_k) <= 1e-12
+
+
+@pytest.mark.parametrize("nb,na", [(20, 2), (8, 7)])
+def test_large_shape_linewidths(nb, na):
+    # nb or nm > 16: g by the GEMM band rotation over the G3 rows, then the terms kernel
+    wl = synth.make_workload("si_tiny", nb=nb, na=na, nk=12, nq=4)
+    ctx = binding.Context.from_workload(wl, q_batch=3, k_tile=5)
+    ctx.set_k(wl.kpts)
+    got = ctx.linewidths(wl.qpts, None, kT=KT, mu=0.0, sigma=0.4, omega_min=1e-6)
+    ref, e_k = reference(wl, wl.kpts, wl.qpts, np.ones(len(wl.qpts)), 0.0, 0.4, 1e-6)
+    assert grouped_err(got, ref, e_k) <= TOL
+
+
+def test_zsnr_ribbon_shape_linewidths():
+    wl = synth.make_workload("stanene", nb=32, na=18, nk=6, nq=2)
+    ctx = binding.Context.from_workload(wl)
+    ctx.set_k(wl.kpts)
+    got = ctx.linewidths(wl.qpts, None, kT=KT, mu=0.0, sigma=0.3, omega_min=1e-6)
+    ref, e_k = reference(wl, wl.kpts, wl.qpts, np.ones(len(wl.qpts)), 0.0, 0.3, 1e-6)
+    assert grouped_err(got, ref, e_k) <= TOL
+
+
+def test_mixed_form_context_linewidths():
+    # a mixed-form context runs the same FP64 chain; its electron eigensolves stop at 1e-12, which
+    # the Gaussian turns into ~1e-12 |eps| |x| / sigma^2 of a term
+    wl = synth.make_workload("si_tiny", nk=30, nq=4)
+    ctx = binding.Context.from_workload(wl, form="mixed")
+    ctx.set_k(wl.kpts)
+    got = ctx.linewidths(wl.qpts, None, kT=KT, mu=0.0, sigma=0.3, omega_min=1e-6)
+    ref, e_k = reference(wl, wl.kpts, wl.qpts, np.ones(len(wl.qpts)), 0.0, 0.3, 1e-6)
+    assert grouped_err(got, ref, e_k) <= 1e-9
