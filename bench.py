@@ -308,6 +308,56 @@ def cpu_baseline(wl, nk_sample, steps=1):
             "seconds": t}
 
 
+def cpu_baseline_config(wl, nq_full, nk_small, nk_large):
+    """The FP64 oracle on a workload's full configuration, timed on samples and extrapolated.
+
+    One q point at two random k subsets (nk_small, nk_large) gives the per-q time as a line in Nk:
+    the k-independent part (the Rp->q sum of Eq. 9, D(q) and its eigensolve) plus a per-k part
+    (H(k), H(k+q), their eigensolves, the Re->k sum and the band rotation).  The full grid's per-q
+    time follows from that line; the configuration's time is Nq times it (the cost is linear in Nq
+    apart from the k-only H(k) work, which the oracle repeats per q and this leaves in)."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(len(wl.kpts))
+    ts = []
+    for n in (nk_small, nk_large):
+        ks = np.sort(perm[:n])
+        t0 = time.perf_counter()
+        oracle.interpolate(wl, wl.kpts[ks], wl.qpts[:1])
+        ts.append(time.perf_counter() - t0)
+    per_k = max((ts[1] - ts[0]) / (nk_large - nk_small), 0.0)
+    per_q0 = max(ts[0] - per_k * nk_small, 0.0)
+    nk = len(wl.kpts)
+    per_q = per_q0 + per_k * nk
+    units = nk * wl.nm * wl.nb * wl.nb
+    return {"value": units / per_q, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 q x {nk_small} and 1 q x {nk_large} random k of {nk} (numpy FP64, BLAS threads = "
+                      f"all cores); per-q time fitted as a + b Nk, extrapolated to {nk} k and {nq_full} q",
+            "seconds_sampled": sum(ts), "s_per_q_k_independent": per_q0, "s_per_k": per_k,
+            "s_per_q_extrapolated": per_q, "s_full_config_extrapolated": per_q * nq_full}
+
+
+def cpu_baseline_adjoint(wl, nq_full, w_nk, omega_min):
+    """The FP64 oracle's loss and gradient (forward plus the reverse chain) on the full k grid for
+    one and for two q points; per-q time = the difference, extrapolated linearly to nq_full q."""
+    import oracle
+    ts = []
+    for nq in (1, 2):
+        t0 = time.perf_counter()
+        oracle.loss_and_grad(wl, wl.kpts, wl.qpts[:nq], w_nk, omega_min)
+        ts.append(time.perf_counter() - t0)
+    per_q = max(ts[1] - ts[0], 0.0)
+    fixed = max(ts[0] - per_q, 0.0)
+    el = len(wl.kpts) * wl.nm * wl.nb * wl.nb
+    full = fixed + per_q * nq_full
+    return {"value": el * nq_full / full, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle.loss_and_grad on all {len(wl.kpts)} k for 1 and 2 q (numpy FP64); per-q time = "
+                      f"their difference, extrapolated to {nq_full} q",
+            "seconds_sampled": sum(ts), "s_per_q": per_q, "s_full_config_extrapolated": full}
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -442,7 +492,7 @@ def time_form(wl, form, args, q_dev, k_dev, rank, world, local, dev, QB, use_gri
     return out
 
 
-def time_backward(args):
+def time_backward(args, cpu=True):
     """eph_interp_backward on the differentiation workload (mos2_diff: 48x48 k grid x 256 q, FP64):
     the library call on the resident grid (forward Re->k sum and its adjoint sum-factorised), its
     stage breakdown, the same call on the points as a plain k list (dense GEMMs), and one
@@ -499,19 +549,32 @@ def time_backward(args):
 
     ms_autograd = timed(step, 3)
     el = nk * nq * nm * nb * nb
-    # dominant kernel: k_band_adjoint (stage "band" of the backward call), V_{k+q} (2 c g) V_k^H
-    # with the loss terms: 2 Nb^3 Nm complex multiply-adds per (k,q) pair at 8 flop each
+    # the band stage of the backward call: per (q batch, k tile) two launches of the FP64-accuracy
+    # tensor-core rotation k_band_tc_small64, g = V_{k+q}^H G3 V_k with the loss terms in its
+    # epilogue (2 c g over G3, L per pair), then V_{k+q} (2 c g) V_k^H over the same rows.  Against
+    # HBM: per pair G3 in and 2 c g out, 2 c g in and G3bar out (complex128 rows of Nm Nb^2), V_{k+q}
+    # per pair and V_k per tile in each launch
     band_ms, band_n = prof.get("band", (0.0, 0))
-    cmac = 2.0 * nb ** 3 * nm * nk * nq
-    ach = 8.0 * cmac / (band_ms * 1e-3) if band_ms else None
-    roof = {"bound": "alu", "kernel": "k_band_adjoint (FP64, V_{k+q} (2 c g) V_k^H and the loss terms)",
-            "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_FLOPS if ach else None, "flop_per_cmac": 8, "launches": band_n,
-            "ms_per_launch": band_ms / max(band_n, 1),
-            # G3 rows and V_k, V_{k+q} read, G3bar written (complex128), w and omega
-            "algorithmic_bytes_per_launch": 16.0 * nk * nq * (2 * nm * nb * nb + 2 * nb * nb) / max(band_n, 1),
+    pairs = float(nk) * nq
+    ppt = max(1, min(4, 128 // (((nm * nb + 31) // 32) * 32)))
+    per_pair = 4 * 16.0 * nm * nb * nb + 2 * (16.0 * nb * nb + 16.0 * nb * nb / ppt) + 8.0 * nb
+    ach = per_pair * pairs / (band_ms * 1e-3) if band_ms else None
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    roof = {"bound": "hbm",
+            "kernel": "k_band_tc_small64 (tcgen05 kind::f16, six-digit operands, FP64 accuracy): the rotation with the "
+                      "loss terms, then its adjoint (V conjugate-transposed) in place",
+            "achieved": ach / 1e9 if ach else None, "peak": peak, "unit": "GB/s",
+            "frac": ach / 1e9 / peak if (ach and peak) else None,
+            "launches": band_n, "ms_per_launch": band_ms / max(band_n, 1),
+            "algorithmic_bytes_per_pair": per_pair, "pairs_per_launch_pair": pairs / max(band_n // 2, 1),
+            "cmac_per_pair": 4 * nb ** 3 * nm,
+            "fp64_equivalent_tflops": 8.0 * 4 * nb ** 3 * nm * pairs / (band_ms * 1e-3) / 1e12 if band_ms else None,
             "share_of_call": band_ms / ms_grid if ms_grid else None,
-            "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
+            "note": "issue-bound on the integer digit arithmetic like the forward rotation "
+                    "(profiles/k_band_tc_small64_si_fp64_grid24.md); the FP64 CUDA-core adjoint (band_alu) took "
+                    "206.7 ms per call, 43 % of the FP64 peak",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs, measured" if peak else "unavailable"}
     return {"workload": "mos2_diff: Nb=11 Nm=9 Ne=Np=144, 48x48 k grid x 256 q, FP64 adjoint (forward recomputed)",
             "ms_per_call": ms_grid, "g_elements_per_s": el / (ms_grid * 1e-3), "k_path": "grid (kpts NULL)",
             "stage_ms_per_call": {k: round(v[0], 3) for k, v in prof.items() if v[0] > 0},
@@ -520,11 +583,13 @@ def time_backward(args):
             "autograd_step": {"what": "EphLoss.apply + backward() on CUDA tensors: eph_set_gw (device copy of "
                                       "g(Re,Rp)), eph_interp_backward on the grid, grad scaling",
                               "ms_per_step": ms_autograd, "host_round_trips": 0},
-            "parity": "vs FP64 CPU adjoint <= 1e-12, central differences <= 1e-6 (tests/test_gpu_adjoint.py)"}
+            "parity": "vs FP64 CPU adjoint <= 1e-12, central differences <= 1e-6 (tests/test_gpu_adjoint.py)",
+            # the same loss and gradient by the FP64 oracle on the host cores (same weights)
+            "cpu_baseline": cpu_baseline_adjoint(wl, nq, w_np, 1e-6) if cpu else None}
 
 
 def time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=False):
-    """eph_linewidths (fused consumer, FP64) over the same q points the timed steps cover."""
+    """eph_linewidths (FP64 consumer of g) over the same q points the timed steps cover."""
     import torch
 
     from paper_2603_10295_gb300 import binding
@@ -549,14 +614,16 @@ def time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=False):
     ms = e0.elapsed_time(e1)
     ctx.close()
     return {"what": f"electron linewidths (imaginary Fan-Migdal self-energy, 300 K, Gaussian 0.05 eV) over "
-                    f"{nq} q x {nk} k, g never written to HBM",
+                    f"{nq} q x {nk} k; g formed over the G3 rows of the k-tile workspace by the FP64-accuracy "
+                    "tensor-core rotation and reduced there by k_linewidth_terms, never returned",
             "ms_per_step": ms / args.steps, "g_elements_per_s": nq * nk * nm * nb * nb / (ms * 1e-3),
             "parity": "vs oracle.linewidths <= 1e-10 per k (tests/test_gpu_linewidths.py)"}
 
 
-def time_workload(name, args, dev, legs, warmup, steps):
+def time_workload(name, args, dev, legs, warmup, steps, cpu_k=None):
     """Forward throughput on another of the paper-shaped workloads (device buffers, CUDA events).
-    legs: (form, uniform-grid path, q points per call)."""
+    legs: (form, uniform-grid path, q points per call); cpu_k: the two k sample sizes of the
+    oracle's timing on the same workload (None: no CPU baseline)."""
     import torch
 
     from paper_2603_10295_gb300 import binding, synth
@@ -594,6 +661,8 @@ def time_workload(name, args, dev, legs, warmup, steps):
         del g, e, o
         ctx.close()
         torch.cuda.empty_cache()
+    if cpu_k is not None:
+        out["cpu_baseline"] = cpu_baseline_config(wl, synth.CONFIGS[name]["q"][1], *cpu_k)
     return out
 
 
@@ -1034,13 +1103,17 @@ def run_libeph(args):
             if e2e_mixed is not None:
                 line["mixed"]["e2e"] = e2e_mixed
     single = rank == 0 and world == 1
+    # oracle k samples (small, large) per workload for the per-configuration CPU baselines
+    cpu_k = {"mos2": (1000, 4000), "stanene": (8, 32)} if not args.no_cpu_baseline else {"mos2": None, "stanene": None}
     if single and not args.no_other:
         # the MoS2-shaped (200x200 grid, Nb=11, Nm=9) and stanene-shaped (Nb=120, Nm=180) workloads
         line["other_workloads"] = {
-            "mos2": time_workload("mos2", args, dev, [("fp64", True, QB), ("mixed", True, QB), ("mixed", False, QB)], 2, 5),
+            "mos2": time_workload("mos2", args, dev, [("fp64", True, QB), ("mixed", True, QB), ("mixed", False, QB)], 2, 5,
+                                  cpu_k=cpu_k["mos2"]),
             # FP64: one q per call keeps the Re->k GEMM's k tiles whole waves of 152 rows; the mixed
             # form batches 4 q so that their dynamical-matrix eigensolves run side by side
-            "stanene": time_workload("stanene", args, dev, [("fp64", False, 1), ("mixed", False, 4)], 2, 3)}
+            "stanene": time_workload("stanene", args, dev, [("fp64", False, 1), ("mixed", False, 4)], 2, 3,
+                                     cpu_k=cpu_k["stanene"])}
         line["other_workloads"]["batched_graph"] = {
             "what": "one CUDA graph: stanene-shaped (Nb=120, Nm=180, Ne=Np=15, 512 k) + si_tiny-shaped "
                     "(Nb=8, 1024 k) + MoS2-shaped (Nb=11, 48x48 k grid) contexts, uneven q batches "
@@ -1054,7 +1127,7 @@ def run_libeph(args):
     if single and not args.no_linewidths:
         line["linewidths"] = time_linewidths(wl, args, q_dev, k_dev, dev, QB, use_grid=legs[0][1])
     if single and not args.no_backward:
-        line["backward"] = time_backward(args)
+        line["backward"] = time_backward(args, cpu=not args.no_cpu_baseline)
     if single:
         line["fp64_peak_probe"] = fp64_peak_probe(dev)
     if single and not args.no_cpu_baseline:
