@@ -179,6 +179,8 @@ CAPTURES = {
     "si-fp64-grid": ("si_full", dict(nq=8), "fp64", 4, 2, "grid24"),
     "si-fp64-grid-dfma": ("si_full", dict(nq=8), "fp64", 4, 2, "grid24", dict(band_alu=True)),
     "mos2-diff-backward": ("mos2_diff", dict(nq=8), "fp64", 4, 1, "backward"),
+    # FP64 form on a k list of 16,000 random k with the silicon Re set: the tensor-core Re->k GEMM
+    "si-fp64-list": ("si_full", dict(nk=16000, nq=8), "fp64", 4, 2, "list"),
 }
 
 
@@ -944,6 +946,27 @@ def run_libeph(args):
         # the method's work: 8 flop per complex multiply-add; the kernel (3M) issues 3 DFMA = 6 flop
         ach = 8.0 * cmac_launch / t if t else None
         issued = 6.0 * cmac_launch / t if t else None
+        if 2 * ne <= 512 and nb <= 16 and nm <= 16:
+            # the tensor-core form (k_tc_zgemm64): 34 bf16 digit products per K step on the real
+            # embedding (M = k tile, N = 2 NW per q, K = 2 Ne padded to 32); digits read once, Y
+            # written once in complex128
+            kp = ((2 * ne + 31) // 32) * 32
+            iss = 34 * 2.0 * nkt * 2 * NW * kp * QB
+            peak = peaks.get("bf16_tflops")
+            useful = ach / 1e12 if ach else None
+            return {"bound": "tensor",
+                    "kernel": "k_tc_zgemm64 (Re->k contraction fused with H(k+q) at FP64 accuracy: tcgen05 kind::f16, "
+                              "seven base-128 digits per operand, exact level sums, integer-assembled doubles)",
+                    "achieved": useful, "peak": peak, "unit": "TFLOP/s",
+                    "frac": useful / peak if (useful and peak) else None, "flop_per_cmac": 8,
+                    "achieved_issued": iss / t / 1e12 if t else None,
+                    "frac_issued": iss / t / 1e12 / peak if (t and peak) else None,
+                    "note": "frac: the complex contraction at 8 flop per complex multiply-add; frac_issued: the 34 "
+                            "digit products per K step the kernel issues; the FP64 DFMA GEMM (option gemm_alu) ran "
+                            "this stage at 94 % of the FP64 peak in 123 ms per step",
+                    "algorithmic_bytes": 2.0 * 7 * (nkt * kp + QB * 2 * NW * kp) + 16.0 * QB * nkt * NW,
+                    "traffic": TRAFFIC.get(("k_tc_zgemm64", args.workload, QB)),
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), measured" if peak else "unavailable"}
         return {"bound": "alu", "kernel": "k_zgemm (Re->k contraction fused with H(k+q), FP64 DFMA, 3M)",
                 "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": (ach / FP64_PEAK_FLOPS) if ach else None, "flop_per_cmac": 8,

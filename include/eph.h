@@ -47,7 +47,12 @@ enum eph_status {
 };
 
 enum eph_form {
-  EPH_FORM_FP64 = 0,  /* every contraction in FP64 (DFMA) */
+  EPH_FORM_FP64 = 0,  /* every result to FP64 accuracy: FP64 DFMA, except the band rotation
+                         (nb <= 16, nm*nb <= 128) and, on k lists, the Re->k contraction with
+                         H(k+q) (2 ne <= 512, nb, nm <= 16), which run on the tensor cores from
+                         six- or seven-digit fixed-point BF16 operands with exact level sums and
+                         integer-assembled doubles (~1e-13 of each pair's or column's largest
+                         term; options band_alu and gemm_alu select DFMA) */
   EPH_FORM_MIXED = 1  /* split precision on the large contractions, g as complex64: on k lists the
                          Re->k contraction of g and H(k+q) are tcgen05 tensor-core products of
                          fixed-point BF16 digits with FP32 accumulation; the Rp->q contraction
@@ -89,6 +94,12 @@ typedef struct eph_options {
                          form).  The same switch applies to the FP64 band products of
                          eph_interp_backward, eph_interp_vjp, eph_bloch_to_wannier and
                          eph_linewidths (six-digit tensor-core products, or FP64 DFMA) */
+  int gemm_alu;       /* the Re->k contraction of Eq. 10 on a k list in FP64 (the FP64 form's k-list
+                         path and every FP64 chain): 0 (default) = on the tensor cores, seven
+                         balanced base-128 digits per operand (power-of-two scale per phase row and
+                         per W_q column), exact level sums, doubles assembled from 64-bit integers
+                         (~1e-14 of each column's largest term; needs 2 ne <= 512, nb, nm <= 16);
+                         1 = FP64 DFMA GEMM */
 } eph_options;
 
 /* Fills *opt with the defaults (FP64 form, host pointers, automatic batching). */

@@ -35,7 +35,8 @@ class EphOptions(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("device_ptrs", ctypes.c_int), ("q_batch", ctypes.c_int),
                 ("k_tile", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("workspace_mb", ctypes.c_int),
                 ("mixed_scheme", ctypes.c_int), ("eig_plain_fp64", ctypes.c_int), ("async_", ctypes.c_int),
-                ("band_alu", ctypes.c_int)]
+                ("band_alu", ctypes.c_int),
+                ("gemm_alu", ctypes.c_int)]
 
 
 class EphError(RuntimeError):
@@ -168,7 +169,7 @@ class Context:
     def __init__(self, nb, na, H_Re, Phi_Rp, g_ReRp, Re, Rp, masses, we=None, wp=None, form="fp64",
                  device_ptrs=False, q_batch=0, k_tile=0, max_sweeps=0, workspace_mb=0, stream=None,
                  mixed_scheme="digits", eig_plain_fp64=False, async_mode=False, rp_slice=None,
-                 band_alu=False):
+                 band_alu=False, gemm_alu=False):
         """rp_slice = (rp_begin, rp_count): g_ReRp holds only those Rp rows (eph_create_rp_slice)."""
         self.lib = load_library()
         self.nb, self.na, self.nm = int(nb), int(na), 3 * int(na)
@@ -193,6 +194,7 @@ class Context:
         opt.eig_plain_fp64 = int(bool(eig_plain_fp64))
         opt.async_ = int(bool(async_mode))
         opt.band_alu = int(bool(band_alu))
+        opt.gemm_alu = int(bool(gemm_alu))
         handle = ctypes.c_void_p()
         st = None
         if stream is not None:

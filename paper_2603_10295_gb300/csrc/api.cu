@@ -138,6 +138,9 @@ struct eph_ctx {
   DBuf g_stage2, est[2], ost[2];
   DBuf Pacc;  // adjoint: phase rows of the q batches whose G1bar rows await the gradient GEMM
   DBuf UkH;   // adjoint of large shapes: V_k^H of the k tile
+  // FP64 k list on the tensor cores: digit planes of the phases (per k list) and of W_q (per q batch)
+  DBuf zA, zAe, zB, zBe;
+  bool zA_ready = false;
   cudaEvent_t set_done[2] = {};
   bool set_pending[2] = {false, false};
   int stage_set = 0;
@@ -377,7 +380,7 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
                   &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair, &ctx->g1in,
                   &ctx->aS2, &ctx->aS1, &ctx->aS0, &ctx->DG, &ctx->sG, &ctx->DP, &ctx->G1f, &ctx->g_stage2,
-                  &ctx->est[0], &ctx->est[1], &ctx->ost[0], &ctx->ost[1], &ctx->Pacc, &ctx->UkH};
+                  &ctx->est[0], &ctx->est[1], &ctx->ost[0], &ctx->ost[1], &ctx->Pacc, &ctx->UkH, &ctx->zA, &ctx->zAe, &ctx->zB, &ctx->zBe};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -650,6 +653,7 @@ extern "C" int eph_set_k(eph_ctx* ctx, int nk, const double* kpts, double* eps_k
   if (!ctx) return EPH_EINVAL;
   if (nk < 1 || !kpts) return fail(ctx, EPH_EINVAL, "eph_set_k: nk < 1 or kpts NULL");
   ctx->k_ready = false;
+  ctx->zA_ready = false;  // the phases change with the k list
   ctx->has_grid = false;
   const void* dk = nullptr;
   EPH_TRY(stage_in(ctx, ctx->kpts, kpts, (size_t)nk * 3 * sizeof(double), &dk));
@@ -665,6 +669,7 @@ extern "C" int eph_set_k_grid(eph_ctx* ctx, int n1, int n2, int n3, const double
   if (n1 < 1 || n2 < 1 || n3 < 1 || (long)n1 * n2 * n3 > 2147483647L)
     return fail(ctx, EPH_EINVAL, "eph_set_k_grid: bad grid size");
   ctx->k_ready = false;
+  ctx->zA_ready = false;  // the phases change with the k list
   ctx->has_grid = false;
   const double s[3] = {shift ? shift[0] : 0.0, shift ? shift[1] : 0.0, shift ? shift[2] : 0.0};
   const int nk = n1 * n2 * n3;
@@ -701,6 +706,7 @@ extern "C" int eph_set_k_window(eph_ctx* ctx, int nk, const double* kpts, double
   // pass 1: the band energies of every k of the list
   EPH_TRY(eph_set_k(ctx, nk, kpts, nullptr));
   ctx->k_ready = false;
+  ctx->zA_ready = false;  // the phases change with the k list
   const int nb = ctx->nb;
   const long nblk = ((long)nk + 1023) / 1024;
   EPH_TRY(ensure(ctx, ctx->scr_flag, (size_t)nk * sizeof(int)));
@@ -747,6 +753,7 @@ extern "C" int eph_set_k_grid_ibz(eph_ctx* ctx, int n1, int n2, int n3, const do
   }
   *nk_kept = 0;
   ctx->k_ready = false;
+  ctx->zA_ready = false;  // the phases change with the k list
   ctx->has_grid = false;
   const long nk = (long)n1 * n2 * n3;
   const long nblk = (nk + 1023) / 1024;
@@ -791,6 +798,7 @@ extern "C" int eph_set_k_grid_ibz(eph_ctx* ctx, int n1, int n2, int n3, const do
 namespace {
 // H(k), its eigenpairs and the k-side operands for the k list already in ctx->kpts.
 int set_k_resident(eph_ctx* ctx, int nk, double* eps_k) {
+  ctx->zA_ready = false;
   const int nb = ctx->nb, ne = ctx->ne, nb2 = nb * nb;
   EPH_TRY(ensure(ctx, ctx->Pk, (size_t)nk * ne * sizeof(double2)));
   EPH_TRY(ensure(ctx, ctx->eps_k, (size_t)nk * nb * sizeof(double)));
@@ -1079,6 +1087,35 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
 }
 
 // Per (q batch, k tile): Y = P_k W_q (H(k+q) | G3), then the H(k+q) eigensolves.
+// The Re->k contraction of a k list on the tensor cores at FP64 accuracy (seven-digit operands).
+bool use_tc_rek(const eph_ctx* ctx) {
+  return !ctx->opt.gemm_alu && !ctx->big && !ctx->has_grid && 2 * ctx->ne <= 512;
+}
+
+// Y[q][k] = P_k W_q for one (q batch, k tile): the phases' digits once per k list, W_q's at the
+// first tile of a q batch (every caller starts a batch at k0 = 0, right after its q prelude).
+int tc_rek_tile(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
+  const int ne = ctx->ne, Kp = (2 * ne + 31) / 32 * 32;
+  const long nk = ctx->nk, N = 2 * p.NW;
+  if (!ctx->zA_ready) {
+    EPH_TRY(ensure(ctx, ctx->zA, (size_t)7 * nk * Kp * 2));
+    EPH_TRY(ensure(ctx, ctx->zAe, (size_t)nk * sizeof(int)));
+    EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_zdigits_rows(as<double2>(ctx->Pk), ne, (int)nk, ne, Kp, as<int>(ctx->zAe),
+                                                           ctx->zA.p, ctx->stream));
+    ctx->zA_ready = true;
+  }
+  if (k0 == 0) {
+    EPH_TRY(ensure(ctx, ctx->zB, (size_t)7 * p.QB * N * Kp * 2));
+    EPH_TRY(ensure(ctx, ctx->zBe, (size_t)p.QB * N * sizeof(int)));
+    EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_zdigits_cols(as<double2>(ctx->W), p.NW, (long)ne * p.NW, nqb, ne, (int)p.NW,
+                                                          Kp, as<int>(ctx->zBe), ctx->zB.p, ctx->stream));
+  }
+  EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_tc_zgemm64(ctx->zA.p, nk, (int)k0, nkt, as<int>(ctx->zAe), ctx->zB.p,
+                                                      (int)(nqb * N), as<int>(ctx->zBe), Kp, as<double2>(ctx->Y),
+                                                      (int)N, p.NW, (long)nkt * p.NW, ctx->status + 1, ctx->stream));
+  return EPH_OK;
+}
+
 int k_tile_forward(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
   const int nb = ctx->nb, ne = ctx->ne, nb2 = nb * nb;
   double2* Y = as<double2>(ctx->Y);
@@ -1090,6 +1127,8 @@ int k_tile_forward(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
     EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_axis_dft(as<double2>(ctx->S2), (long)B1 * C, nqb, C, B1,
                                                       as<double2>(ctx->E1), N1, j0, nj, paired, Y,
                                                       (long)nkt * p.NW, ctx->stream));
+  } else if (use_tc_rek(ctx)) {
+    EPH_TRY(tc_rek_tile(ctx, p, nqb, k0, nkt));
   } else {
     EPH_LAUNCH_S(EPH_STAGE_FT_K, launch_zgemm(nkt, (int)p.NW, ne, as<double2>(ctx->Pk) + k0 * ne, ne, 0,
                                               as<double2>(ctx->W), p.NW, (long)ne * p.NW, Y, p.NW, (long)nkt * p.NW,

@@ -260,6 +260,21 @@ cudaError_t launch_band_tc_small64_ex(const double2* X, long xq, long xk, const 
                                       int nk, int nm, int nb, double2* out, long oq, long ok, const int* keep, bool adj,
                                       const double* wk, const double* om, double omega_min, double* Lpair, int* err,
                                       cudaStream_t st);
+// FP64-accuracy complex GEMM on the tensor cores (seven base-128 digits per operand, exact level
+// sums, doubles assembled from 64-bit integers): digit planes [7][rows][Kp] (bf16) of a complex
+// row-major P[rows][ne] (K = (e, re/im), Kp a multiple of 32, 2 ne <= Kp), with the largest biased
+// exponent of each row in ea; of the columns of W[q][e][c] (nq x ncol columns) as 2 ncol rows per q
+// (Re / Im of the product), with the column exponents in eb (per row).
+cudaError_t launch_zdigits_rows(const double2* P, long ldp, int rows, int ne, int Kp, int* ea, void* planes,
+                                cudaStream_t st);
+cudaError_t launch_zdigits_cols(const double2* W, long ldw, long sW, int nq, int ne, int ncol, int Kp, int* eb,
+                                void* planes, cudaStream_t st);
+// C[q][row][c] = sum_e P[a_row0 + row][e] W[q][e][c] for rows < M and the N = nq ncq real columns
+// (ncq = 2 ncol per q; C complex128, row stride ldc, q stride sCq); Kp <= 512.  *err |= 1..8 on a
+// barrier timeout.
+cudaError_t launch_tc_zgemm64(const void* a_planes, long a_rows, int a_row0, int M, const int* ea, const void* b_planes,
+                              int N, const int* eb, int Kp, double2* C, int ncq, long ldc, long sCq, int* err,
+                              cudaStream_t st);
 cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const double2* Ukq, const double2* Uk, int nq,
                            int nk, int nm, int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err,
                            cudaStream_t st);

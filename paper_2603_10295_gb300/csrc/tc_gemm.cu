@@ -953,6 +953,374 @@ __global__ void __launch_bounds__(tcb::THREADS, 1) k_tc_band_gemm(const __grid_c
   }
 }
 
+// ----------------------------------------------------------------------------- FP64-accuracy complex GEMM
+// C = A B^T on the real embedding of a complex product (the Re->k contraction of Eq. 10 on a k
+// list in the FP64 form): A rows m with K = (e, re/im), B rows n = the output's real columns with
+// the same K.  Every operand value x is seven balanced base-128 digits of x / s, with s =
+// 2^(emax - 1021) a power of two per A row and per B row (emax >= the biased exponent of every
+// value of the row, so |x / s| < 1/2):
+//   x / s = sum_{i<7} d_i 2^-7(i+1),  |d_i| <= 64,  stored as d_i 2^-7i (exact in bf16).
+// The digit products of levels l = i + j <= 7 (34 MMAs per K step) go to six accumulators: levels
+// 0-4 each alone, where the sum is n_l 2^-7l with an integer |n_l| <= K 5 2^12 < 2^24 for K <= 512
+// (exact in FP32), levels 5-7 together.  That sum is 2^-35 below level 0 and takes 19 MMAs per K
+// step, each rounding it in FP32: ~K 2^-24 of it, 2^-50 of the result (with levels 4-7 together,
+// 2^-28 below level 0, the same roundings measured ~1e-12).  The dropped levels >= 8 are below
+// 2^-53 of the result.  The epilogue forms the integer Z = sum_l n_l 2^7(6-l) (units of
+// 2^-56 s_A s_B; |Z| < K 2^54 <= 2^63 for K <= 512) and assembles the double from Z with integer
+// operations, rounded to nearest.  One accumulator set of 6 x 80 TMEM columns: the next tile's
+// MMAs wait for the epilogue.
+namespace tz {
+constexpr int BM = 128, BN = 80, BK = 32, STAGES = 2, ND = 7, NACC = 6;
+constexpr int A_T = BM * BK * 2;                   // 8 KiB per digit tile
+constexpr int B_T = BN * BK * 2;                   // 5 KiB loaded per B digit tile ...
+constexpr int B_SLOT = 8192;                       // ... in an 8 KiB slot (every tile 1 KiB aligned)
+constexpr int STAGE_BYTES = ND * (A_T + B_SLOT);   // 112 KiB
+constexpr int TX_BYTES = ND * (A_T + B_T);         // 91 KiB delivered per stage
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;  // 225.25 KiB
+constexpr uint32_t TMEM_COLS = 512;                // accumulators at columns 0, 80, ..., 400
+constexpr int THREADS = 192;
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+// x + OFF7 makes all seven base-128 fields of a value |X| <= 2^48 non-negative: OFF7 = 64 sum 128^i
+constexpr long long OFF7 = 64LL * (((1LL << 49) - 1) / 127);
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+
+// the integer nearest to v (finite, |v| < 2^62), from the IEEE bits
+__device__ __forceinline__ long long f2ll(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const int be = (int)((b >> 23) & 0xFF);
+  if (be == 0) return 0;
+  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+  const int e = be - 150;  // v = m 2^e
+  long long r = 0;
+  if (e >= 0)
+    r = m << e;
+  else if (e > -25)
+    r = (m + (1LL << (-e - 1))) >> (-e);
+  return (b >> 31) ? -r : r;
+}
+
+// Z 2^E as a double rounded to nearest (|Z| < 2^63), from integer operations
+__device__ __forceinline__ double ll2d(long long Z, int E) {
+  if (Z == 0) return 0.0;
+  const unsigned long long sgn = Z < 0 ? (1ULL << 63) : 0ULL;
+  const unsigned long long M = Z < 0 ? 0ULL - (unsigned long long)Z : (unsigned long long)Z;
+  const int lz = __clzll((long long)M);
+  const unsigned long long N = M << lz;  // leading one at bit 63
+  unsigned long long r = N + 0x400ULL;   // round at bit 11: 53 significant bits remain
+  int ex = 63 - lz + E;                  // exponent of the leading bit
+  if (r < N) {                           // the rounding carried out of bit 63
+    r = 1ULL << 63;
+    ++ex;
+  }
+  const long long be = (long long)ex + 1023;
+  if (be <= 0) return 0.0;  // below the normal range
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | ((r >> 11) & 0xFFFFFFFFFFFFFULL)));
+}
+
+// Z from the six level sums (levels 0-4 exact integers times 2^-7l, levels 5-7 rounded)
+__device__ __forceinline__ long long combine(uint32_t l0, uint32_t l1, uint32_t l2, uint32_t l3, uint32_t l4,
+                                             uint32_t l5) {
+  unsigned long long z = (unsigned long long)f2ll(__uint_as_float(l0)) << 42;
+  z += (unsigned long long)f2ll(__uint_as_float(l1) * 0x1p7f) << 35;
+  z += (unsigned long long)f2ll(__uint_as_float(l2) * 0x1p14f) << 28;
+  z += (unsigned long long)f2ll(__uint_as_float(l3) * 0x1p21f) << 21;
+  z += (unsigned long long)f2ll(__uint_as_float(l4) * 0x1p28f) << 14;
+  z += (unsigned long long)f2ll(__uint_as_float(l5) * 0x1p42f);
+  return (long long)z;
+}
+
+__device__ __forceinline__ int dexp(double x) { return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// the seven digits of x relative to 2^(emax - 1021) (emax >= its biased exponent), as bf16 bits
+__device__ __forceinline__ void digits7(double x, int emax, uint32_t (&h)[ND]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  long long X = 0;  // round(x / 2^(emax - 1021) * 2^49), |X| <= 2^48
+  if (e != 0) {
+    const long long m = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+    const int sh = emax + 5 - e;  // >= 5
+    X = sh < 54 ? (m + (1LL << (sh - 1))) >> sh : 0LL;
+    if (b >> 63) X = -X;
+  }
+  const unsigned long long Y = (unsigned long long)(X + OFF7);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    const uint32_t f = i == 0 ? (uint32_t)(Y >> 42) : (uint32_t)((Y >> (7 * (ND - 1 - i))) & 127u);
+    // (f - 64) 2^-7i: exact FP32 arithmetic from the bits of 2^23 + f; its bf16 is the top half
+    const float v = (__uint_as_float(0x4B000000u | f) - 8388672.0f) * __uint_as_float((uint32_t)(127 - 7 * i) << 23);
+    h[i] = __float_as_uint(v) >> 16;
+  }
+}
+}  // namespace tz
+
+struct TzMaps {
+  CUtensorMap a[tz::ND];
+  CUtensorMap b[tz::ND];
+};
+
+// A planes [7][rows][Kp] of P (row stride ldp, ne complex values per row): K = (e, re/im).
+// ea[row] = the largest biased exponent of the row.
+__global__ void k_zdig_rows_exp(const double2* __restrict__ P, long ldp, int rows, int ne, int* __restrict__ ea) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  int m = 0;
+  for (int e = 0; e < ne; ++e) {
+    const double2 z = P[(long)r * ldp + e];
+    m = max(m, max(tz::dexp(z.x), tz::dexp(z.y)));
+  }
+  ea[r] = m;
+}
+
+__global__ void k_zdig_rows(const double2* __restrict__ P, long ldp, int rows, int ne, int Kp,
+                            const int* __restrict__ ea, uint32_t* __restrict__ planes, long plane_words) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int half = Kp / 2;
+  if (t >= (long)rows * half) return;
+  const int r = (int)(t / half), e = (int)(t - (long)r * half);
+  uint32_t hr[tz::ND], hi[tz::ND];
+  if (e < ne) {
+    const double2 z = P[(long)r * ldp + e];
+    tz::digits7(z.x, ea[r], hr);
+    tz::digits7(z.y, ea[r], hi);
+  } else {
+#pragma unroll
+    for (int d = 0; d < tz::ND; ++d) hr[d] = hi[d] = 0u;
+  }
+#pragma unroll
+  for (int d = 0; d < tz::ND; ++d) planes[d * plane_words + t] = hr[d] | (hi[d] << 16);
+}
+
+// B planes [7][nq ncq][Kp] of W[q][e][c] (complex, row stride ldw, q stride sW, ncq / 2 columns):
+// row 2c holds (Re W, -Im W) and row 2c + 1 (Im W, Re W) along K = (e, re/im), so that A B^T gives
+// Re and Im of P W.  eb[row] = the largest biased exponent of the column (both rows).
+__global__ void k_zdig_cols_exp(const double2* __restrict__ W, long ldw, long sW, int nq, int ne, int ncol,
+                                int* __restrict__ eb) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)nq * ncol) return;
+  const int q = (int)(t / ncol), c = (int)(t - (long)q * ncol);
+  int m = 0;
+  for (int e = 0; e < ne; ++e) {
+    const double2 z = W[(long)q * sW + (long)e * ldw + c];
+    m = max(m, max(tz::dexp(z.x), tz::dexp(z.y)));
+  }
+  eb[2 * t] = m;
+  eb[2 * t + 1] = m;
+}
+
+__global__ void k_zdig_cols(const double2* __restrict__ W, long ldw, long sW, int nq, int ne, int ncol, int Kp,
+                            const int* __restrict__ eb, uint32_t* __restrict__ planes, long plane_words) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;  // (q, c, e), e fastest
+  const int half = Kp / 2;
+  if (t >= (long)nq * ncol * half) return;
+  const long qc = t / half;
+  const int e = (int)(t - qc * half);
+  const int q = (int)(qc / ncol), c = (int)(qc - (long)q * ncol);
+  uint32_t hr[tz::ND], hi[tz::ND];
+  if (e < ne) {
+    const double2 z = W[(long)q * sW + (long)e * ldw + c];
+    const int em = eb[2 * qc];
+    tz::digits7(z.x, em, hr);
+    tz::digits7(z.y, em, hi);
+  } else {
+#pragma unroll
+    for (int d = 0; d < tz::ND; ++d) hr[d] = hi[d] = 0u;
+  }
+  const long w0 = (2 * qc) * half + e, w1 = (2 * qc + 1) * half + e;  // words of rows 2c and 2c + 1
+#pragma unroll
+  for (int d = 0; d < tz::ND; ++d) {
+    const uint32_t nhi = hi[d] ? hi[d] ^ 0x8000u : 0u;  // the digits of -Im W
+    planes[d * plane_words + w0] = hr[d] | (nhi << 16);
+    planes[d * plane_words + w1] = hi[d] | (hr[d] << 16);
+  }
+}
+
+// C[q][row][c] (complex128; q = n / ncq, c = (n mod ncq) / 2 for the real column n) from the A rows
+// a_row0 .. a_row0 + M - 1 and the N B rows; tiles 128 x 80, n tiles fastest (the CTAs on one A row
+// tile run together and share it through L2).  Bounded waits: on a timeout *err is set and the
+// CTA stops, drains what it issued and frees its TMEM.
+__global__ void __launch_bounds__(tz::THREADS, 1) k_tc_zgemm64(const __grid_constant__ TzMaps maps, int M, int a_row0,
+                                                              int N, int Kp, const int* __restrict__ ea,
+                                                              const int* __restrict__ eb, double2* __restrict__ C,
+                                                              int ncq, long ldc, long sCq, int* __restrict__ err) {
+  using namespace tc;
+  using tz::BK;
+  using tz::BM;
+  using tz::BN;
+  using tz::ND;
+  using tz::STAGES;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * tz::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;  // the accumulators hold a finished tile
+  uint64_t* acce = accf + 1;        // the accumulators have been drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkb = Kp / BK;
+  const int ntn = (N + BN - 1) / BN, ntm = (M + BM - 1) / BM;
+  const long ntiles = (long)ntn * ntm;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 4);  // one arrival per epilogue warp
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tz::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto atile = [&](int s, int d) -> unsigned char* { return smem + s * tz::STAGE_BYTES + d * tz::A_T; };
+  auto btile = [&](int s, int d) -> unsigned char* { return smem + s * tz::STAGE_BYTES + ND * tz::A_T + d * tz::B_SLOT; };
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- TMA producer
+      long it = 0;
+      for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        const int m0 = (int)(t / ntn) * BM, n0 = (int)(t % ntn) * BN;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1))) {
+            *abort_flag = 1;
+            atomicOr(err, 1);
+            break;
+          }
+          if (*abort_flag) break;
+          mbar_arrive_expect_tx(&full[s], tz::TX_BYTES);
+#pragma unroll
+          for (int d = 0; d < ND; ++d) tma_load_2d(atile(s, d), &maps.a[d], kb * BK, a_row0 + m0, &full[s]);
+#pragma unroll
+          for (int d = 0; d < ND; ++d) tma_load_2d(btile(s, d), &maps.b[d], kb * BK, n0, &full[s]);
+        }
+      }
+      // after an abort: wait (bounded) for the loads still in flight
+      if (*abort_flag)
+        for (long j = (it > STAGES ? it - STAGES : 0); j < it; ++j) mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      long it = 0, lt = 0;
+      for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++lt) {
+        if (lt >= 1 && !mbar_wait(acce, (uint32_t)((lt - 1) & 1))) {
+          *abort_flag = 1;
+          atomicOr(err, 8);
+          break;
+        }
+        fence_after();
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (*abort_flag || !mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1))) {
+            *abort_flag = 1;
+            atomicOr(err, 2);
+            ok = false;
+            break;
+          }
+          fence_after();
+          uint64_t da[ND], db[ND];
+#pragma unroll
+          for (int d = 0; d < ND; ++d) {
+            da[d] = tch::smem_desc64(smem_u32(atile(s, d)));
+            db[d] = tch::smem_desc64(smem_u32(btile(s, d)));
+          }
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K
+            const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+#pragma unroll
+            for (int l = 0; l <= 7; ++l) {
+              const uint32_t dst = tmem + (uint32_t)((l < 5 ? l : 5) * BN);
+#pragma unroll
+              for (int i = (l > ND - 1 ? l - (ND - 1) : 0); i <= (l < ND - 1 ? l : ND - 1); ++i) {
+                const bool first = (l < 5) ? (i == 0) : (l == 5 && i == 0);
+                tz::mma(dst, da[i] + o, db[l - i] + o, first ? acc : 1u);
+              }
+            }
+          }
+          mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+        }
+        mma_commit(accf);  // the tile's accumulators are complete (or the loop was aborted)
+        if (!ok) break;
+      }
+    }
+    __syncwarp();
+  } else {  // ---- epilogue, warps 2..5: TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    long lt = 0;
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const bool ok = mbar_wait(accf, (uint32_t)(lt & 1));
+      if (!ok || *abort_flag) {
+        if (!ok) atomicOr(err, 4);
+        break;
+      }
+      fence_after();
+      const int m0 = (int)(t / ntn) * BM, n0 = (int)(t % ntn) * BN;
+      const int row = m0 + quarter * 32 + lane;
+      const bool live = row < M;
+      const int erow = live ? ea[a_row0 + row] - 1021 - 56 : 0;
+      const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r0[16], r1[16], r2[16], r3[16], r4[16], r5[16];
+        tmem_ld16(tl + c0, r0);
+        tmem_ld16(tl + BN + c0, r1);
+        tmem_ld16(tl + 2 * BN + c0, r2);
+        tmem_ld16(tl + 3 * BN + c0, r3);
+        tmem_ld16(tl + 4 * BN + c0, r4);
+        tmem_ld16(tl + 5 * BN + c0, r5);
+        tmem_ld_wait();
+        if (live) {
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+            const int n = n0 + c0 + i;  // even; N is even, so n + 1 < N with n
+            if (n < N) {
+              const int q = n / ncq, c = (n - q * ncq) >> 1;
+              const int E = erow + eb[n] - 1021;
+              const double re = tz::ll2d(tz::combine(r0[i], r1[i], r2[i], r3[i], r4[i], r5[i]), E);
+              const double im =
+                  tz::ll2d(tz::combine(r0[i + 1], r1[i + 1], r2[i + 1], r3[i + 1], r4[i + 1], r5[i + 1]), E);
+              C[(long)q * sCq + (long)row * ldc + c] = make_double2(re, im);
+            }
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) tcf::mbar_arrive(acce);
+    }
+  }
+  // drain: after an abort the producer waits (bounded) for its last loads (above); every warp
+  // then meets here before the TMEM is released
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tz::TMEM_COLS) : "memory");
+  }
+}
+
 // ----------------------------------------------------------------------------- host side
 namespace {
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -1100,6 +1468,63 @@ cudaError_t launch_tc_split_gemm(const void* mAhi, const void* mAlo, const void*
                                                      *static_cast<const CUtensorMap*>(mBhi),
                                                      *static_cast<const CUtensorMap*>(mBlo), M, a_row0, Nr, Kp, C,
                                                      ldc, sC, err);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------- FP64-accuracy complex GEMM, host
+cudaError_t launch_zdigits_rows(const double2* P, long ldp, int rows, int ne, int Kp, int* ea, void* planes,
+                                cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  if (Kp % tz::BK != 0 || 2 * ne > Kp) return cudaErrorInvalidValue;
+  k_zdig_rows_exp<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, ldp, rows, ne, ea);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long words = (long)rows * (Kp / 2);
+  k_zdig_rows<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(P, ldp, rows, ne, Kp, ea, static_cast<uint32_t*>(planes),
+                                                               words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zdigits_cols(const double2* W, long ldw, long sW, int nq, int ne, int ncol, int Kp, int* eb,
+                                void* planes, cudaStream_t st) {
+  if (nq <= 0 || ncol <= 0) return cudaSuccess;
+  if (Kp % tz::BK != 0 || 2 * ne > Kp) return cudaErrorInvalidValue;
+  const long cols = (long)nq * ncol;
+  k_zdig_cols_exp<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(W, ldw, sW, nq, ne, ncol, eb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long words = cols * (Kp / 2);
+  k_zdig_cols<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(W, ldw, sW, nq, ne, ncol, Kp, eb,
+                                                               static_cast<uint32_t*>(planes), 2 * words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_zgemm64(const void* a_planes, long a_rows, int a_row0, int M, const int* ea, const void* b_planes,
+                              int N, const int* eb, int Kp, double2* C, int ncq, long ldc, long sCq, int* err,
+                              cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  // exact sums of levels 0-4 and the int64 combination need K <= 512
+  if (Kp % tz::BK != 0 || Kp <= 0 || Kp > 512 || (N & 1) || (ncq & 1) || ncq <= 0) return cudaErrorInvalidValue;
+  if (a_row0 < 0 || a_row0 + (long)M > a_rows) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(C) & 15) != 0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_zgemm64, cudaFuncAttributeMaxDynamicSharedMemorySize, tz::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorInvalidDevice;
+  TzMaps maps;
+  const size_t aplane = (size_t)a_rows * Kp * 2, bplane = (size_t)N * Kp * 2;
+  for (int d = 0; d < tz::ND; ++d) {
+    if ((e = make_tc_map_bf16_sw64(&maps.a[d], static_cast<const char*>(a_planes) + d * aplane, a_rows, Kp, tz::BM)) !=
+        cudaSuccess)
+      return e;
+    if ((e = make_tc_map_bf16_sw64(&maps.b[d], static_cast<const char*>(b_planes) + d * bplane, N, Kp, tz::BN)) !=
+        cudaSuccess)
+      return e;
+  }
+  const long ntiles = (long)((N + tz::BN - 1) / tz::BN) * ((M + tz::BM - 1) / tz::BM);
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  k_tc_zgemm64<<<grid, tz::THREADS, tz::SMEM_BYTES, st>>>(maps, M, a_row0, N, Kp, ea, eb, C, ncq, ldc, sCq, err);
   return cudaGetLastError();
 }
 
