@@ -50,7 +50,10 @@ EIG_FP64_FLOPS = {(8, "fp64"): (2 * 1769472000 + 59392000 + 548864000) / 256000,
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at one step = 4 q x 64,000 k
 TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
            ("k_zgemm", "si_full", 4): 242432512.0 + 1777470464.0,
-           ("k_band_rotate", "si_full", 4): 2097285888.0 + 1534482688.0}
+           ("k_band_rotate", "si_full", 4): 2097285888.0 + 1534482688.0,
+           # the 16,000-k capture (bench.py --capture si-fp64-list) scaled to the 64,000-k launch: the
+           # phase digits and Y, which dominate, grow with the k rows (B digits, 22 MB, do not)
+           ("k_tc_zgemm64", "si_full", 4): 4.0 * (137323520.0 + 412080128.0)}
 # DRAM bytes per unit (pair or matrix) of the current kernels from the 24^3-grid captures
 # (bench.py --capture si-fp64-grid / si-mixed-grid, 55,296 pairs per launch), scaled to a launch
 # by its units: these kernels stream their inputs once, so traffic grows in proportion

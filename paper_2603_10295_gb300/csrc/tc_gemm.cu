@@ -968,7 +968,8 @@ __global__ void __launch_bounds__(tcb::THREADS, 1) k_tc_band_gemm(const __grid_c
 // 2^-53 of the result.  The epilogue forms the integer Z = sum_l n_l 2^7(6-l) (units of
 // 2^-56 s_A s_B; |Z| < K 2^54 <= 2^63 for K <= 512) and assembles the double from Z with integer
 // operations, rounded to nearest.  One accumulator set of 6 x 80 TMEM columns: the next tile's
-// MMAs wait for the epilogue.
+// MMAs wait for the epilogue, which twelve warps share (three per TMEM lane quarter) so that its
+// dependent integer chains overlap.
 namespace tz {
 constexpr int BM = 128, BN = 80, BK = 32, STAGES = 2, ND = 7, NACC = 6;
 constexpr int A_T = BM * BK * 2;                   // 8 KiB per digit tile
@@ -976,9 +977,11 @@ constexpr int B_T = BN * BK * 2;                   // 5 KiB loaded per B digit t
 constexpr int B_SLOT = 8192;                       // ... in an 8 KiB slot (every tile 1 KiB aligned)
 constexpr int STAGE_BYTES = ND * (A_T + B_SLOT);   // 112 KiB
 constexpr int TX_BYTES = ND * (A_T + B_T);         // 91 KiB delivered per stage
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;  // 225.25 KiB
+constexpr int META_BYTES = BN * 12;               // per tile: column offsets (8 B) and exponents (4 B)
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + META_BYTES;  // 226.2 KiB
 constexpr uint32_t TMEM_COLS = 512;                // accumulators at columns 0, 80, ..., 400
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 12;                      // three per TMEM lane quarter, every third 16-column chunk
+constexpr int THREADS = 64 + 32 * EPI_WARPS;       // producer, MMA issuer, epilogue
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 // x + OFF7 makes all seven base-128 fields of a value |X| <= 2^48 non-negative: OFF7 = 64 sum 128^i
@@ -1025,14 +1028,23 @@ __device__ __forceinline__ double ll2d(long long Z, int E) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | ((r >> 11) & 0xFFFFFFFFFFFFFULL)));
 }
 
+// the integer v (|v| < 2^24, an exact integer in FP32), from the IEEE bits in 32-bit operations
+__device__ __forceinline__ int f2i24(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
+  const int sh = 150 - (int)((b >> 23) & 0xFFu);  // 0 .. 150; >= 24 only for v = 0
+  const int r = sh < 24 ? (int)(m >> sh) : 0;
+  return (int)b < 0 ? -r : r;
+}
+
 // Z from the six level sums (levels 0-4 exact integers times 2^-7l, levels 5-7 rounded)
 __device__ __forceinline__ long long combine(uint32_t l0, uint32_t l1, uint32_t l2, uint32_t l3, uint32_t l4,
                                              uint32_t l5) {
-  unsigned long long z = (unsigned long long)f2ll(__uint_as_float(l0)) << 42;
-  z += (unsigned long long)f2ll(__uint_as_float(l1) * 0x1p7f) << 35;
-  z += (unsigned long long)f2ll(__uint_as_float(l2) * 0x1p14f) << 28;
-  z += (unsigned long long)f2ll(__uint_as_float(l3) * 0x1p21f) << 21;
-  z += (unsigned long long)f2ll(__uint_as_float(l4) * 0x1p28f) << 14;
+  unsigned long long z = (unsigned long long)(long long)f2i24(__uint_as_float(l0)) << 42;
+  z += (unsigned long long)(long long)f2i24(__uint_as_float(l1) * 0x1p7f) << 35;
+  z += (unsigned long long)(long long)f2i24(__uint_as_float(l2) * 0x1p14f) << 28;
+  z += (unsigned long long)(long long)f2i24(__uint_as_float(l3) * 0x1p21f) << 21;
+  z += (unsigned long long)(long long)f2i24(__uint_as_float(l4) * 0x1p28f) << 14;
   z += (unsigned long long)f2ll(__uint_as_float(l5) * 0x1p42f);
   return (long long)z;
 }
@@ -1164,6 +1176,9 @@ __global__ void __launch_bounds__(tz::THREADS, 1) k_tc_zgemm64(const __grid_cons
   uint64_t* acce = accf + 1;        // the accumulators have been drained
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // barriers and flags take the first 64 bytes after the stages; the column data follow at +128
+  long* coff = reinterpret_cast<long*>(smem + STAGES * tz::STAGE_BYTES + 128);  // [BN] C offset of column
+  int* cexp = reinterpret_cast<int*>(coff + BN);                                  // [BN] its scale exponent
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkb = Kp / BK;
@@ -1176,7 +1191,7 @@ __global__ void __launch_bounds__(tz::THREADS, 1) k_tc_zgemm64(const __grid_cons
       mbar_init(&empty[s], 1);
     }
     mbar_init(accf, 1);
-    mbar_init(acce, 4);  // one arrival per epilogue warp
+    mbar_init(acce, tz::EPI_WARPS);  // one arrival per epilogue warp
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1267,8 +1282,8 @@ __global__ void __launch_bounds__(tz::THREADS, 1) k_tc_zgemm64(const __grid_cons
       }
     }
     __syncwarp();
-  } else {  // ---- epilogue, warps 2..5: TMEM lane quarter = warp % 4
-    const int quarter = warp & 3;
+  } else {  // ---- epilogue, warps 2..13: TMEM lane quarter = warp % 4, chunk share (warp - 2) / 4
+    const int quarter = warp & 3, share = (warp - 2) >> 2;
     long lt = 0;
     for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const bool ok = mbar_wait(accf, (uint32_t)(lt & 1));
@@ -1278,12 +1293,28 @@ __global__ void __launch_bounds__(tz::THREADS, 1) k_tc_zgemm64(const __grid_cons
       }
       fence_after();
       const int m0 = (int)(t / ntn) * BM, n0 = (int)(t % ntn) * BN;
+      // the tile's column offsets into C and scale exponents, once per tile (the epilogue threads,
+      // named barrier 1: the previous tile's readers are done before the rewrite)
+      {
+        const int et = threadIdx.x - 64;
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * tz::EPI_WARPS) : "memory");
+        if (et < BN) {
+          const int n = n0 + et;
+          if (n < N) {
+            const int q = n / ncq;
+            coff[et] = (long)q * sCq + ((n - q * ncq) >> 1);
+            cexp[et] = eb[n] - 1021;
+          }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * tz::EPI_WARPS) : "memory");
+      }
       const int row = m0 + quarter * 32 + lane;
       const bool live = row < M;
       const int erow = live ? ea[a_row0 + row] - 1021 - 56 : 0;
+      double2* crow = C + (long)row * ldc;
       const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
+      for (int c0 = 16 * share; c0 < BN; c0 += 16 * (tz::EPI_WARPS / 4)) {
         uint32_t r0[16], r1[16], r2[16], r3[16], r4[16], r5[16];
         tmem_ld16(tl + c0, r0);
         tmem_ld16(tl + BN + c0, r1);
@@ -1297,12 +1328,11 @@ __global__ void __launch_bounds__(tz::THREADS, 1) k_tc_zgemm64(const __grid_cons
           for (int i = 0; i < 16; i += 2) {
             const int n = n0 + c0 + i;  // even; N is even, so n + 1 < N with n
             if (n < N) {
-              const int q = n / ncq, c = (n - q * ncq) >> 1;
-              const int E = erow + eb[n] - 1021;
+              const int E = erow + cexp[c0 + i];
               const double re = tz::ll2d(tz::combine(r0[i], r1[i], r2[i], r3[i], r4[i], r5[i]), E);
               const double im =
                   tz::ll2d(tz::combine(r0[i + 1], r1[i + 1], r2[i + 1], r3[i + 1], r4[i + 1], r5[i + 1]), E);
-              C[(long)q * sCq + (long)row * ldc + c] = make_double2(re, im);
+              crow[coff[c0 + i]] = make_double2(re, im);
             }
           }
         }
