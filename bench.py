@@ -1130,7 +1130,7 @@ def run_libeph(args):
                 line["mixed"]["e2e"] = e2e_mixed
     single = rank == 0 and world == 1
     # oracle k samples (small, large) per workload for the per-configuration CPU baselines
-    cpu_k = {"mos2": (1000, 4000), "stanene": (8, 32)} if not args.no_cpu_baseline else {"mos2": None, "stanene": None}
+    cpu_k = {"mos2": (1000, 4000), "stanene": (2, 6)} if not args.no_cpu_baseline else {"mos2": None, "stanene": None}
     if single and not args.no_other:
         # the MoS2-shaped (200x200 grid, Nb=11, Nm=9) and stanene-shaped (Nb=120, Nm=180) workloads
         line["other_workloads"] = {

@@ -141,6 +141,10 @@ struct eph_ctx {
   // FP64 k list on the tensor cores: digit planes of the phases (per k list) and of W_q (per q batch)
   DBuf zA, zAe, zB, zBe;
   bool zA_ready = false;
+  // Eq. 9 and the adjoint's gradient GEMM on the tensor cores: digits of g(Re,Rp)^T (per context,
+  // again after eph_set_gw), of the q batch's phases, of G1bar^T and of the conjugated phases
+  DBuf zG, zGe, zP, zPe, zH, zHe, zQ, zQe;
+  bool zG_ready = false;
   cudaEvent_t set_done[2] = {};
   bool set_pending[2] = {false, false};
   int stage_set = 0;
@@ -380,7 +384,8 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
                   &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair, &ctx->g1in,
                   &ctx->aS2, &ctx->aS1, &ctx->aS0, &ctx->DG, &ctx->sG, &ctx->DP, &ctx->G1f, &ctx->g_stage2,
-                  &ctx->est[0], &ctx->est[1], &ctx->ost[0], &ctx->ost[1], &ctx->Pacc, &ctx->UkH, &ctx->zA, &ctx->zAe, &ctx->zB, &ctx->zBe};
+                  &ctx->est[0], &ctx->est[1], &ctx->ost[0], &ctx->ost[1], &ctx->Pacc, &ctx->UkH, &ctx->zA, &ctx->zAe, &ctx->zB, &ctx->zBe, &ctx->zG, &ctx->zGe, &ctx->zP, &ctx->zPe, &ctx->zH,
+                  &ctx->zHe, &ctx->zQ, &ctx->zQe};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -403,6 +408,7 @@ namespace {
 // Digits of the resident g(Re,Rp) for the mixed form's tensor-core Eq. 9 (after creation and
 // after eph_set_gw).
 int form_gw_digits(eph_ctx* ctx) {
+  ctx->zG_ready = false;  // the FP64-accuracy digits are rebuilt at the next Eq. 9
   if (!ctx->eq9_tc) return EPH_OK;
   const long X = (long)ctx->nm * ctx->ne * ctx->nb * ctx->nb;
   const size_t slice = (size_t)2 * X * ctx->kpp;
@@ -912,6 +918,37 @@ int ensure_q_workspace(eph_ctx* ctx, const QPlan& p, bool with_y = true) {
   return EPH_OK;
 }
 
+// Eq. 9 in FP64 accuracy on the tensor cores, G1[q][x] = sum_Rp P_q[Rp] g(Re,Rp)[Rp][x], as the
+// product (x rows of g(Re,Rp)^T) x (the q batch's phases): while the digits of g(Re,Rp) fit 1/16
+// of the device (at most 4 GiB) and 2 nrp <= 512.
+long tc_x(const eph_ctx* ctx) { return (long)ctx->nm * ctx->ne * ctx->nb * ctx->nb; }
+bool use_tc_eq9(const eph_ctx* ctx) {
+  const long X = tc_x(ctx), kp = (2L * ctx->nrp + 31) / 32 * 32;
+  const size_t cap = std::min((size_t)4 << 30, ctx->mem_total ? ctx->mem_total / 16 : (size_t)4 << 30);
+  return !ctx->opt.gemm_alu && 2L * ctx->nrp <= 512 && (size_t)14 * X * kp <= cap && X <= 2147483647L;
+}
+
+// Pq: the phases of the nqb q points (rows of np), qb_cap: the most q points of a call (buffer size)
+int tc_eq9(eph_ctx* ctx, int qb_cap, int nqb, const double2* Pq, double2* G1) {
+  const long X = tc_x(ctx);
+  const int Kp = (2 * ctx->nrp + 31) / 32 * 32;
+  if (!ctx->zG_ready) {
+    EPH_TRY(ensure(ctx, ctx->zG, (size_t)14 * X * Kp));
+    EPH_TRY(ensure(ctx, ctx->zGe, (size_t)X * sizeof(int)));
+    EPH_LAUNCH_S(EPH_STAGE_FT_Q, eph::launch_zdigits_rows(ctx->gW, 1, X, (int)X, ctx->nrp, Kp, as<int>(ctx->zGe),
+                                                          ctx->zG.p, ctx->stream));
+    ctx->zG_ready = true;
+  }
+  EPH_TRY(ensure(ctx, ctx->zP, (size_t)14 * 2 * qb_cap * Kp));
+  EPH_TRY(ensure(ctx, ctx->zPe, (size_t)2 * qb_cap * sizeof(int)));
+  EPH_LAUNCH_S(EPH_STAGE_FT_Q, eph::launch_zdigits_cols(Pq + ctx->rp0, 1, ctx->np, nqb, ctx->nrp, 1, Kp, 0,
+                                                        as<int>(ctx->zPe), ctx->zP.p, ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_FT_Q, eph::launch_tc_zgemm64(ctx->zG.p, X, 0, (int)X, as<int>(ctx->zGe), ctx->zP.p, 2 * nqb,
+                                                      as<int>(ctx->zPe), Kp, G1, 2, 1, X, 0, 0, ctx->status + 1,
+                                                      ctx->stream));
+  return EPH_OK;
+}
+
 // Per q batch, before the k loop: phases, D(q) -> omega, u; Eq. 9; W_q; on a product k grid
 // (grid_stages) also the first two axis transforms of W_q.
 // g1_in: the caller's G1 of these q points (eph_interp_q_g1), else Eq. 9 runs on the resident slice.
@@ -948,8 +985,11 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
                                                               as<double2>(ctx->G1), ctx->stream));
     G1src = as<double2>(ctx->G1);
   } else if (!G1src) {
-    EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, p.X, ctx->nrp, Pp + ctx->rp0, np, ctx->gW, p.X,
-                                               as<double2>(ctx->G1), p.X, ctx->stream));
+    if (use_tc_eq9(ctx))
+      EPH_TRY(tc_eq9(ctx, p.QB, nqb, Pp, as<double2>(ctx->G1)));
+    else
+      EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, p.X, ctx->nrp, Pp + ctx->rp0, np, ctx->gW, p.X,
+                                                 as<double2>(ctx->G1), p.X, ctx->stream));
     G1src = as<double2>(ctx->G1);
   }
   // W_q = [ e^{i q.Re} H(Re) | mode-rotated G1 ], row e of length NW
@@ -1100,19 +1140,20 @@ int tc_rek_tile(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
   if (!ctx->zA_ready) {
     EPH_TRY(ensure(ctx, ctx->zA, (size_t)7 * nk * Kp * 2));
     EPH_TRY(ensure(ctx, ctx->zAe, (size_t)nk * sizeof(int)));
-    EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_zdigits_rows(as<double2>(ctx->Pk), ne, (int)nk, ne, Kp, as<int>(ctx->zAe),
-                                                           ctx->zA.p, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_PHASE, eph::launch_zdigits_rows(as<double2>(ctx->Pk), ne, 1, (int)nk, ne, Kp,
+                                                           as<int>(ctx->zAe), ctx->zA.p, ctx->stream));
     ctx->zA_ready = true;
   }
   if (k0 == 0) {
     EPH_TRY(ensure(ctx, ctx->zB, (size_t)7 * p.QB * N * Kp * 2));
     EPH_TRY(ensure(ctx, ctx->zBe, (size_t)p.QB * N * sizeof(int)));
     EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_zdigits_cols(as<double2>(ctx->W), p.NW, (long)ne * p.NW, nqb, ne, (int)p.NW,
-                                                          Kp, as<int>(ctx->zBe), ctx->zB.p, ctx->stream));
+                                                          Kp, 0, as<int>(ctx->zBe), ctx->zB.p, ctx->stream));
   }
   EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_tc_zgemm64(ctx->zA.p, nk, (int)k0, nkt, as<int>(ctx->zAe), ctx->zB.p,
                                                       (int)(nqb * N), as<int>(ctx->zBe), Kp, as<double2>(ctx->Y),
-                                                      (int)N, p.NW, (long)nkt * p.NW, ctx->status + 1, ctx->stream));
+                                                      (int)N, p.NW, (long)nkt * p.NW, 1, 0, ctx->status + 1,
+                                                      ctx->stream));
   return EPH_OK;
 }
 
@@ -1524,8 +1565,12 @@ extern "C" int eph_g1_partial(eph_ctx* ctx, int nq, const double* qpts, double* 
     EPH_LAUNCH_S(EPH_STAGE_PHASE, launch_phase(qdev + 3L * q0, nqb, ctx->Rp, ctx->wp, np, as<double2>(ctx->Pp), np,
                                                ctx->stream));
     // Eq. 9 over the Rp vectors of this slice only: the partial sums of all slices add up to G1
-    EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, X, ctx->nrp, as<double2>(ctx->Pp) + ctx->rp0, np, ctx->gW, X, dst,
-                                               X, ctx->stream));
+    // (the same kernels as eph_interp_q's own Eq. 9, so a whole context gets the same bits)
+    if (use_tc_eq9(ctx))
+      EPH_TRY(tc_eq9(ctx, QB, nqb, as<double2>(ctx->Pp), dst));
+    else
+      EPH_LAUNCH_S(EPH_STAGE_FT_Q, launch_skinny(nqb, X, ctx->nrp, as<double2>(ctx->Pp) + ctx->rp0, np, ctx->gW, X, dst,
+                                                 X, ctx->stream));
     if (!ctx->opt.device_ptrs)
       EPH_CK(cudaMemcpyAsync(reinterpret_cast<double2*>(G1) + (long)q0 * X, dst, (size_t)nqb * X * sizeof(double2),
                              cudaMemcpyDeviceToHost, ctx->stream));
@@ -1876,8 +1921,26 @@ int grad_acc_init(eph_ctx* ctx, const QPlan& p, GradAcc* a) {
 // rows for the next batch of nqb q points (flushing first if they would not fit)
 int grad_acc_flush(eph_ctx* ctx, const QPlan& p, GradAcc* a, double2* grad) {
   if (a->n == 0) return EPH_OK;
-  EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ctx->np, (int)p.X, (int)a->n, as<double2>(ctx->Pacc), ctx->np, 0,
-                                              as<double2>(ctx->G1bar), p.X, 0, grad, p.X, 0, 1, 1, ctx->stream));
+  const long X = p.X;
+  const int Kp = (int)(2 * a->n + 31) / 32 * 32;
+  const size_t cap = std::min((size_t)4 << 30, ctx->mem_total ? ctx->mem_total / 16 : (size_t)4 << 30);
+  if (!ctx->opt.gemm_alu && (size_t)14 * X * Kp <= cap && X <= 2147483647L) {
+    // on the tensor cores at FP64 accuracy: grad^T[x][Rp] += sum_q G1bar^T[x][q] conj(P_q(Rp))
+    EPH_TRY(ensure(ctx, ctx->zH, (size_t)14 * X * Kp));
+    EPH_TRY(ensure(ctx, ctx->zHe, (size_t)X * sizeof(int)));
+    EPH_TRY(ensure(ctx, ctx->zQ, (size_t)14 * 2 * ctx->np * Kp));
+    EPH_TRY(ensure(ctx, ctx->zQe, (size_t)2 * ctx->np * sizeof(int)));
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_zdigits_rows(as<double2>(ctx->G1bar), 1, X, (int)X, (int)a->n, Kp,
+                                                         as<int>(ctx->zHe), ctx->zH.p, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_zdigits_cols(as<double2>(ctx->Pacc), ctx->np, 0, 1, (int)a->n, ctx->np, Kp,
+                                                         1, as<int>(ctx->zQe), ctx->zQ.p, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_tc_zgemm64(ctx->zH.p, X, 0, (int)X, as<int>(ctx->zHe), ctx->zQ.p,
+                                                       2 * ctx->np, as<int>(ctx->zQe), Kp, grad, 2 * ctx->np, 1, 0, X,
+                                                       1, ctx->status + 1, ctx->stream));
+  } else {
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ctx->np, (int)p.X, (int)a->n, as<double2>(ctx->Pacc), ctx->np, 0,
+                                                as<double2>(ctx->G1bar), p.X, 0, grad, p.X, 0, 1, 1, ctx->stream));
+  }
   a->n = 0;
   return EPH_OK;
 }

@@ -1,8 +1,9 @@
 // Band rotation g_nu = V_{k+q}^H G3_nu V_k (the last step of Eq. 7's evaluation, Eqs. 4-5
 // gauges) for shapes beyond the shared-memory kernels, on the tcgen05 tensor cores: the mixed
 // form's large-Nb path.  Two batched products of the fixed-point digit scheme of the H(k+q)
-// contraction with four digits per operand (levels <= 3, ~2^-32 of each row's scale; float-pair
-// results), on the real embedding of the complex matrices (K = 2 Nb, re/im interleaved):
+// contraction with four digits per operand (levels <= 3, ~2^-32 of each row's scale; results
+// rounded to one FP32 per element), on the real embedding of the complex matrices (K = 2 Nb,
+// re/im interleaved):
 //   stage 1, per pair:  C1[2n' + c][nu Nb + a] = (re, im)_c of T[(nu, a)][n'],  T = G3_nu V_k,
 //                       A = V_k embedded (rows 2n' + c, K = 2b + t), B = the G3 rows (nu, a);
 //   stage 2, per pair:  C2[2m + c][nu Nb + n'] = (re, im)_c of g_nu[m][n'],
@@ -143,8 +144,8 @@ __global__ void k_gdigits(const TC* __restrict__ Y, long ldy, long off, int nrow
 }
 
 // Stage-2 B digits, one warp per row w = p nrow + j, j = nu nb + n': K = 2a + t of
-// T[(nu, a)][n'] part t = C1[p][2n' + t][nu nb + a] (float pair hi + lo).
-__global__ void k_tdigits(const float2* __restrict__ C1, long sC, int nrow, int nb, long rows, int kp,
+// T[(nu, a)][n'] part t = C1[p][2n' + t][nu nb + a].
+__global__ void k_tdigits(const float* __restrict__ C1, long sC, int nrow, int nb, long rows, int kp,
                           float* __restrict__ sB, __nv_bfloat16* __restrict__ D, long slice) {
   const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -152,27 +153,27 @@ __global__ void k_tdigits(const float2* __restrict__ C1, long sC, int nrow, int 
   const long p = w / nrow;
   const int j = (int)(w - p * nrow);
   const int nu = j / nb, np_ = j - nu * nb;
-  const float2* src = C1 + p * sC + (long)nu * nb;
-  float2 x[MAXKL];
+  const float* src = C1 + p * sC + (long)nu * nb;
+  float x[MAXKL];
   int eb = 0;
 #pragma unroll
   for (int i = 0; i < MAXKL; ++i) {
     const int kk = lane + 32 * i;
-    x[i] = kk < 2 * nb ? src[(long)(2 * np_ + (kk & 1)) * nrow + (kk >> 1)] : make_float2(0.f, 0.f);
-    eb = max(eb, (int)((__float_as_uint(x[i].x) >> 23) & 0xFF));
+    x[i] = kk < 2 * nb ? src[(long)(2 * np_ + (kk & 1)) * nrow + (kk >> 1)] : 0.f;
+    eb = max(eb, (int)((__float_as_uint(x[i]) >> 23) & 0xFF));
   }
   eb = warp_max_int(eb);
-  const int es = eb ? eb - 127 + 2 : 0;  // |hi + lo| <= |hi| (1 + 2^-24): still within s / 2 + 2^-25 s
+  const int es = eb ? eb - 127 + 2 : 0;
   if (lane == 0) sB[w] = ldexpf(1.f, es);
 #pragma unroll
   for (int i = 0; i < MAXKL; ++i) {
     const int kk = lane + 32 * i;
-    if (kk < kp) put_digits(fixedF_f(x[i].x, es) + fixedF_f(x[i].y, es), D, slice, w * kp + kk);
+    if (kk < kp) put_digits(fixedF_f(x[i], es), D, slice, w * kp + kk);
   }
 }
 
-// g[iq][kk][nu][m][n'] = complex64 of C2[p][2m + c][nu nb + n'] (hi + lo), pair p0 + p = iq nk + kk.
-__global__ void k_gout(const float2* __restrict__ C2, long sC, int nrow, int nb, int nm, long npairs, int nk, long p0,
+// g[iq][kk][nu][m][n'] = complex64 of C2[p][2m + c][nu nb + n'], pair p0 + p = iq nk + kk.
+__global__ void k_gout(const float* __restrict__ C2, long sC, int nrow, int nb, int nm, long npairs, int nk, long p0,
                        float2* __restrict__ g, long sgq) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long per = (long)nm * nb * nb;
@@ -182,11 +183,10 @@ __global__ void k_gout(const float2* __restrict__ C2, long sC, int nrow, int nb,
   const int nu = (int)(rem / (nb * nb));
   const int r2 = (int)(rem - (long)nu * nb * nb);
   const int m = r2 / nb, n = r2 - m * nb;
-  const float2* src = C2 + p * sC + (long)nu * nb + n;
-  const float2 re = src[(long)(2 * m) * nrow], im = src[(long)(2 * m + 1) * nrow];
+  const float* src = C2 + p * sC + (long)nu * nb + n;
   const long P = p0 + p;
   const long iq = P / nk, kk = P - iq * nk;
-  g[iq * sgq + kk * per + rem] = make_float2(__fadd_rn(re.x, re.y), __fadd_rn(im.x, im.y));
+  g[iq * sgq + kk * per + rem] = make_float2(src[(long)(2 * m) * nrow], src[(long)(2 * m + 1) * nrow]);
 }
 
 size_t align_up(size_t x) { return (x + 1023) & ~(size_t)1023; }
@@ -203,9 +203,9 @@ BandTcShape band_tc_shape(int nk, int nm, int nb) {
   s.M = 2 * nb;
   s.Nr = (long)nm * nb;
   s.a1 = align_up((size_t)NDIG * nk * s.M * s.kp * 2);
-  // B digits (shared by both stages), C float pairs (C1 then C2), A2 digits, B row scales
+  // B digits (shared by both stages), C in FP32 (C1 then C2), A2 digits, B row scales
   s.per_pair =
-      (size_t)NDIG * s.Nr * s.kp * 2 + (size_t)s.M * s.Nr * 8 + (size_t)NDIG * s.M * s.kp * 2 + (size_t)s.Nr * 4;
+      (size_t)NDIG * s.Nr * s.kp * 2 + (size_t)s.M * s.Nr * 4 + (size_t)NDIG * s.M * s.kp * 2 + (size_t)s.Nr * 4;
   return s;
 }
 
@@ -237,8 +237,8 @@ cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const
   __nv_bfloat16* A1 = reinterpret_cast<__nv_bfloat16*>(base);
   char* chunk = base + sh.a1;
   __nv_bfloat16* Bd = reinterpret_cast<__nv_bfloat16*>(chunk);
-  float2* C = reinterpret_cast<float2*>(chunk + align_up((size_t)NDIG * PB * Nr * kp * 2));
-  __nv_bfloat16* A2 = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(C) + align_up((size_t)PB * M * Nr * 8));
+  float* C = reinterpret_cast<float*>(chunk + align_up((size_t)NDIG * PB * Nr * kp * 2));
+  __nv_bfloat16* A2 = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(C) + align_up((size_t)PB * M * Nr * 4));
   float* sB = reinterpret_cast<float*>(reinterpret_cast<char*>(A2) + align_up((size_t)NDIG * PB * M * kp * 2));
   cudaError_t e;
   // A digits of V_k for every k of the tile (stage 1)

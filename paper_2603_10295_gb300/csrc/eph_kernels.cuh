@@ -230,9 +230,10 @@ cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M
                                  float sA, const float* sB, float* C, long ldc, long sC, int* err, cudaStream_t st);
 // Batched products of the band rotation: four digits per operand (maps: 4 CUtensorMaps each,
 // 64-byte swizzle), levels <= 3 in two accumulators (level 0 exact), two accumulator sets so the
-// epilogue overlaps the next tile; C float pairs; A rows as launch_tc_hkq_gemm_b, m tiles fastest.
+// epilogue overlaps the next tile; C one FP32 per element (ldc, sC in floats); A rows as
+// launch_tc_hkq_gemm_b, m tiles fastest.
 cudaError_t launch_tc_band_gemm(const void* maps_a4, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
-                                float sA, const float* sB, float2* C, long ldc, long sC, int* err, int a_mod,
+                                float sA, const float* sB, float* C, long ldc, long sC, int* err, int a_mod,
                                 int a_qoff, int a_stride, cudaStream_t st);
 // Band rotation of large shapes on the tensor cores (mixed form): g[iq][kk] (complex64, rows iq
 // sgq apart, pair (iq, kk) at kk nm nb^2) = V_{k+q}^H G3_nu V_k for the nq x nk pairs of a tile,
@@ -262,19 +263,20 @@ cudaError_t launch_band_tc_small64_ex(const double2* X, long xq, long xk, const 
                                       cudaStream_t st);
 // FP64-accuracy complex GEMM on the tensor cores (seven base-128 digits per operand, exact level
 // sums, doubles assembled from 64-bit integers): digit planes [7][rows][Kp] (bf16) of a complex
-// row-major P[rows][ne] (K = (e, re/im), Kp a multiple of 32, 2 ne <= Kp), with the largest biased
-// exponent of each row in ea; of the columns of W[q][e][c] (nq x ncol columns) as 2 ncol rows per q
-// (Re / Im of the product), with the column exponents in eb (per row).
-cudaError_t launch_zdigits_rows(const double2* P, long ldp, int rows, int ne, int Kp, int* ea, void* planes,
+// P with element (r, e) at P[r sr + e se] (K = (e, re/im), Kp a multiple of 32, 2 ne <= Kp), with
+// the largest biased exponent of each row in ea; of the columns of W[q][e][c] (nq x ncol columns;
+// conj(W) with cj) as 2 ncol rows per q (Re / Im of the product), with the column exponents in eb
+// (per row).
+cudaError_t launch_zdigits_rows(const double2* P, long sr, long se, int rows, int ne, int Kp, int* ea, void* planes,
                                 cudaStream_t st);
-cudaError_t launch_zdigits_cols(const double2* W, long ldw, long sW, int nq, int ne, int ncol, int Kp, int* eb,
+cudaError_t launch_zdigits_cols(const double2* W, long ldw, long sW, int nq, int ne, int ncol, int Kp, int cj, int* eb,
                                 void* planes, cudaStream_t st);
-// C[q][row][c] = sum_e P[a_row0 + row][e] W[q][e][c] for rows < M and the N = nq ncq real columns
-// (ncq = 2 ncol per q; C complex128, row stride ldc, q stride sCq); Kp <= 512.  *err |= 1..8 on a
-// barrier timeout.
+// C[q sCq + row ldc + c scol] (=, or += with acc) sum_e P[a_row0 + row][e] W[q][e][c] for rows < M
+// and the N = nq ncq real columns (ncq = 2 ncol per q; C complex128); Kp <= 512.  *err |= 1..8 on
+// a barrier timeout.
 cudaError_t launch_tc_zgemm64(const void* a_planes, long a_rows, int a_row0, int M, const int* ea, const void* b_planes,
-                              int N, const int* eb, int Kp, double2* C, int ncq, long ldc, long sCq, int* err,
-                              cudaStream_t st);
+                              int N, const int* eb, int Kp, double2* C, int ncq, long ldc, long sCq, long scol, int acc,
+                              int* err, cudaStream_t st);
 cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const double2* Ukq, const double2* Uk, int nq,
                            int nk, int nm, int nb, float2* g, long sgq, void* work, size_t work_bytes, int* err,
                            cudaStream_t st);

@@ -752,10 +752,13 @@ __global__ void __launch_bounds__(tch::THREADS, 1) k_tc_hkq_gemm(const __grid_co
 }
 
 // ----------------------------------------------------------------------------- batched band products
-// The band rotation's products (complex64 result, ~2^-31 relative suffices): four digits per
-// operand, levels <= 3, with level 0 exact in its own accumulator and levels 1-3 in a second one
-// (their sum is at most 2^-7 of level 0, so its FP32 rounding is ~2^-31 of the result), which
-// leaves room for two accumulator sets: the epilogue of one tile runs under the MMAs of the next.
+// The band rotation's products (complex64 result): four digits per operand, levels <= 3, with
+// level 0 exact in its own accumulator and levels 1-3 in a second one (their sum is at most 2^-7
+// of level 0, so its FP32 rounding is ~2^-31 of the result), which leaves room for two
+// accumulator sets: the epilogue of one tile runs under the MMAs of the next.  The result is
+// written as one FP32 per element, the two sums added and rounded once (2^-24 of the element):
+// the second stage's digits and the complex64 g need no more, and a float pair would double the
+// bytes the epilogue writes and the next step reads.
 // 32-wide K slices (64-byte swizzle), three 64 KiB stages.  Batch q reads A rows
 // a_row0 + ((q + a_qoff) mod a_mod) a_stride + m; tiles (m fastest, then n, then q).
 namespace tcb {
@@ -769,7 +772,7 @@ constexpr int THREADS = 192;
 
 __global__ void __launch_bounds__(tcb::THREADS, 1) k_tc_band_gemm(const __grid_constant__ TcMaps10 maps, int M,
                                                                  int a_row0, int Nr, int Kp, int nq, float sA,
-                                                                 const float* __restrict__ sB, float2* __restrict__ C,
+                                                                 const float* __restrict__ sB, float* __restrict__ C,
                                                                  long ldc, long sC, int* __restrict__ err, int a_mod,
                                                                  int a_qoff, int a_stride) {
   using namespace tc;
@@ -910,7 +913,7 @@ __global__ void __launch_bounds__(tcb::THREADS, 1) k_tc_band_gemm(const __grid_c
       tch::tile_coords_mfast(t, ntm, ntn, &q, &m0, &n0);
       const int row = m0 + quarter * 32 + lane;
       const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-      float2* crow = C + (long)q * sC + (long)row * ldc;
+      float* crow = C + (long)q * sC + (long)row * ldc;
       const float* srow = sB + (long)q * Nr;
       const float sc = sA * 0x1p-16f;
 #pragma unroll 1
@@ -921,20 +924,20 @@ __global__ void __launch_bounds__(tcb::THREADS, 1) k_tc_band_gemm(const __grid_c
         tmem_ld_wait();
         if (row < M) {
 #pragma unroll
-          for (int i = 0; i < 16; i += 2) {
+          for (int i = 0; i < 16; i += 4) {
             const int col = n0 + c0 + i;
-            float2 v[2];
+            float v[4];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              float h = __uint_as_float(r0[i + u]), l = 0.f;
-              tch::two_sum(h, l, __uint_as_float(r1[i + u]));
+            for (int u = 0; u < 4; ++u) {
               const float f = (col + u < Nr) ? sc * srow[col + u] : 0.f;  // powers of two: exact
-              v[u] = make_float2(h * f, l * f);
+              v[u] = __fadd_rn(__uint_as_float(r0[i + u]), __uint_as_float(r1[i + u])) * f;
             }
-            if (col + 1 < Nr) {
-              *reinterpret_cast<float4*>(crow + col) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-            } else if (col < Nr) {
-              crow[col] = v[0];
+            if (col + 3 < Nr && ((reinterpret_cast<uintptr_t>(crow + col) & 15) == 0)) {
+              *reinterpret_cast<float4*>(crow + col) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (col + u < Nr) crow[col + u] = v[u];
             }
           }
         }
@@ -1078,20 +1081,21 @@ struct TzMaps {
   CUtensorMap b[tz::ND];
 };
 
-// A planes [7][rows][Kp] of P (row stride ldp, ne complex values per row): K = (e, re/im).
-// ea[row] = the largest biased exponent of the row.
-__global__ void k_zdig_rows_exp(const double2* __restrict__ P, long ldp, int rows, int ne, int* __restrict__ ea) {
+// A planes [7][rows][Kp] of P (element (r, e) at P[r sr + e se], ne complex values per row):
+// K = (e, re/im).  ea[row] = the largest biased exponent of the row.
+__global__ void k_zdig_rows_exp(const double2* __restrict__ P, long sr, long se, int rows, int ne,
+                                int* __restrict__ ea) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   int m = 0;
   for (int e = 0; e < ne; ++e) {
-    const double2 z = P[(long)r * ldp + e];
+    const double2 z = P[(long)r * sr + (long)e * se];
     m = max(m, max(tz::dexp(z.x), tz::dexp(z.y)));
   }
   ea[r] = m;
 }
 
-__global__ void k_zdig_rows(const double2* __restrict__ P, long ldp, int rows, int ne, int Kp,
+__global__ void k_zdig_rows(const double2* __restrict__ P, long sr, long se, int rows, int ne, int Kp,
                             const int* __restrict__ ea, uint32_t* __restrict__ planes, long plane_words) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int half = Kp / 2;
@@ -1099,7 +1103,7 @@ __global__ void k_zdig_rows(const double2* __restrict__ P, long ldp, int rows, i
   const int r = (int)(t / half), e = (int)(t - (long)r * half);
   uint32_t hr[tz::ND], hi[tz::ND];
   if (e < ne) {
-    const double2 z = P[(long)r * ldp + e];
+    const double2 z = P[(long)r * sr + (long)e * se];
     tz::digits7(z.x, ea[r], hr);
     tz::digits7(z.y, ea[r], hi);
   } else {
@@ -1110,9 +1114,10 @@ __global__ void k_zdig_rows(const double2* __restrict__ P, long ldp, int rows, i
   for (int d = 0; d < tz::ND; ++d) planes[d * plane_words + t] = hr[d] | (hi[d] << 16);
 }
 
-// B planes [7][nq ncq][Kp] of W[q][e][c] (complex, row stride ldw, q stride sW, ncq / 2 columns):
-// row 2c holds (Re W, -Im W) and row 2c + 1 (Im W, Re W) along K = (e, re/im), so that A B^T gives
-// Re and Im of P W.  eb[row] = the largest biased exponent of the column (both rows).
+// B planes [7][nq ncq][Kp] of W[q][e][c] (complex, row stride ldw, q stride sW, ncq / 2 columns;
+// conj(W) with cj): row 2c holds (Re W, -Im W) and row 2c + 1 (Im W, Re W) along K = (e, re/im),
+// so that A B^T gives Re and Im of P W.  eb[row] = the largest biased exponent of the column (both
+// rows).
 __global__ void k_zdig_cols_exp(const double2* __restrict__ W, long ldw, long sW, int nq, int ne, int ncol,
                                 int* __restrict__ eb) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1128,7 +1133,7 @@ __global__ void k_zdig_cols_exp(const double2* __restrict__ W, long ldw, long sW
 }
 
 __global__ void k_zdig_cols(const double2* __restrict__ W, long ldw, long sW, int nq, int ne, int ncol, int Kp,
-                            const int* __restrict__ eb, uint32_t* __restrict__ planes, long plane_words) {
+                            int cj, const int* __restrict__ eb, uint32_t* __restrict__ planes, long plane_words) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;  // (q, c, e), e fastest
   const int half = Kp / 2;
   if (t >= (long)nq * ncol * half) return;
@@ -1140,7 +1145,7 @@ __global__ void k_zdig_cols(const double2* __restrict__ W, long ldw, long sW, in
     const double2 z = W[(long)q * sW + (long)e * ldw + c];
     const int em = eb[2 * qc];
     tz::digits7(z.x, em, hr);
-    tz::digits7(z.y, em, hi);
+    tz::digits7(cj ? -z.y : z.y, em, hi);
   } else {
 #pragma unroll
     for (int d = 0; d < tz::ND; ++d) hr[d] = hi[d] = 0u;
@@ -1154,14 +1159,16 @@ __global__ void k_zdig_cols(const double2* __restrict__ W, long ldw, long sW, in
   }
 }
 
-// C[q][row][c] (complex128; q = n / ncq, c = (n mod ncq) / 2 for the real column n) from the A rows
-// a_row0 .. a_row0 + M - 1 and the N B rows; tiles 128 x 80, n tiles fastest (the CTAs on one A row
+// C[q sCq + row ldc + c scol] (complex128; q = n / ncq, c = (n mod ncq) / 2 for the real column n;
+// added to what C holds with acc) from the A rows a_row0 .. a_row0 + M - 1 and the N B rows;
+// tiles 128 x 80, n tiles fastest (the CTAs on one A row
 // tile run together and share it through L2).  Bounded waits: on a timeout *err is set and the
 // CTA stops, drains what it issued and frees its TMEM.
 __global__ void __launch_bounds__(tz::THREADS, 1) k_tc_zgemm64(const __grid_constant__ TzMaps maps, int M, int a_row0,
                                                               int N, int Kp, const int* __restrict__ ea,
                                                               const int* __restrict__ eb, double2* __restrict__ C,
-                                                              int ncq, long ldc, long sCq, int* __restrict__ err) {
+                                                              int ncq, long ldc, long sCq, long scol, int acc,
+                                                              int* __restrict__ err) {
   using namespace tc;
   using tz::BK;
   using tz::BM;
@@ -1302,7 +1309,7 @@ __global__ void __launch_bounds__(tz::THREADS, 1) k_tc_zgemm64(const __grid_cons
           const int n = n0 + et;
           if (n < N) {
             const int q = n / ncq;
-            coff[et] = (long)q * sCq + ((n - q * ncq) >> 1);
+            coff[et] = (long)q * sCq + (long)((n - q * ncq) >> 1) * scol;
             cexp[et] = eb[n] - 1021;
           }
         }
@@ -1332,7 +1339,13 @@ __global__ void __launch_bounds__(tz::THREADS, 1) k_tc_zgemm64(const __grid_cons
               const double re = tz::ll2d(tz::combine(r0[i], r1[i], r2[i], r3[i], r4[i], r5[i]), E);
               const double im =
                   tz::ll2d(tz::combine(r0[i + 1], r1[i + 1], r2[i + 1], r3[i + 1], r4[i + 1], r5[i + 1]), E);
-              crow[coff[c0 + i]] = make_double2(re, im);
+              double2* o = crow + coff[c0 + i];
+              if (acc) {
+                const double2 v = *o;
+                *o = make_double2(v.x + re, v.y + im);
+              } else {
+                *o = make_double2(re, im);
+              }
             }
           }
         }
@@ -1443,12 +1456,12 @@ cudaError_t launch_tc_hkq_gemm_b(const void* maps_a5, const void* maps_b5, int M
 }
 
 cudaError_t launch_tc_band_gemm(const void* maps_a4, const void* maps_b4, int M, int a_row0, int Nr, int Kp, int nq,
-                                float sA, const float* sB, float2* C, long ldc, long sC, int* err, int a_mod,
+                                float sA, const float* sB, float* C, long ldc, long sC, int* err, int a_mod,
                                 int a_qoff, int a_stride, cudaStream_t st) {
   if (M <= 0 || Nr <= 0 || nq <= 0) return cudaSuccess;
   if (Kp % tcb::BK != 0 || Kp <= 0 || Kp > 1024) return cudaErrorInvalidValue;  // exact level-0 sums need K <= 1024
   if (a_mod < 1 || a_qoff < 0 || a_stride < 0) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(C) & 15) != 0 || (ldc & 1) || (sC & 1)) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(C) & 15) != 0) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_tc_band_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tcb::SMEM_BYTES);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -1502,20 +1515,20 @@ cudaError_t launch_tc_split_gemm(const void* mAhi, const void* mAlo, const void*
 }
 
 // ----------------------------------------------------------------------------- FP64-accuracy complex GEMM, host
-cudaError_t launch_zdigits_rows(const double2* P, long ldp, int rows, int ne, int Kp, int* ea, void* planes,
+cudaError_t launch_zdigits_rows(const double2* P, long sr, long se, int rows, int ne, int Kp, int* ea, void* planes,
                                 cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
   if (Kp % tz::BK != 0 || 2 * ne > Kp) return cudaErrorInvalidValue;
-  k_zdig_rows_exp<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, ldp, rows, ne, ea);
+  k_zdig_rows_exp<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, sr, se, rows, ne, ea);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long words = (long)rows * (Kp / 2);
-  k_zdig_rows<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(P, ldp, rows, ne, Kp, ea, static_cast<uint32_t*>(planes),
-                                                               words);
+  k_zdig_rows<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(P, sr, se, rows, ne, Kp, ea,
+                                                               static_cast<uint32_t*>(planes), words);
   return cudaGetLastError();
 }
 
-cudaError_t launch_zdigits_cols(const double2* W, long ldw, long sW, int nq, int ne, int ncol, int Kp, int* eb,
+cudaError_t launch_zdigits_cols(const double2* W, long ldw, long sW, int nq, int ne, int ncol, int Kp, int cj, int* eb,
                                 void* planes, cudaStream_t st) {
   if (nq <= 0 || ncol <= 0) return cudaSuccess;
   if (Kp % tz::BK != 0 || 2 * ne > Kp) return cudaErrorInvalidValue;
@@ -1524,14 +1537,14 @@ cudaError_t launch_zdigits_cols(const double2* W, long ldw, long sW, int nq, int
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long words = cols * (Kp / 2);
-  k_zdig_cols<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(W, ldw, sW, nq, ne, ncol, Kp, eb,
+  k_zdig_cols<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(W, ldw, sW, nq, ne, ncol, Kp, cj, eb,
                                                                static_cast<uint32_t*>(planes), 2 * words);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_zgemm64(const void* a_planes, long a_rows, int a_row0, int M, const int* ea, const void* b_planes,
-                              int N, const int* eb, int Kp, double2* C, int ncq, long ldc, long sCq, int* err,
-                              cudaStream_t st) {
+                              int N, const int* eb, int Kp, double2* C, int ncq, long ldc, long sCq, long scol, int acc,
+                              int* err, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   // exact sums of levels 0-4 and the int64 combination need K <= 512
   if (Kp % tz::BK != 0 || Kp <= 0 || Kp > 512 || (N & 1) || (ncq & 1) || ncq <= 0) return cudaErrorInvalidValue;
@@ -1554,7 +1567,8 @@ cudaError_t launch_tc_zgemm64(const void* a_planes, long a_rows, int a_row0, int
   }
   const long ntiles = (long)((N + tz::BN - 1) / tz::BN) * ((M + tz::BM - 1) / tz::BM);
   const int grid = (int)(ntiles < sms ? ntiles : sms);
-  k_tc_zgemm64<<<grid, tz::THREADS, tz::SMEM_BYTES, st>>>(maps, M, a_row0, N, Kp, ea, eb, C, ncq, ldc, sCq, err);
+  k_tc_zgemm64<<<grid, tz::THREADS, tz::SMEM_BYTES, st>>>(maps, M, a_row0, N, Kp, ea, eb, C, ncq, ldc, sCq, scol, acc,
+                                                          err);
   return cudaGetLastError();
 }
 

@@ -86,3 +86,33 @@ def test_backward_on_a_k_list_with_tensor_core_rek():
     L, grad = binding.Context.from_workload(wl, q_batch=2, k_tile=33).loss_and_grad(wl.kpts, wl.qpts, w, 1e-6)
     assert abs(L - L_ref) <= 1e-12 * abs(L_ref)
     assert float(np.abs(grad - g_ref).max() / np.abs(g_ref).max()) <= 1e-12
+
+
+# Eq. 9 (G1 = P_q g(Re,Rp)) and the adjoint's gradient GEMM (grad += P_q^H G1bar) take the same
+# tensor-core GEMM: against the DFMA kernels of the same context (option gemm_alu)
+def test_eq9_tensor_core_against_dfma_on_the_grid():
+    wl = synth.make_workload("mos2_diff", nq=5)
+    out = []
+    for alu in (False, True):
+        ctx = binding.Context.from_workload(wl, q_batch=3, gemm_alu=alu)
+        eps_k = ctx.set_k_grid(*wl.kgrid)
+        out.append((eps_k,) + ctx.interp_q(wl.qpts))
+    assert np.abs(out[0][1] - out[1][1]).max() <= 1e-13 * np.abs(out[1][1]).max()
+    d = pair_rel(out[0][3], out[1][3])
+    print(f"Eq. 9 tensor cores vs DFMA: g {d:.3g}")
+    assert d <= 1e-12
+
+
+def test_backward_gradient_gemm_tensor_core_against_dfma():
+    wl = synth.make_workload("mos2_diff", nq=6)
+    eps_k, _ = oracle.electron_eigen(oracle.hamiltonian_k(wl.kpts, wl.Re, wl.we, wl.H_Re))
+    w = oracle.fermi_weights(eps_k, 2)[0]
+    res = []
+    for alu in (False, True):
+        ctx = binding.Context.from_workload(wl, q_batch=2, gemm_alu=alu)
+        ctx.set_k_grid(*wl.kgrid)
+        res.append(ctx.loss_and_grad(None, wl.qpts, w, 1e-6))
+    (L, g), (La, ga) = res
+    print(f"backward tensor cores vs DFMA: L {abs(L - La) / abs(La):.3g} grad {np.abs(g - ga).max() / np.abs(ga).max():.3g}")
+    assert abs(L - La) <= 1e-12 * abs(La)
+    assert np.abs(g - ga).max() <= 1e-12 * np.abs(ga).max()
