@@ -862,14 +862,16 @@ __device__ __forceinline__ void mma_levels64(uint32_t acc, int ncol, uint32_t sA
 //
 // Pair (iq, kk) reads its rows [nu][a][b] at X + iq xq + kk xk and writes [nu][m][n] at
 // out + iq oq + kk ok; the two may be the same rows (a tile's input is in shared memory before its
-// output is written, and no two tiles share a pair).  adj = 0: V_{k+q}^H X V_k (the band rotation);
-// adj = 1: V_{k+q} X V_k^H (its adjoint, the same products with both V conjugate-transposed).
-// wk non-NULL: the loss terms of the adjoint, c = w_nk / omega_qnu (0 for omega <= omega_min):
-// Lpair[iq nk + kk] = sum c |g|^2 (fixed order) and 2 c g written instead of g.
-template <int KP>
+// output is written, and no two tiles share a pair).  ADJ = false: V_{k+q}^H X V_k (the band
+// rotation); ADJ: V_{k+q} X V_k^H (its adjoint, the same products with both V conjugate-transposed).
+// LOSS: the loss terms of the adjoint, c = w_nk / omega_qnu (0 for omega <= omega_min):
+// Lpair[iq nk + kk] = sum c |g|^2 (fixed order) and 2 c g written instead of g.  (Template flags:
+// the plain rotation compiles without either path; as runtime switches they cost it ~35 % at the
+// MoS2 shapes.)
+template <int KP, bool ADJ, bool LOSS>
 __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_tc_small64(
     const double2* X, long xq, long xk, const double2* __restrict__ Ukq, const double2* __restrict__ Uk, int nq,
-    int nk, int nm, int nb, int RS, int PPT, double2* g, long oq, long ok, const int* __restrict__ keep, int adj,
+    int nk, int nm, int nb, int RS, int PPT, double2* g, long oq, long ok, const int* __restrict__ keep,
     const double* __restrict__ wk, const double* __restrict__ om, double omega_min, double* __restrict__ Lpair,
     int* __restrict__ err, uint32_t tmem_cols, int nslots, unsigned slot_bytes, unsigned slot_cols) {
   using namespace bts;
@@ -998,12 +1000,12 @@ __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_t
     for (int e = tid; e < (PPT + 1) * nb2; e += THREADS) {
       const int jj = (int)(((unsigned)e * div_nb2) >> 16), r2 = e - jj * nb2;
       const int a = (int)(((unsigned)r2 * div_nb) >> 16), c = r2 - a * nb;
-      const int rv = adj ? c * nb + a : r2;
+      const int rv = ADJ ? c * nb + a : r2;
       float vr[ND], vi[ND];
       if (jj < PPT) {
         if (qg * PPT + jj >= nq) continue;
         double2 u = vsm[jj * nb2 + rv];
-        if (adj) u.y = -u.y;
+        if constexpr (ADJ) u.y = -u.y;
         bt64::xdigits(bt64::dfixed48(u.x, 1022), vr);
         bt64::xdigits(bt64::dfixed48(u.y, 1022), vi);
         const uint32_t o0 = off<KP>(jj * KP + 2 * c, 2 * a), o1 = off<KP>(jj * KP + 2 * c + 1, 2 * a);
@@ -1014,7 +1016,7 @@ __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_t
         }
       } else {
         double2 u = vsm[PPT * nb2 + rv];
-        if (adj) u.y = -u.y;
+        if constexpr (ADJ) u.y = -u.y;
         bt64::xdigits(bt64::dfixed48(u.x, 1022), vr);
         bt64::xdigits(bt64::dfixed48(u.y, 1022), vi);
         const uint32_t o0 = off<KP>(2 * c, 2 * a), o1 = off<KP>(2 * c + 1, 2 * a);
@@ -1135,7 +1137,7 @@ __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_t
         // U = X_U 2^-48 2^(gex - 1021) 2; stage-2 A holds U / (2^B 2^-48 2^(gex - 1021) 2)
         const int E = B - 48 + (gex - 1021) + 1 + 1 - 48;
         double inv = 0.0;  // loss: 1 / omega of the row's mode, 0 at or below omega_min
-        if (wk) {
+        if constexpr (LOSS) {
           const double w = om[(long)iq * nm + nu2];
           inv = w > omega_min ? 1.0 / w : 0.0;
         }
@@ -1145,7 +1147,7 @@ __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_t
             const long long xr = bt64::combine(l0[2 * n], l1[2 * n], l2[2 * n], l3[2 * n], l4[2 * n]);
             const long long xi = bt64::combine(l0[2 * n + 1], l1[2 * n + 1], l2[2 * n + 1], l3[2 * n + 1], l4[2 * n + 1]);
             double2 v = zero ? make_double2(0.0, 0.0) : make_double2(bt64::i2d_scaled(xr, E), bt64::i2d_scaled(xi, E));
-            if (wk) {
+            if constexpr (LOSS) {
               const double c = wk[(long)kk * nb + n] * inv;
               lsum = fma(c, fma(v.x, v.x, v.y * v.y), lsum);
               v = make_double2(2.0 * c * v.x, 2.0 * c * v.y);
@@ -1154,7 +1156,7 @@ __global__ void __launch_bounds__((KP == 16 ? 3 : 2) * bts::THREADS, 1) k_band_t
           }
         }
       }
-      if (wk) {
+      if constexpr (LOSS) {
         // a pair's rows are whole warps (RS is a multiple of 32): warp sums, then the pair's warps in order
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
@@ -1309,23 +1311,25 @@ cudaError_t launch_band_tc_small64_ex(const double2* X, long xq, long xk, const 
   if (nslots < 1) return cudaErrorInvalidConfiguration;
   uint32_t cols = 32;
   while (cols < (uint32_t)(nslots * slot_cols)) cols <<= 1;
-  const void* kern = s.kp == 16 ? reinterpret_cast<const void*>(k_band_tc_small64<16>)
-                                : reinterpret_cast<const void*>(k_band_tc_small64<32>);
+  const bool loss = wk != nullptr;
+  if (adj && loss) return cudaErrorInvalidValue;
+  using Kern = void (*)(const double2*, long, long, const double2*, const double2*, int, int, int, int, int, int, double2*,
+                        long, long, const int*, const double*, const double*, double, double*, int*, uint32_t, int,
+                        unsigned, unsigned);
+  Kern kern = s.kp == 16 ? (adj ? k_band_tc_small64<16, true, false>
+                                : (loss ? k_band_tc_small64<16, false, true> : k_band_tc_small64<16, false, false>))
+                         : (adj ? k_band_tc_small64<32, true, false>
+                                : (loss ? k_band_tc_small64<32, false, true> : k_band_tc_small64<32, false, false>));
   cudaError_t e;
   size_t smem = 0;
   int occ = 0;
-  if ((e = small_occupancy(kern, (size_t)nslots * slot_bytes + 64, (int)(512 / cols), &smem, &occ,
-                           nslots * bts::THREADS)) != cudaSuccess)
+  if ((e = small_occupancy(reinterpret_cast<const void*>(kern), (size_t)nslots * slot_bytes + 64, (int)(512 / cols),
+                           &smem, &occ, nslots * bts::THREADS)) != cudaSuccess)
     return e;
   const long grid = std::min((ntiles + nslots - 1) / nslots, (long)sms * occ);
-  if (s.kp == 16)
-    k_band_tc_small64<16><<<(unsigned)grid, nslots * bts::THREADS, smem, st>>>(
-        X, xq, xk, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, out, oq, ok, keep, adj ? 1 : 0, wk, om, omega_min, Lpair, err,
-        cols, nslots, slot_bytes, slot_cols);
-  else
-    k_band_tc_small64<32><<<(unsigned)grid, nslots * bts::THREADS, smem, st>>>(
-        X, xq, xk, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, out, oq, ok, keep, adj ? 1 : 0, wk, om, omega_min, Lpair, err,
-        cols, nslots, slot_bytes, slot_cols);
+  kern<<<(unsigned)grid, nslots * bts::THREADS, smem, st>>>(X, xq, xk, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, out, oq,
+                                                              ok, keep, wk, om, omega_min, Lpair, err, cols, nslots,
+                                                              slot_bytes, slot_cols);
   return cudaGetLastError();
 }
 
