@@ -94,12 +94,14 @@ typedef struct eph_options {
                          form).  The same switch applies to the FP64 band products of
                          eph_interp_backward, eph_interp_vjp, eph_bloch_to_wannier and
                          eph_linewidths (six-digit tensor-core products, or FP64 DFMA) */
-  int gemm_alu;       /* the Re->k contraction of Eq. 10 on a k list in FP64 (the FP64 form's k-list
-                         path and every FP64 chain): 0 (default) = on the tensor cores, seven
-                         balanced base-128 digits per operand (power-of-two scale per phase row and
-                         per W_q column), exact level sums, doubles assembled from 64-bit integers
-                         (~1e-14 of each column's largest term; needs 2 ne <= 512, nb, nm <= 16);
-                         1 = FP64 DFMA GEMM */
+  int gemm_alu;       /* the FP64-accuracy GEMMs: the Re->k contraction of Eq. 10 on a k list (FP64
+                         form and every FP64 chain; 2 ne <= 512, nb, nm <= 16), Eq. 9 (2 Np <= 512,
+                         digit planes of g(Re,Rp) within 1/16 of the device), the adjoint's gradient
+                         GEMM, and the mixed form's mode rotation for nm > 16: 0 (default) = on the
+                         tensor cores, seven balanced base-128 digits per operand (power-of-two
+                         scale per row and per column), exact level sums, doubles assembled from
+                         64-bit integers (~1e-14 of each column's largest term); 1 = FP64 DFMA
+                         (double-float for the mixed form's mode rotation) */
 } eph_options;
 
 /* Fills *opt with the defaults (FP64 form, host pointers, automatic batching). */
@@ -331,8 +333,9 @@ int eph_set_k_grid_ibz(eph_ctx* ctx, int n1, int n2, int n3, const double* shift
  * eph_interp_q with pair screening: pairs (q,k) with no eps_{m,k+q} in [e_lo, e_hi] get g = 0
  * without the band rotation (the only step after eps_{k+q} is known); keep [nq][nk] (int, may
  * be NULL) receives 1 for the pairs computed and 0 for the screened ones.  eps_kq and omega are
- * complete.  Both forms (in the mixed form the screened pairs get g = 0 from its band
- * rotation kernel; g complex64) with nb, nm <= 16; EPH_ENOTSUP otherwise.
+ * complete.  Both forms (g complex64 in the mixed form) and every supported shape: for nb,
+ * nm <= 16 the screened pairs skip the band rotation (its kernels write their g as 0); beyond,
+ * every pair is rotated and the screened ones are zeroed afterwards (no work saved).
  */
 int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, double e_lo, double e_hi, double* eps_kq,
                         double* omega, void* g, int* keep);
@@ -405,13 +408,31 @@ int eph_profile_reset(eph_ctx* ctx);
  *                 enqueued since the last check (async mode).
  *   eph_autotune  picks q_batch and k_tile for nq q points by timing candidate
  *                 decompositions (q_batch 1..16, k tiles of nk, nk/2, nk/4) with CUDA
- *                 events on the context's stream; the choice is stored in the context
- *                 and cached per problem shape for the process.  Needs device pointers
- *                 and synchronous mode; allocates its probe outputs.
+ *                 events on the context's stream, then, at that decomposition, the kernel
+ *                 variants band_alu and gemm_alu (each must be 3 % faster than the
+ *                 tensor-core default to replace it; both meet the form's accuracy);
+ *                 the choice is applied to the context's options and cached per problem
+ *                 shape and device (name, SM count) for the process, and in the tuning
+ *                 file if one is set.  Needs device pointers and synchronous mode;
+ *                 allocates its probe outputs.
+ *   eph_tune_file sets the process's tuning file (NULL: none) and clears the process
+ *                 cache; reads the file if it exists (entries of other devices are kept
+ *                 but never match).  Returns the number of entries read, or EPH_EINVAL for
+ *                 a malformed line (the cache stays empty).  Timed entries are appended.
+ *                 Line format: "eph-tune 1 <device, spaces as _> <SMs> <form> <scheme>
+ *                 <grid> <nb> <nm> <ne> <np> <nk> <nq> : <q_batch> <k_tile> <band_alu>
+ *                 <gemm_alu>"; lines starting with # are comments.  No CUDA call.
+ *   eph_tuning    the context's current choice and where it came from.
  */
+typedef struct {
+  int q_batch, k_tile, band_alu, gemm_alu;
+  int source; /* 0: not tuned, 1: timed by eph_autotune, 2: this process's cache, 3: the tuning file */
+} eph_tuning_info;
 int eph_reserve(eph_ctx* ctx, int nq);
 int eph_sync(eph_ctx* ctx);
 int eph_autotune(eph_ctx* ctx, int nq, const double* qpts, int* q_batch_out, int* k_tile_out);
+int eph_tune_file(const char* path);
+int eph_tuning(const eph_ctx* ctx, eph_tuning_info* out);
 
 /*
  * The batched Hermitian eigensolver of the interpolation, on caller matrices: the

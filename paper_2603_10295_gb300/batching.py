@@ -122,8 +122,9 @@ def graph_of_materials(specs, form, device, autotune=True):
     specs: [(workload, q batch sizes, chunk, use the uniform k grid)]; each material takes the
     first sum(batches) q points of its workload, and every batch runs as calls of at most `chunk`
     q points whose g goes through one ring buffer per material.  With autotune, eph_autotune picks
-    (q_batch, k_tile) for a call of `chunk` q points on a synchronous context first (the choice is
-    cached per problem shape), and the graph's context uses that choice.
+    (q_batch, k_tile) and the kernel variants (band_alu, gemm_alu) for a call of `chunk` q points on
+    a synchronous context first (the choice is cached per problem shape), and the graph's context
+    uses that choice.
     Returns (GraphBatcher, [Material]) with the graph captured."""
     from .binding import Context
     dev = torch.device(device)
@@ -134,6 +135,7 @@ def graph_of_materials(specs, form, device, autotune=True):
         q_dev = torch.from_numpy(wl.qpts[:nq].copy()).to(dev)
         k_dev = torch.from_numpy(wl.kpts).to(dev)
         tuned = (0, 0)
+        variants = {}
         if autotune:
             tctx = Context.from_workload(wl, form=form, device_ptrs=True, stream=torch.cuda.current_stream(dev))
             if grid:
@@ -141,10 +143,12 @@ def graph_of_materials(specs, form, device, autotune=True):
             else:
                 tctx.eph_set_k(nk, k_dev, None)
             tuned = tctx.eph_autotune(min(chunk, nq), q_dev[:min(chunk, nq)])
+            t = tctx.tuning()
+            variants = {"band_alu": bool(t["band_alu"]), "gemm_alu": bool(t["gemm_alu"])}
             tctx.close()
             torch.cuda.empty_cache()
         ctx = Context.from_workload(wl, form=form, device_ptrs=True, async_mode=True, stream=gb.stream,
-                                    q_batch=tuned[0], k_tile=tuned[1])
+                                    q_batch=tuned[0], k_tile=tuned[1], **variants)
         eps_k = torch.empty(nk, nb, dtype=torch.float64, device=dev)
         with torch.cuda.stream(gb.stream):
             if grid:

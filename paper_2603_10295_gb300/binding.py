@@ -26,7 +26,7 @@ EXPORTS = ("eph_default_options", "eph_create", "eph_set_k", "eph_interp_q", "ep
            "eph_reserve", "eph_sync", "eph_autotune", "eph_linewidths", "eph_interp_vjp",
            "eph_set_k_grid", "eph_bloch_to_wannier", "eph_set_k_window", "eph_interp_q_window", "eph_eigh",
            "eph_create_rp_slice", "eph_g1_partial", "eph_interp_q_g1", "eph_set_gw", "eph_set_k_grid_ibz",
-           "eph_interp_q_multi")
+           "eph_interp_q_multi", "eph_tune_file", "eph_tuning")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGES = ("phase", "ft_q", "eig", "mode", "ft_k", "band", "adj", "tc")
 
@@ -37,6 +37,21 @@ class EphOptions(ctypes.Structure):
                 ("mixed_scheme", ctypes.c_int), ("eig_plain_fp64", ctypes.c_int), ("async_", ctypes.c_int),
                 ("band_alu", ctypes.c_int),
                 ("gemm_alu", ctypes.c_int)]
+
+
+class TuningInfo(ctypes.Structure):
+    """eph_tuning_info of include/eph.h."""
+    _fields_ = [("q_batch", ctypes.c_int), ("k_tile", ctypes.c_int), ("band_alu", ctypes.c_int),
+                ("gemm_alu", ctypes.c_int), ("source", ctypes.c_int)]
+
+
+def tune_file(path):
+    """eph_tune_file: the process's tuning file (None: none); returns the number of entries read."""
+    lib = load_library()
+    rc = lib.eph_tune_file(None if path is None else str(path).encode())
+    if rc < 0:
+        raise EphError(rc, "eph_tune_file: malformed tuning file")
+    return rc
 
 
 class EphError(RuntimeError):
@@ -93,6 +108,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.eph_sync.restype = i
     lib.eph_autotune.argtypes = [vp, i, dp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.eph_autotune.restype = i
+    lib.eph_tune_file.argtypes = [ctypes.c_char_p]
+    lib.eph_tune_file.restype = i
+    lib.eph_tuning.argtypes = [vp, ctypes.POINTER(TuningInfo)]
+    lib.eph_tuning.restype = i
     lib.eph_linewidths.argtypes = [vp, i, dp, dp, d, d, d, d, dp]
     lib.eph_linewidths.restype = i
     lib.eph_interp_vjp.argtypes = [vp, i, dp, i, dp, vp, dp]
@@ -307,6 +326,13 @@ class Context:
         qb, kt = ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.eph_autotune(self.handle, int(nq), _ptr(qpts), ctypes.byref(qb), ctypes.byref(kt)))
         return qb.value, kt.value
+
+    def tuning(self):
+        """The context's (q_batch, k_tile, band_alu, gemm_alu) and their source (eph_tuning)."""
+        t = TuningInfo()
+        self._check(self.lib.eph_tuning(self.handle, ctypes.byref(t)))
+        return {"q_batch": t.q_batch, "k_tile": t.k_tile, "band_alu": t.band_alu, "gemm_alu": t.gemm_alu,
+                "source": ("none", "timed", "process cache", "file")[t.source]}
 
     def eph_interp_vjp(self, nk, kpts, nq, qpts, grad_g, grad_g_ReRp):
         self._check(self.lib.eph_interp_vjp(self.handle, int(nk), _ptr(kpts), int(nq), _ptr(qpts), _ptr(grad_g),

@@ -198,6 +198,25 @@ cudaError_t launch_loss_terms(double2* Y, long ldy, const double* wk, const doub
   return cudaGetLastError();
 }
 
+// g = 0 on the pairs (q, k) with keep[q nk + k] == 0: pair (q, k) holds `per` elements of `eb` bytes
+// at g + (q sgq + k per) eb (a block of threads per pair; eb = 8 or 16)
+__global__ void k_zero_masked(char* __restrict__ g, int eb, long sgq, long per, int nk, const int* __restrict__ keep) {
+  const long pair = blockIdx.x;
+  if (keep[pair]) return;
+  const long q = pair / nk, k = pair - q * nk;
+  char* base = g + (q * sgq + k * per) * eb;
+  const long words = per * eb / 8;
+  for (long i = threadIdx.x; i < words; i += blockDim.x) reinterpret_cast<unsigned long long*>(base)[i] = 0ULL;
+}
+
+cudaError_t launch_zero_masked(void* g, int eb, long sgq, long per, int nq, int nk, const int* keep, cudaStream_t st) {
+  const long pairs = (long)nq * nk;
+  if (pairs <= 0 || !keep) return cudaSuccess;
+  if ((eb != 8 && eb != 16) || pairs > 2147483647L || (reinterpret_cast<uintptr_t>(g) & 7)) return cudaErrorInvalidValue;
+  k_zero_masked<<<(unsigned)pairs, 128, 0, st>>>(static_cast<char*>(g), eb, sgq, per, nk, keep);
+  return cudaGetLastError();
+}
+
 // out[b][j][i] = conj(in[b][i][j]) for a batch of n x n complex matrices (V^H of eigenvector sets)
 __global__ void k_conj_transpose(const double2* __restrict__ in, int n, long total, double2* __restrict__ out) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -144,7 +144,9 @@ struct eph_ctx {
   // Eq. 9 and the adjoint's gradient GEMM on the tensor cores: digits of g(Re,Rp)^T (per context,
   // again after eph_set_gw), of the q batch's phases, of G1bar^T and of the conjugated phases
   DBuf zG, zGe, zP, zPe, zH, zHe, zQ, zQe;
+  DBuf zM, zMe, zU, zUe;  // the mixed form's large-shape mode rotation: digits of G1 rows and of u
   bool zG_ready = false;
+  int tune_source = 0;  // eph_tuning: 0 not tuned, 1 timed, 2 process cache, 3 tuning file
   cudaEvent_t set_done[2] = {};
   bool set_pending[2] = {false, false};
   int stage_set = 0;
@@ -385,7 +387,7 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair, &ctx->g1in,
                   &ctx->aS2, &ctx->aS1, &ctx->aS0, &ctx->DG, &ctx->sG, &ctx->DP, &ctx->G1f, &ctx->g_stage2,
                   &ctx->est[0], &ctx->est[1], &ctx->ost[0], &ctx->ost[1], &ctx->Pacc, &ctx->UkH, &ctx->zA, &ctx->zAe, &ctx->zB, &ctx->zBe, &ctx->zG, &ctx->zGe, &ctx->zP, &ctx->zPe, &ctx->zH,
-                  &ctx->zHe, &ctx->zQ, &ctx->zQe};
+                  &ctx->zHe, &ctx->zQ, &ctx->zQe, &ctx->zM, &ctx->zMe, &ctx->zU, &ctx->zUe};
   for (DBuf* b : bufs) release(*b);
   for (auto& p : ctx->pending) {
     ctx->pool.push_back(p.a);
@@ -949,6 +951,37 @@ int tc_eq9(eph_ctx* ctx, int qb_cap, int nqb, const double2* Pq, double2* G1) {
   return EPH_OK;
 }
 
+// The mode rotation of large shapes in the mixed form on the FP64-accuracy tensor-core GEMM (it
+// replaces double-float GEMMs; the FP64 form keeps DFMA): for one q,
+//   W_q[e][nu][b] = sum_c u[c][nu] G1[c][e][b],
+// A = the rows (e, b) of G1 (element (r, c) at G1[c ne nb^2 + r]), B = the columns of u; one launch
+// per Re vector e (rows e nb^2 .. e nb^2 + nb^2 - 1 of A) writes W_q's G2 block of that e.
+bool use_tc_mode(const eph_ctx* ctx) {
+  const long rows = (long)ctx->ne * ctx->nb * ctx->nb, kp = (2L * ctx->nm + 31) / 32 * 32;
+  const size_t cap = std::min((size_t)4 << 30, ctx->mem_total ? ctx->mem_total / 16 : (size_t)4 << 30);
+  return ctx->opt.form == EPH_FORM_MIXED && !ctx->opt.gemm_alu && ctx->nm > 16 && 2L * ctx->nm <= 512 &&
+         (size_t)14 * rows * kp <= cap && rows <= 2147483647L;
+}
+
+int tc_mode_rotate(eph_ctx* ctx, int iq, const double2* G1, double2* Wq, long NW) {
+  const int nm = ctx->nm, ne = ctx->ne, nb2 = ctx->nb * ctx->nb;
+  const long rows = (long)ne * nb2;
+  const int Kp = (2 * nm + 31) / 32 * 32;
+  EPH_TRY(ensure(ctx, ctx->zM, (size_t)14 * rows * Kp));
+  EPH_TRY(ensure(ctx, ctx->zMe, (size_t)rows * sizeof(int)));
+  EPH_TRY(ensure(ctx, ctx->zU, (size_t)14 * 2 * nm * Kp));
+  EPH_TRY(ensure(ctx, ctx->zUe, (size_t)2 * nm * sizeof(int)));
+  EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_zdigits_rows(G1, 1, rows, (int)rows, nm, Kp, as<int>(ctx->zMe), ctx->zM.p,
+                                                        ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_zdigits_cols(as<double2>(ctx->uq) + (long)iq * nm * nm, nm, 0, 1, nm, nm, Kp, 0,
+                                                        as<int>(ctx->zUe), ctx->zU.p, ctx->stream));
+  for (int e = 0; e < ne; ++e)
+    EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_tc_zgemm64(ctx->zM.p, rows, e * nb2, nb2, as<int>(ctx->zMe), ctx->zU.p,
+                                                        2 * nm, as<int>(ctx->zUe), Kp, Wq + (long)e * NW, 2 * nm, 1, 0,
+                                                        nb2, 0, ctx->status + 1, ctx->stream));
+  return EPH_OK;
+}
+
 // Per q batch, before the k loop: phases, D(q) -> omega, u; Eq. 9; W_q; on a product k grid
 // (grid_stages) also the first two axis transforms of W_q.
 // g1_in: the caller's G1 of these q points (eph_interp_q_g1), else Eq. 9 runs on the resident slice.
@@ -1005,7 +1038,9 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
       const double2* ut = as<double2>(ctx->ut) + (long)iq * nm * nm;
       const double2* G1 = G1src + (long)iq * p.X;
       double2* Wq = W + (long)iq * ne * p.NW + nb2;
-      if (ctx->opt.form == EPH_FORM_MIXED)  // double-float on the FP32 pipe (~1e-13): the g of this form is c64
+      if (use_tc_mode(ctx))
+        EPH_TRY(tc_mode_rotate(ctx, iq, G1, Wq, p.NW));
+      else if (ctx->opt.form == EPH_FORM_MIXED)  // double-float on the FP32 pipe (~1e-13): the g of this form is c64
         EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_zgemm_df_b2(nm, nb2, nm, ut, nm, 0, 0, G1, (long)ne * nb2, nb2, 0, Wq,
                                                              nb2, p.NW, 0, ne, 1, 0, 0, ctx->stream));
       else
@@ -1092,11 +1127,14 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
                                                       keep));
     return EPH_OK;
   }
+  // large shapes rotate every pair; the screened ones (energy window) are zeroed afterwards
+  const long per = (long)nm * nb2;
   if (use_band_tc(ctx)) {  // mixed form: two batched five-digit tensor-core products
     EPH_TRY(ensure(ctx, ctx->tcband, band_tc_bytes(ctx, (long)nqb * nkt, nkt)));
     EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc(Y, 0, p.NW, nb2, Ukq, Uk, nqb, nkt, nm, nb,
                                                      reinterpret_cast<float2*>(out), sgq, ctx->tcband.p, ctx->tcband.n,
                                                      ctx->status + 1, ctx->stream));
+    if (keep) EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zero_masked(out, 8, sgq, per, nqb, nkt, keep, ctx->stream));
     return EPH_OK;
   }
   double2* T = as<double2>(ctx->Tbuf);
@@ -1123,6 +1161,8 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
                                                         out + (long)iq * sgq + (long)kb * nm * nb2, nb,
                                                         (long)nm * nb2, nb2, nkc, nm, 1, ctx->stream));
     }
+  if (keep)
+    EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zero_masked(out, mixed ? 8 : 16, sgq, per, nqb, nkt, keep, ctx->stream));
   return EPH_OK;
 }
 
@@ -1344,6 +1384,9 @@ int interp_q_mixed(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, dou
                                                          as<double2>(ctx->Uk) + k0 * nb2, nqb, nkt, nm, nb, dst,
                                                          host ? (long)nkt * gcols : (long)nk * gcols, ctx->tcband.p,
                                                          ctx->tcband.n, ctx->status + 1, ctx->stream));
+        if (keep)  // every pair was rotated: the screened ones are zeroed
+          EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_zero_masked(dst, 8, host ? (long)nkt * gcols : (long)nk * gcols,
+                                                               gcols, nqb, nkt, keep, ctx->stream));
         if (host)
           for (int iq = 0; iq < nqb; ++iq)
             EPH_CK(cudaMemcpyAsync(gout + 2L * ((long)(q0 + iq) * nk + k0) * gcols,
@@ -1752,7 +1795,6 @@ extern "C" int eph_interp_q_window(eph_ctx* ctx, int nq, const double* qpts, dou
   if (!ctx) return EPH_EINVAL;
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_interp_q_window before eph_set_k");
   if (nq < 1 || !qpts || !(e_lo <= e_hi)) return fail(ctx, EPH_EINVAL, "eph_interp_q_window: bad arguments");
-  if (ctx->big) return fail(ctx, EPH_ENOTSUP, "eph_interp_q_window: nb, nm <= 16");
   if (!whole_g(ctx)) return fail(ctx, EPH_ESTATE, "eph_interp_q_window on an Rp-slice context");
   const Window w{e_lo, e_hi, keep};
   if (mixed_list(ctx)) {  // the mixed form's tensor-core k-list path
@@ -2222,33 +2264,125 @@ extern "C" int eph_reserve(eph_ctx* ctx, int nq) {
 }
 
 namespace {
+// Autotuner state: the choices per problem shape and device, for the process and, after
+// eph_tune_file, in a text file (one line per entry, appended as entries are timed):
+//   eph-tune 1 <device name, spaces as _> <SMs> <form> <scheme> <grid> <nb> <nm> <ne> <np> <nk> <nq>
+//     : <q_batch> <k_tile> <band_alu> <gemm_alu>
 struct TuneKey {
-  int form, scheme, grid, nb, nm, ne, np, nk, nq;
+  std::string dev;
+  int sms, form, scheme, grid, nb, nm, ne, np, nk, nq;
   bool operator<(const TuneKey& o) const {
-    const int a[9] = {form, scheme, grid, nb, nm, ne, np, nk, nq};
-    const int b[9] = {o.form, o.scheme, o.grid, o.nb, o.nm, o.ne, o.np, o.nk, o.nq};
-    for (int i = 0; i < 9; ++i)
+    if (dev != o.dev) return dev < o.dev;
+    const int a[10] = {sms, form, scheme, grid, nb, nm, ne, np, nk, nq};
+    const int b[10] = {o.sms, o.form, o.scheme, o.grid, o.nb, o.nm, o.ne, o.np, o.nk, o.nq};
+    for (int i = 0; i < 10; ++i)
       if (a[i] != b[i]) return a[i] < b[i];
     return false;
   }
 };
-std::map<TuneKey, std::pair<int, int>> g_tuned;
+struct TuneVal {
+  int q_batch, k_tile, band_alu, gemm_alu, from_file;
+};
+std::map<TuneKey, TuneVal> g_tuned;
+std::string g_tune_path;
 std::mutex g_tune_mutex;
+
+// parses one entry line; false if it is not one
+bool parse_tune_line(const char* line, TuneKey* k, TuneVal* v) {
+  char dev[256];
+  int ver = 0, n = 0;
+  const int got = std::sscanf(line, " eph-tune %d %255s %d %d %d %d %d %d %d %d %d %d : %d %d %d %d %n", &ver, dev, &k->sms,
+                              &k->form, &k->scheme, &k->grid, &k->nb, &k->nm, &k->ne, &k->np, &k->nk, &k->nq,
+                              &v->q_batch, &v->k_tile, &v->band_alu, &v->gemm_alu, &n);
+  if (got != 16 || ver != 1) return false;
+  for (const char* c = line + n; *c; ++c)
+    if (*c != '\n' && *c != '\r' && *c != ' ' && *c != '\t') return false;
+  if (k->sms < 1 || k->nb < 1 || k->nm < 1 || k->nk < 1 || k->nq < 1 || v->q_batch < 0 || v->q_batch > 16 ||
+      v->k_tile < 0 || (v->band_alu & ~1) || (v->gemm_alu & ~1))
+    return false;
+  k->dev = dev;
+  v->from_file = 1;
+  return true;
+}
+
+std::string device_id(int* sms) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    *sms = 0;
+    return "unknown";
+  }
+  *sms = prop.multiProcessorCount;
+  std::string name = prop.name;
+  for (char& c : name)
+    if (c == ' ' || c == '\t') c = '_';
+  return name.empty() ? std::string("unknown") : name;
+}
+
+void apply_tuning(eph_ctx* ctx, const TuneVal& v, int source) {
+  ctx->opt.q_batch = v.q_batch;
+  ctx->opt.k_tile = v.k_tile;
+  ctx->opt.band_alu = v.band_alu;
+  ctx->opt.gemm_alu = v.gemm_alu;
+  ctx->tune_source = source;
+}
 }  // namespace
+
+extern "C" int eph_tune_file(const char* path) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned.clear();
+  g_tune_path = path ? path : "";
+  if (!path) return 0;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return 0;  // created by the first timed entry
+  char line[1024];
+  int count = 0, rc = 0;
+  while (std::fgets(line, sizeof line, f)) {
+    const char* c = line;
+    while (*c == ' ' || *c == '\t') ++c;
+    if (*c == '#' || *c == '\n' || *c == '\r' || *c == 0) continue;
+    TuneKey k;
+    TuneVal v;
+    if (!parse_tune_line(line, &k, &v)) {
+      rc = EPH_EINVAL;
+      break;
+    }
+    g_tuned[k] = v;
+    ++count;
+  }
+  std::fclose(f);
+  if (rc != 0) {
+    g_tuned.clear();
+    return rc;
+  }
+  return count;
+}
+
+extern "C" int eph_tuning(const eph_ctx* ctx, eph_tuning_info* out) {
+  if (!ctx || !out) return EPH_EINVAL;
+  out->q_batch = ctx->opt.q_batch;
+  out->k_tile = ctx->opt.k_tile;
+  out->band_alu = ctx->opt.band_alu;
+  out->gemm_alu = ctx->opt.gemm_alu;
+  out->source = ctx->tune_source;
+  return EPH_OK;
+}
 
 extern "C" int eph_autotune(eph_ctx* ctx, int nq, const double* qpts, int* q_batch_out, int* k_tile_out) {
   if (!ctx) return EPH_EINVAL;
   if (!ctx->k_ready) return fail(ctx, EPH_ESTATE, "eph_autotune before eph_set_k");
   if (nq < 1 || !qpts || !ctx->opt.device_ptrs || ctx->opt.async)
     return fail(ctx, EPH_EINVAL, "eph_autotune needs nq >= 1, device pointers and synchronous mode");
-  const TuneKey key{ctx->opt.form, ctx->opt.mixed_scheme, ctx->has_grid ? 1 : 0, ctx->nb, ctx->nm, ctx->ne, ctx->np,
-                    ctx->nk, nq};
+  int sms = 0;
+  const std::string dev = device_id(&sms);
+  const TuneKey key{dev,      sms,     ctx->opt.form, ctx->opt.mixed_scheme, ctx->has_grid ? 1 : 0, ctx->nb, ctx->nm,
+                    ctx->ne, ctx->np, ctx->nk,        nq};
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
-      ctx->opt.q_batch = it->second.first;
-      ctx->opt.k_tile = it->second.second;
+      apply_tuning(ctx, it->second, it->second.from_file ? 3 : 2);
       if (q_batch_out) *q_batch_out = ctx->opt.q_batch;
       if (k_tile_out) *k_tile_out = ctx->opt.k_tile;
       return EPH_OK;
@@ -2266,51 +2400,83 @@ extern "C" int eph_autotune(eph_ctx* ctx, int nq, const double* qpts, int* q_bat
     cudaFree(g);
     return fail(ctx, EPH_ENOMEM, "eph_autotune probe buffers");
   }
-  const int q0 = ctx->opt.q_batch, k0 = ctx->opt.k_tile;
-  const int qbs[] = {1, 2, 4, 8, 16};
-  const long kts[] = {0, (long)((nk + 1) / 2), (long)((nk + 3) / 4)};
+  const eph_options saved = ctx->opt;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  int rc = EPH_OK;
+  // one candidate: a warm-up call (sizes the workspace), then one timed call
+  auto time_it = [&](float* ms) -> int {
+    int r = eph_interp_q(ctx, nq, qpts, eps, om, g);
+    if (r != EPH_OK) return r;
+    cudaEventRecord(e0, ctx->stream);
+    r = eph_interp_q(ctx, nq, qpts, eps, om, g);
+    cudaEventRecord(e1, ctx->stream);
+    if (r != EPH_OK) return r;
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    return EPH_OK;
+  };
+  // the decomposition: q_batch 1..16 and k tiles of nk, nk/2, nk/4 with the default kernels
+  const int qbs[] = {1, 2, 4, 8, 16};
+  const long kts[] = {0, (long)((nk + 1) / 2), (long)((nk + 3) / 4)};
   float best = 1e30f;
-  int bq = q0, bk = k0, rc = EPH_OK;
+  TuneVal bv{saved.q_batch, saved.k_tile, saved.band_alu, saved.gemm_alu, 0};
   for (int qb : qbs) {
-    if (qb > nq) break;
+    if (qb > nq || rc != EPH_OK) break;
     for (long kt : kts) {
       if (kt != 0 && kt >= nk) continue;
       ctx->opt.q_batch = qb;
       ctx->opt.k_tile = (int)kt;
-      rc = eph_interp_q(ctx, nq, qpts, eps, om, g);  // warm-up: sizes the workspace
-      if (rc != EPH_OK) break;
-      cudaEventRecord(e0, ctx->stream);
-      rc = eph_interp_q(ctx, nq, qpts, eps, om, g);
-      cudaEventRecord(e1, ctx->stream);
-      if (rc != EPH_OK) break;
-      cudaEventSynchronize(e1);
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      if ((rc = time_it(&ms)) != EPH_OK) break;
       if (ms < best) {
         best = ms;
-        bq = qb;
-        bk = (int)kt;
+        bv.q_batch = qb;
+        bv.k_tile = (int)kt;
       }
     }
-    if (rc != EPH_OK) break;
+  }
+  // the kernel variants at that decomposition: the CUDA-core band rotation (band_alu) and the
+  // FP64 DFMA GEMMs (gemm_alu) against their tensor-core forms; a variant must be 3 % faster
+  // to replace the default
+  for (int which = 0; which < 2 && rc == EPH_OK; ++which) {
+    ctx->opt.q_batch = bv.q_batch;
+    ctx->opt.k_tile = bv.k_tile;
+    ctx->opt.band_alu = which == 0 ? 1 - bv.band_alu : bv.band_alu;
+    ctx->opt.gemm_alu = which == 1 ? 1 - bv.gemm_alu : bv.gemm_alu;
+    float ms = 0.f;
+    if ((rc = time_it(&ms)) != EPH_OK) break;
+    if (ms < 0.97f * best) {
+      best = ms;
+      bv.band_alu = ctx->opt.band_alu;
+      bv.gemm_alu = ctx->opt.gemm_alu;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(eps);
   cudaFree(om);
   cudaFree(g);
-  ctx->opt.q_batch = (rc == EPH_OK) ? bq : q0;
-  ctx->opt.k_tile = (rc == EPH_OK) ? bk : k0;
-  if (rc != EPH_OK) return rc;
+  if (rc != EPH_OK) {
+    ctx->opt = saved;
+    return rc;
+  }
+  apply_tuning(ctx, bv, 1);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[key] = {bq, bk};
+    g_tuned[key] = bv;
+    if (!g_tune_path.empty()) {
+      if (FILE* f = std::fopen(g_tune_path.c_str(), "a")) {
+        std::fprintf(f, "eph-tune 1 %s %d %d %d %d %d %d %d %d %d %d : %d %d %d %d\n", dev.c_str(), sms, key.form,
+                     key.scheme, key.grid, key.nb, key.nm, key.ne, key.np, key.nk, key.nq, bv.q_batch, bv.k_tile,
+                     bv.band_alu, bv.gemm_alu);
+        std::fclose(f);
+      }
+    }
   }
-  if (q_batch_out) *q_batch_out = bq;
-  if (k_tile_out) *k_tile_out = bk;
+  if (q_batch_out) *q_batch_out = bv.q_batch;
+  if (k_tile_out) *k_tile_out = bv.k_tile;
   return EPH_OK;
 }
 

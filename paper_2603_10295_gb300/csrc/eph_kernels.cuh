@@ -182,6 +182,9 @@ cudaError_t launch_mode_rotate_adj(const double2* G2b, const double2* u, int nq,
 // (q batch, k tile); c = wk[k][n] / om[q][nu], 0 for om <= omega_min.
 cudaError_t launch_loss_terms(double2* Y, long ldy, const double* wk, const double* om, double omega_min, int nq,
                               int nk, int nm, int nb, double* Lpair, cudaStream_t st);
+// g = 0 on the pairs with keep[q nk + k] == 0 (pair (q, k): per elements of eb = 8 or 16 bytes at
+// element q sgq + k per).
+cudaError_t launch_zero_masked(void* g, int eb, long sgq, long per, int nq, int nk, const int* keep, cudaStream_t st);
 // out[b] = in[b]^H for a batch of n x n complex matrices.
 cudaError_t launch_conj_transpose(const double2* in, int n, long batch, double2* out, cudaStream_t st);
 

@@ -112,6 +112,7 @@ def test_every_entry_point_rejects_a_null_context_without_gpu(lib):
     assert lib.eph_reserve(None, 4) == E
     assert lib.eph_sync(None) == E
     assert lib.eph_autotune(None, 4, None, ctypes.byref(i), ctypes.byref(i)) == E
+    assert lib.eph_tuning(None, ctypes.byref(binding.TuningInfo())) == E
     assert lib.eph_profile(None, 1) == E
     assert lib.eph_profile_read(None, 0, ctypes.byref(ms), ctypes.byref(n)) == E
     assert lib.eph_profile_reset(None) == E
@@ -147,3 +148,26 @@ def test_rp_slice_bounds_checked_without_gpu(lib):
                                        g.ctypes.data, R.ctypes.data, None, R.ctypes.data, None, m.ctypes.data,
                                        begin, count, ctypes.byref(opt), None) == binding.EPH_EINVAL
         assert not h.value
+
+
+def test_tuning_file_is_read_and_checked_without_gpu(tmp_path):
+    # eph_tune_file reads the autotuner's file format on the host (no CUDA call): comments and
+    # entries of any device; a malformed line rejects the file and leaves the cache empty
+    binding.load_library()
+    f = tmp_path / "tune.txt"
+    assert binding.tune_file(f) == 0                 # absent: created by the first timed entry
+    f.write_text("# libeph tuning\n"
+                 "eph-tune 1 NVIDIA_GB300 152 0 0 1 8 6 216 216 64000 4 : 4 0 0 0\n"
+                 "\n"
+                 "eph-tune 1 Other_GPU 80 1 0 0 11 9 144 144 2304 16 : 8 1152 1 0\n")
+    assert binding.tune_file(f) == 2
+    for bad in ("eph-tune 2 X 1 0 0 0 1 1 1 1 1 1 : 1 0 0 0\n",          # unknown version
+                "eph-tune 1 X 1 0 0 0 1 1 1 1 1 1 : 1 0 0 2\n",          # gemm_alu not 0/1
+                "eph-tune 1 X 1 0 0 0 1 1 1 1 1 1 : 1 0 0 0 extra\n",    # trailing text
+                "eph-tune 1 X 1 0 0 0 1 1 1 1 1 1 : 17 0 0 0\n",         # q_batch above 16
+                "eph-tune 1 X 1 0 0 0 1 1 1 1 1\n"):                     # truncated
+        f.write_text(bad)
+        with pytest.raises(binding.EphError) as ei:
+            binding.tune_file(f)
+        assert ei.value.code == binding.EPH_EINVAL
+    assert binding.tune_file(None) == 0

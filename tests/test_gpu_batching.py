@@ -94,6 +94,8 @@ def test_autotune_picks_valid_tiles_and_keeps_results():
     ctx2 = binding.Context.from_workload(wl, device_ptrs=True, stream=torch.cuda.current_stream())
     ctx2.eph_set_k(nk, torch.from_numpy(wl.kpts).to(dev))
     assert ctx2.eph_autotune(6, q) == (qb, kt)
+    assert ctx2.tuning()["source"] == "process cache"
+    assert ctx2.tuning() == dict(ctx.tuning(), source="process cache")
     # and the results still match the oracle
     ref = oracle.interpolate(wl)
     assert gauge.max_rel_S(bufs1[2].cpu().numpy(), ref[3], ref[0], ref[1], ref[2]) <= 1e-12
@@ -171,3 +173,36 @@ def test_multi_material_call_in_a_graph_and_errors():
     with pytest.raises(binding.EphError) as ei:
         binding.interp_q_multi([ctxs[0], ctxs[0]], [2, 2], [q, q])
     assert ei.value.code == binding.EPH_EINVAL
+
+
+def test_autotune_file_round_trip(tmp_path):
+    # a timed choice (decomposition and kernel variants) goes to the tuning file; after the file
+    # is set again (the process cache cleared), a new context of the same shape takes it from there
+    import torch
+    dev = torch.device("cuda:0")
+    wl = synth.make_workload("si_tiny", nk=96, nq=6)
+    f = tmp_path / "tune.txt"
+    assert binding.tune_file(f) == 0
+    try:
+        ctx = binding.Context.from_workload(wl, device_ptrs=True, stream=torch.cuda.current_stream())
+        ctx.eph_set_k(len(wl.kpts), torch.from_numpy(wl.kpts).to(dev))
+        q = torch.from_numpy(wl.qpts).to(dev)
+        ctx.eph_autotune(6, q)
+        t1 = ctx.tuning()
+        assert t1["source"] == "timed"
+        assert len(f.read_text().splitlines()) == 1
+        assert binding.tune_file(f) == 1
+        ctx2 = binding.Context.from_workload(wl, device_ptrs=True, stream=torch.cuda.current_stream())
+        ctx2.eph_set_k(len(wl.kpts), torch.from_numpy(wl.kpts).to(dev))
+        ctx2.eph_autotune(6, q)
+        assert ctx2.tuning() == dict(t1, source="file")
+        # the tuned context still matches the oracle
+        e = torch.empty(6, len(wl.kpts), wl.nb, dtype=torch.float64, device=dev)
+        o = torch.empty(6, wl.nm, dtype=torch.float64, device=dev)
+        g = torch.empty(6, len(wl.kpts), wl.nm, wl.nb, wl.nb, dtype=torch.complex128, device=dev)
+        ctx2.eph_interp_q(6, q, e, o, g)
+        torch.cuda.synchronize()
+        ref = oracle.interpolate(wl)
+        assert gauge.max_rel_S(g.cpu().numpy(), ref[3], ref[0], ref[1], ref[2]) <= 1e-12
+    finally:
+        binding.tune_file(None)

@@ -77,12 +77,15 @@ def test_mixed_large_odd_row_length():
 
 
 def test_large_shapes_rejected_where_not_supported():
-    # the energy-window call keeps its warp-resident kernels: nb, nm <= 16
+    # the persistent multi-material rotation keeps its warp-resident kernel: nb, nm <= 16
+    import torch
+    dev = torch.device("cuda:0")
     wl = synth.make_workload("si_tiny", nb=20, nk=4, nq=2)
-    ctx = binding.Context.from_workload(wl)
-    ctx.set_k_window(wl.kpts, -1e3, 1e3)
+    ctx = binding.Context.from_workload(wl, device_ptrs=True, stream=torch.cuda.current_stream())
+    ctx.eph_set_k(len(wl.kpts), torch.from_numpy(wl.kpts).to(dev))
+    q = torch.from_numpy(wl.qpts).to(dev)
     with pytest.raises(binding.EphError) as ei:
-        ctx.interp_q_window(wl.qpts, -1e3, 1e3)
+        binding.interp_q_multi([ctx], [2], [q])
     assert ei.value.code == binding.EPH_ENOTSUP
 
 

@@ -164,8 +164,28 @@ def test_window_errors():
     with pytest.raises(binding.EphError) as ei:
         ctx.set_k_window(wl.kpts, 1.0, 0.0)
     assert ei.value.code == binding.EPH_EINVAL
-    big = binding.Context.from_workload(synth.make_workload("si_tiny", nb=20, nk=4, nq=2), form="mixed")
-    big.set_k(wl.kpts[:4])
     with pytest.raises(binding.EphError) as ei:
-        big.interp_q_window(wl.qpts, -1.0, 1.0)
-    assert ei.value.code == binding.EPH_ENOTSUP
+        ctx.interp_q_window(wl.qpts, -1.0, 1.0)   # before eph_set_k
+    assert ei.value.code == binding.EPH_ESTATE
+
+
+@pytest.mark.parametrize("form,nb,na", [("fp64", 20, 2), ("fp64", 8, 7), ("mixed", 20, 2)])
+def test_pair_screening_large_shapes(form, nb, na):
+    # nb or nm > 16: every pair is rotated (GEMMs, or the mixed form's tensor-core products) and
+    # the screened ones are zeroed afterwards; eps_kq, omega and the kept g match the unscreened call
+    wl = synth.make_workload("si_tiny", nb=nb, na=na, nk=24, nq=4)
+    ref = oracle.interpolate(wl)
+    lo, hi = gap_window(np.concatenate([ref[0].ravel(), ref[1].ravel()]), 30, 32, min_gap=1e-8)
+    expect = ((ref[1] >= lo) & (ref[1] <= hi)).any(axis=2).astype(np.int32)
+    assert 0 < expect.sum() < expect.size
+    ctx = binding.Context.from_workload(wl, form=form, q_batch=3, k_tile=10)
+    ctx.set_k(wl.kpts)
+    e_kq, om, g, keep = ctx.interp_q_window(wl.qpts, lo, hi)
+    assert np.array_equal(keep, expect)
+    full = binding.Context.from_workload(wl, form=form, q_batch=3, k_tile=10)
+    full.set_k(wl.kpts)
+    e_f, om_f, g_f = full.interp_q(wl.qpts)
+    assert np.array_equal(e_kq, e_f) and np.array_equal(om, om_f)
+    m = keep.astype(bool)
+    assert np.array_equal(g[m], g_f[m])
+    assert not np.any(g[~m])
