@@ -982,6 +982,20 @@ int tc_mode_rotate(eph_ctx* ctx, int iq, const double2* G1, double2* Wq, long NW
   return EPH_OK;
 }
 
+// One axis transform of the sum factorisation: the double-float kernel for a paired (whole,
+// unshifted) axis unless gemm_alu asks for FP64 DFMA, the FP64 kernel otherwise.  Its error,
+// ~2^-47 of each term, grows with the slot count B: the FP64 form takes it for B <= 9 (the
+// silicon box, B = 7: 9e-14 of the pair maximum against DFMA) and keeps DFMA beyond (the MoS2 box,
+// B = 13, measured 5.9e-13, too close to the form's 1e-12); the mixed form takes it for any B.
+cudaError_t axis_dft(eph_ctx* ctx, const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
+                     int nj, int paired, double2* out, long sa_out) {
+  const size_t df_smem = (size_t)(N / 2 + 1) * (B > 1 ? (B - 1) / 2 : 1) * 16;
+  const bool df_ok = ctx->opt.form == EPH_FORM_MIXED || B <= 9;
+  if (paired && df_ok && !ctx->opt.gemm_alu && j0 == 0 && nj == N && df_smem <= 48 * 1024)
+    return eph::launch_axis_dft_df(in, sa_in, A, C, B, E, N, out, sa_out, ctx->stream);
+  return eph::launch_axis_dft(in, sa_in, A, C, B, E, N, j0, nj, paired, out, sa_out, ctx->stream);
+}
+
 // Per q batch, before the k loop: phases, D(q) -> omega, u; Eq. 9; W_q; on a product k grid
 // (grid_stages) also the first two axis transforms of W_q.
 // g1_in: the caller's G1 of these q points (eph_interp_q_g1), else Eq. 9 runs on the resident slice.
@@ -1058,13 +1072,12 @@ int q_prelude(eph_ctx* ctx, const QPlan& p, const double* qb, int nqb, bool grid
     EPH_CK(cudaMemsetAsync(ctx->Wbox.p, 0, (size_t)nqb * vol * NW * sizeof(double2), ctx->stream));
     EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_box_scatter(W, (long)ne * NW, NW, ne, (int)NW, as<int>(ctx->rebox),
                                                          ctx->we, as<double2>(ctx->Wbox), vol * NW, nqb, ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_axis_dft(as<double2>(ctx->Wbox), (long)B3 * NW, nqb * B1 * B2, NW, B3,
-                                                      as<double2>(ctx->E3), N3, 0, N3, ctx->gshift[2] == 0.0,
-                                                      as<double2>(ctx->S1), (long)N3 * NW, ctx->stream));
-    EPH_LAUNCH_S(EPH_STAGE_MODE, eph::launch_axis_dft(as<double2>(ctx->S1), (long)B2 * N3 * NW, nqb * B1,
-                                                      (long)N3 * NW, B2, as<double2>(ctx->E2), N2, 0, N2,
-                                                      ctx->gshift[1] == 0.0, as<double2>(ctx->S2),
-                                                      (long)N2 * N3 * NW, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_MODE, axis_dft(ctx, as<double2>(ctx->Wbox), (long)B3 * NW, nqb * B1 * B2, NW, B3,
+                                          as<double2>(ctx->E3), N3, 0, N3, ctx->gshift[2] == 0.0,
+                                          as<double2>(ctx->S1), (long)N3 * NW));
+    EPH_LAUNCH_S(EPH_STAGE_MODE, axis_dft(ctx, as<double2>(ctx->S1), (long)B2 * N3 * NW, nqb * B1, (long)N3 * NW, B2,
+                                          as<double2>(ctx->E2), N2, 0, N2, ctx->gshift[1] == 0.0,
+                                          as<double2>(ctx->S2), (long)N2 * N3 * NW));
   }
   return EPH_OK;
 }
@@ -1205,9 +1218,8 @@ int k_tile_forward(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
     const int j0 = (int)(k0 / slab), nj = (int)(nkt / slab), B1 = ctx->bext[0], N1 = ctx->gn[0];
     const long C = slab * p.NW;
     const int paired = ctx->gshift[0] == 0.0 && j0 == 0 && nj == N1;
-    EPH_LAUNCH_S(EPH_STAGE_FT_K, eph::launch_axis_dft(as<double2>(ctx->S2), (long)B1 * C, nqb, C, B1,
-                                                      as<double2>(ctx->E1), N1, j0, nj, paired, Y,
-                                                      (long)nkt * p.NW, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_FT_K, axis_dft(ctx, as<double2>(ctx->S2), (long)B1 * C, nqb, C, B1, as<double2>(ctx->E1),
+                                          N1, j0, nj, paired, Y, (long)nkt * p.NW));
   } else if (use_tc_rek(ctx)) {
     EPH_TRY(tc_rek_tile(ctx, p, nqb, k0, nkt));
   } else {
@@ -1828,16 +1840,28 @@ int adj_workspace(eph_ctx* ctx, const QPlan& p) {
   return EPH_OK;
 }
 
+// One adjoint axis transform: the paired kernel over a whole unshifted axis, else the general one.
+cudaError_t axis_adj(eph_ctx* ctx, const double2* in, long sa_in, long sj_in, long ldr_in, int A, int R, int CC, int B,
+                     const double2* E, int N, int j0, int nj, bool unshifted, double2* out, long sa_out, long sb_out,
+                     long ldr_out, int accumulate) {
+  const size_t smem = (size_t)(N / 2 + 1) * (B > 1 ? (B - 1) / 2 : 1) * sizeof(double2);
+  if (unshifted && j0 == 0 && nj == N && smem <= 48 * 1024)
+    return eph::launch_axis_adj_paired(in, sa_in, sj_in, ldr_in, A, R, CC, B, E, N, out, sa_out, sb_out, ldr_out,
+                                       accumulate, ctx->stream);
+  return eph::launch_axis_adj(in, sa_in, sj_in, ldr_in, A, R, CC, B, E, j0, nj, out, sa_out, sb_out, ldr_out, accumulate,
+                              ctx->stream);
+}
+
 int adj_k_tile(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt, const double2* Pk, double2* G2b) {
   double2* Y = as<double2>(ctx->Y);
   const int nb2 = ctx->nb * ctx->nb, ne = ctx->ne;
   if (ctx->has_grid) {
     const long slab = (long)ctx->gn[1] * ctx->gn[2];
     const int j0 = (int)(k0 / slab), nj = (int)(nkt / slab), B1 = ctx->bext[0];
-    EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_axis_adj(Y + nb2, (long)nkt * p.NW, slab * p.NW, p.NW, nqb, (int)slab,
-                                                     (int)p.gcols, B1, as<double2>(ctx->E1), j0, nj,
-                                                     as<double2>(ctx->aS2), (long)B1 * slab * p.gcols,
-                                                     slab * p.gcols, p.gcols, k0 > 0, ctx->stream));
+    EPH_LAUNCH_S(EPH_STAGE_ADJ, axis_adj(ctx, Y + nb2, (long)nkt * p.NW, slab * p.NW, p.NW, nqb, (int)slab,
+                                         (int)p.gcols, B1, as<double2>(ctx->E1), ctx->gn[0], j0, nj,
+                                         ctx->gshift[0] == 0.0, as<double2>(ctx->aS2), (long)B1 * slab * p.gcols,
+                                         slab * p.gcols, p.gcols, k0 > 0));
     return EPH_OK;
   }
   EPH_LAUNCH_S(EPH_STAGE_ADJ, launch_zgemm_ah(ne, (int)p.gcols, nkt, Pk + k0 * ne, ne, 0, Y + nb2, p.NW,
@@ -1852,13 +1876,12 @@ int adj_k_finish(eph_ctx* ctx, const QPlan& p, int nqb, double2* G2b, bool weigh
   const int B1 = ctx->bext[0], B2 = ctx->bext[1], B3 = ctx->bext[2];
   const int N2 = ctx->gn[1], N3 = ctx->gn[2];
   const long C = p.gcols;
-  EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_axis_adj(as<double2>(ctx->aS2), (long)N2 * N3 * C, (long)N3 * C, 0,
-                                                   nqb * B1, 1, (int)(N3 * C), B2, as<double2>(ctx->E2), 0, N2,
-                                                   as<double2>(ctx->aS1), (long)B2 * N3 * C, (long)N3 * C, 0, 0,
-                                                   ctx->stream));
-  EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_axis_adj(as<double2>(ctx->aS1), (long)N3 * C, C, 0, nqb * B1 * B2, 1,
-                                                   (int)C, B3, as<double2>(ctx->E3), 0, N3, as<double2>(ctx->aS0),
-                                                   (long)B3 * C, C, 0, 0, ctx->stream));
+  EPH_LAUNCH_S(EPH_STAGE_ADJ, axis_adj(ctx, as<double2>(ctx->aS2), (long)N2 * N3 * C, (long)N3 * C, 0, nqb * B1, 1,
+                                       (int)(N3 * C), B2, as<double2>(ctx->E2), N2, 0, N2, ctx->gshift[1] == 0.0,
+                                       as<double2>(ctx->aS1), (long)B2 * N3 * C, (long)N3 * C, 0, 0));
+  EPH_LAUNCH_S(EPH_STAGE_ADJ, axis_adj(ctx, as<double2>(ctx->aS1), (long)N3 * C, C, 0, nqb * B1 * B2, 1, (int)C, B3,
+                                       as<double2>(ctx->E3), N3, 0, N3, ctx->gshift[2] == 0.0, as<double2>(ctx->aS0),
+                                       (long)B3 * C, C, 0, 0));
   const long vol = (long)B1 * B2 * B3;
   EPH_LAUNCH_S(EPH_STAGE_ADJ, eph::launch_box_gather(as<double2>(ctx->aS0), vol * C, (int)C, as<int>(ctx->rebox),
                                                      weighted ? ctx->we : nullptr, ctx->ne, G2b, (long)ctx->ne * C,

@@ -126,11 +126,21 @@ cudaError_t launch_box_scatter(const double2* W, long sWq, long ldw, int ne, int
 cudaError_t launch_axis_adj(const double2* in, long sa_in, long sj_in, long ldr_in, int A, int R, int CC, int B,
                             const double2* E, int j0, int nj, double2* out, long sa_out, long sb_out, long ldr_out,
                             int accumulate, cudaStream_t st);
+// The same over a whole unshifted axis (j0 = 0, nj = N): the conjugate symmetries of E in j and in
+// the slots leave a quarter of the FP64 operations.
+cudaError_t launch_axis_adj_paired(const double2* in, long sa_in, long sj_in, long ldr_in, int A, int R, int CC, int B,
+                                   const double2* E, int N, double2* out, long sa_out, long sb_out, long ldr_out,
+                                   int accumulate, cudaStream_t st);
 // G[q][e][c] = w_e Sbox[q][box[e]][c]  (adjoint of the box scatter; we = NULL: weights 1)
 cudaError_t launch_box_gather(const double2* Sbox, long sBq, int ncols, const int* box, const double* we, int ne,
                               double2* G, long sGq, int nq, cudaStream_t st);
 cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
                             int nj, int paired, double2* out, long sa_out, cudaStream_t st);
+// The paired transform (whole unshifted axis, j0 = 0, nj = N) in double-float arithmetic on the
+// FP32 pipe (~2^-46 of each output's largest term; ~2 FP64 operations per output for the splits
+// and joins instead of ~8).
+cudaError_t launch_axis_dft_df(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N,
+                               double2* out, long sa_out, cudaStream_t st);
 
 // ---- energy-window prescreening (screen.cu) ------------------------------------------------
 // idx[0..*count) = ascending k with some eps[k][n] in [e_lo, e_hi]; flag, pos [nk], tot [ceil(nk/1024)]

@@ -134,6 +134,132 @@ __global__ void __launch_bounds__(256) k_axis_dft(const double2* __restrict__ in
   }
 }
 
+// The paired transform in double-float arithmetic on the FP32 pipe (GB300's FP64 unit runs at
+// ~1/64 of its FP32 rate): every FP64 value is split into a float pair (hi, lo), hi the nearest
+// float and lo the nearest float to the remainder (48 significant bits, relative 2^-48), products
+// are formed exactly with an FMA (two-product) and accumulated with error-free two-sums, and each
+// output is joined back to a double.  The splits and joins take the integer-operation conversions
+// below plus one FP64 addition per real value: ~2 FP64 operations per output instead of ~8.
+// Accuracy ~2^-46 of the largest term of each output (the FP64 kernel: ~2^-53).
+namespace {
+__device__ __forceinline__ float d2f_rn_i(double x) {  // nearest float (normal range), integer operations
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) + (1ULL << 28);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned mag = __funnelshift_l(lo, hi, 3) - (896u << 23);
+  return (e > 896u && e < 1151u) ? __uint_as_float(mag | (hi & 0x80000000u)) : 0.f;
+}
+__device__ __forceinline__ double f2d_exact_i(float x) {  // exact, integer operations
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u) return 0.0;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_split(double x) {
+  const float h = d2f_rn_i(x);
+  return DF{h, d2f_rn_i(x - f2d_exact_i(h))};
+}
+__device__ __forceinline__ double df_join(float s, float t) { return f2d_exact_i(s) + f2d_exact_i(t); }
+// (S, T) += a b: the product's rounding error from an FMA, the sum's from a two-sum
+__device__ __forceinline__ void df_fma(float& S, float& T, DF a, DF b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float pe = __fmaf_rn(a.h, b.h, -p);
+  const float t = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, pe));
+  const float s = __fadd_rn(S, p);
+  const float bb = __fsub_rn(s, S);
+  const float e = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  S = s;
+  T = __fadd_rn(T, __fadd_rn(e, t));
+}
+// (S1, T1) + sg (S2, T2) joined to a double (sg = +-1)
+__device__ __forceinline__ double df_addj(float S1, float T1, float S2, float T2, float sg) {
+  const float b2 = sg * S2;
+  const float s = __fadd_rn(S1, b2);
+  const float bb = __fsub_rn(s, S1);
+  const float e = __fadd_rn(__fsub_rn(S1, __fsub_rn(s, bb)), __fsub_rn(b2, bb));
+  return df_join(s, __fadd_rn(__fadd_rn(T1, sg * T2), e));
+}
+}  // namespace
+
+template <int BMAX>
+__global__ void __launch_bounds__(256) k_axis_dft_df(const double2* __restrict__ in, long sa_in, long C,
+                                                     const double2* __restrict__ E, int N,
+                                                     double2* __restrict__ out, long sa_out) {
+  constexpr int MM = (BMAX - 1) / 2;
+  extern __shared__ float4 ef[];  // [N / 2 + 1][MM]: (cos hi, cos lo, sin hi, sin lo) of slot 2m - 1
+  const int a = blockIdx.y;
+  const int nh = N / 2 + 1;
+  for (int t = threadIdx.x; t < nh * MM; t += blockDim.x) {
+    const int j = t / MM, m = t - j * MM + 1;
+    const double2 w = E[(long)j * BMAX + 2 * m - 1];
+    const DF c = df_split(w.x), sn = df_split(w.y);
+    ef[t] = make_float4(c.h, c.l, sn.h, sn.l);
+  }
+  __syncthreads();
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const double2* src = in + (long)a * sa_in + c;
+  DF x0r, x0i, ur[MM > 0 ? MM : 1], ui[MM > 0 ? MM : 1], wr[MM > 0 ? MM : 1], wi[MM > 0 ? MM : 1];
+  {
+    const double2 v0 = src[0];
+    x0r = df_split(v0.x);
+    x0i = df_split(v0.y);
+#pragma unroll
+    for (int m = 1; m <= MM; ++m) {
+      const double2 p = src[(long)(2 * m - 1) * C], q = src[(long)(2 * m) * C];
+      ur[m - 1] = df_split(p.x + q.x);
+      ui[m - 1] = df_split(p.y + q.y);
+      wr[m - 1] = df_split(p.x - q.x);
+      wi[m - 1] = df_split(p.y - q.y);
+    }
+  }
+  double2* dst = out + (long)a * sa_out + c;
+  for (int j = 0; 2 * j <= N; ++j) {
+    float arS = x0r.h, arT = x0r.l, aiS = x0i.h, aiT = x0i.l, brS = 0.f, brT = 0.f, biS = 0.f, biT = 0.f;
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      const float4 w = ef[j * MM + m];
+      const DF cm{w.x, w.y}, sm{w.z, w.w};
+      df_fma(arS, arT, cm, ur[m]);
+      df_fma(aiS, aiT, cm, ui[m]);
+      df_fma(brS, brT, sm, wr[m]);
+      df_fma(biS, biT, sm, wi[m]);
+    }
+    dst[(long)j * C] = make_double2(df_addj(arS, arT, biS, biT, -1.f), df_addj(aiS, aiT, brS, brT, 1.f));
+    const int jm = N - j;
+    if (j != 0 && jm != j)
+      dst[(long)jm * C] = make_double2(df_addj(arS, arT, biS, biT, 1.f), df_addj(aiS, aiT, brS, brT, -1.f));
+  }
+}
+
+cudaError_t launch_axis_dft_df(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N,
+                               double2* out, long sa_out, cudaStream_t st) {
+  if (A <= 0 || C <= 0) return cudaSuccess;
+  if (B < 1 || B > 33 || (B & 1) == 0 || A > 65535) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)(N / 2 + 1) * ((B - 1) / 2 > 0 ? (B - 1) / 2 : 1) * sizeof(float4);
+  if (smem > 48 * 1024) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((C + 255) / 256), (unsigned)A, 1);
+  auto go = [&](auto kern) -> cudaError_t {
+    kern<<<grid, 256, smem, st>>>(in, sa_in, C, E, N, out, sa_out);
+    return cudaGetLastError();
+  };
+  switch (B) {
+#define EPH_AXIS_B(V) \
+  case V:             \
+    return go(k_axis_dft_df<V>);
+    EPH_AXIS_B(1) EPH_AXIS_B(3) EPH_AXIS_B(5) EPH_AXIS_B(7) EPH_AXIS_B(9) EPH_AXIS_B(11) EPH_AXIS_B(13)
+    EPH_AXIS_B(15) EPH_AXIS_B(17) EPH_AXIS_B(19) EPH_AXIS_B(21) EPH_AXIS_B(23) EPH_AXIS_B(25) EPH_AXIS_B(27)
+    EPH_AXIS_B(29) EPH_AXIS_B(31) EPH_AXIS_B(33)
+#undef EPH_AXIS_B
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
                             int nj, int paired, double2* out, long sa_out, cudaStream_t st) {
   if (A <= 0 || C <= 0 || nj <= 0) return cudaSuccess;
@@ -208,6 +334,101 @@ __global__ void __launch_bounds__(256) k_axis_adj(const double2* __restrict__ in
   }
 #pragma unroll
   for (int b = 0; b < BMAX; ++b) dst[(long)b * sb_out] = make_double2(ar[b], ai[b]);
+}
+
+// The same adjoint over a whole unshifted axis (j0 = 0, nj = N, symmetric slots): E[N - j] =
+// conj(E[j]) and slot 2m holds conj of slot 2m - 1, so with S = x_j + x_{N-j}, D = x_{N-j} - x_j
+// (S = x_j, D = -x_j when j has no partner) and (c, s) = E[j][2m - 1],
+//   out[2m - 1] += c S + i s D,  out[2m] += c S - i s D,  out[0] += S:
+// two real products per complex term for two slots and two j, a quarter of the FP64 operations.
+template <int BMAX>
+__global__ void __launch_bounds__(256) k_axis_adj_paired(const double2* __restrict__ in, long sa_in, long sj_in,
+                                                         long ldr_in, int R, int CC, const double2* __restrict__ E,
+                                                         int N, double2* __restrict__ out, long sa_out, long sb_out,
+                                                         long ldr_out, int accumulate) {
+  constexpr int MM = (BMAX - 1) / 2;
+  extern __shared__ double2 eo[];  // [N / 2 + 1][MM]: E[j][2m - 1]
+  const int a = blockIdx.y;
+  const int nh = N / 2 + 1;
+  for (int t = threadIdx.x; t < nh * MM; t += blockDim.x) {
+    const int j = t / MM, m = t - j * MM + 1;
+    eo[t] = E[(long)j * BMAX + 2 * m - 1];
+  }
+  __syncthreads();
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)R * CC) return;
+  const int r = (int)(idx / CC), c = (int)(idx - (long)r * CC);
+  double pr[MM > 0 ? MM : 1], pi[MM > 0 ? MM : 1], qr[MM > 0 ? MM : 1], qi[MM > 0 ? MM : 1];
+#pragma unroll
+  for (int m = 0; m < MM; ++m) pr[m] = pi[m] = qr[m] = qi[m] = 0.0;
+  double s0r = 0.0, s0i = 0.0;
+  const double2* src = in + (long)a * sa_in + (long)r * ldr_in + c;
+  for (int j = 0; 2 * j <= N; ++j) {
+    const int jm = N - j;
+    const double2 x = src[(long)j * sj_in];
+    double Sr = x.x, Si = x.y, Dr = -x.x, Di = -x.y;
+    if (j != 0 && jm != j) {
+      const double2 y = src[(long)jm * sj_in];
+      Sr = x.x + y.x;
+      Si = x.y + y.y;
+      Dr = y.x - x.x;
+      Di = y.y - x.y;
+    }
+    s0r += Sr;
+    s0i += Si;
+    const double2* e = eo + j * MM;
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      const double2 w = e[m];
+      pr[m] = fma(w.x, Sr, pr[m]);
+      pi[m] = fma(w.x, Si, pi[m]);
+      qr[m] = fma(w.y, Dr, qr[m]);
+      qi[m] = fma(w.y, Di, qi[m]);
+    }
+  }
+  double2* dst = out + (long)a * sa_out + (long)r * ldr_out + c;
+  auto put = [&](int b, double vr, double vi) {
+    double2* o = dst + (long)b * sb_out;
+    if (accumulate) {
+      const double2 v = *o;
+      vr += v.x;
+      vi += v.y;
+    }
+    *o = make_double2(vr, vi);
+  };
+  put(0, s0r, s0i);
+#pragma unroll
+  for (int m = 0; m < MM; ++m) {
+    put(2 * m + 1, pr[m] - qi[m], pi[m] + qr[m]);  // c S + i s D
+    put(2 * m + 2, pr[m] + qi[m], pi[m] - qr[m]);  // c S - i s D
+  }
+}
+
+cudaError_t launch_axis_adj_paired(const double2* in, long sa_in, long sj_in, long ldr_in, int A, int R, int CC, int B,
+                                   const double2* E, int N, double2* out, long sa_out, long sb_out, long ldr_out,
+                                   int accumulate, cudaStream_t st) {
+  if (A <= 0 || R <= 0 || CC <= 0 || N <= 0) return cudaSuccess;
+  if (B < 1 || B > 33 || (B & 1) == 0 || A > 65535) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)(N / 2 + 1) * (B > 1 ? (B - 1) / 2 : 1) * sizeof(double2);
+  if (smem > 48 * 1024) return cudaErrorInvalidValue;
+  const long cols = (long)R * CC;
+  const dim3 grid((unsigned)((cols + 255) / 256), (unsigned)A, 1);
+  auto go = [&](auto kern) -> cudaError_t {
+    kern<<<grid, 256, smem, st>>>(in, sa_in, sj_in, ldr_in, R, CC, E, N, out, sa_out, sb_out, ldr_out, accumulate);
+    return cudaGetLastError();
+  };
+  switch (B) {
+#define EPH_AXIS_ADJ_B(V) \
+  case V:                 \
+    return go(k_axis_adj_paired<V>);
+    EPH_AXIS_ADJ_B(1) EPH_AXIS_ADJ_B(3) EPH_AXIS_ADJ_B(5) EPH_AXIS_ADJ_B(7) EPH_AXIS_ADJ_B(9) EPH_AXIS_ADJ_B(11)
+    EPH_AXIS_ADJ_B(13) EPH_AXIS_ADJ_B(15) EPH_AXIS_ADJ_B(17) EPH_AXIS_ADJ_B(19) EPH_AXIS_ADJ_B(21)
+    EPH_AXIS_ADJ_B(23) EPH_AXIS_ADJ_B(25) EPH_AXIS_ADJ_B(27) EPH_AXIS_ADJ_B(29) EPH_AXIS_ADJ_B(31)
+    EPH_AXIS_ADJ_B(33)
+#undef EPH_AXIS_ADJ_B
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_axis_adj(const double2* in, long sa_in, long sj_in, long ldr_in, int A, int R, int CC, int B,

@@ -90,16 +90,21 @@ def test_backward_on_a_k_list_with_tensor_core_rek():
 
 # Eq. 9 (G1 = P_q g(Re,Rp)) and the adjoint's gradient GEMM (grad += P_q^H G1bar) take the same
 # tensor-core GEMM: against the DFMA kernels of the same context (option gemm_alu)
-def test_eq9_tensor_core_against_dfma_on_the_grid():
-    wl = synth.make_workload("mos2_diff", nq=5)
+# on a uniform grid gemm_alu also selects the FP64 axis transforms of the sum factorisation
+# instead of their double-float form (whole unshifted axes of at most 9 slots in the FP64 form:
+# the silicon boxes here; the 13-slot MoS2 box keeps FP64 transforms)
+@pytest.mark.parametrize("name,grid", [("mos2_diff", None), ("si_tiny", (4, 5, 6)), ("si_tiny", (3, 3, 3))])
+def test_eq9_tensor_core_against_dfma_on_the_grid(name, grid):
+    wl = synth.make_workload(name, nq=5)
+    grid = grid or wl.kgrid
     out = []
     for alu in (False, True):
         ctx = binding.Context.from_workload(wl, q_batch=3, gemm_alu=alu)
-        eps_k = ctx.set_k_grid(*wl.kgrid)
+        eps_k = ctx.set_k_grid(*grid)
         out.append((eps_k,) + ctx.interp_q(wl.qpts))
     assert np.abs(out[0][1] - out[1][1]).max() <= 1e-13 * np.abs(out[1][1]).max()
     d = pair_rel(out[0][3], out[1][3])
-    print(f"Eq. 9 tensor cores vs DFMA: g {d:.3g}")
+    print(f"{name} {grid}: tensor-core Eq. 9 and double-float axes vs DFMA: g {d:.3g}")
     assert d <= 1e-12
 
 
