@@ -491,7 +491,7 @@ def time_form(wl, form, args, q_dev, k_dev, rank, world, local, dev, QB, use_gri
     setk_share_ms = setk_ms * (args.steps * QB) / len(wl.qpts)
     out = dict(value=world * units_rank / ((el_ms + setk_share_ms) * 1e-3), ms_per_step=el_ms / args.steps,
                setk_ms=setk_ms, setk_share_ms=setk_share_ms, launches=launches, prof=prof, clocks=clk,
-               g_bytes=g.numel() * g.element_size())
+               g_bytes=g.numel() * g.element_size(), form=form)
     del g, eps_kq, om
     torch.cuda.empty_cache()
     return out
@@ -838,10 +838,24 @@ def run_libeph(args):
         outs = float(args.steps) * QB * nk * NW / max(ft_n, 1)
         t = ft_ms / max(ft_n, 1) * 1e-3
         ach = (4 * M + 2) * outs / t
+        algo = 16.0 * outs * (1 + (2 * M + 1) / float(wl.kgrid[0]))
+        if r.get("form") == "mixed" or 2 * M + 1 <= 9:
+            # the double-float kernel (k_axis_dft_df, FP32 pipe): its floor is the HBM traffic
+            peak = peaks.get("hbm_gbs")
+            gbs = algo / t / 1e9
+            return {"bound": "hbm",
+                    "kernel": "k_axis_dft_df (axis 1 of the sum-factorised Re->k contraction, double-float on the "
+                              "FP32 pipe)",
+                    "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak if peak else None,
+                    "algorithmic_bytes": algo, "outputs_per_launch": outs,
+                    "fp64_equivalent_tflops": ach / 1e12, "flop_per_output": 4 * M + 2,
+                    "note": "algorithmic bytes: the slot columns read once, the outputs written once (16 B each); "
+                            "the FP64 kernel k_axis_dft ran this stage at 75 % of the FP64 peak",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs, measured" if peak else "unavailable"}
         return {"bound": "alu", "kernel": "k_axis_dft (axis 1 of the sum-factorised Re->k contraction)",
                 "achieved": ach / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_FLOPS, "flop_per_output": 4 * M + 2, "outputs_per_launch": outs,
-                "algorithmic_bytes": 16.0 * outs * (1 + (2 * M + 1) / float(wl.kgrid[0]))}
+                "algorithmic_bytes": algo}
 
     def roof_hkq(r):
         # H(k+q) on the tensor cores: 15 bf16 digit products per K step (5 x 5 digits, levels <= 4);
