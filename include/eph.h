@@ -441,13 +441,14 @@ int eph_tuning(const eph_ctx* ctx, eph_tuning_info* out);
  *   A     [batch][n][n] complex128 (re, im), row-major; only the Hermitian part is used
  *         (the imaginary parts of the diagonal are ignored).
  *   w     [batch][n] eigenvalues, ascending (ties in input order).
- *   V     [batch][n][n] complex128, column j the unit eigenvector of w[j] (V^H A V = diag w).
+ *   V     [batch][n][n] complex128, column j the unit eigenvector of w[j] (V^H A V = diag w);
+ *         it holds intermediate results during the call, so it must not overlap A.
  * Host or device pointers per the context's device_ptrs option; the call runs on the
  * context's stream and is synchronous unless the context is in async mode.
  * 1 <= n <= 256, batch >= 1.  Precision follows the context's form: FP64 eigenvalues and
  * eigenvectors (residual ~1e-15 ||A||) for EPH_FORM_FP64; for EPH_FORM_MIXED eigenvalues
  * within ~1e-12 ||A|| and eigenvectors within ~1e-8.  eig_plain_fp64 selects the plain FP64
- * Jacobi sweeps.  Errors: EPH_EINVAL (sizes, NULL pointers), EPH_ENOTCONV (a matrix reached
+ * Jacobi sweeps.  Errors: EPH_EINVAL (sizes, NULL pointers, A and V overlapping), EPH_ENOTCONV (a matrix reached
  * max_sweeps; results still written), EPH_ENOMEM, EPH_ECUDA.
  */
 int eph_eigh(eph_ctx* ctx, int n, int batch, const void* A, double* w, void* V);

@@ -2238,6 +2238,10 @@ extern "C" int eph_eigh(eph_ctx* ctx, int n, int batch, const void* A, double* w
   if (!ctx) return EPH_EINVAL;
   if (n < 1 || n > 256 || batch < 1 || !A || !w || !V) return fail(ctx, EPH_EINVAL, "eph_eigh: bad size or NULL pointer");
   const size_t nn = (size_t)n * n, abytes = (size_t)batch * nn * sizeof(double2);
+  if (ctx->opt.device_ptrs) {
+    const char *a0 = static_cast<const char*>(A), *v0 = static_cast<const char*>(V);
+    if (v0 < a0 + abytes && a0 < v0 + abytes) return fail(ctx, EPH_EINVAL, "eph_eigh: A and V overlap");
+  }
   const void* dA = nullptr;
   EPH_TRY(stage_in(ctx, ctx->eigA, A, abytes, &dA));
   double* dw = w;

@@ -57,6 +57,41 @@ __device__ __forceinline__ double f2d_i(float x) {
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
+// Double-float (h + l, two FP32 words, ~2^-48 relative) for the first refinement step, which runs
+// on the FP32 pipe: exact two-sum (Knuth) and the two-product of an FMA; the rn intrinsics keep
+// the compiler from contracting or reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (S, T) += a b for double-float a, b: the head product's error from an FMA, the cross terms in
+// FP32 (their error and the dropped a_l b_l are below 2^-48 |a b|), the head sum's error from a
+// two-sum; T collects the small parts
+__device__ __forceinline__ void df_acc(float& S, float& T, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float t = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fmaf_rn(ah, bh, -p)));
+  float s, e;
+  two_sum(S, p, s, e);
+  S = s;
+  T = __fadd_rn(T, __fadd_rn(e, t));
+}
+// normalised (h, l) of (ah + al) + (bh + bl)
+__device__ __forceinline__ float2 df_add(float ah, float al, float bh, float bl) {
+  float s, e, h, l;
+  two_sum(ah, bh, s, e);
+  two_sum(s, __fadd_rn(e, __fadd_rn(al, bl)), h, l);
+  return make_float2(h, l);
+}
+// split of a double into h + l (|residual| <= 2^-48 |x|; magnitudes below 2^-126 flush to 0)
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = d2f_i(x);
+  return make_float2(h, d2f_i(x - f2d_i(h)));
+}
+__device__ __forceinline__ float4 shfl_f4(float4 v, int src) {
+  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
 template <typename T>
 struct Cx;
 template <>
@@ -370,10 +405,88 @@ __global__ void __launch_bounds__(128) k_jacobi(const double2* __restrict__ A, l
 // pair still couples above rounding level (4e-15 ||A||_F; 1e-11 for the looser target)
 // after three steps, the warp falls back to the robust sequence: two Newton-Schulz steps,
 // A' = V^H A V and FP64 Jacobi sweeps to polish_tol ||A||_F with a first-order finish.
+// Dynamic shared memory of k_jacobi_mixed<np> for its four warps: per warp the A entries of its
+// 32 / np matrices as double2, double (3M pre-sums) and float4 (double-float split), then per lane
+// np float4 + np float2 (w = A x_j of a double-float step) and np / 2 + 1 float4 (pair products).
+constexpr size_t jm_smem_bytes(int np) {
+  return 4 * ((size_t)np * np * (32 / np) * 40 + (size_t)np * 32 * 24 + (size_t)(np / 2 + 1) * 32 * 16);
+}
+
+// Loads the group's matrix (its Hermitian part: the diagonal's imaginary parts dropped), padded to
+// NP with zeros, and scales it by a power of two to ||A||_F in [0.5, 1) (exact), which keeps every
+// FP32 quantity in range; the eigenvalues are scaled back by 1 / isc at the end.
+template <int NP>
+__device__ __forceinline__ void jm_load(const double2* __restrict__ A, long sA, long lda, int n, long mat, bool valid,
+                                        int j, int base, double2 (&a)[NP], double& fro2, double& isc) {
+#pragma unroll
+  for (int r = 0; r < NP; ++r) a[r] = (valid && r < n && j < n) ? A[mat * sA + (long)r * lda + j] : make_double2(0.0, 0.0);
+#pragma unroll
+  for (int r = 0; r < NP; ++r)
+    if (r == j) a[r].y = 0.0;
+  double my2 = 0.0;
+#pragma unroll
+  for (int r = 0; r < NP; ++r) my2 = fma(a[r].x, a[r].x, fma(a[r].y, a[r].y, my2));
+  fro2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) fro2 += shfl_d(my2, base + i);
+  int fexp = 0;
+  frexp(sqrt(fro2), &fexp);
+  isc = fro2 > 0.0 ? ldexp(1.0, -fexp) : 1.0;
+#pragma unroll
+  for (int r = 0; r < NP; ++r) a[r] = make_double2(a[r].x * isc, a[r].y * isc);
+  fro2 *= isc * isc;
+}
+
+// FP32 preconditioning of k_jacobi_mixed, a kernel of its own: cyclic Jacobi sweeps in FP32 on the
+// scaled matrix until its off-diagonal norm is below 1e-6 ||A||_F (12 sweeps at most), with the
+// same lane layout; writes the n x n FP32 eigenvector estimate of matrix m to T + m sT (row-major,
+// unsorted).  Its small register and code footprint keeps 6 CTAs per SM busy, where the fused
+// kernel ran these latency-bound sweeps at the refinement's occupancy.
+template <int NP>
+__global__ void __launch_bounds__(128) k_jacobi_f32(const double2* __restrict__ A, long sA, long lda, int n,
+                                                    long batch, float2* __restrict__ T, long sT) {
+  constexpr int G = 32 / NP;
+  const int lane = threadIdx.x & 31;
+  const int grp0 = lane / NP;
+  const bool in_group = grp0 < G;
+  const int grp = in_group ? grp0 : 0;
+  const int j = in_group ? lane - grp * NP : 0;
+  const int base = grp * NP;
+  const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long mat = warp * G + grp;
+  const bool valid = in_group && mat < batch;
+  double2 a[NP];
+  double fro2, isc;
+  jm_load<NP>(A, sA, lda, n, mat, valid, j, base, a, fro2, isc);
+  float2 vf[NP];
+  float2 af[NP];
+#pragma unroll
+  for (int r = 0; r < NP; ++r) {
+    af[r] = make_float2(d2f_i(a[r].x), d2f_i(a[r].y));
+    vf[r] = make_float2(r == j ? 1.f : 0.f, 0.f);
+  }
+  const float fro2f = (float)fro2;
+  const float thr32 = 1e-30f * fro2f + 1e-37f;
+  const float tol32 = 1e-12f * fro2f;
+  bool c32 = !valid;
+  int s32 = 0;
+  while (__any_sync(0xffffffffu, !c32) && s32 < 12) {
+    Sweep<NP, 0, float>::run(af, vf, j, base, thr32);
+    ++s32;
+    const float off = group_off2<NP>(af, j, base);  // shuffles: every lane takes part
+    if (valid && off <= tol32) c32 = true;
+  }
+  if (valid && j < n) {
+#pragma unroll
+    for (int r = 0; r < NP; ++r)
+      if (r < n) T[mat * sT + (long)r * n + j] = vf[r];
+  }
+}
+
 template <int NP>
 __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict__ A, long sA, long lda, int n,
-                                                      long batch, double* __restrict__ w, long sw,
-                                                      double2* __restrict__ V, long sV, int max_sweeps,
+                                                      long batch, double* __restrict__ w, long sw, double2* V,
+                                                      long sV, const float2* T, long sT, int max_sweeps,
                                                       double polish_tol, int* __restrict__ status) {
   constexpr int G = 32 / NP;
   constexpr int H = NP / 2;
@@ -388,49 +501,15 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
   const bool valid = in_group && mat < batch;
 
   double2 a[NP];
-#pragma unroll
-  for (int r = 0; r < NP; ++r) a[r] = (valid && r < n && j < n) ? A[mat * sA + (long)r * lda + j] : make_double2(0.0, 0.0);
-#pragma unroll
-  for (int r = 0; r < NP; ++r)
-    if (r == j) a[r].y = 0.0;
-  double my2 = 0.0;
-#pragma unroll
-  for (int r = 0; r < NP; ++r) my2 = fma(a[r].x, a[r].x, fma(a[r].y, a[r].y, my2));
-  double fro2 = 0.0;
-#pragma unroll
-  for (int i = 0; i < NP; ++i) fro2 += shfl_d(my2, base + i);
-  // the solve runs on A scaled by a power of two to ||A||_F in [0.5, 1) (exact), which keeps
-  // every FP32 quantity in range; the eigenvalues are scaled back at the end
-  int fexp = 0;
-  frexp(sqrt(fro2), &fexp);
-  const double isc = fro2 > 0.0 ? ldexp(1.0, -fexp) : 1.0;
-#pragma unroll
-  for (int r = 0; r < NP; ++r) a[r] = make_double2(a[r].x * isc, a[r].y * isc);
-  fro2 *= isc * isc;
-
-  // ---- FP32 preconditioning sweeps
+  double fro2, isc;
+  jm_load<NP>(A, sA, lda, n, mat, valid, j, base, a, fro2, isc);
+  // the FP32 eigenvector estimate of k_jacobi_f32 (padded columns: unit vectors)
   double2 v[NP];
-  {
-    float2 vf[NP];
-    float2 af[NP];
 #pragma unroll
-    for (int r = 0; r < NP; ++r) {
-      af[r] = make_float2(d2f_i(a[r].x), d2f_i(a[r].y));
-      vf[r] = make_float2(r == j ? 1.f : 0.f, 0.f);
-    }
-    const float fro2f = (float)fro2;
-    const float thr32 = 1e-30f * fro2f + 1e-37f;
-    const float tol32 = 1e-12f * fro2f;
-    bool c32 = !valid;
-    int s32 = 0;
-    while (__any_sync(0xffffffffu, !c32) && s32 < 12) {
-      Sweep<NP, 0, float>::run(af, vf, j, base, thr32);
-      ++s32;
-      const float off = group_off2<NP>(af, j, base);  // shuffles: every lane takes part
-      if (valid && off <= tol32) c32 = true;
-    }
-#pragma unroll
-    for (int r = 0; r < NP; ++r) v[r] = make_double2(f2d_i(vf[r].x), f2d_i(vf[r].y));
+  for (int r = 0; r < NP; ++r) {
+    float2 t = make_float2(r == j ? 1.f : 0.f, 0.f);
+    if (valid && j < n) t = r < n ? T[mat * sT + (long)r * n + j] : make_float2(0.f, 0.f);
+    v[r] = make_double2(f2d_i(t.x), f2d_i(t.y));
   }
 
   // ---- refinement
@@ -438,74 +517,47 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
   const float th2f = loose ? 1e-8f : 1e-16f;  // (final |E_ij|)^2
   const float tolc2f = (float)((loose ? 1e-22 : 1.6e-29) * fro2);  // (1e-11 ||A||_F)^2, (4e-15 ||A||_F)^2
   const float thc2f = 1e-6f;  // (largest first-order angle)^2
-  // A and its 3M pre-sums in shared memory (per warp; element (r, s) of group g at
-  // [(r NP + s) G + g], so the groups of a warp read consecutive words): frees the registers
-  // of the column copy for the refinement
-  __shared__ double2 shA[4][NP * NP * G];
-  __shared__ double shP[4][NP * NP * G];
+  // Shared memory per warp (jm_smem_bytes): A, its 3M pre-sums and its double-float split
+  // (element (r, s) of group g at [(r NP + s) G + g], so the groups of a warp read consecutive
+  // words; frees the registers of the column copy for the refinement), then per lane the
+  // double-float w = A x_j and w_re + w_im of a step (row r at [r 32 + lane]) and the pair
+  // products of its slots (slot d at [d 32 + lane]).
+  extern __shared__ __align__(16) unsigned char jm_smem[];
+  constexpr int EL = NP * NP * G;
   const int wib = (threadIdx.x >> 5) & 3;
+  double2* shA = reinterpret_cast<double2*>(jm_smem) + wib * EL;
+  double* shP = reinterpret_cast<double*>(jm_smem + 4 * EL * 16) + wib * EL;
+  float4* shD = reinterpret_cast<float4*>(jm_smem + 4 * EL * 24) + wib * EL;  // (Re h, Re l, Im h, Im l)
+  float4* shW = reinterpret_cast<float4*>(jm_smem + 4 * EL * 40) + wib * NP * 32 + lane;
+  float2* shWp = reinterpret_cast<float2*>(jm_smem + 4 * EL * 40 + 4 * NP * 32 * 16) + wib * NP * 32 + lane;
+  float4* shGS = reinterpret_cast<float4*>(jm_smem + 4 * EL * 40 + 4 * NP * 32 * 24) + wib * (H + 1) * 32 + lane;
   if (in_group) {
 #pragma unroll
     for (int r = 0; r < NP; ++r) {
-      shA[wib][(r * NP + j) * G + grp] = a[r];
-      shP[wib][(r * NP + j) * G + grp] = a[r].x + a[r].y;
+      shA[(r * NP + j) * G + grp] = a[r];
+      shP[(r * NP + j) * G + grp] = a[r].x + a[r].y;
+      const float2 sx = df_split(a[r].x), sy = df_split(a[r].y);
+      shD[(r * NP + j) * G + grp] = make_float4(sx.x, sx.y, sy.x, sy.y);
     }
   }
   __syncwarp();
   bool done = !valid;
   double lam = 0.0;
-#pragma unroll 1
-  for (int step = 0; step < 3; ++step) {
-    if (__all_sync(0xffffffffu, done)) break;
-    double xp[NP], xm[NP];
-#pragma unroll
-    for (int r = 0; r < NP; ++r) {
-      xp[r] = v[r].x + v[r].y;
-      xm[r] = v[r].x - v[r].y;
-    }
-    // w = A x_j (three multiplications per complex product)
-    double2 wv[NP];
-    double wp[NP];
-#pragma unroll
-    for (int r = 0; r < NP; ++r) {
-      double t1 = 0.0, t2 = 0.0, t3 = 0.0;
-#pragma unroll
-      for (int s2 = 0; s2 < NP; ++s2) {
-        const double2 ars = shA[wib][(r * NP + s2) * G + grp];  // A[r][s2]
-        const double prs = shP[wib][(r * NP + s2) * G + grp];
-        t1 = fma(ars.x, v[s2].x, t1);
-        t2 = fma(ars.y, v[s2].y, t2);
-        t3 = fma(prs, xp[s2], t3);
-      }
-      wv[r] = make_double2(t1 - t2, t3 - t1 - t2);
-      wp[r] = wv[r].x + wv[r].y;
-    }
-    // slot d: the pair (i = j + d mod NP, j); g = x_i^H x_j, s = x_i^H w_j
-    auto pair_products = [&](int src, double2& g, double2& sv) {
-      double g1 = 0.0, g2 = 0.0, g3 = 0.0, s1 = 0.0, s2v = 0.0, s3 = 0.0;
-#pragma unroll
-      for (int r = 0; r < NP; ++r) {
-        const double2 xi = shfl_d2(v[r], src);
-        const double mi = shfl_d(xm[r], src);
-        g1 = fma(xi.x, v[r].x, g1);
-        g2 = fma(xi.y, v[r].y, g2);
-        g3 = fma(mi, xp[r], g3);
-        s1 = fma(xi.x, wv[r].x, s1);
-        s2v = fma(xi.y, wv[r].y, s2v);
-        s3 = fma(mi, wp[r], s3);
-      }
-      g = make_double2(g1 + g2, g3 - g1 + g2);
-      sv = make_double2(s1 + s2v, s3 - s1 + s2v);
-    };
-    double2 g0, s0;
-    pair_products(base + j, g0, s0);
+
+  // The correction of one step from the products of the pairs.  slot0(gx, sx) gives the real
+  // parts of x_j^H x_j and x_j^H (A x_j) in double; slot(d, src, gf, sf) gives g = x_i^H x_j and
+  // s = x_i^H (A x_j) in FP32 for slot d >= 1, whose x_i the lane src holds; pre_update() runs
+  // once every product is taken.  A step may end the refinement only if final_ok.
+  auto correct = [&](auto&& slot0, auto&& slot, auto&& pre_update, bool final_ok) {
+    double g0x, s0x;
+    slot0(g0x, s0x);
     // Rayleigh quotient of x_j: 1 / g0 = 1 + e + e^2 + e^3 with e = 1 - g0 (|e| ~ 1e-6, then
     // ~1e-12; a larger |e| leaves the step unconverged through the diagonal of R/2)
-    const double e0 = 1.0 - g0.x;
-    const double lt = s0.x * fma(e0, fma(e0, e0 + 1.0, 1.0), 1.0);
+    const double e0 = 1.0 - g0x;
+    const double lt = s0x * fma(e0, fma(e0, e0 + 1.0, 1.0), 1.0);
     // The bookkeeping of the correction runs in FP32: K, the angle tests and the eigenvalue
     // shift need ~1e-7 relative precision only.  Their inputs S_ij, G_ij and the gap
-    // lam_j - lam_i are formed in FP64 (they are small differences).
+    // lam_j - lam_i are formed at the step's precision (they are small differences).
     const float ltf = d2f_i(lt);
     const float e0f = d2f_i(e0);
     float emx = 0.25f * e0f * e0f;  // squared bound on |E_ij|
@@ -518,14 +570,13 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     for (int d = 1; d <= H; ++d) {
       int i = j + d;
       if (i >= NP) i -= NP;
-      double2 g, sv;
-      pair_products(base + i, g, sv);
+      float2 gf, sf;
+      slot(d, base + i, gf, sf);
       const double li = shfl_d(lt, base + i);
       const float lif = shfl_d(ltf, base + i);
       const float gap = d2f_i(lt - li);
       const float hm = 0.5f * (lif + ltf);
-      const float2 gf = make_float2(d2f_i(g.x), d2f_i(g.y));
-      const float2 num = make_float2(fmaf(-hm, gf.x, d2f_i(sv.x)), fmaf(-hm, gf.y, d2f_i(sv.y)));
+      const float2 num = make_float2(fmaf(-hm, gf.x, sf.x), fmaf(-hm, gf.y, sf.y));
       const float n2 = fmaf(num.x, num.x, num.y * num.y);
       const bool own = !(2 * d == NP && j >= H);
       float2 K = make_float2(0.f, 0.f);
@@ -544,6 +595,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       kf[d - 1] = K;
       if (own) er[d] = make_float2(hh.x + K.x, hh.y + K.y);
     }
+    pre_update();
     // mirrored half: lane i' = j - d holds the pair (j, i') in its slot d; E_{i'j} = conj(h - k)
 #pragma unroll
     for (int d = 1; d <= H; ++d) {
@@ -587,11 +639,172 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     if (!done) {
 #pragma unroll
       for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x + f2d_i(acc[r].x), v[r].y + f2d_i(acc[r].y));
-      if (emx_g <= th2f && !unres_g) {
+      if (final_ok && emx_g <= th2f && !unres_g) {
         done = true;
         lam = lt + f2d_i(shift);
       }
     }
+  };
+
+  // FP64 products: w = A x_j with three multiplications per complex product, then the pairs
+  auto step64 = [&]() {
+    double xp[NP], xm[NP];
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      xp[r] = v[r].x + v[r].y;
+      xm[r] = v[r].x - v[r].y;
+    }
+    double2 wv[NP];
+    double wp[NP];
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+#pragma unroll
+      for (int s2 = 0; s2 < NP; ++s2) {
+        const double2 ars = shA[(r * NP + s2) * G + grp];  // A[r][s2]
+        const double prs = shP[(r * NP + s2) * G + grp];
+        t1 = fma(ars.x, v[s2].x, t1);
+        t2 = fma(ars.y, v[s2].y, t2);
+        t3 = fma(prs, xp[s2], t3);
+      }
+      wv[r] = make_double2(t1 - t2, t3 - t1 - t2);
+      wp[r] = wv[r].x + wv[r].y;
+    }
+    // g = x_i^H x_j, s = x_i^H w_j for the lane src holding x_i
+    auto pair = [&](int src, double2& g, double2& sv) {
+      double g1 = 0.0, g2 = 0.0, g3 = 0.0, s1 = 0.0, s2v = 0.0, s3 = 0.0;
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        const double2 xi = shfl_d2(v[r], src);
+        const double mi = shfl_d(xm[r], src);
+        g1 = fma(xi.x, v[r].x, g1);
+        g2 = fma(xi.y, v[r].y, g2);
+        g3 = fma(mi, xp[r], g3);
+        s1 = fma(xi.x, wv[r].x, s1);
+        s2v = fma(xi.y, wv[r].y, s2v);
+        s3 = fma(mi, wp[r], s3);
+      }
+      g = make_double2(g1 + g2, g3 - g1 + g2);
+      sv = make_double2(s1 + s2v, s3 - s1 + s2v);
+    };
+    auto slot0 = [&](double& gx, double& sx) {
+      double2 g, sv;
+      pair(base + j, g, sv);
+      gx = g.x;
+      sx = sv.x;
+    };
+    auto slot = [&](int, int src, float2& gf, float2& sf) {
+      double2 g, sv;
+      pair(src, g, sv);
+      gf = make_float2(d2f_i(g.x), d2f_i(g.y));
+      sf = make_float2(d2f_i(sv.x), d2f_i(sv.y));
+    };
+    correct(slot0, slot, [] {}, true);
+  };
+
+  // Double-float products on the FP32 pipe (~2^-47 of the largest term per product sum): w = A x_j
+  // with four multiplications per complex product from the split copy of A, the pairs with three.
+  // x_j is split on entry and joined back before the update (a change below 2^-48 |x_j|).  Both
+  // product phases are loops over rows and slots with their results in shared memory: unrolled,
+  // the step's ~7,000 instructions overflow the instruction cache.
+  auto step_df = [&](bool final_ok) {
+    float4 vd[NP];  // (Re h, Re l, Im h, Im l)
+    float2 xpd[NP], xmd[NP];
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      const float2 sx = df_split(v[r].x), sy = df_split(v[r].y);
+      vd[r] = make_float4(sx.x, sx.y, sy.x, sy.y);
+      xpd[r] = df_add(sx.x, sx.y, sy.x, sy.y);
+      xmd[r] = df_add(sx.x, sx.y, -sy.x, -sy.y);
+    }
+#pragma unroll 1
+    for (int r = 0; r < NP; ++r) {
+      float S1 = 0.f, T1 = 0.f, S2 = 0.f, T2 = 0.f, S3 = 0.f, T3 = 0.f, S4 = 0.f, T4 = 0.f;
+      const float4* arow = shD + r * NP * G + grp;
+#pragma unroll
+      for (int s2 = 0; s2 < NP; ++s2) {
+        const float4 ad = arow[s2 * G];  // A[r][s2]
+        df_acc(S1, T1, ad.x, ad.y, vd[s2].x, vd[s2].y);
+        df_acc(S2, T2, ad.z, ad.w, vd[s2].z, vd[s2].w);
+        df_acc(S3, T3, ad.x, ad.y, vd[s2].z, vd[s2].w);
+        df_acc(S4, T4, ad.z, ad.w, vd[s2].x, vd[s2].y);
+      }
+      const float2 wx = df_add(S1, T1, -S2, -T2), wy = df_add(S3, T3, S4, T4);
+      shW[r * 32] = make_float4(wx.x, wx.y, wy.x, wy.y);
+      shWp[r * 32] = df_add(wx.x, wx.y, wy.x, wy.y);
+    }
+    double g0x = 0.0, s0x = 0.0;
+#pragma unroll 1
+    for (int d = 0; d <= H; ++d) {
+      int i = j + d;
+      if (i >= NP) i -= NP;
+      const int src = base + i;
+      float G1 = 0.f, U1 = 0.f, G2 = 0.f, U2 = 0.f, G3 = 0.f, U3 = 0.f;
+      float R1 = 0.f, V1 = 0.f, R2 = 0.f, V2 = 0.f, R3 = 0.f, V3 = 0.f;
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        const float4 xi = shfl_f4(vd[r], src);
+        const float2 mi = shfl_d2(xmd[r], src);
+        const float4 wr = shW[r * 32];
+        const float2 wpr = shWp[r * 32];
+        df_acc(G1, U1, xi.x, xi.y, vd[r].x, vd[r].y);
+        df_acc(G2, U2, xi.z, xi.w, vd[r].z, vd[r].w);
+        df_acc(G3, U3, mi.x, mi.y, xpd[r].x, xpd[r].y);
+        df_acc(R1, V1, xi.x, xi.y, wr.x, wr.y);
+        df_acc(R2, V2, xi.z, xi.w, wr.z, wr.w);
+        df_acc(R3, V3, mi.x, mi.y, wpr.x, wpr.y);
+      }
+      // real part p1 + p2, imaginary part p3 - (p1 - p2), each from exact head sums
+      auto parts = [](float P1, float Q1, float P2, float Q2, float P3, float Q3, float2& f, double& x) {
+        float hs, he;
+        two_sum(P1, P2, hs, he);
+        const float rt = __fadd_rn(he, __fadd_rn(Q1, Q2));
+        x = f2d_i(hs) + f2d_i(rt);
+        f.x = __fadd_rn(hs, rt);
+        float ds, de;
+        two_sum(P1, -P2, ds, de);
+        const float dt = __fadd_rn(de, __fsub_rn(Q1, Q2));
+        float ys, ye;
+        two_sum(P3, -ds, ys, ye);
+        f.y = __fadd_rn(ys, __fadd_rn(ye, __fsub_rn(Q3, dt)));
+      };
+      float2 gf, sf;
+      double gx, sx;
+      parts(G1, U1, G2, U2, G3, U3, gf, gx);
+      parts(R1, V1, R2, V2, R3, V3, sf, sx);
+      shGS[d * 32] = make_float4(gf.x, gf.y, sf.x, sf.y);
+      if (d == 0) {
+        g0x = gx;
+        s0x = sx;
+      }
+    }
+    auto slot0 = [&](double& gx, double& sx) {
+      gx = g0x;
+      sx = s0x;
+    };
+    auto slot = [&](int d, int, float2& gf, float2& sf) {
+      const float4 q = shGS[d * 32];
+      gf = make_float2(q.x, q.y);
+      sf = make_float2(q.z, q.w);
+    };
+    auto rejoin = [&] {
+#pragma unroll
+      for (int r = 0; r < NP; ++r)
+        v[r] = make_double2(f2d_i(vd[r].x) + f2d_i(vd[r].y), f2d_i(vd[r].z) + f2d_i(vd[r].w));
+    };
+    correct(slot0, slot, rejoin, final_ok);
+  };
+
+  // The first step runs in double-float (from the FP32 eigenvectors it only has to reach ~1e-12);
+  // the FP64 eigendecomposition then finishes with FP64 steps, the looser target (a single step
+  // as a rule) stays in double-float, whose eigenvalues are exact to ~1e-14 ||A||.
+#pragma unroll 1
+  for (int step = 0; step < 3; ++step) {
+    if (__all_sync(0xffffffffu, done)) break;
+    if (step == 0 || loose)
+      step_df(loose);
+    else
+      step64();
   }
 
   if (!__all_sync(0xffffffffu, done)) {
@@ -642,7 +855,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
         const double2 vs = v[s2];
 #pragma unroll
         for (int r = 0; r < NP; ++r) {
-          const double2 cs = shA[wib][(r * NP + s2) * G + grp];  // A[r][s2]
+          const double2 cs = shA[(r * NP + s2) * G + grp];  // A[r][s2]
           wv[r].x = fma(cs.x, vs.x, fma(-cs.y, vs.y, wv[r].x));
           wv[r].y = fma(cs.x, vs.y, fma(cs.y, vs.x, wv[r].y));
         }
@@ -768,10 +981,29 @@ cudaError_t launch_jacobi_mixed(const double2* A, long sA, long lda, int n, long
   const int threads = 128;
   const long blocks = (warps * 32 + threads - 1) / threads;
   if (blocks > 2147483647L) return cudaErrorInvalidConfiguration;
-#define EPH_JM(NPV)                                                                                              \
-  case NPV:                                                                                                      \
-    k_jacobi_mixed<NPV><<<(unsigned)blocks, threads, 0, st>>>(A, sA, lda, n, batch, w, sw, V, sV, max_sweeps, \
-                                                               polish_tol, status);                              \
+  // the FP32 estimate passes through V (n x n float2 inside each matrix's n x n double2), so V
+  // must hold n x n per matrix and must not overlap A
+  if (sV < (long)n * n) return cudaErrorInvalidValue;
+  {
+    const char* a0 = reinterpret_cast<const char*>(A);
+    const char* a1 = reinterpret_cast<const char*>(A + (batch - 1) * sA + (long)(n - 1) * lda + n);
+    const char* v0 = reinterpret_cast<const char*>(V);
+    const char* v1 = reinterpret_cast<const char*>(V + (batch - 1) * sV + (long)n * n);
+    if (v0 < a1 && a0 < v1) return cudaErrorInvalidValue;
+  }
+  float2* T = reinterpret_cast<float2*>(V);
+  const long sT = 2 * sV;
+  const size_t smem = jm_smem_bytes(np);
+#define EPH_JM(NPV)                                                                                                  \
+  case NPV:                                                                                                          \
+    if (smem > 48 * 1024) {                                                                                          \
+      cudaError_t e = cudaFuncSetAttribute(k_jacobi_mixed<NPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                           (int)smem);                                                               \
+      if (e != cudaSuccess) return e;                                                                                \
+    }                                                                                                                \
+    k_jacobi_f32<NPV><<<(unsigned)blocks, threads, 0, st>>>(A, sA, lda, n, batch, T, sT);                            \
+    k_jacobi_mixed<NPV><<<(unsigned)blocks, threads, smem, st>>>(A, sA, lda, n, batch, w, sw, V, sV, T, sT,         \
+                                                                  max_sweeps, polish_tol, status);                   \
     break;
   switch (np) {
     EPH_JM(2) EPH_JM(4) EPH_JM(6) EPH_JM(8) EPH_JM(10) EPH_JM(12)

@@ -121,3 +121,7 @@ def test_device_pointers_and_errors(ctxs):
     assert ei.value.code == binding.EPH_EINVAL
     with pytest.raises(binding.EphError):
         ctx.eph_eigh(10, 0, dA, dw, dV)
+    # V carries intermediate results: an in-place call is rejected, not silently wrong
+    with pytest.raises(binding.EphError) as ei:
+        ctx.eph_eigh(10, 33, dA, dw, dA)
+    assert ei.value.code == binding.EPH_EINVAL
