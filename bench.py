@@ -40,13 +40,14 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # x 64000 k), from an ncu capture of that launch; profiles/k_zgemm_si_full_fp64.md,
 # profiles/k_tc_fixed_gemm_si_full.md, profiles/k_jacobi_mixed_si_full.md.
 # Keyed by (kernel, workload, q batch).
-# FP64 flops per matrix of the batched H(k+q) eigensolve (2 x DFMA + DADD + DMUL thread
-# instructions executed, from one ncu capture; profiles/k_jacobi_mixed_si_full.md), keyed by (nb, form)
-# FP64 flops per 8x8 eigensolve (2 DFMA + DMUL + DADD thread instructions from one ncu capture of
-# the 256,000-matrix launch: 1.7695e9 DFMA, 5.94e7 DMUL, 5.489e8 DADD)
-EIG_FP64_FLOPS = {(8, "fp64"): (2 * 1769472000 + 59392000 + 548864000) / 256000,
-                  # mixed form (eigensolves stop at ~1e-12 ||A||): one launch of 55,296 matrices
-                  (8, "mixed"): (2 * 197296128 + 62816256 + 12386304) / 55296}
+# Per-matrix work of the batched 8x8 H(k+q) eigensolve (k_jacobi_f32<8> FP32 sweeps + k_jacobi_mixed<8>
+# refinement, one eig call), keyed by (nb, form), from one ncu capture of the 55,296-matrix launches
+# (bench.py --capture si-fp64-grid / si-mixed-grid, profiles/k_jacobi_split_si_full.md): FP64 flops
+# (2 DFMA + DMUL + DADD thread instructions) and warp instructions issued, both kernels summed
+EIG_COUNTS = {(8, "fp64"): dict(fp64_flop=None, warp_inst=None),
+              (8, "mixed"): dict(fp64_flop=None, warp_inst=None)}
+# instruction issue of GB300: 152 SMs x 4 schedulers x one warp instruction per clock x 2.07 GHz
+ISSUE_PEAK = 152 * 4 * 2.07e9
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at one step = 4 q x 64,000 k
 TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
            ("k_zgemm", "si_full", 4): 242432512.0 + 1777470464.0,
@@ -57,8 +58,9 @@ TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
 # DRAM bytes per unit (pair or matrix) of the current kernels from the 24^3-grid captures
 # (bench.py --capture si-fp64-grid / si-mixed-grid, 55,296 pairs per launch), scaled to a launch
 # by its units: these kernels stream their inputs once, so traffic grows in proportion
-TRAFFIC_PER_UNIT = {("k_jacobi_mixed", "si_full", 4, "fp64"): (56772608.0 + 10082304.0) / 55296,
-                    ("k_jacobi_mixed", "si_full", 4, "mixed"): (56966912.0 + 10144256.0) / 55296,
+TRAFFIC_PER_UNIT = {  # one eig call: k_jacobi_f32 + k_jacobi_mixed (A is read by both)
+                    ("k_jacobi", "si_full", 4, "fp64"): (56679424.0 + 1968384.0 + 85091584.0 + 15082752.0) / 55296,
+                    ("k_jacobi", "si_full", 4, "mixed"): (56681472.0 + 1915648.0 + 85043200.0 + 14231040.0) / 55296,
                     ("k_band_tc_small64", "si_full", 4, "grid"): (424918528.0 + 287893248.0) / 55296,
                     ("k_band_tc_small", "si_full", 4, "grid"): (424756224.0 + 136090112.0) / 55296}
 
@@ -897,19 +899,33 @@ def run_libeph(args):
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
 
     def roof_eig(r, form="fp64"):
+        # two floors for the eigensolve: its FP64 flops at the FP64 unit peak, and its warp
+        # instructions at one per scheduler and clock; the higher one bounds it
         eg_ms, eg_n = r["prof"]["eig"]
-        per = EIG_FP64_FLOPS.get((nb, form))
+        c = EIG_COUNTS.get((nb, form)) or {}
         t = eg_ms / max(eg_n, 1) * 1e-3
         mats = float(args.steps) * QB * nk / max(eg_n, 1)
-        ach = per * mats / t if per else None
-        return {"bound": "alu", "kernel": "k_jacobi_mixed<%d> (FP32 Jacobi sweeps, two FP64 Ogita-Aishima "
-                                          "refinement steps)" % (nb + (nb & 1)),
-                "achieved": ach / 1e12 if ach else None, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_FLOPS if ach else None,
-                "fp64_flop_per_matrix": per, "matrices_per_launch": mats,
-                "traffic": (TRAFFIC_PER_UNIT.get(("k_jacobi_mixed", args.workload, QB, form), 0.0) * mats) or None,
-                "algorithmic_bytes": mats * (nb * nb * 16 + nb * nb * 16 + nb * 8),
-                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
+        f64, wi = c.get("fp64_flop"), c.get("warp_inst")
+        kern = ("k_jacobi_f32<%d> (FP32 Jacobi sweeps) + k_jacobi_mixed<%d> (Ogita-Aishima refinement: one "
+                "double-float step on the FP32 pipe%s)" % (nb + (nb & 1), nb + (nb & 1),
+                                                           ", one FP64 step" if form == "fp64" else ""))
+        out = {"bound": "alu", "kernel": kern, "achieved": None, "peak": None, "unit": None, "frac": None,
+               "matrices_per_call": mats, "fp64_flop_per_matrix": f64, "warp_inst_per_matrix": wi,
+               "traffic": (TRAFFIC_PER_UNIT.get(("k_jacobi", args.workload, QB, form), 0.0) * mats) or None,
+               "algorithmic_bytes": mats * (nb * nb * 16 + nb * nb * 16 + nb * 8)}
+        if not (f64 and wi and t):
+            return out
+        t64, tis = f64 * mats / FP64_PEAK_FLOPS, wi * mats / ISSUE_PEAK
+        out.update({"fp64_frac": t64 / t, "issue_frac": tis / t})
+        if t64 >= tis:
+            out.update({"achieved": f64 * mats / t / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                        "frac": t64 / t, "binding": "FP64 pipe",
+                        "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"})
+        else:
+            out.update({"achieved": wi * mats / t / 1e12, "peak": ISSUE_PEAK / 1e12,
+                        "unit": "T warp instructions/s", "frac": tis / t, "binding": "instruction issue",
+                        "peak_source": "152 SMs x 4 schedulers x 1 warp instruction/clk x 2.07 GHz"})
+        return out
 
     def roof_band_tc(r, g3_bytes, fp64=False):
         # the fused tensor-core band rotation (k_band_tc_small, mixed; k_band_tc_small64, FP64 form)

@@ -111,7 +111,7 @@ cudaError_t launch_band_adjoint(double2* Y, long ldy, const double2* Ukq, const 
     if (e != cudaSuccess) return e;
   }
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
-  k_band_adjoint<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, wk, om, omega_min, nk, nm, nb, Lpair);
+  k_band_adjoint<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, wk, om, omega_min, nk, nm, nb, Lpair), note_launch();
   return cudaGetLastError();
 }
 
@@ -151,7 +151,7 @@ cudaError_t launch_band_vjp(double2* Y, long ldy, const double2* gbar, long sgq,
     if (e != cudaSuccess) return e;
   }
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
-  k_band_vjp<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, gbar, sgq, Ukq, Uk, nk, nm, nb);
+  k_band_vjp<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, gbar, sgq, Ukq, Uk, nk, nm, nb), note_launch();
   return cudaGetLastError();
 }
 
@@ -194,7 +194,7 @@ cudaError_t launch_loss_terms(double2* Y, long ldy, const double* wk, const doub
   const long pairs = (long)nq * nk;
   if (pairs <= 0) return cudaSuccess;
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
-  k_loss_terms<<<(unsigned)pairs, 256, 0, st>>>(Y, ldy, wk, om, omega_min, nk, nm, nb, Lpair);
+  k_loss_terms<<<(unsigned)pairs, 256, 0, st>>>(Y, ldy, wk, om, omega_min, nk, nm, nb, Lpair), note_launch();
   return cudaGetLastError();
 }
 
@@ -213,7 +213,7 @@ cudaError_t launch_zero_masked(void* g, int eb, long sgq, long per, int nq, int 
   const long pairs = (long)nq * nk;
   if (pairs <= 0 || !keep) return cudaSuccess;
   if ((eb != 8 && eb != 16) || pairs > 2147483647L || (reinterpret_cast<uintptr_t>(g) & 7)) return cudaErrorInvalidValue;
-  k_zero_masked<<<(unsigned)pairs, 128, 0, st>>>(static_cast<char*>(g), eb, sgq, per, nk, keep);
+  k_zero_masked<<<(unsigned)pairs, 128, 0, st>>>(static_cast<char*>(g), eb, sgq, per, nk, keep), note_launch();
   return cudaGetLastError();
 }
 
@@ -230,7 +230,7 @@ __global__ void k_conj_transpose(const double2* __restrict__ in, int n, long tot
 cudaError_t launch_conj_transpose(const double2* in, int n, long batch, double2* out, cudaStream_t st) {
   const long total = batch * n * n;
   if (total <= 0) return cudaSuccess;
-  k_conj_transpose<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(in, n, total, out);
+  k_conj_transpose<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(in, n, total, out), note_launch();
   return cudaGetLastError();
 }
 
@@ -242,7 +242,7 @@ __global__ void k_mass_factors(const double* __restrict__ invsqrtm, int nm, doub
 
 cudaError_t launch_mass_factors(const double* invsqrtm, int nm, double s, double* f, cudaStream_t st) {
   if (nm <= 0) return cudaSuccess;
-  k_mass_factors<<<(nm + 127) / 128, 128, 0, st>>>(invsqrtm, nm, s, f);
+  k_mass_factors<<<(nm + 127) / 128, 128, 0, st>>>(invsqrtm, nm, s, f), note_launch();
   return cudaGetLastError();
 }
 
@@ -259,7 +259,7 @@ __global__ void k_scale_modes(double2* __restrict__ X, long per_q, long blk, con
 cudaError_t launch_scale_modes(double2* X, int nq, int nm, long blk, const double* f, cudaStream_t st) {
   const long n = (long)nq * nm * blk;
   if (n <= 0) return cudaSuccess;
-  k_scale_modes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, (long)nm * blk, blk, f, n);
+  k_scale_modes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, (long)nm * blk, blk, f, n), note_launch();
   return cudaGetLastError();
 }
 
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256) k_sum_into(const double* __restrict__ v, 
 
 cudaError_t launch_sum_into(const double* v, long n, double* L, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_sum_into<<<1, 256, 0, st>>>(v, n, L);
+  k_sum_into<<<1, 256, 0, st>>>(v, n, L), note_launch();
   return cudaGetLastError();
 }
 
@@ -322,7 +322,7 @@ cudaError_t launch_mode_rotate_adj(const double2* G2b, const double2* u, int nq,
   if (nm > 16 || nq > 65535) return cudaErrorInvalidValue;
   long per_q = (long)ne * nb2;
   dim3 grid((unsigned)((per_q + 255) / 256), nq);
-  k_mode_rotate_adj<16><<<grid, 256, 0, st>>>(G2b, u, nm, ne, nb2, G1b);
+  k_mode_rotate_adj<16><<<grid, 256, 0, st>>>(G2b, u, nm, ne, nb2, G1b), note_launch();
   return cudaGetLastError();
 }
 

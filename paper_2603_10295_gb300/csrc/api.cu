@@ -305,9 +305,10 @@ double omega_unit_ev() {
       eb_ = take_event(ctx);                                      \
       if (ea_) cudaEventRecord(ea_, ctx->stream);                 \
     }                                                             \
+    const long long k0_ = eph::t_kernel_launches;                 \
     cudaError_t e_ = (call);                                      \
     if (e_ != cudaSuccess) return fail(ctx, EPH_ECUDA, #call, e_); \
-    ++ctx->launches;                                              \
+    ctx->launches += eph::t_kernel_launches - k0_;                \
     if (ea_ && eb_) {                                             \
       cudaEventRecord(eb_, ctx->stream);                          \
       ctx->pending.push_back({(stage), ea_, eb_});                \
@@ -323,6 +324,10 @@ double omega_unit_ev() {
     int r_ = (call);            \
     if (r_ != EPH_OK) return r_; \
   } while (0)
+
+namespace eph {
+thread_local long long t_kernel_launches = 0;
+}  // namespace eph
 
 extern "C" {
 
@@ -414,10 +419,11 @@ int form_gw_digits(eph_ctx* ctx) {
   if (!ctx->eq9_tc) return EPH_OK;
   const long X = (long)ctx->nm * ctx->ne * ctx->nb * ctx->nb;
   const size_t slice = (size_t)2 * X * ctx->kpp;
+  const long long k0 = eph::t_kernel_launches;
   cudaError_t e = eph::launch_digits_b(ctx->gW, X, 0, 0, (int)X, ctx->nrp, ctx->kpp, 1, static_cast<float*>(ctx->sG.p),
                                        ctx->DG.p, (long)slice, 4, ctx->stream);
   if (e != cudaSuccess) return fail(ctx, EPH_ECUDA, "g(Re,Rp) digits", e);
-  ++ctx->launches;
+  ctx->launches += eph::t_kernel_launches - k0;
   return EPH_OK;
 }
 
@@ -1775,12 +1781,13 @@ extern "C" int eph_interp_q_multi(int nctx, eph_ctx* const* ctxs, const int* nq,
         eb = take_event(c0);
         if (ea) cudaEventRecord(ea, c0->stream);
       }
+      const long long k0 = eph::t_kernel_launches;
       const cudaError_t e = eph::launch_band_rotate_multi(segs, nseg, total, mnb, mnm, nsm, c0->stream);
       if (e != cudaSuccess) {
         rc = fail(c0, EPH_ECUDA, "launch_band_rotate_multi", e);
         break;
       }
-      ++c0->launches;
+      c0->launches += eph::t_kernel_launches - k0;
       if (ea && eb) {
         cudaEventRecord(eb, c0->stream);
         c0->pending.push_back({EPH_STAGE_BAND, ea, eb});

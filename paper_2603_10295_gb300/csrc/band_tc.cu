@@ -244,7 +244,7 @@ cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const
   // A digits of V_k for every k of the tile (stage 1)
   {
     const long slice = (long)nk * M * kp;
-    k_vdigits<<<(unsigned)((slice + 255) / 256), 256, 0, st>>>(Uk, (long)nb * nb, nb, nk, kp, 0, A1, slice);
+    k_vdigits<<<(unsigned)((slice + 255) / 256), 256, 0, st>>>(Uk, (long)nb * nb, nb, nk, kp, 0, A1, slice), note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   CUtensorMap mA1[5], mA2[5], mB[5];
@@ -261,26 +261,26 @@ cudaError_t launch_band_tc(const void* Y, int y_f32, long ldy, long y_off, const
     const unsigned gblocks = (unsigned)((rows * 32 + 255) / 256);
     if (y_f32)
       k_gdigits<float2><<<gblocks, 256, 0, st>>>(static_cast<const float2*>(Y) + p0 * ldy, ldy, y_off, (int)Nr, nb,
-                                                 rows, kp, sB, Bd, bslice);
+                                                 rows, kp, sB, Bd, bslice), note_launch();
     else
       k_gdigits<double2><<<gblocks, 256, 0, st>>>(static_cast<const double2*>(Y) + p0 * ldy, ldy, y_off, (int)Nr, nb,
-                                                  rows, kp, sB, Bd, bslice);
+                                                  rows, kp, sB, Bd, bslice), note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_tc_band_gemm(mA1, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, nk,
                                  (int)(p0 % nk), M, st)) != cudaSuccess)
       return e;
     // stage 2: g = V_{k+q}^H T per pair
     k_tdigits<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(C, (long)M * Nr, (int)Nr, nb, rows, kp, sB, Bd,
-                                                                   bslice);
+                                                                   bslice), note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_vdigits<<<(unsigned)((aslice + 255) / 256), 256, 0, st>>>(Ukq + p0 * nb * nb, (long)nb * nb, nb, pb, kp, 1, A2,
-                                                                aslice);
+                                                                aslice), note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_tc_band_gemm(mA2, mB, M, 0, (int)Nr, kp, (int)pb, 2.0f, sB, C, Nr, (long)M * Nr, err, (int)pb, 0, M,
                                  st)) != cudaSuccess)
       return e;
     const long tot = pb * nm * nb * nb;
-    k_gout<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, (long)M * Nr, (int)Nr, nb, nm, pb, nk, p0, g, sgq);
+    k_gout<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, (long)M * Nr, (int)Nr, nb, nm, pb, nk, p0, g, sgq), note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1270,7 +1270,7 @@ cudaError_t launch_band_tc_small(const void* Y, int y_f32, long ldy, const doubl
       return e;                                                                                                       \
     const long grid = std::min(ntiles, (long)sms * occ);                                                              \
     kern<<<(unsigned)grid, bts::THREADS, smem, st>>>(static_cast<const TCT*>(Y), ldy, Ukq, Uk, nq, nk, nm, nb, s.rs,  \
-                                                     s.ppt, g, sgq, keep, err, s.cols, vec16);                        \
+                                                     s.ppt, g, sgq, keep, err, s.cols, vec16), note_launch();                        \
   } while (0)
   if (y_f32) {
     if (s.kp == 16) EPH_SMALL_LAUNCH(float2, 16); else EPH_SMALL_LAUNCH(float2, 32);
@@ -1329,7 +1329,7 @@ cudaError_t launch_band_tc_small64_ex(const double2* X, long xq, long xk, const 
   const long grid = std::min((ntiles + nslots - 1) / nslots, (long)sms * occ);
   kern<<<(unsigned)grid, nslots * bts::THREADS, smem, st>>>(X, xq, xk, Ukq, Uk, nq, nk, nm, nb, s.rs, s.ppt, out, oq,
                                                               ok, keep, wk, om, omega_min, Lpair, err, cols, nslots,
-                                                              slot_bytes, slot_cols);
+                                                              slot_bytes, slot_cols), note_launch();
   return cudaGetLastError();
 }
 

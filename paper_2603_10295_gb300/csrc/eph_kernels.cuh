@@ -6,6 +6,12 @@
 
 namespace eph {
 
+// ---- launch accounting --------------------------------------------------------
+// Every kernel launch site counts itself (kernels enqueued by this host thread); a context adds
+// the difference over each of its calls to its launch count.
+extern thread_local long long t_kernel_launches;
+inline void note_launch() { ++t_kernel_launches; }
+
 // ---- complex helpers (double2 / float2 = re, im) ---------------------------
 __host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));

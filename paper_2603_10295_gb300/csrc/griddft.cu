@@ -35,7 +35,7 @@ __global__ void k_axis_phase(int N, int B, double shift, double2* __restrict__ E
 cudaError_t launch_axis_phase(int N, int B, double shift, double2* E, cudaStream_t st) {
   const int total = N * B;
   if (total <= 0) return cudaSuccess;
-  k_axis_phase<<<(total + 255) / 256, 256, 0, st>>>(N, B, shift, E);
+  k_axis_phase<<<(total + 255) / 256, 256, 0, st>>>(N, B, shift, E), note_launch();
   return cudaGetLastError();
 }
 
@@ -59,7 +59,7 @@ cudaError_t launch_box_scatter(const double2* W, long sWq, long ldw, int ne, int
                                const double* we, double2* Wbox, long sBq, int nq, cudaStream_t st) {
   const long total = (long)nq * ne * ncols;
   if (total <= 0) return cudaSuccess;
-  k_box_scatter<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(W, sWq, ldw, ne, ncols, box, we, Wbox, sBq, nq);
+  k_box_scatter<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(W, sWq, ldw, ne, ncols, box, we, Wbox, sBq, nq), note_launch();
   return cudaGetLastError();
 }
 
@@ -244,7 +244,7 @@ cudaError_t launch_axis_dft_df(const double2* in, long sa_in, int A, long C, int
   if (smem > 48 * 1024) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((C + 255) / 256), (unsigned)A, 1);
   auto go = [&](auto kern) -> cudaError_t {
-    kern<<<grid, 256, smem, st>>>(in, sa_in, C, E, N, out, sa_out);
+    kern<<<grid, 256, smem, st>>>(in, sa_in, C, E, N, out, sa_out), note_launch();
     return cudaGetLastError();
   };
   switch (B) {
@@ -273,7 +273,7 @@ cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B,
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    kern<<<grid, 256, smem, st>>>(in, sa_in, C, B, E, N, j0, nj, paired, out, sa_out);
+    kern<<<grid, 256, smem, st>>>(in, sa_in, C, B, E, N, j0, nj, paired, out, sa_out), note_launch();
     return cudaGetLastError();
   };
   switch (B) {
@@ -414,7 +414,7 @@ cudaError_t launch_axis_adj_paired(const double2* in, long sa_in, long sj_in, lo
   const long cols = (long)R * CC;
   const dim3 grid((unsigned)((cols + 255) / 256), (unsigned)A, 1);
   auto go = [&](auto kern) -> cudaError_t {
-    kern<<<grid, 256, smem, st>>>(in, sa_in, sj_in, ldr_in, R, CC, E, N, out, sa_out, sb_out, ldr_out, accumulate);
+    kern<<<grid, 256, smem, st>>>(in, sa_in, sj_in, ldr_in, R, CC, E, N, out, sa_out, sb_out, ldr_out, accumulate), note_launch();
     return cudaGetLastError();
   };
   switch (B) {
@@ -446,7 +446,7 @@ cudaError_t launch_axis_adj(const double2* in, long sa_in, long sj_in, long ldr_
       if (e != cudaSuccess) return e;
     }
     kern<<<grid, 256, smem, st>>>(in, sa_in, sj_in, ldr_in, R, CC, E, j0, nj, out, sa_out, sb_out, ldr_out,
-                                  accumulate);
+                                  accumulate), note_launch();
     return cudaGetLastError();
   };
   switch (B) {
@@ -482,7 +482,7 @@ cudaError_t launch_box_gather(const double2* Sbox, long sBq, int ncols, const in
                               double2* G, long sGq, int nq, cudaStream_t st) {
   const long total = (long)nq * ne * ncols;
   if (total <= 0) return cudaSuccess;
-  k_box_gather<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Sbox, sBq, ncols, box, we, ne, G, sGq, nq);
+  k_box_gather<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Sbox, sBq, ncols, box, we, ne, G, sGq, nq), note_launch();
   return cudaGetLastError();
 }
 
@@ -503,7 +503,7 @@ __global__ void k_grid_points(int n1, int n2, int n3, double s1, double s2, doub
 cudaError_t launch_grid_points(int n1, int n2, int n3, const double* shift, double* k, cudaStream_t st) {
   const long nk = (long)n1 * n2 * n3;
   if (nk <= 0) return cudaSuccess;
-  k_grid_points<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(n1, n2, n3, shift[0], shift[1], shift[2], k);
+  k_grid_points<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(n1, n2, n3, shift[0], shift[1], shift[2], k), note_launch();
   return cudaGetLastError();
 }
 

@@ -83,10 +83,22 @@ __device__ __forceinline__ float2 df_add(float ah, float al, float bh, float bl)
   two_sum(s, __fadd_rn(e, __fadd_rn(al, bl)), h, l);
   return make_float2(h, l);
 }
-// split of a double into h + l (|residual| <= 2^-48 |x|; magnitudes below 2^-126 flush to 0)
+// split of a double into h + l (|residual| <= 2^-48 |x|; magnitudes below 2^-126 flush to 0),
+// by integer and FP32 operations: h = x rounded to 24 bits (d2f_i); x - h, an integer D of at most
+// 29 bits in units of x's last place (the bit patterns of x and h differ by exactly that, also
+// when h rounded up to the next power of two), goes to FP32 as 2^14 D_hi + D_lo through two
+// exact magic-number conversions and one rounding FMA, then takes its power of two
 __device__ __forceinline__ float2 df_split(double x) {
   const float h = d2f_i(x);
-  return make_float2(h, d2f_i(x - f2d_i(h)));
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 949 || e >= 1151) return make_float2(h, 0.f);  // the last place of x is below FP32's range
+  const long long hb = (b + (1LL << 28)) & ~((1LL << 29) - 1);
+  const int D = (int)(b - hb);  // |D| <= 2^28
+  const float dlo = __int_as_float(0x4B000000 | (D & 0x3FFF)) - 8388608.f;           // D mod 2^14
+  const float dhi = __int_as_float(0x4B400000 + (D >> 14)) - 12582912.f;             // floor(D / 2^14)
+  const float l = fmaf(dhi, 16384.f, dlo) * __int_as_float((e - 948) << 23);        // x 2^(e - 1075)
+  return make_float2(h, b < 0 ? -l : l);
 }
 __device__ __forceinline__ float4 shfl_f4(float4 v, int src) {
   return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
@@ -412,29 +424,47 @@ constexpr size_t jm_smem_bytes(int np) {
   return 4 * ((size_t)np * np * (32 / np) * 40 + (size_t)np * 32 * 24 + (size_t)(np / 2 + 1) * 32 * 16);
 }
 
+// x 2^s by an exponent add (integer operations: on GB300 every FP64 instruction costs the FP64
+// pipe ~64 issue slots); zero, subnormal inputs and results below 2^-1022 give 0
+__device__ __forceinline__ double scale2_i(double x, int s) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0 || e + s <= 0) return 0.0;
+  return __longlong_as_double(b + ((long long)s << 52));
+}
+
 // Loads the group's matrix (its Hermitian part: the diagonal's imaginary parts dropped), padded to
-// NP with zeros, and scales it by a power of two to ||A||_F in [0.5, 1) (exact), which keeps every
-// FP32 quantity in range; the eigenvalues are scaled back by 1 / isc at the end.
+// NP with zeros, and scales it by 2^sexp (exact) so that its largest entry lies in [0.5, 1), which
+// keeps every FP32 quantity in range; the eigenvalues are scaled back by 2^-sexp at the end.
+// fro2f: ||A||_F^2 of the scaled matrix in FP32 (it only sets thresholds), in [0.25, NP^2).
+// Integer and FP32 operations only.
 template <int NP>
 __device__ __forceinline__ void jm_load(const double2* __restrict__ A, long sA, long lda, int n, long mat, bool valid,
-                                        int j, int base, double2 (&a)[NP], double& fro2, double& isc) {
+                                        int j, int base, double2 (&a)[NP], float& fro2f, int& sexp) {
 #pragma unroll
   for (int r = 0; r < NP; ++r) a[r] = (valid && r < n && j < n) ? A[mat * sA + (long)r * lda + j] : make_double2(0.0, 0.0);
 #pragma unroll
   for (int r = 0; r < NP; ++r)
     if (r == j) a[r].y = 0.0;
-  double my2 = 0.0;
+  int em = 0;  // largest biased exponent of the group's entries
 #pragma unroll
-  for (int r = 0; r < NP; ++r) my2 = fma(a[r].x, a[r].x, fma(a[r].y, a[r].y, my2));
-  fro2 = 0.0;
+  for (int r = 0; r < NP; ++r) {
+    em = max(em, (int)((__double_as_longlong(a[r].x) >> 52) & 0x7FF));
+    em = max(em, (int)((__double_as_longlong(a[r].y) >> 52) & 0x7FF));
+  }
 #pragma unroll
-  for (int i = 0; i < NP; ++i) fro2 += shfl_d(my2, base + i);
-  int fexp = 0;
-  frexp(sqrt(fro2), &fexp);
-  isc = fro2 > 0.0 ? ldexp(1.0, -fexp) : 1.0;
+  for (int i = 0; i < NP; ++i) em = max(em, __shfl_sync(0xffffffffu, em, base + i));
+  sexp = em > 0 ? 1022 - em : 0;
+  float my2 = 0.f;
 #pragma unroll
-  for (int r = 0; r < NP; ++r) a[r] = make_double2(a[r].x * isc, a[r].y * isc);
-  fro2 *= isc * isc;
+  for (int r = 0; r < NP; ++r) {
+    a[r] = make_double2(scale2_i(a[r].x, sexp), scale2_i(a[r].y, sexp));
+    const float fx = d2f_i(a[r].x), fy = d2f_i(a[r].y);
+    my2 = fmaf(fx, fx, fmaf(fy, fy, my2));
+  }
+  fro2f = 0.f;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) fro2f += shfl_d(my2, base + i);
 }
 
 // FP32 preconditioning of k_jacobi_mixed, a kernel of its own: cyclic Jacobi sweeps in FP32 on the
@@ -456,8 +486,9 @@ __global__ void __launch_bounds__(128) k_jacobi_f32(const double2* __restrict__ 
   const long mat = warp * G + grp;
   const bool valid = in_group && mat < batch;
   double2 a[NP];
-  double fro2, isc;
-  jm_load<NP>(A, sA, lda, n, mat, valid, j, base, a, fro2, isc);
+  float fro2f;
+  int sexp;
+  jm_load<NP>(A, sA, lda, n, mat, valid, j, base, a, fro2f, sexp);
   float2 vf[NP];
   float2 af[NP];
 #pragma unroll
@@ -465,7 +496,6 @@ __global__ void __launch_bounds__(128) k_jacobi_f32(const double2* __restrict__ 
     af[r] = make_float2(d2f_i(a[r].x), d2f_i(a[r].y));
     vf[r] = make_float2(r == j ? 1.f : 0.f, 0.f);
   }
-  const float fro2f = (float)fro2;
   const float thr32 = 1e-30f * fro2f + 1e-37f;
   const float tol32 = 1e-12f * fro2f;
   bool c32 = !valid;
@@ -501,8 +531,10 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
   const bool valid = in_group && mat < batch;
 
   double2 a[NP];
-  double fro2, isc;
-  jm_load<NP>(A, sA, lda, n, mat, valid, j, base, a, fro2, isc);
+  float fro2f;
+  int sexp;
+  jm_load<NP>(A, sA, lda, n, mat, valid, j, base, a, fro2f, sexp);
+  const double fro2 = f2d_i(fro2f);
   // the FP32 eigenvector estimate of k_jacobi_f32 (padded columns: unit vectors)
   double2 v[NP];
 #pragma unroll
@@ -515,7 +547,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
   // ---- refinement
   const bool loose = polish_tol >= 1e-13;
   const float th2f = loose ? 1e-8f : 1e-16f;  // (final |E_ij|)^2
-  const float tolc2f = (float)((loose ? 1e-22 : 1.6e-29) * fro2);  // (1e-11 ||A||_F)^2, (4e-15 ||A||_F)^2
+  const float tolc2f = (loose ? 1e-22f : 1.6e-29f) * fro2f;  // (1e-11 ||A||_F)^2, (4e-15 ||A||_F)^2
   const float thc2f = 1e-6f;  // (largest first-order angle)^2
   // Shared memory per warp (jm_smem_bytes): A, its 3M pre-sums and its double-float split
   // (element (r, s) of group g at [(r NP + s) G + g], so the groups of a warp read consecutive
@@ -535,7 +567,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
 #pragma unroll
     for (int r = 0; r < NP; ++r) {
       shA[(r * NP + j) * G + grp] = a[r];
-      shP[(r * NP + j) * G + grp] = a[r].x + a[r].y;
+      if (!loose) shP[(r * NP + j) * G + grp] = a[r].x + a[r].y;  // read by FP64 steps only
       const float2 sx = df_split(a[r].x), sy = df_split(a[r].y);
       shD[(r * NP + j) * G + grp] = make_float4(sx.x, sx.y, sy.x, sy.y);
     }
@@ -546,9 +578,10 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
 
   // The correction of one step from the products of the pairs.  slot0(gx, sx) gives the real
   // parts of x_j^H x_j and x_j^H (A x_j) in double; slot(d, src, gf, sf) gives g = x_i^H x_j and
-  // s = x_i^H (A x_j) in FP32 for slot d >= 1, whose x_i the lane src holds; pre_update() runs
-  // once every product is taken.  A step may end the refinement only if final_ok.
-  auto correct = [&](auto&& slot0, auto&& slot, auto&& pre_update, bool final_ok) {
+  // s = x_i^H (A x_j) in FP32 for slot d >= 1, whose x_i the lane src holds; xhead(r) is x_j[r]
+  // in FP32 and update(acc, keep) sets x_j += acc (x_j unchanged where keep).  A step may end the
+  // refinement only if final_ok.
+  auto correct = [&](auto&& slot0, auto&& slot, auto&& xhead, auto&& update, bool final_ok) {
     double g0x, s0x;
     slot0(g0x, s0x);
     // Rayleigh quotient of x_j: 1 / g0 = 1 + e + e^2 + e^3 with e = 1 - g0 (|e| ~ 1e-6, then
@@ -595,7 +628,6 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       kf[d - 1] = K;
       if (own) er[d] = make_float2(hh.x + K.x, hh.y + K.y);
     }
-    pre_update();
     // mirrored half: lane i' = j - d holds the pair (j, i') in its slot d; E_{i'j} = conj(h - k)
 #pragma unroll
     for (int d = 1; d <= H; ++d) {
@@ -621,7 +653,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     float2 xf[NP], acc[NP];
 #pragma unroll
     for (int r = 0; r < NP; ++r) {
-      xf[r] = make_float2(d2f_i(v[r].x), d2f_i(v[r].y));
+      xf[r] = xhead(r);
       acc[r] = make_float2(0.f, 0.f);
     }
 #pragma unroll
@@ -636,9 +668,8 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
         acc[r].y = fmaf(xi.x, e.y, fmaf(xi.y, e.x, acc[r].y));
       }
     }
+    update(acc, done);
     if (!done) {
-#pragma unroll
-      for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x + f2d_i(acc[r].x), v[r].y + f2d_i(acc[r].y));
       if (final_ok && emx_g <= th2f && !unres_g) {
         done = true;
         lam = lt + f2d_i(shift);
@@ -699,7 +730,13 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       gf = make_float2(d2f_i(g.x), d2f_i(g.y));
       sf = make_float2(d2f_i(sv.x), d2f_i(sv.y));
     };
-    correct(slot0, slot, [] {}, true);
+    auto xhead = [&](int r) { return make_float2(d2f_i(v[r].x), d2f_i(v[r].y)); };
+    auto update = [&](const float2(&acc)[NP], bool keep) {
+      if (keep) return;
+#pragma unroll
+      for (int r = 0; r < NP; ++r) v[r] = make_double2(v[r].x + f2d_i(acc[r].x), v[r].y + f2d_i(acc[r].y));
+    };
+    correct(slot0, slot, xhead, update, true);
   };
 
   // Double-float products on the FP32 pipe (~2^-47 of the largest term per product sum): w = A x_j
@@ -755,11 +792,11 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
         df_acc(R3, V3, mi.x, mi.y, wpr.x, wpr.y);
       }
       // real part p1 + p2, imaginary part p3 - (p1 - p2), each from exact head sums
-      auto parts = [](float P1, float Q1, float P2, float Q2, float P3, float Q3, float2& f, double& x) {
+      auto parts = [d](float P1, float Q1, float P2, float Q2, float P3, float Q3, float2& f, double& x) {
         float hs, he;
         two_sum(P1, P2, hs, he);
         const float rt = __fadd_rn(he, __fadd_rn(Q1, Q2));
-        x = f2d_i(hs) + f2d_i(rt);
+        if (d == 0) x = f2d_i(hs) + f2d_i(rt);
         f.x = __fadd_rn(hs, rt);
         float ds, de;
         two_sum(P1, -P2, ds, de);
@@ -769,7 +806,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
         f.y = __fadd_rn(ys, __fadd_rn(ye, __fsub_rn(Q3, dt)));
       };
       float2 gf, sf;
-      double gx, sx;
+      double gx = 0.0, sx = 0.0;
       parts(G1, U1, G2, U2, G3, U3, gf, gx);
       parts(R1, V1, R2, V2, R3, V3, sf, sx);
       shGS[d * 32] = make_float4(gf.x, gf.y, sf.x, sf.y);
@@ -787,12 +824,20 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
       gf = make_float2(q.x, q.y);
       sf = make_float2(q.z, q.w);
     };
-    auto rejoin = [&] {
+    auto xhead = [&](int r) { return make_float2(vd[r].x, vd[r].z); };
+    // x_j = (h + l) + acc joined to double with one FP64 addition per value: (h + acc) by a two-sum,
+    // its error into l
+    auto update = [&](const float2(&acc)[NP], bool keep) {
+      auto join = [](float h, float l, float c) {
+        float s, e;
+        two_sum(h, c, s, e);
+        return f2d_i(s) + f2d_i(__fadd_rn(l, e));
+      };
 #pragma unroll
       for (int r = 0; r < NP; ++r)
-        v[r] = make_double2(f2d_i(vd[r].x) + f2d_i(vd[r].y), f2d_i(vd[r].z) + f2d_i(vd[r].w));
+        v[r] = make_double2(join(vd[r].x, vd[r].y, keep ? 0.f : acc[r].x), join(vd[r].z, vd[r].w, keep ? 0.f : acc[r].y));
     };
-    correct(slot0, slot, rejoin, final_ok);
+    correct(slot0, slot, xhead, update, final_ok);
   };
 
   // The first step runs in double-float (from the FP32 eigenvectors it only has to reach ~1e-12);
@@ -962,7 +1007,7 @@ __global__ void __launch_bounds__(128) k_jacobi_mixed(const double2* __restrict_
     if (i < n && (li < lam || (li == lam && i < j))) ++rank;
   }
   if (valid && j < n) {
-    w[mat * sw + rank] = lam / isc;
+    w[mat * sw + rank] = scale2_i(lam, -sexp);
     double2* out = V + mat * sV;
 #pragma unroll
     for (int r = 0; r < NP; ++r)
@@ -1001,9 +1046,9 @@ cudaError_t launch_jacobi_mixed(const double2* A, long sA, long lda, int n, long
                                            (int)smem);                                                               \
       if (e != cudaSuccess) return e;                                                                                \
     }                                                                                                                \
-    k_jacobi_f32<NPV><<<(unsigned)blocks, threads, 0, st>>>(A, sA, lda, n, batch, T, sT);                            \
+    k_jacobi_f32<NPV><<<(unsigned)blocks, threads, 0, st>>>(A, sA, lda, n, batch, T, sT), note_launch();                            \
     k_jacobi_mixed<NPV><<<(unsigned)blocks, threads, smem, st>>>(A, sA, lda, n, batch, w, sw, V, sV, T, sT,         \
-                                                                  max_sweeps, polish_tol, status);                   \
+                                                                  max_sweeps, polish_tol, status), note_launch();                   \
     break;
   switch (np) {
     EPH_JM(2) EPH_JM(4) EPH_JM(6) EPH_JM(8) EPH_JM(10) EPH_JM(12)
@@ -1027,7 +1072,7 @@ cudaError_t launch_jacobi(const double2* A, long sA, long lda, int n, long batch
   if (blocks > 2147483647L) return cudaErrorInvalidConfiguration;
 #define EPH_JC(NPV)                                                                                       \
   case NPV:                                                                                               \
-    k_jacobi<NPV><<<(unsigned)blocks, threads, 0, st>>>(A, sA, lda, n, batch, w, sw, V, sV, max_sweeps, status); \
+    k_jacobi<NPV><<<(unsigned)blocks, threads, 0, st>>>(A, sA, lda, n, batch, w, sw, V, sV, max_sweeps, status), note_launch(); \
     break;
   switch (np) {
     EPH_JC(2) EPH_JC(4) EPH_JC(6) EPH_JC(8) EPH_JC(10) EPH_JC(12) EPH_JC(14) EPH_JC(16)

@@ -229,7 +229,7 @@ cudaError_t launch_jacobi_big(const double2* A, long sA, long lda, int n, long b
   // latency of these global (L2-resident) accesses needs many threads in flight: about n^2 / 8
   // threads (128 .. 1024)
   k_jacobi_big<<<(unsigned)batch, threads_for((long)n * n / 8), 0, st>>>(A, sA, lda, n, w, sw, V, sV, work,
-                                                                         max_sweeps, status);
+                                                                         max_sweeps, status), note_launch();
   return cudaGetLastError();
 }
 
@@ -589,7 +589,7 @@ cudaError_t launch_eigh_big(const double2* A, long sA, long lda, int n, long bat
     }
     // FP32 eigenvectors; when they do not fit in shared memory they live in G (free until the Gram)
     k_jacobi32_big<<<(unsigned)nb, threads_for((long)sh.np * sh.np / 4), sh.smem, st>>>(
-        Ab, sA, lda, n, sh.np, sh.lds, sh.vsm, reinterpret_cast<float2*>(G), Vw, 12);
+        Ab, sA, lda, n, sh.np, sh.lds, sh.vsm, reinterpret_cast<float2*>(G), Vw, 12), note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // The products: FP64 for the FP64 eigendecomposition; double-float on the FP32 pipe (~1e-13
     // relative) when eigenvalues are needed to ~1e-12 ||A|| (polish_tol >= 1e-13)
@@ -609,7 +609,7 @@ cudaError_t launch_eigh_big(const double2* A, long sA, long lda, int n, long bat
       if ((e = mh(Vw, Vw, G)) != cudaSuccess) return e;
       if ((e = mm(Vw, n, nn, G, T)) != cudaSuccess) return e;
       const long tot = (long)nb * nn;
-      k_ns_update<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Vw, T, tot);
+      k_ns_update<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Vw, T, tot), note_launch();
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // A' = V^H (A V)
@@ -620,10 +620,10 @@ cudaError_t launch_eigh_big(const double2* A, long sA, long lda, int n, long bat
     const double th2 = polish_tol >= 1e-13 ? 1e-10 : 1e-16;
     k_jacobi_polish_big<<<(unsigned)nb, threads_for(nn / 8), 0, st>>>(M, Vw, n, lam, polish_tol, th2,
                                                                        polish_tol >= 1e-13 ? 1 : 0, max_sweeps,
-                                                                       status);
+                                                                       status), note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = mm(Vw, n, nn, M, T)) != cudaSuccess) return e;
-    k_eig_sort_big<<<(unsigned)nb, threads_for(nn / 4), 0, st>>>(Vw, T, lam, n, w + b0 * sw, sw, V + b0 * sV, sV);
+    k_eig_sort_big<<<(unsigned)nb, threads_for(nn / 4), 0, st>>>(Vw, T, lam, n, w + b0 * sw, sw, V + b0 * sV, sV), note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

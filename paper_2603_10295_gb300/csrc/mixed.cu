@@ -45,7 +45,7 @@ __global__ void k_split_a(const double2* __restrict__ P, long ldp, int n, int ne
 cudaError_t launch_split_a(const double2* P, long ldp, int n, int ne, int kp, float* Ahi, float* Alo, cudaStream_t st) {
   const long tot = (long)n * kp;
   if (tot <= 0) return cudaSuccess;
-  k_split_a<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, ldp, n, ne, kp, Ahi, Alo);
+  k_split_a<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, ldp, n, ne, kp, Ahi, Alo), note_launch();
   return cudaGetLastError();
 }
 
@@ -77,7 +77,7 @@ cudaError_t launch_split_b(const double2* W, long ldw, long sW, int col0, int nc
                            float* Bhi, float* Blo, cudaStream_t st) {
   const long tot = 2L * ncols * kp * nq;
   if (tot <= 0) return cudaSuccess;
-  k_split_b<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, kp, nq, Bhi, Blo);
+  k_split_b<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, kp, nq, Bhi, Blo), note_launch();
   return cudaGetLastError();
 }
 
@@ -115,7 +115,7 @@ cudaError_t launch_digits_a(const double2* P, long ldp, int n, int ne, int kp, d
   if (ndig < 1 || ndig > 5 || (plane_rows > 0 && plane_rows < n)) return cudaErrorInvalidValue;
   const long plane = plane_rows > 0 ? (long)plane_rows * kp : tot;
   k_digits_a<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, ldp, n, ne, kp, 1.0 / scale, ndig,
-                                                          static_cast<__nv_bfloat16*>(D), plane);
+                                                          static_cast<__nv_bfloat16*>(D), plane), note_launch();
   return cudaGetLastError();
 }
 
@@ -129,7 +129,7 @@ __global__ void k_f32pairs_to_c128(const float2* __restrict__ X, long n, double2
 
 cudaError_t launch_f32pairs_to_c128(const float2* X, long n, double2* Y, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_f32pairs_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, n, Y);
+  k_f32pairs_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, n, Y), note_launch();
   return cudaGetLastError();
 }
 
@@ -205,12 +205,12 @@ cudaError_t launch_digits_b(const double2* W, long ldw, long sW, int col0, int n
   if (ndig < 1 || ndig > 5) return cudaErrorInvalidValue;
   const long cols = (long)ncols * nq;
   if (cols <= 0) return cudaSuccess;
-  k_colscale_b<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, nq, sB, 2L * ncols);
+  k_colscale_b<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, nq, sB, 2L * ncols), note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long tot = 2L * ncols * kp * nq;
   k_digits_b<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(W, ldw, sW, col0, ncols, ne, kp, nq, sB, slice, ndig,
-                                                           static_cast<__nv_bfloat16*>(D));
+                                                           static_cast<__nv_bfloat16*>(D)), note_launch();
   return cudaGetLastError();
 }
 
@@ -225,7 +225,7 @@ __global__ void k_pairs_to_c128(const float2* __restrict__ Hp, long n, double2* 
 
 cudaError_t launch_pairs_to_c128(const float2* Hp, long n, double2* H, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_pairs_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Hp, n, H);
+  k_pairs_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Hp, n, H), note_launch();
   return cudaGetLastError();
 }
 
@@ -349,7 +349,7 @@ cudaError_t launch_band_rotate_ff(const float* Y, long ldy_floats, const double2
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
   k_band_rotate_ff<float2><<<(unsigned)pairs, 128, smem, st>>>(reinterpret_cast<const float2*>(Y), ldy_floats / 2, Ukq,
                                                                 Uk, nk, nm, nb, reinterpret_cast<float2*>(g),
-                                                                sgq_floats / 2, keep);
+                                                                sgq_floats / 2, keep), note_launch();
   return cudaGetLastError();
 }
 
@@ -365,7 +365,7 @@ cudaError_t launch_band_rotate_ff_f64(const double2* Y, long ldy, const double2*
     if (e != cudaSuccess) return e;
   }
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
-  k_band_rotate_ff<double2><<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq, keep);
+  k_band_rotate_ff<double2><<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq, keep), note_launch();
   return cudaGetLastError();
 }
 

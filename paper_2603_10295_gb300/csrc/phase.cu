@@ -29,7 +29,7 @@ cudaError_t launch_phase(const double* pts, int n, const int* R, const double* w
   if (total <= 0) return cudaSuccess;
   int threads = 256;
   long blocks = (total + threads - 1) / threads;
-  k_phase<<<(unsigned)blocks, threads, 0, st>>>(pts, n, R, w, nR, P, ldp);
+  k_phase<<<(unsigned)blocks, threads, 0, st>>>(pts, n, R, w, nR, P, ldp), note_launch();
   return cudaGetLastError();
 }
 
@@ -53,7 +53,7 @@ cudaError_t launch_scale_rows(const double2* Q, int nq, const double2* H, int ne
   if (total <= 0) return cudaSuccess;
   int threads = 256;
   k_scale_rows<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(Q, nq, H, ne, cols, B, ldb,
-                                                                                sB);
+                                                                                sB), note_launch();
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ cudaError_t launch_phonon_post(const double* lam, const double2* e, int nq, int 
                                double unit, double* omega, double2* u, cudaStream_t st) {
   long tot = (long)nq * nm * nm;
   if (tot <= 0) return cudaSuccess;
-  k_phonon_post<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(lam, e, nq, nm, invsqrtm, unit, omega, u);
+  k_phonon_post<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(lam, e, nq, nm, invsqrtm, unit, omega, u), note_launch();
   return cudaGetLastError();
 }
 
@@ -77,7 +77,7 @@ cudaError_t launch_mode_rotate(const double2* G1, const double2* u, int nq, int 
   if (nm > 16 || nq > 65535) return cudaErrorInvalidValue;
   long per_q = (long)ne * nb2;
   dim3 grid((unsigned)((per_q + 255) / 256), nq);
-  k_mode_rotate<16><<<grid, 256, 0, st>>>(G1, u, nm, ne, nb2, W, ldw, sW);
+  k_mode_rotate<16><<<grid, 256, 0, st>>>(G1, u, nm, ne, nb2, W, ldw, sW), note_launch();
   return cudaGetLastError();
 }
 
@@ -204,7 +204,7 @@ cudaError_t launch_band_rotate(const double2* Y, long ldy, const double2* Ukq, c
     if (e != cudaSuccess) return e;
   }
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
-  k_band_rotate<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq, keep);
+  k_band_rotate<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, nk, nm, nb, g, sgq, keep), note_launch();
   return cudaGetLastError();
 }
 
@@ -251,7 +251,7 @@ cudaError_t launch_band_rotate_multi(const BandSegs& segs, int nseg, long total,
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const long grid = std::min<long>(total, (long)nsm * per_sm);
-  k_band_rotate_multi<<<(unsigned)grid, 128, smem, st>>>(segs, nseg, total);
+  k_band_rotate_multi<<<(unsigned)grid, 128, smem, st>>>(segs, nseg, total), note_launch();
   return cudaGetLastError();
 }
 
@@ -323,7 +323,7 @@ cudaError_t launch_band_linewidth(const double2* Y, long ldy, const double2* Ukq
   }
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
   k_band_linewidth<<<(unsigned)pairs, 128, smem, st>>>(Y, ldy, Ukq, Uk, epsk, epskq, om, wq, nk, nm, nb, kT, mu, sigma,
-                                                       omega_min, part);
+                                                       omega_min, part), note_launch();
   return cudaGetLastError();
 }
 
@@ -392,7 +392,7 @@ cudaError_t launch_linewidth_terms(const double2* G, long ldg, const double* eps
   if (pairs > 2147483647L) return cudaErrorInvalidConfiguration;
   const size_t smem = (size_t)(nb + nm + 128) * sizeof(double);
   k_linewidth_terms<<<(unsigned)pairs, 128, smem, st>>>(G, ldg, epsk, epskq, om, wq, nk, nm, nb, kT, mu, sigma,
-                                                        omega_min, part);
+                                                        omega_min, part), note_launch();
   return cudaGetLastError();
 }
 
@@ -407,7 +407,7 @@ __global__ void k_sum_over_q(const double* __restrict__ part, int nq, long per_q
 
 cudaError_t launch_sum_over_q(const double* part, int nq, long per_q, double* acc, cudaStream_t st) {
   if (per_q <= 0 || nq <= 0) return cudaSuccess;
-  k_sum_over_q<<<(unsigned)((per_q + 255) / 256), 256, 0, st>>>(part, nq, per_q, acc);
+  k_sum_over_q<<<(unsigned)((per_q + 255) / 256), 256, 0, st>>>(part, nq, per_q, acc), note_launch();
   return cudaGetLastError();
 }
 

@@ -119,17 +119,17 @@ cudaError_t launch_ibz_select(int n1, int n2, int n3, const int* t, int* flag, i
   const long nk = (long)n1 * n2 * n3;
   if (nk <= 0) return cudaSuccess;
   const long nblk = (nk + 1023) / 1024;
-  k_ibz_flags<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(n1, n2, n3, t[0], t[1], t[2], flag);
-  k_scan_blocks<<<(unsigned)nblk, 1024, 0, st>>>(flag, nk, pos, tot);
-  k_scan_totals<<<1, 32, 0, st>>>(tot, (int)nblk, count);
-  k_compact<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(flag, pos, tot, nk, idx);
+  k_ibz_flags<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(n1, n2, n3, t[0], t[1], t[2], flag), note_launch();
+  k_scan_blocks<<<(unsigned)nblk, 1024, 0, st>>>(flag, nk, pos, tot), note_launch();
+  k_scan_totals<<<1, 32, 0, st>>>(tot, (int)nblk, count), note_launch();
+  k_compact<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(flag, pos, tot, nk, idx), note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_ibz_weights(const int* idx, const int* count, int n_max, int n1, int n2, int n3, const int* t,
                                double* w, cudaStream_t st) {
   if (n_max <= 0) return cudaSuccess;
-  k_ibz_weights<<<(n_max + 255) / 256, 256, 0, st>>>(idx, count, n1, n2, n3, t[0], t[1], t[2], w);
+  k_ibz_weights<<<(n_max + 255) / 256, 256, 0, st>>>(idx, count, n1, n2, n3, t[0], t[1], t[2], w), note_launch();
   return cudaGetLastError();
 }
 
@@ -138,23 +138,23 @@ cudaError_t launch_window_select(const double* eps, long nk, int nb, double e_lo
   if (nk <= 0) return cudaSuccess;
   const long nblk = (nk + 1023) / 1024;
   if (nblk > 2147483647L) return cudaErrorInvalidValue;
-  k_window_flags<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(eps, nk, nb, e_lo, e_hi, flag);
-  k_scan_blocks<<<(unsigned)nblk, 1024, 0, st>>>(flag, nk, pos, tot);
-  k_scan_totals<<<1, 32, 0, st>>>(tot, (int)nblk, count);
-  k_compact<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(flag, pos, tot, nk, idx);
+  k_window_flags<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(eps, nk, nb, e_lo, e_hi, flag), note_launch();
+  k_scan_blocks<<<(unsigned)nblk, 1024, 0, st>>>(flag, nk, pos, tot), note_launch();
+  k_scan_totals<<<1, 32, 0, st>>>(tot, (int)nblk, count), note_launch();
+  k_compact<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(flag, pos, tot, nk, idx), note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_window_flags(const double* eps, long n, int nb, double e_lo, double e_hi, int* flag,
                                 cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_window_flags<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(eps, n, nb, e_lo, e_hi, flag);
+  k_window_flags<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(eps, n, nb, e_lo, e_hi, flag), note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_points(const double* kpts, const int* idx, int n, double* out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_gather_points<<<(n + 255) / 256, 256, 0, st>>>(kpts, idx, n, out);
+  k_gather_points<<<(n + 255) / 256, 256, 0, st>>>(kpts, idx, n, out), note_launch();
   return cudaGetLastError();
 }
 

@@ -1451,7 +1451,7 @@ cudaError_t launch_tc_hkq_gemm_b(const void* maps_a5, const void* maps_b5, int M
   const long ntiles = (long)((Nr + tch::BN - 1) / tch::BN) * ((M + tch::BM - 1) / tch::BM) * nq;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
   kern<<<grid, tch::THREADS, tch::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err, a_mod, a_qoff,
-                                                    a_stride, morder);
+                                                    a_stride, morder), note_launch();
   return cudaGetLastError();
 }
 
@@ -1475,7 +1475,7 @@ cudaError_t launch_tc_band_gemm(const void* maps_a4, const void* maps_b4, int M,
   const long ntiles = (long)((Nr + tcb::BN - 1) / tcb::BN) * ((M + tcb::BM - 1) / tcb::BM) * nq;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
   k_tc_band_gemm<<<grid, tcb::THREADS, tcb::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err,
-                                                               a_mod, a_qoff, a_stride);
+                                                               a_mod, a_qoff, a_stride), note_launch();
   return cudaGetLastError();
 }
 
@@ -1493,7 +1493,7 @@ cudaError_t launch_tc_fixed_gemm(const void* maps_a3, const void* maps_b4, int M
   for (int d = 0; d < 4; ++d) maps.b[d] = static_cast<const CUtensorMap*>(maps_b4)[d];
   const long ntiles = (long)((Nr + tcf::BN - 1) / tcf::BN) * ((M + tcf::BM - 1) / tcf::BM) * nq;
   const int grid = (int)(ntiles < sms ? ntiles : sms);
-  k_tc_fixed_gemm<<<grid, tcf::THREADS, tcf::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err);
+  k_tc_fixed_gemm<<<grid, tcf::THREADS, tcf::SMEM_BYTES, st>>>(maps, M, a_row0, Nr, Kp, nq, sA, sB, C, ldc, sC, err), note_launch();
   return cudaGetLastError();
 }
 
@@ -1510,7 +1510,7 @@ cudaError_t launch_tc_split_gemm(const void* mAhi, const void* mAlo, const void*
                                                      *static_cast<const CUtensorMap*>(mAlo),
                                                      *static_cast<const CUtensorMap*>(mBhi),
                                                      *static_cast<const CUtensorMap*>(mBlo), M, a_row0, Nr, Kp, C,
-                                                     ldc, sC, err);
+                                                     ldc, sC, err), note_launch();
   return cudaGetLastError();
 }
 
@@ -1519,12 +1519,12 @@ cudaError_t launch_zdigits_rows(const double2* P, long sr, long se, int rows, in
                                 cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
   if (Kp % tz::BK != 0 || 2 * ne > Kp) return cudaErrorInvalidValue;
-  k_zdig_rows_exp<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, sr, se, rows, ne, ea);
+  k_zdig_rows_exp<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, sr, se, rows, ne, ea), note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long words = (long)rows * (Kp / 2);
   k_zdig_rows<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(P, sr, se, rows, ne, Kp, ea,
-                                                               static_cast<uint32_t*>(planes), words);
+                                                               static_cast<uint32_t*>(planes), words), note_launch();
   return cudaGetLastError();
 }
 
@@ -1533,12 +1533,12 @@ cudaError_t launch_zdigits_cols(const double2* W, long ldw, long sW, int nq, int
   if (nq <= 0 || ncol <= 0) return cudaSuccess;
   if (Kp % tz::BK != 0 || 2 * ne > Kp) return cudaErrorInvalidValue;
   const long cols = (long)nq * ncol;
-  k_zdig_cols_exp<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(W, ldw, sW, nq, ne, ncol, eb);
+  k_zdig_cols_exp<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(W, ldw, sW, nq, ne, ncol, eb), note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long words = cols * (Kp / 2);
   k_zdig_cols<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(W, ldw, sW, nq, ne, ncol, Kp, cj, eb,
-                                                               static_cast<uint32_t*>(planes), 2 * words);
+                                                               static_cast<uint32_t*>(planes), 2 * words), note_launch();
   return cudaGetLastError();
 }
 
@@ -1568,7 +1568,7 @@ cudaError_t launch_tc_zgemm64(const void* a_planes, long a_rows, int a_row0, int
   const long ntiles = (long)((N + tz::BN - 1) / tz::BN) * ((M + tz::BM - 1) / tz::BM);
   const int grid = (int)(ntiles < sms ? ntiles : sms);
   k_tc_zgemm64<<<grid, tz::THREADS, tz::SMEM_BYTES, st>>>(maps, M, a_row0, N, Kp, ea, eb, C, ncq, ldc, sCq, scol, acc,
-                                                          err);
+                                                          err), note_launch();
   return cudaGetLastError();
 }
 

@@ -126,7 +126,7 @@ cudaError_t launch_zgemm(int M, int N, int K, const double2* A, long lda, long s
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   if (!grid_ok(M, N, batch)) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
-  k_zgemm<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0);
+  k_zgemm<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0), note_launch();
   return cudaGetLastError();
 }
 
@@ -138,9 +138,9 @@ cudaError_t launch_zgemm_b2(int M, int N, int K, const double2* A, long lda, lon
   if (batch > 65535 || !grid_ok(M, N, 1)) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
   if (adj)
-    k_zgemm<true, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nbat2, sA2, sB2, sC2);
+    k_zgemm<true, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nbat2, sA2, sB2, sC2), note_launch();
   else
-    k_zgemm<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nbat2, sA2, sB2, sC2);
+    k_zgemm<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nbat2, sA2, sB2, sC2), note_launch();
   return cudaGetLastError();
 }
 
@@ -150,9 +150,9 @@ cudaError_t launch_zgemm_ah(int M, int N, int K, const double2* A, long lda, lon
   if (!grid_ok(M, N, batch)) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
   if (acc)
-    k_zgemm<true, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0);
+    k_zgemm<true, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0), note_launch();
   else
-    k_zgemm<true, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0);
+    k_zgemm<true, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0), note_launch();
   return cudaGetLastError();
 }
 
@@ -214,7 +214,7 @@ static cudaError_t skinny_dispatch(int M, long N, int K, const double2* P, long 
   unsigned blocks = (unsigned)((N + threads - 1) / threads);
 #define EPH_SK(MQ)                                                                                   \
   case MQ:                                                                                           \
-    k_skinny<MQ, REAL_B><<<blocks, threads, 0, st>>>(M, N, K, P, ldp, B, ldb, cs, C, ldc); \
+    k_skinny<MQ, REAL_B><<<blocks, threads, 0, st>>>(M, N, K, P, ldp, B, ldb, cs, C, ldc), note_launch(); \
     break;
   switch (M) {
     EPH_SK(1) EPH_SK(2) EPH_SK(3) EPH_SK(4) EPH_SK(5) EPH_SK(6) EPH_SK(7) EPH_SK(8)
@@ -248,7 +248,7 @@ __global__ void k_transpose(const double2* __restrict__ in, int n, long batch, d
 cudaError_t launch_transpose(const double2* in, int n, long batch, double2* out, cudaStream_t st) {
   const long tot = (long)n * n * batch;
   if (tot <= 0) return cudaSuccess;
-  k_transpose<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, n, batch, out);
+  k_transpose<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, n, batch, out), note_launch();
   return cudaGetLastError();
 }
 
@@ -373,7 +373,7 @@ cudaError_t launch_zgemm_df(int M, int N, int K, const double2* A, long lda, lon
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   if (!grid_ok(M, N, batch)) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
-  k_zgemm_df<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0);
+  k_zgemm_df<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, 1, 0, 0, 0), note_launch();
   return cudaGetLastError();
 }
 
@@ -385,7 +385,7 @@ cudaError_t launch_zgemm_df_b2(int M, int N, int K, const double2* A, long lda, 
   if (batch > 65535 || !grid_ok(M, N, 1)) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)(((N + BN - 1) / BN) * batch), (M + BM - 1) / BM, 1);
 #define EPH_DF(ADJV, O32)                                                                                         \
-  k_zgemm_df<ADJV, O32><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nbat2, sA2, sB2, sC2)
+  k_zgemm_df<ADJV, O32><<<grid, 256, 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, nbat2, sA2, sB2, sC2), note_launch()
   if (adj && out32)
     EPH_DF(true, true);
   else if (adj)
