@@ -38,15 +38,19 @@ UNIT = "g elements/s"
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one bench launch (q batch 4
 # x 64000 k), from an ncu capture of that launch; profiles/k_zgemm_si_full_fp64.md,
-# profiles/k_tc_fixed_gemm_si_full.md, profiles/k_jacobi_mixed_si_full.md.
+# profiles/k_tc_fixed_gemm_si_full.md, profiles/k_jacobi_split_si_full.md.
 # Keyed by (kernel, workload, q batch).
-# Per-matrix work of the batched 8x8 H(k+q) eigensolve (k_jacobi_f32<8> FP32 sweeps + k_jacobi_mixed<8>
-# refinement, one eig call), keyed by (nb, form), from one ncu capture of the 55,296-matrix launches
-# (bench.py --capture si-fp64-grid / si-mixed-grid, profiles/k_jacobi_split_si_full.md): FP64 flops
-# (2 DFMA + DMUL + DADD thread instructions) and warp instructions issued, both kernels summed
-EIG_COUNTS = {(8, "fp64"): dict(fp64_flop=None, warp_inst=None),
-              (8, "mixed"): dict(fp64_flop=None, warp_inst=None)}
-# instruction issue of GB300: 152 SMs x 4 schedulers x one warp instruction per clock x 2.07 GHz
+# Per-matrix work of the batched 8x8 H(k+q) eigensolve, keyed by (nb, form): (kernel, warp
+# instructions issued, FP64 flops = 2 DFMA + DMUL + DADD thread instructions) per kernel of one eig
+# call, from one ncu capture of the 55,296-matrix launches (bench.py --capture si-fp64-grid /
+# si-mixed-grid; profiles/k_jacobi_split_si_full.md)
+EIG_COUNTS = {(8, "fp64"): [("k_jacobi_f32<8>", 161562742 / 55296, 0.0),
+                            ("k_jacobi_mixed<8>", 205258752 / 55296, (2 * 185794560 + 884736 + 69451776) / 55296)],
+              (8, "mixed"): [("k_jacobi_f32<8>", 161562742 / 55296, 0.0),
+                             ("k_jacobi_mixed<8>", 147654144 / 55296, (2 * 884736 + 442368 + 11059200) / 55296)]}
+# instruction issue of GB300: 152 SMs x 4 schedulers x one warp instruction per clock x 2.07 GHz,
+# which equals the FP64 unit peak in flop/s (152 SMs x 2 DFMA x 2 flop per clock): a kernel's floor
+# in issue slots is max(warp instructions, FP64 flops)
 ISSUE_PEAK = 152 * 4 * 2.07e9
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at one step = 4 q x 64,000 k
 TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
@@ -59,8 +63,8 @@ TRAFFIC = {("k_tc_fixed_gemm", "si_full", 4): 185421824.0 + 731285504.0,
 # (bench.py --capture si-fp64-grid / si-mixed-grid, 55,296 pairs per launch), scaled to a launch
 # by its units: these kernels stream their inputs once, so traffic grows in proportion
 TRAFFIC_PER_UNIT = {  # one eig call: k_jacobi_f32 + k_jacobi_mixed (A is read by both)
-                    ("k_jacobi", "si_full", 4, "fp64"): (56679424.0 + 1968384.0 + 85091584.0 + 15082752.0) / 55296,
-                    ("k_jacobi", "si_full", 4, "mixed"): (56681472.0 + 1915648.0 + 85043200.0 + 14231040.0) / 55296,
+                    ("k_jacobi", "si_full", 4, "fp64"): (56677888.0 + 2453248.0 + 85100800.0 + 15118848.0) / 55296,
+                    ("k_jacobi", "si_full", 4, "mixed"): (56679424.0 + 2064128.0 + 85020928.0 + 14424064.0) / 55296,
                     ("k_band_tc_small64", "si_full", 4, "grid"): (424918528.0 + 287893248.0) / 55296,
                     ("k_band_tc_small", "si_full", 4, "grid"): (424756224.0 + 136090112.0) / 55296}
 
@@ -899,32 +903,32 @@ def run_libeph(args):
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"}
 
     def roof_eig(r, form="fp64"):
-        # two floors for the eigensolve: its FP64 flops at the FP64 unit peak, and its warp
-        # instructions at one per scheduler and clock; the higher one bounds it
+        # each kernel of the eigensolve is bounded by its warp instructions at one per scheduler and
+        # clock or by its FP64 flops at the FP64 unit peak, whichever is larger (both in issue
+        # slots, the two peaks being equal); the kernels run one after the other, so their floors add
         eg_ms, eg_n = r["prof"]["eig"]
-        c = EIG_COUNTS.get((nb, form)) or {}
+        ks = EIG_COUNTS.get((nb, form))
         t = eg_ms / max(eg_n, 1) * 1e-3
         mats = float(args.steps) * QB * nk / max(eg_n, 1)
-        f64, wi = c.get("fp64_flop"), c.get("warp_inst")
-        kern = ("k_jacobi_f32<%d> (FP32 Jacobi sweeps) + k_jacobi_mixed<%d> (Ogita-Aishima refinement: one "
-                "double-float step on the FP32 pipe%s)" % (nb + (nb & 1), nb + (nb & 1),
-                                                           ", one FP64 step" if form == "fp64" else ""))
-        out = {"bound": "alu", "kernel": kern, "achieved": None, "peak": None, "unit": None, "frac": None,
-               "matrices_per_call": mats, "fp64_flop_per_matrix": f64, "warp_inst_per_matrix": wi,
+        npd = nb + (nb & 1)
+        out = {"bound": "alu",
+               "kernel": "k_jacobi_f32<%d> (FP32 Jacobi sweeps) + k_jacobi_mixed<%d> (Ogita-Aishima refinement: "
+                         "one double-float step on the FP32 pipe%s)"
+                         % (npd, npd, ", one FP64 step" if form == "fp64" else ""),
+               "achieved": None, "peak": ISSUE_PEAK / 1e12, "unit": "T issue slots/s", "frac": None,
+               "matrices_per_call": mats,
                "traffic": (TRAFFIC_PER_UNIT.get(("k_jacobi", args.workload, QB, form), 0.0) * mats) or None,
-               "algorithmic_bytes": mats * (nb * nb * 16 + nb * nb * 16 + nb * 8)}
-        if not (f64 and wi and t):
+               "algorithmic_bytes": mats * (nb * nb * 16 + nb * nb * 16 + nb * 8),
+               "peak_source": "152 SMs x 4 schedulers x 1 warp instruction/clk x 2.07 GHz (= the FP64 unit "
+                              "peak in flop/s)"}
+        if not (ks and t):
             return out
-        t64, tis = f64 * mats / FP64_PEAK_FLOPS, wi * mats / ISSUE_PEAK
-        out.update({"fp64_frac": t64 / t, "issue_frac": tis / t})
-        if t64 >= tis:
-            out.update({"achieved": f64 * mats / t / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                        "frac": t64 / t, "binding": "FP64 pipe",
-                        "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 unit count, max clock)"})
-        else:
-            out.update({"achieved": wi * mats / t / 1e12, "peak": ISSUE_PEAK / 1e12,
-                        "unit": "T warp instructions/s", "frac": tis / t, "binding": "instruction issue",
-                        "peak_source": "152 SMs x 4 schedulers x 1 warp instruction/clk x 2.07 GHz"})
+        slots = sum(max(wi, f64) for _, wi, f64 in ks)
+        out.update({"achieved": slots * mats / t / 1e12, "frac": slots * mats / ISSUE_PEAK / t,
+                    "issue_slots_per_matrix": slots,
+                    "per_kernel": [{"kernel": k, "warp_inst_per_matrix": wi, "fp64_flop_per_matrix": f64,
+                                    "binding": "FP64 pipe" if f64 > wi else "instruction issue"}
+                                   for k, wi, f64 in ks]})
         return out
 
     def roof_band_tc(r, g3_bytes, fp64=False):
