@@ -111,12 +111,17 @@ struct Cx<double> {
   using T2 = double2;
   __device__ static T2 make(double x, double y) { return make_double2(x, y); }
   __device__ static double rsq(double x) { return rsqrt(x); }
+  // 2 sign(dd) / (|dd| + sqrt(s)), s > 0
+  __device__ static double rot_r(double dd, double s) { return copysign(2.0, dd) / (fabs(dd) + sqrt(s)); }
 };
 template <>
 struct Cx<float> {
   using T2 = float2;
   __device__ static T2 make(float x, float y) { return make_float2(x, y); }
   __device__ static float rsq(float x) { return rsqrtf(x); }
+  // the FP32 preconditioning only steers the sweeps (the refinement sets the accuracy): the
+  // hardware reciprocal square root and division, no IEEE-rounding sequences or slow paths
+  __device__ static float rot_r(float dd, float s) { return __fdividef(copysignf(2.f, dd), fabsf(dd) + s * rsqrtf(s)); }
 };
 
 // One round of the circle schedule in precision T (double for the eigensolve proper,
@@ -146,7 +151,7 @@ __device__ __forceinline__ void jacobi_round(typename Cx<T>::T2 (&a)[NP], typena
   T2 sig = Cx<T>::make(0, 0);
   if (b2 > thresh2) {
     const T dd = aqq - app;
-    const T r = copysign(T(2), dd) / (fabs(dd) + sqrt(fma(dd, dd, T(4) * b2)));
+    const T r = Cx<T>::rot_r(dd, fma(dd, dd, T(4) * b2));
     tb = r * b2;
     c = Cx<T>::rsq(fma(r * r, b2, T(1)));
     const T cr = c * r;
@@ -473,7 +478,7 @@ __device__ __forceinline__ void jm_load(const double2* __restrict__ A, long sA, 
 // unsorted).  Its small register and code footprint keeps 6 CTAs per SM busy, where the fused
 // kernel ran these latency-bound sweeps at the refinement's occupancy.
 template <int NP>
-__global__ void __launch_bounds__(128) k_jacobi_f32(const double2* __restrict__ A, long sA, long lda, int n,
+__global__ void __launch_bounds__(128, (NP <= 8 ? 6 : 1)) k_jacobi_f32(const double2* __restrict__ A, long sA, long lda, int n,
                                                     long batch, float2* __restrict__ T, long sT) {
   constexpr int G = 32 / NP;
   const int lane = threadIdx.x & 31;
