@@ -844,7 +844,11 @@ def run_libeph(args):
         outs = float(args.steps) * QB * nk * NW / max(ft_n, 1)
         t = ft_ms / max(ft_n, 1) * 1e-3
         ach = (4 * M + 2) * outs / t
-        algo = 16.0 * outs * (1 + (2 * M + 1) / float(wl.kgrid[0]))
+        # the slot columns read once (16 B), the outputs written once: 16 B each, except the mixed
+        # form's G3 columns (all but the first Nb^2 of each row), written as complex64
+        mixed_out = r.get("form") == "mixed"
+        out_bytes = (16.0 * nb * nb + (8.0 if mixed_out else 16.0) * nm * nb * nb) / NW
+        algo = outs * (out_bytes + 16.0 * (2 * M + 1) / float(wl.kgrid[0]))
         if r.get("form") == "mixed" or 2 * M + 1 <= 9:
             # the double-float kernel (k_axis_dft_df, FP32 pipe): its floor is the HBM traffic
             peak = peaks.get("hbm_gbs")
@@ -855,8 +859,9 @@ def run_libeph(args):
                     "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak if peak else None,
                     "algorithmic_bytes": algo, "outputs_per_launch": outs,
                     "fp64_equivalent_tflops": ach / 1e12, "flop_per_output": 4 * M + 2,
-                    "note": "algorithmic bytes: the slot columns read once, the outputs written once (16 B each); "
-                            "the FP64 kernel k_axis_dft ran this stage at 75 % of the FP64 peak",
+                    "note": "algorithmic bytes: the slot columns read once (16 B), the outputs written once (16 B; "
+                            "the mixed form's G3 columns 8 B, complex64 for the band rotation); the FP64 kernel "
+                            "k_axis_dft ran this stage at 75 % of the FP64 peak",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs, measured" if peak else "unavailable"}
         return {"bound": "alu", "kernel": "k_axis_dft (axis 1 of the sum-factorised Re->k contraction)",
                 "achieved": ach / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
@@ -931,7 +936,7 @@ def run_libeph(args):
                                    for k, wi, f64 in ks]})
         return out
 
-    def roof_band_tc(r, g3_bytes, fp64=False):
+    def roof_band_tc(r, g3_bytes, fp64=False, grid=False):
         # the fused tensor-core band rotation (k_band_tc_small, mixed; k_band_tc_small64, FP64 form)
         # against HBM: G3 rows in (complex128 from the FP64 grid transforms, complex64 from the
         # tensor-core contraction), V_{k+q} per pair and V_k per tile of pairs (two q at one k for
@@ -944,7 +949,10 @@ def run_libeph(args):
         t = bd_ms * 1e-3
         ach = per_pair * pairs / t if t else None
         peak = peaks.get("hbm_gbs")
-        key = ("k_band_tc_small64" if fp64 else "k_band_tc_small", args.workload, QB, "grid" if g3_bytes == 16.0 else "list")
+        # traffic per pair from the 24^3 captures: the FP64 kernel on the grid path; the mixed kernel's
+        # capture read complex128 G3, which its grid path no longer does (complex64 from axis 1)
+        key = ("k_band_tc_small64" if fp64 else "k_band_tc_small", args.workload, QB,
+               "grid" if (g3_bytes == 16.0 and not grid) else ("grid_c64" if grid else "list"))
         tr = TRAFFIC_PER_UNIT.get(key)
         return {"bound": "hbm",
                 "kernel": "k_band_tc_small64 (tcgen05 kind::f16, six-digit operands, exact level sums, FP64 accuracy, "
@@ -1069,7 +1077,7 @@ def run_libeph(args):
                              "gpu_launches": m["launches"], "clocks": m["clocks"]}
             mst = {k: v[0] for k, v in m["prof"].items()}
             if use_grid:
-                sr = {"eig": roof_eig(m, "mixed"), "ft_k": roof_axis(m), "band": roof_band_tc(m, 16.0)}
+                sr = {"eig": roof_eig(m, "mixed"), "ft_k": roof_axis(m), "band": roof_band_tc(m, 8.0, grid=True)}
                 line["mixed"]["roofline"] = sr[max(("eig", "ft_k", "band"), key=lambda k: mst.get(k, 0.0))]
                 line["mixed"]["stage_rooflines"] = sr
             else:

@@ -159,6 +159,11 @@ struct eph_ctx {
   double gshift[3] = {0.0, 0.0, 0.0};
   DBuf rebox, E1, E2, E3, Wbox, S1, S2;
   DBuf aS2, aS1, aS0;  // adjoint of the product-grid transforms: after axis 1, axis 2, axis 3
+  // mixed form on the grid path: the G3 columns of the k tile as complex64 [q][k][nm nb^2] (axis 1
+  // writes them there for the forward's band rotation, which needs FP32 only); g3f_tile: the current
+  // tile's G3 is there, not in Y
+  DBuf G3g;
+  bool g3f_tile = false;
   long long launches = 0;
   std::string err;
   // per-stage event timing
@@ -386,7 +391,7 @@ void eph_destroy(eph_ctx* ctx) {
                   &ctx->D, &ctx->lamq, &ctx->evq, &ctx->omq, &ctx->uq, &ctx->G1, &ctx->W, &ctx->Y,
                   &ctx->eps_tile, &ctx->Ukq, &ctx->g_stage, &ctx->wk, &ctx->G2bar, &ctx->G1bar,
                   &ctx->Lpair, &ctx->Lacc, &ctx->grad, &ctx->Ahi, &ctx->Alo, &ctx->Bhi, &ctx->Blo,
-                  &ctx->G3f, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut, &ctx->eigA, &ctx->eigW, &ctx->eigV, &ctx->tcband,
+                  &ctx->G3f, &ctx->G3g, &ctx->Hkq, &ctx->g_stage32, &ctx->DA, &ctx->DB, &ctx->sB, &ctx->jwork, &ctx->ut, &ctx->eigA, &ctx->eigW, &ctx->eigV, &ctx->tcband,
                   &ctx->Tbuf, &ctx->wqb, &ctx->lwpart, &ctx->lwacc, &ctx->rebox, &ctx->E1,
                   &ctx->E2, &ctx->E3, &ctx->Wbox, &ctx->S1, &ctx->S2, &ctx->Pku, &ctx->Ppu, &ctx->mfac, &ctx->scr_flag, &ctx->scr_pos, &ctx->scr_tot,
                   &ctx->scr_idx, &ctx->scr_k, &ctx->scr_count, &ctx->DBH, &ctx->sBH, &ctx->Hpair, &ctx->g1in,
@@ -993,12 +998,20 @@ int tc_mode_rotate(eph_ctx* ctx, int iq, const double2* G1, double2* Wq, long NW
 // ~2^-47 of each term, grows with the slot count B: the FP64 form takes it for B <= 9 (the
 // silicon box, B = 7: 9e-14 of the pair maximum against DFMA) and keeps DFMA beyond (the MoS2 box,
 // B = 13, measured 5.9e-13, too close to the form's 1e-12); the mixed form takes it for any B.
-cudaError_t axis_dft(eph_ctx* ctx, const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
-                     int nj, int paired, double2* out, long sa_out) {
+// the double-float kernel takes the transform: paired, whole axis, its phase table in 48 KB of shared
+// memory, and accurate enough for the form (FP64: boxes of at most 9 slots per axis)
+bool axis_df(const eph_ctx* ctx, int B, int N, int j0, int nj, int paired) {
   const size_t df_smem = (size_t)(N / 2 + 1) * (B > 1 ? (B - 1) / 2 : 1) * 16;
   const bool df_ok = ctx->opt.form == EPH_FORM_MIXED || B <= 9;
-  if (paired && df_ok && !ctx->opt.gemm_alu && j0 == 0 && nj == N && df_smem <= 48 * 1024)
-    return eph::launch_axis_dft_df(in, sa_in, A, C, B, E, N, out, sa_out, ctx->stream);
+  return paired && df_ok && !ctx->opt.gemm_alu && j0 == 0 && nj == N && df_smem <= 48 * 1024;
+}
+// out32 (double-float kernel only): columns c mod nw >= nd as complex64, see launch_axis_dft_df
+cudaError_t axis_dft(eph_ctx* ctx, const double2* in, long sa_in, int A, long C, int B, const double2* E, int N, int j0,
+                     int nj, int paired, double2* out, long sa_out, int nw = 1, int nd = 1, float2* out32 = nullptr,
+                     long sa_out32 = 0) {
+  if (axis_df(ctx, B, N, j0, nj, paired))
+    return eph::launch_axis_dft_df(in, sa_in, A, C, B, E, N, out, sa_out, ctx->stream, nw, nd, out32, sa_out32);
+  if (out32) return cudaErrorInvalidValue;
   return eph::launch_axis_dft(in, sa_in, A, C, B, E, N, j0, nj, paired, out, sa_out, ctx->stream);
 }
 
@@ -1127,7 +1140,12 @@ int band_rotate(eph_ctx* ctx, const QPlan& p, int nqb, int nkt, long k0, double2
   const double2* Uk = as<double2>(ctx->Uk) + k0 * nb2;
   const bool mixed = ctx->opt.form == EPH_FORM_MIXED;  // complex64 g, sgq in elements
   if (mixed && !ctx->big) {
-    if (small_band_tc(ctx))
+    if (small_band_tc(ctx) && ctx->g3f_tile)  // G3 as complex64 rows from the axis-1 transform
+      EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc_small(as<float2>(ctx->G3g) + (long)iq0 * nkt * (p.NW - nb2), 1,
+                                                             p.NW - nb2, Ukq, Uk, nqb, nkt, nm, nb,
+                                                             reinterpret_cast<float2*>(out), sgq, keep,
+                                                             ctx->status + 1, ctx->stream));
+    else if (small_band_tc(ctx))
       EPH_LAUNCH_S(EPH_STAGE_BAND, eph::launch_band_tc_small(Y + nb2, 0, p.NW, Ukq, Uk, nqb, nkt, nm, nb,
                                                              reinterpret_cast<float2*>(out), sgq, keep,
                                                              ctx->status + 1, ctx->stream));
@@ -1216,16 +1234,29 @@ int tc_rek_tile(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
   return EPH_OK;
 }
 
-int k_tile_forward(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt) {
+// want_g3f: the caller's band rotation takes complex64 G3 (the mixed form's forward): where the
+// double-float axis kernel runs and the rotation is the fused tensor-core kernel, axis 1 writes the
+// G3 columns to G3g (ctx->g3f_tile)
+int k_tile_forward(eph_ctx* ctx, const QPlan& p, int nqb, long k0, int nkt, bool want_g3f = false) {
   const int nb = ctx->nb, ne = ctx->ne, nb2 = nb * nb;
   double2* Y = as<double2>(ctx->Y);
+  ctx->g3f_tile = false;
   if (ctx->has_grid) {  // axis-1 transform of the slabs j1 in [j0, j0 + nj) (tiles are whole slabs)
     const long slab = (long)ctx->gn[1] * ctx->gn[2];
     const int j0 = (int)(k0 / slab), nj = (int)(nkt / slab), B1 = ctx->bext[0], N1 = ctx->gn[0];
     const long C = slab * p.NW;
     const int paired = ctx->gshift[0] == 0.0 && j0 == 0 && nj == N1;
+    const bool g3f = want_g3f && ctx->opt.form == EPH_FORM_MIXED && !ctx->big && small_band_tc(ctx) &&
+                     axis_df(ctx, B1, N1, j0, nj, paired);
+    float2* G3g = nullptr;
+    if (g3f) {
+      EPH_TRY(ensure(ctx, ctx->G3g, (size_t)p.QB * p.KT * (p.NW - nb2) * sizeof(float2)));
+      G3g = as<float2>(ctx->G3g);
+    }
     EPH_LAUNCH_S(EPH_STAGE_FT_K, axis_dft(ctx, as<double2>(ctx->S2), (long)B1 * C, nqb, C, B1, as<double2>(ctx->E1),
-                                          N1, j0, nj, paired, Y, (long)nkt * p.NW));
+                                          N1, j0, nj, paired, Y, (long)nkt * p.NW, (int)p.NW, nb2, G3g,
+                                          (long)nkt * (p.NW - nb2)));
+    ctx->g3f_tile = g3f;
   } else if (use_tc_rek(ctx)) {
     EPH_TRY(tc_rek_tile(ctx, p, nqb, k0, nkt));
   } else {
@@ -1519,7 +1550,7 @@ int interp_fp64(eph_ctx* ctx, int nq, const double* qpts, double* eps_kq, double
                              ctx->stream));
     for (long k0 = 0; k0 < nk; k0 += p.KT) {
       const int nkt = (int)((nk - k0 < p.KT) ? nk - k0 : p.KT);
-      EPH_TRY(k_tile_forward(ctx, p, nqb, k0, nkt));
+      EPH_TRY(k_tile_forward(ctx, p, nqb, k0, nkt, g != nullptr));
       if (eps_kq && !staged)
         for (int iq = 0; iq < nqb; ++iq)  // one contiguous copy per q (rows of the tile)
           EPH_CK(cudaMemcpyAsync(eps_kq + ((long)(q0 + iq) * nk + k0) * nb,

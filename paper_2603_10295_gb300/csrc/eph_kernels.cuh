@@ -144,9 +144,12 @@ cudaError_t launch_axis_dft(const double2* in, long sa_in, int A, long C, int B,
                             int nj, int paired, double2* out, long sa_out, cudaStream_t st);
 // The paired transform (whole unshifted axis, j0 = 0, nj = N) in double-float arithmetic on the
 // FP32 pipe (~2^-46 of each output's largest term; ~2 FP64 operations per output for the splits
-// and joins instead of ~8).
+// and joins instead of ~8).  With out32 (C a multiple of nw): the columns c with c mod nw >= nd go
+// to out32[a][j][c / nw][c mod nw - nd] as complex64 (a stride sa_out32, rows of nw - nd), rounded
+// from the double-float sums without FP64 joins; the others to out as before.
 cudaError_t launch_axis_dft_df(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N,
-                               double2* out, long sa_out, cudaStream_t st);
+                               double2* out, long sa_out, cudaStream_t st, int nw = 1, int nd = 1,
+                               float2* out32 = nullptr, long sa_out32 = 0);
 
 // ---- energy-window prescreening (screen.cu) ------------------------------------------------
 // idx[0..*count) = ascending k with some eps[k][n] in [e_lo, e_hi]; flag, pos [nk], tot [ceil(nk/1024)]

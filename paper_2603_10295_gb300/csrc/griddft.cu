@@ -175,6 +175,14 @@ __device__ __forceinline__ void df_fma(float& S, float& T, DF a, DF b) {
   S = s;
   T = __fadd_rn(T, __fadd_rn(e, t));
 }
+// (S1, T1) + sg (S2, T2) rounded to FP32 (sg = +-1): the head sum by a two-sum, no FP64 operation
+__device__ __forceinline__ float df_addf(float S1, float T1, float S2, float T2, float sg) {
+  const float b2 = sg * S2;
+  const float s = __fadd_rn(S1, b2);
+  const float bb = __fsub_rn(s, S1);
+  const float e = __fadd_rn(__fsub_rn(S1, __fsub_rn(s, bb)), __fsub_rn(b2, bb));
+  return __fadd_rn(s, __fadd_rn(__fadd_rn(T1, sg * T2), e));
+}
 // (S1, T1) + sg (S2, T2) joined to a double (sg = +-1)
 __device__ __forceinline__ double df_addj(float S1, float T1, float S2, float T2, float sg) {
   const float b2 = sg * S2;
@@ -185,10 +193,14 @@ __device__ __forceinline__ double df_addj(float S1, float T1, float S2, float T2
 }
 }  // namespace
 
+// With out32, column c of every row of nw columns whose index c mod nw is >= nd is written as
+// complex64 to out32[a][j][c / nw][c mod nw - nd] (rows of nw - nd) instead of to out: the
+// consumer of those columns needs FP32 only, and they skip the FP64 joins.
 template <int BMAX>
 __global__ void __launch_bounds__(256) k_axis_dft_df(const double2* __restrict__ in, long sa_in, long C,
                                                      const double2* __restrict__ E, int N,
-                                                     double2* __restrict__ out, long sa_out) {
+                                                     double2* __restrict__ out, long sa_out, int nw, int nd,
+                                                     float2* __restrict__ out32, long sa_out32) {
   constexpr int MM = (BMAX - 1) / 2;
   extern __shared__ float4 ef[];  // [N / 2 + 1][MM]: (cos hi, cos lo, sin hi, sin lo) of slot 2m - 1
   const int a = blockIdx.y;
@@ -218,6 +230,10 @@ __global__ void __launch_bounds__(256) k_axis_dft_df(const double2* __restrict__
     }
   }
   double2* dst = out + (long)a * sa_out + c;
+  const int cw = out32 ? (int)(c % nw) : 0;
+  const bool f32o = out32 != nullptr && cw >= nd;
+  const long C32 = out32 ? (C / nw) * (nw - nd) : 0;
+  float2* dst32 = f32o ? out32 + (long)a * sa_out32 + (c / nw) * (nw - nd) + (cw - nd) : nullptr;
   for (int j = 0; 2 * j <= N; ++j) {
     float arS = x0r.h, arT = x0r.l, aiS = x0i.h, aiT = x0i.l, brS = 0.f, brT = 0.f, biS = 0.f, biT = 0.f;
 #pragma unroll
@@ -229,22 +245,30 @@ __global__ void __launch_bounds__(256) k_axis_dft_df(const double2* __restrict__
       df_fma(brS, brT, sm, wr[m]);
       df_fma(biS, biT, sm, wi[m]);
     }
-    dst[(long)j * C] = make_double2(df_addj(arS, arT, biS, biT, -1.f), df_addj(aiS, aiT, brS, brT, 1.f));
     const int jm = N - j;
-    if (j != 0 && jm != j)
-      dst[(long)jm * C] = make_double2(df_addj(arS, arT, biS, biT, 1.f), df_addj(aiS, aiT, brS, brT, -1.f));
+    if (f32o) {
+      dst32[(long)j * C32] = make_float2(df_addf(arS, arT, biS, biT, -1.f), df_addf(aiS, aiT, brS, brT, 1.f));
+      if (j != 0 && jm != j)
+        dst32[(long)jm * C32] = make_float2(df_addf(arS, arT, biS, biT, 1.f), df_addf(aiS, aiT, brS, brT, -1.f));
+    } else {
+      dst[(long)j * C] = make_double2(df_addj(arS, arT, biS, biT, -1.f), df_addj(aiS, aiT, brS, brT, 1.f));
+      if (j != 0 && jm != j)
+        dst[(long)jm * C] = make_double2(df_addj(arS, arT, biS, biT, 1.f), df_addj(aiS, aiT, brS, brT, -1.f));
+    }
   }
 }
 
 cudaError_t launch_axis_dft_df(const double2* in, long sa_in, int A, long C, int B, const double2* E, int N,
-                               double2* out, long sa_out, cudaStream_t st) {
+                               double2* out, long sa_out, cudaStream_t st, int nw, int nd, float2* out32,
+                               long sa_out32) {
   if (A <= 0 || C <= 0) return cudaSuccess;
   if (B < 1 || B > 33 || (B & 1) == 0 || A > 65535) return cudaErrorInvalidValue;
+  if (out32 && (nw < 1 || nd < 0 || nd > nw || C % nw != 0)) return cudaErrorInvalidValue;
   const size_t smem = (size_t)(N / 2 + 1) * ((B - 1) / 2 > 0 ? (B - 1) / 2 : 1) * sizeof(float4);
   if (smem > 48 * 1024) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((C + 255) / 256), (unsigned)A, 1);
   auto go = [&](auto kern) -> cudaError_t {
-    kern<<<grid, 256, smem, st>>>(in, sa_in, C, E, N, out, sa_out), note_launch();
+    kern<<<grid, 256, smem, st>>>(in, sa_in, C, E, N, out, sa_out, nw, nd, out32, sa_out32), note_launch();
     return cudaGetLastError();
   };
   switch (B) {
