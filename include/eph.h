@@ -76,9 +76,10 @@ typedef struct eph_options {
   int mixed_scheme;  /* mixed form only: 0 = fixed-point BF16 digits (3 for the phases, 4 for g)
                         with exact FP32 tensor-core accumulation (default; needs 2*ne <= 1024),
                         1 = two-term split TF32 (3 products) */
-  int eig_plain_fp64; /* 0 (default): FP32 Jacobi sweeps, then FP64 refinement to full FP64
-                         accuracy (Ogita-Aishima steps for n <= 12; plain FP64 sweeps for n = 13..16;
-                         Newton-Schulz, A' = V^H A V and FP64 polish sweeps for n > 16);
+  int eig_plain_fp64; /* 0 (default): FP32 Jacobi sweeps, then refinement to full FP64 accuracy
+                         (n <= 12: Ogita-Aishima steps, the first in double-float on the FP32 pipe,
+                         the last in FP64; plain FP64 sweeps for n = 13..16; Newton-Schulz,
+                         A' = V^H A V and FP64 polish sweeps for n > 16);
                          1: plain FP64 Jacobi sweeps only */
   int async;          /* 1: eph_interp_q only enqueues work (no host synchronisation, no event
                          timing); its status is read by eph_sync.  With device pointers a sequence

@@ -402,26 +402,30 @@ __global__ void __launch_bounds__(128) k_jacobi(const double2* __restrict__ A, l
   }
 }
 
-// FP32-preconditioned variant: the same sweeps first run in FP32 (64x the FP64 rate on
-// GB300) to an off-diagonal norm of ~1e-6 ||A||, then the FP32 eigenvectors X are refined
-// in FP64 by the Ogita-Aishima iteration (Ogita & Aishima, Japan J. Indust. Appl. Math. 35,
-// 2018), written for Hermitian A with the correction split into Hermitian and
-// anti-Hermitian parts:
+// FP32-preconditioned variant, two kernels: k_jacobi_f32 runs the same sweeps in FP32 (64x the
+// FP64 rate on GB300) to an off-diagonal norm of ~1e-6 ||A||; k_jacobi_mixed refines its
+// eigenvectors X by the Ogita-Aishima iteration (Ogita & Aishima, Japan J. Indust. Appl. Math.
+// 35, 2018), written for Hermitian A with the correction split into Hermitian and anti-Hermitian
+// parts:
 //   R = I - X^H X,  S = X^H A X,  lam_j = S_jj / (X^H X)_jj,
 //   K_ij = (S_ij + (lam_i + lam_j) R_ij / 2) / (lam_j - lam_i)  (K^H = -K, one numerator per pair),
 //   X <- X (I + R/2 + K),
 // which makes X unitary and A-diagonal to second order in |R/2 + K| (the quadratic step of
-// Newton's method for the eigendecomposition).  The FP64 work per step is three products
-// of n^3 / 2 to n^3 complex multiply-adds (the Hermitian X^H X and X^H (A X) on half of
-// the pairs); the update X (R/2 + K), a small correction, runs in FP32.  lam_j plus the
+// Newton's method for the eigendecomposition).  The work per step is three products of n^3 / 2
+// to n^3 complex multiply-adds (A X, and the Hermitian X^H X and X^H (A X) on half of the
+// pairs); the update X (R/2 + K), a small correction, runs in FP32.  lam_j plus the
 // second-order shift sum_i |K_ij|^2 (lam_j - lam_i) is accurate to third order.
-// A step is final once every |(R/2 + K)_ij| <= th (X then exact to th^2): th = 1e-8 for
-// the FP64 eigendecomposition (two steps from FP32), 1e-4 when eigenvectors are needed to
-// ~1e-8 and eigenvalues to 1e-12 ||A|| (one step).  Pairs whose first-order angle would
-// exceed 1e-3 (near-degenerate relative to the FP32 accuracy) are left out of K; if such a
-// pair still couples above rounding level (4e-15 ||A||_F; 1e-11 for the looser target)
-// after three steps, the warp falls back to the robust sequence: two Newton-Schulz steps,
-// A' = V^H A V and FP64 Jacobi sweeps to polish_tol ||A||_F with a first-order finish.
+// The first step forms the products in double-float on the FP32 pipe (~2^-47 of the largest
+// term): from the FP32 estimate it only has to reach ~1e-12.  Later steps use FP64 products,
+// except for the looser target below, which stays in double-float.
+// A step is final once every |(R/2 + K)_ij| <= th (X then exact to th^2): th = 1e-8 for the
+// FP64 eigendecomposition, and there only after an FP64 step (a double-float step then an FP64
+// step from FP32); 1e-4 when eigenvectors are needed to ~1e-8 and eigenvalues to 1e-12 ||A||
+// (one double-float step).  Pairs whose first-order angle would exceed 1e-3 (near-degenerate
+// relative to the FP32 accuracy) are left out of K; if such a pair still couples above rounding
+// level (4e-15 ||A||_F; 1e-11 for the looser target) after three steps, the warp falls back to
+// the robust sequence: two Newton-Schulz steps, A' = V^H A V and FP64 Jacobi sweeps to
+// polish_tol ||A||_F with a first-order finish.
 // Dynamic shared memory of k_jacobi_mixed<np> for its four warps: per warp the A entries of its
 // 32 / np matrices as double2, double (3M pre-sums) and float4 (double-float split), then per lane
 // np float4 + np float2 (w = A x_j of a double-float step) and np / 2 + 1 float4 (pair products).
