@@ -125,3 +125,16 @@ def test_device_pointers_and_errors(ctxs):
     with pytest.raises(binding.EphError) as ei:
         ctx.eph_eigh(10, 33, dA, dw, dA)
     assert ei.value.code == binding.EPH_EINVAL
+
+
+@pytest.mark.parametrize("n,plain,kernels", [(8, False, 2), (11, False, 2), (14, False, 1), (8, True, 1)])
+def test_launch_count_is_the_kernels_launched(n, plain, kernels):
+    # the context counts every kernel each of its calls enqueues (the bench's gpu_launches):
+    # n <= 12 runs the FP32 sweeps and the refinement as two kernels, n = 13..16 and the plain
+    # FP64 option one
+    wl = synth.make_workload("si_tiny", nk=4, nq=2)
+    ctx = binding.Context.from_workload(wl, eig_plain_fp64=plain)
+    A = rand_herm(np.random.default_rng(n), 40, n)
+    before = ctx.launches()
+    ctx.eigh(A)
+    assert ctx.launches() - before == kernels
