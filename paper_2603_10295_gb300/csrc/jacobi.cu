@@ -434,8 +434,10 @@ constexpr size_t jm_smem_bytes(int np) {
 }
 
 // x 2^s by an exponent add (integer operations: on GB300 every FP64 instruction costs the FP64
-// pipe ~64 issue slots); zero, subnormal inputs and results below 2^-1022 give 0
+// pipe ~64 issue slots); s = 0 returns x, otherwise zero, subnormal inputs and results below
+// 2^-1022 give 0
 __device__ __forceinline__ double scale2_i(double x, int s) {
+  if (s == 0) return x;
   const long long b = __double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7FF);
   if (e == 0 || e + s <= 0) return 0.0;
