@@ -43,7 +43,7 @@ enum eph_status {
   EPH_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
   EPH_ENOTCONV = -4,  /* a batched Jacobi eigensolve hit its sweep cap */
   EPH_ESTATE = -5,    /* call out of order (e.g. eph_interp_q before eph_set_k) */
-  EPH_ENOTSUP = -6    /* size or form not supported by this build */
+  EPH_ENOTSUP = -6    /* size or form the library does not support */
 };
 
 enum eph_form {
