@@ -1131,15 +1131,21 @@ def run_libeph(args):
         for i in range(args.warmup):
             hctx.eph_interp_q(QB, q_h[i * QB:(i + 1) * QB], *outs[i % len(outs)])
         hctx.eph_sync()
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-            torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(args.warmup, nsteps):
-            hctx.eph_interp_q(QB, q_h[i * QB:(i + 1) * QB], *outs[i % len(outs)])
-        hctx.eph_sync()
-        t_e2e = time.perf_counter() - t0
+        # three timed passes over the same K steps, the median reported: the copies share the
+        # host's memory and link with other tenants, and single passes of the same code have
+        # ranged over 1.6x
+        passes = []
+        for _ in range(3):
+            if world > 1:
+                import torch.distributed as dist
+                dist.barrier()
+                torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(args.warmup, nsteps):
+                hctx.eph_interp_q(QB, q_h[i * QB:(i + 1) * QB], *outs[i % len(outs)])
+            hctx.eph_sync()
+            passes.append(time.perf_counter() - t0)
+        t_e2e = sorted(passes)[1]
         hctx.close()
         if cpus and old_aff is not None:
             try:
@@ -1157,7 +1163,9 @@ def run_libeph(args):
                "d2h_bytes_per_step": g_h.numel() * g_h.element_size() + ekq_h.numel() * 8 + om_h.numel() * 8,
                "ms_per_step": 1e3 * t_e2e / args.steps, "k_setup_ms": 1e3 * t_setk,
                "host_numa_node": node, "d2h_gbs_effective": (g_h.numel() * g_h.element_size() + ekq_h.numel() * 8)
-               * args.steps / t_e2e / 1e9}
+               * args.steps / t_e2e / 1e9,
+               "timing": "median of 3 timed passes of the K steps",
+               "ms_per_step_passes": [1e3 * x / args.steps for x in passes]}
         del g_h
         return out
 
