@@ -1069,8 +1069,9 @@ def run_libeph(args):
             line["mixed"] = {"value": m["value"], "unit": UNIT, "ms_per_step": m["ms_per_step"],
                              "k_path": line["config"]["k_path"],
                              "gain_vs_fp64": m["value"] / head["value"],
-                             "dtype": "f64 Re->k and eigensolve refinement, tensor-core (bf16 digit) band rotation "
-                                      "and Eq. 9, c64 g" if use_grid else "bf16 digits / f32 accumulate",
+                             "dtype": "double-float (FP32 pipe) Re->k axis transforms and eigensolve refinement, "
+                                      "tensor-core (bf16 digit) band rotation and Eq. 9, c64 g" if use_grid
+                                      else "bf16 digits / f32 accumulate",
                              "rel_err_bar": "<= 1e-6 on |g|^2 subspace sums (tests/test_gpu_mixed.py, "
                                             "tests/test_gpu_grid.py); eps, omega <= 1e-10",
                              "stage_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in m["prof"].items()},
