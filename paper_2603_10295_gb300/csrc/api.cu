@@ -1500,6 +1500,11 @@ int prepare_fp64(eph_ctx* ctx, int nq, bool want_g, QPlan* out) {
     EPH_TRY(big_workspace(ctx, p));
     if (use_band_tc(ctx)) EPH_TRY(ensure(ctx, ctx->tcband, band_tc_bytes(ctx, (long)p.QB * p.KT, (int)p.KT)));
   }
+  // the mixed form's forward on a single whole-axis grid tile writes its G3 as complex64
+  // (k_tile_forward): allocated here too, so that a graph captured after eph_reserve allocates nothing
+  if (want_g && ctx->opt.form == EPH_FORM_MIXED && !ctx->big && ctx->has_grid && small_band_tc(ctx) &&
+      p.KT >= ctx->nk && ctx->gshift[0] == 0.0 && axis_df(ctx, ctx->bext[0], ctx->gn[0], 0, ctx->gn[0], 1))
+    EPH_TRY(ensure(ctx, ctx->G3g, (size_t)p.QB * p.KT * (p.NW - ctx->nb * ctx->nb) * sizeof(float2)));
   if (host && want_g) {
     const size_t gb = (size_t)p.QB * p.KT * p.gcols * sizeof(double2);
     EPH_TRY(ensure(ctx, ctx->g_stage, gb));
